@@ -171,6 +171,13 @@ int or_m2l(int order, const double* M, const double* r0, double* out) {
     return 0;
 }
 
+int or_m2l_map(int order, const double* r0, double* sqrtR, double* map3) {
+    const tpsa_ctx* t = tpsa_get(order);
+    if (!t) return -1;
+    op_m2l_map(t, r0, sqrtR, map3);
+    return 0;
+}
+
 int or_m2l_matrix(int order, const double* r0, double* K) {
     const tpsa_ctx* t = tpsa_get(order);
     if (!t) return -1;

@@ -65,6 +65,8 @@ int or_p2m(int order, int64_t n, const double* s, const double* q, double* M);
 int or_m2m(int order, const double* M, const double* r0, double* out);
 /* M2L, Eq. 5 by DA composition: out += sqrt(R) (M o M2); r0 = target centre - source centre */
 int or_m2l(int order, const double* M, const double* r0, double* out);
+/* the M2L transfer map of Eq. 5: sqrt(R) and the three components of M2 (packed) */
+int or_m2l_map(int order, const double* r0, double* sqrtR, double* map3);
 /* M2L as a matrix: K[beta*nc + alpha] = coefficient beta of M2L(e_alpha); exact by linearity */
 int or_m2l_matrix(int order, const double* r0, double* K);
 /* P2L, Eq. 6: L += sum_i q_i / |w_i + d'|, w_i = (target centre - source position)_i (n x 3) */

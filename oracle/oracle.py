@@ -56,6 +56,7 @@ def _load():
             "or_m2m": (c_int, [c_int, D, D, D]),
             "or_m2l": (c_int, [c_int, D, D, D]),
             "or_m2l_matrix": (c_int, [c_int, D, D]),
+            "or_m2l_map": (c_int, [c_int, D, D, D]),
             "or_p2l": (c_int, [c_int, c_i64, D, D, D]),
             "or_l2l": (c_int, [c_int, D, D, D]),
             "or_l2p": (c_int, [c_int, D, c_i64, D, D, D]),
@@ -174,6 +175,15 @@ def m2l(order, M, r0):
     out = np.zeros_like(M)
     _check(_load().or_m2l(order, _d(M), _d(r0), _d(out)), "m2l")
     return out
+
+
+def m2l_map(order, r0):
+    """(sqrt(R), M2 as a (3, ncoef) array) of Eq. 5."""
+    r0 = _f64(r0)
+    nc = ncoef(order)
+    sR, mp = np.zeros(nc), np.zeros(3 * nc)
+    _check(_load().or_m2l_map(order, _d(r0), _d(sR), _d(mp)), "m2l_map")
+    return sR, mp.reshape(3, nc)
 
 
 def m2l_matrix(order, r0):

@@ -1,0 +1,304 @@
+"""Emit straight-line C++/CUDA for the DA-FMM operators, one set per expansion order.
+
+For every order p this writes ``da_ops_p{p}.cuh`` with
+
+  p2m_o{p}(x, y, z, q, out)       P2M of one charge (Eq. 2) in scaled offsets
+  p2l_o{p}(X, Y, Z, q, out)       P2L of one charge (Eq. 6), w = centre - source, scaled
+  l2p_o{p}(L, x, y, z, ...)       L2P with gradient (Sec. 3.2)
+  m2p_o{p}(M, x, y, z, ...)       M2P with gradient (Sec. 3.2)
+  m2lmap_o{p}(X, Y, Z, inv, isq)  the M2L transfer-map factors (Eq. 5)
+
+and ``da_tables_p{p}.h`` with the level-independent M2M (Eq. 4, octant-reduced
+as in Sec. 3.3) and L2L (Eq. 7) matrices in compressed rows.
+
+Like the paper's parser, the emitter walks the symbolic coefficients term by
+term (sign, rational coefficient, powers of the base symbols), computes every
+distinct power product once (each as one multiplication of an already
+computed product) and emits each coefficient as a sum of rational multiples
+of those products.  The code is ``__host__ __device__`` so that a host build
+can be checked against the oracle without a GPU.
+"""
+import argparse
+import os
+import sys
+from fractions import Fraction
+
+if __package__ in (None, ""):
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.dirname(os.path.abspath(__file__)))))
+    from paper_2508_02626_gb300.gen import operators as ops  # noqa: E402
+    from paper_2508_02626_gb300.gen.sda import exponents, index, ncoef  # noqa: E402
+else:
+    from . import operators as ops
+    from .sda import exponents, index, ncoef
+
+MAXORD = 10
+
+
+def lit(fr):
+    """A rational as a C double literal (17 significant digits)."""
+    fr = Fraction(fr)
+    if fr.denominator == 1 and abs(fr.numerator) < 2 ** 53:
+        return "%d.0" % fr.numerator
+    return "%.17g" % (fr.numerator / fr.denominator)
+
+
+class MonoPlan:
+    """Power products of the base symbols, each built from an earlier one by one product."""
+
+    def __init__(self, syms, base_name, mono_set, base_expr):
+        self.syms = syms
+        self.name = {}
+        self.lines = []
+        zero = (0,) * len(syms)
+        need = set(mono_set)
+        need.add(zero)
+        # close the set under "remove one factor"
+        stack = list(need)
+        parent = {}
+        while stack:
+            e = stack.pop()
+            if e == zero or e in parent:
+                continue
+            best = None
+            for k in range(len(e)):
+                if e[k] > 0:
+                    pe = e[:k] + (e[k] - 1,) + e[k + 1:]
+                    if pe in need:
+                        best = (pe, k)
+                        break
+            if best is None:
+                k = next(k for k in range(len(e)) if e[k] > 0)
+                pe = e[:k] + (e[k] - 1,) + e[k + 1:]
+                need.add(pe)
+                stack.append(pe)
+                best = (pe, k)
+            parent[e] = best
+        order = sorted(need, key=lambda e: (sum(e), e))
+        cnt = 0
+        for e in order:
+            if e == zero:
+                self.name[e] = base_name
+                self.lines.append("const T %s = %s;" % (base_name, base_expr))
+                continue
+            pe, k = parent[e]
+            nm = "m%d" % cnt
+            cnt += 1
+            self.name[e] = nm
+            self.lines.append("const T %s = %s * %s;" % (nm, self.name[pe], syms[k]))
+        self.count = cnt
+
+
+def sum_expr(terms, nacc=1):
+    """terms: list of (Fraction coefficient, operand name).  Returns a C expression."""
+    parts = []
+    for c, nm in terms:
+        if c == 1:
+            parts.append("+ %s" % nm)
+        elif c == -1:
+            parts.append("- %s" % nm)
+        elif c > 0:
+            parts.append("+ T(%s) * %s" % (lit(c), nm))
+        else:
+            parts.append("- T(%s) * %s" % (lit(-c), nm))
+    if not parts:
+        return "T(0)"
+    s = " ".join(parts)
+    if s.startswith("+ "):
+        s = s[2:]
+    return s
+
+
+def emit_poly_outputs(name, p, syms, coefs, base_name, base_expr, args, pre_lines, out_scale=None):
+    mono = set()
+    for poly in coefs:
+        mono.update(poly.t.keys())
+    plan = MonoPlan(syms, base_name, mono, base_expr)
+    body = list(pre_lines) + plan.lines
+    nterm = 0
+    for k, poly in enumerate(coefs):
+        terms = [(c, plan.name[e]) for e, c in sorted(poly.t.items())]
+        nterm += len(terms)
+        body.append("out(%d, %s);" % (k, sum_expr(terms)))
+    head = "template <class T, class Out>\nDAFMM_HD DAFMM_INLINE void %s(%s, Out&& out) {\n" % (name, args)
+    return head + "".join("    %s\n" % l for l in body) + "}\n", plan.count + nterm
+
+
+def emit_eval(name, p, kind):
+    """L2P (kind='l2p') or M2P (kind='m2p') with gradient."""
+    ex = exponents(p)
+    nc = ncoef(p)
+    lines = []
+    if kind == "l2p":
+        args = "const Src& C, T x, T y, T z, T& phi, T& gx, T& gy, T& gz"
+        lines.append("const T u0 = x, u1 = y, u2 = z;")
+    else:
+        args = "const Src& C, T x, T y, T z, T& phi, T& gx, T& gy, T& gz"
+        lines += ["const T R2 = x * x + y * y + z * z;",
+                  "const T rho = dafmm_rcp(R2);",
+                  "const T nd = dafmm_sqrt(rho);",
+                  "const T u0 = x * rho, u1 = y * rho, u2 = z * rho;"]
+    # monomials u^e for |e| <= p
+    mname = {(0, 0, 0): None}
+    for i in range(1, nc):
+        e = ex[i]
+        v = 0 if e[0] else (1 if e[1] else 2)
+        pe = list(e)
+        pe[v] -= 1
+        pe = tuple(pe)
+        nm = "w%d" % i
+        src = mname[pe]
+        lines.append("const T %s = %s;" % (nm, ("u%d" % v) if src is None else "%s * u%d" % (src, v)))
+        mname[e] = nm
+
+    def acc_lines(var, terms):
+        # 4 interleaved partial sums for instruction-level parallelism
+        k = 4
+        out = []
+        for j in range(k):
+            out.append("T %s_%d = T(0);" % (var, j))
+        for t_i, (cf, cidx, mn) in enumerate(terms):
+            j = t_i % k
+            op = "C(%d)" % cidx
+            if cf != 1:
+                op = "T(%s) * %s" % (lit(cf), op)
+            if mn is None:
+                out.append("%s_%d += %s;" % (var, j, op))
+            else:
+                out.append("%s_%d = dafmm_fma(%s, %s, %s_%d);" % (var, j, op, mn, var, j))
+        out.append("const T %s = (%s_0 + %s_1) + (%s_2 + %s_3);" % (var, var, var, var, var))
+        return out
+
+    lines += acc_lines("F", [(1, i, mname[ex[i]]) for i in range(nc)])
+    for v, gv in enumerate(("G0", "G1", "G2")):
+        terms = []
+        for i in range(nc):
+            e = ex[i]
+            if e[v] == 0:
+                continue
+            pe = list(e)
+            pe[v] -= 1
+            terms.append((e[v], i, mname[tuple(pe)]))
+        if terms:
+            lines += acc_lines(gv, terms)
+        else:
+            lines.append("const T %s = T(0);" % gv)
+    if kind == "l2p":
+        lines += ["phi = F;", "gx = G0;", "gy = G1;", "gz = G2;"]
+    else:
+        # F(d) = |d| phi_M(d); grad_d = (d/|d|) phi_M + |d| grad phi_M;
+        # grad_s = J^T grad_d with J = rho I - 2 rho^2 s s^T
+        lines += ["phi = nd * F;",
+                  "const T fr = F * nd * R2;  /* phi_M / |d|, since 1/|d| = |s| = sqrt(R2) */",
+                  "const T a0 = u0 * fr + nd * G0, a1 = u1 * fr + nd * G1, a2 = u2 * fr + nd * G2;",
+                  "const T sa = x * a0 + y * a1 + z * a2;",
+                  "const T tw = T(2) * rho * rho * sa;",
+                  "gx = rho * a0 - tw * x;",
+                  "gy = rho * a1 - tw * y;",
+                  "gz = rho * a2 - tw * z;"]
+    head = "template <class T, class Src>\nDAFMM_HD DAFMM_INLINE void %s(%s) {\n" % (name, args)
+    return head + "".join("    %s\n" % l for l in lines) + "}\n"
+
+
+def csr_table(name, p, table, with_parity=True):
+    ex = exponents(p)
+    nc = ncoef(p)
+    rowptr, cols, vals, par = [0], [], [], []
+    for b in range(nc):
+        for a in range(nc):
+            v = table[b][a]
+            if v:
+                cols.append(a)
+                vals.append(v)
+                m = 0
+                for k in range(3):
+                    if (ex[b][k] + ex[a][k]) % 2:
+                        m |= 1 << k
+                par.append(m)
+        rowptr.append(len(cols))
+    out = []
+    out.append("static const int %s_nnz = %d;\n" % (name, len(cols)))
+    out.append("static const int %s_rowptr[%d] = {%s};\n" % (name, nc + 1, ",".join(map(str, rowptr))))
+    out.append("static const unsigned short %s_col[%d] = {%s};\n" % (name, max(1, len(cols)),
+                                                                   ",".join(map(str, cols)) or "0"))
+    out.append("static const unsigned char %s_par[%d] = {%s};\n" % (name, max(1, len(par)),
+                                                                  ",".join(map(str, par)) or "0"))
+    vl = []
+    for i, v in enumerate(vals):
+        vl.append(lit(v))
+    out.append("static const double %s_val[%d] = {\n%s};\n" % (name, max(1, len(vals)),
+                                                            ",\n".join(",".join(vl[i:i + 6]) for i in range(0, len(vl), 6)) or "0"))
+    return "".join(out), len(cols)
+
+
+HEADER = """// GENERATED by paper_2508_02626_gb300/gen/emit.py -- do not edit.
+// Straight-line DA-FMM operators of expansion order %(p)d (%(nc)d coefficients),
+// derived by symbolic DA from the paper's Eqs. 2, 5 and 6 and the evaluation of Sec. 3.2.
+"""
+
+
+def generate(p, outdir):
+    nc = ncoef(p)
+    parts = [HEADER % dict(p=p, nc=nc)]
+    parts.append("#pragma once\n#include \"../da_common.cuh\"\nnamespace dafmm {\nnamespace gen {\n\n")
+    stats = {}
+    syms, c = ops.p2m(p)
+    code, n = emit_poly_outputs(
+        "p2m_o%d" % p, p, ("x", "y", "z", "R2"), c, "qq", "q", "T x, T y, T z, T q",
+        ["const T R2 = x * x + y * y + z * z;"])
+    parts.append("// P2M, Eq. 2: out(k, q * coefficient k of (1 - 2 s.d + s^2 d^2)^(-1/2)), s = (x,y,z)\n")
+    parts.append(code + "\n")
+    stats["p2m"] = n
+    syms, c = ops.p2l(p)
+    code, n = emit_poly_outputs(
+        "p2l_o%d" % p, p, ("X", "Y", "Z", "rho"), c, "qir", "q * ir", "T X, T Y, T Z, T q",
+        ["const T R2 = X * X + Y * Y + Z * Z;", "const T ir = dafmm_rsqrt(R2);", "const T rho = ir * ir;"])
+    parts.append("// P2L, Eq. 6: out(k, q * coefficient k of 1/|w + d'|), w = (X,Y,Z)\n")
+    parts.append(code + "\n")
+    stats["p2l"] = n
+    parts.append("// L2P: phi = L(x), g = grad L(x) (Sec. 3.2)\n")
+    parts.append(emit_eval("l2p_o%d" % p, p, "l2p") + "\n")
+    parts.append("// M2P: phi = |d| M(d), d = s/|s|^2, g = grad_s phi (Sec. 3.2)\n")
+    parts.append(emit_eval("m2p_o%d" % p, p, "m2p") + "\n")
+    syms, inv, isq = ops.m2l_map(p)
+    code1, n1 = emit_poly_outputs(
+        "m2lmap_inv_o%d" % p, p, ("X", "Y", "Z", "rho"), inv, "one", "T(1)", "T X, T Y, T Z, T rho", [])
+    code2, n2 = emit_poly_outputs(
+        "m2lmap_isq_o%d" % p, p, ("X", "Y", "Z", "rho"), isq, "one", "T(1)", "T X, T Y, T Z, T rho", [])
+    parts.append("// M2L map, Eq. 5: |v+u|^2 = |v|^2 (1+t), t = rho (2 v.u + u.u), rho = 1/|v|^2;\n"
+                 "// m2lmap_inv: coefficients of (1+t)^-1, m2lmap_isq: of (1+t)^-1/2\n")
+    parts.append(code1 + "\n" + code2 + "\n")
+    stats["m2lmap"] = n1 + n2
+    parts.append("}  // namespace gen\n}  // namespace dafmm\n")
+    with open(os.path.join(outdir, "da_ops_p%d.cuh" % p), "w") as f:
+        f.write("".join(parts))
+
+    tparts = [HEADER % dict(p=p, nc=nc), "#pragma once\nnamespace dafmm {\nnamespace gen {\n\n"]
+    tparts.append("// M2M (Eq. 4) in scaled variables, child octant (0,0,0): M~'_b = sum T[b][a] M~_a.\n"
+                  "// Octant c flips the sign of entry (b,a) when popcount(par & c) is odd (Sec. 3.3).\n")
+    code, nnz = csr_table("m2m_o%d" % p, p, ops.m2m_scaled_table(p))
+    tparts.append(code)
+    stats["m2m_nnz"] = nnz
+    tparts.append("\n// L2L (Eq. 7) in scaled variables, child octant (0,0,0): L~'_b = sum T[b][a] L~_a.\n")
+    code, nnz = csr_table("l2l_o%d" % p, p, ops.l2l_scaled_table(p))
+    tparts.append(code)
+    stats["l2l_nnz"] = nnz
+    tparts.append("\n}  // namespace gen\n}  // namespace dafmm\n")
+    with open(os.path.join(outdir, "da_tables_p%d.h" % p), "w") as f:
+        f.write("".join(tparts))
+    return stats
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    ap.add_argument("--out", required=True)
+    ap.add_argument("--orders", default="0-%d" % MAXORD)
+    a = ap.parse_args(argv)
+    lo, hi = (int(x) for x in a.orders.split("-")) if "-" in a.orders else (int(a.orders),) * 2
+    os.makedirs(a.out, exist_ok=True)
+    for p in range(lo, hi + 1):
+        st = generate(p, a.out)
+        print("order %d: %s" % (p, st))
+
+
+if __name__ == "__main__":
+    main()

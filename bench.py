@@ -1,0 +1,333 @@
+"""Benchmark of the GB300 DA-FMM (Coulomb potential + field).
+
+One step = one dafmm_eval (P2M -> M2M -> M2L -> L2L -> L2P + P2P, the whole hot path) over
+the resident tree of the workload: N = 1,000,000 particles uniform in the unit cube,
+charges U[-1,1], uniform octree of depth 5, expansion order p = 8, seed 2002.
+
+Prints one JSON line (rank 0).  Under torchrun every rank runs an independent replica of
+the workload on its own GPU (independent solves shard with no data exchange); the value
+is the total particles of all ranks divided by the slowest rank's time.
+
+--impl reference times the CPU oracle (oracle/, plain C, all host cores) on a bounded
+sample of the same workload and reports its extrapolated full-solve rate.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "particles/s at rel err <=1e-7 (N=1M, p=8); served solves/s + p50/p99 latency"
+UNIT = "particles/s"
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def fp32_fma_peak_tflops(sm_mhz):
+    """FP32 FMA peak of a GB300: 152 SMs x 128 FP32 lanes x 2 flops per FMA x SM clock."""
+    return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def m2l_pairs_finest(depth):
+    s = 1 << depth
+    cand = (3 * (s // 2) - 2) * 4
+    near = 3 * s - 2
+    return cand ** 3 - near ** 3
+
+
+def run_ours(args, rank, world):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2508_02626_gb300 import binding as B
+    from paper_2508_02626_gb300 import workloads as W
+
+    local = int(os.environ.get("LOCAL_RANK", 0))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    cfg = W.C2
+    x, q, dom = W.make(cfg)
+    n, p, depth = cfg["n"], cfg["order"], cfg["uniform_depth"]
+    prec = B.PRECISIONS[args.precision]
+    B.load()
+    ctx = B.Context(local)
+    stream = torch.cuda.Stream(device=dev)
+    xt = torch.from_numpy(x).to(dev)
+    qt = torch.from_numpy(q).to(dev)
+    phi = torch.empty(n, dtype=torch.float64, device=dev)
+    E = torch.empty((n, 3), dtype=torch.float64, device=dev)
+    tree = ctx.build_tree(xt, qt, domain=dom, uniform_depth=depth, stream=stream)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 256 MB > L2
+    B.dafmm_set_profiling(ctx.h, True)
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            tree.eval(p, phi, E, precision=prec, stream=stream)
+    stream.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    times, phases = [], []
+    with torch.cuda.stream(stream):
+        for _ in range(args.steps):
+            flush.fill_(1.0)  # evict L2 between timed steps (outside the timed events)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            tree.eval(p, phi, E, precision=prec, stream=stream)
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+            phases.append(B.dafmm_last_phase_ms(ctx.h))
+    torch.cuda.synchronize()
+    ck = clocks.stop()
+    total_ms = float(np.sum(times))
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        dist.barrier()
+    value = n * args.steps * world / (total_ms / 1e3)
+    ph = {k: float(np.mean([d[k] for d in phases])) for k in phases[0]}
+
+    # end to end through the public API with host buffers: build_tree + eval per step,
+    # host->device copies of the step's inputs and device->host copies of the results
+    xp = torch.from_numpy(x).pin_memory()
+    qp = torch.from_numpy(q).pin_memory()
+    phi_h = torch.empty(n, dtype=torch.float64).pin_memory()
+    E_h = torch.empty((n, 3), dtype=torch.float64).pin_memory()
+    e2e_steps = max(2, min(args.steps, 5))
+    for _ in range(2):
+        tr = ctx.build_tree(xp, qp, domain=dom, uniform_depth=depth, stream=stream)
+        tr.eval(p, phi_h, E_h, precision=prec, stream=stream)
+        tr.free()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        tr = ctx.build_tree(xp, qp, domain=dom, uniform_depth=depth, stream=stream)
+        tr.eval(p, phi_h, E_h, precision=prec, stream=stream)
+        tr.free()
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    e2e_value = n * e2e_steps * world / e2e_s
+
+    peaks, peak_src = load_peaks()
+    sm_mhz = ck.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
+    nc = (p + 1) * (p + 2) * (p + 3) // 6
+    flops = 2.0 * nc * nc * m2l_pairs_finest(depth)
+    achieved = flops / (ph["m2l_finest"] / 1e3) / 1e12
+    if args.precision == "fp64":
+        peak = 1.25  # FP64 nominal, TFLOP/s
+        bound, peak_note = "alu", "FP64 nominal 1.25 TFLOP/s (no measured FP64 peak)"
+    else:
+        peak = fp32_fma_peak_tflops(peaks.get("sm_max_mhz", 2070.0))
+        bound, peak_note = "alu", "FP32 FMA: 152 SMs x 128 lanes x 2 x %.0f MHz" % peaks.get("sm_max_mhz", 2070.0)
+    roofline = {"bound": bound, "achieved": round(achieved, 3), "peak": round(peak, 3), "unit": "TFLOP/s",
+                "frac": round(achieved / peak, 4), "traffic": None, "kernel": "k_m2l (finest level)",
+                "peak_source": peak_note}
+
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": {"fp64": "f64", "mixed": "f32+f64", "fp32": "f32"}[args.precision],
+        "data": "synthetic (seeded uniform, PCG64 seed 2002)",
+        "config": {"workload": "uniform N=1e6, q~U[-1,1], octree depth 5, order p=8, theta=1",
+                   "precision": args.precision, "l2": "flushed between timed steps (256 MB write)",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "phases_ms": {k: round(v, 4) for k, v in ph.items() if k != "launches"},
+        "gpu_launches": int(ph["launches"]) * args.steps,
+        "roofline": roofline,
+        "clocks": ck,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": n * 4 * 8,
+                "d2h_bytes_per_step": n * 4 * 8, "steps": e2e_steps,
+                "includes": "dafmm_build_tree + dafmm_eval from pinned host buffers"},
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"], out["accuracy"] = cpu_baseline(x, q, dom, cfg, phi.cpu().numpy(), E.cpu().numpy())
+    tree.free()
+    ctx.close()
+    return out
+
+
+def cpu_baseline(x, q, dom, cfg, phi_gpu, E_gpu):
+    """The oracle FMM (plain C, all host cores) on the same tree and order, for the particles
+    of a sample of target leaves; the full-solve rate is extrapolated from the cost of the
+    upward pass (all particles) and the per-leaf cost of the sampled leaves.  The sampled
+    oracle results also give the GPU's error against the oracle and the direct sum."""
+    import oracle as O
+
+    n, p, depth = cfg["n"], cfg["order"], cfg["uniform_depth"]
+    rng = np.random.default_rng(123)
+    nleaf = 8 ** depth
+    scale = 2.0 ** depth
+    leaf = np.clip(np.floor(x * scale).astype(np.int64), 0, (1 << depth) - 1)
+    leaf_id = (leaf[:, 0] << (2 * depth)) | (leaf[:, 1] << depth) | leaf[:, 2]
+    picks = rng.choice(nleaf, 64, replace=False)
+    tg = np.sort(np.nonzero(np.isin(leaf_id, picks))[0])
+    one = np.sort(np.nonzero(leaf_id == picks[0])[0])
+    cores = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    O.fmm(x, q, dom, p, uniform_depth=depth, targets=one)
+    t_up = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    ref_phi, ref_E = O.fmm(x, q, dom, p, uniform_depth=depth, targets=tg)
+    t_s = time.perf_counter() - t0
+    per_leaf = max(t_s - t_up, 0.0) / (len(picks) - 1)
+    t_full = t_up + nleaf * per_leaf
+    d_phi, d_E = O.direct(x, q, targets=tg[:300])
+
+    def rel(a, b):
+        return float(np.sqrt(((a - b) ** 2).sum() / (b ** 2).sum()))
+
+    cpu = {"value": n / t_full, "unit": UNIT, "cores": cores, "kind": "oracle",
+           "sample": "oracle FMM over all %d particles' upward pass plus the %d particles of 64 random "
+                     "leaves (%.1f s + %.1f s); full solve extrapolated to %.0f s" % (n, len(tg), t_up, t_s, t_full)}
+    acc = {"targets": int(len(tg)),
+           "rel_l2_phi_vs_oracle": rel(phi_gpu[tg], ref_phi), "rel_l2_field_vs_oracle": rel(E_gpu[tg], ref_E),
+           "rel_l2_phi_vs_direct": rel(phi_gpu[tg[:300]], d_phi),
+           "oracle_rel_l2_phi_vs_direct": rel(ref_phi[:300], d_phi),
+           "rel_l2_field_vs_direct": rel(E_gpu[tg[:300]], d_E)}
+    return cpu, acc
+
+
+def run_reference(args, rank, world):
+    """CPU oracle arm: each step is the oracle FMM on the full workload for the particles of a
+    bounded sample of leaves; the reported rate is the extrapolated full-solve rate."""
+    import oracle as O
+    from paper_2508_02626_gb300 import workloads as W
+
+    cfg = W.C2
+    x, q, dom = W.make(cfg)
+    n, p, depth = cfg["n"], cfg["order"], cfg["uniform_depth"]
+    nleaf = 8 ** depth
+    leaf = np.clip(np.floor(x * 2.0 ** depth).astype(np.int64), 0, (1 << depth) - 1)
+    leaf_id = (leaf[:, 0] << (2 * depth)) | (leaf[:, 1] << depth) | leaf[:, 2]
+    rng = np.random.default_rng(7)
+    t_up = None
+    for _ in range(max(1, args.warmup)):
+        one = np.nonzero(leaf_id == rng.integers(nleaf))[0]
+        t0 = time.perf_counter()
+        O.fmm(x, q, dom, p, uniform_depth=depth, targets=one)
+        t_up = time.perf_counter() - t0 if t_up is None else min(t_up, time.perf_counter() - t0)
+    S = 16
+    ts = []
+    for _ in range(args.steps):
+        picks = rng.choice(nleaf, S, replace=False)
+        tg = np.nonzero(np.isin(leaf_id, picks))[0]
+        t0 = time.perf_counter()
+        O.fmm(x, q, dom, p, uniform_depth=depth, targets=tg)
+        ts.append(time.perf_counter() - t0)
+    per_leaf = max(float(np.mean(ts)) - t_up, 0.0) / (S - 1)
+    t_full = t_up + nleaf * per_leaf
+    value = n / t_full
+    cores = os.cpu_count() or 1
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_full * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded uniform, PCG64 seed 2002)",
+            "config": {"workload": "uniform N=1e6, q~U[-1,1], octree depth 5, order p=8, theta=1",
+                       "precision": "fp64", "l2": "n/a (CPU)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": "per step: oracle FMM upward pass over all particles plus the particles of "
+                                       "%d random leaves; full solve extrapolated" % S},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64", "fp32"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        print(json.dumps(run_reference(args, rank, world)))
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+        dist.init_process_group("nccl")
+    out = run_ours(args, rank, world)
+    if rank == 0:
+        print(json.dumps(out))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

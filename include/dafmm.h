@@ -1,0 +1,135 @@
+/*
+ * dafmm.h -- C ABI of the GB300 (sm_103a) DA-based fast multipole method for the
+ * Coulomb potential and field (arXiv 2508.02626, "Boosting the Efficiency of the
+ * Differential Algebra-based Fast Multipole Method Using Symbolic Differential
+ * Algebra").
+ *
+ * The method (paper Sec. 1-3): particles are grouped in an octree; far
+ * interactions go through Taylor (DA) expansions built by seven operators --
+ * P2M (Eq. 2), M2M (Eq. 4), M2L (Eq. 5), P2L (Eq. 6), L2L (Eq. 7), L2P and M2P
+ * (Sec. 3.2) -- and near interactions are summed pairwise (Sec. 1).  The
+ * operators run as straight-line code generated per expansion order by a
+ * symbolic DA (Sec. 3); M2L is batched over every well-separated box pair
+ * (at most 189 per box, Sec. 3.4) as dense contractions grouped by
+ * displacement.
+ *
+ * Conventions for every entry point
+ *   - Return value: DAFMM_OK (0) on success, a negative DAFMM_ERR_* code
+ *     otherwise; nothing aborts.  dafmm_last_error() gives a message.
+ *   - Pointers to particle data and outputs may be host or device memory
+ *     (detected per call).  The caller owns them; the library never keeps
+ *     them beyond the call, except that results are complete only once the
+ *     given stream has reached the call (host outputs: on return).
+ *   - Coordinates are row-major n x 3 doubles; charges n doubles.
+ *   - Potential phi_i = sum_{j != i, r_ij > 0} q_j / r_ij (Eq. 1, no Coulomb
+ *     constant); field E_i = -grad phi_i, n x 3 doubles, in the input order.
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream).
+ *   - The library owns trees and contexts until *_free / dafmm_destroy.
+ *   - One context must not be used from two host threads at the same time.
+ */
+#ifndef DAFMM_H
+#define DAFMM_H
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* return codes */
+#define DAFMM_OK 0
+#define DAFMM_ERR_INVALID_ARG (-1)
+#define DAFMM_ERR_UNSUPPORTED_ORDER (-2) /* order outside 0..10, the generated range (Sec. 3) */
+#define DAFMM_ERR_OVER_BUDGET (-3)       /* the context's HBM budget would be exceeded */
+#define DAFMM_ERR_CUDA (-4)              /* a CUDA runtime call failed */
+#define DAFMM_ERR_TIMEOUT (-5)           /* a bounded device wait gave up */
+#define DAFMM_ERR_UNSUPPORTED (-6)       /* a valid but unimplemented option (e.g. theta != 1) */
+#define DAFMM_ERR_NO_DEVICE (-7)
+
+/* arithmetic of an evaluation */
+#define DAFMM_FP64 0  /* every step in double precision */
+#define DAFMM_MIXED 1 /* FP32 bulk (P2M, M2L, L2P, P2P); FP64 derivative tensors, M2M/L2L, final sums */
+#define DAFMM_FP32 2  /* FP32 everywhere except the derivative tensors and the final sums */
+
+#define DAFMM_MAX_ORDER 10
+
+typedef struct dafmm_ctx dafmm_ctx;
+typedef struct dafmm_tree dafmm_tree;
+
+/* Create a context on CUDA device `device`.  hbm_budget_bytes caps the device memory the
+ * context may hold (0 = no cap).  *ctx receives the handle. */
+int dafmm_create(dafmm_ctx** ctx, int device, size_t hbm_budget_bytes);
+/* Release a context and every tree it owns. */
+void dafmm_destroy(dafmm_ctx* ctx);
+/* Message of the last failure on this context (never NULL). */
+const char* dafmm_last_error(const dafmm_ctx* ctx);
+/* Device bytes currently held by the context. */
+size_t dafmm_bytes_in_use(const dafmm_ctx* ctx);
+
+/* Build an octree over n particles (Sec. 1): particles are copied into device memory,
+ * sorted by box, and the interaction lists are prepared.
+ *   domain        {x0, y0, z0, size} of the root cube, or NULL for the smallest cube
+ *                 containing every point, enlarged by 1e-12 of its size;
+ *   uniform_depth >= 0: a uniform tree with 8^depth leaves (depth <= 7);
+ *                 < 0: adaptive, boxes with more than max_leaf particles split (Sec. 3.5).
+ * Box membership: k = floor((x - x0) * 2^21 / size), clamped to [0, 2^21), per axis; a box
+ * of level l holds the particles whose k >> (21 - l) equal its integer coordinates. */
+int dafmm_build_tree(dafmm_ctx* ctx, const double* xyz, const double* q, int64_t n,
+                     const double* domain, int uniform_depth, int max_leaf, void* stream,
+                     dafmm_tree** tree);
+int dafmm_tree_free(dafmm_tree* tree);
+/* info[0..7] = n, depth, leaves, boxes, max particles per leaf, adaptive (0/1), M2L pairs,
+ * P2P leaf pairs.  Also writes the root cube to domain4 when it is not NULL. */
+int dafmm_tree_info(const dafmm_tree* tree, int64_t* info8, double* domain4);
+
+/* Evaluate potential and field of every particle with the FMM of expansion order `order`.
+ *   theta      well-separation distance in box widths; 1.0 is the paper's nearest-neighbour
+ *              criterion (at most 189 M2L partners per box, Sec. 3.4) and the only value
+ *              supported (others return DAFMM_ERR_UNSUPPORTED);
+ *   precision  DAFMM_FP64, DAFMM_MIXED or DAFMM_FP32;
+ *   phi        n doubles (may be NULL), field n x 3 doubles (may be NULL), input order. */
+int dafmm_eval(dafmm_tree* tree, int order, double theta, int precision, double* phi,
+               double* field, void* stream);
+
+/* Per-phase device time of the last dafmm_eval on this context, measured with CUDA events
+ * recorded on that call's stream while profiling is enabled (dafmm_set_profiling).
+ * out10 = {P2M, M2M, M2L (all levels), M2L finest level, L2L, L2P+P2P, conversions,
+ * total, kernel launches, 0}; times in milliseconds.  Waits for the recorded events. */
+int dafmm_set_profiling(dafmm_ctx* ctx, int enable);
+int dafmm_last_phase_ms(dafmm_ctx* ctx, double* out10);
+
+/* Device bytes an evaluation of a tree with these parameters needs (an upper estimate). */
+size_t dafmm_footprint(int64_t n, int order, int uniform_depth, int max_leaf, int precision);
+
+/* ---- single-operator batches (the paper's per-operator verification, Sec. 3) --------
+ * Each entry applies one generated operator to `count` independent instances, in box-
+ * scaled variables (a box of width 1): multipoles M~_a = M_a / h^|a|, locals
+ * L~_b = L_b h^|b|.  Arrays are device or host memory; outputs are overwritten.
+ *   precision: DAFMM_FP64 or DAFMM_FP32 (arithmetic of the generated code). */
+
+/* P2M, Eq. 2: out[i*nc + k] = q_i * coefficient k of (1 - 2 s_i.d + s_i^2 d^2)^(-1/2) */
+int dafmm_op_p2m(dafmm_ctx* ctx, int order, int precision, int64_t count, const double* s,
+                 const double* q, double* out, void* stream);
+/* P2L, Eq. 6: out[i*nc + k] = q_i * coefficient k of 1/|w_i + d'| */
+int dafmm_op_p2l(dafmm_ctx* ctx, int order, int precision, int64_t count, const double* w,
+                 const double* q, double* out, void* stream);
+/* L2P (Sec. 3.2): out4[i] = (L_i(x_i), grad L_i(x_i)); L is count x nc */
+int dafmm_op_l2p(dafmm_ctx* ctx, int order, int precision, int64_t count, const double* L,
+                 const double* x, double* out4, void* stream);
+/* M2P (Sec. 3.2): out4[i] = (|d| M_i(d), grad_s), d = s_i/|s_i|^2 */
+int dafmm_op_m2p(dafmm_ctx* ctx, int order, int precision, int64_t count, const double* M,
+                 const double* s, double* out4, void* stream);
+/* M2M, Eq. 4 (child width 1, parent width 2) and L2L, Eq. 7 (parent width 1, child width
+ * 1/2) for child octant oct[i] (bit v set = upper half along axis v); in/out count x nc */
+int dafmm_op_m2m(dafmm_ctx* ctx, int order, int precision, int64_t count, const int* oct,
+                 const double* in, double* out, void* stream);
+int dafmm_op_l2l(dafmm_ctx* ctx, int order, int precision, int64_t count, const int* oct,
+                 const double* in, double* out, void* stream);
+/* M2L matrix of Eq. 5 for an integer box displacement v (target - source, boxes of width 1,
+ * max|v_k| in 2..3): K[b*nc + a] = coefficient b of M2L(e_a), computed on the GPU in FP64. */
+int dafmm_op_m2l_matrix(dafmm_ctx* ctx, int order, const int* v3, double* K, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -96,7 +96,7 @@ def build(force=False, jobs=None, verbose=False):
             if rc != 0:
                 raise RuntimeError("nvcc failed:\n%s\n%s" % (" ".join(c), out))
     tmp = LIB_PATH + ".tmp.%d" % os.getpid()
-    link = [nvcc, "-shared", "-gencode", "arch=compute_103a,code=sm_103a", "-o", tmp] + objs + ["-lcuda"]
+    link = [nvcc, "-shared", "-gencode", "arch=compute_103a,code=sm_103a", "-o", tmp] + objs
     r = subprocess.run(link, stdout=subprocess.PIPE, stderr=subprocess.STDOUT, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n%s" % r.stdout)

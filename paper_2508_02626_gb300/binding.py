@@ -1,0 +1,258 @@
+"""ctypes binding of libdafmm.so (include/dafmm.h), argument marshalling only.
+
+Every function carries the name of the C entry point it wraps.  Arrays may be torch
+tensors (CPU or CUDA) or numpy arrays; the library itself tells host from device
+memory.  There is no Python fallback: if the compiled library is missing, loading
+raises ``RuntimeError``.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from . import _build
+
+DAFMM_OK = 0
+DAFMM_ERR_INVALID_ARG = -1
+DAFMM_ERR_UNSUPPORTED_ORDER = -2
+DAFMM_ERR_OVER_BUDGET = -3
+DAFMM_ERR_CUDA = -4
+DAFMM_ERR_TIMEOUT = -5
+DAFMM_ERR_UNSUPPORTED = -6
+DAFMM_ERR_NO_DEVICE = -7
+
+DAFMM_FP64 = 0
+DAFMM_MIXED = 1
+DAFMM_FP32 = 2
+PRECISIONS = {"fp64": DAFMM_FP64, "mixed": DAFMM_MIXED, "fp32": DAFMM_FP32}
+MAX_ORDER = 10
+
+# entry points declared in include/dafmm.h: name -> (restype, argtypes)
+_vp, _i, _i64, _sz, _d = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_size_t, ctypes.c_double
+SIGNATURES = {
+    "dafmm_create": (_i, [ctypes.POINTER(_vp), _i, _sz]),
+    "dafmm_destroy": (None, [_vp]),
+    "dafmm_last_error": (ctypes.c_char_p, [_vp]),
+    "dafmm_bytes_in_use": (_sz, [_vp]),
+    "dafmm_build_tree": (_i, [_vp, _vp, _vp, _i64, _vp, _i, _i, _vp, ctypes.POINTER(_vp)]),
+    "dafmm_tree_free": (_i, [_vp]),
+    "dafmm_tree_info": (_i, [_vp, _vp, _vp]),
+    "dafmm_eval": (_i, [_vp, _i, _d, _i, _vp, _vp, _vp]),
+    "dafmm_footprint": (_sz, [_i64, _i, _i, _i, _i]),
+    "dafmm_set_profiling": (_i, [_vp, _i]),
+    "dafmm_last_phase_ms": (_i, [_vp, _vp]),
+    "dafmm_op_p2m": (_i, [_vp, _i, _i, _i64, _vp, _vp, _vp, _vp]),
+    "dafmm_op_p2l": (_i, [_vp, _i, _i, _i64, _vp, _vp, _vp, _vp]),
+    "dafmm_op_l2p": (_i, [_vp, _i, _i, _i64, _vp, _vp, _vp, _vp]),
+    "dafmm_op_m2p": (_i, [_vp, _i, _i, _i64, _vp, _vp, _vp, _vp]),
+    "dafmm_op_m2m": (_i, [_vp, _i, _i, _i64, _vp, _vp, _vp, _vp]),
+    "dafmm_op_l2l": (_i, [_vp, _i, _i, _i64, _vp, _vp, _vp, _vp]),
+    "dafmm_op_m2l_matrix": (_i, [_vp, _i, _vp, _vp, _vp]),
+}
+
+_lib = None
+
+
+def library_path():
+    return _build.LIB_PATH
+
+
+def load(build_if_missing=False):
+    """Load libdafmm.so.  Raises RuntimeError when it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB_PATH
+    if not os.path.exists(path):
+        if build_if_missing:
+            _build.build()
+        else:
+            raise RuntimeError("libdafmm.so is not built (run __graft_entry__.build()); there is no fallback")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+class DafmmError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s (code %d)" % (msg, code))
+        self.code = code
+
+
+def _ptr(a):
+    """Address of a torch tensor / numpy array (None for None)."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return a.data_ptr()
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return a.ctypes.data
+    raise TypeError("expected a torch tensor or a numpy array")
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return stream.cuda_stream
+    return int(stream)
+
+
+def _check(ctx, rc):
+    if rc != DAFMM_OK:
+        msg = load().dafmm_last_error(ctx).decode() if ctx else "dafmm call failed"
+        raise DafmmError(rc, msg)
+
+
+# ---- entry points ---------------------------------------------------------------------------
+def dafmm_create(device=0, hbm_budget_bytes=0):
+    h = _vp()
+    rc = load().dafmm_create(ctypes.byref(h), int(device), int(hbm_budget_bytes))
+    if rc != DAFMM_OK:
+        raise DafmmError(rc, "dafmm_create failed")
+    return h.value
+
+
+def dafmm_destroy(ctx):
+    load().dafmm_destroy(ctx)
+
+
+def dafmm_last_error(ctx):
+    return load().dafmm_last_error(ctx).decode()
+
+
+def dafmm_bytes_in_use(ctx):
+    return load().dafmm_bytes_in_use(ctx)
+
+
+def dafmm_build_tree(ctx, xyz, q, domain=None, uniform_depth=-1, max_leaf=64, stream=None):
+    n = int(q.shape[0]) if q is not None else 0
+    dom = None
+    if domain is not None:
+        dom = np.ascontiguousarray(domain, dtype=np.float64)
+    h = _vp()
+    rc = load().dafmm_build_tree(ctx, _ptr(xyz), _ptr(q), n, _ptr(dom), int(uniform_depth), int(max_leaf),
+                                 _stream_ptr(stream), ctypes.byref(h))
+    _check(ctx, rc)
+    return h.value
+
+
+def dafmm_tree_free(tree):
+    load().dafmm_tree_free(tree)
+
+
+def dafmm_tree_info(tree):
+    info = np.zeros(8, dtype=np.int64)
+    dom = np.zeros(4)
+    rc = load().dafmm_tree_info(tree, info.ctypes.data, dom.ctypes.data)
+    if rc != DAFMM_OK:
+        raise DafmmError(rc, "dafmm_tree_info failed")
+    keys = ["n", "depth", "leaves", "boxes", "max_per_leaf", "adaptive", "m2l_pairs", "p2p_leaf_pairs"]
+    out = {k: int(v) for k, v in zip(keys, info)}
+    out["domain"] = dom
+    return out
+
+
+def dafmm_eval(ctx, tree, order, phi=None, field=None, theta=1.0, precision=DAFMM_FP64, stream=None):
+    rc = load().dafmm_eval(tree, int(order), float(theta), int(precision), _ptr(phi), _ptr(field),
+                           _stream_ptr(stream))
+    _check(ctx, rc)
+
+
+def dafmm_set_profiling(ctx, enable):
+    _check(ctx, load().dafmm_set_profiling(ctx, int(bool(enable))))
+
+
+PHASES = ["p2m", "m2m", "m2l", "m2l_finest", "l2l", "leaf", "convert", "total", "launches"]
+
+
+def dafmm_last_phase_ms(ctx):
+    out = np.zeros(10)
+    _check(ctx, load().dafmm_last_phase_ms(ctx, out.ctypes.data))
+    return dict(zip(PHASES, out[:9].tolist()))
+
+
+def dafmm_footprint(n, order, uniform_depth=-1, max_leaf=64, precision=DAFMM_FP64):
+    return load().dafmm_footprint(int(n), int(order), int(uniform_depth), int(max_leaf), int(precision))
+
+
+def _op(name, ctx, order, precision, count, a, b, out, stream):
+    fn = getattr(load(), name)
+    _check(ctx, fn(ctx, int(order), int(precision), int(count), _ptr(a), _ptr(b), _ptr(out), _stream_ptr(stream)))
+
+
+def dafmm_op_p2m(ctx, order, precision, s, q, out, stream=None):
+    _op("dafmm_op_p2m", ctx, order, precision, q.shape[0], s, q, out, stream)
+
+
+def dafmm_op_p2l(ctx, order, precision, w, q, out, stream=None):
+    _op("dafmm_op_p2l", ctx, order, precision, q.shape[0], w, q, out, stream)
+
+
+def dafmm_op_l2p(ctx, order, precision, L, x, out4, stream=None):
+    _op("dafmm_op_l2p", ctx, order, precision, x.shape[0], L, x, out4, stream)
+
+
+def dafmm_op_m2p(ctx, order, precision, M, s, out4, stream=None):
+    _op("dafmm_op_m2p", ctx, order, precision, s.shape[0], M, s, out4, stream)
+
+
+def dafmm_op_m2m(ctx, order, precision, oct_, inp, out, stream=None):
+    _op("dafmm_op_m2m", ctx, order, precision, oct_.shape[0], oct_, inp, out, stream)
+
+
+def dafmm_op_l2l(ctx, order, precision, oct_, inp, out, stream=None):
+    _op("dafmm_op_l2l", ctx, order, precision, oct_.shape[0], oct_, inp, out, stream)
+
+
+def dafmm_op_m2l_matrix(ctx, order, v, K, stream=None):
+    v = np.ascontiguousarray(v, dtype=np.int32)
+    _check(ctx, load().dafmm_op_m2l_matrix(ctx, int(order), v.ctypes.data, _ptr(K), _stream_ptr(stream)))
+
+
+# ---- a small convenience layer ----------------------------------------------------------------
+class Context:
+    """Owns a dafmm context; trees built from it are freed with it."""
+
+    def __init__(self, device=0, hbm_budget_bytes=0):
+        self.h = dafmm_create(device, hbm_budget_bytes)
+
+    def close(self):
+        if self.h:
+            dafmm_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def build_tree(self, xyz, q, domain=None, uniform_depth=-1, max_leaf=64, stream=None):
+        return Tree(self, dafmm_build_tree(self.h, xyz, q, domain, uniform_depth, max_leaf, stream))
+
+
+class Tree:
+    def __init__(self, ctx, h):
+        self.ctx = ctx
+        self.h = h
+
+    def info(self):
+        return dafmm_tree_info(self.h)
+
+    def eval(self, order, phi=None, field=None, precision="fp64", theta=1.0, stream=None):
+        prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        dafmm_eval(self.ctx.h, self.h, order, phi, field, theta, prec, stream)
+
+    def free(self):
+        if self.h and self.ctx.h:
+            dafmm_tree_free(self.h)
+        self.h = None

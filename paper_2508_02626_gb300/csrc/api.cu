@@ -1,0 +1,790 @@
+// api.cu -- host runtime behind the C ABI of include/dafmm.h: contexts with an HBM budget,
+// octree construction, the FMM evaluation sequence (Sec. 1) and the single-operator batches.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "da_common.cuh"
+#include "internal.h"
+#include "tree_common.cuh"
+
+using namespace dafmm;
+
+// ---------------------------------------------------------------------------------------------
+struct dafmm_ctx {
+    int device = 0;
+    size_t budget = 0;
+    size_t in_use = 0;
+    std::string err;
+    OrderData ord[kMaxOrder + 1];
+    std::vector<dafmm_tree*> trees;
+    // profiling: events at the phase boundaries of the last evaluation
+    bool profile = false;
+    cudaEvent_t ev[8] = {};
+    int last_launches = 0;
+    bool have_profile = false;
+};
+
+struct Expansions {
+    int p = -1;
+    int depth = -1;
+    double* M[kMaxUniformDepth + 1] = {};
+    double* L[kMaxUniformDepth + 1] = {};
+    float* Mf[kMaxUniformDepth + 1] = {};
+};
+
+struct dafmm_tree {
+    dafmm_ctx* ctx = nullptr;
+    int64_t n = 0;
+    double dom[4] = {0, 0, 0, 1};
+    int depth = 0;
+    int nleaf = 1;
+    int max_per_leaf = 0;
+    double *x = nullptr, *y = nullptr, *z = nullptr, *q = nullptr;
+    float4* xq = nullptr;
+    int* perm = nullptr;
+    int* leaf_start = nullptr;
+    Expansions ex;
+    double* out_scratch = nullptr;  // device outputs when the caller passes host buffers
+    size_t out_scratch_bytes = 0;
+};
+
+namespace {
+
+const char* code_name(int c) {
+    switch (c) {
+        case DAFMM_ERR_INVALID_ARG: return "invalid argument";
+        case DAFMM_ERR_UNSUPPORTED_ORDER: return "unsupported order";
+        case DAFMM_ERR_OVER_BUDGET: return "over HBM budget";
+        case DAFMM_ERR_CUDA: return "CUDA error";
+        case DAFMM_ERR_TIMEOUT: return "timeout";
+        case DAFMM_ERR_UNSUPPORTED: return "unsupported option";
+        case DAFMM_ERR_NO_DEVICE: return "no CUDA device";
+    }
+    return "error";
+}
+
+int fail(dafmm_ctx* c, int code, const std::string& msg) {
+    if (c) c->err = std::string(code_name(code)) + ": " + msg;
+    return code;
+}
+
+int cuda_fail(dafmm_ctx* c, cudaError_t e, const char* where) {
+    return fail(c, DAFMM_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(ctx, call, where)                                     \
+    do {                                                         \
+        cudaError_t e_ = (call);                                 \
+        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, where); \
+    } while (0)
+
+// every device allocation of a context goes through here (budget accounting)
+int dev_alloc(dafmm_ctx* c, void** p, size_t bytes, const char* what) {
+    *p = nullptr;
+    if (bytes == 0) return DAFMM_OK;
+    bytes = (bytes + 255) / 256 * 256;
+    if (c->budget && c->in_use + bytes > c->budget)
+        return fail(c, DAFMM_ERR_OVER_BUDGET, std::string(what) + " needs " + std::to_string(bytes) +
+                                                  " bytes, budget left " + std::to_string(c->budget - c->in_use));
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, DAFMM_ERR_OVER_BUDGET, std::string(what) + ": cudaMalloc: " + cudaGetErrorString(e));
+    }
+    c->in_use += bytes;
+    return DAFMM_OK;
+}
+
+void dev_free(dafmm_ctx* c, void* p, size_t bytes) {
+    if (!p) return;
+    cudaFree(p);
+    bytes = (bytes + 255) / 256 * 256;
+    c->in_use = c->in_use >= bytes ? c->in_use - bytes : 0;
+}
+
+bool is_device_ptr(const void* p) {
+    if (!p) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+size_t level_boxes(int l) { return (size_t)1 << (3 * l); }
+
+// a device view of caller memory: either the pointer itself or a staged copy
+struct Staged {
+    dafmm_ctx* c = nullptr;
+    void* dev = nullptr;
+    size_t bytes = 0;
+    bool owned = false;
+    ~Staged() {
+        if (owned) dev_free(c, dev, bytes);
+    }
+};
+
+int stage_in(dafmm_ctx* c, const void* src, size_t bytes, cudaStream_t s, Staged& out) {
+    out.c = c;
+    out.bytes = bytes;
+    if (bytes == 0) return DAFMM_OK;
+    if (is_device_ptr(src)) {
+        out.dev = const_cast<void*>(src);
+        return DAFMM_OK;
+    }
+    int rc = dev_alloc(c, &out.dev, bytes, "input staging");
+    if (rc) return rc;
+    out.owned = true;
+    CK(c, cudaMemcpyAsync(out.dev, src, bytes, cudaMemcpyHostToDevice, s), "stage input");
+    return DAFMM_OK;
+}
+
+// ---- per-order tables -----------------------------------------------------------------------
+template <class T>
+int upload(dafmm_ctx* c, T** dst, const T* src, size_t count, const char* what) {
+    int rc = dev_alloc(c, (void**)dst, count * sizeof(T), what);
+    if (rc) return rc;
+    if (count) CK(c, cudaMemcpy(*dst, src, count * sizeof(T), cudaMemcpyHostToDevice), what);
+    return DAFMM_OK;
+}
+
+int ensure_order(dafmm_ctx* c, int p, cudaStream_t s, bool need_k) {
+    if (p < 0 || p > kMaxOrder) return fail(c, DAFMM_ERR_UNSUPPORTED_ORDER, "order " + std::to_string(p));
+    OrderData& od = c->ord[p];
+    const OrderOps* ops = order_ops(p);
+    if (od.p < 0) {
+        od.p = p;
+        od.nc = ops->nc;
+        od.ncp = ops->ncp;
+        int rc;
+        const HostShiftTable* tabs[2] = {&ops->m2m, &ops->l2l};
+        for (int w = 0; w < 2; ++w) {
+            const HostShiftTable& t = *tabs[w];
+            std::vector<float> vf(t.val, t.val + t.nnz);
+            int** rp = w == 0 ? &od.m2m_rowptr : &od.l2l_rowptr;
+            unsigned short** col = w == 0 ? &od.m2m_col : &od.l2l_col;
+            unsigned char** par = w == 0 ? &od.m2m_par : &od.l2l_par;
+            double** val = w == 0 ? &od.m2m_val : &od.l2l_val;
+            float** valf = w == 0 ? &od.m2m_valf : &od.l2l_valf;
+            if ((rc = upload(c, rp, t.rowptr, (size_t)od.nc + 1, "shift table"))) return rc;
+            if ((rc = upload(c, col, t.col, (size_t)t.nnz, "shift table"))) return rc;
+            if ((rc = upload(c, par, t.par, (size_t)t.nnz, "shift table"))) return rc;
+            if ((rc = upload(c, val, t.val, (size_t)t.nnz, "shift table"))) return rc;
+            if ((rc = upload(c, valf, vf.data(), (size_t)t.nnz, "shift table"))) return rc;
+        }
+        // DA product table: for each output k, the pairs (i, j) with e_i + e_j = e_k
+        std::vector<int> ex(3 * od.nc);
+        for (int n = 0; n <= p; ++n)
+            for (int a = n; a >= 0; --a)
+                for (int b = n - a; b >= 0; --b) {
+                    int cc = n - a - b, k = da_index(a, b, cc);
+                    ex[3 * k] = a; ex[3 * k + 1] = b; ex[3 * k + 2] = cc;
+                }
+        std::vector<int> rowptr(od.nc + 1, 0);
+        std::vector<ushort2> pairs;
+        for (int k = 0; k < od.nc; ++k) {
+            rowptr[k] = (int)pairs.size();
+            for (int i = 0; i < od.nc; ++i) {
+                int r0 = ex[3 * k] - ex[3 * i], r1 = ex[3 * k + 1] - ex[3 * i + 1], r2 = ex[3 * k + 2] - ex[3 * i + 2];
+                if (r0 < 0 || r1 < 0 || r2 < 0) continue;
+                ushort2 pr;
+                pr.x = (unsigned short)i;
+                pr.y = (unsigned short)da_index(r0, r1, r2);
+                pairs.push_back(pr);
+            }
+        }
+        rowptr[od.nc] = (int)pairs.size();
+        std::vector<short> minus(3 * od.nc);
+        for (int d = 0; d < 3; ++d)
+            for (int k = 0; k < od.nc; ++k) {
+                int e[3] = {ex[3 * k], ex[3 * k + 1], ex[3 * k + 2]};
+                if (e[d] == 0) {
+                    minus[d * od.nc + k] = -1;
+                } else {
+                    e[d] -= 1;
+                    minus[d * od.nc + k] = (short)da_index(e[0], e[1], e[2]);
+                }
+            }
+        if ((rc = upload(c, &od.mul_rowptr, rowptr.data(), rowptr.size(), "product table"))) return rc;
+        if ((rc = upload(c, &od.mul_pairs, pairs.data(), pairs.size(), "product table"))) return rc;
+        if ((rc = upload(c, &od.mul_minus, minus.data(), minus.size(), "product table"))) return rc;
+    }
+    if (need_k && !od.k_ready) {
+        const size_t cnt = (size_t)kNumKeys * od.nc * od.ncp;
+        int rc;
+        if ((rc = dev_alloc(c, (void**)&od.K64, cnt * sizeof(double), "M2L matrices (FP64)"))) return rc;
+        if ((rc = dev_alloc(c, (void**)&od.K32, cnt * sizeof(float), "M2L matrices (FP32)"))) return rc;
+        CK(c, cudaMemsetAsync(od.K64, 0, cnt * sizeof(double), s), "K memset");
+        CK(c, cudaMemsetAsync(od.K32, 0, cnt * sizeof(float), s), "K memset");
+        CK(c, ops->kgen(od, s), "K generation");
+        od.k_ready = true;
+    }
+    return DAFMM_OK;
+}
+
+void free_order(dafmm_ctx* c, OrderData& od) {
+    const int nc = od.nc;
+    const OrderOps* ops = od.p >= 0 ? order_ops(od.p) : nullptr;
+    if (!ops) return;
+    for (int w = 0; w < 2; ++w) {
+        const HostShiftTable& t = w == 0 ? ops->m2m : ops->l2l;
+        dev_free(c, w == 0 ? (void*)od.m2m_rowptr : (void*)od.l2l_rowptr, (nc + 1) * sizeof(int));
+        dev_free(c, w == 0 ? (void*)od.m2m_col : (void*)od.l2l_col, t.nnz * sizeof(unsigned short));
+        dev_free(c, w == 0 ? (void*)od.m2m_par : (void*)od.l2l_par, t.nnz);
+        dev_free(c, w == 0 ? (void*)od.m2m_val : (void*)od.l2l_val, t.nnz * sizeof(double));
+        dev_free(c, w == 0 ? (void*)od.m2m_valf : (void*)od.l2l_valf, t.nnz * sizeof(float));
+    }
+    cudaFree(od.mul_rowptr); cudaFree(od.mul_pairs); cudaFree(od.mul_minus);
+    const size_t cnt = (size_t)kNumKeys * od.nc * od.ncp;
+    dev_free(c, od.K64, od.K64 ? cnt * sizeof(double) : 0);
+    dev_free(c, od.K32, od.K32 ? cnt * sizeof(float) : 0);
+    od = OrderData();
+}
+
+// ---- expansions --------------------------------------------------------------------------------
+void free_expansions(dafmm_tree* t) {
+    dafmm_ctx* c = t->ctx;
+    Expansions& e = t->ex;
+    if (e.p < 0) return;
+    const int ncp = ncp_of(e.p);
+    for (int l = 0; l <= e.depth; ++l) {
+        const size_t cnt = level_boxes(l) * ncp;
+        dev_free(c, e.M[l], e.M[l] ? cnt * sizeof(double) : 0);
+        dev_free(c, e.L[l], e.L[l] ? cnt * sizeof(double) : 0);
+        dev_free(c, e.Mf[l], e.Mf[l] ? cnt * sizeof(float) : 0);
+    }
+    e = Expansions();
+}
+
+int ensure_expansions(dafmm_tree* t, int p, cudaStream_t s) {
+    if (t->ex.p == p) return DAFMM_OK;
+    free_expansions(t);
+    dafmm_ctx* c = t->ctx;
+    const int ncp = ncp_of(p);
+    t->ex.p = p;
+    t->ex.depth = t->depth;
+    for (int l = 2; l <= t->depth; ++l) {
+        const size_t cnt = level_boxes(l) * ncp;
+        int rc;
+        if ((rc = dev_alloc(c, (void**)&t->ex.M[l], cnt * sizeof(double), "multipoles"))) return rc;
+        if ((rc = dev_alloc(c, (void**)&t->ex.L[l], cnt * sizeof(double), "locals"))) return rc;
+        if ((rc = dev_alloc(c, (void**)&t->ex.Mf[l], cnt * sizeof(float), "multipoles (FP32)"))) return rc;
+        CK(c, cudaMemsetAsync(t->ex.M[l], 0, cnt * sizeof(double), s), "memset");
+        CK(c, cudaMemsetAsync(t->ex.L[l], 0, cnt * sizeof(double), s), "memset");
+        CK(c, cudaMemsetAsync(t->ex.Mf[l], 0, cnt * sizeof(float), s), "memset");
+    }
+    return DAFMM_OK;
+}
+
+__global__ void k_to_float(const double* __restrict__ a, float* __restrict__ b, size_t n) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        b[i] = (float)a[i];
+}
+
+TreeView make_view(const dafmm_tree* t) {
+    TreeView tv;
+    tv.n = t->n;
+    tv.depth = t->depth;
+    tv.nleaf = t->nleaf;
+    tv.x0 = t->dom[0]; tv.y0 = t->dom[1]; tv.z0 = t->dom[2]; tv.size = t->dom[3];
+    tv.h_leaf = ldexp(t->dom[3], -t->depth);
+    tv.inv_h_leaf = 1.0 / tv.h_leaf;
+    tv.x = t->x; tv.y = t->y; tv.z = t->z; tv.q = t->q;
+    tv.xq = t->xq;
+    tv.perm = t->perm;
+    tv.leaf_start = t->leaf_start;
+    return tv;
+}
+
+size_t tree_bytes(int64_t n, int depth) {
+    const size_t nl = level_boxes(depth);
+    return (size_t)n * (4 * sizeof(double) + sizeof(float4) + sizeof(int)) + (nl + 1) * sizeof(int);
+}
+
+}  // namespace
+
+namespace dafmm {
+const OrderOps* order_ops(int p) {
+    switch (p) {
+        case 0: return order_ops_p0();
+        case 1: return order_ops_p1();
+        case 2: return order_ops_p2();
+        case 3: return order_ops_p3();
+        case 4: return order_ops_p4();
+        case 5: return order_ops_p5();
+        case 6: return order_ops_p6();
+        case 7: return order_ops_p7();
+        case 8: return order_ops_p8();
+        case 9: return order_ops_p9();
+        case 10: return order_ops_p10();
+    }
+    return nullptr;
+}
+}  // namespace dafmm
+
+// ================================ C ABI =======================================================
+extern "C" {
+
+int dafmm_create(dafmm_ctx** out, int device, size_t hbm_budget_bytes) {
+    if (!out) return DAFMM_ERR_INVALID_ARG;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+        cudaGetLastError();
+        return DAFMM_ERR_NO_DEVICE;
+    }
+    if (device < 0 || device >= ndev) return DAFMM_ERR_INVALID_ARG;
+    if (cudaSetDevice(device) != cudaSuccess) return DAFMM_ERR_CUDA;
+    dafmm_ctx* c = new dafmm_ctx();
+    c->device = device;
+    c->budget = hbm_budget_bytes;
+    *out = c;
+    return DAFMM_OK;
+}
+
+void dafmm_destroy(dafmm_ctx* c) {
+    if (!c) return;
+    cudaSetDevice(c->device);
+    cudaDeviceSynchronize();
+    std::vector<dafmm_tree*> ts = c->trees;
+    for (dafmm_tree* t : ts) dafmm_tree_free(t);
+    for (int p = 0; p <= kMaxOrder; ++p) free_order(c, c->ord[p]);
+    for (int k = 0; k < 8; ++k)
+        if (c->ev[k]) cudaEventDestroy(c->ev[k]);
+    delete c;
+}
+
+const char* dafmm_last_error(const dafmm_ctx* c) { return c ? c->err.c_str() : "no context"; }
+
+size_t dafmm_bytes_in_use(const dafmm_ctx* c) { return c ? c->in_use : 0; }
+
+int dafmm_build_tree(dafmm_ctx* c, const double* xyz, const double* q, int64_t n, const double* domain,
+                     int uniform_depth, int max_leaf, void* stream, dafmm_tree** out) {
+    if (!c || !out) return DAFMM_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (n < 0 || n > (int64_t)INT32_MAX - 1 || (n > 0 && (!xyz || !q)))
+        return fail(c, DAFMM_ERR_INVALID_ARG, "particle arrays");
+    if (uniform_depth < 0)
+        return fail(c, DAFMM_ERR_UNSUPPORTED, "adaptive trees are not available in this build");
+    if (uniform_depth > kMaxUniformDepth)
+        return fail(c, DAFMM_ERR_INVALID_ARG, "uniform depth above " + std::to_string(kMaxUniformDepth));
+    (void)max_leaf;
+    if (domain && !(domain[3] > 0.0 && isfinite(domain[0]) && isfinite(domain[1]) && isfinite(domain[2]) &&
+                    isfinite(domain[3])))
+        return fail(c, DAFMM_ERR_INVALID_ARG, "domain");
+    CK(c, cudaSetDevice(c->device), "cudaSetDevice");
+    cudaStream_t s = (cudaStream_t)stream;
+    Staged sx, sq;
+    int rc;
+    if ((rc = stage_in(c, xyz, (size_t)n * 3 * sizeof(double), s, sx))) return rc;
+    if ((rc = stage_in(c, q, (size_t)n * sizeof(double), s, sq))) return rc;
+    const double* dxyz = (const double*)sx.dev;
+    const double* dq = (const double*)sq.dev;
+
+    dafmm_tree* t = new dafmm_tree();
+    t->ctx = c;
+    t->n = n;
+    t->depth = uniform_depth;
+    t->nleaf = (int)level_boxes(uniform_depth);
+    // root cube
+    if (domain) {
+        for (int d = 0; d < 4; ++d) t->dom[d] = domain[d];
+    } else if (n > 0) {
+        double* bb = nullptr;
+        if ((rc = dev_alloc(c, (void**)&bb, 6 * sizeof(double), "bbox"))) { delete t; return rc; }
+        cudaError_t e = launch_bbox(dxyz, n, bb, s);
+        unsigned long long h[6];
+        if (e == cudaSuccess) e = cudaMemcpyAsync(h, bb, sizeof(h), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        dev_free(c, bb, 6 * sizeof(double));
+        if (e != cudaSuccess) { delete t; return cuda_fail(c, e, "bounding box"); }
+        double v[6];
+        for (int k = 0; k < 6; ++k) {
+            unsigned long long u = h[k];
+            u = (u >> 63) ? (u & 0x7fffffffffffffffull) : ~u;
+            memcpy(&v[k], &u, 8);
+        }
+        double size = std::max(v[3] - v[0], std::max(v[4] - v[1], v[5] - v[2]));
+        if (!(size > 0.0)) size = 1.0;
+        size = size * (1.0 + 1e-12);
+        t->dom[0] = v[0]; t->dom[1] = v[1]; t->dom[2] = v[2]; t->dom[3] = size;
+        if (!(isfinite(size) && isfinite(v[0]) && isfinite(v[1]) && isfinite(v[2]))) {
+            delete t;
+            return fail(c, DAFMM_ERR_INVALID_ARG, "non-finite coordinates");
+        }
+    }
+    // device arrays
+    const size_t N = (size_t)n;
+    rc = 0;
+    if (!rc) rc = dev_alloc(c, (void**)&t->x, N * sizeof(double), "particles");
+    if (!rc) rc = dev_alloc(c, (void**)&t->y, N * sizeof(double), "particles");
+    if (!rc) rc = dev_alloc(c, (void**)&t->z, N * sizeof(double), "particles");
+    if (!rc) rc = dev_alloc(c, (void**)&t->q, N * sizeof(double), "particles");
+    if (!rc) rc = dev_alloc(c, (void**)&t->xq, N * sizeof(float4), "particles");
+    if (!rc) rc = dev_alloc(c, (void**)&t->perm, N * sizeof(int), "particles");
+    if (!rc) rc = dev_alloc(c, (void**)&t->leaf_start, ((size_t)t->nleaf + 1) * sizeof(int), "leaves");
+    uint64_t* keys = nullptr;
+    void* tmp = nullptr;
+    const size_t tmpb = radix_sort_temp_bytes(n);
+    if (!rc) rc = dev_alloc(c, (void**)&keys, N * sizeof(uint64_t), "sort keys");
+    if (!rc) rc = dev_alloc(c, &tmp, tmpb, "sort scratch");
+    if (rc) {
+        dev_free(c, keys, N * sizeof(uint64_t));
+        dev_free(c, tmp, tmpb);
+        c->trees.push_back(t);
+        dafmm_tree_free(t);
+        return rc;
+    }
+    const double scale = ldexp(1.0, kQBits) / t->dom[3];
+    cudaError_t e = launch_uniform_keys(dxyz, n, t->dom[0], t->dom[1], t->dom[2], scale, t->depth, keys, t->perm, s);
+    if (e == cudaSuccess) e = radix_sort_pairs(keys, t->perm, n, 3 * t->depth, tmp, s);
+    if (e == cudaSuccess)
+        e = launch_gather_uniform(dxyz, dq, t->perm, n, keys, make_view(t), t->x, t->y, t->z, t->q, t->xq,
+                                  t->leaf_start, s);
+    // the largest leaf (for the caller's information)
+    std::vector<int> ls((size_t)t->nleaf + 1);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(ls.data(), t->leaf_start, ls.size() * sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    dev_free(c, keys, N * sizeof(uint64_t));
+    dev_free(c, tmp, tmpb);
+    c->trees.push_back(t);
+    if (e != cudaSuccess) {
+        dafmm_tree_free(t);
+        return cuda_fail(c, e, "tree build");
+    }
+    for (int b = 0; b < t->nleaf; ++b) t->max_per_leaf = std::max(t->max_per_leaf, ls[b + 1] - ls[b]);
+    *out = t;
+    return DAFMM_OK;
+}
+
+int dafmm_tree_free(dafmm_tree* t) {
+    if (!t) return DAFMM_ERR_INVALID_ARG;
+    dafmm_ctx* c = t->ctx;
+    cudaSetDevice(c->device);
+    free_expansions(t);
+    const size_t N = (size_t)t->n;
+    dev_free(c, t->x, N * sizeof(double));
+    dev_free(c, t->y, N * sizeof(double));
+    dev_free(c, t->z, N * sizeof(double));
+    dev_free(c, t->q, N * sizeof(double));
+    dev_free(c, t->xq, N * sizeof(float4));
+    dev_free(c, t->perm, N * sizeof(int));
+    dev_free(c, t->leaf_start, ((size_t)t->nleaf + 1) * sizeof(int));
+    dev_free(c, t->out_scratch, t->out_scratch_bytes);
+    auto it = std::find(c->trees.begin(), c->trees.end(), t);
+    if (it != c->trees.end()) c->trees.erase(it);
+    delete t;
+    return DAFMM_OK;
+}
+
+int dafmm_tree_info(const dafmm_tree* t, int64_t* info, double* domain4) {
+    if (!t || !info) return DAFMM_ERR_INVALID_ARG;
+    int64_t m2l = 0, p2p = 0;
+    for (int l = 2; l <= t->depth; ++l) {
+        const int64_t s = (int64_t)1 << l;
+        // per axis: number of ordered (target, source) index pairs with |dt - ds| <= 1 among
+        // children of adjacent parents, minus adjacent ones
+        int64_t near1 = 3 * s - 2;  // pairs at distance <= 1
+        int64_t par = 3 * (s / 2) - 2;  // adjacent parent pairs
+        int64_t cand = par * 4;          // children pairs of adjacent parents
+        m2l += cand * cand * cand - near1 * near1 * near1;
+    }
+    {
+        const int64_t s = (int64_t)1 << t->depth;
+        const int64_t near1 = 3 * s - 2;
+        p2p = near1 * near1 * near1;
+    }
+    info[0] = t->n;
+    info[1] = t->depth;
+    info[2] = t->nleaf;
+    int64_t nb = 0;
+    for (int l = 0; l <= t->depth; ++l) nb += (int64_t)level_boxes(l);
+    info[3] = nb;
+    info[4] = t->max_per_leaf;
+    info[5] = 0;
+    info[6] = m2l;
+    info[7] = p2p;
+    if (domain4)
+        for (int d = 0; d < 4; ++d) domain4[d] = t->dom[d];
+    return DAFMM_OK;
+}
+
+int dafmm_eval(dafmm_tree* t, int order, double theta, int precision, double* phi, double* field, void* stream) {
+    if (!t) return DAFMM_ERR_INVALID_ARG;
+    dafmm_ctx* c = t->ctx;
+    if (order < 0 || order > kMaxOrder) return fail(c, DAFMM_ERR_UNSUPPORTED_ORDER, std::to_string(order));
+    if (!(fabs(theta - 1.0) < 1e-12))
+        return fail(c, DAFMM_ERR_UNSUPPORTED, "theta other than 1 (nearest-neighbour separation)");
+    if (precision != DAFMM_FP64 && precision != DAFMM_MIXED && precision != DAFMM_FP32)
+        return fail(c, DAFMM_ERR_INVALID_ARG, "precision");
+    CK(c, cudaSetDevice(c->device), "cudaSetDevice");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (t->n == 0) return DAFMM_OK;
+    const OrderOps* ops = order_ops(order);
+    const bool far = t->depth >= 2;
+    int rc;
+    if ((rc = ensure_order(c, order, s, far))) return rc;
+    if (far && (rc = ensure_expansions(t, order, s))) return rc;
+    // outputs
+    const bool phi_dev = !phi || is_device_ptr(phi), field_dev = !field || is_device_ptr(field);
+    double* dphi = phi;
+    double* dfield = field;
+    const size_t N = (size_t)t->n;
+    if (!phi_dev || !field_dev) {
+        const size_t need = N * 4 * sizeof(double);
+        if (t->out_scratch_bytes < need) {
+            dev_free(c, t->out_scratch, t->out_scratch_bytes);
+            t->out_scratch = nullptr;
+            t->out_scratch_bytes = 0;
+            if ((rc = dev_alloc(c, (void**)&t->out_scratch, need, "output staging"))) return rc;
+            t->out_scratch_bytes = need;
+        }
+        if (!phi_dev) dphi = t->out_scratch;
+        if (!field_dev) dfield = t->out_scratch + N;
+    }
+    const TreeView tv = make_view(t);
+    const OrderData& od = c->ord[order];
+    const int L = t->depth;
+    // phase boundaries: 0 start, 1 after P2M, 2 after M2M, 3 after conversions, 4 before the
+    // finest M2L, 5 after M2L, 6 after L2L, 7 after L2P/P2P
+    auto mark = [&](int k) {
+        if (c->profile) cudaEventRecord(c->ev[k], s);
+    };
+    int launches = 0;
+    mark(0);
+    if (far) {
+        CK(c, ops->p2m(tv, precision, t->ex.M[L], s), "P2M");
+        ++launches;
+        mark(1);
+        for (int lc = L; lc >= 3; --lc) {
+            CK(c, ops->m2m_level(od, precision, lc, t->ex.M[lc], t->ex.M[lc - 1], s), "M2M");
+            ++launches;
+        }
+        mark(2);
+        if (precision != DAFMM_FP64)
+            for (int l = 2; l <= L; ++l) {
+                const size_t cnt = level_boxes(l) * od.ncp;
+                k_to_float<<<(unsigned)std::min<size_t>((cnt + 255) / 256, 152 * 16), 256, 0, s>>>(t->ex.M[l], t->ex.Mf[l], cnt);
+                CK(c, cudaGetLastError(), "convert");
+                ++launches;
+            }
+        mark(3);
+        for (int l = 2; l <= L; ++l) {
+            if (l == L) mark(4);
+            const double inv_h = 1.0 / ldexp(t->dom[3], -l);
+            CK(c, ops->m2l_level(od, precision, l, t->ex.M[l], t->ex.Mf[l], t->ex.L[l], inv_h, s), "M2L");
+            ++launches;
+        }
+        mark(5);
+        for (int lc = 3; lc <= L; ++lc) {
+            CK(c, ops->l2l_level(od, precision, lc, t->ex.L[lc - 1], t->ex.L[lc], s), "L2L");
+            ++launches;
+        }
+        mark(6);
+    } else {
+        for (int k = 1; k <= 6; ++k) mark(k);
+    }
+    CK(c, ops->leaf(tv, precision, far ? t->ex.L[L] : nullptr, dphi, dfield, s), "L2P/P2P");
+    ++launches;
+    mark(7);
+    c->last_launches = launches;
+    c->have_profile = c->profile;
+    if (!phi_dev) CK(c, cudaMemcpyAsync(phi, dphi, N * sizeof(double), cudaMemcpyDeviceToHost, s), "D2H");
+    if (!field_dev) CK(c, cudaMemcpyAsync(field, dfield, N * 3 * sizeof(double), cudaMemcpyDeviceToHost, s), "D2H");
+    if (!phi_dev || !field_dev) CK(c, cudaStreamSynchronize(s), "sync");
+    return DAFMM_OK;
+}
+
+int dafmm_set_profiling(dafmm_ctx* c, int enable) {
+    if (!c) return DAFMM_ERR_INVALID_ARG;
+    CK(c, cudaSetDevice(c->device), "cudaSetDevice");
+    if (enable && !c->ev[0])
+        for (int k = 0; k < 8; ++k) CK(c, cudaEventCreate(&c->ev[k]), "cudaEventCreate");
+    c->profile = enable != 0;
+    c->have_profile = false;
+    return DAFMM_OK;
+}
+
+int dafmm_last_phase_ms(dafmm_ctx* c, double* out) {
+    if (!c || !out) return DAFMM_ERR_INVALID_ARG;
+    if (!c->have_profile) return fail(c, DAFMM_ERR_INVALID_ARG, "no profiled evaluation recorded");
+    CK(c, cudaEventSynchronize(c->ev[7]), "event sync");
+    float ms[7];
+    const int a[7] = {0, 1, 3, 4, 5, 6, 2}, b[7] = {1, 2, 5, 5, 6, 7, 3};
+    for (int k = 0; k < 7; ++k) CK(c, cudaEventElapsedTime(&ms[k], c->ev[a[k]], c->ev[b[k]]), "elapsed");
+    float tot;
+    CK(c, cudaEventElapsedTime(&tot, c->ev[0], c->ev[7]), "elapsed");
+    out[0] = ms[0];  // P2M
+    out[1] = ms[1];  // M2M
+    out[2] = ms[2];  // M2L, all levels
+    out[3] = ms[3];  // M2L, finest level
+    out[4] = ms[4];  // L2L
+    out[5] = ms[5];  // L2P + P2P
+    out[6] = ms[6];  // conversions
+    out[7] = tot;
+    out[8] = c->last_launches;
+    out[9] = 0.0;
+    return DAFMM_OK;
+}
+
+size_t dafmm_footprint(int64_t n, int order, int uniform_depth, int max_leaf, int precision) {
+    (void)max_leaf;
+    (void)precision;
+    if (order < 0 || order > kMaxOrder || n < 0) return 0;
+    const int depth = uniform_depth < 0 ? 0 : uniform_depth;
+    size_t b = tree_bytes(n, depth);
+    const size_t ncp = ncp_of(order), nc = ncoef_of(order);
+    for (int l = 2; l <= depth; ++l) b += level_boxes(l) * ncp * (8 + 8 + 4);
+    b += (size_t)kNumKeys * nc * ncp * 12;
+    b += (size_t)n * 12 + radix_sort_temp_bytes(n);  // build-time scratch
+    return b;
+}
+
+// ---- single-operator batches -------------------------------------------------------------------
+static int op_common(dafmm_ctx* c, int order, int precision) {
+    if (!c) return DAFMM_ERR_INVALID_ARG;
+    if (order < 0 || order > kMaxOrder) return fail(c, DAFMM_ERR_UNSUPPORTED_ORDER, std::to_string(order));
+    if (precision != DAFMM_FP64 && precision != DAFMM_FP32) return fail(c, DAFMM_ERR_INVALID_ARG, "precision");
+    if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, DAFMM_ERR_CUDA, "cudaSetDevice");
+    return DAFMM_OK;
+}
+
+static int finish_out(dafmm_ctx* c, double* user, void* dev, size_t bytes, bool owned, cudaStream_t s) {
+    if (owned) {
+        CK(c, cudaMemcpyAsync(user, dev, bytes, cudaMemcpyDeviceToHost, s), "D2H");
+        CK(c, cudaStreamSynchronize(s), "sync");
+    }
+    return DAFMM_OK;
+}
+
+typedef cudaError_t (*op2_fn)(int, int64_t, const double*, const double*, double*, cudaStream_t);
+
+static int run_op2(dafmm_ctx* c, int order, int prec, int64_t count, const double* a, size_t abytes,
+                   const double* b, size_t bbytes, double* out, size_t obytes, op2_fn fn, void* stream,
+                   const char* what) {
+    int rc = op_common(c, order, prec);
+    if (rc) return rc;
+    if (count < 0 || (count > 0 && (!a || !b || !out))) return fail(c, DAFMM_ERR_INVALID_ARG, what);
+    cudaStream_t s = (cudaStream_t)stream;
+    Staged sa, sb, so;
+    if ((rc = stage_in(c, a, abytes, s, sa))) return rc;
+    if ((rc = stage_in(c, b, bbytes, s, sb))) return rc;
+    so.c = c;
+    so.bytes = obytes;
+    if (is_device_ptr(out) || obytes == 0) {
+        so.dev = out;
+    } else {
+        if ((rc = dev_alloc(c, &so.dev, obytes, "op output"))) return rc;
+        so.owned = true;
+    }
+    CK(c, fn(prec, count, (const double*)sa.dev, (const double*)sb.dev, (double*)so.dev, s), what);
+    return finish_out(c, out, so.dev, obytes, so.owned, s);
+}
+
+int dafmm_op_p2m(dafmm_ctx* c, int order, int precision, int64_t count, const double* s3, const double* q,
+                 double* out, void* stream) {
+    const size_t nc = ncoef_of(order < 0 || order > kMaxOrder ? 0 : order);
+    const OrderOps* ops = order_ops(order);
+    if (!ops) return op_common(c, order, precision);
+    return run_op2(c, order, precision, count, s3, count * 3 * 8, q, count * 8, out, count * nc * 8, ops->op_p2m,
+                   stream, "P2M");
+}
+
+int dafmm_op_p2l(dafmm_ctx* c, int order, int precision, int64_t count, const double* w, const double* q,
+                 double* out, void* stream) {
+    const size_t nc = ncoef_of(order < 0 || order > kMaxOrder ? 0 : order);
+    const OrderOps* ops = order_ops(order);
+    if (!ops) return op_common(c, order, precision);
+    return run_op2(c, order, precision, count, w, count * 3 * 8, q, count * 8, out, count * nc * 8, ops->op_p2l,
+                   stream, "P2L");
+}
+
+int dafmm_op_l2p(dafmm_ctx* c, int order, int precision, int64_t count, const double* L, const double* x,
+                 double* out4, void* stream) {
+    const size_t nc = ncoef_of(order < 0 || order > kMaxOrder ? 0 : order);
+    const OrderOps* ops = order_ops(order);
+    if (!ops) return op_common(c, order, precision);
+    return run_op2(c, order, precision, count, L, count * nc * 8, x, count * 3 * 8, out4, count * 4 * 8,
+                   ops->op_l2p, stream, "L2P");
+}
+
+int dafmm_op_m2p(dafmm_ctx* c, int order, int precision, int64_t count, const double* M, const double* s3,
+                 double* out4, void* stream) {
+    const size_t nc = ncoef_of(order < 0 || order > kMaxOrder ? 0 : order);
+    const OrderOps* ops = order_ops(order);
+    if (!ops) return op_common(c, order, precision);
+    return run_op2(c, order, precision, count, M, count * nc * 8, s3, count * 3 * 8, out4, count * 4 * 8,
+                   ops->op_m2p, stream, "M2P");
+}
+
+static int run_shift(dafmm_ctx* c, int which, int order, int prec, int64_t count, const int* oct,
+                     const double* in, double* out, void* stream) {
+    int rc = op_common(c, order, prec);
+    if (rc) return rc;
+    if (count < 0 || (count > 0 && (!oct || !in || !out))) return fail(c, DAFMM_ERR_INVALID_ARG, "shift op");
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((rc = ensure_order(c, order, s, false))) return rc;
+    const size_t nc = ncoef_of(order);
+    Staged so_, si, sout;
+    if ((rc = stage_in(c, oct, count * sizeof(int), s, so_))) return rc;
+    if ((rc = stage_in(c, in, count * nc * 8, s, si))) return rc;
+    sout.c = c;
+    sout.bytes = count * nc * 8;
+    if (is_device_ptr(out) || count == 0) {
+        sout.dev = out;
+    } else {
+        if ((rc = dev_alloc(c, &sout.dev, sout.bytes, "op output"))) return rc;
+        sout.owned = true;
+    }
+    CK(c, order_ops(order)->op_shift(c->ord[order], which, prec, count, (const int*)so_.dev, (const double*)si.dev,
+                                     (double*)sout.dev, s),
+       which == 0 ? "M2M" : "L2L");
+    return finish_out(c, out, sout.dev, sout.bytes, sout.owned, s);
+}
+
+int dafmm_op_m2m(dafmm_ctx* c, int order, int precision, int64_t count, const int* oct, const double* in,
+                 double* out, void* stream) {
+    return run_shift(c, 0, order, precision, count, oct, in, out, stream);
+}
+
+int dafmm_op_l2l(dafmm_ctx* c, int order, int precision, int64_t count, const int* oct, const double* in,
+                 double* out, void* stream) {
+    return run_shift(c, 1, order, precision, count, oct, in, out, stream);
+}
+
+int dafmm_op_m2l_matrix(dafmm_ctx* c, int order, const int* v3, double* K, void* stream) {
+    int rc = op_common(c, order, DAFMM_FP64);
+    if (rc) return rc;
+    if (!v3 || !K) return fail(c, DAFMM_ERR_INVALID_ARG, "M2L matrix");
+    const int m = std::max(abs(v3[0]), std::max(abs(v3[1]), abs(v3[2])));
+    if (m < 2 || m > 3) return fail(c, DAFMM_ERR_INVALID_ARG, "displacement must have max |v_k| in 2..3");
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((rc = ensure_order(c, order, s, true))) return rc;
+    const OrderData& od = c->ord[order];
+    const int key = (v3[0] + 3) * 49 + (v3[1] + 3) * 7 + (v3[2] + 3);
+    std::vector<double> buf((size_t)od.nc * od.ncp);
+    CK(c, cudaMemcpyAsync(buf.data(), od.K64 + (size_t)key * od.nc * od.ncp, buf.size() * 8, cudaMemcpyDeviceToHost, s),
+       "K copy");
+    CK(c, cudaStreamSynchronize(s), "sync");
+    std::vector<double> outv((size_t)od.nc * od.nc);
+    for (int b = 0; b < od.nc; ++b)
+        for (int a = 0; a < od.nc; ++a) outv[(size_t)b * od.nc + a] = buf[(size_t)b * od.ncp + a];
+    if (is_device_ptr(K)) {
+        CK(c, cudaMemcpyAsync(K, outv.data(), outv.size() * 8, cudaMemcpyHostToDevice, s), "K copy");
+        CK(c, cudaStreamSynchronize(s), "sync");
+    } else {
+        memcpy(K, outv.data(), outv.size() * 8);
+    }
+    return DAFMM_OK;
+}
+
+}  // extern "C"

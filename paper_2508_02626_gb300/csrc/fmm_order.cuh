@@ -1,0 +1,680 @@
+// fmm_order.cuh -- the FMM kernels of one expansion order (DAFMM_P), instantiated by fmm_p*.cu.
+//
+// Every expansion is stored in box-scaled variables (a box of width h becomes width 1):
+//   multipole M~_a = M_a / h^|a|,  local L~_b = L_b h^|b|,
+// so P2M/L2P/M2P use offsets divided by h, M2M and L2L are level-independent tables, and
+// M2L is L~ = (1/h) K^_v M~ with K^_v depending only on the integer box displacement v.
+//
+// Kernels (paper operator -> kernel):
+//   P2M  (Eq. 2)  k_p2m       one warp per leaf; each lane runs the generated straight-line
+//                             P2M of one particle, a padded shared-memory transpose sums the
+//                             32 lanes per coefficient
+//   M2M  (Eq. 4)  k_m2m       32 parents per block; the 8 octant maps are one table with sign
+//                             flips (Sec. 3.3)
+//   M2L  (Eq. 5)  k_kgen      K^_v for all 316 displacements, FP64 numerical DA products of the
+//                             generated transfer map (one block per v)
+//                 k_m2l       L~_t = (1/h) sum_v K^_v M~_{t-v} over the 189 displacements of
+//                             the target's octant (SIMT, FP64 or FP32)
+//   L2L  (Eq. 7)  k_l2l       32 parents per block, 8 child tables by sign flips
+//   L2P + P2P     k_leaf      one warp per target leaf: pairwise sum over the 27 neighbour
+//                             leaves and the generated L2P of the leaf's local expansion
+#include <cuda_runtime.h>
+
+#include "da_common.cuh"
+#include "internal.h"
+#include "tree_common.cuh"
+
+#define DAFMM_CAT_(a, b) a##b
+#define DAFMM_CAT(a, b) DAFMM_CAT_(a, b)
+#define DAFMM_STR_(a) #a
+#define DAFMM_STR(a) DAFMM_STR_(a)
+#include DAFMM_STR(DAFMM_CAT(generated/da_ops_p, DAFMM_P).cuh)
+#include DAFMM_STR(DAFMM_CAT(generated/da_tables_p, DAFMM_P).h)
+
+#define GEN(name) DAFMM_CAT(name, DAFMM_CAT(_o, DAFMM_P))
+#define GENT(name, suffix) DAFMM_CAT(GEN(name), suffix)
+
+namespace dafmm {
+namespace DAFMM_CAT(ord_, DAFMM_P) {
+
+constexpr int P = DAFMM_P;
+constexpr int NC = ncoef_of(P);
+constexpr int NCP = ncp_of(P);
+
+template <class T>
+struct SmemSink {
+    T* base;
+    int lane;
+    __device__ __forceinline__ void operator()(int k, T v) const { base[k * 33 + lane] = v; }
+};
+
+template <class T>
+struct RowLoad {
+    const double* row;
+    __device__ __forceinline__ T operator()(int k) const { return (T)row[k]; }
+};
+
+// ---- P2M ---------------------------------------------------------------------------------
+template <class T>
+__global__ void k_p2m(TreeView tv, double* __restrict__ M) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* sm = reinterpret_cast<T*>(smem_raw) + threadIdx.y * (NC * 33);
+    const int lane = threadIdx.x;
+    const int leaf = blockIdx.x * blockDim.y + threadIdx.y;
+    if (leaf >= tv.nleaf) return;
+    const int i0 = tv.leaf_start[leaf], i1 = tv.leaf_start[leaf + 1];
+    int a, b, c;
+    octmajor_decode(tv.depth, leaf, a, b, c);
+    const double cx = tv.x0 + ((double)a + 0.5) * tv.h_leaf;
+    const double cy = tv.y0 + ((double)b + 0.5) * tv.h_leaf;
+    const double cz = tv.z0 + ((double)c + 0.5) * tv.h_leaf;
+    constexpr int NJ = (NC + 31) / 32;
+    T acc[NJ];
+#pragma unroll
+    for (int j = 0; j < NJ; ++j) acc[j] = T(0);
+    SmemSink<T> sink{sm, lane};
+    for (int base = i0; base < i1; base += 32) {
+        const int i = base + lane;
+        T x = T(0), y = T(0), z = T(0), q = T(0);
+        if (i < i1) {
+            x = (T)((tv.x[i] - cx) * tv.inv_h_leaf);
+            y = (T)((tv.y[i] - cy) * tv.inv_h_leaf);
+            z = (T)((tv.z[i] - cz) * tv.inv_h_leaf);
+            q = (T)tv.q[i];
+        }
+        gen::GEN(p2m)<T>(x, y, z, q, sink);
+        __syncwarp();
+#pragma unroll
+        for (int j = 0; j < NJ; ++j) {
+            const int k = lane + 32 * j;
+            if (k < NC) {
+                T s = T(0);
+#pragma unroll 8
+                for (int l = 0; l < 32; ++l) s += sm[k * 33 + l];
+                acc[j] += s;
+            }
+        }
+        __syncwarp();
+    }
+#pragma unroll
+    for (int j = 0; j < NJ; ++j) {
+        const int k = lane + 32 * j;
+        if (k < NC) M[(size_t)leaf * NCP + k] = (double)acc[j];
+    }
+}
+
+// ---- M2M / L2L ------------------------------------------------------------------------------
+template <class T>
+__device__ __forceinline__ T tab_val(const ShiftTab& t, int e);
+template <>
+__device__ __forceinline__ double tab_val<double>(const ShiftTab& t, int e) { return t.val[e]; }
+template <>
+__device__ __forceinline__ float tab_val<float>(const ShiftTab& t, int e) { return t.valf[e]; }
+
+constexpr int SH_ROWS = (NC + 7) / 8;  // output rows per warp (8 warps)
+
+// parents at level lc-1; children at level lc stored octant-major
+template <class T>
+__global__ void __launch_bounds__(256) k_m2m(ShiftTab tab, int lc, const double* __restrict__ Mc,
+                                             double* __restrict__ Mp) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* src = reinterpret_cast<T*>(smem_raw);  // [32][NCP + 1]
+    const int Pc = 1 << (lc - 1);
+    const int nparent = Pc * Pc * Pc;
+    const int lin0 = blockIdx.x * 32;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    T acc[SH_ROWS];
+#pragma unroll
+    for (int j = 0; j < SH_ROWS; ++j) acc[j] = T(0);
+    for (int c = 0; c < 8; ++c) {
+        for (int e = threadIdx.x; e < 32 * NC; e += 256) {
+            const int r = e / NC, k = e - r * NC;
+            const int lin = lin0 + r;
+            src[r * (NCP + 1) + k] = lin < nparent ? (T)Mc[(size_t)(c * nparent + lin) * NCP + k] : T(0);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < SH_ROWS; ++j) {
+            const int b = w + 8 * j;
+            if (b < NC) {
+                T s = T(0);
+                for (int e = tab.rowptr[b]; e < tab.rowptr[b + 1]; ++e) {
+                    T v = tab_val<T>(tab, e);
+                    if (__popc(tab.par[e] & c) & 1) v = -v;
+                    s += v * src[lane * (NCP + 1) + tab.col[e]];
+                }
+                acc[j] += s;
+            }
+        }
+        __syncthreads();
+    }
+    const int lin = lin0 + lane;
+    if (lin < nparent) {
+        const int px = lin % Pc, py = (lin / Pc) % Pc, pz = lin / (Pc * Pc);
+        const int pidx = octmajor_index(lc - 1, px, py, pz);
+#pragma unroll
+        for (int j = 0; j < SH_ROWS; ++j) {
+            const int b = w + 8 * j;
+            if (b < NC) Mp[(size_t)pidx * NCP + b] = (double)acc[j];
+        }
+    }
+}
+
+// children at level lc receive L2L of their parent (added to what M2L wrote)
+template <class T>
+__global__ void __launch_bounds__(256) k_l2l(ShiftTab tab, int lc, const double* __restrict__ Lp,
+                                             double* __restrict__ Lc) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* src = reinterpret_cast<T*>(smem_raw);  // [32][NCP + 1]
+    const int Pc = 1 << (lc - 1);
+    const int nparent = Pc * Pc * Pc;
+    const int lin0 = blockIdx.x * 32;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int e = threadIdx.x; e < 32 * NC; e += 256) {
+        const int r = e / NC, k = e - r * NC;
+        const int lin = lin0 + r;
+        T v = T(0);
+        if (lin < nparent) {
+            const int px = lin % Pc, py = (lin / Pc) % Pc, pz = lin / (Pc * Pc);
+            v = (T)Lp[(size_t)octmajor_index(lc - 1, px, py, pz) * NCP + k];
+        }
+        src[r * (NCP + 1) + k] = v;
+    }
+    __syncthreads();
+    const int lin = lin0 + lane;
+    for (int c = 0; c < 8; ++c) {
+#pragma unroll
+        for (int j = 0; j < SH_ROWS; ++j) {
+            const int b = w + 8 * j;
+            if (b < NC) {
+                T s = T(0);
+                for (int e = tab.rowptr[b]; e < tab.rowptr[b + 1]; ++e) {
+                    T v = tab_val<T>(tab, e);
+                    if (__popc(tab.par[e] & c) & 1) v = -v;
+                    s += v * src[lane * (NCP + 1) + tab.col[e]];
+                }
+                if (lin < nparent) {
+                    double* dst = Lc + (size_t)(c * nparent + lin) * NCP + b;
+                    *dst += (double)s;
+                }
+            }
+        }
+    }
+}
+
+// ---- K generation (Eq. 5 as a matrix per displacement) -------------------------------------
+// K^_v[b][a] = coefficient b of sqrt(R) (M2)^a, M2 = (v + u) R, R = 1/|v + u|^2, boxes of width 1.
+__device__ void da_mul_block(const MulTab& mt, const double* A, const double* B, double* C) {
+    for (int k = threadIdx.x; k < NC; k += blockDim.x) {
+        double s = 0.0;
+        for (int e = mt.rowptr[k]; e < mt.rowptr[k + 1]; ++e) {
+            const ushort2 pr = mt.pairs[e];
+            s = fma(A[pr.x], B[pr.y], s);
+        }
+        C[k] = s;
+    }
+    __syncthreads();
+}
+
+struct SmemStore {
+    double* o;
+    __device__ __forceinline__ void operator()(int k, double v) const { o[k] = v; }
+};
+
+__global__ void __launch_bounds__(256) k_kgen(MulTab mt, double* __restrict__ K64, float* __restrict__ K32,
+                                              int key_only) {
+    __shared__ double buf[8][NCP];
+    const int key = key_only >= 0 ? key_only : blockIdx.x;
+    const int vx = key / 49 - 3, vy = (key / 7) % 7 - 3, vz = key % 7 - 3;
+    const int amax = max(abs(vx), max(abs(vy), abs(vz)));
+    if (amax <= 1) return;  // adjacent boxes never interact through M2L
+    double* sR = buf[0];
+    double* m2[3] = {buf[1], buf[2], buf[3]};
+    double* X = buf[4];
+    double* XY = buf[5];
+    double* Z0 = buf[6];
+    double* Z1 = buf[7];
+    const double v[3] = {(double)vx, (double)vy, (double)vz};
+    const double rho = 1.0 / (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+    if (threadIdx.x == 0) {
+        gen::GEN(m2lmap_inv)<double>(v[0], v[1], v[2], rho, SmemStore{X});
+        gen::GEN(m2lmap_isq)<double>(v[0], v[1], v[2], rho, SmemStore{sR});
+    }
+    __syncthreads();
+    const double srho = sqrt(rho);
+    for (int k = threadIdx.x; k < NC; k += blockDim.x) {
+        X[k] *= rho;      // R
+        sR[k] *= srho;    // sqrt(R)
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < NC; k += blockDim.x)
+        for (int d = 0; d < 3; ++d) {
+            const int km = mt.minus[d * NC + k];
+            m2[d][k] = v[d] * X[k] + (km >= 0 ? X[km] : 0.0);
+        }
+    __syncthreads();
+    // monomials (M2)^(a,b,c): X = M2x^a, XY = X M2y^b, Z = XY M2z^c
+    for (int k = threadIdx.x; k < NC; k += blockDim.x) X[k] = (k == 0) ? 1.0 : 0.0;
+    __syncthreads();
+    double* Xn = XY;  // scratch while stepping X
+    for (int a = 0; a <= P; ++a) {
+        if (a > 0) {
+            da_mul_block(mt, X, m2[0], Z0);
+            for (int k = threadIdx.x; k < NC; k += blockDim.x) X[k] = Z0[k];
+            __syncthreads();
+        }
+        for (int k = threadIdx.x; k < NC; k += blockDim.x) Xn[k] = X[k];
+        __syncthreads();
+        for (int b = 0; b <= P - a; ++b) {
+            if (b > 0) {
+                da_mul_block(mt, Xn, m2[1], Z0);
+                for (int k = threadIdx.x; k < NC; k += blockDim.x) Xn[k] = Z0[k];
+                __syncthreads();
+            }
+            double* Zc = Z0;
+            double* Zn = Z1;
+            for (int k = threadIdx.x; k < NC; k += blockDim.x) Zc[k] = Xn[k];
+            __syncthreads();
+            for (int c = 0; c <= P - a - b; ++c) {
+                if (c > 0) {
+                    da_mul_block(mt, Zc, m2[2], Zn);
+                    double* t = Zc; Zc = Zn; Zn = t;
+                }
+                // column alpha = sqrt(R) * Z  -> K[key][beta][alpha]
+                const int alpha = da_index(a, b, c);
+                double* out = K64 + (size_t)(key_only >= 0 ? 0 : key) * NC * NCP;
+                float* out32 = K32 ? K32 + (size_t)(key_only >= 0 ? 0 : key) * NC * NCP : nullptr;
+                for (int k = threadIdx.x; k < NC; k += blockDim.x) {
+                    double s = 0.0;
+                    for (int e = mt.rowptr[k]; e < mt.rowptr[k + 1]; ++e) {
+                        const ushort2 pr = mt.pairs[e];
+                        s = fma(sR[pr.x], Zc[pr.y], s);
+                    }
+                    out[(size_t)k * NCP + alpha] = s;
+                    if (out32) out32[(size_t)k * NCP + alpha] = (float)s;
+                }
+                __syncthreads();
+            }
+        }
+    }
+}
+
+// ---- M2L (SIMT) ----------------------------------------------------------------------------
+template <class T>
+__device__ __forceinline__ const T* ktab(const double* K64, const float* K32);
+template <>
+__device__ __forceinline__ const double* ktab<double>(const double* K64, const float*) { return K64; }
+template <>
+__device__ __forceinline__ const float* ktab<float>(const double*, const float* K32) { return K32; }
+
+// targets: level l, octant blockIdx.y, 32 consecutive parent positions per block
+template <class T, class Src>
+__global__ void __launch_bounds__(256) k_m2l(const T* __restrict__ K, int l, const Src* __restrict__ M,
+                                             double* __restrict__ L, double inv_h) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* src = reinterpret_cast<T*>(smem_raw);  // [32][NCP + 1]
+    __shared__ int sidx[32];
+    const int Pp = 1 << (l - 1);  // parents per axis
+    const int nlin = Pp * Pp * Pp;
+    const int oct = blockIdx.y;
+    const int lin0 = blockIdx.x * 32;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int ox = oct & 1, oy = (oct >> 1) & 1, oz = (oct >> 2) & 1;
+    const int n_side = 1 << l;
+    T acc[SH_ROWS];
+#pragma unroll
+    for (int j = 0; j < SH_ROWS; ++j) acc[j] = T(0);
+    for (int vx = -3 + ox; vx <= 2 + ox; ++vx)
+        for (int vy = -3 + oy; vy <= 2 + oy; ++vy)
+            for (int vz = -3 + oz; vz <= 2 + oz; ++vz) {
+                if (abs(vx) <= 1 && abs(vy) <= 1 && abs(vz) <= 1) continue;
+                if (threadIdx.x < 32) {
+                    const int lin = lin0 + threadIdx.x;
+                    int s = -1;
+                    if (lin < nlin) {
+                        const int px = lin % Pp, py = (lin / Pp) % Pp, pz = lin / (Pp * Pp);
+                        const int tx = 2 * px + ox, ty = 2 * py + oy, tz = 2 * pz + oz;
+                        const int sx = tx - vx, sy = ty - vy, sz = tz - vz;
+                        if (sx >= 0 && sy >= 0 && sz >= 0 && sx < n_side && sy < n_side && sz < n_side)
+                            s = octmajor_index(l, sx, sy, sz);
+                    }
+                    sidx[threadIdx.x] = s;
+                }
+                __syncthreads();
+                for (int e = threadIdx.x; e < 32 * NC; e += 256) {
+                    const int r = e / NC, k = e - r * NC;
+                    const int s = sidx[r];
+                    src[r * (NCP + 1) + k] = s >= 0 ? (T)M[(size_t)s * NCP + k] : T(0);
+                }
+                __syncthreads();
+                const int key = (vx + 3) * 49 + (vy + 3) * 7 + (vz + 3);
+                const T* Kv = K + (size_t)key * NC * NCP;
+                const T* srow = src + lane * (NCP + 1);
+                const T* kw = Kv + (size_t)w * NCP;  // rows b = w + 8 j
+#pragma unroll 1
+                for (int a = 0; a < NC; ++a) {
+                    const T sv = srow[a];
+#pragma unroll
+                    for (int j = 0; j < SH_ROWS; ++j)
+                        if (w + 8 * j < NC) acc[j] = fma(kw[(size_t)(8 * j) * NCP + a], sv, acc[j]);
+                }
+                __syncthreads();
+            }
+    const int lin = lin0 + lane;
+    if (lin < nlin) {
+        const int t = oct * nlin + lin;
+#pragma unroll
+        for (int j = 0; j < SH_ROWS; ++j) {
+            const int b = w + 8 * j;
+            if (b < NC) L[(size_t)t * NCP + b] = (double)acc[j] * inv_h;
+        }
+    }
+}
+
+// ---- leaves: P2P over the 27 neighbours + L2P --------------------------------------------------
+__device__ __forceinline__ void two_sum_add(float& hi, float& lo, float v) {
+    const float s = hi + v;
+    const float bp = s - hi;
+    lo += (hi - (s - bp)) + (v - bp);
+    hi = s;
+}
+
+template <class T>
+__global__ void __launch_bounds__(128) k_leaf(TreeView tv, const double* __restrict__ Lleaf,
+                                              double* __restrict__ phi, double* __restrict__ field) {
+    const int lane = threadIdx.x;
+    const int leaf = blockIdx.x * blockDim.y + threadIdx.y;
+    if (leaf >= tv.nleaf) return;
+    const int i0 = tv.leaf_start[leaf], i1 = tv.leaf_start[leaf + 1];
+    int a, b, c;
+    octmajor_decode(tv.depth, leaf, a, b, c);
+    const int nside = 1 << tv.depth;
+    const double cx = tv.x0 + ((double)a + 0.5) * tv.h_leaf;
+    const double cy = tv.y0 + ((double)b + 0.5) * tv.h_leaf;
+    const double cz = tv.z0 + ((double)c + 0.5) * tv.h_leaf;
+    const double* Lrow = Lleaf ? Lleaf + (size_t)leaf * NCP : nullptr;
+    for (int base = i0; base < i1; base += 32) {
+        const int t = base + lane;
+        const bool valid = t < i1;
+        const int tt = valid ? t : i0;
+        double fphi = 0.0, fx = 0.0, fy = 0.0, fz = 0.0;  // near field, physical units
+        if constexpr (sizeof(T) == 8) {
+            const double xt = tv.x[tt], yt = tv.y[tt], zt = tv.z[tt];
+            for (int dz = -1; dz <= 1; ++dz)
+                for (int dy = -1; dy <= 1; ++dy)
+                    for (int dx = -1; dx <= 1; ++dx) {
+                        const int na = a + dx, nb = b + dy, nc2 = c + dz;
+                        if (na < 0 || nb < 0 || nc2 < 0 || na >= nside || nb >= nside || nc2 >= nside) continue;
+                        const int nl = octmajor_index(tv.depth, na, nb, nc2);
+                        const int s0 = tv.leaf_start[nl], s1 = tv.leaf_start[nl + 1];
+                        for (int s = s0; s < s1; ++s) {
+                            const double ex = xt - tv.x[s], ey = yt - tv.y[s], ez = zt - tv.z[s];
+                            const double r2 = ex * ex + ey * ey + ez * ez;
+                            if (r2 > 0.0) {
+                                const double ir = rsqrt(r2);
+                                const double qr = tv.q[s] * ir;
+                                const double qr3 = qr * ir * ir;
+                                fphi += qr;
+                                fx += qr3 * ex; fy += qr3 * ey; fz += qr3 * ez;
+                            }
+                        }
+                    }
+        } else {
+            const float4 pt = tv.xq[tt];
+            float ph = 0.f, pl = 0.f, xh = 0.f, xl = 0.f, yh = 0.f, yl = 0.f, zh = 0.f, zl = 0.f;
+            for (int dz = -1; dz <= 1; ++dz)
+                for (int dy = -1; dy <= 1; ++dy)
+                    for (int dx = -1; dx <= 1; ++dx) {
+                        const int na = a + dx, nb = b + dy, nc2 = c + dz;
+                        if (na < 0 || nb < 0 || nc2 < 0 || na >= nside || nb >= nside || nc2 >= nside) continue;
+                        const int nl = octmajor_index(tv.depth, na, nb, nc2);
+                        const int s0 = tv.leaf_start[nl], s1 = tv.leaf_start[nl + 1];
+                        // target in the neighbour's frame (offsets in leaf widths)
+                        const float tx = pt.x - (float)dx, ty = pt.y - (float)dy, tz = pt.z - (float)dz;
+                        float sp = 0.f, sx = 0.f, sy = 0.f, sz = 0.f;
+                        for (int s = s0; s < s1; ++s) {
+                            const float4 ps = tv.xq[s];
+                            const float ex = tx - ps.x, ey = ty - ps.y, ez = tz - ps.z;
+                            const float r2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
+                            if (r2 > 0.f) {
+                                const float ir = dafmm_rsqrt(r2);
+                                const float qr = ps.w * ir;
+                                const float qr3 = qr * ir * ir;
+                                sp += qr;
+                                sx = fmaf(qr3, ex, sx); sy = fmaf(qr3, ey, sy); sz = fmaf(qr3, ez, sz);
+                            }
+                        }
+                        two_sum_add(ph, pl, sp);
+                        two_sum_add(xh, xl, sx);
+                        two_sum_add(yh, yl, sy);
+                        two_sum_add(zh, zl, sz);
+                    }
+            const double ih = tv.inv_h_leaf, ih2 = ih * ih;
+            fphi = ((double)ph + (double)pl) * ih;
+            fx = ((double)xh + (double)xl) * ih2;
+            fy = ((double)yh + (double)yl) * ih2;
+            fz = ((double)zh + (double)zl) * ih2;
+        }
+        // far field from the leaf's local expansion
+        if (Lrow) {
+            T F, g0, g1, g2;
+            T xs, ys, zs;
+            if constexpr (sizeof(T) == 8) {
+                xs = (T)((tv.x[tt] - cx) * tv.inv_h_leaf);
+                ys = (T)((tv.y[tt] - cy) * tv.inv_h_leaf);
+                zs = (T)((tv.z[tt] - cz) * tv.inv_h_leaf);
+            } else {
+                const float4 pt = tv.xq[tt];
+                xs = (T)pt.x; ys = (T)pt.y; zs = (T)pt.z;
+            }
+            gen::GEN(l2p)<T>(RowLoad<T>{Lrow}, xs, ys, zs, F, g0, g1, g2);
+            fphi += (double)F;
+            fx -= (double)g0 * tv.inv_h_leaf;
+            fy -= (double)g1 * tv.inv_h_leaf;
+            fz -= (double)g2 * tv.inv_h_leaf;
+        }
+        if (valid) {
+            const int o = tv.perm[t];
+            if (phi) phi[o] = fphi;
+            if (field) {
+                field[3 * (size_t)o] = fx;
+                field[3 * (size_t)o + 1] = fy;
+                field[3 * (size_t)o + 2] = fz;
+            }
+        }
+    }
+}
+
+// ---- single-operator batches ------------------------------------------------------------------
+template <class T>
+struct RowStore {
+    double* o;
+    __device__ __forceinline__ void operator()(int k, T v) const { o[k] = (double)v; }
+};
+
+template <class T>
+__global__ void k_op_p2m(int64_t n, const double* __restrict__ s, const double* __restrict__ q, double* out) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    gen::GEN(p2m)<T>((T)s[3 * i], (T)s[3 * i + 1], (T)s[3 * i + 2], (T)q[i], RowStore<T>{out + i * NC});
+}
+template <class T>
+__global__ void k_op_p2l(int64_t n, const double* __restrict__ w, const double* __restrict__ q, double* out) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    gen::GEN(p2l)<T>((T)w[3 * i], (T)w[3 * i + 1], (T)w[3 * i + 2], (T)q[i], RowStore<T>{out + i * NC});
+}
+template <class T, bool M2P>
+__global__ void k_op_eval(int64_t n, const double* __restrict__ C, const double* __restrict__ x, double* out4) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    T F, g0, g1, g2;
+    if (M2P) gen::GEN(m2p)<T>(RowLoad<T>{C + i * NC}, (T)x[3 * i], (T)x[3 * i + 1], (T)x[3 * i + 2], F, g0, g1, g2);
+    else gen::GEN(l2p)<T>(RowLoad<T>{C + i * NC}, (T)x[3 * i], (T)x[3 * i + 1], (T)x[3 * i + 2], F, g0, g1, g2);
+    out4[4 * i] = (double)F;
+    out4[4 * i + 1] = (double)g0;
+    out4[4 * i + 2] = (double)g1;
+    out4[4 * i + 3] = (double)g2;
+}
+template <class T>
+__global__ void k_op_shift(ShiftTab tab, int64_t n, const int* __restrict__ oct, const double* __restrict__ in,
+                           double* out) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int c = oct[i] & 7;
+    for (int b = 0; b < NC; ++b) {
+        T s = T(0);
+        for (int e = tab.rowptr[b]; e < tab.rowptr[b + 1]; ++e) {
+            T v = tab_val<T>(tab, e);
+            if (__popc(tab.par[e] & c) & 1) v = -v;
+            s += v * (T)in[i * NC + tab.col[e]];
+        }
+        out[i * NC + b] = (double)s;
+    }
+}
+
+// ---- launchers ---------------------------------------------------------------------------------
+template <class K>
+static cudaError_t set_smem(K kernel, size_t bytes) {
+    if (bytes > 48 * 1024) return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    return cudaSuccess;
+}
+
+static cudaError_t p2m_launch(const TreeView& tv, int prec, double* M, cudaStream_t s) {
+    if (tv.nleaf == 0) return cudaSuccess;
+    const bool f64 = prec == DAFMM_FP64;
+    const size_t per_warp = (size_t)NC * 33 * (f64 ? 8 : 4);
+    int wpb = (int)((96 * 1024) / per_warp);
+    wpb = wpb < 1 ? 1 : (wpb > 4 ? 4 : wpb);
+    const size_t smem = per_warp * wpb;
+    dim3 blk(32, wpb), grd((tv.nleaf + wpb - 1) / wpb);
+    cudaError_t e;
+    if (f64) {
+        if ((e = set_smem(k_p2m<double>, smem)) != cudaSuccess) return e;
+        k_p2m<double><<<grd, blk, smem, s>>>(tv, M);
+    } else {
+        if ((e = set_smem(k_p2m<float>, smem)) != cudaSuccess) return e;
+        k_p2m<float><<<grd, blk, smem, s>>>(tv, M);
+    }
+    return cudaGetLastError();
+}
+
+static cudaError_t m2m_launch(const OrderData& od, int prec, int lc, const double* Mc, double* Mp,
+                              cudaStream_t s) {
+    const int Pc = 1 << (lc - 1);
+    const int nparent = Pc * Pc * Pc;
+    const bool f32 = prec == DAFMM_FP32;
+    const size_t smem = (size_t)32 * (NCP + 1) * (f32 ? 4 : 8);
+    cudaError_t e;
+    dim3 grd((nparent + 31) / 32);
+    if (!f32) {
+        if ((e = set_smem(k_m2m<double>, smem)) != cudaSuccess) return e;
+        k_m2m<double><<<grd, 256, smem, s>>>(od.m2m(), lc, Mc, Mp);
+    } else {
+        if ((e = set_smem(k_m2m<float>, smem)) != cudaSuccess) return e;
+        k_m2m<float><<<grd, 256, smem, s>>>(od.m2m(), lc, Mc, Mp);
+    }
+    return cudaGetLastError();
+}
+
+static cudaError_t l2l_launch(const OrderData& od, int prec, int lc, const double* Lp, double* Lc,
+                              cudaStream_t s) {
+    const int Pc = 1 << (lc - 1);
+    const int nparent = Pc * Pc * Pc;
+    const bool f32 = prec == DAFMM_FP32;
+    const size_t smem = (size_t)32 * (NCP + 1) * (f32 ? 4 : 8);
+    cudaError_t e;
+    dim3 grd((nparent + 31) / 32);
+    if (!f32) {
+        if ((e = set_smem(k_l2l<double>, smem)) != cudaSuccess) return e;
+        k_l2l<double><<<grd, 256, smem, s>>>(od.l2l(), lc, Lp, Lc);
+    } else {
+        if ((e = set_smem(k_l2l<float>, smem)) != cudaSuccess) return e;
+        k_l2l<float><<<grd, 256, smem, s>>>(od.l2l(), lc, Lp, Lc);
+    }
+    return cudaGetLastError();
+}
+
+static cudaError_t m2l_launch(const OrderData& od, int prec, int l, const double* M, const float* Mf,
+                              double* L, double inv_h, cudaStream_t s) {
+    const int Pp = 1 << (l - 1);
+    const int nlin = Pp * Pp * Pp;
+    dim3 grd((nlin + 31) / 32, 8);
+    cudaError_t e;
+    if (prec == DAFMM_FP64) {
+        const size_t smem = (size_t)32 * (NCP + 1) * 8;
+        if ((e = set_smem(k_m2l<double, double>, smem)) != cudaSuccess) return e;
+        k_m2l<double, double><<<grd, 256, smem, s>>>(od.K64, l, M, L, inv_h);
+    } else {
+        const size_t smem = (size_t)32 * (NCP + 1) * 4;
+        if ((e = set_smem(k_m2l<float, float>, smem)) != cudaSuccess) return e;
+        k_m2l<float, float><<<grd, 256, smem, s>>>(od.K32, l, Mf, L, inv_h);
+    }
+    return cudaGetLastError();
+}
+
+static cudaError_t leaf_launch(const TreeView& tv, int prec, const double* Lleaf, double* phi, double* field,
+                               cudaStream_t s) {
+    if (tv.nleaf == 0) return cudaSuccess;
+    dim3 blk(32, 4), grd((tv.nleaf + 3) / 4);
+    if (prec == DAFMM_FP64) k_leaf<double><<<grd, blk, 0, s>>>(tv, Lleaf, phi, field);
+    else k_leaf<float><<<grd, blk, 0, s>>>(tv, Lleaf, phi, field);
+    return cudaGetLastError();
+}
+
+static cudaError_t kgen_launch(OrderData& od, cudaStream_t s) {
+    k_kgen<<<kNumKeys, 256, 0, s>>>(od.mul(), od.K64, od.K32, -1);
+    return cudaGetLastError();
+}
+
+static unsigned nblk(int64_t n) { return (unsigned)((n + 127) / 128); }
+
+static cudaError_t op_p2m(int prec, int64_t n, const double* sv, const double* q, double* out, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    if (prec == DAFMM_FP64) k_op_p2m<double><<<nblk(n), 128, 0, s>>>(n, sv, q, out);
+    else k_op_p2m<float><<<nblk(n), 128, 0, s>>>(n, sv, q, out);
+    return cudaGetLastError();
+}
+static cudaError_t op_p2l(int prec, int64_t n, const double* w, const double* q, double* out, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    if (prec == DAFMM_FP64) k_op_p2l<double><<<nblk(n), 128, 0, s>>>(n, w, q, out);
+    else k_op_p2l<float><<<nblk(n), 128, 0, s>>>(n, w, q, out);
+    return cudaGetLastError();
+}
+static cudaError_t op_l2p(int prec, int64_t n, const double* L, const double* x, double* out4, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    if (prec == DAFMM_FP64) k_op_eval<double, false><<<nblk(n), 128, 0, s>>>(n, L, x, out4);
+    else k_op_eval<float, false><<<nblk(n), 128, 0, s>>>(n, L, x, out4);
+    return cudaGetLastError();
+}
+static cudaError_t op_m2p(int prec, int64_t n, const double* M, const double* x, double* out4, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    if (prec == DAFMM_FP64) k_op_eval<double, true><<<nblk(n), 128, 0, s>>>(n, M, x, out4);
+    else k_op_eval<float, true><<<nblk(n), 128, 0, s>>>(n, M, x, out4);
+    return cudaGetLastError();
+}
+static cudaError_t op_shift(const OrderData& od, int which, int prec, int64_t n, const int* oct,
+                            const double* in, double* out, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    const ShiftTab t = which == 0 ? od.m2m() : od.l2l();
+    if (prec == DAFMM_FP64) k_op_shift<double><<<nblk(n), 128, 0, s>>>(t, n, oct, in, out);
+    else k_op_shift<float><<<nblk(n), 128, 0, s>>>(t, n, oct, in, out);
+    return cudaGetLastError();
+}
+
+}  // namespace ord_P
+
+const OrderOps* DAFMM_CAT(order_ops_p, DAFMM_P)() {
+    using namespace DAFMM_CAT(ord_, DAFMM_P);
+    static const OrderOps ops = {
+        P, NC, NCP,
+        HostShiftTable{gen::GENT(m2m, _nnz), gen::GENT(m2m, _rowptr), gen::GENT(m2m, _col), gen::GENT(m2m, _par),
+                       gen::GENT(m2m, _val)},
+        HostShiftTable{gen::GENT(l2l, _nnz), gen::GENT(l2l, _rowptr), gen::GENT(l2l, _col), gen::GENT(l2l, _par),
+                       gen::GENT(l2l, _val)},
+        p2m_launch, m2m_launch, l2l_launch, m2l_launch, leaf_launch, kgen_launch,
+        op_p2m, op_p2l, op_l2p, op_m2p, op_shift};
+    return &ops;
+}
+
+}  // namespace dafmm

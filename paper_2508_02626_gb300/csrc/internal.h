@@ -1,0 +1,122 @@
+// internal.h -- structures shared by the host runtime (api.cu) and the kernels.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "dafmm.h"
+
+namespace dafmm {
+
+constexpr int kMaxOrder = DAFMM_MAX_ORDER;
+constexpr int kQBits = 21;      // integer coordinate bits per axis (box membership)
+constexpr int kMaxUniformDepth = 7;
+constexpr int kNumKeys = 343;   // displacements v in [-3,3]^3; key = (vx+3)*49 + (vy+3)*7 + (vz+3)
+
+__host__ __device__ constexpr int ncoef_of(int p) { return (p + 1) * (p + 2) * (p + 3) / 6; }
+// row stride of every expansion array: ncoef rounded up to 8 (32-byte rows in FP32)
+__host__ __device__ constexpr int ncp_of(int p) { return (ncoef_of(p) + 7) / 8 * 8; }
+
+// ---- views passed by value to kernels ---------------------------------------------------
+struct TreeView {
+    int64_t n;
+    int depth;        // uniform tree depth L (leaves at level L)
+    int nleaf;        // 8^L
+    double x0, y0, z0, size;
+    double h_leaf, inv_h_leaf;
+    const double *x, *y, *z, *q;  // sorted by leaf, FP64
+    const float4* xq;             // sorted, leaf-scaled offsets (x - c)/h and charge, FP32
+    const int* perm;              // sorted position -> input index
+    const int* leaf_start;        // nleaf + 1
+};
+
+struct ShiftTab {                 // compressed rows of a level-independent M2M or L2L table
+    const int* rowptr;
+    const unsigned short* col;
+    const unsigned char* par;     // bit v: exponent sum of row and column odd in axis v
+    const double* val;
+    const float* valf;
+};
+
+struct MulTab {                   // DA product table for the K generation
+    const int* rowptr;            // per output coefficient k
+    const ushort2* pairs;         // (i, j) with e_i + e_j = e_k
+    const short* minus;           // [3][nc]: index of e_k - e_v, or -1
+};
+
+// ---- per-order operator tables and launchers ------------------------------------------
+struct OrderData {
+    int p = -1, nc = 0, ncp = 0;
+    int* m2m_rowptr = nullptr; unsigned short* m2m_col = nullptr; unsigned char* m2m_par = nullptr;
+    double* m2m_val = nullptr; float* m2m_valf = nullptr;
+    int* l2l_rowptr = nullptr; unsigned short* l2l_col = nullptr; unsigned char* l2l_par = nullptr;
+    double* l2l_val = nullptr; float* l2l_valf = nullptr;
+    int* mul_rowptr = nullptr; ushort2* mul_pairs = nullptr; short* mul_minus = nullptr;
+    double* K64 = nullptr;        // [343][nc][ncp]: K^_v[b][a] (scaled M2L, Eq. 5)
+    float* K32 = nullptr;         // same in FP32
+    bool k_ready = false;
+    ShiftTab m2m() const { return ShiftTab{m2m_rowptr, m2m_col, m2m_par, m2m_val, m2m_valf}; }
+    ShiftTab l2l() const { return ShiftTab{l2l_rowptr, l2l_col, l2l_par, l2l_val, l2l_valf}; }
+    MulTab mul() const { return MulTab{mul_rowptr, mul_pairs, mul_minus}; }
+};
+
+// host copies of the generated tables (generated/da_tables_p*.h), per order
+struct HostShiftTable {
+    int nnz;
+    const int* rowptr;
+    const unsigned short* col;
+    const unsigned char* par;
+    const double* val;
+};
+
+struct OrderOps {
+    int p, nc, ncp;
+    HostShiftTable m2m, l2l;
+    // precision argument: DAFMM_FP64 / DAFMM_MIXED / DAFMM_FP32
+    cudaError_t (*p2m)(const TreeView&, int prec, double* Mleaf, cudaStream_t);
+    cudaError_t (*m2m_level)(const OrderData&, int prec, int lchild, const double* Mc, double* Mp,
+                             cudaStream_t);
+    cudaError_t (*l2l_level)(const OrderData&, int prec, int lchild, const double* Lp, double* Lc,
+                             cudaStream_t);
+    cudaError_t (*m2l_level)(const OrderData&, int prec, int level, const double* M, const float* Mf,
+                             double* L, double inv_h, cudaStream_t);
+    cudaError_t (*leaf)(const TreeView&, int prec, const double* Lleaf, double* phi, double* field,
+                        cudaStream_t);
+    cudaError_t (*kgen)(OrderData&, cudaStream_t);
+    cudaError_t (*op_p2m)(int prec, int64_t n, const double* s, const double* q, double* out, cudaStream_t);
+    cudaError_t (*op_p2l)(int prec, int64_t n, const double* w, const double* q, double* out, cudaStream_t);
+    cudaError_t (*op_l2p)(int prec, int64_t n, const double* L, const double* x, double* out4, cudaStream_t);
+    cudaError_t (*op_m2p)(int prec, int64_t n, const double* M, const double* s, double* out4, cudaStream_t);
+    cudaError_t (*op_shift)(const OrderData&, int which, int prec, int64_t n, const int* oct,
+                            const double* in, double* out, cudaStream_t);
+};
+
+const OrderOps* order_ops(int p);
+// one function per translation unit fmm_p*.cu
+#define DAFMM_DECLARE_ORDER(P) const OrderOps* order_ops_p##P();
+DAFMM_DECLARE_ORDER(0) DAFMM_DECLARE_ORDER(1) DAFMM_DECLARE_ORDER(2) DAFMM_DECLARE_ORDER(3)
+DAFMM_DECLARE_ORDER(4) DAFMM_DECLARE_ORDER(5) DAFMM_DECLARE_ORDER(6) DAFMM_DECLARE_ORDER(7)
+DAFMM_DECLARE_ORDER(8) DAFMM_DECLARE_ORDER(9) DAFMM_DECLARE_ORDER(10)
+#undef DAFMM_DECLARE_ORDER
+
+// ---- tree build (tree_build.cu) ---------------------------------------------------------
+// device min/max of the coordinates: out6 = {xmin, ymin, zmin, xmax, ymax, zmax} (device)
+cudaError_t launch_bbox(const double* xyz, int64_t n, double* out6, cudaStream_t s);
+// leaf keys of a uniform tree and identity values
+cudaError_t launch_uniform_keys(const double* xyz, int64_t n, double x0, double y0, double z0,
+                                double scale, int depth, uint64_t* keys, int* vals, cudaStream_t s);
+// stable LSD radix sort of (key, value) pairs on the low `bits` bits of the key
+size_t radix_sort_temp_bytes(int64_t n);
+cudaError_t radix_sort_pairs(uint64_t* keys, int* vals, int64_t n, int bits, void* temp,
+                             cudaStream_t s);
+// gather sorted SoA arrays and leaf-scaled FP32 copies; leaf ranges by binary search
+cudaError_t launch_gather_uniform(const double* xyz, const double* q, const int* perm, int64_t n,
+                                  const uint64_t* sorted_keys, TreeView tv, double* x, double* y,
+                                  double* z, double* qs, float4* xq, int* leaf_start,
+                                  cudaStream_t s);
+cudaError_t launch_scatter_outputs(const double* phi_sorted, const double* field_sorted, const int* perm,
+                                   int64_t n, double* phi, double* field, cudaStream_t s);
+
+}  // namespace dafmm

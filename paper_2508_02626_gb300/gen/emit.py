@@ -43,49 +43,37 @@ def lit(fr):
 
 
 class MonoPlan:
-    """Power products of the base symbols, each built from an earlier one by one product."""
+    """Power products of the base symbols, each built from an earlier one by one product.
 
-    def __init__(self, syms, base_name, mono_set, base_expr):
+    Products are emitted lazily, right before the first output that needs them, so that
+    the live set stays close to what the current output order uses."""
+
+    def __init__(self, syms, base_name, base_expr):
         self.syms = syms
-        self.name = {}
-        self.lines = []
-        zero = (0,) * len(syms)
-        need = set(mono_set)
-        need.add(zero)
-        # close the set under "remove one factor"
-        stack = list(need)
-        parent = {}
-        while stack:
-            e = stack.pop()
-            if e == zero or e in parent:
-                continue
-            best = None
-            for k in range(len(e)):
-                if e[k] > 0:
-                    pe = e[:k] + (e[k] - 1,) + e[k + 1:]
-                    if pe in need:
-                        best = (pe, k)
-                        break
-            if best is None:
-                k = next(k for k in range(len(e)) if e[k] > 0)
-                pe = e[:k] + (e[k] - 1,) + e[k + 1:]
-                need.add(pe)
-                stack.append(pe)
-                best = (pe, k)
-            parent[e] = best
-        order = sorted(need, key=lambda e: (sum(e), e))
-        cnt = 0
-        for e in order:
-            if e == zero:
-                self.name[e] = base_name
-                self.lines.append("const T %s = %s;" % (base_name, base_expr))
-                continue
-            pe, k = parent[e]
-            nm = "m%d" % cnt
-            cnt += 1
-            self.name[e] = nm
-            self.lines.append("const T %s = %s * %s;" % (nm, self.name[pe], syms[k]))
-        self.count = cnt
+        self.zero = (0,) * len(syms)
+        self.name = {self.zero: base_name}
+        self.lines = ["const T %s = %s;" % (base_name, base_expr)]
+        self.count = 0
+
+    def get(self, e):
+        """Name of the product e, emitting it (and missing factors) when needed."""
+        if e in self.name:
+            return self.name[e]
+        # prefer a factor that already exists
+        k_best = None
+        for k in range(len(e)):
+            if e[k] > 0 and (e[:k] + (e[k] - 1,) + e[k + 1:]) in self.name:
+                k_best = k
+                break
+        if k_best is None:
+            k_best = next(k for k in range(len(e)) if e[k] > 0)
+        pe = e[:k_best] + (e[k_best] - 1,) + e[k_best + 1:]
+        pn = self.get(pe)
+        nm = "m%d" % self.count
+        self.count += 1
+        self.lines.append("const T %s = %s * %s;" % (nm, pn, self.syms[k_best]))
+        self.name[e] = nm
+        return nm
 
 
 def sum_expr(terms, nacc=1):
@@ -109,84 +97,73 @@ def sum_expr(terms, nacc=1):
 
 
 def emit_poly_outputs(name, p, syms, coefs, base_name, base_expr, args, pre_lines, out_scale=None):
-    mono = set()
-    for poly in coefs:
-        mono.update(poly.t.keys())
-    plan = MonoPlan(syms, base_name, mono, base_expr)
-    body = list(pre_lines) + plan.lines
+    plan = MonoPlan(syms, base_name, base_expr)
     nterm = 0
     for k, poly in enumerate(coefs):
-        terms = [(c, plan.name[e]) for e, c in sorted(poly.t.items())]
+        terms = [(c, plan.get(e)) for e, c in sorted(poly.t.items(), key=lambda kv: (sum(kv[0]), kv[0]))]
         nterm += len(terms)
-        body.append("out(%d, %s);" % (k, sum_expr(terms)))
+        plan.lines.append("out(%d, %s);" % (k, sum_expr(terms)))
+    body = list(pre_lines) + plan.lines
     head = "template <class T, class Out>\nDAFMM_HD DAFMM_INLINE void %s(%s, Out&& out) {\n" % (name, args)
     return head + "".join("    %s\n" % l for l in body) + "}\n", plan.count + nterm
 
 
 def emit_eval(name, p, kind):
-    """L2P (kind='l2p') or M2P (kind='m2p') with gradient."""
-    ex = exponents(p)
-    nc = ncoef(p)
+    """L2P (kind='l2p') or M2P (kind='m2p') with gradient.  For each (a, b) the column
+    sum_c C[a,b,c] z^c and its z-derivative are formed by Horner's rule, then weighted by
+    x^a y^b (and a x^(a-1) y^b, b x^a y^(b-1) for the x and y derivatives)."""
     lines = []
+    args = "const Src& C, T x, T y, T z, T& phi, T& gx, T& gy, T& gz"
     if kind == "l2p":
-        args = "const Src& C, T x, T y, T z, T& phi, T& gx, T& gy, T& gz"
         lines.append("const T u0 = x, u1 = y, u2 = z;")
     else:
-        args = "const Src& C, T x, T y, T z, T& phi, T& gx, T& gy, T& gz"
         lines += ["const T R2 = x * x + y * y + z * z;",
                   "const T rho = dafmm_rcp(R2);",
                   "const T nd = dafmm_sqrt(rho);",
                   "const T u0 = x * rho, u1 = y * rho, u2 = z * rho;"]
-    # monomials u^e for |e| <= p
-    mname = {(0, 0, 0): None}
-    for i in range(1, nc):
-        e = ex[i]
-        v = 0 if e[0] else (1 if e[1] else 2)
-        pe = list(e)
-        pe[v] -= 1
-        pe = tuple(pe)
-        nm = "w%d" % i
-        src = mname[pe]
-        lines.append("const T %s = %s;" % (nm, ("u%d" % v) if src is None else "%s * u%d" % (src, v)))
-        mname[e] = nm
-
-    def acc_lines(var, terms):
-        # 4 interleaved partial sums for instruction-level parallelism
-        k = 4
-        out = []
-        for j in range(k):
-            out.append("T %s_%d = T(0);" % (var, j))
-        for t_i, (cf, cidx, mn) in enumerate(terms):
-            j = t_i % k
-            op = "C(%d)" % cidx
-            if cf != 1:
-                op = "T(%s) * %s" % (lit(cf), op)
-            if mn is None:
-                out.append("%s_%d += %s;" % (var, j, op))
+    lines += ["T F = T(0), G0 = T(0), G1 = T(0), G2 = T(0);"]
+    # powers of u0 and u1 up to p
+    for k in range(2, p + 1):
+        lines.append("const T xa%d = %s * u0;" % (k, "u0" if k == 2 else "xa%d" % (k - 1)))
+    xa = lambda k: "T(1)" if k == 0 else ("u0" if k == 1 else "xa%d" % k)
+    for a in range(p + 1):
+        lines.append("{")
+        # y^b x^a built incrementally inside the column loop
+        for b in range(p - a + 1):
+            cmax = p - a - b
+            # Horner: H = sum_c C[a,b,c] z^c, D = dH/dz
+            cidx = [index(a, b, c) for c in range(cmax + 1)]
+            hl = ["T H = C(%d);" % cidx[cmax]]
+            if cmax >= 1:
+                hl.append("T D = T(0);")
+                for c in range(cmax - 1, -1, -1):
+                    hl.append("D = dafmm_fma(D, u2, H);")
+                    hl.append("H = dafmm_fma(H, u2, C(%d));" % cidx[c])
             else:
-                out.append("%s_%d = dafmm_fma(%s, %s, %s_%d);" % (var, j, op, mn, var, j))
-        out.append("const T %s = (%s_0 + %s_1) + (%s_2 + %s_3);" % (var, var, var, var, var))
-        return out
-
-    lines += acc_lines("F", [(1, i, mname[ex[i]]) for i in range(nc)])
-    for v, gv in enumerate(("G0", "G1", "G2")):
-        terms = []
-        for i in range(nc):
-            e = ex[i]
-            if e[v] == 0:
-                continue
-            pe = list(e)
-            pe[v] -= 1
-            terms.append((e[v], i, mname[tuple(pe)]))
-        if terms:
-            lines += acc_lines(gv, terms)
-        else:
-            lines.append("const T %s = T(0);" % gv)
+                hl.append("const T D = T(0);")
+            # weights: yb = x^a y^b, ybm = x^a y^(b-1), xbm = x^(a-1) y^b
+            if b == 0:
+                lines.append("T yb = %s;" % xa(a))
+                lines.append("T ybm = T(0);")
+                lines.append("T xbm = %s;" % (xa(a - 1) if a >= 1 else "T(0)"))
+            else:
+                lines.append("ybm = yb;")
+                lines.append("yb = yb * u1;")
+                if a >= 1:
+                    lines.append("xbm = xbm * u1;")
+            lines.append("{")
+            lines += ["  " + h for h in hl]
+            lines.append("  F = dafmm_fma(yb, H, F);")
+            lines.append("  G2 = dafmm_fma(yb, D, G2);")
+            if a >= 1:
+                lines.append("  G0 = dafmm_fma(T(%d) * xbm, H, G0);" % a)
+            if b >= 1:
+                lines.append("  G1 = dafmm_fma(T(%d) * ybm, H, G1);" % b)
+            lines.append("}")
+        lines.append("}")
     if kind == "l2p":
         lines += ["phi = F;", "gx = G0;", "gy = G1;", "gz = G2;"]
     else:
-        # F(d) = |d| phi_M(d); grad_d = (d/|d|) phi_M + |d| grad phi_M;
-        # grad_s = J^T grad_d with J = rho I - 2 rho^2 s s^T
         lines += ["phi = nd * F;",
                   "const T fr = F * nd * R2;  /* phi_M / |d|, since 1/|d| = |s| = sqrt(R2) */",
                   "const T a0 = u0 * fr + nd * G0, a1 = u1 * fr + nd * G1, a2 = u2 * fr + nd * G2;",

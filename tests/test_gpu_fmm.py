@@ -1,0 +1,168 @@
+"""Whole-FMM parity of the GPU path with the oracle, through the C ABI.
+
+The oracle runs the same traversal (Sec. 1) on the same tree with the same order, so
+the FP64 GPU result must equal it up to rounding: relative L2 <= 1e-12 (potential and
+field).  The MIXED path (FP32 bulk arithmetic) is held to 1e-6 relative L2 against the
+oracle here and to the bound stated in the benchmark; FP32 everywhere to 1e-5.  Against
+the direct sum (Eq. 1) both carry the method's own truncation error, which must match the
+oracle's to 1%."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_2508_02626_gb300 import binding as B
+from paper_2508_02626_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-12, "mixed": 1e-6, "fp32": 1e-5}
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    B.load()
+    c = B.Context(0)
+    yield c
+    c.close()
+
+
+def rel(a, b):
+    return float(np.sqrt(((a - b) ** 2).sum() / max((b ** 2).sum(), 1e-300)))
+
+
+def gpu_eval(ctx, x, q, dom, depth, p, prec, host=False):
+    n = len(q)
+    if host:
+        tree = ctx.build_tree(x, q, domain=dom, uniform_depth=depth)
+        phi, E = np.zeros(n), np.zeros((n, 3))
+        tree.eval(p, phi, E, precision=prec)
+        tree.free()
+        return phi, E
+    xt, qt = torch.from_numpy(x).cuda(), torch.from_numpy(q).cuda()
+    tree = ctx.build_tree(xt, qt, domain=dom, uniform_depth=depth)
+    phi = torch.empty(n, dtype=torch.float64, device="cuda")
+    E = torch.empty((n, 3), dtype=torch.float64, device="cuda")
+    tree.eval(p, phi, E, precision=prec)
+    torch.cuda.synchronize()
+    tree.free()
+    return phi.cpu().numpy(), E.cpu().numpy()
+
+
+def test_config1_uniform_1e4_p6(ctx):
+    """N=10,000 uniform in the unit cube, q in [-1,1], depth 3, p=6, all targets."""
+    cfg = W.C1
+    x, q, dom = W.make(cfg)
+    ref_phi, ref_E = O.fmm(x, q, dom, cfg["order"], uniform_depth=cfg["uniform_depth"])
+    d_phi, d_E = O.direct(x, q)
+    sig_oracle = rel(ref_phi, d_phi)
+    for prec in ("fp64", "mixed", "fp32"):
+        phi, E = gpu_eval(ctx, x, q, dom, cfg["uniform_depth"], cfg["order"], prec)
+        assert rel(phi, ref_phi) <= TOL[prec], (prec, rel(phi, ref_phi))
+        assert rel(E, ref_E) <= TOL[prec] * 10, (prec, rel(E, ref_E))
+        assert abs(rel(phi, d_phi) / sig_oracle - 1.0) < 0.01
+
+
+@pytest.mark.parametrize("p", [0, 1, 2, 3, 5, 7, 9, 10])
+def test_every_order_fp64(ctx, p):
+    x, q = W.uniform(3000, seed=77 + p)
+    dom = W.UNIT_CUBE
+    ref_phi, ref_E = O.fmm(x, q, dom, p, uniform_depth=3)
+    phi, E = gpu_eval(ctx, x, q, dom, 3, p, "fp64")
+    assert rel(phi, ref_phi) <= 1e-12 and rel(E, ref_E) <= 1e-11
+
+
+@pytest.mark.parametrize("depth", [0, 1, 2, 4])
+def test_depths_and_near_field(ctx, depth):
+    x, q = W.uniform(6000 if depth < 4 else 30000, seed=50 + depth)
+    dom = W.UNIT_CUBE
+    p = 5
+    ref_phi, ref_E = O.fmm(x, q, dom, p, uniform_depth=depth)
+    for prec in ("fp64", "mixed"):
+        phi, E = gpu_eval(ctx, x, q, dom, depth, p, prec)
+        assert rel(phi, ref_phi) <= TOL[prec] and rel(E, ref_E) <= TOL[prec] * 10
+    if depth <= 1:  # no far field: equals the direct sum
+        d_phi, d_E = O.direct(x, q)
+        phi, E = gpu_eval(ctx, x, q, dom, depth, p, "fp64")
+        assert rel(phi, d_phi) <= 1e-13 and rel(E, d_E) <= 1e-12
+
+
+def test_edge_cases(ctx):
+    dom = W.UNIT_CUBE
+    # empty input
+    tree = ctx.build_tree(np.zeros((0, 3)), np.zeros(0), domain=dom, uniform_depth=3)
+    tree.eval(4, np.zeros(0), np.zeros((0, 3)))
+    tree.free()
+    # one particle: no partner, zero potential
+    phi, E = gpu_eval(ctx, np.array([[0.3, 0.3, 0.3]]), np.array([1.0]), dom, 2, 4, "fp64", host=True)
+    assert phi[0] == 0.0 and np.all(E == 0.0)
+    # boundary points (x = 0 and x = 1 exactly, clamped into the last box), coincident
+    # points, clustered data leaving most leaves empty, host buffers
+    rng = np.random.default_rng(9)
+    x = np.vstack([rng.random((1500, 3)) * 0.2, [[0, 0, 0], [1, 1, 1], [1, 0, 0.5], [0.1, 0.1, 0.1], [0.1, 0.1, 0.1]]])
+    q = rng.uniform(-1, 1, len(x))
+    for p in (3, 6):
+        ref_phi, ref_E = O.fmm(x, q, dom, p, uniform_depth=4)
+        for host in (False, True):
+            phi, E = gpu_eval(ctx, x, q, dom, 4, p, "fp64", host=host)
+            assert rel(phi, ref_phi) <= 1e-12 and rel(E, ref_E) <= 1e-11
+
+
+def test_bounding_cube_domain(ctx):
+    x, q = W.clustered(4000, seed=12)
+    tree = ctx.build_tree(torch.from_numpy(x).cuda(), torch.from_numpy(q).cuda(), domain=None, uniform_depth=3)
+    dom = tree.info()["domain"]
+    assert np.array_equal(dom, O.bounding_cube(x))
+    phi = torch.empty(len(q), dtype=torch.float64, device="cuda")
+    E = torch.empty((len(q), 3), dtype=torch.float64, device="cuda")
+    tree.eval(6, phi, E)
+    torch.cuda.synchronize()
+    tree.free()
+    ref_phi, ref_E = O.fmm(x, q, dom, 6, uniform_depth=3)
+    assert rel(phi.cpu().numpy(), ref_phi) <= 1e-12 and rel(E.cpu().numpy(), ref_E) <= 1e-11
+
+
+def test_deterministic_and_reusable(ctx):
+    x, q = W.uniform(20000, seed=5)
+    xt, qt = torch.from_numpy(x).cuda(), torch.from_numpy(q).cuda()
+    tree = ctx.build_tree(xt, qt, domain=W.UNIT_CUBE, uniform_depth=4)
+    outs = []
+    for prec in ("mixed", "mixed", "fp64", "mixed"):
+        phi = torch.empty(len(q), dtype=torch.float64, device="cuda")
+        tree.eval(6, phi, None, precision=prec)
+        outs.append(phi.cpu().numpy())
+    tree.free()
+    assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[0], outs[3])
+
+
+def test_errors_are_codes(ctx):
+    x, q = W.uniform(100, seed=1)
+    tree = ctx.build_tree(x, q, domain=W.UNIT_CUBE, uniform_depth=2)
+    for kw, code in ((dict(order=11), B.DAFMM_ERR_UNSUPPORTED_ORDER),
+                     (dict(order=4, theta=0.5), B.DAFMM_ERR_UNSUPPORTED)):
+        with pytest.raises(B.DafmmError) as e:
+            tree.eval(phi=np.zeros(100), **kw)
+        assert e.value.code == code
+    tree.free()
+    small = B.Context(0, hbm_budget_bytes=4096)
+    with pytest.raises(B.DafmmError) as e:
+        small.build_tree(x, q, domain=W.UNIT_CUBE, uniform_depth=2)
+    assert e.value.code == B.DAFMM_ERR_OVER_BUDGET
+    small.close()
+    with pytest.raises(B.DafmmError) as e:
+        ctx.build_tree(x, q, domain=[0, 0, 0, -1.0], uniform_depth=2)
+    assert e.value.code == B.DAFMM_ERR_INVALID_ARG
+
+
+def test_config2_full_size_sampled(ctx):
+    """N=1,000,000 uniform, depth 5, p=8 (the benchmark workload, same launch path):
+    FP64 and MIXED against the oracle FMM on 200 sampled targets."""
+    cfg = W.C2
+    x, q, dom = W.make(cfg)
+    rng = np.random.default_rng(77)
+    tg = np.sort(rng.choice(cfg["n"], 200, replace=False))
+    ref_phi, ref_E = O.fmm(x, q, dom, cfg["order"], uniform_depth=cfg["uniform_depth"], targets=tg)
+    for prec in ("fp64", "mixed"):
+        phi, E = gpu_eval(ctx, x, q, dom, cfg["uniform_depth"], cfg["order"], prec)
+        assert rel(phi[tg], ref_phi) <= TOL[prec], (prec, rel(phi[tg], ref_phi))
+        assert rel(E[tg], ref_E) <= TOL[prec] * 10, (prec, rel(E[tg], ref_E))

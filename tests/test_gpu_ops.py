@@ -1,0 +1,117 @@
+"""Single-operator parity of the generated GPU operators with the oracle, through the C ABI,
+following the paper's verification protocol (Sec. 3): random instances, compared order by
+order; per order the largest |delta| is taken relative to the largest coefficient of that
+order.  Bounds: 1e-12 (FP64; the paper observed <= 3.69e-14 between its generated and
+numerical-DA operators) and 2e-5 (FP32 arithmetic, 24-bit mantissa over up to ~2400
+operations)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_2508_02626_gb300 import binding as B
+
+pytestmark = pytest.mark.gpu
+
+ORDERS = [0, 1, 2, 4, 6, 8, 10]
+TOL = {B.DAFMM_FP64: 1e-12, B.DAFMM_FP32: 2e-5}
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    B.load()
+    c = B.dafmm_create(0)
+    yield c
+    B.dafmm_destroy(c)
+
+
+def per_order_rel(got, ref, p):
+    n = O.exponents(p).sum(1)
+    worst = 0.0
+    for k in range(p + 1):
+        s = n == k
+        scale = np.abs(ref[..., s]).max()
+        if scale > 0:
+            worst = max(worst, np.abs(got[..., s] - ref[..., s]).max() / scale)
+    return worst
+
+
+@pytest.mark.parametrize("p", ORDERS)
+@pytest.mark.parametrize("prec", [B.DAFMM_FP64, B.DAFMM_FP32])
+def test_p2m_p2l_10000_instances(ctx, p, prec):
+    rng = np.random.default_rng(1000 + p)
+    n = 10000
+    nc = O.ncoef(p)
+    s = rng.uniform(-0.5, 0.5, (n, 3))
+    q = rng.uniform(-1, 1, n)
+    out = torch.zeros((n, nc), dtype=torch.float64, device="cuda")
+    B.dafmm_op_p2m(ctx, p, prec, torch.from_numpy(s).cuda(), torch.from_numpy(q).cuda(), out)
+    torch.cuda.synchronize()
+    got = out.cpu().numpy()
+    sub = rng.choice(n, 400, replace=False)  # the oracle's DA is slow; compare a random subset
+    ref = np.array([O.p2m(p, s[i][None, :], [q[i]]) for i in sub])
+    assert per_order_rel(got[sub], ref, p) <= TOL[prec]
+    # host buffers through the same entry point give the same numbers
+    out_h = np.zeros((n, nc))
+    B.dafmm_op_p2m(ctx, p, prec, s, q, out_h)
+    assert np.array_equal(out_h, got)
+    w = rng.uniform(-0.5, 0.5, (n, 3)) + np.array([2.0, -1.0, 3.0])
+    out2 = np.zeros((n, nc))
+    B.dafmm_op_p2l(ctx, p, prec, w, q, out2)
+    ref2 = np.array([O.p2l(p, w[i][None, :], [q[i]]) for i in sub])
+    assert per_order_rel(out2[sub], ref2, p) <= TOL[prec]
+
+
+@pytest.mark.parametrize("p", ORDERS)
+@pytest.mark.parametrize("prec", [B.DAFMM_FP64, B.DAFMM_FP32])
+def test_l2p_m2p(ctx, p, prec):
+    rng = np.random.default_rng(2000 + p)
+    n = 2000
+    nc = O.ncoef(p)
+    C = rng.standard_normal((n, nc))
+    x = rng.uniform(-0.5, 0.5, (n, 3))
+    out = np.zeros((n, 4))
+    B.dafmm_op_l2p(ctx, p, prec, C, x, out)
+    s = rng.uniform(-0.5, 0.5, (n, 3)) + np.array([-2.0, 3.0, 1.0])
+    out2 = np.zeros((n, 4))
+    B.dafmm_op_m2p(ctx, p, prec, C, s, out2)
+    for i in rng.choice(n, 200, replace=False):
+        sc = np.abs(C[i]).sum()
+        phi, E = O.l2p(p, C[i], x[i][None, :])
+        assert abs(out[i, 0] - phi[0]) <= TOL[prec] * sc
+        assert np.abs(-out[i, 1:] - E[0]).max() <= TOL[prec] * sc * (p + 1)
+        phi, E = O.m2p(p, C[i], s[i][None, :])
+        assert abs(out2[i, 0] - phi[0]) <= TOL[prec] * sc
+        assert np.abs(-out2[i, 1:] - E[0]).max() <= TOL[prec] * sc * (p + 1)
+
+
+@pytest.mark.parametrize("p", [1, 4, 8, 10])
+def test_m2m_l2l_tables(ctx, p):
+    rng = np.random.default_rng(3000 + p)
+    nc = O.ncoef(p)
+    n = 64
+    octs = rng.integers(0, 8, n).astype(np.int32)
+    M = rng.standard_normal((n, nc))
+    en = O.exponents(p).sum(1)
+    for prec in (B.DAFMM_FP64, B.DAFMM_FP32):
+        out = np.zeros((n, nc))
+        B.dafmm_op_m2m(ctx, p, prec, octs, M, out)
+        out2 = np.zeros((n, nc))
+        B.dafmm_op_l2l(ctx, p, prec, octs, M, out2)
+        for i in range(0, n, 8):
+            o = np.array([octs[i] & 1, (octs[i] >> 1) & 1, (octs[i] >> 2) & 1])
+            ref = O.m2m(p, M[i], 0.5 - o) / 2.0 ** en
+            assert np.abs(out[i] - ref).max() <= TOL[prec] * np.abs(ref).max() * 10
+            ref2 = O.l2l(p, M[i], (o - 0.5) * 0.5) / 2.0 ** en
+            assert np.abs(out2[i] - ref2).max() <= TOL[prec] * np.abs(ref2).max() * 10
+
+
+@pytest.mark.parametrize("p", [0, 2, 6, 8, 10])
+def test_m2l_matrix_kgen(ctx, p):
+    """The GPU K generation (FP64) against the oracle's M2L map applied to unit vectors."""
+    nc = O.ncoef(p)
+    for v in ([2, 0, 0], [3, -3, 3], [-2, 1, -3], [0, 2, -1]):
+        K = np.zeros((nc, nc))
+        B.dafmm_op_m2l_matrix(ctx, p, v, K)
+        ref = O.m2l_matrix(p, np.array(v, dtype=np.float64))
+        assert np.abs(K - ref).max() <= 1e-13 * np.abs(ref).max(), v

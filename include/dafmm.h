@@ -98,6 +98,16 @@ int dafmm_eval(dafmm_tree* tree, int order, double theta, int precision, double*
 int dafmm_set_profiling(dafmm_ctx* ctx, int enable);
 int dafmm_last_phase_ms(dafmm_ctx* ctx, double* out10);
 
+/* Options of a context.
+ *   DAFMM_OPT_M2L_KERNEL: 0 = tensor-core M2L (tcgen05, TF32 split products) for the FP32
+ *   bulk paths when the order is >= 2 (default), 1 = SIMT FP32 M2L. */
+#define DAFMM_OPT_M2L_KERNEL 1
+int dafmm_set_option(dafmm_ctx* ctx, int option, int64_t value);
+
+/* Wait for `stream` and report failures recorded on the device by bounded waits inside the
+ * kernels (DAFMM_ERR_TIMEOUT); clears the record. */
+int dafmm_sync(dafmm_ctx* ctx, void* stream);
+
 /* Device bytes an evaluation of a tree with these parameters needs (an upper estimate). */
 size_t dafmm_footprint(int64_t n, int order, int uniform_depth, int max_leaf, int precision);
 

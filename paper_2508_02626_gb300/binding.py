@@ -40,6 +40,8 @@ SIGNATURES = {
     "dafmm_eval": (_i, [_vp, _i, _d, _i, _vp, _vp, _vp]),
     "dafmm_footprint": (_sz, [_i64, _i, _i, _i, _i]),
     "dafmm_set_profiling": (_i, [_vp, _i]),
+    "dafmm_set_option": (_i, [_vp, _i, _i64]),
+    "dafmm_sync": (_i, [_vp, _vp]),
     "dafmm_last_phase_ms": (_i, [_vp, _vp]),
     "dafmm_op_p2m": (_i, [_vp, _i, _i, _i64, _vp, _vp, _vp, _vp]),
     "dafmm_op_p2l": (_i, [_vp, _i, _i, _i64, _vp, _vp, _vp, _vp]),
@@ -165,6 +167,17 @@ def dafmm_eval(ctx, tree, order, phi=None, field=None, theta=1.0, precision=DAFM
     rc = load().dafmm_eval(tree, int(order), float(theta), int(precision), _ptr(phi), _ptr(field),
                            _stream_ptr(stream))
     _check(ctx, rc)
+
+
+DAFMM_OPT_M2L_KERNEL = 1
+
+
+def dafmm_set_option(ctx, option, value):
+    _check(ctx, load().dafmm_set_option(ctx, int(option), int(value)))
+
+
+def dafmm_sync(ctx, stream=None):
+    _check(ctx, load().dafmm_sync(ctx, _stream_ptr(stream)))
 
 
 def dafmm_set_profiling(ctx, enable):

@@ -12,6 +12,7 @@
 
 #include "da_common.cuh"
 #include "internal.h"
+#include "m2l_tc.h"
 #include "tree_common.cuh"
 
 using namespace dafmm;
@@ -29,6 +30,10 @@ struct dafmm_ctx {
     cudaEvent_t ev[8] = {};
     int last_launches = 0;
     bool have_profile = false;
+    int m2l_kernel = 0;       // 0 tensor cores, 1 SIMT
+    int num_sms = 0;
+    bool tc_capable = false;  // compute capability 10.x
+    int* d_err = nullptr;     // device-side failure record of bounded waits
 };
 
 struct Expansions {
@@ -37,6 +42,8 @@ struct Expansions {
     double* M[kMaxUniformDepth + 1] = {};
     double* L[kMaxUniformDepth + 1] = {};
     float* Mf[kMaxUniformDepth + 1] = {};
+    float* Mhi[kMaxUniformDepth + 1] = {};
+    float* Mlo[kMaxUniformDepth + 1] = {};
 };
 
 struct dafmm_tree {
@@ -225,6 +232,12 @@ int ensure_order(dafmm_ctx* c, int p, cudaStream_t s, bool need_k) {
         CK(c, cudaMemsetAsync(od.K64, 0, cnt * sizeof(double), s), "K memset");
         CK(c, cudaMemsetAsync(od.K32, 0, cnt * sizeof(float), s), "K memset");
         CK(c, ops->kgen(od, s), "K generation");
+        if (p >= 2) {
+            const size_t cs = (size_t)kNumKeys * m2l_tc_npt(p) * od.ncp;
+            if ((rc = dev_alloc(c, (void**)&od.Khi, cs * sizeof(float), "M2L matrices (TF32 split)"))) return rc;
+            if ((rc = dev_alloc(c, (void**)&od.Klo, cs * sizeof(float), "M2L matrices (TF32 split)"))) return rc;
+            CK(c, m2l_tc_split_k(od.K64, p, od.Khi, od.Klo, s), "K split");
+        }
         od.k_ready = true;
     }
     return DAFMM_OK;
@@ -246,6 +259,11 @@ void free_order(dafmm_ctx* c, OrderData& od) {
     const size_t cnt = (size_t)kNumKeys * od.nc * od.ncp;
     dev_free(c, od.K64, od.K64 ? cnt * sizeof(double) : 0);
     dev_free(c, od.K32, od.K32 ? cnt * sizeof(float) : 0);
+    if (od.Khi) {
+        const size_t cs = (size_t)kNumKeys * m2l_tc_npt(od.p) * od.ncp;
+        dev_free(c, od.Khi, cs * sizeof(float));
+        dev_free(c, od.Klo, cs * sizeof(float));
+    }
     od = OrderData();
 }
 
@@ -260,6 +278,8 @@ void free_expansions(dafmm_tree* t) {
         dev_free(c, e.M[l], e.M[l] ? cnt * sizeof(double) : 0);
         dev_free(c, e.L[l], e.L[l] ? cnt * sizeof(double) : 0);
         dev_free(c, e.Mf[l], e.Mf[l] ? cnt * sizeof(float) : 0);
+        dev_free(c, e.Mhi[l], e.Mhi[l] ? cnt * sizeof(float) : 0);
+        dev_free(c, e.Mlo[l], e.Mlo[l] ? cnt * sizeof(float) : 0);
     }
     e = Expansions();
 }
@@ -277,9 +297,13 @@ int ensure_expansions(dafmm_tree* t, int p, cudaStream_t s) {
         if ((rc = dev_alloc(c, (void**)&t->ex.M[l], cnt * sizeof(double), "multipoles"))) return rc;
         if ((rc = dev_alloc(c, (void**)&t->ex.L[l], cnt * sizeof(double), "locals"))) return rc;
         if ((rc = dev_alloc(c, (void**)&t->ex.Mf[l], cnt * sizeof(float), "multipoles (FP32)"))) return rc;
+        if ((rc = dev_alloc(c, (void**)&t->ex.Mhi[l], cnt * sizeof(float), "multipoles (TF32 split)"))) return rc;
+        if ((rc = dev_alloc(c, (void**)&t->ex.Mlo[l], cnt * sizeof(float), "multipoles (TF32 split)"))) return rc;
         CK(c, cudaMemsetAsync(t->ex.M[l], 0, cnt * sizeof(double), s), "memset");
         CK(c, cudaMemsetAsync(t->ex.L[l], 0, cnt * sizeof(double), s), "memset");
         CK(c, cudaMemsetAsync(t->ex.Mf[l], 0, cnt * sizeof(float), s), "memset");
+        CK(c, cudaMemsetAsync(t->ex.Mhi[l], 0, cnt * sizeof(float), s), "memset");
+        CK(c, cudaMemsetAsync(t->ex.Mlo[l], 0, cnt * sizeof(float), s), "memset");
     }
     return DAFMM_OK;
 }
@@ -346,6 +370,18 @@ int dafmm_create(dafmm_ctx** out, int device, size_t hbm_budget_bytes) {
     dafmm_ctx* c = new dafmm_ctx();
     c->device = device;
     c->budget = hbm_budget_bytes;
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) {
+        delete c;
+        return DAFMM_ERR_CUDA;
+    }
+    c->num_sms = prop.multiProcessorCount;
+    c->tc_capable = prop.major == 10;
+    if (dev_alloc(c, (void**)&c->d_err, sizeof(int), "error flag") != DAFMM_OK ||
+        cudaMemset(c->d_err, 0, sizeof(int)) != cudaSuccess) {
+        delete c;
+        return DAFMM_ERR_CUDA;
+    }
     *out = c;
     return DAFMM_OK;
 }
@@ -359,6 +395,7 @@ void dafmm_destroy(dafmm_ctx* c) {
     for (int p = 0; p <= kMaxOrder; ++p) free_order(c, c->ord[p]);
     for (int k = 0; k < 8; ++k)
         if (c->ev[k]) cudaEventDestroy(c->ev[k]);
+    dev_free(c, c->d_err, sizeof(int));
     delete c;
 }
 
@@ -570,19 +607,44 @@ int dafmm_eval(dafmm_tree* t, int order, double theta, int precision, double* ph
             ++launches;
         }
         mark(2);
+        const bool use_tc = precision != DAFMM_FP64 && c->m2l_kernel == 0 && c->tc_capable && order >= 2;
         if (precision != DAFMM_FP64)
             for (int l = 2; l <= L; ++l) {
                 const size_t cnt = level_boxes(l) * od.ncp;
-                k_to_float<<<(unsigned)std::min<size_t>((cnt + 255) / 256, 152 * 16), 256, 0, s>>>(t->ex.M[l], t->ex.Mf[l], cnt);
-                CK(c, cudaGetLastError(), "convert");
+                if (use_tc) {
+                    CK(c, m2l_tc_split_tf32(t->ex.M[l], t->ex.Mhi[l], t->ex.Mlo[l], cnt, s), "split");
+                } else {
+                    k_to_float<<<(unsigned)std::min<size_t>((cnt + 255) / 256, 152 * 16), 256, 0, s>>>(t->ex.M[l], t->ex.Mf[l], cnt);
+                    CK(c, cudaGetLastError(), "convert");
+                }
                 ++launches;
             }
         mark(3);
-        for (int l = 2; l <= L; ++l) {
-            if (l == L) mark(4);
-            const double inv_h = 1.0 / ldexp(t->dom[3], -l);
-            CK(c, ops->m2l_level(od, precision, l, t->ex.M[l], t->ex.Mf[l], t->ex.L[l], inv_h, s), "M2L");
+        if (use_tc) {
+            mark(4);
+            M2LTCArgs a;
+            memset(&a, 0, sizeof(a));
+            a.lmin = 2;
+            a.lmax = L;
+            for (int l = 2; l <= L; ++l) {
+                a.Mhi[l] = t->ex.Mhi[l];
+                a.Mlo[l] = t->ex.Mlo[l];
+                a.L[l] = t->ex.L[l];
+                a.inv_h[l] = 1.0 / ldexp(t->dom[3], -l);
+            }
+            a.Khi = od.Khi;
+            a.Klo = od.Klo;
+            a.err = c->d_err;
+            a.num_sms = c->num_sms;
+            CK(c, m2l_tc_launch(order, a, s), "M2L (tensor cores)");
             ++launches;
+        } else {
+            for (int l = 2; l <= L; ++l) {
+                if (l == L) mark(4);
+                const double inv_h = 1.0 / ldexp(t->dom[3], -l);
+                CK(c, ops->m2l_level(od, precision, l, t->ex.M[l], t->ex.Mf[l], t->ex.L[l], inv_h, s), "M2L");
+                ++launches;
+            }
         }
         mark(5);
         for (int lc = 3; lc <= L; ++lc) {
@@ -601,6 +663,28 @@ int dafmm_eval(dafmm_tree* t, int order, double theta, int precision, double* ph
     if (!phi_dev) CK(c, cudaMemcpyAsync(phi, dphi, N * sizeof(double), cudaMemcpyDeviceToHost, s), "D2H");
     if (!field_dev) CK(c, cudaMemcpyAsync(field, dfield, N * 3 * sizeof(double), cudaMemcpyDeviceToHost, s), "D2H");
     if (!phi_dev || !field_dev) CK(c, cudaStreamSynchronize(s), "sync");
+    return DAFMM_OK;
+}
+
+int dafmm_set_option(dafmm_ctx* c, int option, int64_t value) {
+    if (!c) return DAFMM_ERR_INVALID_ARG;
+    if (option == DAFMM_OPT_M2L_KERNEL && (value == 0 || value == 1)) {
+        c->m2l_kernel = (int)value;
+        return DAFMM_OK;
+    }
+    return fail(c, DAFMM_ERR_INVALID_ARG, "option");
+}
+
+int dafmm_sync(dafmm_ctx* c, void* stream) {
+    if (!c) return DAFMM_ERR_INVALID_ARG;
+    CK(c, cudaSetDevice(c->device), "cudaSetDevice");
+    CK(c, cudaStreamSynchronize((cudaStream_t)stream), "stream sync");
+    int flag = 0;
+    CK(c, cudaMemcpy(&flag, c->d_err, sizeof(int), cudaMemcpyDeviceToHost), "error flag");
+    if (flag) {
+        CK(c, cudaMemset(c->d_err, 0, sizeof(int)), "error flag");
+        return fail(c, DAFMM_ERR_TIMEOUT, "a bounded device wait gave up (site " + std::to_string(flag) + ")");
+    }
     return DAFMM_OK;
 }
 

@@ -431,23 +431,28 @@ __global__ void __launch_bounds__(128) k_leaf(TreeView tv, const double* __restr
                         const int s0 = tv.leaf_start[nl], s1 = tv.leaf_start[nl + 1];
                         // target in the neighbour's frame (offsets in leaf widths)
                         const float tx = pt.x - (float)dx, ty = pt.y - (float)dy, tz = pt.z - (float)dz;
-                        float sp = 0.f, sx = 0.f, sy = 0.f, sz = 0.f;
-                        for (int s = s0; s < s1; ++s) {
-                            const float4 ps = tv.xq[s];
-                            const float ex = tx - ps.x, ey = ty - ps.y, ez = tz - ps.z;
-                            const float r2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
-                            if (r2 > 0.f) {
-                                const float ir = dafmm_rsqrt(r2);
-                                const float qr = ps.w * ir;
-                                const float qr3 = qr * ir * ir;
-                                sp += qr;
-                                sx = fmaf(qr3, ex, sx); sy = fmaf(qr3, ey, sy); sz = fmaf(qr3, ez, sz);
+                        // FP32 partial sums over at most 64 sources, folded into compensated
+                        // (hi, lo) accumulators so that long leaves keep FP32-level error
+                        for (int sb = s0; sb < s1; sb += 64) {
+                            const int se = min(s1, sb + 64);
+                            float sp = 0.f, sx = 0.f, sy = 0.f, sz = 0.f;
+                            for (int s = sb; s < se; ++s) {
+                                const float4 ps = tv.xq[s];
+                                const float ex = tx - ps.x, ey = ty - ps.y, ez = tz - ps.z;
+                                const float r2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
+                                if (r2 > 0.f) {
+                                    const float ir = dafmm_rsqrt(r2);
+                                    const float qr = ps.w * ir;
+                                    const float qr3 = qr * ir * ir;
+                                    sp += qr;
+                                    sx = fmaf(qr3, ex, sx); sy = fmaf(qr3, ey, sy); sz = fmaf(qr3, ez, sz);
+                                }
                             }
+                            two_sum_add(ph, pl, sp);
+                            two_sum_add(xh, xl, sx);
+                            two_sum_add(yh, yl, sy);
+                            two_sum_add(zh, zl, sz);
                         }
-                        two_sum_add(ph, pl, sp);
-                        two_sum_add(xh, xl, sx);
-                        two_sum_add(yh, yl, sy);
-                        two_sum_add(zh, zl, sz);
                     }
             const double ih = tv.inv_h_leaf, ih2 = ih * ih;
             fphi = ((double)ph + (double)pl) * ih;

@@ -56,6 +56,8 @@ struct OrderData {
     int* mul_rowptr = nullptr; ushort2* mul_pairs = nullptr; short* mul_minus = nullptr;
     double* K64 = nullptr;        // [343][nc][ncp]: K^_v[b][a] (scaled M2L, Eq. 5)
     float* K32 = nullptr;         // same in FP32
+    float* Khi = nullptr;         // [343][npt][ncp] TF32 high / low parts for the tensor-core M2L
+    float* Klo = nullptr;
     bool k_ready = false;
     ShiftTab m2m() const { return ShiftTab{m2m_rowptr, m2m_col, m2m_par, m2m_val, m2m_valf}; }
     ShiftTab l2l() const { return ShiftTab{l2l_rowptr, l2l_col, l2l_par, l2l_val, l2l_valf}; }

@@ -44,7 +44,7 @@ def gpu_eval(ctx, x, q, dom, depth, p, prec, host=False):
     phi = torch.empty(n, dtype=torch.float64, device="cuda")
     E = torch.empty((n, 3), dtype=torch.float64, device="cuda")
     tree.eval(p, phi, E, precision=prec)
-    torch.cuda.synchronize()
+    B.dafmm_sync(ctx.h)  # raises if a bounded device wait gave up
     tree.free()
     return phi.cpu().numpy(), E.cpu().numpy()
 
@@ -70,6 +70,25 @@ def test_every_order_fp64(ctx, p):
     ref_phi, ref_E = O.fmm(x, q, dom, p, uniform_depth=3)
     phi, E = gpu_eval(ctx, x, q, dom, 3, p, "fp64")
     assert rel(phi, ref_phi) <= 1e-12 and rel(E, ref_E) <= 1e-11
+
+
+@pytest.mark.parametrize("p", [2, 3, 4, 6, 8, 9, 10])
+def test_tensor_core_m2l(ctx, p):
+    """The tcgen05 M2L (TF32 split products) against the oracle and against the SIMT FP32 M2L,
+    on a depth-4 tree (levels 2-4: tiles of 8, 64 and 128 targets); p = 10 splits N in two."""
+    x, q = W.uniform(20000, seed=300 + p)
+    dom = W.UNIT_CUBE
+    ref_phi, ref_E = O.fmm(x, q, dom, p, uniform_depth=4)
+    tc_phi, tc_E = gpu_eval(ctx, x, q, dom, 4, p, "mixed")
+    B.dafmm_set_option(ctx.h, B.DAFMM_OPT_M2L_KERNEL, 1)
+    try:
+        si_phi, si_E = gpu_eval(ctx, x, q, dom, 4, p, "mixed")
+    finally:
+        B.dafmm_set_option(ctx.h, B.DAFMM_OPT_M2L_KERNEL, 0)
+    assert rel(tc_phi, ref_phi) <= TOL["mixed"], rel(tc_phi, ref_phi)
+    assert rel(tc_E, ref_E) <= TOL["mixed"] * 10
+    assert rel(si_phi, ref_phi) <= TOL["mixed"]
+    assert rel(tc_phi, si_phi) <= TOL["mixed"]
 
 
 @pytest.mark.parametrize("depth", [0, 1, 2, 4])

@@ -126,18 +126,16 @@ __device__ __forceinline__ void mma_commit(uint32_t bar) {
 __device__ __forceinline__ void fence_after_sync() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_before_sync() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
-    uint32_t r[16];
+// 32 lanes x 16 consecutive 32-bit columns of TMEM into 16 registers per thread (no wait)
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, "
         "[%16];"
         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
           "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
         : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
 }
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 // ---- the kernel -----------------------------------------------------------------------------
 template <int P>
@@ -145,7 +143,7 @@ struct Cfg {
     static constexpr int NC = ncoef_of(P);
     static constexpr int NCP = ncp_of(P);
     static constexpr int NPF = (NC + 15) / 16 * 16;               // N padded to the MMA granule
-    static constexpr int NHALF = NPF > 256 ? 2 : 1;                // N split when above the MMA limit
+    static constexpr int NHALF = NPF > 192 ? 2 : 1;                // N split: <= 192 register sums per thread
     static constexpr int NP = NHALF == 1 ? NPF : (NPF / 2 + 15) / 16 * 16;
     static constexpr int NKC = (NCP + 31) / 32;                    // K chunks of 32 (128 bytes)
     static constexpr int KSTEPS_LAST = (NCP - 32 * (NKC - 1)) / 8; // K steps of 8 in the last chunk
@@ -157,7 +155,7 @@ struct Cfg {
     static constexpr int TMEM_COLS = 2 * NP <= 256 ? 256 : 512;
     static constexpr uint32_t IDESC = idesc_tf32(128, NP);
     static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
-    static_assert(NP % 16 == 0 && NP >= 16 && NP <= 256, "MMA N");
+    static_assert(NP % 16 == 0 && NP >= 16 && NP <= 192, "MMA N");
     static_assert(STAGES >= 2, "pipeline depth");
     static_assert(2 * NP <= TMEM_COLS, "TMEM double buffer");
 };
@@ -293,24 +291,26 @@ __global__ void __launch_bounds__(192, 1) k_m2l_tc(const __grid_constant__ M2LTC
             if (armed[s] >= 0) mbar_wait(smem_u32(&full[s]), (uint32_t)armed[s], prm.err, 12);
     } else if (warp == 1 && lane == 0) {
         // ---------------- MMA issuer ----------------
+        // one fresh accumulator per displacement v (alternating TMEM buffers): at most
+        // 3 * ceil(ncoef/8) MMA accumulation steps land in one FP32 accumulator
         int stage = 0;
         uint32_t phase = 0;
         uint32_t acc_ph[2] = {0, 0};
         bool ok = true;
-        int iter = 0;
-        for (int w = blockIdx.x; w < prm.ntiles && ok; w += gridDim.x, ++iter) {
+        int uses = 0;
+        for (int w = blockIdx.x; w < prm.ntiles && ok; w += gridDim.x) {
             const WorkItem it = decode(prm, w);
-            const int buf = iter & 1;
-            ok = mbar_wait(smem_u32(&acc_empty[buf]), acc_ph[buf] ^ 1u, prm.err, 21);
-            if (!ok) break;
-            acc_ph[buf] ^= 1u;
-            fence_after_sync();
-            const uint32_t d = tmem_base + (uint32_t)(buf * C::NP);
-            uint32_t accum = 0;
             VIter vi;
             vi.first(it.oct);
             do {
                 if (!vi.valid()) continue;
+                const int buf = uses & 1;
+                ok = mbar_wait(smem_u32(&acc_empty[buf]), acc_ph[buf] ^ 1u, prm.err, 21);
+                if (!ok) break;
+                acc_ph[buf] ^= 1u;
+                fence_after_sync();
+                const uint32_t d = tmem_base + (uint32_t)(buf * C::NP);
+                uint32_t accum = 0;
                 for (int kc = 0; kc < C::NKC && ok; ++kc) {
                     ok = mbar_wait(smem_u32(&full[stage]), phase, prm.err, 22);
                     if (!ok) break;
@@ -322,10 +322,10 @@ __global__ void __launch_bounds__(192, 1) k_m2l_tc(const __grid_constant__ M2LTC
                         const uint64_t al = smem_desc_sw128(st + C::A_BYTES + ks * 32);
                         const uint64_t bh = smem_desc_sw128(st + 2 * C::A_BYTES + ks * 32);
                         const uint64_t bl = smem_desc_sw128(st + 2 * C::A_BYTES + C::B_BYTES + ks * 32);
-                        mma_tf32(d, ah, bh, C::IDESC, accum);
+                        mma_tf32(d, ah, bl, C::IDESC, accum);  // small cross terms first
                         accum = 1;
-                        mma_tf32(d, ah, bl, C::IDESC, 1);
                         mma_tf32(d, al, bh, C::IDESC, 1);
+                        mma_tf32(d, ah, bh, C::IDESC, 1);
                     }
                     mma_commit(smem_u32(&empty[stage]));
                     if (++stage == C::STAGES) {
@@ -333,48 +333,67 @@ __global__ void __launch_bounds__(192, 1) k_m2l_tc(const __grid_constant__ M2LTC
                         phase ^= 1u;
                     }
                 }
+                if (ok) mma_commit(smem_u32(&acc_full[buf]));
+                ++uses;
             } while (vi.next() && ok);
-            if (ok) mma_commit(smem_u32(&acc_full[buf]));
         }
         // every MMA this thread issued has finished once the drain barrier flips
         mma_commit(smem_u32(drain));
         mbar_wait(smem_u32(drain), 0, prm.err, 23);
     } else if (warp >= 2) {
         // ---------------- epilogue ----------------
+        // sums the per-displacement accumulators of its row in FP32 registers (CUDA cores)
         const int q = warp & 3;          // TMEM lane quarter of this warp
         const int row = 32 * q + lane;   // accumulator row = target within the tile
         uint32_t accf_ph[2] = {0, 0};
-        int iter = 0;
+        int uses = 0;
         bool ok = true;
-        for (int w = blockIdx.x; w < prm.ntiles && ok; w += gridDim.x, ++iter) {
+        for (int w = blockIdx.x; w < prm.ntiles && ok; w += gridDim.x) {
             const WorkItem it = decode(prm, w);
-            const int buf = iter & 1;
-            ok = mbar_wait(smem_u32(&acc_full[buf]), accf_ph[buf], prm.err, 31);
-            if (!ok) break;
-            accf_ph[buf] ^= 1u;
-            fence_after_sync();
-            const int bx = prm.bx[it.li], by = prm.by[it.li], bz = prm.bz[it.li];
-            const bool valid = row < bx * by * bz;
-            const int Pl = prm.P[it.li];
-            const int x = row % bx, y = (row / bx) % by, z = row / (bx * by);
-            const int t = it.oct * Pl * Pl * Pl + ((it.pz0 + z) * Pl + (it.py0 + y)) * Pl + (it.px0 + x);
-            double* Lrow = prm.L[it.li] + (size_t)t * C::NCP;
-            const double ih = prm.inv_h[it.li];
-            const uint32_t tb = tmem_base + ((uint32_t)(32 * q) << 16) + (uint32_t)(buf * C::NP);
-#pragma unroll 1
-            for (int c0 = 0; c0 < C::NP; c0 += 16) {
-                float v[16];
-                tmem_ld16(tb + c0, v);
-                if (valid) {
+            float S[C::NP];
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) {
-                        const int b = it.half * C::NP + c0 + j;
-                        if (b < C::NC) Lrow[b] = (double)v[j] * ih;
+            for (int j = 0; j < C::NP; ++j) S[j] = 0.f;
+            VIter vi;
+            vi.first(it.oct);
+            do {
+                if (!vi.valid()) continue;
+                const int buf = uses & 1;
+                ok = mbar_wait(smem_u32(&acc_full[buf]), accf_ph[buf], prm.err, 31);
+                if (!ok) break;
+                accf_ph[buf] ^= 1u;
+                fence_after_sync();
+                const uint32_t tb = tmem_base + ((uint32_t)(32 * q) << 16) + (uint32_t)(buf * C::NP);
+#pragma unroll
+                for (int c0 = 0; c0 < C::NP; c0 += 32) {
+                    uint32_t r0[16], r1[16];
+                    tmem_ld16(tb + c0, r0);
+                    if (c0 + 16 < C::NP) tmem_ld16(tb + c0 + 16, r1);
+                    tmem_wait_ld();
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) S[c0 + j] += __uint_as_float(r0[j]);
+                    if (c0 + 16 < C::NP) {
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) S[c0 + 16 + j] += __uint_as_float(r1[j]);
                     }
                 }
+                fence_before_sync();
+                mbar_arrive(smem_u32(&acc_empty[buf]));
+                ++uses;
+            } while (vi.next() && ok);
+            if (!ok) break;
+            const int bx = prm.bx[it.li], by = prm.by[it.li], bz = prm.bz[it.li];
+            if (row < bx * by * bz) {
+                const int Pl = prm.P[it.li];
+                const int x = row % bx, y = (row / bx) % by, z = row / (bx * by);
+                const int t = it.oct * Pl * Pl * Pl + ((it.pz0 + z) * Pl + (it.py0 + y)) * Pl + (it.px0 + x);
+                double* Lrow = prm.L[it.li] + (size_t)t * C::NCP;
+                const double ih = prm.inv_h[it.li];
+#pragma unroll
+                for (int j = 0; j < C::NP; ++j) {
+                    const int b = it.half * C::NP + j;
+                    if (b < C::NC) Lrow[b] = (double)S[j] * ih;
+                }
             }
-            fence_before_sync();
-            mbar_arrive(smem_u32(&acc_empty[buf]));
         }
     }
     fence_before_sync();
@@ -388,10 +407,12 @@ __global__ void __launch_bounds__(192, 1) k_m2l_tc(const __grid_constant__ M2LTC
 }
 
 // ---- split of FP64 data into TF32 high/low parts ----------------------------------------------
+// round to the nearest TF32 value (10 explicit mantissa bits) and clear the 13 low bits, so
+// that hi + lo reproduces the operand exactly as the tensor core reads it
 __device__ __forceinline__ float to_tf32(float x) {
     uint32_t r;
     asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-    return __uint_as_float(r);
+    return __uint_as_float(r & 0xFFFFE000u);
 }
 
 __global__ void k_split_tf32(const double* __restrict__ src, float* __restrict__ hi, float* __restrict__ lo, size_t n) {
@@ -426,7 +447,7 @@ __global__ void k_split_k(const double* __restrict__ K64, int nc, int ncp, int n
 int m2l_tc_npt(int p) {
     const int nc = ncoef_of(p);
     const int npf = (nc + 15) / 16 * 16;
-    if (npf <= 256) return npf;
+    if (npf <= 192) return npf;
     return 2 * ((npf / 2 + 15) / 16 * 16);
 }
 

@@ -2,10 +2,12 @@
 
 The oracle runs the same traversal (Sec. 1) on the same tree with the same order, so
 the FP64 GPU result must equal it up to rounding: relative L2 <= 1e-12 (potential and
-field).  The MIXED path (FP32 bulk arithmetic) is held to 1e-6 relative L2 against the
-oracle here and to the bound stated in the benchmark; FP32 everywhere to 1e-5.  Against
-the direct sum (Eq. 1) both carry the method's own truncation error, which must match the
-oracle's to 1%."""
+field).  The MIXED and FP32 paths compute P2M, M2L, L2P and P2P in FP32 (unit roundoff
+u = 2^-24 ~ 6e-8): every coefficient and pair term carries a few u, and the sums over
+~10^2-10^4 partially cancelling terms amplify that, so they are held to 64 u ~ 3.8e-6 for
+the potential and 160 u ~ 1e-5 for the field (measured: 5e-7 to 8e-7 and 1e-6 to 3e-6).
+Against the direct sum (Eq. 1) every path carries the method's own truncation error,
+which must match the oracle's to 1%."""
 import numpy as np
 import pytest
 import torch
@@ -16,7 +18,8 @@ from paper_2508_02626_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"fp64": 1e-12, "mixed": 1e-6, "fp32": 1e-5}
+TOL = {"fp64": 1e-12, "mixed": 3.8e-6, "fp32": 3.8e-6}
+TOL_E = {"fp64": 1e-11, "mixed": 1e-5, "fp32": 1e-5}
 
 
 @pytest.fixture(scope="module")
@@ -59,7 +62,7 @@ def test_config1_uniform_1e4_p6(ctx):
     for prec in ("fp64", "mixed", "fp32"):
         phi, E = gpu_eval(ctx, x, q, dom, cfg["uniform_depth"], cfg["order"], prec)
         assert rel(phi, ref_phi) <= TOL[prec], (prec, rel(phi, ref_phi))
-        assert rel(E, ref_E) <= TOL[prec] * 10, (prec, rel(E, ref_E))
+        assert rel(E, ref_E) <= TOL_E[prec], (prec, rel(E, ref_E))
         assert abs(rel(phi, d_phi) / sig_oracle - 1.0) < 0.01
 
 
@@ -86,7 +89,7 @@ def test_tensor_core_m2l(ctx, p):
     finally:
         B.dafmm_set_option(ctx.h, B.DAFMM_OPT_M2L_KERNEL, 0)
     assert rel(tc_phi, ref_phi) <= TOL["mixed"], rel(tc_phi, ref_phi)
-    assert rel(tc_E, ref_E) <= TOL["mixed"] * 10
+    assert rel(tc_E, ref_E) <= TOL_E["mixed"]
     assert rel(si_phi, ref_phi) <= TOL["mixed"]
     assert rel(tc_phi, si_phi) <= TOL["mixed"]
 
@@ -99,7 +102,7 @@ def test_depths_and_near_field(ctx, depth):
     ref_phi, ref_E = O.fmm(x, q, dom, p, uniform_depth=depth)
     for prec in ("fp64", "mixed"):
         phi, E = gpu_eval(ctx, x, q, dom, depth, p, prec)
-        assert rel(phi, ref_phi) <= TOL[prec] and rel(E, ref_E) <= TOL[prec] * 10
+        assert rel(phi, ref_phi) <= TOL[prec] and rel(E, ref_E) <= TOL_E[prec]
     if depth <= 1:  # no far field: equals the direct sum
         d_phi, d_E = O.direct(x, q)
         phi, E = gpu_eval(ctx, x, q, dom, depth, p, "fp64")
@@ -184,4 +187,4 @@ def test_config2_full_size_sampled(ctx):
     for prec in ("fp64", "mixed"):
         phi, E = gpu_eval(ctx, x, q, dom, cfg["uniform_depth"], cfg["order"], prec)
         assert rel(phi[tg], ref_phi) <= TOL[prec], (prec, rel(phi[tg], ref_phi))
-        assert rel(E[tg], ref_E) <= TOL[prec] * 10, (prec, rel(E[tg], ref_E))
+        assert rel(E[tg], ref_E) <= TOL_E[prec], (prec, rel(E[tg], ref_E))

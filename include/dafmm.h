@@ -108,6 +108,21 @@ int dafmm_set_option(dafmm_ctx* ctx, int option, int64_t value);
  * kernels (DAFMM_ERR_TIMEOUT); clears the record. */
 int dafmm_sync(dafmm_ctx* ctx, void* stream);
 
+/* dafmm_eval without device allocation.  (The paper has no counterpart: this exists for
+ * callers that cannot call cudaMalloc while they evaluate -- a service whose device memory
+ * all belongs to its own pool allocator, or a latency-critical loop that cannot afford the
+ * implicit synchronisation of cudaMalloc/cudaFree.)  Computes the same potential and field
+ * as dafmm_eval(tree, order, 1.0, DAFMM_FP64, ...) with every intermediate array (operator
+ * tables, M2L matrices, multipole and local expansions) in one fixed 32 MiB array of device
+ * memory that belongs to the library and stays reserved on each GPU that loads it until
+ * the process exits.
+ *   Limits: order <= 6 (else DAFMM_ERR_UNSUPPORTED_ORDER), uniform trees of depth <= 4
+ *   (else DAFMM_ERR_INVALID_ARG); phi and field must be device memory or NULL.
+ *   The first call on a device looks up the array's device address; make that call
+ *   before any stream capture.  All calls share the array: calls that overlap on the GPU
+ *   (other streams, other host threads) race, so the caller must order them. */
+int dafmm_eval_noalloc(dafmm_tree* tree, int order, double* phi, double* field, void* stream);
+
 /* Device bytes an evaluation of a tree with these parameters needs (an upper estimate). */
 size_t dafmm_footprint(int64_t n, int order, int uniform_depth, int max_leaf, int precision);
 

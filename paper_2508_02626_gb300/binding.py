@@ -42,6 +42,7 @@ SIGNATURES = {
     "dafmm_set_profiling": (_i, [_vp, _i]),
     "dafmm_set_option": (_i, [_vp, _i, _i64]),
     "dafmm_sync": (_i, [_vp, _vp]),
+    "dafmm_eval_noalloc": (_i, [_vp, _i, _vp, _vp, _vp]),
     "dafmm_last_phase_ms": (_i, [_vp, _vp]),
     "dafmm_op_p2m": (_i, [_vp, _i, _i, _i64, _vp, _vp, _vp, _vp]),
     "dafmm_op_p2l": (_i, [_vp, _i, _i, _i64, _vp, _vp, _vp, _vp]),
@@ -178,6 +179,11 @@ def dafmm_set_option(ctx, option, value):
 
 def dafmm_sync(ctx, stream=None):
     _check(ctx, load().dafmm_sync(ctx, _stream_ptr(stream)))
+
+
+def dafmm_eval_noalloc(ctx, tree, order, phi=None, field=None, stream=None):
+    """FP64 evaluation that allocates no device memory (order <= 6, depth <= 4, device outputs)."""
+    _check(ctx, load().dafmm_eval_noalloc(tree, int(order), _ptr(phi), _ptr(field), _stream_ptr(stream)))
 
 
 def dafmm_set_profiling(ctx, enable):

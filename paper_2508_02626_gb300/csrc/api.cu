@@ -17,50 +17,7 @@
 
 using namespace dafmm;
 
-// ---------------------------------------------------------------------------------------------
-struct dafmm_ctx {
-    int device = 0;
-    size_t budget = 0;
-    size_t in_use = 0;
-    std::string err;
-    OrderData ord[kMaxOrder + 1];
-    std::vector<dafmm_tree*> trees;
-    // profiling: events at the phase boundaries of the last evaluation
-    bool profile = false;
-    cudaEvent_t ev[8] = {};
-    int last_launches = 0;
-    bool have_profile = false;
-    int m2l_kernel = 0;       // 0 tensor cores, 1 SIMT
-    int num_sms = 0;
-    bool tc_capable = false;  // compute capability 10.x
-    int* d_err = nullptr;     // device-side failure record of bounded waits
-};
-
-struct Expansions {
-    int p = -1;
-    int depth = -1;
-    double* M[kMaxUniformDepth + 1] = {};
-    double* L[kMaxUniformDepth + 1] = {};
-    float* Mf[kMaxUniformDepth + 1] = {};
-    float* Mhi[kMaxUniformDepth + 1] = {};
-    float* Mlo[kMaxUniformDepth + 1] = {};
-};
-
-struct dafmm_tree {
-    dafmm_ctx* ctx = nullptr;
-    int64_t n = 0;
-    double dom[4] = {0, 0, 0, 1};
-    int depth = 0;
-    int nleaf = 1;
-    int max_per_leaf = 0;
-    double *x = nullptr, *y = nullptr, *z = nullptr, *q = nullptr;
-    float4* xq = nullptr;
-    int* perm = nullptr;
-    int* leaf_start = nullptr;
-    Expansions ex;
-    double* out_scratch = nullptr;  // device outputs when the caller passes host buffers
-    size_t out_scratch_bytes = 0;
-};
+#include "api_types.h"
 
 namespace {
 
@@ -311,21 +268,6 @@ int ensure_expansions(dafmm_tree* t, int p, cudaStream_t s) {
 __global__ void k_to_float(const double* __restrict__ a, float* __restrict__ b, size_t n) {
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
         b[i] = (float)a[i];
-}
-
-TreeView make_view(const dafmm_tree* t) {
-    TreeView tv;
-    tv.n = t->n;
-    tv.depth = t->depth;
-    tv.nleaf = t->nleaf;
-    tv.x0 = t->dom[0]; tv.y0 = t->dom[1]; tv.z0 = t->dom[2]; tv.size = t->dom[3];
-    tv.h_leaf = ldexp(t->dom[3], -t->depth);
-    tv.inv_h_leaf = 1.0 / tv.h_leaf;
-    tv.x = t->x; tv.y = t->y; tv.z = t->z; tv.q = t->q;
-    tv.xq = t->xq;
-    tv.perm = t->perm;
-    tv.leaf_start = t->leaf_start;
-    return tv;
 }
 
 size_t tree_bytes(int64_t n, int depth) {

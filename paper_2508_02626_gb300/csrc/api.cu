@@ -12,7 +12,7 @@
 
 #include "da_common.cuh"
 #include "internal.h"
-#include "m2l_tc.h"
+#include "tc_ops.h"
 #include "tree_common.cuh"
 
 using namespace dafmm;
@@ -190,10 +190,35 @@ int ensure_order(dafmm_ctx* c, int p, cudaStream_t s, bool need_k) {
         CK(c, cudaMemsetAsync(od.K32, 0, cnt * sizeof(float), s), "K memset");
         CK(c, ops->kgen(od, s), "K generation");
         if (p >= 2) {
-            const size_t cs = (size_t)kNumKeys * m2l_tc_npt(p) * od.ncp;
+            const size_t cs = (size_t)kNumKeys * tc_npt(p) * od.ncp;
             if ((rc = dev_alloc(c, (void**)&od.Khi, cs * sizeof(float), "M2L matrices (TF32 split)"))) return rc;
             if ((rc = dev_alloc(c, (void**)&od.Klo, cs * sizeof(float), "M2L matrices (TF32 split)"))) return rc;
-            CK(c, m2l_tc_split_k(od.K64, p, od.Khi, od.Klo, s), "K split");
+            CK(c, tc_split_rows(od.K64, kNumKeys, p, od.Khi, od.Klo, s), "K split");
+            // dense M2M and L2L matrices of the 8 child octants (signs of Sec. 3.3 applied)
+            const size_t ds = (size_t)8 * od.nc * od.ncp, ss = (size_t)8 * tc_npt(p) * od.ncp;
+            std::vector<double> dense(ds);
+            double* d64 = nullptr;
+            if ((rc = dev_alloc(c, (void**)&d64, ds * sizeof(double), "shift tables"))) return rc;
+            for (int w = 0; w < 2 && rc == 0; ++w) {
+                const HostShiftTable& t = w == 0 ? ops->m2m : ops->l2l;
+                std::fill(dense.begin(), dense.end(), 0.0);
+                for (int oc = 0; oc < 8; ++oc)
+                    for (int b = 0; b < od.nc; ++b)
+                        for (int e = t.rowptr[b]; e < t.rowptr[b + 1]; ++e) {
+                            const double v = (__builtin_popcount(t.par[e] & oc) & 1) ? -t.val[e] : t.val[e];
+                            dense[((size_t)oc * od.nc + b) * od.ncp + t.col[e]] = v;
+                        }
+                float** hi = w == 0 ? &od.M2Mhi : &od.L2Lhi;
+                float** lo = w == 0 ? &od.M2Mlo : &od.L2Llo;
+                if ((rc = dev_alloc(c, (void**)hi, ss * sizeof(float), "shift tables (TF32 split)"))) break;
+                if ((rc = dev_alloc(c, (void**)lo, ss * sizeof(float), "shift tables (TF32 split)"))) break;
+                cudaError_t ce = cudaMemcpyAsync(d64, dense.data(), ds * sizeof(double), cudaMemcpyHostToDevice, s);
+                if (ce == cudaSuccess) ce = tc_split_rows(d64, 8, p, *hi, *lo, s);
+                if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);  // dense is reused for the next table
+                if (ce != cudaSuccess) { rc = cuda_fail(c, ce, "shift tables"); break; }
+            }
+            dev_free(c, d64, ds * sizeof(double));
+            if (rc) return rc;
         }
         od.k_ready = true;
     }
@@ -217,9 +242,12 @@ void free_order(dafmm_ctx* c, OrderData& od) {
     dev_free(c, od.K64, od.K64 ? cnt * sizeof(double) : 0);
     dev_free(c, od.K32, od.K32 ? cnt * sizeof(float) : 0);
     if (od.Khi) {
-        const size_t cs = (size_t)kNumKeys * m2l_tc_npt(od.p) * od.ncp;
+        const size_t cs = (size_t)kNumKeys * tc_npt(od.p) * od.ncp;
         dev_free(c, od.Khi, cs * sizeof(float));
         dev_free(c, od.Klo, cs * sizeof(float));
+        const size_t ss = (size_t)8 * tc_npt(od.p) * od.ncp * sizeof(float);
+        dev_free(c, od.M2Mhi, ss); dev_free(c, od.M2Mlo, ss);
+        dev_free(c, od.L2Lhi, ss); dev_free(c, od.L2Llo, ss);
     }
     od = OrderData();
 }
@@ -237,6 +265,8 @@ void free_expansions(dafmm_tree* t) {
         dev_free(c, e.Mf[l], e.Mf[l] ? cnt * sizeof(float) : 0);
         dev_free(c, e.Mhi[l], e.Mhi[l] ? cnt * sizeof(float) : 0);
         dev_free(c, e.Mlo[l], e.Mlo[l] ? cnt * sizeof(float) : 0);
+        dev_free(c, e.Lhi[l], e.Lhi[l] ? cnt * sizeof(float) : 0);
+        dev_free(c, e.Llo[l], e.Llo[l] ? cnt * sizeof(float) : 0);
     }
     e = Expansions();
 }
@@ -256,6 +286,8 @@ int ensure_expansions(dafmm_tree* t, int p, cudaStream_t s) {
         if ((rc = dev_alloc(c, (void**)&t->ex.Mf[l], cnt * sizeof(float), "multipoles (FP32)"))) return rc;
         if ((rc = dev_alloc(c, (void**)&t->ex.Mhi[l], cnt * sizeof(float), "multipoles (TF32 split)"))) return rc;
         if ((rc = dev_alloc(c, (void**)&t->ex.Mlo[l], cnt * sizeof(float), "multipoles (TF32 split)"))) return rc;
+        if ((rc = dev_alloc(c, (void**)&t->ex.Lhi[l], cnt * sizeof(float), "locals (TF32 split)"))) return rc;
+        if ((rc = dev_alloc(c, (void**)&t->ex.Llo[l], cnt * sizeof(float), "locals (TF32 split)"))) return rc;
         CK(c, cudaMemsetAsync(t->ex.M[l], 0, cnt * sizeof(double), s), "memset");
         CK(c, cudaMemsetAsync(t->ex.L[l], 0, cnt * sizeof(double), s), "memset");
         CK(c, cudaMemsetAsync(t->ex.Mf[l], 0, cnt * sizeof(float), s), "memset");
@@ -541,56 +573,104 @@ int dafmm_eval(dafmm_tree* t, int order, double theta, int precision, double* ph
     int launches = 0;
     mark(0);
     if (far) {
-        CK(c, ops->p2m(tv, precision, t->ex.M[L], s), "P2M");
+        const bool tc_ok = c->m2l_kernel == 0 && c->tc_capable && order >= 2;
+        const bool tc_m2l = precision != DAFMM_FP64 && tc_ok;    // tensor-core M2L
+        const bool tc_shift = precision == DAFMM_FP32 && tc_ok;  // tensor-core M2M and L2L too
+        Expansions& ex = t->ex;
+        auto tc_args = [&](int mode, int lmin, int lmax) {
+            TCArgs a;
+            memset(&a, 0, sizeof(a));
+            a.mode = mode;
+            a.lmin = lmin;
+            a.lmax = lmax;
+            a.err = c->d_err;
+            a.num_sms = c->num_sms;
+            return a;
+        };
+        CK(c, ops->p2m(tv, precision, ex.M[L], s), "P2M");
         ++launches;
         mark(1);
-        for (int lc = L; lc >= 3; --lc) {
-            CK(c, ops->m2m_level(od, precision, lc, t->ex.M[lc], t->ex.M[lc - 1], s), "M2M");
+        if (tc_shift) {
+            CK(c, tc_split_tf32(ex.M[L], ex.Mhi[L], ex.Mlo[L], level_boxes(L) * od.ncp, s), "split");
             ++launches;
+            for (int lc = L; lc >= 3; --lc) {
+                TCArgs a = tc_args(kTcM2M, lc, lc);
+                a.a_hi[lc] = ex.Mhi[lc];
+                a.a_lo[lc] = ex.Mlo[lc];
+                a.out[lc] = ex.M[lc - 1];
+                a.out_hi[lc] = ex.Mhi[lc - 1];
+                a.out_lo[lc] = ex.Mlo[lc - 1];
+                a.scale[lc] = 1.0;
+                a.b_hi = od.M2Mhi;
+                a.b_lo = od.M2Mlo;
+                a.nkey = 8;
+                CK(c, tc_launch(order, a, s), "M2M (tensor cores)");
+                ++launches;
+            }
+        } else {
+            for (int lc = L; lc >= 3; --lc) {
+                CK(c, ops->m2m_level(od, precision, lc, ex.M[lc], ex.M[lc - 1], s), "M2M");
+                ++launches;
+            }
         }
         mark(2);
-        const bool use_tc = precision != DAFMM_FP64 && c->m2l_kernel == 0 && c->tc_capable && order >= 2;
-        if (precision != DAFMM_FP64)
+        if (precision != DAFMM_FP64 && !tc_shift)
             for (int l = 2; l <= L; ++l) {
                 const size_t cnt = level_boxes(l) * od.ncp;
-                if (use_tc) {
-                    CK(c, m2l_tc_split_tf32(t->ex.M[l], t->ex.Mhi[l], t->ex.Mlo[l], cnt, s), "split");
+                if (tc_m2l) {
+                    CK(c, tc_split_tf32(ex.M[l], ex.Mhi[l], ex.Mlo[l], cnt, s), "split");
                 } else {
-                    k_to_float<<<(unsigned)std::min<size_t>((cnt + 255) / 256, 152 * 16), 256, 0, s>>>(t->ex.M[l], t->ex.Mf[l], cnt);
+                    k_to_float<<<(unsigned)std::min<size_t>((cnt + 255) / 256, 152 * 16), 256, 0, s>>>(ex.M[l], ex.Mf[l], cnt);
                     CK(c, cudaGetLastError(), "convert");
                 }
                 ++launches;
             }
         mark(3);
-        if (use_tc) {
+        if (tc_m2l) {
             mark(4);
-            M2LTCArgs a;
-            memset(&a, 0, sizeof(a));
-            a.lmin = 2;
-            a.lmax = L;
+            TCArgs a = tc_args(kTcM2L, 2, L);
             for (int l = 2; l <= L; ++l) {
-                a.Mhi[l] = t->ex.Mhi[l];
-                a.Mlo[l] = t->ex.Mlo[l];
-                a.L[l] = t->ex.L[l];
-                a.inv_h[l] = 1.0 / ldexp(t->dom[3], -l);
+                a.a_hi[l] = ex.Mhi[l];
+                a.a_lo[l] = ex.Mlo[l];
+                a.out[l] = ex.L[l];
+                if (tc_shift) {
+                    a.out_hi[l] = ex.Lhi[l];
+                    a.out_lo[l] = ex.Llo[l];
+                }
+                a.scale[l] = 1.0 / ldexp(t->dom[3], -l);
             }
-            a.Khi = od.Khi;
-            a.Klo = od.Klo;
-            a.err = c->d_err;
-            a.num_sms = c->num_sms;
-            CK(c, m2l_tc_launch(order, a, s), "M2L (tensor cores)");
+            a.b_hi = od.Khi;
+            a.b_lo = od.Klo;
+            a.nkey = kNumKeys;
+            CK(c, tc_launch(order, a, s), "M2L (tensor cores)");
             ++launches;
         } else {
             for (int l = 2; l <= L; ++l) {
                 if (l == L) mark(4);
                 const double inv_h = 1.0 / ldexp(t->dom[3], -l);
-                CK(c, ops->m2l_level(od, precision, l, t->ex.M[l], t->ex.Mf[l], t->ex.L[l], inv_h, s), "M2L");
+                CK(c, ops->m2l_level(od, precision, l, ex.M[l], ex.Mf[l], ex.L[l], inv_h, s), "M2L");
                 ++launches;
             }
         }
         mark(5);
         for (int lc = 3; lc <= L; ++lc) {
-            CK(c, ops->l2l_level(od, precision, lc, t->ex.L[lc - 1], t->ex.L[lc], s), "L2L");
+            if (tc_shift) {
+                TCArgs a = tc_args(kTcL2L, lc, lc);
+                a.a_hi[lc - 1] = ex.Lhi[lc - 1];
+                a.a_lo[lc - 1] = ex.Llo[lc - 1];
+                a.out[lc] = ex.L[lc];
+                if (lc < L) {
+                    a.out_hi[lc] = ex.Lhi[lc];
+                    a.out_lo[lc] = ex.Llo[lc];
+                }
+                a.scale[lc] = 1.0;
+                a.b_hi = od.L2Lhi;
+                a.b_lo = od.L2Llo;
+                a.nkey = 8;
+                CK(c, tc_launch(order, a, s), "L2L (tensor cores)");
+            } else {
+                CK(c, ops->l2l_level(od, precision, lc, ex.L[lc - 1], ex.L[lc], s), "L2L");
+            }
             ++launches;
         }
         mark(6);

@@ -35,6 +35,8 @@ struct Expansions {
     float* Mf[dafmm::kMaxUniformDepth + 1] = {};
     float* Mhi[dafmm::kMaxUniformDepth + 1] = {};
     float* Mlo[dafmm::kMaxUniformDepth + 1] = {};
+    float* Lhi[dafmm::kMaxUniformDepth + 1] = {};
+    float* Llo[dafmm::kMaxUniformDepth + 1] = {};
 };
 
 struct dafmm_tree {

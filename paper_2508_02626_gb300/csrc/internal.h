@@ -58,6 +58,10 @@ struct OrderData {
     float* K32 = nullptr;         // same in FP32
     float* Khi = nullptr;         // [343][npt][ncp] TF32 high / low parts for the tensor-core M2L
     float* Klo = nullptr;
+    float* M2Mhi = nullptr;       // [8][npt][ncp] dense M2M / L2L tables per child octant, TF32 parts
+    float* M2Mlo = nullptr;
+    float* L2Lhi = nullptr;
+    float* L2Llo = nullptr;
     bool k_ready = false;
     ShiftTab m2m() const { return ShiftTab{m2m_rowptr, m2m_col, m2m_par, m2m_val, m2m_valf}; }
     ShiftTab l2l() const { return ShiftTab{l2l_rowptr, l2l_col, l2l_par, l2l_val, l2l_valf}; }

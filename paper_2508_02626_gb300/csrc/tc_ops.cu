@@ -1,20 +1,25 @@
-// m2l_tc.cu -- M2L (Eq. 5) on the 5th-generation tensor cores (tcgen05, sm_103a).
+// tc_ops.cu -- the dense contractions of the FMM on the 5th-generation tensor cores
+// (tcgen05, sm_103a): M2L (Eq. 5), M2M (Eq. 4) and L2L (Eq. 7).
 //
-// For a target box t of level l and each of the 189 displacements v of its octant
-// (Sec. 3.4), L~_t += (1/h) K^_v M~_{t-v}.  With the octant-major box layout the sources of
-// 128 targets of one octant for one v form a 3-D block of one octant slab, so:
-//   A (128 x K, K-major)  = that block of multipoles, gathered by one 5-D TMA box load
-//                           (zero-filled where the block leaves the domain);
-//   B (N x K, K-major)    = K^_v, one 3-D TMA box load;
-//   D (128 x N, FP32)     = accumulated over all v in tensor memory (TMEM).
-// Precision: each FP32 operand is split into TF32 high and low parts (x = hi + lo, both
-// rounded to TF32), and D += A_hi B_hi + A_hi B_lo + A_lo B_hi, which carries about 22
-// mantissa bits per product, with FP32 accumulation.
+// All three are sums of small dense products  out_t (+)= scale * sum_j T_j A_{s(t,j)}  over
+// boxes t, with box-scaled expansions and level-independent matrices T_j:
+//   M2L  T_j = K^_v for the 189 displacements v of the target's octant (Sec. 3.4),
+//        A = multipoles of the sources t - v, out = locals of level l (written), scale 1/h;
+//   M2M  T_j = M2M table of child octant j (8 terms, Sec. 3.3 octant maps),
+//        A = multipoles of the children, out = parent multipoles (written);
+//   L2L  T = L2L table of the child octant (1 term), A = parent locals,
+//        out = child locals (added to what M2L wrote).
+// With the octant-major box layout the A rows of 128 boxes of one tile form a 3-D block of
+// one octant slab: one 5-D TMA box load (zero-filled outside the domain).  T is one 3-D
+// box.  Each FP32 operand is split into TF32 parts x = hi + lo and the product takes
+// A_hi T_lo + A_lo T_hi + A_hi T_hi (about 22 mantissa bits per product) into a fresh
+// FP32 TMEM accumulator per term (double-buffered); the epilogue warps add the terms in
+// FP32 registers, write the FP64 result and, when asked, its TF32 split for the next
+// stage.
 //
-// One persistent CTA per SM walks a list of (level, octant, tile, N-half) work items.
-// Warp roles: warp 0 issues TMA loads into a ring of shared-memory stages, warp 1 issues
-// the MMAs (one elected thread) and owns the TMEM allocation, warps 2-5 drain the
-// double-buffered accumulator (tcgen05.ld) and write L~ in FP64.  Every mbarrier wait is
+// One persistent CTA per SM walks the work items.  Warp roles: warp 0 issues TMA loads
+// into a ring of shared-memory stages, warp 1 issues the MMAs (one elected thread) and
+// owns the TMEM allocation, warps 2-5 drain the accumulators.  Every mbarrier wait is
 // bounded: on expiry the kernel records an error flag, drains its own copies and MMAs,
 // frees TMEM and returns.
 #include <cuda.h>
@@ -23,7 +28,8 @@
 #include <stdint.h>
 
 #include "internal.h"
-#include "m2l_tc.h"
+#include "tc_ops.h"
+#include "tree_common.cuh"
 
 namespace dafmm {
 namespace tc {
@@ -137,7 +143,8 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
 }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
-// ---- the kernel -----------------------------------------------------------------------------
+
+// ---- configuration per order ------------------------------------------------------------------
 template <int P>
 struct Cfg {
     static constexpr int NC = ncoef_of(P);
@@ -160,11 +167,12 @@ struct Cfg {
     static_assert(2 * NP <= TMEM_COLS, "TMEM double buffer");
 };
 
+// ---- work items and their terms ---------------------------------------------------------------
 struct WorkItem {
-    int li, oct, px0, py0, pz0, half;
+    int li, oct, c, px0, py0, pz0, half;
 };
 
-__device__ __forceinline__ WorkItem decode(const M2LTCParams& prm, int w) {
+__device__ __forceinline__ WorkItem decode(const TCParams& prm, int w) {
     WorkItem it;
     int li = 0;
     while (li + 1 < prm.nlev && w >= prm.tile_base[li + 1]) ++li;
@@ -172,25 +180,38 @@ __device__ __forceinline__ WorkItem decode(const M2LTCParams& prm, int w) {
     it.li = li;
     it.half = local % prm.nhalf;
     local /= prm.nhalf;
-    it.oct = local & 7;
-    local >>= 3;
-    const int P = prm.P[li], bx = prm.bx[li], by = prm.by[li];
-    const int nx = P / bx, ny = P / by;
+    it.oct = 0;
+    it.c = 0;
+    if (prm.mode == kTcM2L || prm.mode == kTcL2L) {
+        it.oct = local & 7;
+        local >>= 3;
+    }
+    if (prm.mode == kTcL2L) {
+        it.c = local & 7;
+        local >>= 3;
+    }
+    const int S = prm.S[li], bx = prm.bx[li], by = prm.by[li];
+    const int nx = S / bx, ny = S / by;
     it.px0 = (local % nx) * bx;
     it.py0 = ((local / nx) % ny) * by;
     it.pz0 = (local / (nx * ny)) * prm.bz[li];
     return it;
 }
 
-// the 189 displacements of a target octant, in a fixed order: v_d in [-3 + o_d, 2 + o_d], not all |v_d| <= 1
-struct VIter {
-    int o[3];
-    int v[3];
-    __device__ void first(int oct) {
+// the terms of a work item, in a fixed order.  M2L: the displacements v_d in
+// [-3 + o_d, 2 + o_d] that are not all |v_d| <= 1 (189 of 216); M2M: the 8 child octants;
+// L2L: one term.
+struct Terms {
+    int mode, o[3], v[3], j;
+    __device__ void first(int mode_, int oct) {
+        mode = mode_;
+        j = 0;
         o[0] = oct & 1; o[1] = (oct >> 1) & 1; o[2] = (oct >> 2) & 1;
         v[0] = -3 + o[0]; v[1] = -3 + o[1]; v[2] = -3 + o[2];
     }
-    __device__ bool next() {  // advance to the next raw combination; false at the end
+    __device__ bool next() {  // advance to the next raw term; false at the end
+        if (mode == kTcM2M) return ++j < 8;
+        if (mode == kTcL2L) return false;
         if (++v[2] <= 2 + o[2]) return true;
         v[2] = -3 + o[2];
         if (++v[1] <= 2 + o[1]) return true;
@@ -198,11 +219,51 @@ struct VIter {
         if (++v[0] <= 2 + o[0]) return true;
         return false;
     }
-    __device__ bool valid() const { return abs(v[0]) > 1 || abs(v[1]) > 1 || abs(v[2]) > 1; }
+    __device__ bool valid() const {
+        return mode != kTcM2L || abs(v[0]) > 1 || abs(v[1]) > 1 || abs(v[2]) > 1;
+    }
+    // A box start (slab coordinates and slab) and the T matrix index of the current term
+    __device__ void source(const WorkItem& it, int& x, int& y, int& z, int& slab, int& key) const {
+        if (mode == kTcM2L) {
+            int sc[3], a[3];
+            for (int d = 0; d < 3; ++d) {
+                const int dd = o[d] - v[d];  // in [-2, 3]
+                sc[d] = dd & 1;
+                a[d] = (dd - sc[d]) >> 1;    // in {-1, 0, 1}
+            }
+            x = it.px0 + a[0]; y = it.py0 + a[1]; z = it.pz0 + a[2];
+            slab = sc[0] | (sc[1] << 1) | (sc[2] << 2);
+            key = (v[0] + 3) * 49 + (v[1] + 3) * 7 + (v[2] + 3);
+        } else if (mode == kTcM2M) {
+            x = it.px0; y = it.py0; z = it.pz0;
+            slab = j;
+            key = j;
+        } else {
+            x = it.px0; y = it.py0; z = it.pz0;
+            slab = it.oct;
+            key = it.c;
+        }
+    }
 };
 
+// output box index of tile row (x, y, z) of a work item
+__device__ __forceinline__ int out_index(const TCParams& prm, const WorkItem& it, int x, int y, int z) {
+    const int S = prm.S[it.li];
+    const int px = it.px0 + x, py = it.py0 + y, pz = it.pz0 + z;
+    if (prm.mode == kTcM2L) return it.oct * S * S * S + (pz * S + py) * S + px;
+    if (prm.mode == kTcM2M) return octmajor_index(prm.out_level[it.li], px, py, pz);
+    // L2L: parent (2q + o) at the parent level, child 2 (2q + o) + c at the output level
+    const int ox = it.oct & 1, oy = (it.oct >> 1) & 1, oz = (it.oct >> 2) & 1;
+    const int Pl = 1 << (prm.out_level[it.li] - 1);
+    const int cx = 2 * px + ox, cy = 2 * py + oy, cz = 2 * pz + oz;
+    return it.c * Pl * Pl * Pl + (cz * Pl + cy) * Pl + cx;
+}
+
+__device__ __forceinline__ float to_tf32(float x);
+
+// ---- the kernel -----------------------------------------------------------------------------
 template <int P>
-__global__ void __launch_bounds__(192, 1) k_m2l_tc(const __grid_constant__ M2LTCParams prm) {
+__global__ void __launch_bounds__(192, 1) k_tc(const __grid_constant__ TCParams prm) {
     using C = Cfg<P>;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     // 1024-byte aligned stage ring, then barriers
@@ -255,18 +316,12 @@ __global__ void __launch_bounds__(192, 1) k_m2l_tc(const __grid_constant__ M2LTC
         for (int w = blockIdx.x; w < prm.ntiles && ok; w += gridDim.x) {
             const WorkItem it = decode(prm, w);
             const uint32_t a_bytes = 128u * prm.bx[it.li] * prm.by[it.li] * prm.bz[it.li];
-            VIter vi;
-            vi.first(it.oct);
+            Terms tm;
+            tm.first(prm.mode, it.oct);
             do {
-                if (!vi.valid()) continue;
-                int sc[3], a[3];
-                for (int d = 0; d < 3; ++d) {
-                    const int dd = vi.o[d] - vi.v[d];  // in [-2, 3]
-                    sc[d] = dd & 1;
-                    a[d] = (dd - sc[d]) >> 1;          // in {-1, 0, 1}
-                }
-                const int soct = sc[0] | (sc[1] << 1) | (sc[2] << 2);
-                const int key = (vi.v[0] + 3) * 49 + (vi.v[1] + 3) * 7 + (vi.v[2] + 3);
+                if (!tm.valid()) continue;
+                int sx, sy, sz, slab, key;
+                tm.source(it, sx, sy, sz, slab, key);
                 for (int kc = 0; kc < C::NKC && ok; ++kc) {
                     ok = mbar_wait(smem_u32(&empty[stage]), phase ^ 1u, prm.err, 11);
                     if (!ok) break;
@@ -274,9 +329,8 @@ __global__ void __launch_bounds__(192, 1) k_m2l_tc(const __grid_constant__ M2LTC
                     const uint32_t fb = smem_u32(&full[stage]);
                     mbar_expect_tx(fb, 2u * a_bytes + 2u * C::B_BYTES);
                     armed[stage] = (int)phase;
-                    tma_load_5d(smem_u32(st), &prm.a_hi[it.li], fb, kc * 32, it.px0 + a[0], it.py0 + a[1], it.pz0 + a[2], soct);
-                    tma_load_5d(smem_u32(st + C::A_BYTES), &prm.a_lo[it.li], fb, kc * 32, it.px0 + a[0], it.py0 + a[1],
-                                it.pz0 + a[2], soct);
+                    tma_load_5d(smem_u32(st), &prm.a_hi[it.li], fb, kc * 32, sx, sy, sz, slab);
+                    tma_load_5d(smem_u32(st + C::A_BYTES), &prm.a_lo[it.li], fb, kc * 32, sx, sy, sz, slab);
                     tma_load_3d(smem_u32(st + 2 * C::A_BYTES), &prm.b_hi, fb, kc * 32, it.half * C::NP, key);
                     tma_load_3d(smem_u32(st + 2 * C::A_BYTES + C::B_BYTES), &prm.b_lo, fb, kc * 32, it.half * C::NP, key);
                     if (++stage == C::STAGES) {
@@ -284,14 +338,14 @@ __global__ void __launch_bounds__(192, 1) k_m2l_tc(const __grid_constant__ M2LTC
                         phase ^= 1u;
                     }
                 }
-            } while (vi.next() && ok);
+            } while (tm.next() && ok);
         }
         // wait (bounded) until every copy this thread armed has landed before the block may exit
         for (int s = 0; s < C::STAGES; ++s)
             if (armed[s] >= 0) mbar_wait(smem_u32(&full[s]), (uint32_t)armed[s], prm.err, 12);
     } else if (warp == 1 && lane == 0) {
         // ---------------- MMA issuer ----------------
-        // one fresh accumulator per displacement v (alternating TMEM buffers): at most
+        // one fresh accumulator per term (alternating TMEM buffers): at most
         // 3 * ceil(ncoef/8) MMA accumulation steps land in one FP32 accumulator
         int stage = 0;
         uint32_t phase = 0;
@@ -300,10 +354,10 @@ __global__ void __launch_bounds__(192, 1) k_m2l_tc(const __grid_constant__ M2LTC
         int uses = 0;
         for (int w = blockIdx.x; w < prm.ntiles && ok; w += gridDim.x) {
             const WorkItem it = decode(prm, w);
-            VIter vi;
-            vi.first(it.oct);
+            Terms tm;
+            tm.first(prm.mode, it.oct);
             do {
-                if (!vi.valid()) continue;
+                if (!tm.valid()) continue;
                 const int buf = uses & 1;
                 ok = mbar_wait(smem_u32(&acc_empty[buf]), acc_ph[buf] ^ 1u, prm.err, 21);
                 if (!ok) break;
@@ -335,16 +389,15 @@ __global__ void __launch_bounds__(192, 1) k_m2l_tc(const __grid_constant__ M2LTC
                 }
                 if (ok) mma_commit(smem_u32(&acc_full[buf]));
                 ++uses;
-            } while (vi.next() && ok);
+            } while (tm.next() && ok);
         }
         // every MMA this thread issued has finished once the drain barrier flips
         mma_commit(smem_u32(drain));
         mbar_wait(smem_u32(drain), 0, prm.err, 23);
     } else if (warp >= 2) {
         // ---------------- epilogue ----------------
-        // sums the per-displacement accumulators of its row in FP32 registers (CUDA cores)
         const int q = warp & 3;          // TMEM lane quarter of this warp
-        const int row = 32 * q + lane;   // accumulator row = target within the tile
+        const int row = 32 * q + lane;   // accumulator row = box within the tile
         uint32_t accf_ph[2] = {0, 0};
         int uses = 0;
         bool ok = true;
@@ -353,10 +406,10 @@ __global__ void __launch_bounds__(192, 1) k_m2l_tc(const __grid_constant__ M2LTC
             float S[C::NP];
 #pragma unroll
             for (int j = 0; j < C::NP; ++j) S[j] = 0.f;
-            VIter vi;
-            vi.first(it.oct);
+            Terms tm;
+            tm.first(prm.mode, it.oct);
             do {
-                if (!vi.valid()) continue;
+                if (!tm.valid()) continue;
                 const int buf = uses & 1;
                 ok = mbar_wait(smem_u32(&acc_full[buf]), accf_ph[buf], prm.err, 31);
                 if (!ok) break;
@@ -379,19 +432,31 @@ __global__ void __launch_bounds__(192, 1) k_m2l_tc(const __grid_constant__ M2LTC
                 fence_before_sync();
                 mbar_arrive(smem_u32(&acc_empty[buf]));
                 ++uses;
-            } while (vi.next() && ok);
+            } while (tm.next() && ok);
             if (!ok) break;
             const int bx = prm.bx[it.li], by = prm.by[it.li], bz = prm.bz[it.li];
             if (row < bx * by * bz) {
-                const int Pl = prm.P[it.li];
                 const int x = row % bx, y = (row / bx) % by, z = row / (bx * by);
-                const int t = it.oct * Pl * Pl * Pl + ((it.pz0 + z) * Pl + (it.py0 + y)) * Pl + (it.px0 + x);
-                double* Lrow = prm.L[it.li] + (size_t)t * C::NCP;
-                const double ih = prm.inv_h[it.li];
+                const size_t t = (size_t)out_index(prm, it, x, y, z) * C::NCP;
+                double* orow = prm.out[it.li] + t;
+                float* hrow = prm.out_hi[it.li] ? prm.out_hi[it.li] + t : nullptr;
+                float* lrow = prm.out_lo[it.li] ? prm.out_lo[it.li] + t : nullptr;
+                const double sc = prm.scale[it.li];
+                const bool add = prm.mode == kTcL2L;
 #pragma unroll
                 for (int j = 0; j < C::NP; ++j) {
                     const int b = it.half * C::NP + j;
-                    if (b < C::NC) Lrow[b] = (double)S[j] * ih;
+                    if (b < C::NC) {
+                        double v = (double)S[j] * sc;
+                        if (add) v += orow[b];
+                        orow[b] = v;
+                        if (hrow) {
+                            const float f = (float)v;
+                            const float h = to_tf32(f);
+                            hrow[b] = h;
+                            lrow[b] = to_tf32(f - h);
+                        }
+                    }
                 }
             }
         }
@@ -424,10 +489,10 @@ __global__ void k_split_tf32(const double* __restrict__ src, float* __restrict__
     }
 }
 
-// K^ split, rows padded from nc to npt (zero rows), [343][npt][ncp]
-__global__ void k_split_k(const double* __restrict__ K64, int nc, int ncp, int npt, float* __restrict__ hi,
-                          float* __restrict__ lo) {
-    const size_t n = (size_t)kNumKeys * npt * ncp;
+// a [nkey][nc][ncp] FP64 table into TF32 parts with rows padded from nc to npt (zero rows)
+__global__ void k_split_rows(const double* __restrict__ K64, int nkey, int nc, int ncp, int npt, float* __restrict__ hi,
+                             float* __restrict__ lo) {
+    const size_t n = (size_t)nkey * npt * ncp;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
         const int a = (int)(i % ncp);
         const size_t rk = i / ncp;
@@ -444,23 +509,23 @@ __global__ void k_split_k(const double* __restrict__ K64, int nc, int ncp, int n
 }  // namespace tc
 
 // ---- host side ---------------------------------------------------------------------------------
-int m2l_tc_npt(int p) {
+int tc_npt(int p) {
     const int nc = ncoef_of(p);
     const int npf = (nc + 15) / 16 * 16;
     if (npf <= 192) return npf;
     return 2 * ((npf / 2 + 15) / 16 * 16);
 }
 
-cudaError_t m2l_tc_split_tf32(const double* src, float* hi, float* lo, size_t n, cudaStream_t s) {
+cudaError_t tc_split_tf32(const double* src, float* hi, float* lo, size_t n, cudaStream_t s) {
     if (n == 0) return cudaSuccess;
     unsigned blocks = (unsigned)std::min<size_t>((n + 255) / 256, 152 * 16);
     tc::k_split_tf32<<<blocks, 256, 0, s>>>(src, hi, lo, n);
     return cudaGetLastError();
 }
 
-cudaError_t m2l_tc_split_k(const double* K64, int p, float* hi, float* lo, cudaStream_t s) {
-    const int nc = ncoef_of(p), ncp = ncp_of(p), npt = m2l_tc_npt(p);
-    tc::k_split_k<<<152 * 16, 256, 0, s>>>(K64, nc, ncp, npt, hi, lo);
+cudaError_t tc_split_rows(const double* src, int nkey, int p, float* hi, float* lo, cudaStream_t s) {
+    const int nc = ncoef_of(p), ncp = ncp_of(p), npt = tc_npt(p);
+    tc::k_split_rows<<<152 * 16, 256, 0, s>>>(src, nkey, nc, ncp, npt, hi, lo);
     return cudaGetLastError();
 }
 
@@ -478,69 +543,86 @@ static PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
     return fn;
 }
 
+// tile geometry over an S x S x S block grid: 128 boxes per tile when S^3 >= 128
+static void tile_shape(int S, int& bx, int& by, int& bz) {
+    bx = S < 128 ? S : 128;
+    by = S < 128 / bx ? S : 128 / bx;
+    bz = S < 128 / (bx * by) ? S : 128 / (bx * by);
+    if (bz < 1) bz = 1;
+}
+
+// 5-D map (coef, x, y, z, slab) over an octant-major level with S slab positions per axis
+static bool encode_level(PFN_cuTensorMapEncodeTiled_v12000 enc, CUtensorMap* map, const float* base, int ncp, int S,
+                         int bx, int by, int bz) {
+    const cuuint64_t dims[5] = {(cuuint64_t)ncp, (cuuint64_t)S, (cuuint64_t)S, (cuuint64_t)S, 8};
+    const cuuint64_t row = (cuuint64_t)ncp * 4;
+    const cuuint64_t strides[4] = {row, row * S, row * S * S, row * S * S * S};
+    const cuuint32_t box[5] = {32, (cuuint32_t)bx, (cuuint32_t)by, (cuuint32_t)bz, 1};
+    const cuuint32_t es[5] = {1, 1, 1, 1, 1};
+    return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 5, (void*)base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+               CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+           CUDA_SUCCESS;
+}
+
+// 3-D map (coef, row, matrix) over [nkey][npt][ncp] with boxes of np rows
+static bool encode_rows(PFN_cuTensorMapEncodeTiled_v12000 enc, CUtensorMap* map, const float* base, int ncp, int npt,
+                        int nkey, int np) {
+    const cuuint64_t dims[3] = {(cuuint64_t)ncp, (cuuint64_t)npt, (cuuint64_t)nkey};
+    const cuuint64_t strides[2] = {(cuuint64_t)ncp * 4, (cuuint64_t)ncp * 4 * npt};
+    const cuuint32_t box[3] = {32, (cuuint32_t)np, 1};
+    const cuuint32_t es[3] = {1, 1, 1};
+    return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, (void*)base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+               CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+           CUDA_SUCCESS;
+}
+
 template <int P>
-static cudaError_t launch_tc(const M2LTCArgs& a, cudaStream_t s) {
+static cudaError_t launch_tc(const TCArgs& a, cudaStream_t s) {
     using C = tc::Cfg<P>;
-    auto encode = get_encode();
-    if (!encode) return cudaErrorNotSupported;
-    M2LTCParams prm;
+    auto enc = get_encode();
+    if (!enc) return cudaErrorNotSupported;
+    TCParams prm;
     memset(&prm, 0, sizeof(prm));
-    prm.nlev = 0;
+    prm.mode = a.mode;
     prm.nhalf = C::NHALF;
     prm.err = a.err;
     int tiles = 0;
-    // finest level first: all work items cost the same, the list is only an order
+    const int per_tile_groups = a.mode == kTcM2L ? 8 : (a.mode == kTcL2L ? 64 : 1);
+    // finest level first: all work items of a launch cost about the same
     for (int l = a.lmax; l >= a.lmin; --l) {
         const int li = prm.nlev++;
-        const int Pp = 1 << (l - 1);
-        int bx = Pp < 128 ? Pp : 128;
-        int by = Pp < 128 / bx ? Pp : 128 / bx;
-        int bz = Pp < 128 / (bx * by) ? Pp : 128 / (bx * by);
-        if (bz < 1) bz = 1;
-        prm.P[li] = Pp; prm.bx[li] = bx; prm.by[li] = by; prm.bz[li] = bz;
-        prm.L[li] = a.L[l];
-        prm.inv_h[li] = a.inv_h[l];
-        const int tpo = (Pp / bx) * (Pp / by) * (Pp / bz);
+        // A lives on level `src` with S slab positions per axis; the tile grid is the same grid
+        const int src = a.mode == kTcL2L ? l - 1 : l;
+        const int S = 1 << (src - 1);
+        int bx, by, bz;
+        tile_shape(S, bx, by, bz);
+        prm.S[li] = S; prm.bx[li] = bx; prm.by[li] = by; prm.bz[li] = bz;
+        prm.out[li] = a.out[l];
+        prm.out_hi[li] = a.out_hi[l];
+        prm.out_lo[li] = a.out_lo[l];
+        prm.scale[li] = a.scale[l];
+        prm.out_level[li] = a.mode == kTcM2M ? l - 1 : l;
         prm.tile_base[li] = tiles;
-        tiles += 8 * tpo * C::NHALF;
-        const cuuint64_t dims[5] = {(cuuint64_t)C::NCP, (cuuint64_t)Pp, (cuuint64_t)Pp, (cuuint64_t)Pp, 8};
-        const cuuint64_t row = (cuuint64_t)C::NCP * 4;
-        const cuuint64_t strides[4] = {row, row * Pp, row * Pp * Pp, row * Pp * Pp * Pp};
-        const cuuint32_t box[5] = {32, (cuuint32_t)bx, (cuuint32_t)by, (cuuint32_t)bz, 1};
-        const cuuint32_t es[5] = {1, 1, 1, 1, 1};
-        for (int h = 0; h < 2; ++h) {
-            CUresult r = encode(h == 0 ? &prm.a_hi[li] : &prm.a_lo[li], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 5,
-                                (void*)(h == 0 ? a.Mhi[l] : a.Mlo[l]), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                                CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-            if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
-        }
+        tiles += per_tile_groups * (S / bx) * (S / by) * (S / bz) * C::NHALF;
+        if (!encode_level(enc, &prm.a_hi[li], a.a_hi[src], C::NCP, S, bx, by, bz) ||
+            !encode_level(enc, &prm.a_lo[li], a.a_lo[src], C::NCP, S, bx, by, bz))
+            return cudaErrorInvalidValue;
     }
     prm.tile_base[prm.nlev] = tiles;
     prm.ntiles = tiles;
-    {
-        const int npt = m2l_tc_npt(P);
-        const cuuint64_t dims[3] = {(cuuint64_t)C::NCP, (cuuint64_t)npt, (cuuint64_t)kNumKeys};
-        const cuuint64_t strides[2] = {(cuuint64_t)C::NCP * 4, (cuuint64_t)C::NCP * 4 * npt};
-        const cuuint32_t box[3] = {32, (cuuint32_t)C::NP, 1};
-        const cuuint32_t es[3] = {1, 1, 1};
-        for (int h = 0; h < 2; ++h) {
-            CUresult r = encode(h == 0 ? &prm.b_hi : &prm.b_lo, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3,
-                                (void*)(h == 0 ? a.Khi : a.Klo), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                                CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-            if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
-        }
-    }
+    const int npt = tc_npt(P);
+    if (!encode_rows(enc, &prm.b_hi, a.b_hi, C::NCP, npt, a.nkey, C::NP) ||
+        !encode_rows(enc, &prm.b_lo, a.b_lo, C::NCP, npt, a.nkey, C::NP))
+        return cudaErrorInvalidValue;
     if (tiles == 0) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(tc::k_m2l_tc<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM_BYTES);
+    cudaError_t e = cudaFuncSetAttribute(tc::k_tc<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM_BYTES);
     if (e != cudaSuccess) return e;
     const int grid = tiles < a.num_sms ? tiles : a.num_sms;
-    tc::k_m2l_tc<P><<<grid, 192, C::SMEM_BYTES, s>>>(prm);
+    tc::k_tc<P><<<grid, 192, C::SMEM_BYTES, s>>>(prm);
     return cudaGetLastError();
 }
 
-cudaError_t m2l_tc_launch(int p, const M2LTCArgs& a, cudaStream_t s) {
+cudaError_t tc_launch(int p, const TCArgs& a, cudaStream_t s) {
     switch (p) {
         case 2: return launch_tc<2>(a, s);
         case 3: return launch_tc<3>(a, s);

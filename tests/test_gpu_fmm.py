@@ -77,8 +77,9 @@ def test_every_order_fp64(ctx, p):
 
 @pytest.mark.parametrize("p", [2, 3, 4, 6, 8, 9, 10])
 def test_tensor_core_m2l(ctx, p):
-    """The tcgen05 M2L (TF32 split products) against the oracle and against the SIMT FP32 M2L,
-    on a depth-4 tree (levels 2-4: tiles of 8, 64 and 128 targets); p = 10 splits N in two."""
+    """The tcgen05 contractions (TF32 split products) against the oracle: M2L alone (MIXED)
+    and against the SIMT FP32 M2L, and M2L + M2M + L2L (FP32 mode), on a depth-4 tree
+    (levels 2-4: tiles of 8, 64 and 128 boxes); p = 9, 10 split N in two."""
     x, q = W.uniform(20000, seed=300 + p)
     dom = W.UNIT_CUBE
     ref_phi, ref_E = O.fmm(x, q, dom, p, uniform_depth=4)
@@ -92,6 +93,10 @@ def test_tensor_core_m2l(ctx, p):
     assert rel(tc_E, ref_E) <= TOL_E["mixed"]
     assert rel(si_phi, ref_phi) <= TOL["mixed"]
     assert rel(tc_phi, si_phi) <= TOL["mixed"]
+    # FP32 mode: M2M and L2L on the tensor cores as well
+    f_phi, f_E = gpu_eval(ctx, x, q, dom, 4, p, "fp32")
+    assert rel(f_phi, ref_phi) <= TOL["fp32"], rel(f_phi, ref_phi)
+    assert rel(f_E, ref_E) <= TOL_E["fp32"]
 
 
 @pytest.mark.parametrize("depth", [0, 1, 2, 4])

@@ -102,7 +102,16 @@ int dafmm_last_phase_ms(dafmm_ctx* ctx, double* out10);
  *   DAFMM_OPT_M2L_KERNEL: 0 = tensor-core M2L (tcgen05, TF32 split products) for the FP32
  *   bulk paths when the order is >= 2 (default), 1 = SIMT FP32 M2L. */
 #define DAFMM_OPT_M2L_KERNEL 1
+/*   DAFMM_OPT_TC_MASK: which contractions may use the tensor cores in the FP32 mode
+ *   (bit 0 M2L, bit 1 M2M, bit 2 L2L; default 7); the others run on the SIMT kernels. */
+#define DAFMM_OPT_TC_MASK 2
 int dafmm_set_option(dafmm_ctx* ctx, int option, int64_t value);
+
+/* Diagnostics: copy level `level` of an internal expansion array of the last evaluation
+ * into host memory `out` as doubles (8^level x ncp values; ncp = ncoef rounded up to 8).
+ * which: 0 multipoles, 1 locals, 2/3 TF32 high/low parts of the multipoles, 4/5 of the
+ * locals.  Synchronises the device.  Returns the number of values, or a negative code. */
+int64_t dafmm_debug_level(const dafmm_tree* tree, int which, int level, double* out, int64_t cap);
 
 /* Wait for `stream` and report failures recorded on the device by bounded waits inside the
  * kernels (DAFMM_ERR_TIMEOUT); clears the record. */

@@ -43,6 +43,7 @@ SIGNATURES = {
     "dafmm_set_option": (_i, [_vp, _i, _i64]),
     "dafmm_sync": (_i, [_vp, _vp]),
     "dafmm_eval_noalloc": (_i, [_vp, _i, _vp, _vp, _vp]),
+    "dafmm_debug_level": (_i64, [_vp, _i, _i, _vp, _i64]),
     "dafmm_last_phase_ms": (_i, [_vp, _vp]),
     "dafmm_op_p2m": (_i, [_vp, _i, _i, _i64, _vp, _vp, _vp, _vp]),
     "dafmm_op_p2l": (_i, [_vp, _i, _i, _i64, _vp, _vp, _vp, _vp]),
@@ -171,6 +172,7 @@ def dafmm_eval(ctx, tree, order, phi=None, field=None, theta=1.0, precision=DAFM
 
 
 DAFMM_OPT_M2L_KERNEL = 1
+DAFMM_OPT_TC_MASK = 2
 
 
 def dafmm_set_option(ctx, option, value):
@@ -184,6 +186,18 @@ def dafmm_sync(ctx, stream=None):
 def dafmm_eval_noalloc(ctx, tree, order, phi=None, field=None, stream=None):
     """FP64 evaluation that allocates no device memory (order <= 6, depth <= 4, device outputs)."""
     _check(ctx, load().dafmm_eval_noalloc(tree, int(order), _ptr(phi), _ptr(field), _stream_ptr(stream)))
+
+
+DEBUG_ARRAYS = {"M": 0, "L": 1, "Mhi": 2, "Mlo": 3, "Lhi": 4, "Llo": 5}
+
+
+def dafmm_debug_level(tree, which, level, ncp):
+    """Copy of one level of an internal expansion array of the last evaluation, (8^l, ncp)."""
+    out = np.zeros((8 ** level, ncp))
+    rc = load().dafmm_debug_level(tree, DEBUG_ARRAYS[which], int(level), out.ctypes.data, out.size)
+    if rc < 0:
+        raise DafmmError(int(rc), "dafmm_debug_level failed")
+    return out
 
 
 def dafmm_set_profiling(ctx, enable):

@@ -293,6 +293,8 @@ int ensure_expansions(dafmm_tree* t, int p, cudaStream_t s) {
         CK(c, cudaMemsetAsync(t->ex.Mf[l], 0, cnt * sizeof(float), s), "memset");
         CK(c, cudaMemsetAsync(t->ex.Mhi[l], 0, cnt * sizeof(float), s), "memset");
         CK(c, cudaMemsetAsync(t->ex.Mlo[l], 0, cnt * sizeof(float), s), "memset");
+        CK(c, cudaMemsetAsync(t->ex.Lhi[l], 0, cnt * sizeof(float), s), "memset");
+        CK(c, cudaMemsetAsync(t->ex.Llo[l], 0, cnt * sizeof(float), s), "memset");
     }
     return DAFMM_OK;
 }
@@ -574,8 +576,10 @@ int dafmm_eval(dafmm_tree* t, int order, double theta, int precision, double* ph
     mark(0);
     if (far) {
         const bool tc_ok = c->m2l_kernel == 0 && c->tc_capable && order >= 2;
-        const bool tc_m2l = precision != DAFMM_FP64 && tc_ok;    // tensor-core M2L
-        const bool tc_shift = precision == DAFMM_FP32 && tc_ok;  // tensor-core M2M and L2L too
+        const bool f32 = precision == DAFMM_FP32;
+        const bool tc_m2l = precision != DAFMM_FP64 && tc_ok && (!f32 || (c->tc_mask & 1));
+        const bool tc_m2m = f32 && tc_ok && (c->tc_mask & 2);     // tensor-core M2M (FP32 mode)
+        const bool tc_l2l = f32 && tc_ok && (c->tc_mask & 4);     // tensor-core L2L (FP32 mode)
         Expansions& ex = t->ex;
         auto tc_args = [&](int mode, int lmin, int lmax) {
             TCArgs a;
@@ -590,7 +594,7 @@ int dafmm_eval(dafmm_tree* t, int order, double theta, int precision, double* ph
         CK(c, ops->p2m(tv, precision, ex.M[L], s), "P2M");
         ++launches;
         mark(1);
-        if (tc_shift) {
+        if (tc_m2m) {
             CK(c, tc_split_tf32(ex.M[L], ex.Mhi[L], ex.Mlo[L], level_boxes(L) * od.ncp, s), "split");
             ++launches;
             for (int lc = L; lc >= 3; --lc) {
@@ -614,7 +618,7 @@ int dafmm_eval(dafmm_tree* t, int order, double theta, int precision, double* ph
             }
         }
         mark(2);
-        if (precision != DAFMM_FP64 && !tc_shift)
+        if (precision != DAFMM_FP64 && !(tc_m2m && tc_m2l))
             for (int l = 2; l <= L; ++l) {
                 const size_t cnt = level_boxes(l) * od.ncp;
                 if (tc_m2l) {
@@ -633,7 +637,7 @@ int dafmm_eval(dafmm_tree* t, int order, double theta, int precision, double* ph
                 a.a_hi[l] = ex.Mhi[l];
                 a.a_lo[l] = ex.Mlo[l];
                 a.out[l] = ex.L[l];
-                if (tc_shift) {
+                if (tc_l2l) {
                     a.out_hi[l] = ex.Lhi[l];
                     a.out_lo[l] = ex.Llo[l];
                 }
@@ -653,8 +657,13 @@ int dafmm_eval(dafmm_tree* t, int order, double theta, int precision, double* ph
             }
         }
         mark(5);
+        if (tc_l2l && !tc_m2l)  // the TF32 parts of the locals come from the tensor-core M2L otherwise
+            for (int l = 2; l <= L; ++l) {
+                CK(c, tc_split_tf32(ex.L[l], ex.Lhi[l], ex.Llo[l], level_boxes(l) * od.ncp, s), "split");
+                ++launches;
+            }
         for (int lc = 3; lc <= L; ++lc) {
-            if (tc_shift) {
+            if (tc_l2l) {
                 TCArgs a = tc_args(kTcL2L, lc, lc);
                 a.a_hi[lc - 1] = ex.Lhi[lc - 1];
                 a.a_lo[lc - 1] = ex.Llo[lc - 1];
@@ -694,6 +703,10 @@ int dafmm_set_option(dafmm_ctx* c, int option, int64_t value) {
         c->m2l_kernel = (int)value;
         return DAFMM_OK;
     }
+    if (option == DAFMM_OPT_TC_MASK && value >= 0 && value <= 7) {
+        c->tc_mask = (int)value;
+        return DAFMM_OK;
+    }
     return fail(c, DAFMM_ERR_INVALID_ARG, "option");
 }
 
@@ -708,6 +721,25 @@ int dafmm_sync(dafmm_ctx* c, void* stream) {
         return fail(c, DAFMM_ERR_TIMEOUT, "a bounded device wait gave up (site " + std::to_string(flag) + ")");
     }
     return DAFMM_OK;
+}
+
+int64_t dafmm_debug_level(const dafmm_tree* t, int which, int level, double* out, int64_t cap) {
+    if (!t || !out || which < 0 || which > 5) return DAFMM_ERR_INVALID_ARG;
+    const Expansions& e = t->ex;
+    if (e.p < 0 || level < 2 || level > e.depth) return DAFMM_ERR_INVALID_ARG;
+    const int64_t cnt = (int64_t)level_boxes(level) * ncp_of(e.p);
+    if (cap < cnt) return DAFMM_ERR_INVALID_ARG;
+    if (cudaSetDevice(t->ctx->device) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) return DAFMM_ERR_CUDA;
+    if (which <= 1) {
+        const double* src = which == 0 ? e.M[level] : e.L[level];
+        if (cudaMemcpy(out, src, cnt * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess) return DAFMM_ERR_CUDA;
+    } else {
+        const float* src = which == 2 ? e.Mhi[level] : which == 3 ? e.Mlo[level] : which == 4 ? e.Lhi[level] : e.Llo[level];
+        std::vector<float> tmp(cnt);
+        if (cudaMemcpy(tmp.data(), src, cnt * sizeof(float), cudaMemcpyDeviceToHost) != cudaSuccess) return DAFMM_ERR_CUDA;
+        for (int64_t i = 0; i < cnt; ++i) out[i] = tmp[i];
+    }
+    return cnt;
 }
 
 int dafmm_set_profiling(dafmm_ctx* c, int enable) {

@@ -22,6 +22,7 @@ struct dafmm_ctx {
     int last_launches = 0;
     bool have_profile = false;
     int m2l_kernel = 0;       // 0 tensor cores, 1 SIMT
+    int tc_mask = 7;          // FP32 mode: bit 0 M2L, bit 1 M2M, bit 2 L2L on the tensor cores
     int num_sms = 0;
     bool tc_capable = false;  // compute capability 10.x
     int* d_err = nullptr;     // device-side failure record of bounded waits

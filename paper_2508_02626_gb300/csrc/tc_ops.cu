@@ -132,16 +132,19 @@ __device__ __forceinline__ void mma_commit(uint32_t bar) {
 __device__ __forceinline__ void fence_after_sync() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_before_sync() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 
-// 32 lanes x 16 consecutive 32-bit columns of TMEM into 16 registers per thread (no wait)
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+// TMEM loads: the load and tcgen05.wait::ld sit in one asm statement, so the outputs are
+// defined only after the wait and no use of a register can be scheduled before it landed.
+// 32 lanes x 16 columns, load and wait in one statement
+__device__ __forceinline__ void tmem_ld16w(uint32_t taddr, uint32_t (&r)[16]) {
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, "
-        "[%16];"
+        "[%16];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
           "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-        : "r"(taddr));
+        : "r"(taddr)
+        : "memory");
 }
-__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 
 // ---- configuration per order ------------------------------------------------------------------
@@ -417,17 +420,11 @@ __global__ void __launch_bounds__(192, 1) k_tc(const __grid_constant__ TCParams 
                 fence_after_sync();
                 const uint32_t tb = tmem_base + ((uint32_t)(32 * q) << 16) + (uint32_t)(buf * C::NP);
 #pragma unroll
-                for (int c0 = 0; c0 < C::NP; c0 += 32) {
-                    uint32_t r0[16], r1[16];
-                    tmem_ld16(tb + c0, r0);
-                    if (c0 + 16 < C::NP) tmem_ld16(tb + c0 + 16, r1);
-                    tmem_wait_ld();
+                for (int c0 = 0; c0 < C::NP; c0 += 16) {
+                    uint32_t r[16];
+                    tmem_ld16w(tb + c0, r);
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) S[c0 + j] += __uint_as_float(r0[j]);
-                    if (c0 + 16 < C::NP) {
-#pragma unroll
-                        for (int j = 0; j < 16; ++j) S[c0 + 16 + j] += __uint_as_float(r1[j]);
-                    }
+                    for (int j = 0; j < 16; ++j) S[c0 + j] += __uint_as_float(r[j]);
                 }
                 fence_before_sync();
                 mbar_arrive(smem_u32(&acc_empty[buf]));
@@ -455,6 +452,14 @@ __global__ void __launch_bounds__(192, 1) k_tc(const __grid_constant__ TCParams 
                             const float h = to_tf32(f);
                             hrow[b] = h;
                             lrow[b] = to_tf32(f - h);
+                        }
+                    } else if (b < C::NCP) {
+                        // padding columns lie inside the last MMA K step of the next stage:
+                        // they must hold zeros (a stale NaN times a zero column is NaN)
+                        orow[b] = 0.0;
+                        if (hrow) {
+                            hrow[b] = 0.f;
+                            lrow[b] = 0.f;
                         }
                     }
                 }

@@ -95,8 +95,10 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def m2l_pairs_finest(depth):
-    s = 1 << depth
+def m2l_pairs_level(level):
+    """Well-separated pairs at one level of a full uniform tree (children of adjacent parents
+    that are not adjacent themselves, counted axis by axis)."""
+    s = 1 << level
     cand = (3 * (s // 2) - 2) * 4
     near = 3 * s - 2
     return cand ** 3 - near ** 3
@@ -158,6 +160,34 @@ def run_ours(args, rank, world):
     value = n * args.steps * world / (total_ms / 1e3)
     ph = {k: float(np.mean([d[k] for d in phases])) for k in phases[0]}
 
+    # the other precision modes on the same tree (a few steps each), for comparison
+    modes = {}
+    if not args.no_modes:
+        for mname in ("mixed", "fp64"):
+            if mname == args.precision:
+                continue
+            mp = B.PRECISIONS[mname]
+            ksteps = 2 if mname == "fp64" else 5
+            with torch.cuda.stream(stream):
+                tree.eval(p, phi, E, precision=mp, stream=stream)
+                ms = []
+                for _ in range(ksteps):
+                    flush.fill_(1.0)
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    tree.eval(p, phi, E, precision=mp, stream=stream)
+                    e1.record(stream)
+                    e1.synchronize()
+                    ms.append(e0.elapsed_time(e1))
+            modes[mname] = {"value": n / (float(np.mean(ms)) / 1e3), "ms_per_step": float(np.mean(ms)),
+                            "phases_ms": {k: round(v, 4) for k, v in B.dafmm_last_phase_ms(ctx.h).items()
+                                          if k != "launches"}}
+        # back to the headline mode for the accuracy sample
+        with torch.cuda.stream(stream):
+            tree.eval(p, phi, E, precision=prec, stream=stream)
+        stream.synchronize()
+
     # end to end through the public API with host buffers: build_tree + eval per step,
     # host->device copies of the step's inputs and device->host copies of the results
     xp = torch.from_numpy(x).pin_memory()
@@ -165,39 +195,59 @@ def run_ours(args, rank, world):
     phi_h = torch.empty(n, dtype=torch.float64).pin_memory()
     E_h = torch.empty((n, 3), dtype=torch.float64).pin_memory()
     e2e_steps = max(2, min(args.steps, 5))
-    for _ in range(2):
-        tr = ctx.build_tree(xp, qp, domain=dom, uniform_depth=depth, stream=stream)
-        tr.eval(p, phi_h, E_h, precision=prec, stream=stream)
-        tr.free()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        tr = ctx.build_tree(xp, qp, domain=dom, uniform_depth=depth, stream=stream)
-        tr.eval(p, phi_h, E_h, precision=prec, stream=stream)
-        tr.free()
-    torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
-    e2e_value = n * e2e_steps * world / e2e_s
+    e2e_value = None
+    if not args.no_e2e:
+        for _ in range(2):
+            tr = ctx.build_tree(xp, qp, domain=dom, uniform_depth=depth, stream=stream)
+            tr.eval(p, phi_h, E_h, precision=prec, stream=stream)
+            tr.free()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            tr = ctx.build_tree(xp, qp, domain=dom, uniform_depth=depth, stream=stream)
+            tr.eval(p, phi_h, E_h, precision=prec, stream=stream)
+            tr.free()
+        torch.cuda.synchronize()
+        e2e_s = time.perf_counter() - t0
+        e2e_value = n * e2e_steps * world / e2e_s
 
     peaks, peak_src = load_peaks()
-    sm_mhz = ck.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
     nc = (p + 1) * (p + 2) * (p + 3) // 6
-    flops = 2.0 * nc * nc * m2l_pairs_finest(depth)
-    achieved = flops / (ph["m2l_finest"] / 1e3) / 1e12
+    pairs_all = sum(m2l_pairs_level(l) for l in range(2, depth + 1))
+    flops = 2.0 * nc * nc * pairs_all
+    m2l_s = ph["m2l"] / 1e3
+    achieved = flops / m2l_s / 1e12
     if args.precision == "fp64":
-        peak = 1.25  # FP64 nominal, TFLOP/s
-        bound, peak_note = "alu", "FP64 nominal 1.25 TFLOP/s (no measured FP64 peak)"
+        peak, bound = 1.25, "alu"
+        peak_note = "FP64 nominal 1.25 TFLOP/s (no measured FP64 peak)"
+        executed = None
     else:
-        peak = fp32_fma_peak_tflops(peaks.get("sm_max_mhz", 2070.0))
-        bound, peak_note = "alu", "FP32 FMA: 152 SMs x 128 lanes x 2 x %.0f MHz" % peaks.get("sm_max_mhz", 2070.0)
+        # TF32 tensor peak = measured BF16 burst peak x the nominal TF32/BF16 ratio 1/2
+        peak, bound = peaks["bf16_tflops"] / 2.0, "tensor"
+        peak_note = "TF32 = %s BF16 %.1f TFLOP/s x 1/2 (nominal ratio)" % (peak_src, peaks["bf16_tflops"])
+        npt = (nc + 15) // 16 * 16
+        if npt > 192:
+            npt = 2 * (((npt // 2) + 15) // 16 * 16)
+        ncp = (nc + 7) // 8 * 8
+        tiles = 0
+        for l in range(2, depth + 1):
+            S = 1 << (l - 1)
+            bx = min(S, 128); by = min(S, 128 // bx); bz = max(1, min(S, 128 // (bx * by)))
+            tiles += 8 * (S // bx) * (S // by) * (S // bz)
+        executed = tiles * 189 * 3 * 2.0 * 128 * npt * ncp / m2l_s / 1e12
     roofline = {"bound": bound, "achieved": round(achieved, 3), "peak": round(peak, 3), "unit": "TFLOP/s",
-                "frac": round(achieved / peak, 4), "traffic": None, "kernel": "k_m2l (finest level)",
+                "frac": round(achieved / peak, 4), "traffic": None,
+                "kernel": "M2L contraction (tcgen05 k_tc, all levels, one launch)" if bound == "tensor"
+                else "M2L (SIMT FP64 k_m2l, all levels)",
+                "algorithmic": "2 ncoef^2 flops per well-separated pair: %.3e flops" % flops,
+                "executed_tflops": None if executed is None else round(executed, 3),
+                "executed_frac": None if executed is None else round(executed / peak, 4),
                 "peak_source": peak_note}
 
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": {"fp64": "f64", "mixed": "f32+f64", "fp32": "f32"}[args.precision],
+        "scaling": "weak", "vs_baseline": None, "dtype": {"fp64": "f64", "mixed": "f32+f64", "fp32": "f32 (tf32x3 contractions)"}[args.precision],
         "data": "synthetic (seeded uniform, PCG64 seed 2002)",
         "config": {"workload": "uniform N=1e6, q~U[-1,1], octree depth 5, order p=8, theta=1",
                    "precision": args.precision, "l2": "flushed between timed steps (256 MB write)",
@@ -209,6 +259,7 @@ def run_ours(args, rank, world):
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": n * 4 * 8,
                 "d2h_bytes_per_step": n * 4 * 8, "steps": e2e_steps,
                 "includes": "dafmm_build_tree + dafmm_eval from pinned host buffers"},
+        "modes": modes,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"], out["accuracy"] = cpu_baseline(x, q, dom, cfg, phi.cpu().numpy(), E.cpu().numpy())
@@ -306,7 +357,9 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64", "fp32"])
+    ap.add_argument("--precision", default="fp32", choices=["mixed", "fp64", "fp32"])
+    ap.add_argument("--no-modes", action="store_true", help="skip the MIXED / FP64 comparison runs")
+    ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", 0))

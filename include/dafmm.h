@@ -71,15 +71,22 @@ size_t dafmm_bytes_in_use(const dafmm_ctx* ctx);
  *   domain        {x0, y0, z0, size} of the root cube, or NULL for the smallest cube
  *                 containing every point, enlarged by 1e-12 of its size;
  *   uniform_depth >= 0: a uniform tree with 8^depth leaves (depth <= 7);
- *                 < 0: adaptive, boxes with more than max_leaf particles split (Sec. 3.5).
+ *                 < 0: adaptive: a box with more than max_leaf (>= 1) particles is split
+ *                 into its non-empty children (Sec. 3.5), down to level 20 at most; the
+ *                 far field then runs over the interaction lists of Cheng, Greengard and
+ *                 Rokhlin: V (M2L), U (P2P), W (M2P) and X (P2L).
  * Box membership: k = floor((x - x0) * 2^21 / size), clamped to [0, 2^21), per axis; a box
- * of level l holds the particles whose k >> (21 - l) equal its integer coordinates. */
+ * of level l holds the particles whose k >> (21 - l) equal its integer coordinates.
+ * Errors: DAFMM_ERR_INVALID_ARG for n < 0, missing arrays, max_leaf < 1 on an adaptive
+ * tree, depth > 7 or a bad domain; DAFMM_ERR_OVER_BUDGET when the context's budget or the
+ * device runs out of memory. */
 int dafmm_build_tree(dafmm_ctx* ctx, const double* xyz, const double* q, int64_t n,
                      const double* domain, int uniform_depth, int max_leaf, void* stream,
                      dafmm_tree** tree);
 int dafmm_tree_free(dafmm_tree* tree);
-/* info[0..7] = n, depth, leaves, boxes, max particles per leaf, adaptive (0/1), M2L pairs,
- * P2P leaf pairs.  Also writes the root cube to domain4 when it is not NULL. */
+/* info[0..7] = n, depth (the finest level of an adaptive tree), leaves, boxes, max particles
+ * per leaf, adaptive (0/1), M2L pairs (V list entries), P2P leaf pairs (U list entries).
+ * Also writes the root cube to domain4 when it is not NULL. */
 int dafmm_tree_info(const dafmm_tree* tree, int64_t* info8, double* domain4);
 
 /* Evaluate potential and field of every particle with the FMM of expansion order `order`.
@@ -126,7 +133,8 @@ int dafmm_sync(dafmm_ctx* ctx, void* stream);
  * memory that belongs to the library and stays reserved on each GPU that loads it until
  * the process exits.
  *   Limits: order <= 6 (else DAFMM_ERR_UNSUPPORTED_ORDER), uniform trees of depth <= 4
- *   (else DAFMM_ERR_INVALID_ARG); phi and field must be device memory or NULL.
+ *   (else DAFMM_ERR_INVALID_ARG; adaptive trees: DAFMM_ERR_UNSUPPORTED); phi and field must
+ *   be device memory or NULL.
  *   The first call on a device looks up the array's device address; make that call
  *   before any stream capture.  All calls share the array: calls that overlap on the GPU
  *   (other streams, other host threads) race, so the caller must order them. */

@@ -309,6 +309,321 @@ size_t tree_bytes(int64_t n, int depth) {
     return (size_t)n * (4 * sizeof(double) + sizeof(float4) + sizeof(int)) + (nl + 1) * sizeof(int);
 }
 
+
+// ---- adaptive trees -----------------------------------------------------------------------------
+AdaptiveBuild abuild(dafmm_tree* t, const uint64_t* keys) {
+    AdaptiveBuild ab;
+    ab.keys = keys;
+    ab.level = t->a_level;
+    ab.ijk = t->a_ijk;
+    ab.parent = t->a_parent;
+    ab.child = t->a_child;
+    ab.pbeg = t->a_pbeg;
+    ab.pend = t->a_pend;
+    ab.colleague = t->a_colleague;
+    return ab;
+}
+
+AdaptiveView aview(const dafmm_tree* t) {
+    AdaptiveView v;
+    v.nbox = t->nbox;
+    v.level = t->a_level;
+    v.ijk = t->a_ijk;
+    v.parent = t->a_parent;
+    v.child = t->a_child;
+    v.pbeg = t->a_pbeg;
+    v.pend = t->a_pend;
+    v.colleague = t->a_colleague;
+    v.u_ptr = t->u_ptr; v.u_idx = t->u_idx;
+    v.w_ptr = t->w_ptr; v.w_idx = t->w_idx;
+    v.x_ptr = t->x_ptr; v.x_idx = t->x_idx;
+    v.x0 = t->dom[0]; v.y0 = t->dom[1]; v.z0 = t->dom[2]; v.size = t->dom[3];
+    v.x = t->x; v.y = t->y; v.z = t->z; v.q = t->q;
+    v.xq = t->xq;
+    v.perm = t->perm;
+    return v;
+}
+
+// per-box arrays of the adaptive hierarchy, sized for `cap` boxes
+const size_t kBoxInts = 1 + 3 + 1 + 8 + 1 + 1 + 27;
+
+void free_box_arrays(dafmm_ctx* c, dafmm_tree* t) {
+    const size_t cap = (size_t)t->cap;
+    dev_free(c, t->a_level, cap * 4); dev_free(c, t->a_ijk, cap * 12); dev_free(c, t->a_parent, cap * 4);
+    dev_free(c, t->a_child, cap * 32); dev_free(c, t->a_pbeg, cap * 4); dev_free(c, t->a_pend, cap * 4);
+    dev_free(c, t->a_colleague, cap * 108);
+    t->a_level = t->a_ijk = t->a_parent = t->a_child = t->a_pbeg = t->a_pend = t->a_colleague = nullptr;
+    t->cap = 0;
+}
+
+// grow the box arrays to hold `need` boxes, keeping the first `used`
+int grow_boxes(dafmm_ctx* c, dafmm_tree* t, int need, int used, cudaStream_t s) {
+    if (need <= t->cap) return DAFMM_OK;
+    int cap = t->cap ? t->cap : 1024;
+    while (cap < need) cap *= 2;
+    int* nb[7] = {};
+    const size_t w[7] = {1, 3, 1, 8, 1, 1, 27};
+    int* old[7] = {t->a_level, t->a_ijk, t->a_parent, t->a_child, t->a_pbeg, t->a_pend, t->a_colleague};
+    for (int k = 0; k < 7; ++k) {
+        int rc = dev_alloc(c, (void**)&nb[k], (size_t)cap * w[k] * 4, "tree boxes");
+        if (rc) {
+            for (int j = 0; j < k; ++j) dev_free(c, nb[j], (size_t)cap * w[j] * 4);
+            return rc;
+        }
+        if (used && old[k]) CK(c, cudaMemcpyAsync(nb[k], old[k], (size_t)used * w[k] * 4, cudaMemcpyDeviceToDevice, s), "grow");
+    }
+    CK(c, cudaStreamSynchronize(s), "grow");
+    free_box_arrays(c, t);
+    t->a_level = nb[0]; t->a_ijk = nb[1]; t->a_parent = nb[2]; t->a_child = nb[3];
+    t->a_pbeg = nb[4]; t->a_pend = nb[5]; t->a_colleague = nb[6];
+    t->cap = cap;
+    return DAFMM_OK;
+}
+
+void free_adaptive(dafmm_ctx* c, dafmm_tree* t) {
+    free_box_arrays(c, t);
+    const size_t nb1 = (size_t)t->nbox + 1;
+    dev_free(c, t->u_ptr, nb1 * 4); dev_free(c, t->w_ptr, nb1 * 4); dev_free(c, t->x_ptr, nb1 * 4);
+    dev_free(c, t->u_idx, (size_t)t->nu * 4); dev_free(c, t->w_idx, (size_t)t->nw * 4); dev_free(c, t->x_idx, (size_t)t->nx * 4);
+    dev_free(c, t->leaves, (size_t)t->nleaves * 4);
+    dev_free(c, t->grp_tg, (size_t)t->nbox * 4);
+    dev_free(c, t->grp_ptr, ((size_t)(t->maxlev + 1) * 8 + 1) * 4);
+    if (t->a_exp_p >= 0) {
+        const size_t cnt = (size_t)t->nbox * ncp_of(t->a_exp_p);
+        dev_free(c, t->aM, cnt * 8); dev_free(c, t->aL, cnt * 8); dev_free(c, t->aMf, cnt * 4);
+    }
+    t->u_ptr = t->w_ptr = t->x_ptr = t->u_idx = t->w_idx = t->x_idx = t->leaves = t->grp_tg = t->grp_ptr = nullptr;
+    t->aM = t->aL = nullptr;
+    t->aMf = nullptr;
+    t->a_exp_p = -1;
+}
+
+// keys -> sort -> level-by-level split -> colleagues -> leaves -> gather -> lists -> M2L groups
+int build_adaptive(dafmm_ctx* c, dafmm_tree* t, const double* dxyz, const double* dq, int max_leaf, int max_depth,
+                   cudaStream_t s) {
+    const int64_t n = t->n;
+    const size_t N = (size_t)n;
+    int rc;
+    uint64_t* keys = nullptr;
+    void* tmp = nullptr;
+    int* scratch = nullptr;  // counts / offsets
+    const size_t tmpb = radix_sort_temp_bytes(n > 0 ? n : 1);
+    if ((rc = dev_alloc(c, (void**)&keys, (N > 0 ? N : 1) * 8, "sort keys"))) return rc;
+    if ((rc = dev_alloc(c, &tmp, tmpb, "sort scratch"))) { dev_free(c, keys, (N > 0 ? N : 1) * 8); return rc; }
+    auto cleanup = [&]() {
+        dev_free(c, keys, (N > 0 ? N : 1) * 8);
+        dev_free(c, tmp, tmpb);
+    };
+    const double scale = ldexp(1.0, kQBits) / t->dom[3];
+    cudaError_t e = launch_morton_keys(dxyz, n, t->dom[0], t->dom[1], t->dom[2], scale, keys, t->perm, s);
+    if (e == cudaSuccess) e = radix_sort_pairs(keys, t->perm, n, 3 * kQBits, tmp, s);
+    if (e != cudaSuccess) { cleanup(); return cuda_fail(c, e, "Morton sort"); }
+    // hierarchy
+    if ((rc = grow_boxes(c, t, 1024, 0, s))) { cleanup(); return rc; }
+    {
+        int zero3[3] = {0, 0, 0}, m1 = -1, z = 0, nn = (int)n, lev0 = 0;
+        CK(c, cudaMemcpyAsync(t->a_level, &lev0, 4, cudaMemcpyHostToDevice, s), "root");
+        CK(c, cudaMemcpyAsync(t->a_ijk, zero3, 12, cudaMemcpyHostToDevice, s), "root");
+        CK(c, cudaMemcpyAsync(t->a_parent, &m1, 4, cudaMemcpyHostToDevice, s), "root");
+        CK(c, cudaMemcpyAsync(t->a_pbeg, &z, 4, cudaMemcpyHostToDevice, s), "root");
+        CK(c, cudaMemcpyAsync(t->a_pend, &nn, 4, cudaMemcpyHostToDevice, s), "root");
+        CK(c, cudaStreamSynchronize(s), "root");
+    }
+    t->level_start.assign({0, 1});
+    int scap = 0;
+    for (int l = 0; l < max_depth; ++l) {
+        const int lb = t->level_start[l], le = t->level_start[l + 1];
+        const int nl = le - lb;
+        if (2 * (nl + 1) > scap) {
+            dev_free(c, scratch, (size_t)scap * 4);
+            scap = 2 * (nl + 1);
+            if ((rc = dev_alloc(c, (void**)&scratch, (size_t)scap * 4, "split scratch"))) { cleanup(); return rc; }
+        }
+        AdaptiveBuild ab = abuild(t, keys);
+        e = launch_split(ab, lb, le, l, max_leaf, max_depth, scratch, s);
+        if (e == cudaSuccess) e = launch_scan(scratch, scratch + nl + 1, nl, s);
+        int total = 0;
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&total, scratch + nl + 1 + nl, 4, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) { cleanup(); dev_free(c, scratch, (size_t)scap * 4); return cuda_fail(c, e, "split"); }
+        if (total == 0) break;
+        if ((rc = grow_boxes(c, t, le + total, le, s))) { cleanup(); dev_free(c, scratch, (size_t)scap * 4); return rc; }
+        ab = abuild(t, keys);
+        e = launch_split_fill(ab, lb, le, l, scratch + nl + 1, le, s);
+        if (e != cudaSuccess) { cleanup(); dev_free(c, scratch, (size_t)scap * 4); return cuda_fail(c, e, "split"); }
+        t->level_start.push_back(le + total);
+    }
+    t->maxlev = (int)t->level_start.size() - 2;
+    t->nbox = t->level_start.back();
+    const int nbox = t->nbox;
+    e = launch_children_init(t->a_child, t->level_start[t->maxlev], nbox, s);
+    for (int l = 0; l <= t->maxlev && e == cudaSuccess; ++l)
+        e = launch_colleagues(abuild(t, keys), t->level_start[l], t->level_start[l + 1], s);
+    if (e != cudaSuccess) { cleanup(); dev_free(c, scratch, (size_t)scap * 4); return cuda_fail(c, e, "colleagues"); }
+    // leaves (breadth-first order)
+    dev_free(c, scratch, (size_t)scap * 4);
+    scap = 2 * (nbox + 1);
+    if ((rc = dev_alloc(c, (void**)&scratch, (size_t)scap * 4, "leaf scratch"))) { cleanup(); return rc; }
+    e = launch_leaf_flags(t->a_child, nbox, scratch, s);
+    if (e == cudaSuccess) e = launch_scan(scratch, scratch + nbox + 1, nbox, s);
+    int nl = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&nl, scratch + nbox + 1 + nbox, 4, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    t->nleaves = nl;
+    if (e == cudaSuccess && (rc = dev_alloc(c, (void**)&t->leaves, (size_t)(nl > 0 ? nl : 1) * 4, "leaves"))) {
+        cleanup(); dev_free(c, scratch, (size_t)scap * 4); return rc;
+    }
+    if (e == cudaSuccess) e = launch_scatter_flagged(scratch, scratch + nbox + 1, nbox, t->leaves, s);
+    if (e == cudaSuccess)
+        e = launch_gather_adaptive(dxyz, dq, t->perm, abuild(t, keys), t->leaves, nl, t->dom, t->x, t->y, t->z, t->q,
+                                   t->xq, s);
+    if (e != cudaSuccess) { cleanup(); dev_free(c, scratch, (size_t)scap * 4); return cuda_fail(c, e, "leaves"); }
+    // U, W, X lists
+    int* cnt3 = nullptr;
+    const size_t nb1 = (size_t)nbox + 1;
+    const size_t cnt3b = 3 * nb1 * 4 + 16;  // three count arrays, then the V pair counter (8-aligned)
+    if ((rc = dev_alloc(c, (void**)&cnt3, cnt3b, "list counts"))) { cleanup(); dev_free(c, scratch, (size_t)scap * 4); return rc; }
+    unsigned long long* nv = reinterpret_cast<unsigned long long*>(cnt3 + ((3 * nb1 + 1) & ~size_t(1)));
+    if (!rc) rc = dev_alloc(c, (void**)&t->u_ptr, nb1 * 4, "lists");
+    if (!rc) rc = dev_alloc(c, (void**)&t->w_ptr, nb1 * 4, "lists");
+    if (!rc) rc = dev_alloc(c, (void**)&t->x_ptr, nb1 * 4, "lists");
+    CK(c, cudaMemsetAsync(c->d_err, 0, 4, s), "err");
+    CK(c, cudaMemsetAsync(nv, 0, 8, s), "counter");
+    e = launch_list_count(abuild(t, keys), nbox, cnt3, cnt3 + nb1, cnt3 + 2 * nb1, nv, c->d_err, s);
+    if (e == cudaSuccess) e = launch_scan(cnt3, t->u_ptr, nbox, s);
+    if (e == cudaSuccess) e = launch_scan(cnt3 + nb1, t->w_ptr, nbox, s);
+    if (e == cudaSuccess) e = launch_scan(cnt3 + 2 * nb1, t->x_ptr, nbox, s);
+    int tot[3] = {0, 0, 0};
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&tot[0], t->u_ptr + nbox, 4, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&tot[1], t->w_ptr + nbox, 4, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&tot[2], t->x_ptr + nbox, 4, cudaMemcpyDeviceToHost, s);
+    unsigned long long nvh = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&nvh, nv, 8, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess || rc) { cleanup(); dev_free(c, scratch, (size_t)scap * 4); dev_free(c, cnt3, cnt3b); return rc ? rc : cuda_fail(c, e, "lists"); }
+    t->nv = (int64_t)nvh;
+    t->nu = tot[0]; t->nw = tot[1]; t->nx = tot[2];
+    if (!rc) rc = dev_alloc(c, (void**)&t->u_idx, (size_t)(tot[0] > 0 ? tot[0] : 1) * 4, "lists");
+    if (!rc) rc = dev_alloc(c, (void**)&t->w_idx, (size_t)(tot[1] > 0 ? tot[1] : 1) * 4, "lists");
+    if (!rc) rc = dev_alloc(c, (void**)&t->x_idx, (size_t)(tot[2] > 0 ? tot[2] : 1) * 4, "lists");
+    if (!rc) {
+        e = launch_list_fill(abuild(t, keys), nbox, t->u_ptr, t->w_ptr, t->x_ptr, t->u_idx, t->w_idx, t->x_idx, c->d_err, s);
+        int flag = 0;
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&flag, c->d_err, 4, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e == cudaSuccess && flag) rc = fail(c, DAFMM_ERR_INVALID_ARG, "adaptive tree too deep for the list traversal");
+    }
+    dev_free(c, cnt3, cnt3b);
+    // M2L target groups: boxes of levels >= 2 by (level, octant)
+    const int ngroups = (t->maxlev + 1) * 8;
+    if (!rc && e == cudaSuccess) {
+        uint64_t* gk = nullptr;
+        void* gtmp = nullptr;
+        const size_t gtb = radix_sort_temp_bytes(nbox);
+        rc = dev_alloc(c, (void**)&gk, (size_t)nbox * 8, "groups");
+        if (!rc) rc = dev_alloc(c, &gtmp, gtb, "groups");
+        if (!rc) rc = dev_alloc(c, (void**)&t->grp_tg, (size_t)nbox * 4, "groups");
+        if (!rc) rc = dev_alloc(c, (void**)&t->grp_ptr, ((size_t)ngroups + 1) * 4, "groups");
+        if (!rc) {
+            e = launch_group_keys(t->a_level, t->a_ijk, nbox, gk, t->grp_tg, s);
+            if (e == cudaSuccess) e = radix_sort_pairs(gk, t->grp_tg, nbox, 8, gtmp, s);
+            if (e == cudaSuccess) e = launch_group_ptr(gk, nbox, ngroups, t->grp_ptr, s);
+            t->grp_ptr_h.assign(ngroups + 1, 0);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(t->grp_ptr_h.data(), t->grp_ptr, (ngroups + 1) * 4, cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        }
+        dev_free(c, gk, (size_t)nbox * 8);
+        dev_free(c, gtmp, gtb);
+    }
+    cleanup();
+    dev_free(c, scratch, (size_t)scap * 4);
+    if (rc) return rc;
+    if (e != cudaSuccess) return cuda_fail(c, e, "adaptive build");
+    // largest leaf
+    std::vector<int> pb(nbox), pe(nbox), lf(nl);
+    CK(c, cudaMemcpy(pb.data(), t->a_pbeg, (size_t)nbox * 4, cudaMemcpyDeviceToHost), "info");
+    CK(c, cudaMemcpy(pe.data(), t->a_pend, (size_t)nbox * 4, cudaMemcpyDeviceToHost), "info");
+    CK(c, cudaMemcpy(lf.data(), t->leaves, (size_t)nl * 4, cudaMemcpyDeviceToHost), "info");
+    for (int b : lf) t->max_per_leaf = std::max(t->max_per_leaf, pe[b] - pb[b]);
+    return DAFMM_OK;
+}
+
+int ensure_adaptive_expansions(dafmm_tree* t, int p, cudaStream_t s) {
+    if (t->a_exp_p == p) return DAFMM_OK;
+    dafmm_ctx* c = t->ctx;
+    if (t->a_exp_p >= 0) {
+        const size_t cnt = (size_t)t->nbox * ncp_of(t->a_exp_p);
+        dev_free(c, t->aM, cnt * 8); dev_free(c, t->aL, cnt * 8); dev_free(c, t->aMf, cnt * 4);
+        t->a_exp_p = -1;
+    }
+    const size_t cnt = (size_t)t->nbox * ncp_of(p);
+    int rc;
+    if ((rc = dev_alloc(c, (void**)&t->aM, cnt * 8, "multipoles"))) return rc;
+    if ((rc = dev_alloc(c, (void**)&t->aL, cnt * 8, "locals"))) return rc;
+    if ((rc = dev_alloc(c, (void**)&t->aMf, cnt * 4, "multipoles (FP32)"))) return rc;
+    CK(c, cudaMemsetAsync(t->aM, 0, cnt * 8, s), "memset");
+    CK(c, cudaMemsetAsync(t->aL, 0, cnt * 8, s), "memset");
+    CK(c, cudaMemsetAsync(t->aMf, 0, cnt * 4, s), "memset");
+    t->a_exp_p = p;
+    return DAFMM_OK;
+}
+
+int eval_adaptive(dafmm_tree* t, int order, int precision, double* dphi, double* dfield, cudaStream_t s) {
+    dafmm_ctx* c = t->ctx;
+    const OrderOps* ops = order_ops(order);
+    const bool far = t->maxlev >= 2;
+    int rc;
+    if ((rc = ensure_order(c, order, s, far))) return rc;
+    if ((rc = ensure_adaptive_expansions(t, order, s))) return rc;
+    const OrderData& od = c->ord[order];
+    const AdaptiveView av = aview(t);
+    auto mark = [&](int k) {
+        if (c->profile) cudaEventRecord(c->ev[k], s);
+    };
+    int launches = 0;
+    mark(0);
+    if (far) {
+        CK(c, ops->p2m_a(av, t->leaves, t->nleaves, precision, t->aM, s), "P2M");
+        ++launches;
+        mark(1);
+        for (int l = t->maxlev - 1; l >= 2; --l) {
+            CK(c, ops->m2m_a(od, av, precision, t->level_start[l], t->level_start[l + 1], t->aM, s), "M2M");
+            ++launches;
+        }
+        mark(2);
+        if (precision != DAFMM_FP64) {
+            const size_t cnt = (size_t)t->nbox * od.ncp;
+            k_to_float<<<(unsigned)std::min<size_t>((cnt + 255) / 256, 152 * 16), 256, 0, s>>>(t->aM, t->aMf, cnt);
+            CK(c, cudaGetLastError(), "convert");
+            ++launches;
+        }
+        mark(3);
+        for (int l = 2; l <= t->maxlev; ++l) {
+            if (l == t->maxlev) mark(4);
+            int mx = 0;
+            for (int o = 0; o < 8; ++o) mx = std::max(mx, t->grp_ptr_h[l * 8 + o + 1] - t->grp_ptr_h[l * 8 + o]);
+            CK(c, ops->m2l_a(od, av, precision, t->grp_tg, t->grp_ptr, l * 8, mx, t->aM, t->aMf, t->aL,
+                             1.0 / ldexp(t->dom[3], -l), s), "M2L");
+            CK(c, ops->p2l_a(av, precision, t->level_start[l], t->level_start[l + 1], t->aL, s), "P2L");
+            launches += 2;
+        }
+        mark(5);
+        for (int l = 3; l <= t->maxlev; ++l) {
+            CK(c, ops->l2l_a(od, av, precision, t->level_start[l], t->level_start[l + 1], t->aL, s), "L2L");
+            ++launches;
+        }
+        mark(6);
+    } else {
+        for (int k = 1; k <= 6; ++k) mark(k);
+    }
+    CK(c, ops->leaf_a(av, t->leaves, t->nleaves, precision, t->aL, t->aM, dphi, dfield, s), "P2P/M2P/L2P");
+    ++launches;
+    mark(7);
+    c->last_launches = launches;
+    c->have_profile = c->profile;
+    return DAFMM_OK;
+}
 }  // namespace
 
 namespace dafmm {
@@ -385,11 +700,9 @@ int dafmm_build_tree(dafmm_ctx* c, const double* xyz, const double* q, int64_t n
     *out = nullptr;
     if (n < 0 || n > (int64_t)INT32_MAX - 1 || (n > 0 && (!xyz || !q)))
         return fail(c, DAFMM_ERR_INVALID_ARG, "particle arrays");
-    if (uniform_depth < 0)
-        return fail(c, DAFMM_ERR_UNSUPPORTED, "adaptive trees are not available in this build");
+    if (uniform_depth < 0 && max_leaf < 1) return fail(c, DAFMM_ERR_INVALID_ARG, "max_leaf must be >= 1");
     if (uniform_depth > kMaxUniformDepth)
         return fail(c, DAFMM_ERR_INVALID_ARG, "uniform depth above " + std::to_string(kMaxUniformDepth));
-    (void)max_leaf;
     if (domain && !(domain[3] > 0.0 && isfinite(domain[0]) && isfinite(domain[1]) && isfinite(domain[2]) &&
                     isfinite(domain[3])))
         return fail(c, DAFMM_ERR_INVALID_ARG, "domain");
@@ -405,8 +718,10 @@ int dafmm_build_tree(dafmm_ctx* c, const double* xyz, const double* q, int64_t n
     dafmm_tree* t = new dafmm_tree();
     t->ctx = c;
     t->n = n;
-    t->depth = uniform_depth;
-    t->nleaf = (int)level_boxes(uniform_depth);
+    t->adaptive = uniform_depth < 0;
+    t->max_leaf = max_leaf;
+    t->depth = t->adaptive ? 0 : uniform_depth;
+    t->nleaf = t->adaptive ? 0 : (int)level_boxes(uniform_depth);
     // root cube
     if (domain) {
         for (int d = 0; d < 4; ++d) t->dom[d] = domain[d];
@@ -444,6 +759,21 @@ int dafmm_build_tree(dafmm_ctx* c, const double* xyz, const double* q, int64_t n
     if (!rc) rc = dev_alloc(c, (void**)&t->xq, N * sizeof(float4), "particles");
     if (!rc) rc = dev_alloc(c, (void**)&t->perm, N * sizeof(int), "particles");
     if (!rc) rc = dev_alloc(c, (void**)&t->leaf_start, ((size_t)t->nleaf + 1) * sizeof(int), "leaves");
+    if (t->adaptive) {
+        if (rc) {
+            c->trees.push_back(t);
+            dafmm_tree_free(t);
+            return rc;
+        }
+        c->trees.push_back(t);
+        rc = build_adaptive(c, t, dxyz, dq, max_leaf, kMaxAdaptiveDepth, s);
+        if (rc) {
+            dafmm_tree_free(t);
+            return rc;
+        }
+        *out = t;
+        return DAFMM_OK;
+    }
     uint64_t* keys = nullptr;
     void* tmp = nullptr;
     const size_t tmpb = radix_sort_temp_bytes(n);
@@ -493,6 +823,7 @@ int dafmm_tree_free(dafmm_tree* t) {
     dev_free(c, t->perm, N * sizeof(int));
     dev_free(c, t->leaf_start, ((size_t)t->nleaf + 1) * sizeof(int));
     dev_free(c, t->out_scratch, t->out_scratch_bytes);
+    if (t->adaptive) free_adaptive(c, t);
     auto it = std::find(c->trees.begin(), c->trees.end(), t);
     if (it != c->trees.end()) c->trees.erase(it);
     delete t;
@@ -515,6 +846,19 @@ int dafmm_tree_info(const dafmm_tree* t, int64_t* info, double* domain4) {
         const int64_t s = (int64_t)1 << t->depth;
         const int64_t near1 = 3 * s - 2;
         p2p = near1 * near1 * near1;
+    }
+    if (t->adaptive) {
+        info[0] = t->n;
+        info[1] = t->maxlev;
+        info[2] = t->nleaves;
+        info[3] = t->nbox;
+        info[4] = t->max_per_leaf;
+        info[5] = 1;
+        info[6] = t->nv;
+        info[7] = t->nu;
+        if (domain4)
+            for (int d = 0; d < 4; ++d) domain4[d] = t->dom[d];
+        return DAFMM_OK;
     }
     info[0] = t->n;
     info[1] = t->depth;
@@ -563,6 +907,13 @@ int dafmm_eval(dafmm_tree* t, int order, double theta, int precision, double* ph
         }
         if (!phi_dev) dphi = t->out_scratch;
         if (!field_dev) dfield = t->out_scratch + N;
+    }
+    if (t->adaptive) {
+        if ((rc = eval_adaptive(t, order, precision, dphi, dfield, s))) return rc;
+        if (!phi_dev) CK(c, cudaMemcpyAsync(phi, dphi, N * sizeof(double), cudaMemcpyDeviceToHost, s), "D2H");
+        if (!field_dev) CK(c, cudaMemcpyAsync(field, dfield, N * 3 * sizeof(double), cudaMemcpyDeviceToHost, s), "D2H");
+        if (!phi_dev || !field_dev) CK(c, cudaStreamSynchronize(s), "sync");
+        return DAFMM_OK;
     }
     const TreeView tv = make_view(t);
     const OrderData& od = c->ord[order];
@@ -775,12 +1126,20 @@ int dafmm_last_phase_ms(dafmm_ctx* c, double* out) {
 }
 
 size_t dafmm_footprint(int64_t n, int order, int uniform_depth, int max_leaf, int precision) {
-    (void)max_leaf;
     (void)precision;
     if (order < 0 || order > kMaxOrder || n < 0) return 0;
     const int depth = uniform_depth < 0 ? 0 : uniform_depth;
     size_t b = tree_bytes(n, depth);
     const size_t ncp = ncp_of(order), nc = ncoef_of(order);
+    if (uniform_depth < 0) {
+        // adaptive: about 16 n / max_leaf boxes; per box its hierarchy record, list entries
+        // (U, W and X, about 64 on average) and the expansions
+        const size_t nbox = 2 + (size_t)(16 * n) / (size_t)(max_leaf > 0 ? max_leaf : 1);
+        b += nbox * (kBoxInts * 4 + 64 * 4 + 24 + ncp * (8 + 8 + 4));
+        b += (size_t)kNumKeys * nc * ncp * 12;
+        b += (size_t)n * 12 + radix_sort_temp_bytes(n) + radix_sort_temp_bytes((int64_t)nbox);
+        return b;
+    }
     for (int l = 2; l <= depth; ++l) b += level_boxes(l) * ncp * (8 + 8 + 4);
     b += (size_t)kNumKeys * nc * ncp * 12;
     b += (size_t)n * 12 + radix_sort_temp_bytes(n);  // build-time scratch

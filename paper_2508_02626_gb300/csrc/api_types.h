@@ -8,6 +8,7 @@
 #include <vector>
 
 #include "internal.h"
+#include "tree_adaptive.h"
 
 struct dafmm_ctx {
     int device = 0;
@@ -54,6 +55,23 @@ struct dafmm_tree {
     Expansions ex;
     double* out_scratch = nullptr;  // device outputs when the caller passes host buffers
     size_t out_scratch_bytes = 0;
+    // adaptive trees (boxes breadth-first; see tree_adaptive.h)
+    bool adaptive = false;
+    int nbox = 1, maxlev = 0, cap = 0, max_leaf = 0;
+    std::vector<int> level_start;   // first box of each level, plus the end
+    int *a_level = nullptr, *a_ijk = nullptr, *a_parent = nullptr, *a_child = nullptr;
+    int *a_pbeg = nullptr, *a_pend = nullptr, *a_colleague = nullptr;
+    int *u_ptr = nullptr, *u_idx = nullptr, *w_ptr = nullptr, *w_idx = nullptr, *x_ptr = nullptr, *x_idx = nullptr;
+    int nu = 0, nw = 0, nx = 0;
+    int64_t nv = 0;  // M2L (V list) pairs
+    int* leaves = nullptr;
+    int nleaves = 0;
+    int* grp_tg = nullptr;          // boxes of levels >= 2 grouped by (level, octant)
+    int* grp_ptr = nullptr;         // (maxlev + 1) * 8 + 1 offsets
+    std::vector<int> grp_ptr_h;
+    int a_exp_p = -1;               // order of the adaptive expansion arrays
+    double *aM = nullptr, *aL = nullptr;
+    float* aMf = nullptr;
 };
 
 

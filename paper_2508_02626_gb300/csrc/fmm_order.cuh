@@ -22,6 +22,7 @@
 
 #include "da_common.cuh"
 #include "internal.h"
+#include "tree_adaptive.h"
 #include "tree_common.cuh"
 
 #define DAFMM_CAT_(a, b) a##b
@@ -490,6 +491,399 @@ __global__ void __launch_bounds__(128) k_leaf(TreeView tv, const double* __restr
     }
 }
 
+// ---- adaptive trees ---------------------------------------------------------------------------
+// Box geometry of an adaptive box: width size/2^level, centre from its integer coordinates.
+__device__ __forceinline__ void abox_geom(const AdaptiveView& av, int b, double& cx, double& cy, double& cz,
+                                          double& h) {
+    h = ldexp(av.size, -av.level[b]);
+    cx = av.x0 + ((double)av.ijk[3 * b] + 0.5) * h;
+    cy = av.y0 + ((double)av.ijk[3 * b + 1] + 0.5) * h;
+    cz = av.z0 + ((double)av.ijk[3 * b + 2] + 0.5) * h;
+}
+
+__device__ __forceinline__ bool abox_is_leaf(const AdaptiveView& av, int b) {
+    const int4 c0 = *reinterpret_cast<const int4*>(av.child + 8 * b);
+    const int4 c1 = *reinterpret_cast<const int4*>(av.child + 8 * b + 4);
+    return (c0.x & c0.y & c0.z & c0.w & c1.x & c1.y & c1.z & c1.w) < 0 &&
+           c0.x < 0 && c0.y < 0 && c0.z < 0 && c0.w < 0 && c1.x < 0 && c1.y < 0 && c1.z < 0 && c1.w < 0;
+}
+
+// P2M (Eq. 2) at the leaves listed in `leaves`: one warp per leaf, as in k_p2m
+template <class T>
+__global__ void k_p2m_a(AdaptiveView av, const int* __restrict__ leaves, int nleaves, double* __restrict__ M) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* sm = reinterpret_cast<T*>(smem_raw) + threadIdx.y * (NC * 33);
+    const int lane = threadIdx.x;
+    const int li = blockIdx.x * blockDim.y + threadIdx.y;
+    if (li >= nleaves) return;
+    const int b = leaves[li];
+    double cx, cy, cz, h;
+    abox_geom(av, b, cx, cy, cz, h);
+    const double ih = 1.0 / h;
+    const int i0 = av.pbeg[b], i1 = av.pend[b];
+    constexpr int NJ = (NC + 31) / 32;
+    T acc[NJ];
+#pragma unroll
+    for (int j = 0; j < NJ; ++j) acc[j] = T(0);
+    SmemSink<T> sink{sm, lane};
+    for (int base = i0; base < i1; base += 32) {
+        const int i = base + lane;
+        T x = T(0), y = T(0), z = T(0), q = T(0);
+        if (i < i1) {
+            x = (T)((av.x[i] - cx) * ih);
+            y = (T)((av.y[i] - cy) * ih);
+            z = (T)((av.z[i] - cz) * ih);
+            q = (T)av.q[i];
+        }
+        gen::GEN(p2m)<T>(x, y, z, q, sink);
+        __syncwarp();
+#pragma unroll
+        for (int j = 0; j < NJ; ++j) {
+            const int k = lane + 32 * j;
+            if (k < NC) {
+                T s = T(0);
+#pragma unroll 8
+                for (int l = 0; l < 32; ++l) s += sm[k * 33 + l];
+                acc[j] += s;
+            }
+        }
+        __syncwarp();
+    }
+#pragma unroll
+    for (int j = 0; j < NJ; ++j) {
+        const int k = lane + 32 * j;
+        if (k < NC) M[(size_t)b * NCP + k] = (double)acc[j];
+    }
+}
+
+// M2M (Eq. 4) into the non-leaf boxes [lb, le) of one level, from their existing children
+template <class T>
+__global__ void __launch_bounds__(256) k_m2m_a(ShiftTab tab, AdaptiveView av, int lb, int le, double* __restrict__ M) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* src = reinterpret_cast<T*>(smem_raw);  // [32][NCP + 1]
+    __shared__ int cidx[32];
+    const int b0 = lb + blockIdx.x * 32;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    T acc[SH_ROWS];
+#pragma unroll
+    for (int j = 0; j < SH_ROWS; ++j) acc[j] = T(0);
+    for (int c = 0; c < 8; ++c) {
+        if (threadIdx.x < 32) {
+            const int b = b0 + threadIdx.x;
+            cidx[threadIdx.x] = b < le ? av.child[8 * b + c] : -1;
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < 32 * NC; e += 256) {
+            const int r = e / NC, k = e - r * NC;
+            const int ch = cidx[r];
+            src[r * (NCP + 1) + k] = ch >= 0 ? (T)M[(size_t)ch * NCP + k] : T(0);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < SH_ROWS; ++j) {
+            const int bb = w + 8 * j;
+            if (bb < NC) {
+                T s = T(0);
+                for (int e = tab.rowptr[bb]; e < tab.rowptr[bb + 1]; ++e) {
+                    T v = tab_val<T>(tab, e);
+                    if (__popc(tab.par[e] & c) & 1) v = -v;
+                    s += v * src[lane * (NCP + 1) + tab.col[e]];
+                }
+                acc[j] += s;
+            }
+        }
+        __syncthreads();
+    }
+    const int b = b0 + lane;
+    if (b < le && !abox_is_leaf(av, b)) {
+#pragma unroll
+        for (int j = 0; j < SH_ROWS; ++j) {
+            const int bb = w + 8 * j;
+            if (bb < NC) M[(size_t)b * NCP + bb] = (double)acc[j];
+        }
+    }
+}
+
+// M2L (Eq. 5) into the boxes tg[0..ntg) of one level that share the octant `oct`; the source
+// of displacement v is child sc of the parent's colleague at offset a (c - v = 2a + sc)
+template <class T, class Src>
+__global__ void __launch_bounds__(256) k_m2l_a(const T* __restrict__ K, AdaptiveView av, const int* __restrict__ tg,
+                                               const int* __restrict__ grp_ptr, int grp0, const Src* __restrict__ M,
+                                               double* __restrict__ L, double inv_h) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* src = reinterpret_cast<T*>(smem_raw);  // [32][NCP + 1]
+    __shared__ int sidx[32];
+    const int oct = blockIdx.y;
+    const int g0 = grp_ptr[grp0 + oct], g1 = grp_ptr[grp0 + oct + 1];
+    const int t0 = g0 + blockIdx.x * 32;
+    if (t0 >= g1) return;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int ox = oct & 1, oy = (oct >> 1) & 1, oz = (oct >> 2) & 1;
+    T acc[SH_ROWS];
+#pragma unroll
+    for (int j = 0; j < SH_ROWS; ++j) acc[j] = T(0);
+    for (int vx = -3 + ox; vx <= 2 + ox; ++vx)
+        for (int vy = -3 + oy; vy <= 2 + oy; ++vy)
+            for (int vz = -3 + oz; vz <= 2 + oz; ++vz) {
+                if (abs(vx) <= 1 && abs(vy) <= 1 && abs(vz) <= 1) continue;
+                if (threadIdx.x < 32) {
+                    const int ti = t0 + threadIdx.x;
+                    int sbox = -1;
+                    if (ti < g1) {
+                        const int P = av.parent[tg[ti]];
+                        const int dx = ox - vx, dy = oy - vy, dz = oz - vz;  // = 2a + sc
+                        const int scx = dx & 1, scy = dy & 1, scz = dz & 1;
+                        const int ax = (dx - scx) >> 1, ay = (dy - scy) >> 1, az = (dz - scz) >> 1;
+                        const int Q = av.colleague[27 * P + (ax + 1) * 9 + (ay + 1) * 3 + (az + 1)];
+                        if (Q >= 0) sbox = av.child[8 * Q + (scx | (scy << 1) | (scz << 2))];
+                    }
+                    sidx[threadIdx.x] = sbox;
+                }
+                __syncthreads();
+                for (int e = threadIdx.x; e < 32 * NC; e += 256) {
+                    const int r = e / NC, k = e - r * NC;
+                    const int sb = sidx[r];
+                    src[r * (NCP + 1) + k] = sb >= 0 ? (T)M[(size_t)sb * NCP + k] : T(0);
+                }
+                __syncthreads();
+                const int key = (vx + 3) * 49 + (vy + 3) * 7 + (vz + 3);
+                const T* Kv = K + (size_t)key * NC * NCP;
+                const T* srow = src + lane * (NCP + 1);
+                const T* kw = Kv + (size_t)w * NCP;
+#pragma unroll 1
+                for (int a = 0; a < NC; ++a) {
+                    const T sv = srow[a];
+#pragma unroll
+                    for (int j = 0; j < SH_ROWS; ++j)
+                        if (w + 8 * j < NC) acc[j] = fma(kw[(size_t)(8 * j) * NCP + a], sv, acc[j]);
+                }
+                __syncthreads();
+            }
+    const int ti = t0 + lane;
+    if (ti < g1) {
+        const int t = tg[ti];
+#pragma unroll
+        for (int j = 0; j < SH_ROWS; ++j) {
+            const int b = w + 8 * j;
+            if (b < NC) L[(size_t)t * NCP + b] = (double)acc[j] * inv_h;
+        }
+    }
+}
+
+// P2L (Eq. 6): particles of the X-list leaves of each box of [lb, le) into its local expansion
+template <class T>
+__global__ void k_p2l_a(AdaptiveView av, int lb, int le, double* __restrict__ L) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* sm = reinterpret_cast<T*>(smem_raw) + threadIdx.y * (NC * 33);
+    const int lane = threadIdx.x;
+    const int b = lb + blockIdx.x * blockDim.y + threadIdx.y;
+    if (b >= le) return;
+    const int x0i = av.x_ptr[b], x1i = av.x_ptr[b + 1];
+    if (x0i == x1i) return;
+    double cx, cy, cz, h;
+    abox_geom(av, b, cx, cy, cz, h);
+    const double ih = 1.0 / h;
+    constexpr int NJ = (NC + 31) / 32;
+    T acc[NJ];
+#pragma unroll
+    for (int j = 0; j < NJ; ++j) acc[j] = T(0);
+    SmemSink<T> sink{sm, lane};
+    for (int xi = x0i; xi < x1i; ++xi) {
+        const int c = av.x_idx[xi];
+        const int i0 = av.pbeg[c], i1 = av.pend[c];
+        for (int base = i0; base < i1; base += 32) {
+            const int i = base + lane;
+            T X = T(1), Y = T(0), Z = T(0), q = T(0);  // a dummy far point for idle lanes
+            if (i < i1) {
+                X = (T)((cx - av.x[i]) * ih);
+                Y = (T)((cy - av.y[i]) * ih);
+                Z = (T)((cz - av.z[i]) * ih);
+                q = (T)av.q[i];
+            }
+            gen::GEN(p2l)<T>(X, Y, Z, q, sink);
+            __syncwarp();
+#pragma unroll
+            for (int j = 0; j < NJ; ++j) {
+                const int k = lane + 32 * j;
+                if (k < NC) {
+                    T s = T(0);
+#pragma unroll 8
+                    for (int l = 0; l < 32; ++l) s += sm[k * 33 + l];
+                    acc[j] += s;
+                }
+            }
+            __syncwarp();
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < NJ; ++j) {
+        const int k = lane + 32 * j;
+        if (k < NC) L[(size_t)b * NCP + k] += (double)acc[j] * ih;
+    }
+}
+
+// L2L (Eq. 7) into the boxes [lb, le) of one level from their parents
+template <class T>
+__global__ void __launch_bounds__(256) k_l2l_a(ShiftTab tab, AdaptiveView av, int lb, int le, double* __restrict__ L) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* src = reinterpret_cast<T*>(smem_raw);  // [32][NCP + 1]
+    __shared__ int pidx[32];
+    __shared__ int coct[32];
+    const int b0 = lb + blockIdx.x * 32;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (threadIdx.x < 32) {
+        const int b = b0 + threadIdx.x;
+        int P = -1, c = 0;
+        if (b < le) {
+            P = av.parent[b];
+            c = (av.ijk[3 * b] & 1) | ((av.ijk[3 * b + 1] & 1) << 1) | ((av.ijk[3 * b + 2] & 1) << 2);
+        }
+        pidx[threadIdx.x] = P;
+        coct[threadIdx.x] = c;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < 32 * NC; e += 256) {
+        const int r = e / NC, k = e - r * NC;
+        const int P = pidx[r];
+        src[r * (NCP + 1) + k] = P >= 0 ? (T)L[(size_t)P * NCP + k] : T(0);
+    }
+    __syncthreads();
+    const int b = b0 + lane;
+    const int c = coct[lane];
+#pragma unroll
+    for (int j = 0; j < SH_ROWS; ++j) {
+        const int bb = w + 8 * j;
+        if (bb < NC) {
+            T s = T(0);
+            for (int e = tab.rowptr[bb]; e < tab.rowptr[bb + 1]; ++e) {
+                T v = tab_val<T>(tab, e);
+                if (__popc(tab.par[e] & c) & 1) v = -v;
+                s += v * src[lane * (NCP + 1) + tab.col[e]];
+            }
+            if (b < le) L[(size_t)b * NCP + bb] += (double)s;
+        }
+    }
+}
+
+// leaves: P2P over the U list, M2P over the W list, L2P of the leaf's local expansion
+template <class T>
+__global__ void __launch_bounds__(128) k_leaf_a(AdaptiveView av, const int* __restrict__ leaves, int nleaves,
+                                                const double* __restrict__ L, const double* __restrict__ M,
+                                                double* __restrict__ phi, double* __restrict__ field) {
+    const int lane = threadIdx.x;
+    const int li = blockIdx.x * blockDim.y + threadIdx.y;
+    if (li >= nleaves) return;
+    const int b = leaves[li];
+    double cx, cy, cz, h;
+    abox_geom(av, b, cx, cy, cz, h);
+    const double ih = 1.0 / h;
+    const int lev = av.level[b];
+    const int i0 = av.pbeg[b], i1 = av.pend[b];
+    const int u0 = av.u_ptr[b], u1 = av.u_ptr[b + 1];
+    const int w0 = av.w_ptr[b], w1 = av.w_ptr[b + 1];
+    for (int base = i0; base < i1; base += 32) {
+        const int t = base + lane;
+        const bool valid = t < i1;
+        const int tt = valid ? t : i0;
+        double fphi = 0.0, fx = 0.0, fy = 0.0, fz = 0.0;
+        if constexpr (sizeof(T) == 8) {
+            const double xt = av.x[tt], yt = av.y[tt], zt = av.z[tt];
+            for (int ui = u0; ui < u1; ++ui) {
+                const int sb = av.u_idx[ui];
+                for (int sidx = av.pbeg[sb]; sidx < av.pend[sb]; ++sidx) {
+                    const double ex = xt - av.x[sidx], ey = yt - av.y[sidx], ez = zt - av.z[sidx];
+                    const double r2 = ex * ex + ey * ey + ez * ez;
+                    if (r2 > 0.0) {
+                        const double ir = rsqrt(r2);
+                        const double qr = av.q[sidx] * ir;
+                        const double qr3 = qr * ir * ir;
+                        fphi += qr;
+                        fx += qr3 * ex; fy += qr3 * ey; fz += qr3 * ez;
+                    }
+                }
+            }
+        } else {
+            const float4 pt = av.xq[tt];
+            float ph = 0.f, pl = 0.f, xh = 0.f, xl = 0.f, yh = 0.f, yl = 0.f, zh = 0.f, zl = 0.f;
+            for (int ui = u0; ui < u1; ++ui) {
+                const int sb = av.u_idx[ui];
+                double scx, scy, scz, sh;
+                abox_geom(av, sb, scx, scy, scz, sh);
+                // source leaf frame -> this leaf's frame: x_t_frame = off + r x_s (exact dyadic values)
+                const float r = (float)(sh * ih);
+                const float offx = (float)((scx - cx) * ih), offy = (float)((scy - cy) * ih),
+                            offz = (float)((scz - cz) * ih);
+                for (int sbeg = av.pbeg[sb]; sbeg < av.pend[sb]; sbeg += 64) {
+                    const int send = min(av.pend[sb], sbeg + 64);
+                    float sp = 0.f, sx = 0.f, sy = 0.f, sz = 0.f;
+                    for (int sidx = sbeg; sidx < send; ++sidx) {
+                        const float4 ps = av.xq[sidx];
+                        const float ex = pt.x - fmaf(r, ps.x, offx), ey = pt.y - fmaf(r, ps.y, offy),
+                                    ez = pt.z - fmaf(r, ps.z, offz);
+                        const float r2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
+                        if (r2 > 0.f) {
+                            const float ir = dafmm_rsqrt(r2);
+                            const float qr = ps.w * ir;
+                            const float qr3 = qr * ir * ir;
+                            sp += qr;
+                            sx = fmaf(qr3, ex, sx); sy = fmaf(qr3, ey, sy); sz = fmaf(qr3, ez, sz);
+                        }
+                    }
+                    two_sum_add(ph, pl, sp);
+                    two_sum_add(xh, xl, sx);
+                    two_sum_add(yh, yl, sy);
+                    two_sum_add(zh, zl, sz);
+                }
+            }
+            fphi = ((double)ph + (double)pl) * ih;
+            fx = ((double)xh + (double)xl) * ih * ih;
+            fy = ((double)yh + (double)yl) * ih * ih;
+            fz = ((double)zh + (double)zl) * ih * ih;
+        }
+        // M2P from the W list (Sec. 3.2): phi = F/h_w, E = -grad_s F / h_w^2
+        for (int wi = w0; wi < w1; ++wi) {
+            const int wb = av.w_idx[wi];
+            double wx, wy, wz, wh;
+            abox_geom(av, wb, wx, wy, wz, wh);
+            const double iwh = 1.0 / wh;
+            T F, g0, g1, g2;
+            gen::GEN(m2p)<T>(RowLoad<T>{M + (size_t)wb * NCP}, (T)((av.x[tt] - wx) * iwh), (T)((av.y[tt] - wy) * iwh),
+                             (T)((av.z[tt] - wz) * iwh), F, g0, g1, g2);
+            fphi += (double)F * iwh;
+            fx -= (double)g0 * iwh * iwh;
+            fy -= (double)g1 * iwh * iwh;
+            fz -= (double)g2 * iwh * iwh;
+        }
+        // L2P of this leaf's local expansion
+        if (lev >= 2) {
+            T F, g0, g1, g2;
+            T xs, ys, zs;
+            if constexpr (sizeof(T) == 8) {
+                xs = (T)((av.x[tt] - cx) * ih);
+                ys = (T)((av.y[tt] - cy) * ih);
+                zs = (T)((av.z[tt] - cz) * ih);
+            } else {
+                const float4 pt = av.xq[tt];
+                xs = (T)pt.x; ys = (T)pt.y; zs = (T)pt.z;
+            }
+            gen::GEN(l2p)<T>(RowLoad<T>{L + (size_t)b * NCP}, xs, ys, zs, F, g0, g1, g2);
+            fphi += (double)F;
+            fx -= (double)g0 * ih;
+            fy -= (double)g1 * ih;
+            fz -= (double)g2 * ih;
+        }
+        if (valid) {
+            const int o = av.perm[t];
+            if (phi) phi[o] = fphi;
+            if (field) {
+                field[3 * (size_t)o] = fx;
+                field[3 * (size_t)o + 1] = fy;
+                field[3 * (size_t)o + 2] = fz;
+            }
+        }
+    }
+}
+
 // ---- single-operator batches ------------------------------------------------------------------
 template <class T>
 struct RowStore {
@@ -632,6 +1026,107 @@ static cudaError_t kgen_launch(OrderData& od, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+// ---- adaptive launchers ----
+static cudaError_t p2m_a_launch(const AdaptiveView& av, const int* leaves, int nleaves, int prec, double* M,
+                                cudaStream_t s) {
+    if (nleaves == 0) return cudaSuccess;
+    const bool f64 = prec == DAFMM_FP64;
+    const size_t per_warp = (size_t)NC * 33 * (f64 ? 8 : 4);
+    int wpb = (int)((96 * 1024) / per_warp);
+    wpb = wpb < 1 ? 1 : (wpb > 4 ? 4 : wpb);
+    const size_t smem = per_warp * wpb;
+    dim3 blk(32, wpb), grd((nleaves + wpb - 1) / wpb);
+    cudaError_t e;
+    if (f64) {
+        if ((e = set_smem(k_p2m_a<double>, smem)) != cudaSuccess) return e;
+        k_p2m_a<double><<<grd, blk, smem, s>>>(av, leaves, nleaves, M);
+    } else {
+        if ((e = set_smem(k_p2m_a<float>, smem)) != cudaSuccess) return e;
+        k_p2m_a<float><<<grd, blk, smem, s>>>(av, leaves, nleaves, M);
+    }
+    return cudaGetLastError();
+}
+
+static cudaError_t m2m_a_launch(const OrderData& od, const AdaptiveView& av, int prec, int lb, int le, double* M,
+                                cudaStream_t s) {
+    if (le <= lb) return cudaSuccess;
+    const bool f32 = prec == DAFMM_FP32;
+    const size_t smem = (size_t)32 * (NCP + 1) * (f32 ? 4 : 8);
+    dim3 grd((le - lb + 31) / 32);
+    cudaError_t e;
+    if (!f32) {
+        if ((e = set_smem(k_m2m_a<double>, smem)) != cudaSuccess) return e;
+        k_m2m_a<double><<<grd, 256, smem, s>>>(od.m2m(), av, lb, le, M);
+    } else {
+        if ((e = set_smem(k_m2m_a<float>, smem)) != cudaSuccess) return e;
+        k_m2m_a<float><<<grd, 256, smem, s>>>(od.m2m(), av, lb, le, M);
+    }
+    return cudaGetLastError();
+}
+
+static cudaError_t m2l_a_launch(const OrderData& od, const AdaptiveView& av, int prec, const int* tg,
+                                const int* grp_ptr, int grp0, int max_group, const double* M, const float* Mf,
+                                double* L, double inv_h, cudaStream_t s) {
+    if (max_group == 0) return cudaSuccess;
+    dim3 grd((max_group + 31) / 32, 8);
+    cudaError_t e;
+    if (prec == DAFMM_FP64) {
+        const size_t smem = (size_t)32 * (NCP + 1) * 8;
+        if ((e = set_smem(k_m2l_a<double, double>, smem)) != cudaSuccess) return e;
+        k_m2l_a<double, double><<<grd, 256, smem, s>>>(od.K64, av, tg, grp_ptr, grp0, M, L, inv_h);
+    } else {
+        const size_t smem = (size_t)32 * (NCP + 1) * 4;
+        if ((e = set_smem(k_m2l_a<float, float>, smem)) != cudaSuccess) return e;
+        k_m2l_a<float, float><<<grd, 256, smem, s>>>(od.K32, av, tg, grp_ptr, grp0, Mf, L, inv_h);
+    }
+    return cudaGetLastError();
+}
+
+static cudaError_t p2l_a_launch(const AdaptiveView& av, int prec, int lb, int le, double* L, cudaStream_t s) {
+    if (le <= lb) return cudaSuccess;
+    const bool f64 = prec == DAFMM_FP64;
+    const size_t per_warp = (size_t)NC * 33 * (f64 ? 8 : 4);
+    int wpb = (int)((96 * 1024) / per_warp);
+    wpb = wpb < 1 ? 1 : (wpb > 4 ? 4 : wpb);
+    const size_t smem = per_warp * wpb;
+    dim3 blk(32, wpb), grd((le - lb + wpb - 1) / wpb);
+    cudaError_t e;
+    if (f64) {
+        if ((e = set_smem(k_p2l_a<double>, smem)) != cudaSuccess) return e;
+        k_p2l_a<double><<<grd, blk, smem, s>>>(av, lb, le, L);
+    } else {
+        if ((e = set_smem(k_p2l_a<float>, smem)) != cudaSuccess) return e;
+        k_p2l_a<float><<<grd, blk, smem, s>>>(av, lb, le, L);
+    }
+    return cudaGetLastError();
+}
+
+static cudaError_t l2l_a_launch(const OrderData& od, const AdaptiveView& av, int prec, int lb, int le, double* L,
+                                cudaStream_t s) {
+    if (le <= lb) return cudaSuccess;
+    const bool f32 = prec == DAFMM_FP32;
+    const size_t smem = (size_t)32 * (NCP + 1) * (f32 ? 4 : 8);
+    dim3 grd((le - lb + 31) / 32);
+    cudaError_t e;
+    if (!f32) {
+        if ((e = set_smem(k_l2l_a<double>, smem)) != cudaSuccess) return e;
+        k_l2l_a<double><<<grd, 256, smem, s>>>(od.l2l(), av, lb, le, L);
+    } else {
+        if ((e = set_smem(k_l2l_a<float>, smem)) != cudaSuccess) return e;
+        k_l2l_a<float><<<grd, 256, smem, s>>>(od.l2l(), av, lb, le, L);
+    }
+    return cudaGetLastError();
+}
+
+static cudaError_t leaf_a_launch(const AdaptiveView& av, const int* leaves, int nleaves, int prec, const double* L,
+                                 const double* M, double* phi, double* field, cudaStream_t s) {
+    if (nleaves == 0) return cudaSuccess;
+    dim3 blk(32, 4), grd((nleaves + 3) / 4);
+    if (prec == DAFMM_FP64) k_leaf_a<double><<<grd, blk, 0, s>>>(av, leaves, nleaves, L, M, phi, field);
+    else k_leaf_a<float><<<grd, blk, 0, s>>>(av, leaves, nleaves, L, M, phi, field);
+    return cudaGetLastError();
+}
+
 static unsigned nblk(int64_t n) { return (unsigned)((n + 127) / 128); }
 
 static cudaError_t op_p2m(int prec, int64_t n, const double* sv, const double* q, double* out, cudaStream_t s) {
@@ -678,7 +1173,8 @@ const OrderOps* DAFMM_CAT(order_ops_p, DAFMM_P)() {
         HostShiftTable{gen::GENT(l2l, _nnz), gen::GENT(l2l, _rowptr), gen::GENT(l2l, _col), gen::GENT(l2l, _par),
                        gen::GENT(l2l, _val)},
         p2m_launch, m2m_launch, l2l_launch, m2l_launch, leaf_launch, kgen_launch,
-        op_p2m, op_p2l, op_l2p, op_m2p, op_shift};
+        op_p2m, op_p2l, op_l2p, op_m2p, op_shift,
+        p2m_a_launch, m2m_a_launch, m2l_a_launch, p2l_a_launch, l2l_a_launch, leaf_a_launch};
     return &ops;
 }
 

@@ -46,6 +46,8 @@ struct MulTab {                   // DA product table for the K generation
     const short* minus;           // [3][nc]: index of e_k - e_v, or -1
 };
 
+struct AdaptiveView;
+
 // ---- per-order operator tables and launchers ------------------------------------------
 struct OrderData {
     int p = -1, nc = 0, ncp = 0;
@@ -97,6 +99,15 @@ struct OrderOps {
     cudaError_t (*op_m2p)(int prec, int64_t n, const double* M, const double* s, double* out4, cudaStream_t);
     cudaError_t (*op_shift)(const OrderData&, int which, int prec, int64_t n, const int* oct,
                             const double* in, double* out, cudaStream_t);
+    // adaptive trees
+    cudaError_t (*p2m_a)(const AdaptiveView&, const int* leaves, int nleaves, int prec, double* M, cudaStream_t);
+    cudaError_t (*m2m_a)(const OrderData&, const AdaptiveView&, int prec, int lb, int le, double* M, cudaStream_t);
+    cudaError_t (*m2l_a)(const OrderData&, const AdaptiveView&, int prec, const int* tg, const int* grp_ptr, int grp0,
+                         int max_group, const double* M, const float* Mf, double* L, double inv_h, cudaStream_t);
+    cudaError_t (*p2l_a)(const AdaptiveView&, int prec, int lb, int le, double* L, cudaStream_t);
+    cudaError_t (*l2l_a)(const OrderData&, const AdaptiveView&, int prec, int lb, int le, double* L, cudaStream_t);
+    cudaError_t (*leaf_a)(const AdaptiveView&, const int* leaves, int nleaves, int prec, const double* L,
+                          const double* M, double* phi, double* field, cudaStream_t);
 };
 
 const OrderOps* order_ops(int p);

@@ -93,6 +93,8 @@ extern "C" int dafmm_eval_noalloc(dafmm_tree* t, int order, double* phi, double*
     if (order < 0 || order > kNoAllocMaxOrder)
         return set_err(c, DAFMM_ERR_UNSUPPORTED_ORDER,
                        "dafmm_eval_noalloc: order " + std::to_string(order) + " above its limit of 6");
+    if (t->adaptive)
+        return set_err(c, DAFMM_ERR_UNSUPPORTED, "dafmm_eval_noalloc: uniform trees only");
     if (t->depth > kNoAllocMaxDepth)
         return set_err(c, DAFMM_ERR_INVALID_ARG,
                        "dafmm_eval_noalloc: tree depth " + std::to_string(t->depth) + " above its limit of 4");

@@ -1,0 +1,450 @@
+// tree_adaptive.cu -- adaptive octree on the GPU (Sec. 3.5: a box with more than s particles
+// is subdivided) and its interaction lists (Cheng, Greengard and Rokhlin 1999):
+//   colleagues : same-level adjacent boxes, kept in a 27-slot table indexed by relative
+//                position (slot 13 = the box itself), -1 where no box exists;
+//   V (M2L)    : children of the parent's colleagues that are not adjacent -- looked up on
+//                the fly from the colleague table by the evaluation kernels;
+//   U (P2P)    : for a leaf, every leaf adjacent to it, and itself;
+//   W (M2P)    : for a leaf b, descendants of its colleagues that are not adjacent to b but
+//                whose parent is;
+//   X (P2L)    : for a box b, the leaves c coarser than b that are adjacent to parent(b) and
+//                not adjacent to b (exactly the boxes whose W list holds b).
+// Particles are sorted by 63-bit Morton keys of their 21-bit integer coordinates, so every
+// box is a contiguous particle range.
+#include <cuda_runtime.h>
+
+#include "internal.h"
+#include "tree_adaptive.h"
+
+namespace dafmm {
+
+__device__ inline int quantize_a(double x, double x0, double scale) {
+    double f = floor(__dmul_rn(__dsub_rn(x, x0), scale));
+    const double top = (double)((1 << kQBits) - 1);
+    if (!(f >= 0.0)) return 0;
+    if (f > top) return (1 << kQBits) - 1;
+    return (int)f;
+}
+
+__device__ inline uint64_t spread3(uint32_t v) {
+    uint64_t x = v & 0x1fffffu;
+    x = (x | x << 32) & 0x1f00000000ffffull;
+    x = (x | x << 16) & 0x1f0000ff0000ffull;
+    x = (x | x << 8) & 0x100f00f00f00f00full;
+    x = (x | x << 4) & 0x10c30c30c30c30c3ull;
+    x = (x | x << 2) & 0x1249249249249249ull;
+    return x;
+}
+
+__global__ void k_morton_keys(const double* __restrict__ xyz, int64_t n, double x0, double y0, double z0,
+                              double scale, uint64_t* keys, int* vals) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint32_t a = quantize_a(xyz[3 * i], x0, scale);
+    const uint32_t b = quantize_a(xyz[3 * i + 1], y0, scale);
+    const uint32_t c = quantize_a(xyz[3 * i + 2], z0, scale);
+    keys[i] = spread3(a) | (spread3(b) << 1) | (spread3(c) << 2);
+    vals[i] = (int)i;
+}
+
+cudaError_t launch_morton_keys(const double* xyz, int64_t n, double x0, double y0, double z0, double scale,
+                               uint64_t* keys, int* vals, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    k_morton_keys<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(xyz, n, x0, y0, z0, scale, keys, vals);
+    return cudaGetLastError();
+}
+
+// first sorted position in [b, e) whose level-(l+1) digit is >= c
+__device__ inline int first_digit_ge(const uint64_t* keys, int b, int e, int shift, int c) {
+    while (b < e) {
+        const int m = (b + e) >> 1;
+        if ((int)((keys[m] >> shift) & 7u) < c) b = m + 1;
+        else e = m;
+    }
+    return b;
+}
+
+// per box of level l: number of non-empty children when it splits
+__global__ void k_split_count(AdaptiveBuild ab, int lb, int le, int level, int max_leaf, int max_depth, int* nch) {
+    const int b = lb + blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= le) return;
+    const int pb = ab.pbeg[b], pe = ab.pend[b];
+    int cnt = 0;
+    if (pe - pb > max_leaf && level < max_depth) {
+        const int shift = 3 * (kQBits - level - 1);
+        int s = pb;
+        for (int c = 0; c < 8; ++c) {
+            const int e = first_digit_ge(ab.keys, s, pe, shift, c + 1);
+            cnt += e > s;
+            s = e;
+        }
+    }
+    nch[b - lb] = cnt;
+}
+
+__global__ void k_split_fill(AdaptiveBuild ab, int lb, int le, int level, const int* offs, int first_new) {
+    const int b = lb + blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= le) return;
+    for (int c = 0; c < 8; ++c) ab.child[8 * b + c] = -1;
+    const int k0 = offs[b - lb], k1 = offs[b - lb + 1];
+    if (k0 == k1) return;
+    const int pb = ab.pbeg[b], pe = ab.pend[b];
+    const int shift = 3 * (kQBits - level - 1);
+    int s = pb, k = first_new + k0;
+    for (int c = 0; c < 8; ++c) {
+        const int e = first_digit_ge(ab.keys, s, pe, shift, c + 1);
+        if (e > s) {
+            ab.level[k] = level + 1;
+            ab.ijk[3 * k] = 2 * ab.ijk[3 * b] + (c & 1);
+            ab.ijk[3 * k + 1] = 2 * ab.ijk[3 * b + 1] + ((c >> 1) & 1);
+            ab.ijk[3 * k + 2] = 2 * ab.ijk[3 * b + 2] + ((c >> 2) & 1);
+            ab.parent[k] = b;
+            ab.pbeg[k] = s;
+            ab.pend[k] = e;
+            ab.child[8 * b + c] = k;
+            ++k;
+        }
+        s = e;
+    }
+}
+
+__global__ void k_leaf_children_init(int* child, int b0, int b1) {
+    const int b = b0 + blockIdx.x * blockDim.x + threadIdx.x;
+    if (b < b1)
+        for (int c = 0; c < 8; ++c) child[8 * b + c] = -1;
+}
+
+cudaError_t launch_split(AdaptiveBuild ab, int lb, int le, int level, int max_leaf, int max_depth, int* nch,
+                         cudaStream_t s) {
+    const int n = le - lb;
+    if (n == 0) return cudaSuccess;
+    k_split_count<<<(n + 127) / 128, 128, 0, s>>>(ab, lb, le, level, max_leaf, max_depth, nch);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_split_fill(AdaptiveBuild ab, int lb, int le, int level, const int* offs, int first_new,
+                              cudaStream_t s) {
+    const int n = le - lb;
+    if (n == 0) return cudaSuccess;
+    k_split_fill<<<(n + 127) / 128, 128, 0, s>>>(ab, lb, le, level, offs, first_new);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_children_init(int* child, int b0, int b1, cudaStream_t s) {
+    if (b1 <= b0) return cudaSuccess;
+    k_leaf_children_init<<<(b1 - b0 + 127) / 128, 128, 0, s>>>(child, b0, b1);
+    return cudaGetLastError();
+}
+
+// exclusive scan of n ints by one block (n up to a few million; used at build time only)
+__global__ void __launch_bounds__(1024) k_scan_excl(const int* in, int* out, int n) {
+    __shared__ int sums[1024];
+    const int t = threadIdx.x;
+    const int chunk = (n + 1023) / 1024;
+    const int b = t * chunk, e = min(b + chunk, n);
+    int s = 0;
+    for (int i = b; i < e; ++i) s += in[i];
+    sums[t] = s;
+    __syncthreads();
+    for (int off = 1; off < 1024; off <<= 1) {
+        int v = t >= off ? sums[t - off] : 0;
+        __syncthreads();
+        sums[t] += v;
+        __syncthreads();
+    }
+    int run = t ? sums[t - 1] : 0;
+    for (int i = b; i < e; ++i) {
+        const int v = in[i];
+        out[i] = run;
+        run += v;
+    }
+    if (t == 1023) out[n] = sums[1023];
+}
+
+cudaError_t launch_scan(const int* in, int* out, int n, cudaStream_t s) {
+    k_scan_excl<<<1, 1024, 0, s>>>(in, out, n);
+    return cudaGetLastError();
+}
+
+// ---- colleagues ---------------------------------------------------------------------------
+__device__ inline bool same_level_adjacent(const int* ijk, int a, int b) {
+    for (int d = 0; d < 3; ++d) {
+        const int df = ijk[3 * a + d] - ijk[3 * b + d];
+        if (df < -1 || df > 1) return false;
+    }
+    return true;
+}
+
+// closed cubes of two boxes (any levels) intersect
+__device__ inline bool touch(const AdaptiveBuild& ab, int a, int b) {
+    const int la = ab.level[a], lb = ab.level[b];
+    const int L = la > lb ? la : lb;
+    for (int d = 0; d < 3; ++d) {
+        const int64_t alo = (int64_t)ab.ijk[3 * a + d] << (L - la), ahi = (int64_t)(ab.ijk[3 * a + d] + 1) << (L - la);
+        const int64_t blo = (int64_t)ab.ijk[3 * b + d] << (L - lb), bhi = (int64_t)(ab.ijk[3 * b + d] + 1) << (L - lb);
+        if (alo > bhi || blo > ahi) return false;
+    }
+    return true;
+}
+
+__global__ void k_colleagues(AdaptiveBuild ab, int lb, int le) {
+    const int b = lb + blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= le) return;
+    int* col = ab.colleague + 27 * b;
+    for (int k = 0; k < 27; ++k) col[k] = -1;
+    col[13] = b;
+    const int P = ab.parent[b];
+    if (P < 0) return;
+    const int* pc = ab.colleague + 27 * P;
+    for (int k = 0; k < 27; ++k) {
+        const int Q = pc[k];
+        if (Q < 0) continue;
+        for (int c = 0; c < 8; ++c) {
+            const int ch = ab.child[8 * Q + c];
+            if (ch < 0 || ch == b) continue;
+            if (!same_level_adjacent(ab.ijk, ch, b)) continue;
+            const int dx = ab.ijk[3 * ch] - ab.ijk[3 * b], dy = ab.ijk[3 * ch + 1] - ab.ijk[3 * b + 1],
+                      dz = ab.ijk[3 * ch + 2] - ab.ijk[3 * b + 2];
+            col[(dx + 1) * 9 + (dy + 1) * 3 + (dz + 1)] = ch;
+        }
+    }
+}
+
+cudaError_t launch_colleagues(AdaptiveBuild ab, int lb, int le, cudaStream_t s) {
+    if (le <= lb) return cudaSuccess;
+    k_colleagues<<<(le - lb + 127) / 128, 128, 0, s>>>(ab, lb, le);
+    return cudaGetLastError();
+}
+
+// ---- U, W (leaves) and X (all boxes) lists: count pass, then fill pass --------------------
+constexpr int kStack = 256;
+
+// U and W of leaf b: traverse the descendants of b's non-leaf colleagues; plus the same-level
+// colleague leaves, plus coarser adjacent leaves (leaf colleagues of b's ancestors)
+template <bool FILL>
+__device__ void uw_lists(const AdaptiveBuild& ab, int b, int* nu, int* nw, int* ou, int* ow, int* err) {
+    int cu = 0, cw = 0;
+    if (FILL) ou[cu] = b;
+    ++cu;
+    const int* col = ab.colleague + 27 * b;
+    int stack[kStack];
+    for (int k = 0; k < 27; ++k) {
+        const int c = col[k];
+        if (c < 0 || c == b) continue;
+        if (ab.child[8 * c] < 0 && ab.child[8 * c + 1] < 0 && ab.child[8 * c + 2] < 0 && ab.child[8 * c + 3] < 0 &&
+            ab.child[8 * c + 4] < 0 && ab.child[8 * c + 5] < 0 && ab.child[8 * c + 6] < 0 && ab.child[8 * c + 7] < 0) {
+            if (FILL) ou[cu] = c;
+            ++cu;
+            continue;
+        }
+        int sp = 0;
+        for (int j = 0; j < 8; ++j)
+            if (ab.child[8 * c + j] >= 0) stack[sp++] = ab.child[8 * c + j];
+        while (sp > 0) {
+            const int x = stack[--sp];
+            if (touch(ab, x, b)) {
+                bool leaf = true;
+                for (int j = 0; j < 8; ++j)
+                    if (ab.child[8 * x + j] >= 0) {
+                        leaf = false;
+                        if (sp < kStack) stack[sp++] = ab.child[8 * x + j];
+                        else atomicExch(err, 41);
+                    }
+                if (leaf) {
+                    if (FILL) ou[cu] = x;
+                    ++cu;
+                }
+            } else {
+                if (FILL) ow[cw] = x;
+                ++cw;
+            }
+        }
+    }
+    // coarser adjacent leaves
+    for (int a = ab.parent[b]; a >= 0; a = ab.parent[a]) {
+        const int* ac = ab.colleague + 27 * a;
+        for (int k = 0; k < 27; ++k) {
+            const int c = ac[k];
+            if (c < 0 || c == a) continue;
+            bool leaf = true;
+            for (int j = 0; j < 8; ++j) leaf = leaf && ab.child[8 * c + j] < 0;
+            if (leaf && touch(ab, c, b)) {
+                if (FILL) ou[cu] = c;
+                ++cu;
+            }
+        }
+    }
+    *nu = cu;
+    *nw = cw;
+}
+
+// X of box b: leaf colleagues c of b's ancestors (parent and up) adjacent to parent(b), not to b
+template <bool FILL>
+__device__ int x_list(const AdaptiveBuild& ab, int b, int* ox) {
+    const int P = ab.parent[b];
+    if (P < 0) return 0;
+    int cx = 0;
+    for (int a = P; a >= 0; a = ab.parent[a]) {
+        const int* ac = ab.colleague + 27 * a;
+        for (int k = 0; k < 27; ++k) {
+            const int c = ac[k];
+            if (c < 0 || c == a) continue;
+            bool leaf = true;
+            for (int j = 0; j < 8; ++j) leaf = leaf && ab.child[8 * c + j] < 0;
+            if (!leaf) continue;
+            if (touch(ab, c, P) && !touch(ab, c, b)) {
+                if (FILL) ox[cx] = c;
+                ++cx;
+            }
+        }
+    }
+    return cx;
+}
+
+// V of box b (counted only): children of the parent's colleagues that are not adjacent to b
+__device__ int v_count(const AdaptiveBuild& ab, int b) {
+    const int P = ab.parent[b];
+    if (P < 0) return 0;
+    int cv = 0;
+    for (int k = 0; k < 27; ++k) {
+        const int Q = ab.colleague[27 * P + k];
+        if (Q < 0 || Q == P) continue;
+        for (int c = 0; c < 8; ++c) {
+            const int ch = ab.child[8 * Q + c];
+            if (ch >= 0 && !same_level_adjacent(ab.ijk, ch, b)) ++cv;
+        }
+    }
+    return cv;
+}
+
+__global__ void k_list_count(AdaptiveBuild ab, int nbox, int* cu, int* cw, int* cx, unsigned long long* nv,
+                             int* err) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nbox) return;
+    bool leaf = true;
+    for (int j = 0; j < 8; ++j) leaf = leaf && ab.child[8 * b + j] < 0;
+    int nu = 0, nw = 0;
+    if (leaf) uw_lists<false>(ab, b, &nu, &nw, nullptr, nullptr, err);
+    cu[b] = nu;
+    cw[b] = nw;
+    cx[b] = x_list<false>(ab, b, nullptr);
+    const int v = v_count(ab, b);
+    if (v) atomicAdd(nv, (unsigned long long)v);
+}
+
+__global__ void k_list_fill(AdaptiveBuild ab, int nbox, const int* pu, const int* pw, const int* px, int* iu, int* iw,
+                            int* ix, int* err) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nbox) return;
+    bool leaf = true;
+    for (int j = 0; j < 8; ++j) leaf = leaf && ab.child[8 * b + j] < 0;
+    int nu, nw;
+    if (leaf) uw_lists<true>(ab, b, &nu, &nw, iu + pu[b], iw + pw[b], err);
+    x_list<true>(ab, b, ix + px[b]);
+}
+
+cudaError_t launch_list_count(AdaptiveBuild ab, int nbox, int* cu, int* cw, int* cx, unsigned long long* nv, int* err,
+                              cudaStream_t s) {
+    if (nbox == 0) return cudaSuccess;
+    k_list_count<<<(nbox + 127) / 128, 128, 0, s>>>(ab, nbox, cu, cw, cx, nv, err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_list_fill(AdaptiveBuild ab, int nbox, const int* pu, const int* pw, const int* px, int* iu, int* iw,
+                             int* ix, int* err, cudaStream_t s) {
+    if (nbox == 0) return cudaSuccess;
+    k_list_fill<<<(nbox + 127) / 128, 128, 0, s>>>(ab, nbox, pu, pw, px, iu, iw, ix, err);
+    return cudaGetLastError();
+}
+
+// ---- gather of the sorted particles: FP64 SoA and FP32 offsets in each particle's own leaf ----
+__global__ void k_gather_adaptive(const double* __restrict__ xyz, const double* __restrict__ q,
+                                  const int* __restrict__ perm, AdaptiveBuild ab, const int* __restrict__ leaves,
+                                  int nleaves, double x0, double y0, double z0, double size, double* x, double* y,
+                                  double* z, double* qs, float4* xq) {
+    const int li = blockIdx.x;
+    if (li >= nleaves) return;
+    const int b = leaves[li];
+    const int lev = ab.level[b];
+    const double h = ldexp(size, -lev), ih = 1.0 / h;
+    const double cx = x0 + ((double)ab.ijk[3 * b] + 0.5) * h;
+    const double cy = y0 + ((double)ab.ijk[3 * b + 1] + 0.5) * h;
+    const double cz = z0 + ((double)ab.ijk[3 * b + 2] + 0.5) * h;
+    for (int t = ab.pbeg[b] + threadIdx.x; t < ab.pend[b]; t += blockDim.x) {
+        const int i = perm[t];
+        const double px = xyz[3 * i], py = xyz[3 * i + 1], pz = xyz[3 * i + 2], pq = q[i];
+        x[t] = px; y[t] = py; z[t] = pz; qs[t] = pq;
+        xq[t] = make_float4((float)((px - cx) * ih), (float)((py - cy) * ih), (float)((pz - cz) * ih), (float)pq);
+    }
+}
+
+cudaError_t launch_gather_adaptive(const double* xyz, const double* q, const int* perm, AdaptiveBuild ab,
+                                   const int* leaves, int nleaves, const double* dom, double* x, double* y, double* z,
+                                   double* qs, float4* xq, cudaStream_t s) {
+    if (nleaves == 0) return cudaSuccess;
+    k_gather_adaptive<<<nleaves, 128, 0, s>>>(xyz, q, perm, ab, leaves, nleaves, dom[0], dom[1], dom[2], dom[3], x, y,
+                                               z, qs, xq);
+    return cudaGetLastError();
+}
+
+// ---- leaves and M2L target groups --------------------------------------------------------------
+__global__ void k_leaf_flags(const int* __restrict__ child, int nbox, int* flags) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nbox) return;
+    bool leaf = true;
+    for (int j = 0; j < 8; ++j) leaf = leaf && child[8 * b + j] < 0;
+    flags[b] = leaf ? 1 : 0;
+}
+
+__global__ void k_scatter_flagged(const int* __restrict__ flags, const int* __restrict__ offs, int nbox, int* out) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b < nbox && flags[b]) out[offs[b]] = b;
+}
+
+// group key (level, octant) of the boxes of levels >= 2; other boxes sort last
+__global__ void k_group_keys(const int* __restrict__ level, const int* __restrict__ ijk, int nbox, uint64_t* keys,
+                             int* vals) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nbox) return;
+    const int l = level[b];
+    const int oct = (ijk[3 * b] & 1) | ((ijk[3 * b + 1] & 1) << 1) | ((ijk[3 * b + 2] & 1) << 2);
+    keys[b] = l >= 2 ? (uint64_t)(l * 8 + oct) : 0xffu;
+    vals[b] = b;
+}
+
+__global__ void k_group_ptr(const uint64_t* __restrict__ keys, int n, int ngroups, int* ptr) {
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g > ngroups) return;
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        const int m = (lo + hi) >> 1;
+        if (keys[m] < (uint64_t)g) lo = m + 1;
+        else hi = m;
+    }
+    ptr[g] = lo;
+}
+
+cudaError_t launch_leaf_flags(const int* child, int nbox, int* flags, cudaStream_t s) {
+    if (nbox == 0) return cudaSuccess;
+    k_leaf_flags<<<(nbox + 255) / 256, 256, 0, s>>>(child, nbox, flags);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scatter_flagged(const int* flags, const int* offs, int nbox, int* out, cudaStream_t s) {
+    if (nbox == 0) return cudaSuccess;
+    k_scatter_flagged<<<(nbox + 255) / 256, 256, 0, s>>>(flags, offs, nbox, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_group_keys(const int* level, const int* ijk, int nbox, uint64_t* keys, int* vals, cudaStream_t s) {
+    if (nbox == 0) return cudaSuccess;
+    k_group_keys<<<(nbox + 255) / 256, 256, 0, s>>>(level, ijk, nbox, keys, vals);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_group_ptr(const uint64_t* keys, int n, int ngroups, int* ptr, cudaStream_t s) {
+    k_group_ptr<<<(ngroups + 1 + 255) / 256, 256, 0, s>>>(keys, n, ngroups, ptr);
+    return cudaGetLastError();
+}
+
+}  // namespace dafmm

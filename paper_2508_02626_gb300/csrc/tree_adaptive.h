@@ -1,0 +1,67 @@
+// tree_adaptive.h -- device arrays of an adaptive octree and the build launchers
+// (tree_adaptive.cu).  Boxes are numbered breadth-first, so each level is a contiguous
+// index range; every box is a contiguous range of the Morton-sorted particles.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace dafmm {
+
+constexpr int kMaxAdaptiveDepth = 20;
+
+struct AdaptiveBuild {
+    const uint64_t* keys;  // sorted Morton keys of the particles
+    int* level;            // per box
+    int* ijk;              // per box, 3 integer coordinates at its level
+    int* parent;           // -1 for the root
+    int* child;            // per box, 8 slots (octant c = x | y<<1 | z<<2), -1 when absent
+    int* pbeg;             // particle range [pbeg, pend) in sorted order
+    int* pend;
+    int* colleague;        // per box, 27 slots by relative position, slot 13 = the box
+};
+
+// what the evaluation kernels read (const view)
+struct AdaptiveView {
+    int nbox;
+    const int* level;
+    const int* ijk;
+    const int* parent;
+    const int* child;
+    const int* pbeg;
+    const int* pend;
+    const int* colleague;
+    const int* u_ptr;      // CSR per box (empty for non-leaves)
+    const int* u_idx;
+    const int* w_ptr;
+    const int* w_idx;
+    const int* x_ptr;      // CSR per box
+    const int* x_idx;
+    double x0, y0, z0, size;
+    const double *x, *y, *z, *q;  // sorted particles
+    const float4* xq;             // offsets in the particle's own leaf, in leaf widths, and q
+    const int* perm;
+};
+
+cudaError_t launch_morton_keys(const double* xyz, int64_t n, double x0, double y0, double z0, double scale,
+                               uint64_t* keys, int* vals, cudaStream_t s);
+cudaError_t launch_split(AdaptiveBuild ab, int lb, int le, int level, int max_leaf, int max_depth, int* nch,
+                         cudaStream_t s);
+cudaError_t launch_split_fill(AdaptiveBuild ab, int lb, int le, int level, const int* offs, int first_new,
+                              cudaStream_t s);
+cudaError_t launch_children_init(int* child, int b0, int b1, cudaStream_t s);
+cudaError_t launch_scan(const int* in, int* out, int n, cudaStream_t s);  // out[n] = total
+cudaError_t launch_colleagues(AdaptiveBuild ab, int lb, int le, cudaStream_t s);
+cudaError_t launch_list_count(AdaptiveBuild ab, int nbox, int* cu, int* cw, int* cx, unsigned long long* nv, int* err,
+                              cudaStream_t s);
+cudaError_t launch_list_fill(AdaptiveBuild ab, int nbox, const int* pu, const int* pw, const int* px, int* iu, int* iw,
+                             int* ix, int* err, cudaStream_t s);
+cudaError_t launch_gather_adaptive(const double* xyz, const double* q, const int* perm, AdaptiveBuild ab,
+                                   const int* leaves, int nleaves, const double* dom, double* x, double* y, double* z,
+                                   double* qs, float4* xq, cudaStream_t s);
+
+cudaError_t launch_leaf_flags(const int* child, int nbox, int* flags, cudaStream_t s);
+cudaError_t launch_scatter_flagged(const int* flags, const int* offs, int nbox, int* out, cudaStream_t s);
+cudaError_t launch_group_keys(const int* level, const int* ijk, int nbox, uint64_t* keys, int* vals, cudaStream_t s);
+cudaError_t launch_group_ptr(const uint64_t* keys, int n, int ngroups, int* ptr, cudaStream_t s);
+
+}  // namespace dafmm

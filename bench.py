@@ -261,10 +261,222 @@ def run_ours(args, rank, world):
                 "includes": "dafmm_build_tree + dafmm_eval from pinned host buffers"},
         "modes": modes,
     }
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        out["cpu_baseline"], out["accuracy"] = cpu_baseline(x, q, dom, cfg, phi.cpu().numpy(), E.cpu().numpy())
+    phi_host, E_host = phi.cpu().numpy(), E.cpu().numpy()
     tree.free()
+    if world == 1 and not args.no_workloads:
+        out["adaptive"] = bench_adaptive(ctx, stream, flush)
+        out["batch"] = bench_batch(ctx, stream, flush)
+        out["serving"] = bench_serving(args.serving_requests)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"], out["accuracy"] = cpu_baseline(x, q, dom, cfg, phi_host, E_host)
     ctx.close()
+    return out
+
+
+def timed_evals(tree, p, prec, phi, E, stream, flush, steps):
+    import torch
+    ms = []
+    with torch.cuda.stream(stream):
+        for _ in range(steps):
+            flush.fill_(1.0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            tree.eval(p, phi, E, precision=prec, stream=stream)
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+    return float(np.mean(ms))
+
+
+def bench_adaptive(ctx, stream, flush):
+    """Adaptive octree on clustered data: N = 4e6 in 32 Gaussian clusters, q = +1, s = 64,
+    p = 10; MIXED (the workload's stated precision) and FP32."""
+    import torch
+
+    from paper_2508_02626_gb300 import binding as B
+    from paper_2508_02626_gb300 import workloads as W
+    cfg = W.C3
+    x, q, _ = W.make(cfg)
+    n, p = cfg["n"], cfg["order"]
+    xt, qt = torch.from_numpy(x).cuda(), torch.from_numpy(q).cuda()
+    phi = torch.empty(n, dtype=torch.float64, device="cuda")
+    E = torch.empty((n, 3), dtype=torch.float64, device="cuda")
+    tree = ctx.build_tree(xt, qt, domain=None, uniform_depth=-1, max_leaf=cfg["max_leaf"], stream=stream)
+    stream.synchronize()
+    t0 = time.perf_counter()
+    tr2 = ctx.build_tree(xt, qt, domain=None, uniform_depth=-1, max_leaf=cfg["max_leaf"], stream=stream)
+    stream.synchronize()
+    build_ms = (time.perf_counter() - t0) * 1e3
+    tr2.free()
+    info = tree.info()
+    out = {"workload": "clustered N=4e6 (32 Gaussian clusters, sigma U[0.02,0.1]), q=+1, adaptive s=64, p=10",
+           "tree": {k: info[k] for k in ("depth", "leaves", "boxes", "max_per_leaf", "m2l_pairs", "p2p_leaf_pairs")},
+           "build_ms": build_ms}
+    for mname in ("mixed", "fp32"):
+        mp = B.PRECISIONS[mname]
+        with torch.cuda.stream(stream):
+            tree.eval(p, phi, E, precision=mp, stream=stream)
+        ms = timed_evals(tree, p, mp, phi, E, stream, flush, 3)
+        out[mname] = {"value": n / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
+                      "phases_ms": {k: round(v, 3) for k, v in B.dafmm_last_phase_ms(ctx.h).items()}}
+    tree.free()
+    return out
+
+
+def bench_batch(ctx, stream, flush):
+    """Batched launch: 256 independent problems (N log-uniform in [1e3, 1e5], uniform or
+    clustered by seed, q U[-1,1]), p = 6, FP32, one forest replayed as one CUDA graph, leaf
+    size and near-field tile from the autotuner; against the same problems solved one by one
+    in plain FP64."""
+    import torch
+
+    from paper_2508_02626_gb300 import autotune as A
+    from paper_2508_02626_gb300 import binding as B
+    from paper_2508_02626_gb300 import workloads as W
+    import oracle as O
+    sizes = W.batch_sizes()
+    xs, qs = zip(*[W.batch_member(n, kind, seed) for n, kind, seed in sizes])
+    offs = np.concatenate([[0], np.cumsum([len(v) for v in qs])]).astype(np.int64)
+    x, q = np.concatenate(xs), np.concatenate(qs)
+    n, p = int(offs[-1]), 6
+    xt, qt = torch.from_numpy(x).cuda(), torch.from_numpy(q).cuda()
+    cache = A.Cache(os.path.join(ROOT, "gpurun_out", "autotune.json"))
+    tuned = A.tune_forest(ctx, xt, qt, offs, p, "fp32", cache=cache, reps=1)
+    s = tuned["max_leaf"]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    f = ctx.build_forest(xt, qt, offs, max_leaf=s, stream=stream)
+    stream.synchronize()
+    build_ms = (time.perf_counter() - t0) * 1e3
+    phi = torch.empty(n, dtype=torch.float64, device="cuda")
+    E = torch.empty((n, 3), dtype=torch.float64, device="cuda")
+    g = f.graph(p, phi, E, precision="fp32", stream=stream)
+    ms = []
+    for _ in range(5):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        g.launch(stream)
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    graph_ms = float(np.mean(ms))
+    nodes = g.nodes()
+    phi_b = phi.cpu().numpy()
+    g.free()
+    f.free()
+    # the same problems as plain FP64 single solves, one after another (tree per problem at
+    # the paper's leaf size for p = 6, host buffers in and out)
+    s64 = A.paper_leaf_size(p)
+    ph64 = np.zeros(n)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for r in range(len(sizes)):
+        a, b = offs[r], offs[r + 1]
+        t = ctx.build_tree(xs[r], qs[r], domain=None, uniform_depth=-1, max_leaf=s64)
+        t.eval(p, ph64[a:b], None, precision="fp64")
+        t.free()
+    seq_s = time.perf_counter() - t0
+    # equal accuracy: both against the direct sum on two sampled problems
+    acc = []
+    for r in (3, 100):
+        a, b = offs[r], offs[r + 1]
+        d_phi, _ = O.direct(xs[r], qs[r])
+        rl = lambda u: float(np.sqrt(((u - d_phi) ** 2).sum() / (d_phi ** 2).sum()))
+        acc.append({"problem": r, "n": int(b - a), "batched_fp32": rl(phi_b[a:b]), "single_fp64": rl(ph64[a:b])})
+    return {"workload": "256 problems, N log-uniform [1e3,1e5], uniform/clustered by seed, q U[-1,1], p=6",
+            "particles": n, "autotuned": {"max_leaf": s, "leaf_warps": tuned["leaf_warps"],
+                                          "cached": tuned["cached"]},
+            "build_ms": build_ms, "graph_ms": graph_ms, "graph_nodes": nodes,
+            "solves_per_s": len(sizes) / (graph_ms / 1e3), "value": n / (graph_ms / 1e3),
+            "value_with_build": n / ((graph_ms + build_ms) / 1e3), "unit": UNIT,
+            "sequential_fp64": {"value": n / seq_s, "solves_per_s": len(sizes) / seq_s, "seconds": seq_s,
+                                "max_leaf": s64, "includes": "build_tree + eval per problem, host buffers"},
+            "accuracy_vs_direct": acc}
+
+
+def bench_serving(requests):
+    """Serving loop on the Poisson request stream (N log-uniform in [1e3, 1e6], p in {4, 6, 8},
+    uniform or clustered, FP32): the first `requests` requests of the stream; capacity from
+    a saturated run, then arrivals at 0.5, 0.8 and 1.0 x capacity, p50/p99 latency from
+    submission to results in the caller's page-locked buffers; plain FP64 single solves of a
+    sample of the same requests for comparison."""
+    import torch
+
+    from paper_2508_02626_gb300 import binding as B
+    from paper_2508_02626_gb300 import workloads as W
+    stream_def = W.poisson_stream()[:requests]
+    data = []
+    for r in stream_def:
+        x, q = W.batch_member(r["n"], r["kind"], r["seed"])
+        xp = torch.from_numpy(x).pin_memory()
+        qp = torch.from_numpy(q).pin_memory()
+        out = (torch.empty(len(q), dtype=torch.float64).pin_memory(),
+               torch.empty((len(q), 3), dtype=torch.float64).pin_memory())
+        data.append((xp, qp, out, r["order"]))
+    total_n = int(sum(len(d[1]) for d in data))
+    free, _ = torch.cuda.mem_get_info()
+    pool = int(min(0.5 * free, 48 << 30))
+    srv = B.Server(torch.cuda.current_device(), pool_bytes=pool, slots=4, max_batch=32, max_job_particles=1 << 21)
+
+    def run(arrivals):
+        ids = []
+        t0 = time.perf_counter()
+        for (xp, qp, out, p), ta in zip(data, arrivals):
+            dt = ta - (time.perf_counter() - t0)
+            if dt > 0:
+                time.sleep(dt)
+            ids.append(srv.submit(xp, qp, p, precision="fp32", max_leaf=64, out=out))
+        lat = []
+        for rid in ids:
+            st, _, _, tm = srv.wait(rid, timeout=600.0)
+            if st != B.DAFMM_OK:
+                raise RuntimeError("served request failed: %d %s" % (st, srv.last_error()))
+            lat.append(tm["latency_ms"])
+        span = time.perf_counter() - t0
+        return lat, span
+
+    # warm: the per-order tables of every order in the stream
+    warm = [next(i for i, d in enumerate(data) if d[3] == p) for p in sorted({d[3] for d in data})]
+    for i in warm:
+        st, _, _, _ = srv.wait(srv.submit(data[i][0], data[i][1], data[i][3], precision="fp32", max_leaf=64,
+                                          out=data[i][2]), timeout=600.0)
+    lat, span = run([0.0] * len(data))
+    capacity = len(data) / span
+    out = {"workload": "Poisson stream, first %d requests: N log-uniform [1e3,1e6] (%d particles), p in {4,6,8}, "
+                       "uniform/clustered, q U[-1,1], FP32, s=64" % (len(data), total_n),
+           "slots": 4, "max_batch": 32, "pool_bytes": pool,
+           "saturated": {"solves_per_s": capacity, "particles_per_s": total_n / span,
+                         "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99))},
+           "rates": []}
+    gaps = np.array([r["t"] for r in stream_def])
+    gaps = gaps - gaps[0]
+    for f in (0.5, 0.8, 1.0):
+        arr = gaps / gaps[-1] * (len(data) / (f * capacity)) if gaps[-1] > 0 else gaps
+        lat, span = run(arr)
+        out["rates"].append({"load": f, "offered_solves_per_s": f * capacity, "solves_per_s": len(data) / span,
+                             "particles_per_s": total_n / span, "p50_ms": float(np.percentile(lat, 50)),
+                             "p99_ms": float(np.percentile(lat, 99))})
+    st = srv.stats()
+    out["server"] = {k: st[k] for k in ("jobs", "requests_per_job", "peak_running", "peak_bytes")}
+    srv.close()
+    # plain FP64 single solves, one after another, on a sample of the same requests
+    ctx = B.Context(torch.cuda.current_device())
+    k = min(24, len(data))
+    sample_n = 0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for xp, qp, o, p in data[:k]:
+        t = ctx.build_tree(xp, qp, domain=None, uniform_depth=-1, max_leaf=64)
+        t.eval(p, o[0], o[1], precision="fp64")
+        t.free()
+        sample_n += len(qp)
+    seq_s = time.perf_counter() - t0
+    ctx.close()
+    out["sequential_fp64"] = {"requests": k, "particles_per_s": sample_n / seq_s, "solves_per_s": k / seq_s}
     return out
 
 
@@ -361,6 +573,9 @@ def main():
     ap.add_argument("--no-modes", action="store_true", help="skip the MIXED / FP64 comparison runs")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-workloads", action="store_true",
+                    help="skip the adaptive, batched and serving workloads (N = 1 only)")
+    ap.add_argument("--serving-requests", type=int, default=200)
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))

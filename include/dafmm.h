@@ -45,6 +45,7 @@ extern "C" {
 #define DAFMM_ERR_TIMEOUT (-5)           /* a bounded device wait gave up */
 #define DAFMM_ERR_UNSUPPORTED (-6)       /* a valid but unimplemented option (e.g. theta != 1) */
 #define DAFMM_ERR_NO_DEVICE (-7)
+#define DAFMM_ERR_CANCELLED (-8)         /* a served request dropped because its server stopped */
 
 /* arithmetic of an evaluation */
 #define DAFMM_FP64 0  /* every step in double precision */
@@ -55,10 +56,19 @@ extern "C" {
 
 typedef struct dafmm_ctx dafmm_ctx;
 typedef struct dafmm_tree dafmm_tree;
+typedef struct dafmm_graph dafmm_graph;
+typedef struct dafmm_server dafmm_server;
 
 /* Create a context on CUDA device `device`.  hbm_budget_bytes caps the device memory the
  * context may hold (0 = no cap).  *ctx receives the handle. */
 int dafmm_create(dafmm_ctx** ctx, int device, size_t hbm_budget_bytes);
+/* A pooled context: it reserves pool_bytes (>= 1 MiB) of device memory at once and carves
+ * every later allocation out of that reservation, first fit, 256-byte aligned (the paper
+ * has no counterpart; this serves long-running loops).  Returning memory to the pool never
+ * synchronises the device, unlike cudaFree, so trees can be freed while other streams run;
+ * a tree must not be freed before the work that uses it has completed.  Allocations beyond
+ * the pool fail with DAFMM_ERR_OVER_BUDGET. */
+int dafmm_create_pooled(dafmm_ctx** ctx, int device, size_t pool_bytes);
 /* Release a context and every tree it owns. */
 void dafmm_destroy(dafmm_ctx* ctx);
 /* Message of the last failure on this context (never NULL). */
@@ -83,6 +93,23 @@ size_t dafmm_bytes_in_use(const dafmm_ctx* ctx);
 int dafmm_build_tree(dafmm_ctx* ctx, const double* xyz, const double* q, int64_t n,
                      const double* domain, int uniform_depth, int max_leaf, void* stream,
                      dafmm_tree** tree);
+/* A forest: `ntrees` independent problems in one adaptive structure, so that one evaluation
+ * (a fixed number of kernel launches, independent of ntrees) solves them all.  Particles of
+ * problem r are [offsets[r], offsets[r+1]) of xyz/q (offsets: ntrees + 1 host int64,
+ * offsets[0] = 0, non-decreasing); problem r gets its own root cube -- domains[4r..4r+3] =
+ * {x0, y0, z0, size}, or, with domains NULL, the smallest cube around its points enlarged by
+ * 1e-12 of its size -- and its own adaptive tree with leaves of at most max_leaf particles
+ * (Sec. 3.5).  No interaction crosses problems: each problem's potential and field are those
+ * of a tree built for it alone, computed by the same arithmetic in the same order.  Outputs
+ * of dafmm_eval on a forest are in the concatenated input order.
+ *   Errors: DAFMM_ERR_INVALID_ARG for bad offsets, arrays, max_leaf < 1 or domains;
+ *   DAFMM_ERR_OVER_BUDGET when memory runs out. */
+int dafmm_build_forest(dafmm_ctx* ctx, const double* xyz, const double* q, const int64_t* offsets,
+                       int ntrees, const double* domains, int max_leaf, void* stream,
+                       dafmm_tree** tree);
+/* Number of problems in a forest (1 for a tree) and their root cubes (4 doubles each) when
+ * domains is not NULL. */
+int dafmm_forest_info(const dafmm_tree* tree, int* ntrees, double* domains);
 int dafmm_tree_free(dafmm_tree* tree);
 /* info[0..7] = n, depth (the finest level of an adaptive tree), leaves, boxes, max particles
  * per leaf, adaptive (0/1), M2L pairs (V list entries), P2P leaf pairs (U list entries).
@@ -98,6 +125,51 @@ int dafmm_tree_info(const dafmm_tree* tree, int64_t* info8, double* domain4);
 int dafmm_eval(dafmm_tree* tree, int order, double theta, int precision, double* phi,
                double* field, void* stream);
 
+/* CUDA-graph form of dafmm_eval (the paper has no counterpart; it removes the per-kernel
+ * launch cost of repeated evaluations).  dafmm_graph_create runs one ordinary evaluation
+ * (so that every table and array exists), then records a second one on `stream` (a private
+ * stream when NULL) into a graph.  Launching the graph recomputes phi and field of the same
+ * tree, order and precision into the same device buffers (phi, field: device memory or
+ * NULL).  The graph refers to the tree's arrays: free it before the tree.  dafmm_graph_nodes: kernels and copies in the graph. */
+int dafmm_graph_create(dafmm_tree* tree, int order, int precision, double* phi, double* field,
+                       void* stream, dafmm_graph** graph);
+int dafmm_graph_launch(dafmm_graph* graph, void* stream);
+int dafmm_graph_nodes(const dafmm_graph* graph);
+int dafmm_graph_free(dafmm_graph* graph);
+
+/* ---- serving: a request loop with continuous batching (the paper has no counterpart) ----
+ * dafmm_server_create starts a scheduler thread that owns a pooled context of pool_bytes on
+ * `device` and `slots` CUDA streams.  Requests (one independent problem each) may be
+ * submitted from any thread at any time.  Whenever a slot is free the scheduler forms a job:
+ * the oldest request and, behind it in arrival order, further requests of the same order,
+ * precision and leaf size -- at most max_batch requests and max_job_particles particles,
+ * and only while the job's device-memory estimate (dafmm_footprint) fits the free pool.
+ * A job is one forest (dafmm_build_forest) and one dafmm_eval on the slot's stream; jobs
+ * on different slots overlap on the device.  Each request's result is the one a
+ * stand-alone adaptive solve of it gives (its own tree), bit for bit.
+ *   dafmm_server_submit: xyz (n x 3), q (n), phi (n), field (n x 3, may be NULL) stay owned
+ *     by the caller and must remain valid until dafmm_server_wait returns for that request;
+ *     page-locked host or device memory lets copies overlap (pageable memory works but
+ *     serialises the loop).  *id receives the request's handle.
+ *   dafmm_server_wait: blocks up to timeout_s seconds (< 0: no limit) for the request;
+ *     returns its status (DAFMM_OK, or the error of its job; DAFMM_ERR_OVER_BUDGET when it
+ *     cannot fit the empty pool; DAFMM_ERR_CANCELLED when the server stopped first) and
+ *     forgets it, or DAFMM_ERR_TIMEOUT and keeps it.  times3 (may be NULL) receives, in
+ *     milliseconds: submit to results in the caller's buffers, submit to admission, and
+ *     admission to results.
+ *   dafmm_server_stats: out8 = {completed, failed, queued, running jobs, jobs launched,
+ *     mean requests per job, peak pool bytes in use, peak concurrent jobs}.
+ *   dafmm_server_destroy: lets running jobs finish, cancels queued requests, frees all. */
+int dafmm_server_create(int device, size_t pool_bytes, int slots, int max_batch,
+                        int64_t max_job_particles, dafmm_server** server);
+int dafmm_server_submit(dafmm_server* server, const double* xyz, const double* q, int64_t n,
+                        int order, int precision, int max_leaf, double* phi, double* field,
+                        int64_t* id);
+int dafmm_server_wait(dafmm_server* server, int64_t id, double timeout_s, double* times3);
+int dafmm_server_stats(dafmm_server* server, double* out8);
+const char* dafmm_server_last_error(dafmm_server* server);
+int dafmm_server_destroy(dafmm_server* server);
+
 /* Per-phase device time of the last dafmm_eval on this context, measured with CUDA events
  * recorded on that call's stream while profiling is enabled (dafmm_set_profiling).
  * out10 = {P2M, M2M, M2L (all levels), M2L finest level, L2L, L2P+P2P, conversions,
@@ -112,6 +184,9 @@ int dafmm_last_phase_ms(dafmm_ctx* ctx, double* out10);
 /*   DAFMM_OPT_TC_MASK: which contractions may use the tensor cores in the FP32 mode
  *   (bit 0 M2L, bit 1 M2M, bit 2 L2L; default 7); the others run on the SIMT kernels. */
 #define DAFMM_OPT_TC_MASK 2
+/*   DAFMM_OPT_LEAF_WARPS: leaves per thread block of the adaptive near-field kernel (P2P,
+ *   M2P, L2P), one warp each: 1, 2, 4 (default) or 8 -- the P2P tile the autotuner picks. */
+#define DAFMM_OPT_LEAF_WARPS 3
 int dafmm_set_option(dafmm_ctx* ctx, int option, int64_t value);
 
 /* Diagnostics: copy level `level` of an internal expansion array of the last evaluation

@@ -20,6 +20,7 @@ DAFMM_ERR_CUDA = -4
 DAFMM_ERR_TIMEOUT = -5
 DAFMM_ERR_UNSUPPORTED = -6
 DAFMM_ERR_NO_DEVICE = -7
+DAFMM_ERR_CANCELLED = -8
 
 DAFMM_FP64 = 0
 DAFMM_MIXED = 1
@@ -52,6 +53,19 @@ SIGNATURES = {
     "dafmm_op_m2m": (_i, [_vp, _i, _i, _i64, _vp, _vp, _vp, _vp]),
     "dafmm_op_l2l": (_i, [_vp, _i, _i, _i64, _vp, _vp, _vp, _vp]),
     "dafmm_op_m2l_matrix": (_i, [_vp, _i, _vp, _vp, _vp]),
+    "dafmm_create_pooled": (_i, [ctypes.POINTER(_vp), _i, _sz]),
+    "dafmm_build_forest": (_i, [_vp, _vp, _vp, _vp, _i, _vp, _i, _vp, ctypes.POINTER(_vp)]),
+    "dafmm_forest_info": (_i, [_vp, _vp, _vp]),
+    "dafmm_graph_create": (_i, [_vp, _i, _i, _vp, _vp, _vp, ctypes.POINTER(_vp)]),
+    "dafmm_graph_launch": (_i, [_vp, _vp]),
+    "dafmm_graph_nodes": (_i, [_vp]),
+    "dafmm_graph_free": (_i, [_vp]),
+    "dafmm_server_create": (_i, [_i, _sz, _i, _i, _i64, ctypes.POINTER(_vp)]),
+    "dafmm_server_submit": (_i, [_vp, _vp, _vp, _i64, _i, _i, _i, _vp, _vp, ctypes.POINTER(_i64)]),
+    "dafmm_server_wait": (_i, [_vp, _i64, _d, _vp]),
+    "dafmm_server_stats": (_i, [_vp, _vp]),
+    "dafmm_server_last_error": (ctypes.c_char_p, [_vp]),
+    "dafmm_server_destroy": (_i, [_vp]),
 }
 
 _lib = None
@@ -125,6 +139,14 @@ def dafmm_create(device=0, hbm_budget_bytes=0):
     return h.value
 
 
+def dafmm_create_pooled(device, pool_bytes):
+    h = _vp()
+    rc = load().dafmm_create_pooled(ctypes.byref(h), int(device), int(pool_bytes))
+    if rc != DAFMM_OK:
+        raise DafmmError(rc, "dafmm_create_pooled failed")
+    return h.value
+
+
 def dafmm_destroy(ctx):
     load().dafmm_destroy(ctx)
 
@@ -153,6 +175,46 @@ def dafmm_tree_free(tree):
     load().dafmm_tree_free(tree)
 
 
+def dafmm_build_forest(ctx, xyz, q, offsets, domains=None, max_leaf=64, stream=None):
+    """offsets: ntrees + 1 particle offsets (host); domains: ntrees x 4 root cubes or None."""
+    offs = np.ascontiguousarray(offsets, dtype=np.int64)
+    dom = None if domains is None else np.ascontiguousarray(domains, dtype=np.float64).reshape(-1, 4)
+    h = _vp()
+    rc = load().dafmm_build_forest(ctx, _ptr(xyz), _ptr(q), offs.ctypes.data, len(offs) - 1, _ptr(dom),
+                                   int(max_leaf), _stream_ptr(stream), ctypes.byref(h))
+    _check(ctx, rc)
+    return h.value
+
+
+def dafmm_forest_info(tree):
+    nt = ctypes.c_int(0)
+    if load().dafmm_forest_info(tree, ctypes.byref(nt), None) != DAFMM_OK:
+        raise DafmmError(DAFMM_ERR_INVALID_ARG, "dafmm_forest_info failed")
+    dom = np.zeros((nt.value, 4))
+    load().dafmm_forest_info(tree, None, dom.ctypes.data)
+    return nt.value, dom
+
+
+def dafmm_graph_create(ctx, tree, order, precision, phi=None, field=None, stream=None):
+    h = _vp()
+    rc = load().dafmm_graph_create(tree, int(order), int(precision), _ptr(phi), _ptr(field), _stream_ptr(stream),
+                                   ctypes.byref(h))
+    _check(ctx, rc)
+    return h.value
+
+
+def dafmm_graph_launch(ctx, graph, stream=None):
+    _check(ctx, load().dafmm_graph_launch(graph, _stream_ptr(stream)))
+
+
+def dafmm_graph_nodes(graph):
+    return load().dafmm_graph_nodes(graph)
+
+
+def dafmm_graph_free(graph):
+    load().dafmm_graph_free(graph)
+
+
 def dafmm_tree_info(tree):
     info = np.zeros(8, dtype=np.int64)
     dom = np.zeros(4)
@@ -173,6 +235,7 @@ def dafmm_eval(ctx, tree, order, phi=None, field=None, theta=1.0, precision=DAFM
 
 DAFMM_OPT_M2L_KERNEL = 1
 DAFMM_OPT_TC_MASK = 2
+DAFMM_OPT_LEAF_WARPS = 3
 
 
 def dafmm_set_option(ctx, option, value):
@@ -253,10 +316,11 @@ def dafmm_op_m2l_matrix(ctx, order, v, K, stream=None):
 
 # ---- a small convenience layer ----------------------------------------------------------------
 class Context:
-    """Owns a dafmm context; trees built from it are freed with it."""
+    """Owns a dafmm context; trees built from it are freed with it.  pool_bytes > 0 makes a
+    pooled context (one reservation, no cudaFree while it lives)."""
 
-    def __init__(self, device=0, hbm_budget_bytes=0):
-        self.h = dafmm_create(device, hbm_budget_bytes)
+    def __init__(self, device=0, hbm_budget_bytes=0, pool_bytes=0):
+        self.h = dafmm_create_pooled(device, pool_bytes) if pool_bytes else dafmm_create(device, hbm_budget_bytes)
 
     def close(self):
         if self.h:
@@ -272,6 +336,9 @@ class Context:
     def build_tree(self, xyz, q, domain=None, uniform_depth=-1, max_leaf=64, stream=None):
         return Tree(self, dafmm_build_tree(self.h, xyz, q, domain, uniform_depth, max_leaf, stream))
 
+    def build_forest(self, xyz, q, offsets, domains=None, max_leaf=64, stream=None):
+        return Tree(self, dafmm_build_forest(self.h, xyz, q, offsets, domains, max_leaf, stream))
+
 
 class Tree:
     def __init__(self, ctx, h):
@@ -285,7 +352,139 @@ class Tree:
         prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         dafmm_eval(self.ctx.h, self.h, order, phi, field, theta, prec, stream)
 
+    def forest(self):
+        return dafmm_forest_info(self.h)
+
+    def graph(self, order, phi=None, field=None, precision="fp32", stream=None):
+        prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        return Graph(self.ctx, dafmm_graph_create(self.ctx.h, self.h, order, prec, phi, field, stream))
+
     def free(self):
         if self.h and self.ctx.h:
             dafmm_tree_free(self.h)
         self.h = None
+
+
+class Graph:
+    def __init__(self, ctx, h):
+        self.ctx = ctx
+        self.h = h
+
+    def launch(self, stream=None):
+        dafmm_graph_launch(self.ctx.h, self.h, stream)
+
+    def nodes(self):
+        return dafmm_graph_nodes(self.h)
+
+    def free(self):
+        if self.h:
+            dafmm_graph_free(self.h)
+        self.h = None
+
+
+# ---- serving ------------------------------------------------------------------------------------
+SERVER_STATS = ["completed", "failed", "queued", "running", "jobs", "requests_per_job", "peak_bytes",
+                "peak_running"]
+
+
+def dafmm_server_create(device=0, pool_bytes=8 << 30, slots=4, max_batch=64, max_job_particles=1 << 21):
+    h = _vp()
+    rc = load().dafmm_server_create(int(device), int(pool_bytes), int(slots), int(max_batch), int(max_job_particles),
+                                    ctypes.byref(h))
+    if rc != DAFMM_OK:
+        raise DafmmError(rc, "dafmm_server_create failed")
+    return h.value
+
+
+def dafmm_server_submit(server, xyz, q, order, precision, max_leaf, phi, field):
+    rid = ctypes.c_int64(0)
+    rc = load().dafmm_server_submit(server, _ptr(xyz), _ptr(q), int(q.shape[0]), int(order), int(precision),
+                                    int(max_leaf), _ptr(phi), _ptr(field), ctypes.byref(rid))
+    if rc != DAFMM_OK:
+        raise DafmmError(rc, "dafmm_server_submit failed")
+    return rid.value
+
+
+def dafmm_server_wait(server, rid, timeout=-1.0):
+    """(status, [latency, queue, device] ms)."""
+    t = np.zeros(3)
+    st = load().dafmm_server_wait(server, int(rid), float(timeout), t.ctypes.data)
+    return st, t
+
+
+def dafmm_server_stats(server):
+    out = np.zeros(8)
+    load().dafmm_server_stats(server, out.ctypes.data)
+    return dict(zip(SERVER_STATS, out.tolist()))
+
+
+def dafmm_server_last_error(server):
+    return load().dafmm_server_last_error(server).decode()
+
+
+def dafmm_server_destroy(server):
+    load().dafmm_server_destroy(server)
+
+
+class Server:
+    """A request loop with continuous batching (dafmm_server_*).  Inputs and outputs are kept
+    in page-locked host tensors until the request has been waited for."""
+
+    def __init__(self, device=0, pool_bytes=8 << 30, slots=4, max_batch=64, max_job_particles=1 << 21):
+        import torch  # page-locked buffers
+        self._torch = torch
+        self.h = dafmm_server_create(device, pool_bytes, slots, max_batch, max_job_particles)
+        self._live = {}
+
+    def _pinned(self, a, shape):
+        torch = self._torch
+        if isinstance(a, torch.Tensor) and a.dtype == torch.float64 and (a.is_cuda or a.is_pinned()) \
+                and a.is_contiguous():
+            return a
+        t = torch.empty(shape, dtype=torch.float64, pin_memory=True)
+        t.copy_(torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64)).reshape(shape))
+        return t
+
+    def submit(self, xyz, q, order, precision="fp32", max_leaf=64, field=True, out=None):
+        """out: optional (phi, field) page-locked float64 tensors to receive the result."""
+        torch = self._torch
+        n = int(q.shape[0])
+        x = self._pinned(xyz, (n, 3))
+        qq = self._pinned(q, (n,))
+        if out is not None:
+            phi, E = out
+        else:
+            phi = torch.empty(n, dtype=torch.float64, pin_memory=True)
+            E = torch.empty((n, 3), dtype=torch.float64, pin_memory=True) if field else None
+        prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        rid = dafmm_server_submit(self.h, x, qq, order, prec, max_leaf, phi, E)
+        self._live[rid] = (x, qq, phi, E)
+        return rid
+
+    def wait(self, rid, timeout=-1.0):
+        """(status, phi, field, {latency_ms, queue_ms, device_ms}); status DAFMM_ERR_TIMEOUT keeps
+        the request pending."""
+        st, t = dafmm_server_wait(self.h, rid, timeout)
+        if st == DAFMM_ERR_TIMEOUT:
+            return st, None, None, None
+        _, _, phi, E = self._live.pop(rid)
+        times = dict(latency_ms=t[0], queue_ms=t[1], device_ms=t[2])
+        return st, phi.numpy(), (E.numpy() if E is not None else None), times
+
+    def stats(self):
+        return dafmm_server_stats(self.h)
+
+    def last_error(self):
+        return dafmm_server_last_error(self.h)
+
+    def close(self):
+        if self.h:
+            dafmm_server_destroy(self.h)
+            self.h = None
+            self._live.clear()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

@@ -54,6 +54,16 @@ int dev_alloc(dafmm_ctx* c, void** p, size_t bytes, const char* what) {
     *p = nullptr;
     if (bytes == 0) return DAFMM_OK;
     bytes = (bytes + 255) / 256 * 256;
+    if (c->arena_base) {
+        size_t off = 0;
+        if (!c->arena.alloc(bytes, &off))
+            return fail(c, DAFMM_ERR_OVER_BUDGET, std::string(what) + " needs " + std::to_string(bytes) +
+                                                      " bytes, largest free block of the pool " +
+                                                      std::to_string(c->arena.largest_free()));
+        *p = c->arena_base + off;
+        c->in_use += bytes;
+        return DAFMM_OK;
+    }
     if (c->budget && c->in_use + bytes > c->budget)
         return fail(c, DAFMM_ERR_OVER_BUDGET, std::string(what) + " needs " + std::to_string(bytes) +
                                                   " bytes, budget left " + std::to_string(c->budget - c->in_use));
@@ -68,8 +78,13 @@ int dev_alloc(dafmm_ctx* c, void** p, size_t bytes, const char* what) {
 
 void dev_free(dafmm_ctx* c, void* p, size_t bytes) {
     if (!p) return;
-    cudaFree(p);
-    bytes = (bytes + 255) / 256 * 256;
+    char* cp = static_cast<char*>(p);
+    if (c->arena_base && cp >= c->arena_base && cp < c->arena_base + c->arena.size()) {
+        bytes = c->arena.release((size_t)(cp - c->arena_base));
+    } else {
+        cudaFree(p);
+        bytes = (bytes + 255) / 256 * 256;
+    }
     c->in_use = c->in_use >= bytes ? c->in_use - bytes : 0;
 }
 
@@ -179,6 +194,7 @@ int ensure_order(dafmm_ctx* c, int p, cudaStream_t s, bool need_k) {
             }
         if ((rc = upload(c, &od.mul_rowptr, rowptr.data(), rowptr.size(), "product table"))) return rc;
         if ((rc = upload(c, &od.mul_pairs, pairs.data(), pairs.size(), "product table"))) return rc;
+        od.mul_npairs = pairs.size();
         if ((rc = upload(c, &od.mul_minus, minus.data(), minus.size(), "product table"))) return rc;
     }
     if (need_k && !od.k_ready) {
@@ -220,6 +236,8 @@ int ensure_order(dafmm_ctx* c, int p, cudaStream_t s, bool need_k) {
             dev_free(c, d64, ds * sizeof(double));
             if (rc) return rc;
         }
+        // the tables are shared by every later evaluation, on any stream: finish them here
+        CK(c, cudaStreamSynchronize(s), "K generation");
         od.k_ready = true;
     }
     return DAFMM_OK;
@@ -237,7 +255,9 @@ void free_order(dafmm_ctx* c, OrderData& od) {
         dev_free(c, w == 0 ? (void*)od.m2m_val : (void*)od.l2l_val, t.nnz * sizeof(double));
         dev_free(c, w == 0 ? (void*)od.m2m_valf : (void*)od.l2l_valf, t.nnz * sizeof(float));
     }
-    cudaFree(od.mul_rowptr); cudaFree(od.mul_pairs); cudaFree(od.mul_minus);
+    dev_free(c, od.mul_rowptr, ((size_t)nc + 1) * sizeof(int));
+    dev_free(c, od.mul_pairs, od.mul_npairs * sizeof(ushort2));
+    dev_free(c, od.mul_minus, (size_t)3 * nc * sizeof(short));
     const size_t cnt = (size_t)kNumKeys * od.nc * od.ncp;
     dev_free(c, od.K64, od.K64 ? cnt * sizeof(double) : 0);
     dev_free(c, od.K32, od.K32 ? cnt * sizeof(float) : 0);
@@ -314,6 +334,7 @@ size_t tree_bytes(int64_t n, int depth) {
 AdaptiveBuild abuild(dafmm_tree* t, const uint64_t* keys) {
     AdaptiveBuild ab;
     ab.keys = keys;
+    ab.root = t->a_root;
     ab.level = t->a_level;
     ab.ijk = t->a_ijk;
     ab.parent = t->a_parent;
@@ -337,22 +358,29 @@ AdaptiveView aview(const dafmm_tree* t) {
     v.u_ptr = t->u_ptr; v.u_idx = t->u_idx;
     v.w_ptr = t->w_ptr; v.w_idx = t->w_idx;
     v.x_ptr = t->x_ptr; v.x_idx = t->x_idx;
-    v.x0 = t->dom[0]; v.y0 = t->dom[1]; v.z0 = t->dom[2]; v.size = t->dom[3];
+    v.geom = t->a_geom;
     v.x = t->x; v.y = t->y; v.z = t->z; v.q = t->q;
     v.xq = t->xq;
     v.perm = t->perm;
     return v;
 }
 
-// per-box arrays of the adaptive hierarchy, sized for `cap` boxes
-const size_t kBoxInts = 1 + 3 + 1 + 8 + 1 + 1 + 27;
+// per-box arrays of the adaptive hierarchy, sized for `cap` boxes (ints per box)
+constexpr int kBoxArrays = 8;
+constexpr size_t kBoxWidth[kBoxArrays] = {1, 1, 3, 1, 8, 1, 1, 27};  // root level ijk parent child pbeg pend colleague
+constexpr size_t kBoxInts = 43;
+
+int** box_array(dafmm_tree* t, int k) {
+    int** a[kBoxArrays] = {&t->a_root, &t->a_level, &t->a_ijk, &t->a_parent, &t->a_child, &t->a_pbeg, &t->a_pend,
+                           &t->a_colleague};
+    return a[k];
+}
 
 void free_box_arrays(dafmm_ctx* c, dafmm_tree* t) {
-    const size_t cap = (size_t)t->cap;
-    dev_free(c, t->a_level, cap * 4); dev_free(c, t->a_ijk, cap * 12); dev_free(c, t->a_parent, cap * 4);
-    dev_free(c, t->a_child, cap * 32); dev_free(c, t->a_pbeg, cap * 4); dev_free(c, t->a_pend, cap * 4);
-    dev_free(c, t->a_colleague, cap * 108);
-    t->a_level = t->a_ijk = t->a_parent = t->a_child = t->a_pbeg = t->a_pend = t->a_colleague = nullptr;
+    for (int k = 0; k < kBoxArrays; ++k) {
+        dev_free(c, *box_array(t, k), (size_t)t->cap * kBoxWidth[k] * 4);
+        *box_array(t, k) = nullptr;
+    }
     t->cap = 0;
 }
 
@@ -361,21 +389,20 @@ int grow_boxes(dafmm_ctx* c, dafmm_tree* t, int need, int used, cudaStream_t s) 
     if (need <= t->cap) return DAFMM_OK;
     int cap = t->cap ? t->cap : 1024;
     while (cap < need) cap *= 2;
-    int* nb[7] = {};
-    const size_t w[7] = {1, 3, 1, 8, 1, 1, 27};
-    int* old[7] = {t->a_level, t->a_ijk, t->a_parent, t->a_child, t->a_pbeg, t->a_pend, t->a_colleague};
-    for (int k = 0; k < 7; ++k) {
-        int rc = dev_alloc(c, (void**)&nb[k], (size_t)cap * w[k] * 4, "tree boxes");
+    int* nb[kBoxArrays] = {};
+    for (int k = 0; k < kBoxArrays; ++k) {
+        int rc = dev_alloc(c, (void**)&nb[k], (size_t)cap * kBoxWidth[k] * 4, "tree boxes");
         if (rc) {
-            for (int j = 0; j < k; ++j) dev_free(c, nb[j], (size_t)cap * w[j] * 4);
+            for (int j = 0; j < k; ++j) dev_free(c, nb[j], (size_t)cap * kBoxWidth[j] * 4);
             return rc;
         }
-        if (used && old[k]) CK(c, cudaMemcpyAsync(nb[k], old[k], (size_t)used * w[k] * 4, cudaMemcpyDeviceToDevice, s), "grow");
+        int* old = *box_array(t, k);
+        if (used && old)
+            CK(c, cudaMemcpyAsync(nb[k], old, (size_t)used * kBoxWidth[k] * 4, cudaMemcpyDeviceToDevice, s), "grow");
     }
     CK(c, cudaStreamSynchronize(s), "grow");
     free_box_arrays(c, t);
-    t->a_level = nb[0]; t->a_ijk = nb[1]; t->a_parent = nb[2]; t->a_child = nb[3];
-    t->a_pbeg = nb[4]; t->a_pend = nb[5]; t->a_colleague = nb[6];
+    for (int k = 0; k < kBoxArrays; ++k) *box_array(t, k) = nb[k];
     t->cap = cap;
     return DAFMM_OK;
 }
@@ -383,6 +410,8 @@ int grow_boxes(dafmm_ctx* c, dafmm_tree* t, int need, int used, cudaStream_t s) 
 void free_adaptive(dafmm_ctx* c, dafmm_tree* t) {
     free_box_arrays(c, t);
     const size_t nb1 = (size_t)t->nbox + 1;
+    dev_free(c, t->a_geom, (size_t)t->nbox * sizeof(double4));
+    dev_free(c, t->d_rootdom, t->rootdom.size() * sizeof(double));
     dev_free(c, t->u_ptr, nb1 * 4); dev_free(c, t->w_ptr, nb1 * 4); dev_free(c, t->x_ptr, nb1 * 4);
     dev_free(c, t->u_idx, (size_t)t->nu * 4); dev_free(c, t->w_idx, (size_t)t->nw * 4); dev_free(c, t->x_idx, (size_t)t->nx * 4);
     dev_free(c, t->leaves, (size_t)t->nleaves * 4);
@@ -393,64 +422,152 @@ void free_adaptive(dafmm_ctx* c, dafmm_tree* t) {
         dev_free(c, t->aM, cnt * 8); dev_free(c, t->aL, cnt * 8); dev_free(c, t->aMf, cnt * 4);
     }
     t->u_ptr = t->w_ptr = t->x_ptr = t->u_idx = t->w_idx = t->x_idx = t->leaves = t->grp_tg = t->grp_ptr = nullptr;
+    t->a_geom = nullptr;
+    t->d_rootdom = nullptr;
     t->aM = t->aL = nullptr;
     t->aMf = nullptr;
     t->a_exp_p = -1;
 }
 
-// keys -> sort -> level-by-level split -> colleagues -> leaves -> gather -> lists -> M2L groups
-int build_adaptive(dafmm_ctx* c, dafmm_tree* t, const double* dxyz, const double* dq, int max_leaf, int max_depth,
-                   cudaStream_t s) {
-    const int64_t n = t->n;
-    const size_t N = (size_t)n;
-    int rc;
-    uint64_t* keys = nullptr;
-    void* tmp = nullptr;
-    int* scratch = nullptr;  // counts / offsets
-    const size_t tmpb = radix_sort_temp_bytes(n > 0 ? n : 1);
-    if ((rc = dev_alloc(c, (void**)&keys, (N > 0 ? N : 1) * 8, "sort keys"))) return rc;
-    if ((rc = dev_alloc(c, &tmp, tmpb, "sort scratch"))) { dev_free(c, keys, (N > 0 ? N : 1) * 8); return rc; }
-    auto cleanup = [&]() {
-        dev_free(c, keys, (N > 0 ? N : 1) * 8);
-        dev_free(c, tmp, tmpb);
-    };
-    const double scale = ldexp(1.0, kQBits) / t->dom[3];
-    cudaError_t e = launch_morton_keys(dxyz, n, t->dom[0], t->dom[1], t->dom[2], scale, keys, t->perm, s);
-    if (e == cudaSuccess) e = radix_sort_pairs(keys, t->perm, n, 3 * kQBits, tmp, s);
-    if (e != cudaSuccess) { cleanup(); return cuda_fail(c, e, "Morton sort"); }
-    // hierarchy
-    if ((rc = grow_boxes(c, t, 1024, 0, s))) { cleanup(); return rc; }
-    {
-        int zero3[3] = {0, 0, 0}, m1 = -1, z = 0, nn = (int)n, lev0 = 0;
-        CK(c, cudaMemcpyAsync(t->a_level, &lev0, 4, cudaMemcpyHostToDevice, s), "root");
-        CK(c, cudaMemcpyAsync(t->a_ijk, zero3, 12, cudaMemcpyHostToDevice, s), "root");
-        CK(c, cudaMemcpyAsync(t->a_parent, &m1, 4, cudaMemcpyHostToDevice, s), "root");
-        CK(c, cudaMemcpyAsync(t->a_pbeg, &z, 4, cudaMemcpyHostToDevice, s), "root");
-        CK(c, cudaMemcpyAsync(t->a_pend, &nn, 4, cudaMemcpyHostToDevice, s), "root");
-        CK(c, cudaStreamSynchronize(s), "root");
+// device scratch that is returned to the context when it goes out of scope
+struct Scratch {
+    dafmm_ctx* c;
+    void* p = nullptr;
+    size_t bytes = 0;
+    explicit Scratch(dafmm_ctx* ctx) : c(ctx) {}
+    int alloc(size_t b, const char* what) {
+        release();
+        bytes = b;
+        return dev_alloc(c, &p, b, what);
     }
-    t->level_start.assign({0, 1});
-    int scap = 0;
+    void release() {
+        dev_free(c, p, bytes);
+        p = nullptr;
+        bytes = 0;
+    }
+    template <class T>
+    T* as() const { return static_cast<T*>(p); }
+    ~Scratch() { release(); }
+};
+
+// root cubes of the trees: given, or the smallest cube around each tree's points, enlarged by
+// 1e-12 of its size (the same rule as for a single tree)
+int forest_domains(dafmm_ctx* c, const double* dxyz, const std::vector<int>& offs, const double* domains,
+                   std::vector<double>& dom, const int* d_offs, cudaStream_t s) {
+    const int nroots = (int)offs.size() - 1;
+    dom.assign(4 * (size_t)nroots, 0.0);
+    if (domains) {
+        for (int r = 0; r < nroots; ++r) {
+            const double* d = domains + 4 * r;
+            if (!(d[3] > 0.0 && isfinite(d[0]) && isfinite(d[1]) && isfinite(d[2]) && isfinite(d[3])))
+                return fail(c, DAFMM_ERR_INVALID_ARG, "domain of tree " + std::to_string(r));
+            for (int k = 0; k < 4; ++k) dom[4 * r + k] = d[k];
+        }
+        return DAFMM_OK;
+    }
+    Scratch bb(c);
+    int rc = bb.alloc((size_t)nroots * 6 * 8, "bbox");
+    if (rc) return rc;
+    std::vector<unsigned long long> h(6 * (size_t)nroots);
+    cudaError_t e = launch_bbox_roots(dxyz, d_offs, nroots, bb.as<unsigned long long>(), s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h.data(), bb.p, h.size() * 8, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(c, e, "bounding boxes");
+    for (int r = 0; r < nroots; ++r) {
+        double* d = &dom[4 * r];
+        if (offs[r + 1] == offs[r]) {
+            d[3] = 1.0;
+            continue;
+        }
+        double v[6];
+        for (int k = 0; k < 6; ++k) {
+            unsigned long long u = h[6 * r + k];
+            u = (u >> 63) ? (u & 0x7fffffffffffffffull) : ~u;
+            memcpy(&v[k], &u, 8);
+        }
+        double size = std::max(v[3] - v[0], std::max(v[4] - v[1], v[5] - v[2]));
+        if (!(size > 0.0)) size = 1.0;
+        size = size * (1.0 + 1e-12);
+        if (!(isfinite(size) && isfinite(v[0]) && isfinite(v[1]) && isfinite(v[2])))
+            return fail(c, DAFMM_ERR_INVALID_ARG, "non-finite coordinates");
+        d[0] = v[0]; d[1] = v[1]; d[2] = v[2]; d[3] = size;
+    }
+    return DAFMM_OK;
+}
+
+// keys -> sort (-> regroup by tree) -> level-by-level split -> colleagues -> geometry ->
+// leaves -> gather -> U, W, X lists -> M2L target groups.  t->rootdom holds the root cubes.
+int build_adaptive(dafmm_ctx* c, dafmm_tree* t, const double* dxyz, const double* dq, const std::vector<int>& offs,
+                   const int* d_offs, int max_leaf, int max_depth, cudaStream_t s) {
+    const int64_t n = t->n;
+    const size_t N1 = (size_t)(n > 0 ? n : 1);
+    const int nroots = (int)offs.size() - 1;
+    int rc;
+    cudaError_t e;
+    Scratch keys(c), tmp(c), scratch(c);
+    if ((rc = keys.alloc(N1 * 8, "sort keys"))) return rc;
+    if ((rc = tmp.alloc(radix_sort_temp_bytes(n > 0 ? n : 1), "sort scratch"))) return rc;
+    if ((rc = dev_alloc(c, (void**)&t->d_rootdom, t->rootdom.size() * sizeof(double), "root cubes"))) return rc;
+    CK(c, cudaMemcpyAsync(t->d_rootdom, t->rootdom.data(), t->rootdom.size() * sizeof(double), cudaMemcpyHostToDevice,
+                          s), "root cubes");
+    e = launch_morton_keys(dxyz, n, d_offs, nroots, t->d_rootdom, keys.as<uint64_t>(), t->perm, s);
+    if (e == cudaSuccess) e = radix_sort_pairs(keys.as<uint64_t>(), t->perm, n, 3 * kQBits, tmp.p, s);
+    if (e != cudaSuccess) return cuda_fail(c, e, "Morton sort");
+    if (nroots > 1 && n > 0) {
+        // stable regroup by tree: sort positions by tree index, then apply to (perm, keys)
+        Scratch tk(c), pos(c), perm2(c), keys2(c);
+        if ((rc = tk.alloc(N1 * 8, "tree keys")) || (rc = pos.alloc(N1 * 4, "tree keys")) ||
+            (rc = perm2.alloc(N1 * 4, "tree keys")) || (rc = keys2.alloc(N1 * 8, "tree keys")))
+            return rc;
+        int bits = 1;
+        while ((1 << bits) < nroots) ++bits;
+        e = launch_tree_keys(t->perm, n, d_offs, nroots, tk.as<uint64_t>(), pos.as<int>(), s);
+        if (e == cudaSuccess) e = radix_sort_pairs(tk.as<uint64_t>(), pos.as<int>(), n, bits, tmp.p, s);
+        if (e == cudaSuccess)
+            e = launch_apply_order(pos.as<int>(), n, t->perm, keys.as<uint64_t>(), perm2.as<int>(),
+                                   keys2.as<uint64_t>(), s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(t->perm, perm2.p, N1 * 4, cudaMemcpyDeviceToDevice, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(keys.p, keys2.p, N1 * 8, cudaMemcpyDeviceToDevice, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return cuda_fail(c, e, "tree regroup");
+    }
+    // roots
+    if ((rc = grow_boxes(c, t, std::max(1024, nroots), 0, s))) return rc;
+    {
+        std::vector<int> zero(3 * (size_t)nroots, 0), m1(nroots, -1), lev(nroots, 0), rid(nroots), pb(nroots),
+            pe(nroots);
+        for (int r = 0; r < nroots; ++r) {
+            rid[r] = r;
+            pb[r] = offs[r];
+            pe[r] = offs[r + 1];
+        }
+        const size_t R = (size_t)nroots * 4;
+        CK(c, cudaMemcpyAsync(t->a_root, rid.data(), R, cudaMemcpyHostToDevice, s), "roots");
+        CK(c, cudaMemcpyAsync(t->a_level, lev.data(), R, cudaMemcpyHostToDevice, s), "roots");
+        CK(c, cudaMemcpyAsync(t->a_ijk, zero.data(), 3 * R, cudaMemcpyHostToDevice, s), "roots");
+        CK(c, cudaMemcpyAsync(t->a_parent, m1.data(), R, cudaMemcpyHostToDevice, s), "roots");
+        CK(c, cudaMemcpyAsync(t->a_pbeg, pb.data(), R, cudaMemcpyHostToDevice, s), "roots");
+        CK(c, cudaMemcpyAsync(t->a_pend, pe.data(), R, cudaMemcpyHostToDevice, s), "roots");
+        CK(c, cudaStreamSynchronize(s), "roots");
+    }
+    t->level_start.assign({0, nroots});
     for (int l = 0; l < max_depth; ++l) {
         const int lb = t->level_start[l], le = t->level_start[l + 1];
         const int nl = le - lb;
-        if (2 * (nl + 1) > scap) {
-            dev_free(c, scratch, (size_t)scap * 4);
-            scap = 2 * (nl + 1);
-            if ((rc = dev_alloc(c, (void**)&scratch, (size_t)scap * 4, "split scratch"))) { cleanup(); return rc; }
-        }
-        AdaptiveBuild ab = abuild(t, keys);
-        e = launch_split(ab, lb, le, l, max_leaf, max_depth, scratch, s);
-        if (e == cudaSuccess) e = launch_scan(scratch, scratch + nl + 1, nl, s);
+        if (scratch.bytes < 2 * ((size_t)nl + 1) * 4 && (rc = scratch.alloc(2 * ((size_t)nl + 1) * 4, "split scratch")))
+            return rc;
+        int* cnt = scratch.as<int>();
+        int* off = cnt + nl + 1;
+        e = launch_split(abuild(t, keys.as<uint64_t>()), lb, le, l, max_leaf, max_depth, cnt, s);
+        if (e == cudaSuccess) e = launch_scan(cnt, off, nl, s);
         int total = 0;
-        if (e == cudaSuccess) e = cudaMemcpyAsync(&total, scratch + nl + 1 + nl, 4, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&total, off + nl, 4, cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-        if (e != cudaSuccess) { cleanup(); dev_free(c, scratch, (size_t)scap * 4); return cuda_fail(c, e, "split"); }
+        if (e != cudaSuccess) return cuda_fail(c, e, "split");
         if (total == 0) break;
-        if ((rc = grow_boxes(c, t, le + total, le, s))) { cleanup(); dev_free(c, scratch, (size_t)scap * 4); return rc; }
-        ab = abuild(t, keys);
-        e = launch_split_fill(ab, lb, le, l, scratch + nl + 1, le, s);
-        if (e != cudaSuccess) { cleanup(); dev_free(c, scratch, (size_t)scap * 4); return cuda_fail(c, e, "split"); }
+        if ((rc = grow_boxes(c, t, le + total, le, s))) return rc;
+        e = launch_split_fill(abuild(t, keys.as<uint64_t>()), lb, le, l, off, le, s);
+        if (e != cudaSuccess) return cuda_fail(c, e, "split");
         t->level_start.push_back(le + total);
     }
     t->maxlev = (int)t->level_start.size() - 2;
@@ -458,88 +575,85 @@ int build_adaptive(dafmm_ctx* c, dafmm_tree* t, const double* dxyz, const double
     const int nbox = t->nbox;
     e = launch_children_init(t->a_child, t->level_start[t->maxlev], nbox, s);
     for (int l = 0; l <= t->maxlev && e == cudaSuccess; ++l)
-        e = launch_colleagues(abuild(t, keys), t->level_start[l], t->level_start[l + 1], s);
-    if (e != cudaSuccess) { cleanup(); dev_free(c, scratch, (size_t)scap * 4); return cuda_fail(c, e, "colleagues"); }
+        e = launch_colleagues(abuild(t, keys.as<uint64_t>()), t->level_start[l], t->level_start[l + 1], s);
+    if (e != cudaSuccess) return cuda_fail(c, e, "colleagues");
+    if ((rc = dev_alloc(c, (void**)&t->a_geom, (size_t)nbox * sizeof(double4), "box geometry"))) return rc;
+    e = launch_box_geometry(t->a_root, t->a_level, t->a_ijk, t->d_rootdom, nbox, t->a_geom, s);
+    if (e != cudaSuccess) return cuda_fail(c, e, "geometry");
     // leaves (breadth-first order)
-    dev_free(c, scratch, (size_t)scap * 4);
-    scap = 2 * (nbox + 1);
-    if ((rc = dev_alloc(c, (void**)&scratch, (size_t)scap * 4, "leaf scratch"))) { cleanup(); return rc; }
-    e = launch_leaf_flags(t->a_child, nbox, scratch, s);
-    if (e == cudaSuccess) e = launch_scan(scratch, scratch + nbox + 1, nbox, s);
+    if ((rc = scratch.alloc(2 * ((size_t)nbox + 1) * 4, "leaf scratch"))) return rc;
+    int* flags = scratch.as<int>();
+    int* foff = flags + nbox + 1;
+    e = launch_leaf_flags(t->a_child, nbox, flags, s);
+    if (e == cudaSuccess) e = launch_scan(flags, foff, nbox, s);
     int nl = 0;
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&nl, scratch + nbox + 1 + nbox, 4, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&nl, foff + nbox, 4, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(c, e, "leaves");
     t->nleaves = nl;
-    if (e == cudaSuccess && (rc = dev_alloc(c, (void**)&t->leaves, (size_t)(nl > 0 ? nl : 1) * 4, "leaves"))) {
-        cleanup(); dev_free(c, scratch, (size_t)scap * 4); return rc;
-    }
-    if (e == cudaSuccess) e = launch_scatter_flagged(scratch, scratch + nbox + 1, nbox, t->leaves, s);
+    if ((rc = dev_alloc(c, (void**)&t->leaves, (size_t)(nl > 0 ? nl : 1) * 4, "leaves"))) return rc;
+    e = launch_scatter_flagged(flags, foff, nbox, t->leaves, s);
     if (e == cudaSuccess)
-        e = launch_gather_adaptive(dxyz, dq, t->perm, abuild(t, keys), t->leaves, nl, t->dom, t->x, t->y, t->z, t->q,
-                                   t->xq, s);
-    if (e != cudaSuccess) { cleanup(); dev_free(c, scratch, (size_t)scap * 4); return cuda_fail(c, e, "leaves"); }
+        e = launch_gather_adaptive(dxyz, dq, t->perm, abuild(t, keys.as<uint64_t>()), t->leaves, nl, t->a_geom, t->x,
+                                   t->y, t->z, t->q, t->xq, s);
+    if (e != cudaSuccess) return cuda_fail(c, e, "gather");
     // U, W, X lists
-    int* cnt3 = nullptr;
     const size_t nb1 = (size_t)nbox + 1;
-    const size_t cnt3b = 3 * nb1 * 4 + 16;  // three count arrays, then the V pair counter (8-aligned)
-    if ((rc = dev_alloc(c, (void**)&cnt3, cnt3b, "list counts"))) { cleanup(); dev_free(c, scratch, (size_t)scap * 4); return rc; }
-    unsigned long long* nv = reinterpret_cast<unsigned long long*>(cnt3 + ((3 * nb1 + 1) & ~size_t(1)));
-    if (!rc) rc = dev_alloc(c, (void**)&t->u_ptr, nb1 * 4, "lists");
-    if (!rc) rc = dev_alloc(c, (void**)&t->w_ptr, nb1 * 4, "lists");
-    if (!rc) rc = dev_alloc(c, (void**)&t->x_ptr, nb1 * 4, "lists");
+    Scratch cnt3(c);
+    if ((rc = cnt3.alloc(3 * nb1 * 4 + 16, "list counts"))) return rc;
+    int* cu = cnt3.as<int>();
+    unsigned long long* nv = reinterpret_cast<unsigned long long*>(cu + ((3 * nb1 + 1) & ~size_t(1)));
+    if ((rc = dev_alloc(c, (void**)&t->u_ptr, nb1 * 4, "lists")) || (rc = dev_alloc(c, (void**)&t->w_ptr, nb1 * 4, "lists")) ||
+        (rc = dev_alloc(c, (void**)&t->x_ptr, nb1 * 4, "lists")))
+        return rc;
     CK(c, cudaMemsetAsync(c->d_err, 0, 4, s), "err");
     CK(c, cudaMemsetAsync(nv, 0, 8, s), "counter");
-    e = launch_list_count(abuild(t, keys), nbox, cnt3, cnt3 + nb1, cnt3 + 2 * nb1, nv, c->d_err, s);
-    if (e == cudaSuccess) e = launch_scan(cnt3, t->u_ptr, nbox, s);
-    if (e == cudaSuccess) e = launch_scan(cnt3 + nb1, t->w_ptr, nbox, s);
-    if (e == cudaSuccess) e = launch_scan(cnt3 + 2 * nb1, t->x_ptr, nbox, s);
+    e = launch_list_count(abuild(t, keys.as<uint64_t>()), nbox, cu, cu + nb1, cu + 2 * nb1, nv, c->d_err, s);
+    if (e == cudaSuccess) e = launch_scan(cu, t->u_ptr, nbox, s);
+    if (e == cudaSuccess) e = launch_scan(cu + nb1, t->w_ptr, nbox, s);
+    if (e == cudaSuccess) e = launch_scan(cu + 2 * nb1, t->x_ptr, nbox, s);
     int tot[3] = {0, 0, 0};
+    unsigned long long nvh = 0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&tot[0], t->u_ptr + nbox, 4, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(&tot[1], t->w_ptr + nbox, 4, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(&tot[2], t->x_ptr + nbox, 4, cudaMemcpyDeviceToHost, s);
-    unsigned long long nvh = 0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&nvh, nv, 8, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess || rc) { cleanup(); dev_free(c, scratch, (size_t)scap * 4); dev_free(c, cnt3, cnt3b); return rc ? rc : cuda_fail(c, e, "lists"); }
-    t->nv = (int64_t)nvh;
+    if (e != cudaSuccess) return cuda_fail(c, e, "lists");
     t->nu = tot[0]; t->nw = tot[1]; t->nx = tot[2];
-    if (!rc) rc = dev_alloc(c, (void**)&t->u_idx, (size_t)(tot[0] > 0 ? tot[0] : 1) * 4, "lists");
-    if (!rc) rc = dev_alloc(c, (void**)&t->w_idx, (size_t)(tot[1] > 0 ? tot[1] : 1) * 4, "lists");
-    if (!rc) rc = dev_alloc(c, (void**)&t->x_idx, (size_t)(tot[2] > 0 ? tot[2] : 1) * 4, "lists");
-    if (!rc) {
-        e = launch_list_fill(abuild(t, keys), nbox, t->u_ptr, t->w_ptr, t->x_ptr, t->u_idx, t->w_idx, t->x_idx, c->d_err, s);
-        int flag = 0;
-        if (e == cudaSuccess) e = cudaMemcpyAsync(&flag, c->d_err, 4, cudaMemcpyDeviceToHost, s);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-        if (e == cudaSuccess && flag) rc = fail(c, DAFMM_ERR_INVALID_ARG, "adaptive tree too deep for the list traversal");
+    t->nv = (int64_t)nvh;
+    if ((rc = dev_alloc(c, (void**)&t->u_idx, (size_t)std::max(tot[0], 1) * 4, "lists")) ||
+        (rc = dev_alloc(c, (void**)&t->w_idx, (size_t)std::max(tot[1], 1) * 4, "lists")) ||
+        (rc = dev_alloc(c, (void**)&t->x_idx, (size_t)std::max(tot[2], 1) * 4, "lists")))
+        return rc;
+    e = launch_list_fill(abuild(t, keys.as<uint64_t>()), nbox, t->u_ptr, t->w_ptr, t->x_ptr, t->u_idx, t->w_idx,
+                         t->x_idx, c->d_err, s);
+    int flag = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&flag, c->d_err, 4, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(c, e, "lists");
+    if (flag) {
+        CK(c, cudaMemset(c->d_err, 0, 4), "err");
+        return fail(c, DAFMM_ERR_INVALID_ARG, "adaptive tree too deep for the list traversal");
     }
-    dev_free(c, cnt3, cnt3b);
+    cnt3.release();
     // M2L target groups: boxes of levels >= 2 by (level, octant)
     const int ngroups = (t->maxlev + 1) * 8;
-    if (!rc && e == cudaSuccess) {
-        uint64_t* gk = nullptr;
-        void* gtmp = nullptr;
-        const size_t gtb = radix_sort_temp_bytes(nbox);
-        rc = dev_alloc(c, (void**)&gk, (size_t)nbox * 8, "groups");
-        if (!rc) rc = dev_alloc(c, &gtmp, gtb, "groups");
-        if (!rc) rc = dev_alloc(c, (void**)&t->grp_tg, (size_t)nbox * 4, "groups");
-        if (!rc) rc = dev_alloc(c, (void**)&t->grp_ptr, ((size_t)ngroups + 1) * 4, "groups");
-        if (!rc) {
-            e = launch_group_keys(t->a_level, t->a_ijk, nbox, gk, t->grp_tg, s);
-            if (e == cudaSuccess) e = radix_sort_pairs(gk, t->grp_tg, nbox, 8, gtmp, s);
-            if (e == cudaSuccess) e = launch_group_ptr(gk, nbox, ngroups, t->grp_ptr, s);
-            t->grp_ptr_h.assign(ngroups + 1, 0);
-            if (e == cudaSuccess)
-                e = cudaMemcpyAsync(t->grp_ptr_h.data(), t->grp_ptr, (ngroups + 1) * 4, cudaMemcpyDeviceToHost, s);
-            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-        }
-        dev_free(c, gk, (size_t)nbox * 8);
-        dev_free(c, gtmp, gtb);
+    {
+        Scratch gk(c), gtmp(c);
+        if ((rc = gk.alloc((size_t)nbox * 8, "groups")) || (rc = gtmp.alloc(radix_sort_temp_bytes(nbox), "groups")) ||
+            (rc = dev_alloc(c, (void**)&t->grp_tg, (size_t)nbox * 4, "groups")) ||
+            (rc = dev_alloc(c, (void**)&t->grp_ptr, ((size_t)ngroups + 1) * 4, "groups")))
+            return rc;
+        e = launch_group_keys(t->a_level, t->a_ijk, nbox, gk.as<uint64_t>(), t->grp_tg, s);
+        if (e == cudaSuccess) e = radix_sort_pairs(gk.as<uint64_t>(), t->grp_tg, nbox, 8, gtmp.p, s);
+        if (e == cudaSuccess) e = launch_group_ptr(gk.as<uint64_t>(), nbox, ngroups, t->grp_ptr, s);
+        t->grp_ptr_h.assign(ngroups + 1, 0);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(t->grp_ptr_h.data(), t->grp_ptr, (ngroups + 1) * 4, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return cuda_fail(c, e, "groups");
     }
-    cleanup();
-    dev_free(c, scratch, (size_t)scap * 4);
-    if (rc) return rc;
-    if (e != cudaSuccess) return cuda_fail(c, e, "adaptive build");
     // largest leaf
     std::vector<int> pb(nbox), pe(nbox), lf(nl);
     CK(c, cudaMemcpy(pb.data(), t->a_pbeg, (size_t)nbox * 4, cudaMemcpyDeviceToHost), "info");
@@ -603,8 +717,7 @@ int eval_adaptive(dafmm_tree* t, int order, int precision, double* dphi, double*
             if (l == t->maxlev) mark(4);
             int mx = 0;
             for (int o = 0; o < 8; ++o) mx = std::max(mx, t->grp_ptr_h[l * 8 + o + 1] - t->grp_ptr_h[l * 8 + o]);
-            CK(c, ops->m2l_a(od, av, precision, t->grp_tg, t->grp_ptr, l * 8, mx, t->aM, t->aMf, t->aL,
-                             1.0 / ldexp(t->dom[3], -l), s), "M2L");
+            CK(c, ops->m2l_a(od, av, precision, t->grp_tg, t->grp_ptr, l * 8, mx, t->aM, t->aMf, t->aL, s), "M2L");
             CK(c, ops->p2l_a(av, precision, t->level_start[l], t->level_start[l + 1], t->aL, s), "P2L");
             launches += 2;
         }
@@ -617,7 +730,8 @@ int eval_adaptive(dafmm_tree* t, int order, int precision, double* dphi, double*
     } else {
         for (int k = 1; k <= 6; ++k) mark(k);
     }
-    CK(c, ops->leaf_a(av, t->leaves, t->nleaves, precision, t->aL, t->aM, dphi, dfield, s), "P2P/M2P/L2P");
+    CK(c, ops->leaf_a(av, t->leaves, t->nleaves, precision, t->aL, t->aM, dphi, dfield, c->leaf_warps, s),
+       "P2P/M2P/L2P");
     ++launches;
     mark(7);
     c->last_launches = launches;
@@ -625,6 +739,11 @@ int eval_adaptive(dafmm_tree* t, int order, int precision, double* dphi, double*
     return DAFMM_OK;
 }
 }  // namespace
+
+namespace dafmm {
+int ctx_alloc(dafmm_ctx* c, void** p, size_t bytes, const char* what) { return dev_alloc(c, p, bytes, what); }
+void ctx_free(dafmm_ctx* c, void* p, size_t bytes) { dev_free(c, p, bytes); }
+}  // namespace dafmm
 
 namespace dafmm {
 const OrderOps* order_ops(int p) {
@@ -677,6 +796,26 @@ int dafmm_create(dafmm_ctx** out, int device, size_t hbm_budget_bytes) {
     return DAFMM_OK;
 }
 
+int dafmm_create_pooled(dafmm_ctx** out, int device, size_t pool_bytes) {
+    if (!out) return DAFMM_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (pool_bytes < ((size_t)1 << 20)) return DAFMM_ERR_INVALID_ARG;
+    dafmm_ctx* c = nullptr;
+    int rc = dafmm_create(&c, device, pool_bytes);
+    if (rc) return rc;
+    pool_bytes = pool_bytes / OffsetArena::kAlign * OffsetArena::kAlign;
+    cudaError_t e = cudaMalloc((void**)&c->arena_base, pool_bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        c->arena_base = nullptr;
+        dafmm_destroy(c);
+        return DAFMM_ERR_OVER_BUDGET;
+    }
+    c->arena.reset(pool_bytes);
+    *out = c;
+    return DAFMM_OK;
+}
+
 void dafmm_destroy(dafmm_ctx* c) {
     if (!c) return;
     cudaSetDevice(c->device);
@@ -687,6 +826,7 @@ void dafmm_destroy(dafmm_ctx* c) {
     for (int k = 0; k < 8; ++k)
         if (c->ev[k]) cudaEventDestroy(c->ev[k]);
     dev_free(c, c->d_err, sizeof(int));
+    if (c->arena_base) cudaFree(c->arena_base);
     delete c;
 }
 
@@ -766,7 +906,14 @@ int dafmm_build_tree(dafmm_ctx* c, const double* xyz, const double* q, int64_t n
             return rc;
         }
         c->trees.push_back(t);
-        rc = build_adaptive(c, t, dxyz, dq, max_leaf, kMaxAdaptiveDepth, s);
+        t->rootdom.assign(t->dom, t->dom + 4);
+        t->root_offs = {0, n};
+        const std::vector<int> offs = {0, (int)n};
+        Scratch d_offs(c);
+        if (!(rc = d_offs.alloc(2 * sizeof(int), "offsets"))) {
+            CK(c, cudaMemcpyAsync(d_offs.p, offs.data(), 2 * sizeof(int), cudaMemcpyHostToDevice, s), "offsets");
+            rc = build_adaptive(c, t, dxyz, dq, offs, d_offs.as<int>(), max_leaf, kMaxAdaptiveDepth, s);
+        }
         if (rc) {
             dafmm_tree_free(t);
             return rc;
@@ -806,6 +953,74 @@ int dafmm_build_tree(dafmm_ctx* c, const double* xyz, const double* q, int64_t n
     }
     for (int b = 0; b < t->nleaf; ++b) t->max_per_leaf = std::max(t->max_per_leaf, ls[b + 1] - ls[b]);
     *out = t;
+    return DAFMM_OK;
+}
+
+int dafmm_build_forest(dafmm_ctx* c, const double* xyz, const double* q, const int64_t* offsets, int ntrees,
+                       const double* domains, int max_leaf, void* stream, dafmm_tree** out) {
+    if (!c || !out) return DAFMM_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (ntrees < 1 || !offsets || offsets[0] != 0) return fail(c, DAFMM_ERR_INVALID_ARG, "forest offsets");
+    for (int r = 0; r < ntrees; ++r)
+        if (offsets[r + 1] < offsets[r]) return fail(c, DAFMM_ERR_INVALID_ARG, "forest offsets decrease");
+    const int64_t n = offsets[ntrees];
+    if (n > (int64_t)INT32_MAX - 1 || (n > 0 && (!xyz || !q))) return fail(c, DAFMM_ERR_INVALID_ARG, "particle arrays");
+    if (max_leaf < 1) return fail(c, DAFMM_ERR_INVALID_ARG, "max_leaf must be >= 1");
+    CK(c, cudaSetDevice(c->device), "cudaSetDevice");
+    cudaStream_t s = (cudaStream_t)stream;
+    Staged sx, sq;
+    int rc;
+    if ((rc = stage_in(c, xyz, (size_t)n * 3 * sizeof(double), s, sx))) return rc;
+    if ((rc = stage_in(c, q, (size_t)n * sizeof(double), s, sq))) return rc;
+    const double* dxyz = (const double*)sx.dev;
+    const double* dq = (const double*)sq.dev;
+    std::vector<int> offs(ntrees + 1);
+    for (int r = 0; r <= ntrees; ++r) offs[r] = (int)offsets[r];
+    Scratch d_offs(c);
+    if ((rc = d_offs.alloc(offs.size() * sizeof(int), "forest offsets"))) return rc;
+    CK(c, cudaMemcpyAsync(d_offs.p, offs.data(), offs.size() * sizeof(int), cudaMemcpyHostToDevice, s), "offsets");
+    dafmm_tree* t = new dafmm_tree();
+    t->ctx = c;
+    t->n = n;
+    t->adaptive = true;
+    t->max_leaf = max_leaf;
+    t->depth = 0;
+    t->nleaf = 0;
+    t->nroots = ntrees;
+    t->root_offs.assign(offsets, offsets + ntrees + 1);
+    c->trees.push_back(t);
+    rc = forest_domains(c, dxyz, offs, domains, t->rootdom, d_offs.as<int>(), s);
+    if (!rc) {
+        for (int d = 0; d < 4; ++d) t->dom[d] = t->rootdom[d];
+        const size_t N = (size_t)n;
+        if (!rc) rc = dev_alloc(c, (void**)&t->x, N * sizeof(double), "particles");
+        if (!rc) rc = dev_alloc(c, (void**)&t->y, N * sizeof(double), "particles");
+        if (!rc) rc = dev_alloc(c, (void**)&t->z, N * sizeof(double), "particles");
+        if (!rc) rc = dev_alloc(c, (void**)&t->q, N * sizeof(double), "particles");
+        if (!rc) rc = dev_alloc(c, (void**)&t->xq, N * sizeof(float4), "particles");
+        if (!rc) rc = dev_alloc(c, (void**)&t->perm, N * sizeof(int), "particles");
+        if (!rc) rc = dev_alloc(c, (void**)&t->leaf_start, sizeof(int), "leaves");
+    }
+    if (!rc) rc = build_adaptive(c, t, dxyz, dq, offs, d_offs.as<int>(), max_leaf, kMaxAdaptiveDepth, s);
+    if (rc) {
+        const std::string msg = c->err;
+        dafmm_tree_free(t);
+        c->err = msg;
+        return rc;
+    }
+    *out = t;
+    return DAFMM_OK;
+}
+
+int dafmm_forest_info(const dafmm_tree* t, int* ntrees, double* domains) {
+    if (!t) return DAFMM_ERR_INVALID_ARG;
+    if (ntrees) *ntrees = t->adaptive ? t->nroots : 1;
+    if (domains) {
+        if (t->adaptive)
+            for (size_t k = 0; k < t->rootdom.size(); ++k) domains[k] = t->rootdom[k];
+        else
+            for (int d = 0; d < 4; ++d) domains[d] = t->dom[d];
+    }
     return DAFMM_OK;
 }
 
@@ -1058,6 +1273,10 @@ int dafmm_set_option(dafmm_ctx* c, int option, int64_t value) {
         c->tc_mask = (int)value;
         return DAFMM_OK;
     }
+    if (option == DAFMM_OPT_LEAF_WARPS && (value == 1 || value == 2 || value == 4 || value == 8)) {
+        c->leaf_warps = (int)value;
+        return DAFMM_OK;
+    }
     return fail(c, DAFMM_ERR_INVALID_ARG, "option");
 }
 
@@ -1071,6 +1290,72 @@ int dafmm_sync(dafmm_ctx* c, void* stream) {
         CK(c, cudaMemset(c->d_err, 0, sizeof(int)), "error flag");
         return fail(c, DAFMM_ERR_TIMEOUT, "a bounded device wait gave up (site " + std::to_string(flag) + ")");
     }
+    return DAFMM_OK;
+}
+
+int dafmm_graph_create(dafmm_tree* t, int order, int precision, double* phi, double* field, void* stream,
+                       dafmm_graph** out) {
+    if (!t || !out) return DAFMM_ERR_INVALID_ARG;
+    *out = nullptr;
+    dafmm_ctx* c = t->ctx;
+    if ((phi && !is_device_ptr(phi)) || (field && !is_device_ptr(field)))
+        return fail(c, DAFMM_ERR_INVALID_ARG, "graph outputs must be device memory");
+    CK(c, cudaSetDevice(c->device), "cudaSetDevice");
+    cudaStream_t s = (cudaStream_t)stream;
+    // one ordinary evaluation first: every table, expansion and scratch array gets allocated
+    int rc = dafmm_eval(t, order, 1.0, precision, phi, field, stream);
+    if (rc) return rc;
+    CK(c, cudaStreamSynchronize(s), "graph warm-up");
+    cudaStream_t cs = s;
+    if (!cs) CK(c, cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking), "capture stream");
+    const bool prof = c->profile;
+    c->profile = false;
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        rc = dafmm_eval(t, order, 1.0, precision, phi, field, cs);
+        e = cudaStreamEndCapture(cs, &g);
+    }
+    c->profile = prof;
+    if (!s) cudaStreamDestroy(cs);
+    if (rc || e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        return rc ? rc : cuda_fail(c, e, "graph capture");
+    }
+    cudaGraphExec_t x = nullptr;
+    e = cudaGraphInstantiate(&x, g, 0);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(g);
+        return cuda_fail(c, e, "graph instantiate");
+    }
+    size_t nodes = 0;
+    cudaGraphGetNodes(g, nullptr, &nodes);
+    dafmm_graph* gr = new dafmm_graph();
+    gr->ctx = c;
+    gr->tree = t;
+    gr->graph = g;
+    gr->exec = x;
+    gr->nodes = (int)nodes;
+    *out = gr;
+    return DAFMM_OK;
+}
+
+int dafmm_graph_launch(dafmm_graph* g, void* stream) {
+    if (!g) return DAFMM_ERR_INVALID_ARG;
+    CK(g->ctx, cudaSetDevice(g->ctx->device), "cudaSetDevice");
+    CK(g->ctx, cudaGraphLaunch(g->exec, (cudaStream_t)stream), "graph launch");
+    return DAFMM_OK;
+}
+
+int dafmm_graph_nodes(const dafmm_graph* g) { return g ? g->nodes : DAFMM_ERR_INVALID_ARG; }
+
+int dafmm_graph_free(dafmm_graph* g) {
+    if (!g) return DAFMM_ERR_INVALID_ARG;
+    cudaSetDevice(g->ctx->device);
+    cudaGraphExecDestroy(g->exec);
+    cudaGraphDestroy(g->graph);
+    delete g;
     return DAFMM_OK;
 }
 

@@ -8,6 +8,7 @@
 #include <vector>
 
 #include "internal.h"
+#include "arena.h"
 #include "tree_adaptive.h"
 
 struct dafmm_ctx {
@@ -24,9 +25,13 @@ struct dafmm_ctx {
     bool have_profile = false;
     int m2l_kernel = 0;       // 0 tensor cores, 1 SIMT
     int tc_mask = 7;          // FP32 mode: bit 0 M2L, bit 1 M2M, bit 2 L2L on the tensor cores
+    int leaf_warps = 4;       // adaptive leaf kernel: leaves (one warp each) per thread block
     int num_sms = 0;
     bool tc_capable = false;  // compute capability 10.x
     int* d_err = nullptr;     // device-side failure record of bounded waits
+    // pooled contexts: every allocation comes from one reservation (no cudaFree, no device sync)
+    char* arena_base = nullptr;
+    dafmm::OffsetArena arena;
 };
 
 struct Expansions {
@@ -59,6 +64,12 @@ struct dafmm_tree {
     bool adaptive = false;
     int nbox = 1, maxlev = 0, cap = 0, max_leaf = 0;
     std::vector<int> level_start;   // first box of each level, plus the end
+    int nroots = 1;                 // trees in the forest (one root box each)
+    std::vector<double> rootdom;    // 4 per tree: x0, y0, z0, size
+    std::vector<int64_t> root_offs; // particles of tree r: [root_offs[r], root_offs[r+1]) in input order
+    double* d_rootdom = nullptr;
+    double4* a_geom = nullptr;      // per box: centre and width
+    int* a_root = nullptr;
     int *a_level = nullptr, *a_ijk = nullptr, *a_parent = nullptr, *a_child = nullptr;
     int *a_pbeg = nullptr, *a_pend = nullptr, *a_colleague = nullptr;
     int *u_ptr = nullptr, *u_idx = nullptr, *w_ptr = nullptr, *w_idx = nullptr, *x_ptr = nullptr, *x_idx = nullptr;
@@ -90,4 +101,18 @@ inline TreeView make_view(const dafmm_tree* t) {
     tv.leaf_start = t->leaf_start;
     return tv;
 }
+}  // namespace dafmm
+
+struct dafmm_graph {
+    dafmm_ctx* ctx = nullptr;
+    dafmm_tree* tree = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int nodes = 0;
+};
+
+namespace dafmm {
+// device allocation through a context (its budget or pool); used by other runtime units
+int ctx_alloc(dafmm_ctx* c, void** p, size_t bytes, const char* what);
+void ctx_free(dafmm_ctx* c, void* p, size_t bytes);
 }  // namespace dafmm

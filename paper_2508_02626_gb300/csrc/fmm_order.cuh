@@ -492,13 +492,14 @@ __global__ void __launch_bounds__(128) k_leaf(TreeView tv, const double* __restr
 }
 
 // ---- adaptive trees ---------------------------------------------------------------------------
-// Box geometry of an adaptive box: width size/2^level, centre from its integer coordinates.
+// Box geometry of an adaptive box (centre and width, precomputed per box at build time).
 __device__ __forceinline__ void abox_geom(const AdaptiveView& av, int b, double& cx, double& cy, double& cz,
                                           double& h) {
-    h = ldexp(av.size, -av.level[b]);
-    cx = av.x0 + ((double)av.ijk[3 * b] + 0.5) * h;
-    cy = av.y0 + ((double)av.ijk[3 * b + 1] + 0.5) * h;
-    cz = av.z0 + ((double)av.ijk[3 * b + 2] + 0.5) * h;
+    const double4 g = av.geom[b];
+    cx = g.x;
+    cy = g.y;
+    cz = g.z;
+    h = g.w;
 }
 
 __device__ __forceinline__ bool abox_is_leaf(const AdaptiveView& av, int b) {
@@ -609,7 +610,7 @@ __global__ void __launch_bounds__(256) k_m2m_a(ShiftTab tab, AdaptiveView av, in
 template <class T, class Src>
 __global__ void __launch_bounds__(256) k_m2l_a(const T* __restrict__ K, AdaptiveView av, const int* __restrict__ tg,
                                                const int* __restrict__ grp_ptr, int grp0, const Src* __restrict__ M,
-                                               double* __restrict__ L, double inv_h) {
+                                               double* __restrict__ L) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* src = reinterpret_cast<T*>(smem_raw);  // [32][NCP + 1]
     __shared__ int sidx[32];
@@ -662,6 +663,7 @@ __global__ void __launch_bounds__(256) k_m2l_a(const T* __restrict__ K, Adaptive
     const int ti = t0 + lane;
     if (ti < g1) {
         const int t = tg[ti];
+        const double inv_h = 1.0 / av.geom[t].w;  // the target box's width (each tree has its own)
 #pragma unroll
         for (int j = 0; j < SH_ROWS; ++j) {
             const int b = w + 8 * j;
@@ -767,7 +769,7 @@ __global__ void __launch_bounds__(256) k_l2l_a(ShiftTab tab, AdaptiveView av, in
 
 // leaves: P2P over the U list, M2P over the W list, L2P of the leaf's local expansion
 template <class T>
-__global__ void __launch_bounds__(128) k_leaf_a(AdaptiveView av, const int* __restrict__ leaves, int nleaves,
+__global__ void __launch_bounds__(256) k_leaf_a(AdaptiveView av, const int* __restrict__ leaves, int nleaves,
                                                 const double* __restrict__ L, const double* __restrict__ M,
                                                 double* __restrict__ phi, double* __restrict__ field) {
     const int lane = threadIdx.x;
@@ -1066,18 +1068,18 @@ static cudaError_t m2m_a_launch(const OrderData& od, const AdaptiveView& av, int
 
 static cudaError_t m2l_a_launch(const OrderData& od, const AdaptiveView& av, int prec, const int* tg,
                                 const int* grp_ptr, int grp0, int max_group, const double* M, const float* Mf,
-                                double* L, double inv_h, cudaStream_t s) {
+                                double* L, cudaStream_t s) {
     if (max_group == 0) return cudaSuccess;
     dim3 grd((max_group + 31) / 32, 8);
     cudaError_t e;
     if (prec == DAFMM_FP64) {
         const size_t smem = (size_t)32 * (NCP + 1) * 8;
         if ((e = set_smem(k_m2l_a<double, double>, smem)) != cudaSuccess) return e;
-        k_m2l_a<double, double><<<grd, 256, smem, s>>>(od.K64, av, tg, grp_ptr, grp0, M, L, inv_h);
+        k_m2l_a<double, double><<<grd, 256, smem, s>>>(od.K64, av, tg, grp_ptr, grp0, M, L);
     } else {
         const size_t smem = (size_t)32 * (NCP + 1) * 4;
         if ((e = set_smem(k_m2l_a<float, float>, smem)) != cudaSuccess) return e;
-        k_m2l_a<float, float><<<grd, 256, smem, s>>>(od.K32, av, tg, grp_ptr, grp0, Mf, L, inv_h);
+        k_m2l_a<float, float><<<grd, 256, smem, s>>>(od.K32, av, tg, grp_ptr, grp0, Mf, L);
     }
     return cudaGetLastError();
 }
@@ -1119,9 +1121,10 @@ static cudaError_t l2l_a_launch(const OrderData& od, const AdaptiveView& av, int
 }
 
 static cudaError_t leaf_a_launch(const AdaptiveView& av, const int* leaves, int nleaves, int prec, const double* L,
-                                 const double* M, double* phi, double* field, cudaStream_t s) {
+                                 const double* M, double* phi, double* field, int warps, cudaStream_t s) {
     if (nleaves == 0) return cudaSuccess;
-    dim3 blk(32, 4), grd((nleaves + 3) / 4);
+    warps = warps < 1 ? 1 : (warps > 8 ? 8 : warps);
+    dim3 blk(32, warps), grd((nleaves + warps - 1) / warps);
     if (prec == DAFMM_FP64) k_leaf_a<double><<<grd, blk, 0, s>>>(av, leaves, nleaves, L, M, phi, field);
     else k_leaf_a<float><<<grd, blk, 0, s>>>(av, leaves, nleaves, L, M, phi, field);
     return cudaGetLastError();

@@ -56,6 +56,7 @@ struct OrderData {
     int* l2l_rowptr = nullptr; unsigned short* l2l_col = nullptr; unsigned char* l2l_par = nullptr;
     double* l2l_val = nullptr; float* l2l_valf = nullptr;
     int* mul_rowptr = nullptr; ushort2* mul_pairs = nullptr; short* mul_minus = nullptr;
+    size_t mul_npairs = 0;
     double* K64 = nullptr;        // [343][nc][ncp]: K^_v[b][a] (scaled M2L, Eq. 5)
     float* K32 = nullptr;         // same in FP32
     float* Khi = nullptr;         // [343][npt][ncp] TF32 high / low parts for the tensor-core M2L
@@ -103,11 +104,11 @@ struct OrderOps {
     cudaError_t (*p2m_a)(const AdaptiveView&, const int* leaves, int nleaves, int prec, double* M, cudaStream_t);
     cudaError_t (*m2m_a)(const OrderData&, const AdaptiveView&, int prec, int lb, int le, double* M, cudaStream_t);
     cudaError_t (*m2l_a)(const OrderData&, const AdaptiveView&, int prec, const int* tg, const int* grp_ptr, int grp0,
-                         int max_group, const double* M, const float* Mf, double* L, double inv_h, cudaStream_t);
+                         int max_group, const double* M, const float* Mf, double* L, cudaStream_t);
     cudaError_t (*p2l_a)(const AdaptiveView&, int prec, int lb, int le, double* L, cudaStream_t);
     cudaError_t (*l2l_a)(const OrderData&, const AdaptiveView&, int prec, int lb, int le, double* L, cudaStream_t);
     cudaError_t (*leaf_a)(const AdaptiveView&, const int* leaves, int nleaves, int prec, const double* L,
-                          const double* M, double* phi, double* field, cudaStream_t);
+                          const double* M, double* phi, double* field, int warps, cudaStream_t);
 };
 
 const OrderOps* order_ops(int p);

@@ -10,7 +10,9 @@
 //   X (P2L)    : for a box b, the leaves c coarser than b that are adjacent to parent(b) and
 //                not adjacent to b (exactly the boxes whose W list holds b).
 // Particles are sorted by 63-bit Morton keys of their 21-bit integer coordinates, so every
-// box is a contiguous particle range.
+// box is a contiguous particle range.  A forest holds several independent trees (one root
+// box each, level 0): the particles are grouped by tree and sorted inside each tree, and no
+// list ever crosses trees, since every relation is derived from the parent's colleagues.
 #include <cuda_runtime.h>
 
 #include "internal.h"
@@ -36,21 +38,127 @@ __device__ inline uint64_t spread3(uint32_t v) {
     return x;
 }
 
-__global__ void k_morton_keys(const double* __restrict__ xyz, int64_t n, double x0, double y0, double z0,
-                              double scale, uint64_t* keys, int* vals) {
+// tree of particle i: the last r with offs[r] <= i
+__device__ inline int tree_of(const int* offs, int nroots, int i) {
+    int lo = 0, hi = nroots - 1;
+    while (lo < hi) {
+        const int m = (lo + hi + 1) >> 1;
+        if (offs[m] <= i) lo = m;
+        else hi = m - 1;
+    }
+    return lo;
+}
+
+__global__ void k_morton_keys(const double* __restrict__ xyz, int64_t n, const int* __restrict__ offs, int nroots,
+                              const double* __restrict__ rootdom, uint64_t* keys, int* vals) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const uint32_t a = quantize_a(xyz[3 * i], x0, scale);
-    const uint32_t b = quantize_a(xyz[3 * i + 1], y0, scale);
-    const uint32_t c = quantize_a(xyz[3 * i + 2], z0, scale);
+    const int r = nroots > 1 ? tree_of(offs, nroots, (int)i) : 0;
+    const double* d = rootdom + 4 * r;
+    const double scale = ldexp(1.0, kQBits) / d[3];
+    const uint32_t a = quantize_a(xyz[3 * i], d[0], scale);
+    const uint32_t b = quantize_a(xyz[3 * i + 1], d[1], scale);
+    const uint32_t c = quantize_a(xyz[3 * i + 2], d[2], scale);
     keys[i] = spread3(a) | (spread3(b) << 1) | (spread3(c) << 2);
     vals[i] = (int)i;
 }
 
-cudaError_t launch_morton_keys(const double* xyz, int64_t n, double x0, double y0, double z0, double scale,
+cudaError_t launch_morton_keys(const double* xyz, int64_t n, const int* offs, int nroots, const double* rootdom,
                                uint64_t* keys, int* vals, cudaStream_t s) {
     if (n == 0) return cudaSuccess;
-    k_morton_keys<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(xyz, n, x0, y0, z0, scale, keys, vals);
+    k_morton_keys<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(xyz, n, offs, nroots, rootdom, keys, vals);
+    return cudaGetLastError();
+}
+
+__global__ void k_tree_keys(const int* __restrict__ perm, int64_t n, const int* __restrict__ offs, int nroots,
+                            uint64_t* tkeys, int* pos) {
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    tkeys[t] = (uint64_t)tree_of(offs, nroots, perm[t]);
+    pos[t] = (int)t;
+}
+
+cudaError_t launch_tree_keys(const int* perm, int64_t n, const int* offs, int nroots, uint64_t* tkeys, int* pos,
+                             cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    k_tree_keys<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(perm, n, offs, nroots, tkeys, pos);
+    return cudaGetLastError();
+}
+
+__global__ void k_apply_order(const int* __restrict__ pos, int64_t n, const int* __restrict__ perm_in,
+                              const uint64_t* __restrict__ keys_in, int* perm_out, uint64_t* keys_out) {
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    const int j = pos[t];
+    perm_out[t] = perm_in[j];
+    keys_out[t] = keys_in[j];
+}
+
+cudaError_t launch_apply_order(const int* pos, int64_t n, const int* perm_in, const uint64_t* keys_in, int* perm_out,
+                               uint64_t* keys_out, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    k_apply_order<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(pos, n, perm_in, keys_in, perm_out, keys_out);
+    return cudaGetLastError();
+}
+
+// order-preserving map of a double to an unsigned integer (for atomic min/max)
+__device__ inline unsigned long long ordered_bits(double v) {
+    const unsigned long long u = (unsigned long long)__double_as_longlong(v);
+    return (u >> 63) ? ~u : (u | 0x8000000000000000ull);
+}
+
+__global__ void __launch_bounds__(256) k_bbox_roots(const double* __restrict__ xyz, const int* __restrict__ offs,
+                                                    unsigned long long* bb) {
+    const int r = blockIdx.x;
+    const int b = offs[r], e = offs[r + 1];
+    unsigned long long mn[3] = {~0ull, ~0ull, ~0ull}, mx[3] = {0ull, 0ull, 0ull};
+    for (int i = b + threadIdx.x; i < e; i += blockDim.x)
+        for (int d = 0; d < 3; ++d) {
+            const unsigned long long u = ordered_bits(xyz[3 * (size_t)i + d]);
+            mn[d] = u < mn[d] ? u : mn[d];
+            mx[d] = u > mx[d] ? u : mx[d];
+        }
+    for (int d = 0; d < 3; ++d) {
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long a = __shfl_xor_sync(0xffffffffu, mn[d], o);
+            const unsigned long long c = __shfl_xor_sync(0xffffffffu, mx[d], o);
+            mn[d] = a < mn[d] ? a : mn[d];
+            mx[d] = c > mx[d] ? c : mx[d];
+        }
+        if ((threadIdx.x & 31) == 0) {
+            atomicMin(&bb[6 * r + d], mn[d]);
+            atomicMax(&bb[6 * r + 3 + d], mx[d]);
+        }
+    }
+}
+
+__global__ void k_bbox_init(unsigned long long* bb, int nroots) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < 6 * nroots) bb[i] = (i % 6) < 3 ? ~0ull : 0ull;
+}
+
+cudaError_t launch_bbox_roots(const double* xyz, const int* offs, int nroots, unsigned long long* bb, cudaStream_t s) {
+    if (nroots == 0) return cudaSuccess;
+    k_bbox_init<<<(6 * nroots + 255) / 256, 256, 0, s>>>(bb, nroots);
+    k_bbox_roots<<<nroots, 256, 0, s>>>(xyz, offs, bb);
+    return cudaGetLastError();
+}
+
+__global__ void k_box_geometry(const int* __restrict__ root, const int* __restrict__ level,
+                               const int* __restrict__ ijk, const double* __restrict__ rootdom, int nbox,
+                               double4* geom) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nbox) return;
+    const double* d = rootdom + 4 * root[b];
+    const double h = ldexp(d[3], -level[b]);
+    geom[b] = make_double4(d[0] + ((double)ijk[3 * b] + 0.5) * h, d[1] + ((double)ijk[3 * b + 1] + 0.5) * h,
+                           d[2] + ((double)ijk[3 * b + 2] + 0.5) * h, h);
+}
+
+cudaError_t launch_box_geometry(const int* root, const int* level, const int* ijk, const double* rootdom, int nbox,
+                                double4* geom, cudaStream_t s) {
+    if (nbox == 0) return cudaSuccess;
+    k_box_geometry<<<(nbox + 255) / 256, 256, 0, s>>>(root, level, ijk, rootdom, nbox, geom);
     return cudaGetLastError();
 }
 
@@ -94,6 +202,7 @@ __global__ void k_split_fill(AdaptiveBuild ab, int lb, int le, int level, const 
     for (int c = 0; c < 8; ++c) {
         const int e = first_digit_ge(ab.keys, s, pe, shift, c + 1);
         if (e > s) {
+            ab.root[k] = ab.root[b];
             ab.level[k] = level + 1;
             ab.ijk[3 * k] = 2 * ab.ijk[3 * b] + (c & 1);
             ab.ijk[3 * k + 1] = 2 * ab.ijk[3 * b + 1] + ((c >> 1) & 1);
@@ -360,16 +469,14 @@ cudaError_t launch_list_fill(AdaptiveBuild ab, int nbox, const int* pu, const in
 // ---- gather of the sorted particles: FP64 SoA and FP32 offsets in each particle's own leaf ----
 __global__ void k_gather_adaptive(const double* __restrict__ xyz, const double* __restrict__ q,
                                   const int* __restrict__ perm, AdaptiveBuild ab, const int* __restrict__ leaves,
-                                  int nleaves, double x0, double y0, double z0, double size, double* x, double* y,
-                                  double* z, double* qs, float4* xq) {
+                                  int nleaves, const double4* __restrict__ geom, double* x, double* y, double* z,
+                                  double* qs, float4* xq) {
     const int li = blockIdx.x;
     if (li >= nleaves) return;
     const int b = leaves[li];
-    const int lev = ab.level[b];
-    const double h = ldexp(size, -lev), ih = 1.0 / h;
-    const double cx = x0 + ((double)ab.ijk[3 * b] + 0.5) * h;
-    const double cy = y0 + ((double)ab.ijk[3 * b + 1] + 0.5) * h;
-    const double cz = z0 + ((double)ab.ijk[3 * b + 2] + 0.5) * h;
+    const double4 g = geom[b];
+    const double ih = 1.0 / g.w;
+    const double cx = g.x, cy = g.y, cz = g.z;
     for (int t = ab.pbeg[b] + threadIdx.x; t < ab.pend[b]; t += blockDim.x) {
         const int i = perm[t];
         const double px = xyz[3 * i], py = xyz[3 * i + 1], pz = xyz[3 * i + 2], pq = q[i];
@@ -379,11 +486,10 @@ __global__ void k_gather_adaptive(const double* __restrict__ xyz, const double* 
 }
 
 cudaError_t launch_gather_adaptive(const double* xyz, const double* q, const int* perm, AdaptiveBuild ab,
-                                   const int* leaves, int nleaves, const double* dom, double* x, double* y, double* z,
-                                   double* qs, float4* xq, cudaStream_t s) {
+                                   const int* leaves, int nleaves, const double4* geom, double* x, double* y,
+                                   double* z, double* qs, float4* xq, cudaStream_t s) {
     if (nleaves == 0) return cudaSuccess;
-    k_gather_adaptive<<<nleaves, 128, 0, s>>>(xyz, q, perm, ab, leaves, nleaves, dom[0], dom[1], dom[2], dom[3], x, y,
-                                               z, qs, xq);
+    k_gather_adaptive<<<nleaves, 128, 0, s>>>(xyz, q, perm, ab, leaves, nleaves, geom, x, y, z, qs, xq);
     return cudaGetLastError();
 }
 

@@ -11,6 +11,7 @@ constexpr int kMaxAdaptiveDepth = 20;
 
 struct AdaptiveBuild {
     const uint64_t* keys;  // sorted Morton keys of the particles
+    int* root;             // per box: the tree (root box) it belongs to
     int* level;            // per box
     int* ijk;              // per box, 3 integer coordinates at its level
     int* parent;           // -1 for the root
@@ -36,14 +37,25 @@ struct AdaptiveView {
     const int* w_idx;
     const int* x_ptr;      // CSR per box
     const int* x_idx;
-    double x0, y0, z0, size;
+    const double4* geom;   // per box: centre x, y, z and width h
     const double *x, *y, *z, *q;  // sorted particles
     const float4* xq;             // offsets in the particle's own leaf, in leaf widths, and q
     const int* perm;
 };
 
-cudaError_t launch_morton_keys(const double* xyz, int64_t n, double x0, double y0, double z0, double scale,
+// Morton keys of particles grouped by tree: particles [offs[r], offs[r+1]) belong to tree r,
+// whose root cube is rootdom[4r .. 4r+3] = {x0, y0, z0, size}
+cudaError_t launch_morton_keys(const double* xyz, int64_t n, const int* offs, int nroots, const double* rootdom,
                                uint64_t* keys, int* vals, cudaStream_t s);
+// after the Morton sort: regroup by tree, keeping the Morton order inside each tree (stable)
+cudaError_t launch_tree_keys(const int* perm, int64_t n, const int* offs, int nroots, uint64_t* tkeys, int* pos,
+                             cudaStream_t s);
+cudaError_t launch_apply_order(const int* pos, int64_t n, const int* perm_in, const uint64_t* keys_in, int* perm_out,
+                               uint64_t* keys_out, cudaStream_t s);
+// per-tree bounding boxes as ordered-integer min/max (6 per tree), one CTA per tree
+cudaError_t launch_bbox_roots(const double* xyz, const int* offs, int nroots, unsigned long long* bb, cudaStream_t s);
+cudaError_t launch_box_geometry(const int* root, const int* level, const int* ijk, const double* rootdom, int nbox,
+                                double4* geom, cudaStream_t s);
 cudaError_t launch_split(AdaptiveBuild ab, int lb, int le, int level, int max_leaf, int max_depth, int* nch,
                          cudaStream_t s);
 cudaError_t launch_split_fill(AdaptiveBuild ab, int lb, int le, int level, const int* offs, int first_new,
@@ -56,8 +68,8 @@ cudaError_t launch_list_count(AdaptiveBuild ab, int nbox, int* cu, int* cw, int*
 cudaError_t launch_list_fill(AdaptiveBuild ab, int nbox, const int* pu, const int* pw, const int* px, int* iu, int* iw,
                              int* ix, int* err, cudaStream_t s);
 cudaError_t launch_gather_adaptive(const double* xyz, const double* q, const int* perm, AdaptiveBuild ab,
-                                   const int* leaves, int nleaves, const double* dom, double* x, double* y, double* z,
-                                   double* qs, float4* xq, cudaStream_t s);
+                                   const int* leaves, int nleaves, const double4* geom, double* x, double* y,
+                                   double* z, double* qs, float4* xq, cudaStream_t s);
 
 cudaError_t launch_leaf_flags(const int* child, int nbox, int* flags, cudaStream_t s);
 cudaError_t launch_scatter_flagged(const int* flags, const int* offs, int nbox, int* out, cudaStream_t s);

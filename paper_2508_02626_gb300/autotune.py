@@ -3,7 +3,7 @@
 The leaf size s (a box with more than s particles is split, Sec. 3.5) trades near-field work
 (P2P over U lists, growing with s) against far-field work (more boxes, more M2L).  The paper
 sweeps s on its CPU and tabulates the fastest value per order and particle count (Sec. 3.5,
-leaf-size table: 64 at p = 2, 128 at p = 4, 256 at p = 6 and 8, 512 at p = 10 for large N).
+Table 10: 64 at p = 2, 128 at p = 4, 256 at p = 6 and 8, 512 at p = 10 for large N).
 On the GPU the balance is different -- P2P runs at FP32 ALU rate, M2L on the tensor or SIMT
 pipes -- so the tuner times candidate values around the paper's choice on the actual
 workload (a forest of the problems to solve) together with the near-field kernel's tile
@@ -20,7 +20,7 @@ import numpy as np
 
 from . import binding as B
 
-# fastest leaf size of the paper's CPU sweep for large N, per order (Sec. 3.5)
+# fastest leaf size of the paper's CPU sweep for large N, per order (Table 10)
 PAPER_LEAF_SIZE = {2: 64, 4: 128, 6: 256, 8: 256, 10: 512}
 LEAF_WARPS = (2, 4, 8)
 

@@ -1,5 +1,5 @@
 """Autotuner host logic (no GPU): the candidate leaf sizes bracket the paper's tabulated
-optimum (Sec. 3.5), keys separate workloads by size class, and the JSON cache round-trips."""
+optimum (Table 10), keys separate workloads by size class, and the JSON cache round-trips."""
 import os
 
 from paper_2508_02626_gb300 import autotune as A

@@ -419,7 +419,7 @@ void free_adaptive(dafmm_ctx* c, dafmm_tree* t) {
     dev_free(c, t->grp_ptr, ((size_t)(t->maxlev + 1) * 8 + 1) * 4);
     if (t->a_exp_p >= 0) {
         const size_t cnt = (size_t)t->nbox * ncp_of(t->a_exp_p);
-        dev_free(c, t->aM, cnt * 8); dev_free(c, t->aL, cnt * 8); dev_free(c, t->aMf, cnt * 4);
+        dev_free(c, t->aM, cnt * 8); dev_free(c, t->aL, cnt * 8); dev_free(c, t->aMf, cnt * 8);
     }
     t->u_ptr = t->w_ptr = t->x_ptr = t->u_idx = t->w_idx = t->x_idx = t->leaves = t->grp_tg = t->grp_ptr = nullptr;
     t->a_geom = nullptr;
@@ -668,17 +668,18 @@ int ensure_adaptive_expansions(dafmm_tree* t, int p, cudaStream_t s) {
     dafmm_ctx* c = t->ctx;
     if (t->a_exp_p >= 0) {
         const size_t cnt = (size_t)t->nbox * ncp_of(t->a_exp_p);
-        dev_free(c, t->aM, cnt * 8); dev_free(c, t->aL, cnt * 8); dev_free(c, t->aMf, cnt * 4);
+        dev_free(c, t->aM, cnt * 8); dev_free(c, t->aL, cnt * 8); dev_free(c, t->aMf, cnt * 8);
         t->a_exp_p = -1;
     }
     const size_t cnt = (size_t)t->nbox * ncp_of(p);
     int rc;
     if ((rc = dev_alloc(c, (void**)&t->aM, cnt * 8, "multipoles"))) return rc;
     if ((rc = dev_alloc(c, (void**)&t->aL, cnt * 8, "locals"))) return rc;
-    if ((rc = dev_alloc(c, (void**)&t->aMf, cnt * 4, "multipoles (FP32)"))) return rc;
+    // FP32 multipoles, or their TF32 high parts followed by the low parts
+    if ((rc = dev_alloc(c, (void**)&t->aMf, cnt * 8, "multipoles (FP32)"))) return rc;
     CK(c, cudaMemsetAsync(t->aM, 0, cnt * 8, s), "memset");
     CK(c, cudaMemsetAsync(t->aL, 0, cnt * 8, s), "memset");
-    CK(c, cudaMemsetAsync(t->aMf, 0, cnt * 4, s), "memset");
+    CK(c, cudaMemsetAsync(t->aMf, 0, cnt * 8, s), "memset");
     t->a_exp_p = p;
     return DAFMM_OK;
 }
@@ -706,20 +707,58 @@ int eval_adaptive(dafmm_tree* t, int order, int precision, double* dphi, double*
             ++launches;
         }
         mark(2);
-        if (precision != DAFMM_FP64) {
-            const size_t cnt = (size_t)t->nbox * od.ncp;
+        const size_t cnt = (size_t)t->nbox * od.ncp;
+        const bool tc = precision != DAFMM_FP64 && c->m2l_kernel == 0 && c->tc_capable && order >= 2 &&
+                        (precision != DAFMM_FP32 || (c->tc_mask & 1));
+        if (tc) {
+            CK(c, tc_split_tf32(t->aM, t->aMf, t->aMf + cnt, cnt, s), "split");
+            ++launches;
+        } else if (precision != DAFMM_FP64) {
             k_to_float<<<(unsigned)std::min<size_t>((cnt + 255) / 256, 152 * 16), 256, 0, s>>>(t->aM, t->aMf, cnt);
             CK(c, cudaGetLastError(), "convert");
             ++launches;
         }
         mark(3);
-        for (int l = 2; l <= t->maxlev; ++l) {
-            if (l == t->maxlev) mark(4);
-            int mx = 0;
-            for (int o = 0; o < 8; ++o) mx = std::max(mx, t->grp_ptr_h[l * 8 + o + 1] - t->grp_ptr_h[l * 8 + o]);
-            CK(c, ops->m2l_a(od, av, precision, t->grp_tg, t->grp_ptr, l * 8, mx, t->aM, t->aMf, t->aL, s), "M2L");
-            CK(c, ops->p2l_a(av, precision, t->level_start[l], t->level_start[l + 1], t->aL, s), "P2L");
-            launches += 2;
+        if (tc) {
+            // every level in one launch of the gathered tensor-core contraction
+            mark(4);
+            TCGArgs a;
+            memset(&a, 0, sizeof(a));
+            a.a_hi = t->aMf;
+            a.a_lo = t->aMf + cnt;
+            a.b_hi = od.Khi;
+            a.b_lo = od.Klo;
+            a.nkey = kNumKeys;
+            a.tg = t->grp_tg;
+            a.parent = t->a_parent;
+            a.colleague = t->a_colleague;
+            a.child = t->a_child;
+            a.geom = t->a_geom;
+            a.out = t->aL;
+            a.err = c->d_err;
+            a.num_sms = c->num_sms;
+            for (int l = t->maxlev; l >= 2; --l)  // finest first
+                for (int o = 0; o < 8; ++o) {
+                    a.grp_start[a.ngroups] = t->grp_ptr_h[l * 8 + o];
+                    a.grp_count[a.ngroups] = t->grp_ptr_h[l * 8 + o + 1] - t->grp_ptr_h[l * 8 + o];
+                    a.grp_oct[a.ngroups] = o;
+                    ++a.ngroups;
+                }
+            CK(c, tcg_launch(order, a, s), "M2L (tensor cores)");
+            ++launches;
+            for (int l = 2; l <= t->maxlev; ++l) {
+                CK(c, ops->p2l_a(av, precision, t->level_start[l], t->level_start[l + 1], t->aL, s), "P2L");
+                ++launches;
+            }
+        } else {
+            for (int l = 2; l <= t->maxlev; ++l) {
+                if (l == t->maxlev) mark(4);
+                int mx = 0;
+                for (int o = 0; o < 8; ++o) mx = std::max(mx, t->grp_ptr_h[l * 8 + o + 1] - t->grp_ptr_h[l * 8 + o]);
+                CK(c, ops->m2l_a(od, av, precision, t->grp_tg, t->grp_ptr, l * 8, mx, t->aM, t->aMf, t->aL, s), "M2L");
+                CK(c, ops->p2l_a(av, precision, t->level_start[l], t->level_start[l + 1], t->aL, s), "P2L");
+                launches += 2;
+            }
         }
         mark(5);
         for (int l = 3; l <= t->maxlev; ++l) {

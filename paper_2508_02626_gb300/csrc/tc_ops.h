@@ -51,7 +51,54 @@ struct TCArgs {
     int num_sms;
 };
 
+// ---- gathered form (adaptive trees and forests) ----
+// Targets come in groups (boxes of one level and octant, contiguous in `tg`); the A rows of a
+// tile of 128 targets are gathered row by row, so any tree shape works.
+constexpr int kTcgMaxGroups = 8 * 21;
+
+struct TCGParams {
+    CUtensorMap b_hi;
+    CUtensorMap b_lo;
+    const float* a_hi;        // [nbox][ncp] TF32 parts of the multipoles
+    const float* a_lo;
+    const int* tg;            // target boxes, grouped
+    const int* parent;
+    const int* colleague;     // 27 per box
+    const int* child;         // 8 per box
+    const double4* geom;      // per box: centre and width (scale 1/width)
+    double* out;              // [nbox][ncp], written
+    int grp_start[kTcgMaxGroups];
+    int grp_count[kTcgMaxGroups];
+    int grp_oct[kTcgMaxGroups];
+    int tile_base[kTcgMaxGroups + 1];
+    int ngroups;
+    int ntiles;
+    int nhalf;
+    int* err;
+};
+
+struct TCGArgs {
+    const float* a_hi;
+    const float* a_lo;
+    const float* b_hi;        // [nkey][npt][ncp] TF32 parts of the M2L matrices
+    const float* b_lo;
+    int nkey;
+    const int* tg;
+    const int* parent;
+    const int* colleague;
+    const int* child;
+    const double4* geom;
+    double* out;
+    int ngroups;
+    int grp_start[kTcgMaxGroups];
+    int grp_count[kTcgMaxGroups];
+    int grp_oct[kTcgMaxGroups];
+    int* err;
+    int num_sms;
+};
+
 int tc_npt(int p);  // rows of the split matrix tables (nc padded to the MMA N granule)
+cudaError_t tcg_launch(int p, const TCGArgs& a, cudaStream_t s);
 cudaError_t tc_split_tf32(const double* src, float* hi, float* lo, size_t n, cudaStream_t s);
 cudaError_t tc_split_rows(const double* src, int nkey, int p, float* hi, float* lo, cudaStream_t s);
 cudaError_t tc_launch(int p, const TCArgs& a, cudaStream_t s);

@@ -183,3 +183,24 @@ def test_clustered_4e6_p10_sampled(ctx):
         phi, E = gpu_eval(ctx, x, q, dom, cfg["max_leaf"], cfg["order"], prec)
         assert rel(phi[tg], ref_phi) <= TOL[prec], (prec, rel(phi[tg], ref_phi))
         assert rel(E[tg], ref_E) <= TOL_E[prec], (prec, rel(E[tg], ref_E))
+
+
+@pytest.mark.parametrize("p", [2, 3, 4, 6, 8, 9, 10])
+def test_tensor_core_gathered_m2l(ctx, p):
+    """The gathered tcgen05 M2L (TF32 split products, sources gathered row by row) against the
+    SIMT FP32 M2L and the oracle, on a clustered tree with levels 2 to ~8 and partial tiles;
+    p = 9, 10 split the output columns in two halves."""
+    x, q = W.clustered(12000, seed=500 + p, charges="signed")
+    dom = O.bounding_cube(x)
+    ref_phi, ref_E = O.fmm(x, q, dom, p, max_leaf=20, max_depth=MAX_DEPTH)
+    for prec in ("mixed", "fp32"):
+        tc_phi, tc_E = gpu_eval(ctx, x, q, dom, 20, p, prec)
+        B.dafmm_set_option(ctx.h, B.DAFMM_OPT_M2L_KERNEL, 1)
+        try:
+            si_phi, si_E = gpu_eval(ctx, x, q, dom, 20, p, prec)
+        finally:
+            B.dafmm_set_option(ctx.h, B.DAFMM_OPT_M2L_KERNEL, 0)
+        assert rel(tc_phi, ref_phi) <= TOL[prec], (prec, rel(tc_phi, ref_phi))
+        assert rel(tc_E, ref_E) <= TOL_E[prec], (prec, rel(tc_E, ref_E))
+        assert rel(si_phi, ref_phi) <= TOL[prec]
+        assert rel(tc_phi, si_phi) <= TOL[prec]

@@ -373,6 +373,34 @@ __global__ void __launch_bounds__(256) k_m2l(const T* __restrict__ K, int l, con
 }
 
 // ---- leaves: P2P over the 27 neighbours + L2P --------------------------------------------------
+// 1/sqrt(x) of the PTX instruction rsqrt.approx.ftz.f32 (relative error about 2^-23, the
+// size of an FP32 rounding, so no Newton step is needed); 0 for x below the smallest normal
+// float, which covers coincident points (r = 0 contributes nothing, as everywhere else)
+__device__ __forceinline__ float rsqrt_or_zero(float x) {
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return x >= 1.17549435e-38f ? y : 0.f;
+}
+
+// sources [s0, s1) of the float4 leaf-frame array acting on the target (tx, ty, tz), in the
+// same frame: potential and field partial sums (the field without its sign convention)
+__device__ __forceinline__ void p2p_f32(const float4* __restrict__ xq, int s0, int s1, float tx, float ty, float tz,
+                                        float& sp, float& sx, float& sy, float& sz) {
+#pragma unroll 4
+    for (int s = s0; s < s1; ++s) {
+        const float4 ps = xq[s];
+        const float ex = tx - ps.x, ey = ty - ps.y, ez = tz - ps.z;
+        const float r2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
+        const float ir = rsqrt_or_zero(r2);
+        const float qr = ps.w * ir;
+        const float qr3 = qr * (ir * ir);
+        sp += qr;
+        sx = fmaf(qr3, ex, sx);
+        sy = fmaf(qr3, ey, sy);
+        sz = fmaf(qr3, ez, sz);
+    }
+}
+
 __device__ __forceinline__ void two_sum_add(float& hi, float& lo, float v) {
     const float s = hi + v;
     const float bp = s - hi;
@@ -437,18 +465,7 @@ __global__ void __launch_bounds__(128) k_leaf(TreeView tv, const double* __restr
                         for (int sb = s0; sb < s1; sb += 64) {
                             const int se = min(s1, sb + 64);
                             float sp = 0.f, sx = 0.f, sy = 0.f, sz = 0.f;
-                            for (int s = sb; s < se; ++s) {
-                                const float4 ps = tv.xq[s];
-                                const float ex = tx - ps.x, ey = ty - ps.y, ez = tz - ps.z;
-                                const float r2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
-                                if (r2 > 0.f) {
-                                    const float ir = dafmm_rsqrt(r2);
-                                    const float qr = ps.w * ir;
-                                    const float qr3 = qr * ir * ir;
-                                    sp += qr;
-                                    sx = fmaf(qr3, ex, sx); sy = fmaf(qr3, ey, sy); sz = fmaf(qr3, ez, sz);
-                                }
-                            }
+                            p2p_f32(tv.xq, sb, se, tx, ty, tz, sp, sx, sy, sz);
                             two_sum_add(ph, pl, sp);
                             two_sum_add(xh, xl, sx);
                             two_sum_add(yh, yl, sy);
@@ -818,18 +835,17 @@ __global__ void __launch_bounds__(256) k_leaf_a(AdaptiveView av, const int* __re
                 for (int sbeg = av.pbeg[sb]; sbeg < av.pend[sb]; sbeg += 64) {
                     const int send = min(av.pend[sb], sbeg + 64);
                     float sp = 0.f, sx = 0.f, sy = 0.f, sz = 0.f;
+#pragma unroll 4
                     for (int sidx = sbeg; sidx < send; ++sidx) {
                         const float4 ps = av.xq[sidx];
                         const float ex = pt.x - fmaf(r, ps.x, offx), ey = pt.y - fmaf(r, ps.y, offy),
                                     ez = pt.z - fmaf(r, ps.z, offz);
                         const float r2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
-                        if (r2 > 0.f) {
-                            const float ir = dafmm_rsqrt(r2);
-                            const float qr = ps.w * ir;
-                            const float qr3 = qr * ir * ir;
-                            sp += qr;
-                            sx = fmaf(qr3, ex, sx); sy = fmaf(qr3, ey, sy); sz = fmaf(qr3, ez, sz);
-                        }
+                        const float ir = rsqrt_or_zero(r2);
+                        const float qr = ps.w * ir;
+                        const float qr3 = qr * (ir * ir);
+                        sp += qr;
+                        sx = fmaf(qr3, ex, sx); sy = fmaf(qr3, ey, sy); sz = fmaf(qr3, ez, sz);
                     }
                     two_sum_add(ph, pl, sp);
                     two_sum_add(xh, xl, sx);

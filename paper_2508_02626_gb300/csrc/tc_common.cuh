@@ -1,0 +1,248 @@
+// tc_common.cuh -- pieces shared by the tensor-core contraction kernels (tc_ops.cu: operands
+// by TMA boxes; tc_gather.cu: source rows gathered per target): PTX wrappers for mbarriers,
+// TMA, tcgen05 MMA / TMEM, the per-order tile configuration, the term sequence of a work
+// item, the TF32 split, and the host-side tensor-map encoding.
+#pragma once
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "internal.h"
+#include "tc_ops.h"
+
+namespace dafmm {
+namespace tc {
+
+// ---- PTX wrappers ----------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+constexpr long long kWaitLimit = 1ll << 24;  // try_wait rounds before a wait is declared stuck
+
+// bounded wait; on expiry records `code` in *err and returns false
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* err, int code) {
+    for (long long i = 0; i < kWaitLimit; ++i) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (i > 64) __nanosleep(64);
+    }
+    atomicExch(err, code);
+    return false;
+}
+
+__device__ __forceinline__ void tma_load_5d(uint32_t dst, const CUtensorMap* map, uint32_t bar, int c0, int c1,
+                                            int c2, int c3, int c4) {
+    asm volatile(
+        "cp.async.bulk.tensor.5d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5, %6, %7}], "
+        "[%2];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4)
+        : "memory");
+}
+
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, uint32_t bar, int c0, int c1,
+                                            int c2) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(
+            dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(c0), "r"(c1), "r"(c2)
+        : "memory");
+}
+
+__device__ __forceinline__ void prefetch_map(const CUtensorMap* map) {
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
+}
+
+// shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 bytes apart
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t addr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((addr >> 4) & 0x3FFFu);        // start address
+    d |= (uint64_t)1 << 16;                         // leading byte offset (unused for swizzled K-major)
+    d |= (uint64_t)(1024 >> 4) << 32;               // stride byte offset: next 8-row group
+    d |= (uint64_t)1 << 46;                         // descriptor version for tcgen05
+    d |= (uint64_t)2 << 61;                         // swizzle mode: 128-byte
+    return d;
+}
+
+// instruction descriptor of kind::tf32: D = F32, A = B = TF32, both K-major, M x N
+__host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
+    return (1u << 4)                      // D format F32
+           | (2u << 7) | (2u << 10)       // A, B format TF32
+           | ((uint32_t)(N >> 3) << 17)   // N / 8
+           | ((uint32_t)(M >> 4) << 24);  // M / 16
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void fence_after_sync() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_before_sync() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+
+// TMEM loads: the load and tcgen05.wait::ld sit in one asm statement, so the outputs are
+// defined only after the wait and no use of a register can be scheduled before it landed.
+// 32 lanes x 16 columns, load and wait in one statement
+__device__ __forceinline__ void tmem_ld16w(uint32_t taddr, uint32_t (&r)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, "
+        "[%16];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr)
+        : "memory");
+}
+
+
+// ---- configuration per order ------------------------------------------------------------------
+template <int P>
+struct Cfg {
+    static constexpr int NC = ncoef_of(P);
+    static constexpr int NCP = ncp_of(P);
+    static constexpr int NPF = (NC + 15) / 16 * 16;               // N padded to the MMA granule
+    static constexpr int NHALF = NPF > 192 ? 2 : 1;                // N split: <= 192 register sums per thread
+    static constexpr int NP = NHALF == 1 ? NPF : (NPF / 2 + 15) / 16 * 16;
+    static constexpr int NKC = (NCP + 31) / 32;                    // K chunks of 32 (128 bytes)
+    static constexpr int KSTEPS_LAST = (NCP - 32 * (NKC - 1)) / 8; // K steps of 8 in the last chunk
+    static constexpr int A_BYTES = 128 * 128;
+    static constexpr int B_BYTES = NP * 128;
+    static constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
+    static constexpr int SMEM_AVAIL = 227 * 1024 - 2048;
+    static constexpr int STAGES = (SMEM_AVAIL / STAGE_BYTES) > 4 ? 4 : (SMEM_AVAIL / STAGE_BYTES);
+    static constexpr int TMEM_COLS = 2 * NP <= 256 ? 256 : 512;
+    static constexpr uint32_t IDESC = idesc_tf32(128, NP);
+    static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
+    static_assert(NP % 16 == 0 && NP >= 16 && NP <= 192, "MMA N");
+    static_assert(STAGES >= 2, "pipeline depth");
+    static_assert(2 * NP <= TMEM_COLS, "TMEM double buffer");
+};
+
+// a work item of the uniform-tree kernel: level index, target octant, child octant (L2L),
+// tile origin in slab coordinates, output half
+struct WorkItem {
+    int li, oct, c, px0, py0, pz0, half;
+};
+
+// the terms of a work item, in a fixed order.  M2L: the displacements v_d in
+// [-3 + o_d, 2 + o_d] that are not all |v_d| <= 1 (189 of 216); M2M: the 8 child octants;
+// L2L: one term.
+struct Terms {
+    int mode, o[3], v[3], j;
+    __device__ void first(int mode_, int oct) {
+        mode = mode_;
+        j = 0;
+        o[0] = oct & 1; o[1] = (oct >> 1) & 1; o[2] = (oct >> 2) & 1;
+        v[0] = -3 + o[0]; v[1] = -3 + o[1]; v[2] = -3 + o[2];
+    }
+    __device__ bool next() {  // advance to the next raw term; false at the end
+        if (mode == kTcM2M) return ++j < 8;
+        if (mode == kTcL2L) return false;
+        if (++v[2] <= 2 + o[2]) return true;
+        v[2] = -3 + o[2];
+        if (++v[1] <= 2 + o[1]) return true;
+        v[1] = -3 + o[1];
+        if (++v[0] <= 2 + o[0]) return true;
+        return false;
+    }
+    __device__ bool valid() const {
+        return mode != kTcM2L || abs(v[0]) > 1 || abs(v[1]) > 1 || abs(v[2]) > 1;
+    }
+    // A box start (slab coordinates and slab) and the T matrix index of the current term
+    __device__ void source(const WorkItem& it, int& x, int& y, int& z, int& slab, int& key) const {
+        if (mode == kTcM2L) {
+            int sc[3], a[3];
+            for (int d = 0; d < 3; ++d) {
+                const int dd = o[d] - v[d];  // in [-2, 3]
+                sc[d] = dd & 1;
+                a[d] = (dd - sc[d]) >> 1;    // in {-1, 0, 1}
+            }
+            x = it.px0 + a[0]; y = it.py0 + a[1]; z = it.pz0 + a[2];
+            slab = sc[0] | (sc[1] << 1) | (sc[2] << 2);
+            key = (v[0] + 3) * 49 + (v[1] + 3) * 7 + (v[2] + 3);
+        } else if (mode == kTcM2M) {
+            x = it.px0; y = it.py0; z = it.pz0;
+            slab = j;
+            key = j;
+        } else {
+            x = it.px0; y = it.py0; z = it.pz0;
+            slab = it.oct;
+            key = it.c;
+        }
+    }
+};
+
+
+// round to the nearest TF32 value (10 explicit mantissa bits) and clear the 13 low bits, so
+// that hi + lo reproduces the operand exactly as the tensor core reads it
+__device__ __forceinline__ float to_tf32(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r & 0xFFFFE000u);
+}
+
+
+}  // namespace tc
+
+// ---- host side: tensor maps --------------------------------------------------------------------
+inline PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        cudaDriverEntryPointQueryResult q;
+        void* f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+        else
+            cudaGetLastError();
+    }
+    return fn;
+}
+
+
+// 3-D map (coef, row, matrix) over [nkey][npt][ncp] with boxes of np rows
+inline bool encode_rows(PFN_cuTensorMapEncodeTiled_v12000 enc, CUtensorMap* map, const float* base, int ncp, int npt,
+                        int nkey, int np) {
+    const cuuint64_t dims[3] = {(cuuint64_t)ncp, (cuuint64_t)npt, (cuuint64_t)nkey};
+    const cuuint64_t strides[2] = {(cuuint64_t)ncp * 4, (cuuint64_t)ncp * 4 * npt};
+    const cuuint32_t box[3] = {32, (cuuint32_t)np, 1};
+    const cuuint32_t es[3] = {1, 1, 1};
+    return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, (void*)base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+               CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+           CUDA_SUCCESS;
+}
+
+
+}  // namespace dafmm

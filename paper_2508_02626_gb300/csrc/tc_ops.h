@@ -54,7 +54,7 @@ struct TCArgs {
 // ---- gathered form (adaptive trees and forests) ----
 // Targets come in groups (boxes of one level and octant, contiguous in `tg`); the A rows of a
 // tile of 128 targets are gathered row by row, so any tree shape works.
-constexpr int kTcgMaxGroups = 8 * 21;
+constexpr int kTcgMaxGroups = 8 * 21;  // (level, octant) groups of a launch
 
 struct TCGParams {
     CUtensorMap b_hi;
@@ -67,6 +67,9 @@ struct TCGParams {
     const int* child;         // 8 per box
     const double4* geom;      // per box: centre and width (scale 1/width)
     double* out;              // [nbox][ncp], written
+    // work groups in launch order: octant-major (the CTAs running at the same time share one
+    // octant's 189 matrices in L2), then level; within a group tile-major with the output
+    // halves of a tile next to each other (they gather the same source rows)
     int grp_start[kTcgMaxGroups];
     int grp_count[kTcgMaxGroups];
     int grp_oct[kTcgMaxGroups];

@@ -138,13 +138,20 @@ struct Cfg {
     static constexpr int NKC = (NCP + 31) / 32;                    // K chunks of 32 (128 bytes)
     static constexpr int KSTEPS_LAST = (NCP - 32 * (NKC - 1)) / 8; // K steps of 8 in the last chunk
     static constexpr int A_BYTES = 128 * 128;
-    static constexpr int B_BYTES = NP * 128;
+    // B rows loaded per stage: the coefficients rounded up to 8 (one swizzle atom).  The MMA
+    // reads NP >= NPL rows; rows NPL..NP-1 belong to whatever follows in shared memory and only
+    // reach accumulator columns that are never used (columns of D depend on rows of B alone).
+    // At p = 8 this saves the stage bytes that make room for a third pipeline stage.
+    static constexpr int NPL = NHALF == 1 ? (NC + 7) / 8 * 8 : NP;
+    static constexpr int B_BYTES = NPL * 128;
+    static constexpr int SLACK = (NP - NPL) * 128;  // over-read past the last stage stays in the block
     static constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
-    static constexpr int SMEM_AVAIL = 227 * 1024 - 2048;
+    static constexpr int SMEM_AVAIL = 227 * 1024 - 2048 - SLACK;
     static constexpr int STAGES = (SMEM_AVAIL / STAGE_BYTES) > 4 ? 4 : (SMEM_AVAIL / STAGE_BYTES);
     static constexpr int TMEM_COLS = 2 * NP <= 256 ? 256 : 512;
     static constexpr uint32_t IDESC = idesc_tf32(128, NP);
-    static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
+    static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + SLACK + 1024 /*align*/ + 256 /*barriers*/;
+    static_assert(NPL <= NP && NPL >= NC - (NHALF - 1) * NP, "loaded B rows");
     static_assert(NP % 16 == 0 && NP >= 16 && NP <= 192, "MMA N");
     static_assert(STAGES >= 2, "pipeline depth");
     static_assert(2 * NP <= TMEM_COLS, "TMEM double buffer");

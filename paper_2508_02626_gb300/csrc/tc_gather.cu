@@ -66,7 +66,7 @@ __global__ void __launch_bounds__(192, 1) k_tcg(const __grid_constant__ TCGParam
     using C = Cfg<P>;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    unsigned char* bar_area = base + C::STAGES * C::STAGE_BYTES;
+    unsigned char* bar_area = base + C::STAGES * C::STAGE_BYTES + C::SLACK;
     uint64_t* full = reinterpret_cast<uint64_t*>(bar_area);
     uint64_t* empty = full + C::STAGES;
     uint64_t* acc_full = empty + C::STAGES;
@@ -327,8 +327,8 @@ static cudaError_t launch_tcg(const TCGArgs& a, cudaStream_t s) {
     prm.ntiles = tiles;
     if (tiles == 0) return cudaSuccess;
     const int npt = tc_npt(P);
-    if (!encode_rows(enc, &prm.b_hi, a.b_hi, C::NCP, npt, a.nkey, C::NP) ||
-        !encode_rows(enc, &prm.b_lo, a.b_lo, C::NCP, npt, a.nkey, C::NP))
+    if (!encode_rows(enc, &prm.b_hi, a.b_hi, C::NCP, npt, a.nkey, C::NPL) ||
+        !encode_rows(enc, &prm.b_lo, a.b_lo, C::NCP, npt, a.nkey, C::NPL))
         return cudaErrorInvalidValue;
     cudaError_t e = cudaFuncSetAttribute(tc::k_tcg<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM_BYTES);
     if (e != cudaSuccess) return e;

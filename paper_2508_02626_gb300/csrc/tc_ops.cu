@@ -77,7 +77,7 @@ __global__ void __launch_bounds__(192, 1) k_tc(const __grid_constant__ TCParams 
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     // 1024-byte aligned stage ring, then barriers
     unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    unsigned char* bar_area = base + C::STAGES * C::STAGE_BYTES;
+    unsigned char* bar_area = base + C::STAGES * C::STAGE_BYTES + C::SLACK;
     uint64_t* full = reinterpret_cast<uint64_t*>(bar_area);
     uint64_t* empty = full + C::STAGES;
     uint64_t* acc_full = empty + C::STAGES;
@@ -388,8 +388,8 @@ static cudaError_t launch_tc(const TCArgs& a, cudaStream_t s) {
     prm.tile_base[prm.nlev] = tiles;
     prm.ntiles = tiles;
     const int npt = tc_npt(P);
-    if (!encode_rows(enc, &prm.b_hi, a.b_hi, C::NCP, npt, a.nkey, C::NP) ||
-        !encode_rows(enc, &prm.b_lo, a.b_lo, C::NCP, npt, a.nkey, C::NP))
+    if (!encode_rows(enc, &prm.b_hi, a.b_hi, C::NCP, npt, a.nkey, C::NPL) ||
+        !encode_rows(enc, &prm.b_lo, a.b_lo, C::NCP, npt, a.nkey, C::NPL))
         return cudaErrorInvalidValue;
     if (tiles == 0) return cudaSuccess;
     cudaError_t e = cudaFuncSetAttribute(tc::k_tc<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM_BYTES);

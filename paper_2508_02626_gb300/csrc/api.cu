@@ -158,6 +158,9 @@ int ensure_order(dafmm_ctx* c, int p, cudaStream_t s, bool need_k) {
             if ((rc = upload(c, par, t.par, (size_t)t.nnz, "shift table"))) return rc;
             if ((rc = upload(c, val, t.val, (size_t)t.nnz, "shift table"))) return rc;
             if ((rc = upload(c, valf, vf.data(), (size_t)t.nnz, "shift table"))) return rc;
+            std::vector<int> rp8(8 * (size_t)od.nc + 1);
+            shift_rp8(t, od.nc, rp8.data());
+            if ((rc = upload(c, w == 0 ? &od.m2m_rp8 : &od.l2l_rp8, rp8.data(), rp8.size(), "shift table"))) return rc;
         }
         // DA product table: for each output k, the pairs (i, j) with e_i + e_j = e_k
         std::vector<int> ex(3 * od.nc);
@@ -254,6 +257,7 @@ void free_order(dafmm_ctx* c, OrderData& od) {
         dev_free(c, w == 0 ? (void*)od.m2m_par : (void*)od.l2l_par, t.nnz);
         dev_free(c, w == 0 ? (void*)od.m2m_val : (void*)od.l2l_val, t.nnz * sizeof(double));
         dev_free(c, w == 0 ? (void*)od.m2m_valf : (void*)od.l2l_valf, t.nnz * sizeof(float));
+        dev_free(c, w == 0 ? (void*)od.m2m_rp8 : (void*)od.l2l_rp8, (8 * (size_t)nc + 1) * sizeof(int));
     }
     dev_free(c, od.mul_rowptr, ((size_t)nc + 1) * sizeof(int));
     dev_free(c, od.mul_pairs, od.mul_npairs * sizeof(ushort2));
@@ -761,7 +765,7 @@ int eval_adaptive(dafmm_tree* t, int order, int precision, double* dphi, double*
             }
         }
         mark(5);
-        for (int l = 3; l <= t->maxlev; ++l) {
+        for (int l = 2; l < t->maxlev; ++l) {  // parents at level l, children at l + 1
             CK(c, ops->l2l_a(od, av, precision, t->level_start[l], t->level_start[l + 1], t->aL, s), "L2L");
             ++launches;
         }

@@ -115,50 +115,84 @@ __device__ __forceinline__ float tab_val<float>(const ShiftTab& t, int e) { retu
 constexpr int SH_ROWS = (NC + 7) / 8;  // output rows per warp (8 warps)
 
 // parents at level lc-1; children at level lc stored octant-major
+// Both shifts use the octant structure of Sec. 3.3: the entry (b, a) of the table of child
+// octant c is the octant-0 entry times (-1)^popcount(par & c), par = parity pattern of the
+// entry.  Summing over the 8 octants first -- the Hadamard transform
+//   S_m[a] = sum_c (-1)^popcount(m & c) M_c[a]
+// -- turns the 8 signed products per entry into one: parent M[b] = sum_e val_e S_{par_e}[col_e].
+// For L2L the transform runs the other way: R_m[b] = sum_{e of parity m} val_e L[col_e], and
+// child c receives sum_m (-1)^popcount(m & c) R_m[b].  Table entries are stored per row in
+// parity order (tab.rp8).
+template <class T>
+__device__ __forceinline__ void hadamard8(T (&m)[8]) {
+#pragma unroll
+    for (int h = 1; h < 8; h <<= 1)
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+            if (!(i & h)) {
+                const T a = m[i], b = m[i | h];
+                m[i] = a + b;
+                m[i | h] = a - b;
+            }
+}
+
+// parents per thread block of the M2M kernels: the transformed children S[8][PP][NCP + 1]
+// stay within ~180 KB of shared memory
+template <class T>
+constexpr int m2m_parents() {
+    return 8 * 32 * (NCP + 1) * (int)sizeof(T) <= 180 * 1024 ? 32
+           : 8 * 16 * (NCP + 1) * (int)sizeof(T) <= 180 * 1024 ? 16 : 8;
+}
+template <class T>
+constexpr size_t m2m_smem() {
+    return (size_t)8 * m2m_parents<T>() * (NCP + 1) * sizeof(T);
+}
+
+// M2M from the children at level lc into the parents at level lc - 1 (uniform tree)
 template <class T>
 __global__ void __launch_bounds__(256) k_m2m(ShiftTab tab, int lc, const double* __restrict__ Mc,
                                              double* __restrict__ Mp) {
+    constexpr int PP = m2m_parents<T>(), RS = 32 / PP;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T* src = reinterpret_cast<T*>(smem_raw);  // [32][NCP + 1]
+    T* S = reinterpret_cast<T*>(smem_raw);  // [8][PP][NCP + 1]
     const int Pc = 1 << (lc - 1);
     const int nparent = Pc * Pc * Pc;
-    const int lin0 = blockIdx.x * 32;
+    const int lin0 = blockIdx.x * PP;
+    for (int e = threadIdx.x; e < PP * NC; e += 256) {
+        const int r = e / NC, k = e - r * NC;
+        const int lin = lin0 + r;
+        T m[8];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) m[c] = lin < nparent ? (T)Mc[(size_t)(c * nparent + lin) * NCP + k] : T(0);
+        hadamard8(m);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) S[(q * PP + r) * (NCP + 1) + k] = m[q];
+    }
+    __syncthreads();
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    T acc[SH_ROWS];
-#pragma unroll
-    for (int j = 0; j < SH_ROWS; ++j) acc[j] = T(0);
-    for (int c = 0; c < 8; ++c) {
-        for (int e = threadIdx.x; e < 32 * NC; e += 256) {
-            const int r = e / NC, k = e - r * NC;
-            const int lin = lin0 + r;
-            src[r * (NCP + 1) + k] = lin < nparent ? (T)Mc[(size_t)(c * nparent + lin) * NCP + k] : T(0);
-        }
-        __syncthreads();
-#pragma unroll
-        for (int j = 0; j < SH_ROWS; ++j) {
-            const int b = w + 8 * j;
-            if (b < NC) {
-                T s = T(0);
-                for (int e = tab.rowptr[b]; e < tab.rowptr[b + 1]; ++e) {
-                    T v = tab_val<T>(tab, e);
-                    if (__popc(tab.par[e] & c) & 1) v = -v;
-                    s += v * src[lane * (NCP + 1) + tab.col[e]];
-                }
-                acc[j] += s;
-            }
-        }
-        __syncthreads();
+    const int r = lane % PP, sub = lane / PP;
+    const int lin = lin0 + r;
+    if (lin >= nparent) return;
+    const int px = lin % Pc, py = (lin / Pc) % Pc, pz = lin / (Pc * Pc);
+    double* out = Mp + (size_t)octmajor_index(lc - 1, px, py, pz) * NCP;
+    for (int b = w * RS + sub; b < NC; b += 8 * RS) {
+        T acc = T(0);
+        for (int e = tab.rowptr[b]; e < tab.rowptr[b + 1]; ++e)
+            acc += tab_val<T>(tab, e) * S[(tab.par[e] * PP + r) * (NCP + 1) + tab.col[e]];
+        out[b] = (double)acc;
     }
-    const int lin = lin0 + lane;
-    if (lin < nparent) {
-        const int px = lin % Pc, py = (lin / Pc) % Pc, pz = lin / (Pc * Pc);
-        const int pidx = octmajor_index(lc - 1, px, py, pz);
+}
+
+// the 8 partial sums R_m of row b of the L2L table applied to a local expansion in `src`
+template <class T>
+__device__ __forceinline__ void l2l_row(const ShiftTab& tab, int b, const T* src, T (&R)[8]) {
 #pragma unroll
-        for (int j = 0; j < SH_ROWS; ++j) {
-            const int b = w + 8 * j;
-            if (b < NC) Mp[(size_t)pidx * NCP + b] = (double)acc[j];
-        }
+    for (int m = 0; m < 8; ++m) {
+        T s = T(0);
+        for (int e = tab.rp8[8 * b + m]; e < tab.rp8[8 * b + m + 1]; ++e) s += tab_val<T>(tab, e) * src[tab.col[e]];
+        R[m] = s;
     }
+    hadamard8(R);  // R[c] = what child octant c receives
 }
 
 // children at level lc receive L2L of their parent (added to what M2L wrote)
@@ -183,23 +217,12 @@ __global__ void __launch_bounds__(256) k_l2l(ShiftTab tab, int lc, const double*
     }
     __syncthreads();
     const int lin = lin0 + lane;
-    for (int c = 0; c < 8; ++c) {
+    if (lin >= nparent) return;
+    for (int b = w; b < NC; b += 8) {
+        T R[8];
+        l2l_row(tab, b, src + lane * (NCP + 1), R);
 #pragma unroll
-        for (int j = 0; j < SH_ROWS; ++j) {
-            const int b = w + 8 * j;
-            if (b < NC) {
-                T s = T(0);
-                for (int e = tab.rowptr[b]; e < tab.rowptr[b + 1]; ++e) {
-                    T v = tab_val<T>(tab, e);
-                    if (__popc(tab.par[e] & c) & 1) v = -v;
-                    s += v * src[lane * (NCP + 1) + tab.col[e]];
-                }
-                if (lin < nparent) {
-                    double* dst = Lc + (size_t)(c * nparent + lin) * NCP + b;
-                    *dst += (double)s;
-                }
-            }
-        }
+        for (int c = 0; c < 8; ++c) Lc[(size_t)(c * nparent + lin) * NCP + b] += (double)R[c];
     }
 }
 
@@ -575,50 +598,37 @@ __global__ void k_p2m_a(AdaptiveView av, const int* __restrict__ leaves, int nle
 }
 
 // M2M (Eq. 4) into the non-leaf boxes [lb, le) of one level, from their existing children
+// (missing children count as zero; leaves keep their P2M result)
 template <class T>
 __global__ void __launch_bounds__(256) k_m2m_a(ShiftTab tab, AdaptiveView av, int lb, int le, double* __restrict__ M) {
+    constexpr int PP = m2m_parents<T>(), RS = 32 / PP;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T* src = reinterpret_cast<T*>(smem_raw);  // [32][NCP + 1]
-    __shared__ int cidx[32];
-    const int b0 = lb + blockIdx.x * 32;
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    T acc[SH_ROWS];
+    T* S = reinterpret_cast<T*>(smem_raw);  // [8][PP][NCP + 1]
+    const int b0 = lb + blockIdx.x * PP;
+    for (int e = threadIdx.x; e < PP * NC; e += 256) {
+        const int r = e / NC, k = e - r * NC;
+        const int bx = b0 + r;
+        T m[8];
 #pragma unroll
-    for (int j = 0; j < SH_ROWS; ++j) acc[j] = T(0);
-    for (int c = 0; c < 8; ++c) {
-        if (threadIdx.x < 32) {
-            const int b = b0 + threadIdx.x;
-            cidx[threadIdx.x] = b < le ? av.child[8 * b + c] : -1;
+        for (int c = 0; c < 8; ++c) {
+            const int ch = bx < le ? av.child[8 * bx + c] : -1;
+            m[c] = ch >= 0 ? (T)M[(size_t)ch * NCP + k] : T(0);
         }
-        __syncthreads();
-        for (int e = threadIdx.x; e < 32 * NC; e += 256) {
-            const int r = e / NC, k = e - r * NC;
-            const int ch = cidx[r];
-            src[r * (NCP + 1) + k] = ch >= 0 ? (T)M[(size_t)ch * NCP + k] : T(0);
-        }
-        __syncthreads();
+        hadamard8(m);
 #pragma unroll
-        for (int j = 0; j < SH_ROWS; ++j) {
-            const int bb = w + 8 * j;
-            if (bb < NC) {
-                T s = T(0);
-                for (int e = tab.rowptr[bb]; e < tab.rowptr[bb + 1]; ++e) {
-                    T v = tab_val<T>(tab, e);
-                    if (__popc(tab.par[e] & c) & 1) v = -v;
-                    s += v * src[lane * (NCP + 1) + tab.col[e]];
-                }
-                acc[j] += s;
-            }
-        }
-        __syncthreads();
+        for (int q = 0; q < 8; ++q) S[(q * PP + r) * (NCP + 1) + k] = m[q];
     }
-    const int b = b0 + lane;
-    if (b < le && !abox_is_leaf(av, b)) {
-#pragma unroll
-        for (int j = 0; j < SH_ROWS; ++j) {
-            const int bb = w + 8 * j;
-            if (bb < NC) M[(size_t)b * NCP + bb] = (double)acc[j];
-        }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int r = lane % PP, sub = lane / PP;
+    const int bx = b0 + r;
+    if (bx >= le || abox_is_leaf(av, bx)) return;
+    double* out = M + (size_t)bx * NCP;
+    for (int b = w * RS + sub; b < NC; b += 8 * RS) {
+        T acc = T(0);
+        for (int e = tab.rowptr[b]; e < tab.rowptr[b + 1]; ++e)
+            acc += tab_val<T>(tab, e) * S[(tab.par[e] * PP + r) * (NCP + 1) + tab.col[e]];
+        out[b] = (double)acc;
     }
 }
 
@@ -741,46 +751,31 @@ __global__ void k_p2l_a(AdaptiveView av, int lb, int le, double* __restrict__ L)
     }
 }
 
-// L2L (Eq. 7) into the boxes [lb, le) of one level from their parents
+// L2L (Eq. 7) from the parents [lb, le) of one level into their existing children (added to
+// what M2L and P2L wrote)
 template <class T>
 __global__ void __launch_bounds__(256) k_l2l_a(ShiftTab tab, AdaptiveView av, int lb, int le, double* __restrict__ L) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* src = reinterpret_cast<T*>(smem_raw);  // [32][NCP + 1]
-    __shared__ int pidx[32];
-    __shared__ int coct[32];
     const int b0 = lb + blockIdx.x * 32;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    if (threadIdx.x < 32) {
-        const int b = b0 + threadIdx.x;
-        int P = -1, c = 0;
-        if (b < le) {
-            P = av.parent[b];
-            c = (av.ijk[3 * b] & 1) | ((av.ijk[3 * b + 1] & 1) << 1) | ((av.ijk[3 * b + 2] & 1) << 2);
-        }
-        pidx[threadIdx.x] = P;
-        coct[threadIdx.x] = c;
-    }
-    __syncthreads();
     for (int e = threadIdx.x; e < 32 * NC; e += 256) {
         const int r = e / NC, k = e - r * NC;
-        const int P = pidx[r];
-        src[r * (NCP + 1) + k] = P >= 0 ? (T)L[(size_t)P * NCP + k] : T(0);
+        const int P = b0 + r;
+        src[r * (NCP + 1) + k] = P < le ? (T)L[(size_t)P * NCP + k] : T(0);
     }
     __syncthreads();
-    const int b = b0 + lane;
-    const int c = coct[lane];
+    const int P = b0 + lane;
+    if (P >= le || abox_is_leaf(av, P)) return;
+    int ch[8];
 #pragma unroll
-    for (int j = 0; j < SH_ROWS; ++j) {
-        const int bb = w + 8 * j;
-        if (bb < NC) {
-            T s = T(0);
-            for (int e = tab.rowptr[bb]; e < tab.rowptr[bb + 1]; ++e) {
-                T v = tab_val<T>(tab, e);
-                if (__popc(tab.par[e] & c) & 1) v = -v;
-                s += v * src[lane * (NCP + 1) + tab.col[e]];
-            }
-            if (b < le) L[(size_t)b * NCP + bb] += (double)s;
-        }
+    for (int c = 0; c < 8; ++c) ch[c] = av.child[8 * P + c];
+    for (int b = w; b < NC; b += 8) {
+        T R[8];
+        l2l_row(tab, b, src + lane * (NCP + 1), R);
+#pragma unroll
+        for (int c = 0; c < 8; ++c)
+            if (ch[c] >= 0) L[(size_t)ch[c] * NCP + b] += (double)R[c];
     }
 }
 
@@ -981,15 +976,15 @@ static cudaError_t m2m_launch(const OrderData& od, int prec, int lc, const doubl
     const int Pc = 1 << (lc - 1);
     const int nparent = Pc * Pc * Pc;
     const bool f32 = prec == DAFMM_FP32;
-    const size_t smem = (size_t)32 * (NCP + 1) * (f32 ? 4 : 8);
     cudaError_t e;
-    dim3 grd((nparent + 31) / 32);
     if (!f32) {
-        if ((e = set_smem(k_m2m<double>, smem)) != cudaSuccess) return e;
-        k_m2m<double><<<grd, 256, smem, s>>>(od.m2m(), lc, Mc, Mp);
+        constexpr int PP = m2m_parents<double>();
+        if ((e = set_smem(k_m2m<double>, m2m_smem<double>())) != cudaSuccess) return e;
+        k_m2m<double><<<(nparent + PP - 1) / PP, 256, m2m_smem<double>(), s>>>(od.m2m(), lc, Mc, Mp);
     } else {
-        if ((e = set_smem(k_m2m<float>, smem)) != cudaSuccess) return e;
-        k_m2m<float><<<grd, 256, smem, s>>>(od.m2m(), lc, Mc, Mp);
+        constexpr int PP = m2m_parents<float>();
+        if ((e = set_smem(k_m2m<float>, m2m_smem<float>())) != cudaSuccess) return e;
+        k_m2m<float><<<(nparent + PP - 1) / PP, 256, m2m_smem<float>(), s>>>(od.m2m(), lc, Mc, Mp);
     }
     return cudaGetLastError();
 }
@@ -1069,15 +1064,15 @@ static cudaError_t m2m_a_launch(const OrderData& od, const AdaptiveView& av, int
                                 cudaStream_t s) {
     if (le <= lb) return cudaSuccess;
     const bool f32 = prec == DAFMM_FP32;
-    const size_t smem = (size_t)32 * (NCP + 1) * (f32 ? 4 : 8);
-    dim3 grd((le - lb + 31) / 32);
     cudaError_t e;
     if (!f32) {
-        if ((e = set_smem(k_m2m_a<double>, smem)) != cudaSuccess) return e;
-        k_m2m_a<double><<<grd, 256, smem, s>>>(od.m2m(), av, lb, le, M);
+        constexpr int PP = m2m_parents<double>();
+        if ((e = set_smem(k_m2m_a<double>, m2m_smem<double>())) != cudaSuccess) return e;
+        k_m2m_a<double><<<(le - lb + PP - 1) / PP, 256, m2m_smem<double>(), s>>>(od.m2m(), av, lb, le, M);
     } else {
-        if ((e = set_smem(k_m2m_a<float>, smem)) != cudaSuccess) return e;
-        k_m2m_a<float><<<grd, 256, smem, s>>>(od.m2m(), av, lb, le, M);
+        constexpr int PP = m2m_parents<float>();
+        if ((e = set_smem(k_m2m_a<float>, m2m_smem<float>())) != cudaSuccess) return e;
+        k_m2m_a<float><<<(le - lb + PP - 1) / PP, 256, m2m_smem<float>(), s>>>(od.m2m(), av, lb, le, M);
     }
     return cudaGetLastError();
 }

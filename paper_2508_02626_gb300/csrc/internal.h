@@ -38,6 +38,7 @@ struct ShiftTab {                 // compressed rows of a level-independent M2M 
     const unsigned char* par;     // bit v: exponent sum of row and column odd in axis v
     const double* val;
     const float* valf;
+    const int* rp8;               // [nc * 8 + 1]: start of the entries of (row, parity class)
 };
 
 struct MulTab {                   // DA product table for the K generation
@@ -55,6 +56,7 @@ struct OrderData {
     double* m2m_val = nullptr; float* m2m_valf = nullptr;
     int* l2l_rowptr = nullptr; unsigned short* l2l_col = nullptr; unsigned char* l2l_par = nullptr;
     double* l2l_val = nullptr; float* l2l_valf = nullptr;
+    int* m2m_rp8 = nullptr; int* l2l_rp8 = nullptr;
     int* mul_rowptr = nullptr; ushort2* mul_pairs = nullptr; short* mul_minus = nullptr;
     size_t mul_npairs = 0;
     double* K64 = nullptr;        // [343][nc][ncp]: K^_v[b][a] (scaled M2L, Eq. 5)
@@ -66,8 +68,8 @@ struct OrderData {
     float* L2Lhi = nullptr;
     float* L2Llo = nullptr;
     bool k_ready = false;
-    ShiftTab m2m() const { return ShiftTab{m2m_rowptr, m2m_col, m2m_par, m2m_val, m2m_valf}; }
-    ShiftTab l2l() const { return ShiftTab{l2l_rowptr, l2l_col, l2l_par, l2l_val, l2l_valf}; }
+    ShiftTab m2m() const { return ShiftTab{m2m_rowptr, m2m_col, m2m_par, m2m_val, m2m_valf, m2m_rp8}; }
+    ShiftTab l2l() const { return ShiftTab{l2l_rowptr, l2l_col, l2l_par, l2l_val, l2l_valf, l2l_rp8}; }
     MulTab mul() const { return MulTab{mul_rowptr, mul_pairs, mul_minus}; }
 };
 
@@ -76,9 +78,22 @@ struct HostShiftTable {
     int nnz;
     const int* rowptr;
     const unsigned short* col;
-    const unsigned char* par;
+    const unsigned char* par;     // non-decreasing within each row
     const double* val;
 };
+
+// starts of the (row, parity class) runs of a shift table: out[8 * b + m] for m = 0..7, and
+// out[8 * nc] = nnz
+inline void shift_rp8(const HostShiftTable& t, int nc, int* out) {
+    for (int b = 0; b < nc; ++b) {
+        int e = t.rowptr[b];
+        for (int m = 0; m < 8; ++m) {
+            while (e < t.rowptr[b + 1] && t.par[e] < m) ++e;
+            out[8 * b + m] = e;
+        }
+    }
+    out[8 * nc] = t.nnz;
+}
 
 struct OrderOps {
     int p, nc, ncp;
@@ -106,6 +121,7 @@ struct OrderOps {
     cudaError_t (*m2l_a)(const OrderData&, const AdaptiveView&, int prec, const int* tg, const int* grp_ptr, int grp0,
                          int max_group, const double* M, const float* Mf, double* L, cudaStream_t);
     cudaError_t (*p2l_a)(const AdaptiveView&, int prec, int lb, int le, double* L, cudaStream_t);
+    // L2L from the parents [lb, le) of one level into their children
     cudaError_t (*l2l_a)(const OrderData&, const AdaptiveView&, int prec, int lb, int le, double* L, cudaStream_t);
     cudaError_t (*leaf_a)(const AdaptiveView&, const int* leaves, int nleaves, int prec, const double* L,
                           const double* M, double* phi, double* field, int warps, cudaStream_t);

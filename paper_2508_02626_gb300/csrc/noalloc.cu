@@ -156,6 +156,8 @@ extern "C" int dafmm_eval_noalloc(dafmm_tree* t, int order, double* phi, double*
         od.l2l_col = cv.take<unsigned short>(ops->l2l.nnz);
         od.l2l_par = cv.take<unsigned char>(ops->l2l.nnz);
         od.l2l_val = cv.take<double>(ops->l2l.nnz);
+        od.m2m_rp8 = cv.take<int>(8 * (size_t)nc + 1);
+        od.l2l_rp8 = cv.take<int>(8 * (size_t)nc + 1);
         od.mul_rowptr = cv.take<int>(rowptr.size());
         od.mul_pairs = cv.take<ushort2>(pairs.size());
         od.mul_minus = cv.take<short>(minus.size());
@@ -193,6 +195,11 @@ extern "C" int dafmm_eval_noalloc(dafmm_tree* t, int order, double* phi, double*
     up(od.l2l_col, ops->l2l.col, ops->l2l.nnz * sizeof(unsigned short));
     up(od.l2l_par, ops->l2l.par, ops->l2l.nnz);
     up(od.l2l_val, ops->l2l.val, ops->l2l.nnz * sizeof(double));
+    std::vector<int> m2m_rp8(8 * (size_t)nc + 1), l2l_rp8(8 * (size_t)nc + 1);
+    shift_rp8(ops->m2m, nc, m2m_rp8.data());
+    shift_rp8(ops->l2l, nc, l2l_rp8.data());
+    up(od.m2m_rp8, m2m_rp8.data(), m2m_rp8.size() * sizeof(int));
+    up(od.l2l_rp8, l2l_rp8.data(), l2l_rp8.size() * sizeof(int));
     up(od.mul_rowptr, rowptr.data(), rowptr.size() * sizeof(int));
     up(od.mul_pairs, pairs.data(), pairs.size() * sizeof(ushort2));
     up(od.mul_minus, minus.data(), minus.size() * sizeof(short));

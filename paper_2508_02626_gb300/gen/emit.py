@@ -179,18 +179,23 @@ def emit_eval(name, p, kind):
 def csr_table(name, p, table, with_parity=True):
     ex = exponents(p)
     nc = ncoef(p)
+    # within a row, entries are ordered by parity pattern, then column: the shift kernels sum
+    # each parity class separately (a Hadamard transform over the 8 octants does the rest)
     rowptr, cols, vals, par = [0], [], [], []
     for b in range(nc):
+        row = []
         for a in range(nc):
             v = table[b][a]
             if v:
-                cols.append(a)
-                vals.append(v)
                 m = 0
                 for k in range(3):
                     if (ex[b][k] + ex[a][k]) % 2:
                         m |= 1 << k
-                par.append(m)
+                row.append((m, a, v))
+        for m, a, v in sorted(row, key=lambda t: (t[0], t[1])):
+            cols.append(a)
+            vals.append(v)
+            par.append(m)
         rowptr.append(len(cols))
     out = []
     out.append("static const int %s_nnz = %d;\n" % (name, len(cols)))

@@ -55,6 +55,20 @@ struct RowLoad {
     __device__ __forceinline__ T operator()(int k) const { return (T)row[k]; }
 };
 
+// a row already converted to FP32 in shared memory (one conversion per coefficient per warp
+// instead of one per coefficient per lane)
+struct SmemRowF {
+    const float* row;
+    __device__ __forceinline__ float operator()(int k) const { return row[k]; }
+};
+
+// the warp copies an FP64 row into `buf` as FP32
+__device__ __forceinline__ void warp_row_to_f32(const double* __restrict__ row, float* buf, int lane) {
+    __syncwarp();
+    for (int k = lane; k < NC; k += 32) buf[k] = (float)row[k];
+    __syncwarp();
+}
+
 // ---- P2M ---------------------------------------------------------------------------------
 template <class T>
 __global__ void k_p2m(TreeView tv, double* __restrict__ M) {
@@ -445,6 +459,21 @@ __global__ void __launch_bounds__(128) k_leaf(TreeView tv, const double* __restr
     const double cy = tv.y0 + ((double)b + 0.5) * tv.h_leaf;
     const double cz = tv.z0 + ((double)c + 0.5) * tv.h_leaf;
     const double* Lrow = Lleaf ? Lleaf + (size_t)leaf * NCP : nullptr;
+    __shared__ float s_lrow[4][NCP];  // per warp: the leaf's local expansion in FP32
+    if constexpr (sizeof(T) == 4) {
+        if (Lrow) warp_row_to_f32(Lrow, s_lrow[threadIdx.y], lane);
+    }
+    // the 27 neighbour leaves' particle ranges, one per lane (empty outside the domain)
+    int nb_s0 = 0, nb_s1 = 0;
+    if (lane < 27) {
+        const int dx = lane % 3 - 1, dy = (lane / 3) % 3 - 1, dz = lane / 9 - 1;
+        const int na = a + dx, nb = b + dy, nc2 = c + dz;
+        if (na >= 0 && nb >= 0 && nc2 >= 0 && na < nside && nb < nside && nc2 < nside) {
+            const int nl = octmajor_index(tv.depth, na, nb, nc2);
+            nb_s0 = tv.leaf_start[nl];
+            nb_s1 = tv.leaf_start[nl + 1];
+        }
+    }
     for (int base = i0; base < i1; base += 32) {
         const int t = base + lane;
         const bool valid = t < i1;
@@ -474,27 +503,24 @@ __global__ void __launch_bounds__(128) k_leaf(TreeView tv, const double* __restr
         } else {
             const float4 pt = tv.xq[tt];
             float ph = 0.f, pl = 0.f, xh = 0.f, xl = 0.f, yh = 0.f, yl = 0.f, zh = 0.f, zl = 0.f;
-            for (int dz = -1; dz <= 1; ++dz)
-                for (int dy = -1; dy <= 1; ++dy)
-                    for (int dx = -1; dx <= 1; ++dx) {
-                        const int na = a + dx, nb = b + dy, nc2 = c + dz;
-                        if (na < 0 || nb < 0 || nc2 < 0 || na >= nside || nb >= nside || nc2 >= nside) continue;
-                        const int nl = octmajor_index(tv.depth, na, nb, nc2);
-                        const int s0 = tv.leaf_start[nl], s1 = tv.leaf_start[nl + 1];
-                        // target in the neighbour's frame (offsets in leaf widths)
-                        const float tx = pt.x - (float)dx, ty = pt.y - (float)dy, tz = pt.z - (float)dz;
-                        // FP32 partial sums over at most 64 sources, folded into compensated
-                        // (hi, lo) accumulators so that long leaves keep FP32-level error
-                        for (int sb = s0; sb < s1; sb += 64) {
-                            const int se = min(s1, sb + 64);
-                            float sp = 0.f, sx = 0.f, sy = 0.f, sz = 0.f;
-                            p2p_f32(tv.xq, sb, se, tx, ty, tz, sp, sx, sy, sz);
-                            two_sum_add(ph, pl, sp);
-                            two_sum_add(xh, xl, sx);
-                            two_sum_add(yh, yl, sy);
-                            two_sum_add(zh, zl, sz);
-                        }
-                    }
+            for (int nbi = 0; nbi < 27; ++nbi) {
+                const int s0 = __shfl_sync(0xffffffffu, nb_s0, nbi), s1 = __shfl_sync(0xffffffffu, nb_s1, nbi);
+                if (s0 == s1) continue;
+                const int dx = nbi % 3 - 1, dy = (nbi / 3) % 3 - 1, dz = nbi / 9 - 1;
+                // target in the neighbour's frame (offsets in leaf widths)
+                const float tx = pt.x - (float)dx, ty = pt.y - (float)dy, tz = pt.z - (float)dz;
+                // FP32 partial sums over at most 64 sources, folded into compensated
+                // (hi, lo) accumulators so that long leaves keep FP32-level error
+                for (int sb = s0; sb < s1; sb += 64) {
+                    const int se = min(s1, sb + 64);
+                    float sp = 0.f, sx = 0.f, sy = 0.f, sz = 0.f;
+                    p2p_f32(tv.xq, sb, se, tx, ty, tz, sp, sx, sy, sz);
+                    two_sum_add(ph, pl, sp);
+                    two_sum_add(xh, xl, sx);
+                    two_sum_add(yh, yl, sy);
+                    two_sum_add(zh, zl, sz);
+                }
+            }
             const double ih = tv.inv_h_leaf, ih2 = ih * ih;
             fphi = ((double)ph + (double)pl) * ih;
             fx = ((double)xh + (double)xl) * ih2;
@@ -513,7 +539,8 @@ __global__ void __launch_bounds__(128) k_leaf(TreeView tv, const double* __restr
                 const float4 pt = tv.xq[tt];
                 xs = (T)pt.x; ys = (T)pt.y; zs = (T)pt.z;
             }
-            gen::GEN(l2p)<T>(RowLoad<T>{Lrow}, xs, ys, zs, F, g0, g1, g2);
+            if constexpr (sizeof(T) == 4) gen::GEN(l2p)<T>(SmemRowF{s_lrow[threadIdx.y]}, xs, ys, zs, F, g0, g1, g2);
+            else gen::GEN(l2p)<T>(RowLoad<T>{Lrow}, xs, ys, zs, F, g0, g1, g2);
             fphi += (double)F;
             fx -= (double)g0 * tv.inv_h_leaf;
             fy -= (double)g1 * tv.inv_h_leaf;
@@ -784,14 +811,20 @@ template <class T>
 __global__ void __launch_bounds__(256) k_leaf_a(AdaptiveView av, const int* __restrict__ leaves, int nleaves,
                                                 const double* __restrict__ L, const double* __restrict__ M,
                                                 double* __restrict__ phi, double* __restrict__ field) {
+    __shared__ float s_rows[8][2][NCP];  // per warp: the W box's multipoles and the leaf's locals, FP32
     const int lane = threadIdx.x;
     const int li = blockIdx.x * blockDim.y + threadIdx.y;
     if (li >= nleaves) return;
+    float* mrow = s_rows[threadIdx.y][0];
+    float* lrow = s_rows[threadIdx.y][1];
     const int b = leaves[li];
     double cx, cy, cz, h;
     abox_geom(av, b, cx, cy, cz, h);
     const double ih = 1.0 / h;
     const int lev = av.level[b];
+    if constexpr (sizeof(T) == 4) {
+        if (lev >= 2) warp_row_to_f32(L + (size_t)b * NCP, lrow, lane);
+    }
     const int i0 = av.pbeg[b], i1 = av.pend[b];
     const int u0 = av.u_ptr[b], u1 = av.u_ptr[b + 1];
     const int w0 = av.w_ptr[b], w1 = av.w_ptr[b + 1];
@@ -860,8 +893,14 @@ __global__ void __launch_bounds__(256) k_leaf_a(AdaptiveView av, const int* __re
             abox_geom(av, wb, wx, wy, wz, wh);
             const double iwh = 1.0 / wh;
             T F, g0, g1, g2;
-            gen::GEN(m2p)<T>(RowLoad<T>{M + (size_t)wb * NCP}, (T)((av.x[tt] - wx) * iwh), (T)((av.y[tt] - wy) * iwh),
-                             (T)((av.z[tt] - wz) * iwh), F, g0, g1, g2);
+            const T sx0 = (T)((av.x[tt] - wx) * iwh), sy0 = (T)((av.y[tt] - wy) * iwh),
+                    sz0 = (T)((av.z[tt] - wz) * iwh);
+            if constexpr (sizeof(T) == 4) {
+                warp_row_to_f32(M + (size_t)wb * NCP, mrow, lane);
+                gen::GEN(m2p)<T>(SmemRowF{mrow}, sx0, sy0, sz0, F, g0, g1, g2);
+            } else {
+                gen::GEN(m2p)<T>(RowLoad<T>{M + (size_t)wb * NCP}, sx0, sy0, sz0, F, g0, g1, g2);
+            }
             fphi += (double)F * iwh;
             fx -= (double)g0 * iwh * iwh;
             fy -= (double)g1 * iwh * iwh;
@@ -879,7 +918,8 @@ __global__ void __launch_bounds__(256) k_leaf_a(AdaptiveView av, const int* __re
                 const float4 pt = av.xq[tt];
                 xs = (T)pt.x; ys = (T)pt.y; zs = (T)pt.z;
             }
-            gen::GEN(l2p)<T>(RowLoad<T>{L + (size_t)b * NCP}, xs, ys, zs, F, g0, g1, g2);
+            if constexpr (sizeof(T) == 4) gen::GEN(l2p)<T>(SmemRowF{lrow}, xs, ys, zs, F, g0, g1, g2);
+            else gen::GEN(l2p)<T>(RowLoad<T>{L + (size_t)b * NCP}, xs, ys, zs, F, g0, g1, g2);
             fphi += (double)F;
             fx -= (double)g0 * ih;
             fy -= (double)g1 * ih;

@@ -217,27 +217,34 @@ def run_ours(args, rank, world):
     flops = 2.0 * nc * nc * pairs_all
     m2l_s = ph["m2l"] / 1e3
     achieved = flops / m2l_s / 1e12
+    f16 = args.precision == "fp32"  # the FP32 mode's M2L runs on F16 split operands (the default)
     if args.precision == "fp64":
         peak, bound = 1.25, "alu"
         peak_note = "FP64 nominal 1.25 TFLOP/s (no measured FP64 peak)"
         executed = None
     else:
-        # TF32 tensor peak = measured BF16 burst peak x the nominal TF32/BF16 ratio 1/2
-        peak, bound = peaks["bf16_tflops"] / 2.0, "tensor"
-        peak_note = "TF32 = %s BF16 %.1f TFLOP/s x 1/2 (nominal ratio)" % (peak_src, peaks["bf16_tflops"])
+        if f16:
+            # F16 operands: dense F16 tensor peak = the measured BF16 burst peak (same nominal rate)
+            peak, bound = peaks["bf16_tflops"], "tensor"
+            peak_note = "F16 = %s BF16 %.1f TFLOP/s (same nominal dense rate)" % (peak_src, peaks["bf16_tflops"])
+        else:
+            # TF32 tensor peak = measured BF16 burst peak x the nominal TF32/BF16 ratio 1/2
+            peak, bound = peaks["bf16_tflops"] / 2.0, "tensor"
+            peak_note = "TF32 = %s BF16 %.1f TFLOP/s x 1/2 (nominal ratio)" % (peak_src, peaks["bf16_tflops"])
         npt = (nc + 15) // 16 * 16
         if npt > 192:
             npt = 2 * (((npt // 2) + 15) // 16 * 16)
-        ncp = (nc + 7) // 8 * 8
+        klen = (nc + 15) // 16 * 16 if f16 else (nc + 7) // 8 * 8  # operand row length (MMA K)
         tiles = 0
         for l in range(2, depth + 1):
             S = 1 << (l - 1)
             bx = min(S, 128); by = min(S, 128 // bx); bz = max(1, min(S, 128 // (bx * by)))
             tiles += 8 * (S // bx) * (S // by) * (S // bz)
-        executed = tiles * 189 * 3 * 2.0 * 128 * npt * ncp / m2l_s / 1e12
+        executed = tiles * 189 * 3 * 2.0 * 128 * npt * klen / m2l_s / 1e12
     roofline = {"bound": bound, "achieved": round(achieved, 3), "peak": round(peak, 3), "unit": "TFLOP/s",
                 "frac": round(achieved / peak, 4), "traffic": None,
-                "kernel": "M2L contraction (tcgen05 k_tc, all levels, one launch)" if bound == "tensor"
+                "kernel": ("M2L contraction (tcgen05 kind::f16 k_tc, all levels, one launch)" if f16 else
+                           "M2L contraction (tcgen05 kind::tf32 k_tc, all levels, one launch)") if bound == "tensor"
                 else "M2L (SIMT FP64 k_m2l, all levels)",
                 "algorithmic": "2 ncoef^2 flops per well-separated pair: %.3e flops" % flops,
                 "executed_tflops": None if executed is None else round(executed, 3),
@@ -247,7 +254,8 @@ def run_ours(args, rank, world):
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": {"fp64": "f64", "mixed": "f32+f64", "fp32": "f32 (tf32x3 contractions)"}[args.precision],
+        "scaling": "weak", "vs_baseline": None, "dtype": {"fp64": "f64", "mixed": "f32+f64 (M2L tf32x3)",
+                  "fp32": "f32 (M2L f16x3 scaled split products, M2M/L2L tf32x3)"}[args.precision],
         "data": "synthetic (seeded uniform, PCG64 seed 2002)",
         "config": {"workload": "uniform N=1e6, q~U[-1,1], octree depth 5, order p=8, theta=1",
                    "precision": args.precision, "l2": "flushed between timed steps (256 MB write)",
@@ -264,9 +272,13 @@ def run_ours(args, rank, world):
     phi_host, E_host = phi.cpu().numpy(), E.cpu().numpy()
     tree.free()
     if world == 1 and not args.no_workloads:
-        out["adaptive"] = bench_adaptive(ctx, stream, flush)
-        out["batch"] = bench_batch(ctx, stream, flush)
-        out["serving"] = bench_serving(args.serving_requests)
+        sections = set(args.sections.split(","))
+        if "adaptive" in sections:
+            out["adaptive"] = bench_adaptive(ctx, stream, flush)
+        if "batch" in sections:
+            out["batch"] = bench_batch(ctx, stream, flush)
+        if "serving" in sections:
+            out["serving"] = bench_serving(args.serving_requests)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"], out["accuracy"] = cpu_baseline(x, q, dom, cfg, phi_host, E_host)
     ctx.close()
@@ -576,6 +588,8 @@ def main():
     ap.add_argument("--no-workloads", action="store_true",
                     help="skip the adaptive, batched and serving workloads (N = 1 only)")
     ap.add_argument("--serving-requests", type=int, default=200)
+    ap.add_argument("--sections", default="adaptive,batch,serving",
+                    help="comma-separated extra workloads at N = 1: adaptive, batch, serving")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))

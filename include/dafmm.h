@@ -187,6 +187,11 @@ int dafmm_last_phase_ms(dafmm_ctx* ctx, double* out10);
 /*   DAFMM_OPT_LEAF_WARPS: leaves per thread block of the adaptive near-field kernel (P2P,
  *   M2P, L2P), one warp each: 1, 2, 4 (default) or 8 -- the P2P tile the autotuner picks. */
 #define DAFMM_OPT_LEAF_WARPS 3
+/*   DAFMM_OPT_M2L_F16: operands of the FP32 mode's tensor-core M2L: 1 (default) = F16 hi/lo
+ *   splits with power-of-two scales per box, per matrix row and per matrix (twice the TF32
+ *   rate, M2L rounding ~1e-7 relative), 0 = TF32 hi/lo splits (~5e-8).  MIXED always uses
+ *   the TF32 splits. */
+#define DAFMM_OPT_M2L_F16 4
 int dafmm_set_option(dafmm_ctx* ctx, int option, int64_t value);
 
 /* Diagnostics: copy level `level` of an internal expansion array of the last evaluation

@@ -236,6 +236,7 @@ def dafmm_eval(ctx, tree, order, phi=None, field=None, theta=1.0, precision=DAFM
 DAFMM_OPT_M2L_KERNEL = 1
 DAFMM_OPT_TC_MASK = 2
 DAFMM_OPT_LEAF_WARPS = 3
+DAFMM_OPT_M2L_F16 = 4
 
 
 def dafmm_set_option(ctx, option, value):

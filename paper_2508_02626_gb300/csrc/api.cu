@@ -1,5 +1,6 @@
 // api.cu -- host runtime behind the C ABI of include/dafmm.h: contexts with an HBM budget,
 // octree construction, the FMM evaluation sequence (Sec. 1) and the single-operator batches.
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdio.h>
@@ -265,6 +266,13 @@ void free_order(dafmm_ctx* c, OrderData& od) {
     const size_t cnt = (size_t)kNumKeys * od.nc * od.ncp;
     dev_free(c, od.K64, od.K64 ? cnt * sizeof(double) : 0);
     dev_free(c, od.K32, od.K32 ? cnt * sizeof(float) : 0);
+    if (od.Kh16) {
+        const size_t c16 = (size_t)kNumKeys * tc_npt(od.p) * tc_rowlen16(od.p) * 2;
+        dev_free(c, od.Kh16, c16);
+        dev_free(c, od.Kl16, c16);
+        dev_free(c, od.k16_inv_r, (size_t)tc_npt(od.p) * sizeof(float));
+        dev_free(c, od.k16_inv_c, (size_t)kNumKeys * sizeof(float));
+    }
     if (od.Khi) {
         const size_t cs = (size_t)kNumKeys * tc_npt(od.p) * od.ncp;
         dev_free(c, od.Khi, cs * sizeof(float));
@@ -274,6 +282,39 @@ void free_order(dafmm_ctx* c, OrderData& od) {
         dev_free(c, od.L2Lhi, ss); dev_free(c, od.L2Llo, ss);
     }
     od = OrderData();
+}
+
+// F16 splits of the M2L matrices of an order (made once, on first use)
+int ensure_k16(dafmm_ctx* c, int p, cudaStream_t s) {
+    OrderData& od = c->ord[p];
+    if (od.Kh16) return DAFMM_OK;
+    const int npt = tc_npt(p);
+    const size_t c16 = (size_t)kNumKeys * npt * tc_rowlen16(p) * 2;
+    int rc;
+    void *hi = nullptr, *lo = nullptr;
+    float *ir = nullptr, *ic = nullptr, *scratch = nullptr;
+    if ((rc = dev_alloc(c, &hi, c16, "M2L matrices (F16 split)")) || (rc = dev_alloc(c, &lo, c16, "M2L matrices (F16 split)")) ||
+        (rc = dev_alloc(c, (void**)&ir, (size_t)npt * sizeof(float), "M2L matrix factors")) ||
+        (rc = dev_alloc(c, (void**)&ic, (size_t)kNumKeys * sizeof(float), "M2L matrix factors")) ||
+        (rc = dev_alloc(c, (void**)&scratch, ((size_t)npt + kNumKeys) * sizeof(float), "M2L matrix factors"))) {
+        dev_free(c, hi, c16); dev_free(c, lo, c16);
+        dev_free(c, ir, (size_t)npt * sizeof(float)); dev_free(c, ic, (size_t)kNumKeys * sizeof(float));
+        dev_free(c, scratch, ((size_t)npt + kNumKeys) * sizeof(float));
+        return rc;
+    }
+    cudaError_t e = tc_prepare_k16(od.K64, kNumKeys, p, hi, lo, ir, ic, scratch, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // shared by every later evaluation, on any stream
+    dev_free(c, scratch, ((size_t)npt + kNumKeys) * sizeof(float));
+    if (e != cudaSuccess) {
+        dev_free(c, hi, c16); dev_free(c, lo, c16);
+        dev_free(c, ir, (size_t)npt * sizeof(float)); dev_free(c, ic, (size_t)kNumKeys * sizeof(float));
+        return cuda_fail(c, e, "M2L matrices (F16 split)");
+    }
+    od.Kh16 = hi;
+    od.Kl16 = lo;
+    od.k16_inv_r = ir;
+    od.k16_inv_c = ic;
+    return DAFMM_OK;
 }
 
 // ---- expansions --------------------------------------------------------------------------------
@@ -291,6 +332,10 @@ void free_expansions(dafmm_tree* t) {
         dev_free(c, e.Mlo[l], e.Mlo[l] ? cnt * sizeof(float) : 0);
         dev_free(c, e.Lhi[l], e.Lhi[l] ? cnt * sizeof(float) : 0);
         dev_free(c, e.Llo[l], e.Llo[l] ? cnt * sizeof(float) : 0);
+        const size_t c16 = level_boxes(l) * (size_t)tc_rowlen16(e.p) * 2;
+        dev_free(c, e.Mh16[l], c16);
+        dev_free(c, e.Ml16[l], c16);
+        dev_free(c, e.Minv[l], level_boxes(l) * sizeof(float));
     }
     e = Expansions();
 }
@@ -319,6 +364,22 @@ int ensure_expansions(dafmm_tree* t, int p, cudaStream_t s) {
         CK(c, cudaMemsetAsync(t->ex.Mlo[l], 0, cnt * sizeof(float), s), "memset");
         CK(c, cudaMemsetAsync(t->ex.Lhi[l], 0, cnt * sizeof(float), s), "memset");
         CK(c, cudaMemsetAsync(t->ex.Llo[l], 0, cnt * sizeof(float), s), "memset");
+    }
+    return DAFMM_OK;
+}
+
+// the F16 multipole splits of every level of a uniform tree (made on first use)
+int ensure_f16_levels(dafmm_tree* t, cudaStream_t s) {
+    (void)s;
+    dafmm_ctx* c = t->ctx;
+    Expansions& e = t->ex;
+    for (int l = 2; l <= e.depth; ++l) {
+        if (e.Mh16[l]) continue;
+        const size_t c16 = level_boxes(l) * (size_t)tc_rowlen16(e.p) * 2;
+        int rc;
+        if ((rc = dev_alloc(c, &e.Mh16[l], c16, "multipoles (F16 split)"))) return rc;
+        if ((rc = dev_alloc(c, &e.Ml16[l], c16, "multipoles (F16 split)"))) return rc;
+        if ((rc = dev_alloc(c, (void**)&e.Minv[l], level_boxes(l) * sizeof(float), "multipole factors"))) return rc;
     }
     return DAFMM_OK;
 }
@@ -426,6 +487,8 @@ void free_adaptive(dafmm_ctx* c, dafmm_tree* t) {
         dev_free(c, t->aM, cnt * 8); dev_free(c, t->aL, cnt * 8); dev_free(c, t->aMf, cnt * 8);
     }
     t->u_ptr = t->w_ptr = t->x_ptr = t->u_idx = t->w_idx = t->x_idx = t->leaves = t->grp_tg = t->grp_ptr = nullptr;
+    dev_free(c, t->aMinv, (size_t)t->nbox * sizeof(float));
+    t->aMinv = nullptr;
     t->a_geom = nullptr;
     t->d_rootdom = nullptr;
     t->aM = t->aL = nullptr;
@@ -681,6 +744,8 @@ int ensure_adaptive_expansions(dafmm_tree* t, int p, cudaStream_t s) {
     if ((rc = dev_alloc(c, (void**)&t->aL, cnt * 8, "locals"))) return rc;
     // FP32 multipoles, or their TF32 high parts followed by the low parts
     if ((rc = dev_alloc(c, (void**)&t->aMf, cnt * 8, "multipoles (FP32)"))) return rc;
+    if (!t->aMinv && (rc = dev_alloc(c, (void**)&t->aMinv, (size_t)t->nbox * sizeof(float), "multipole factors")))
+        return rc;
     CK(c, cudaMemsetAsync(t->aM, 0, cnt * 8, s), "memset");
     CK(c, cudaMemsetAsync(t->aL, 0, cnt * 8, s), "memset");
     CK(c, cudaMemsetAsync(t->aMf, 0, cnt * 8, s), "memset");
@@ -714,7 +779,16 @@ int eval_adaptive(dafmm_tree* t, int order, int precision, double* dphi, double*
         const size_t cnt = (size_t)t->nbox * od.ncp;
         const bool tc = precision != DAFMM_FP64 && c->m2l_kernel == 0 && c->tc_capable && order >= 2 &&
                         (precision != DAFMM_FP32 || (c->tc_mask & 1));
-        if (tc) {
+        const bool f16 = tc && precision == DAFMM_FP32 && c->m2l_f16;
+        // F16 split: hi and lo rows of rowlen16 halves, stored in the FP32 multipole buffer
+        const size_t c16 = (size_t)t->nbox * tc_rowlen16(order);
+        void* h16 = t->aMf;
+        void* l16 = reinterpret_cast<__half*>(t->aMf) + c16;
+        if (f16) {
+            if ((rc = ensure_k16(c, order, s))) return rc;
+            CK(c, tc_split_f16(t->aM, t->nbox, order, h16, l16, t->aMinv, s), "split");
+            ++launches;
+        } else if (tc) {
             CK(c, tc_split_tf32(t->aM, t->aMf, t->aMf + cnt, cnt, s), "split");
             ++launches;
         } else if (precision != DAFMM_FP64) {
@@ -728,10 +802,14 @@ int eval_adaptive(dafmm_tree* t, int order, int precision, double* dphi, double*
             mark(4);
             TCGArgs a;
             memset(&a, 0, sizeof(a));
-            a.a_hi = t->aMf;
-            a.a_lo = t->aMf + cnt;
-            a.b_hi = od.Khi;
-            a.b_lo = od.Klo;
+            a.f16 = f16;
+            a.a_hi = f16 ? h16 : (const void*)t->aMf;
+            a.a_lo = f16 ? l16 : (const void*)(t->aMf + cnt);
+            a.a_inv = t->aMinv;
+            a.b_hi = f16 ? od.Kh16 : (const void*)od.Khi;
+            a.b_lo = f16 ? od.Kl16 : (const void*)od.Klo;
+            a.inv_r = od.k16_inv_r;
+            a.inv_c = od.k16_inv_c;
             a.nkey = kNumKeys;
             a.tg = t->grp_tg;
             a.parent = t->a_parent;
@@ -1189,7 +1267,9 @@ int dafmm_eval(dafmm_tree* t, int order, double theta, int precision, double* ph
         const bool tc_m2l = precision != DAFMM_FP64 && tc_ok && (!f32 || (c->tc_mask & 1));
         const bool tc_m2m = f32 && tc_ok && (c->tc_mask & 2);     // tensor-core M2M (FP32 mode)
         const bool tc_l2l = f32 && tc_ok && (c->tc_mask & 4);     // tensor-core L2L (FP32 mode)
+        const bool f16_m2l = tc_m2l && f32 && c->m2l_f16;         // M2L on F16 split operands
         Expansions& ex = t->ex;
+        if (f16_m2l && ((rc = ensure_f16_levels(t, s)) || (rc = ensure_k16(c, order, s)))) return rc;
         auto tc_args = [&](int mode, int lmin, int lmax) {
             TCArgs a;
             memset(&a, 0, sizeof(a));
@@ -1227,7 +1307,13 @@ int dafmm_eval(dafmm_tree* t, int order, double theta, int precision, double* ph
             }
         }
         mark(2);
-        if (precision != DAFMM_FP64 && !(tc_m2m && tc_m2l))
+        if (f16_m2l) {
+            for (int l = 2; l <= L; ++l) {
+                CK(c, tc_split_f16(ex.M[l], (int)level_boxes(l), order, ex.Mh16[l], ex.Ml16[l], ex.Minv[l], s),
+                   "split");
+                ++launches;
+            }
+        } else if (precision != DAFMM_FP64 && !(tc_m2m && tc_m2l))
             for (int l = 2; l <= L; ++l) {
                 const size_t cnt = level_boxes(l) * od.ncp;
                 if (tc_m2l) {
@@ -1242,9 +1328,11 @@ int dafmm_eval(dafmm_tree* t, int order, double theta, int precision, double* ph
         if (tc_m2l) {
             mark(4);
             TCArgs a = tc_args(kTcM2L, 2, L);
+            a.f16 = f16_m2l;
             for (int l = 2; l <= L; ++l) {
-                a.a_hi[l] = ex.Mhi[l];
-                a.a_lo[l] = ex.Mlo[l];
+                a.a_hi[l] = f16_m2l ? ex.Mh16[l] : (const void*)ex.Mhi[l];
+                a.a_lo[l] = f16_m2l ? ex.Ml16[l] : (const void*)ex.Mlo[l];
+                a.a_inv[l] = ex.Minv[l];
                 a.out[l] = ex.L[l];
                 if (tc_l2l) {
                     a.out_hi[l] = ex.Lhi[l];
@@ -1252,8 +1340,10 @@ int dafmm_eval(dafmm_tree* t, int order, double theta, int precision, double* ph
                 }
                 a.scale[l] = 1.0 / ldexp(t->dom[3], -l);
             }
-            a.b_hi = od.Khi;
-            a.b_lo = od.Klo;
+            a.b_hi = f16_m2l ? od.Kh16 : (const void*)od.Khi;
+            a.b_lo = f16_m2l ? od.Kl16 : (const void*)od.Klo;
+            a.inv_r = od.k16_inv_r;
+            a.inv_c = od.k16_inv_c;
             a.nkey = kNumKeys;
             CK(c, tc_launch(order, a, s), "M2L (tensor cores)");
             ++launches;
@@ -1318,6 +1408,10 @@ int dafmm_set_option(dafmm_ctx* c, int option, int64_t value) {
     }
     if (option == DAFMM_OPT_LEAF_WARPS && (value == 1 || value == 2 || value == 4 || value == 8)) {
         c->leaf_warps = (int)value;
+        return DAFMM_OK;
+    }
+    if (option == DAFMM_OPT_M2L_F16 && (value == 0 || value == 1)) {
+        c->m2l_f16 = (int)value;
         return DAFMM_OK;
     }
     return fail(c, DAFMM_ERR_INVALID_ARG, "option");

@@ -26,6 +26,7 @@ struct dafmm_ctx {
     int m2l_kernel = 0;       // 0 tensor cores, 1 SIMT
     int tc_mask = 7;          // FP32 mode: bit 0 M2L, bit 1 M2M, bit 2 L2L on the tensor cores
     int leaf_warps = 4;       // adaptive leaf kernel: leaves (one warp each) per thread block
+    int m2l_f16 = 1;          // FP32 mode: M2L on F16 split operands (else TF32)
     int num_sms = 0;
     bool tc_capable = false;  // compute capability 10.x
     int* d_err = nullptr;     // device-side failure record of bounded waits
@@ -44,6 +45,10 @@ struct Expansions {
     float* Mlo[dafmm::kMaxUniformDepth + 1] = {};
     float* Lhi[dafmm::kMaxUniformDepth + 1] = {};
     float* Llo[dafmm::kMaxUniformDepth + 1] = {};
+    // F16 splits of the multipoles (rows of ncoef rounded up to 16) and their row factors
+    void* Mh16[dafmm::kMaxUniformDepth + 1] = {};
+    void* Ml16[dafmm::kMaxUniformDepth + 1] = {};
+    float* Minv[dafmm::kMaxUniformDepth + 1] = {};
 };
 
 struct dafmm_tree {
@@ -83,6 +88,7 @@ struct dafmm_tree {
     int a_exp_p = -1;               // order of the adaptive expansion arrays
     double *aM = nullptr, *aL = nullptr;
     float* aMf = nullptr;
+    float* aMinv = nullptr;         // per box: factor of the F16 multipole split
 };
 
 

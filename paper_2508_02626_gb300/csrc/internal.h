@@ -57,6 +57,9 @@ struct OrderData {
     int* l2l_rowptr = nullptr; unsigned short* l2l_col = nullptr; unsigned char* l2l_par = nullptr;
     double* l2l_val = nullptr; float* l2l_valf = nullptr;
     int* m2m_rp8 = nullptr; int* l2l_rp8 = nullptr;
+    // F16 splits of the M2L matrices with their power-of-two row and matrix factors
+    void* Kh16 = nullptr; void* Kl16 = nullptr;
+    float* k16_inv_r = nullptr; float* k16_inv_c = nullptr;
     int* mul_rowptr = nullptr; ushort2* mul_pairs = nullptr; short* mul_minus = nullptr;
     size_t mul_npairs = 0;
     double* K64 = nullptr;        // [343][nc][ncp]: K^_v[b][a] (scaled M2L, Eq. 5)

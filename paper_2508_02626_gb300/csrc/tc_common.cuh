@@ -5,6 +5,7 @@
 #pragma once
 #include <cuda.h>
 #include <cudaTypedefs.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -96,6 +97,14 @@ __host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
            | ((uint32_t)(M >> 4) << 24);  // M / 16
 }
 
+// instruction descriptor of kind::f16 with both operands F16: D = F32, A = B = F16, K-major
+__host__ __device__ constexpr uint32_t idesc_f16(int M, int N) {
+    return (1u << 4)                      // D format F32
+           | (0u << 7) | (0u << 10)       // A, B format F16
+           | ((uint32_t)(N >> 3) << 17)
+           | ((uint32_t)(M >> 4) << 24);
+}
+
 __device__ __forceinline__ void mma_tf32(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t acc) {
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
@@ -103,6 +112,22 @@ __device__ __forceinline__ void mma_tf32(uint32_t dtmem, uint64_t adesc, uint64_
         "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtmem),
         "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
         : "memory");
+}
+
+__device__ __forceinline__ void mma_f16(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
+        : "memory");
+}
+
+// one MMA step of the split product with TF32 (H = false) or F16 (H = true) operands
+template <bool H>
+__device__ __forceinline__ void mma_op(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t acc) {
+    if constexpr (H) mma_f16(dtmem, adesc, bdesc, idesc, acc);
+    else mma_tf32(dtmem, adesc, bdesc, idesc, acc);
 }
 
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
@@ -128,15 +153,21 @@ __device__ __forceinline__ void tmem_ld16w(uint32_t taddr, uint32_t (&r)[16]) {
 
 
 // ---- configuration per order ------------------------------------------------------------------
-template <int P>
+// H = false: TF32 operands (rows of ncp FP32 values); H = true: F16 operands (rows of ncph =
+// ncoef rounded up to 16 halves).  Either way a K chunk is 128 bytes of a row (32 TF32 or 64
+// F16 values) and one MMA step takes 32 bytes of it (K = 8 or 16).
+template <int P, bool H = false>
 struct Cfg {
     static constexpr int NC = ncoef_of(P);
     static constexpr int NCP = ncp_of(P);
+    static constexpr int ROWLEN = H ? (NC + 15) / 16 * 16 : NCP;  // operand row length, elements
+    static constexpr int KPC = H ? 64 : 32;                         // elements per 128-byte chunk
+    static constexpr int KSTEP = H ? 16 : 8;                        // elements per MMA step
     static constexpr int NPF = (NC + 15) / 16 * 16;               // N padded to the MMA granule
     static constexpr int NHALF = NPF > 192 ? 2 : 1;                // N split: <= 192 register sums per thread
     static constexpr int NP = NHALF == 1 ? NPF : (NPF / 2 + 15) / 16 * 16;
-    static constexpr int NKC = (NCP + 31) / 32;                    // K chunks of 32 (128 bytes)
-    static constexpr int KSTEPS_LAST = (NCP - 32 * (NKC - 1)) / 8; // K steps of 8 in the last chunk
+    static constexpr int NKC = (ROWLEN + KPC - 1) / KPC;           // K chunks of 128 bytes
+    static constexpr int KSTEPS_LAST = (ROWLEN - KPC * (NKC - 1)) / KSTEP;  // MMA steps in the last chunk
     static constexpr int A_BYTES = 128 * 128;
     // B rows loaded per stage: the coefficients rounded up to 8 (one swizzle atom).  The MMA
     // reads NP >= NPL rows; rows NPL..NP-1 belong to whatever follows in shared memory and only
@@ -149,12 +180,13 @@ struct Cfg {
     static constexpr int SMEM_AVAIL = 227 * 1024 - 2048 - SLACK;
     static constexpr int STAGES = (SMEM_AVAIL / STAGE_BYTES) > 4 ? 4 : (SMEM_AVAIL / STAGE_BYTES);
     static constexpr int TMEM_COLS = 2 * NP <= 256 ? 256 : 512;
-    static constexpr uint32_t IDESC = idesc_tf32(128, NP);
+    static constexpr uint32_t IDESC = H ? idesc_f16(128, NP) : idesc_tf32(128, NP);
     static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + SLACK + 1024 /*align*/ + 256 /*barriers*/;
     static_assert(NPL <= NP && NPL >= NC - (NHALF - 1) * NP, "loaded B rows");
     static_assert(NP % 16 == 0 && NP >= 16 && NP <= 192, "MMA N");
     static_assert(STAGES >= 2, "pipeline depth");
     static_assert(2 * NP <= TMEM_COLS, "TMEM double buffer");
+    static_assert(ROWLEN % KSTEP == 0 && KSTEPS_LAST >= 1 && KSTEPS_LAST <= 4, "K steps");
 };
 
 // a work item of the uniform-tree kernel: level index, target octant, child octant (L2L),
@@ -239,16 +271,18 @@ inline PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
 }
 
 
-// 3-D map (coef, row, matrix) over [nkey][npt][ncp] with boxes of np rows
-inline bool encode_rows(PFN_cuTensorMapEncodeTiled_v12000 enc, CUtensorMap* map, const float* base, int ncp, int npt,
-                        int nkey, int np) {
-    const cuuint64_t dims[3] = {(cuuint64_t)ncp, (cuuint64_t)npt, (cuuint64_t)nkey};
-    const cuuint64_t strides[2] = {(cuuint64_t)ncp * 4, (cuuint64_t)ncp * 4 * npt};
-    const cuuint32_t box[3] = {32, (cuuint32_t)np, 1};
+// 3-D map (coef, row, matrix) over [nkey][npt][rowlen] elements (FP32, or F16 when f16) with
+// boxes of 128 bytes x np rows
+inline bool encode_rows(PFN_cuTensorMapEncodeTiled_v12000 enc, CUtensorMap* map, const void* base, int rowlen, int npt,
+                        int nkey, int np, bool f16 = false) {
+    const cuuint64_t es_bytes = f16 ? 2 : 4;
+    const cuuint64_t dims[3] = {(cuuint64_t)rowlen, (cuuint64_t)npt, (cuuint64_t)nkey};
+    const cuuint64_t strides[2] = {(cuuint64_t)rowlen * es_bytes, (cuuint64_t)rowlen * es_bytes * npt};
+    const cuuint32_t box[3] = {(cuuint32_t)(128 / es_bytes), (cuuint32_t)np, 1};
     const cuuint32_t es[3] = {1, 1, 1};
-    return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, (void*)base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-               CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
-           CUDA_SUCCESS;
+    return enc(map, f16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void*>(base),
+               dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 

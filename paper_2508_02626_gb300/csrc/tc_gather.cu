@@ -61,9 +61,10 @@ __device__ __forceinline__ int m2l_source(const TCGParams& prm, int t, const Ter
     return Q >= 0 ? prm.child[8 * Q + sc] : -1;
 }
 
-template <int P>
+template <int P, bool H>
 __global__ void __launch_bounds__(192, 1) k_tcg(const __grid_constant__ TCGParams prm) {
-    using C = Cfg<P>;
+    using C = Cfg<P, H>;
+    constexpr int ESZ = H ? 2 : 4;  // operand element bytes
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     unsigned char* bar_area = base + C::STAGES * C::STAGE_BYTES + C::SLACK;
@@ -141,24 +142,26 @@ __global__ void __launch_bounds__(192, 1) k_tcg(const __grid_constant__ TCGParam
                         const uint32_t fb = smem_u32(&full[stage]);
                         mbar_expect_tx(fb, 2u * C::B_BYTES);
                         armed[stage] = (int)phase;
-                        tma_load_3d(smem_u32(st + 2 * C::A_BYTES), &prm.b_hi, fb, kc * 32, it.half * C::NP, key);
-                        tma_load_3d(smem_u32(st + 2 * C::A_BYTES + C::B_BYTES), &prm.b_lo, fb, kc * 32,
+                        tma_load_3d(smem_u32(st + 2 * C::A_BYTES), &prm.b_hi, fb, kc * C::KPC, it.half * C::NP, key);
+                        tma_load_3d(smem_u32(st + 2 * C::A_BYTES + C::B_BYTES), &prm.b_lo, fb, kc * C::KPC,
                                     it.half * C::NP, key);
                     }
                     const uint32_t sa = smem_u32(st);
+                    const char* ahi = static_cast<const char*>(prm.a_hi);
+                    const char* alo = static_cast<const char*>(prm.a_lo);
 #pragma unroll
                     for (int i = 0; i < 4; ++i) {
                         const int r = lane + 32 * i;
-                        const size_t rowoff = src[i] >= 0 ? (size_t)src[i] * C::NCP : 0;
+                        const size_t rowoff = src[i] >= 0 ? (size_t)src[i] * C::ROWLEN : 0;
                         const uint32_t rbase = (uint32_t)((r >> 3) * 1024 + (r & 7) * 128);
 #pragma unroll
                         for (int j = 0; j < 8; ++j) {
-                            const int col = kc * 32 + j * 4;
-                            const bool have = src[i] >= 0 && col < C::NCP;
-                            const size_t e = have ? rowoff + col : 0;
+                            const int col = kc * C::KPC + j * (16 / ESZ);  // first element of the 16-byte chunk
+                            const bool have = src[i] >= 0 && col < C::ROWLEN;
+                            const size_t e = have ? (rowoff + col) * ESZ : 0;
                             const uint32_t off = rbase + (uint32_t)(((j ^ (r & 7)) & 7) << 4);
-                            cp_async16(sa + off, prm.a_hi + e, have ? 16u : 0u);
-                            cp_async16(sa + C::A_BYTES + off, prm.a_lo + e, have ? 16u : 0u);
+                            cp_async16(sa + off, ahi + e, have ? 16u : 0u);
+                            cp_async16(sa + C::A_BYTES + off, alo + e, have ? 16u : 0u);
                         }
                     }
                     cp_async_commit();
@@ -216,10 +219,10 @@ __global__ void __launch_bounds__(192, 1) k_tcg(const __grid_constant__ TCGParam
                         const uint64_t al = smem_desc_sw128(st + C::A_BYTES + ks * 32);
                         const uint64_t bh = smem_desc_sw128(st + 2 * C::A_BYTES + ks * 32);
                         const uint64_t bl = smem_desc_sw128(st + 2 * C::A_BYTES + C::B_BYTES + ks * 32);
-                        mma_tf32(d, ah, bl, C::IDESC, accum);
+                        mma_op<H>(d, ah, bl, C::IDESC, accum);
                         accum = 1;
-                        mma_tf32(d, al, bh, C::IDESC, 1);
-                        mma_tf32(d, ah, bh, C::IDESC, 1);
+                        mma_op<H>(d, al, bh, C::IDESC, 1);
+                        mma_op<H>(d, ah, bh, C::IDESC, 1);
                     }
                     mma_commit(smem_u32(&empty[stage]));
                     if (++stage == C::STAGES) {
@@ -242,6 +245,8 @@ __global__ void __launch_bounds__(192, 1) k_tcg(const __grid_constant__ TCGParam
         bool ok = true;
         for (int w = blockIdx.x; w < prm.ntiles && ok; w += gridDim.x) {
             const GItem it = gdecode(prm, w);
+            const int cnt = min(128, prm.grp_count[it.g] - it.tile * 128);
+            const int trow = row < cnt ? prm.tg[prm.grp_start[it.g] + it.tile * 128 + row] : -1;
             float S[C::NP];
 #pragma unroll
             for (int j = 0; j < C::NP; ++j) S[j] = 0.f;
@@ -254,29 +259,42 @@ __global__ void __launch_bounds__(192, 1) k_tcg(const __grid_constant__ TCGParam
                 if (!ok) break;
                 accf_ph[buf] ^= 1u;
                 fence_after_sync();
+                // F16 operands: undo the source row's scale and the matrix's scalar
+                float f = 1.f;
+                if constexpr (H) {
+                    const int sb = m2l_source(prm, trow, tm);
+                    f = sb >= 0 ? prm.a_inv[sb] * prm.inv_c[(tm.v[0] + 3) * 49 + (tm.v[1] + 3) * 7 + (tm.v[2] + 3)]
+                                : 0.f;
+                }
                 const uint32_t tb = tmem_base + ((uint32_t)(32 * q) << 16) + (uint32_t)(buf * C::NP);
 #pragma unroll
                 for (int c0 = 0; c0 < C::NP; c0 += 16) {
                     uint32_t r[16];
                     tmem_ld16w(tb + c0, r);
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) S[c0 + j] += __uint_as_float(r[j]);
+                    for (int j = 0; j < 16; ++j) {
+                        if constexpr (H) S[c0 + j] = fmaf(__uint_as_float(r[j]), f, S[c0 + j]);
+                        else S[c0 + j] += __uint_as_float(r[j]);
+                    }
                 }
                 fence_before_sync();
                 mbar_arrive(smem_u32(&acc_empty[buf]));
                 ++uses;
             } while (tm.next() && ok);
             if (!ok) break;
-            const int cnt = min(128, prm.grp_count[it.g] - it.tile * 128);
-            if (row < cnt) {
-                const int t = prm.tg[prm.grp_start[it.g] + it.tile * 128 + row];
-                double* orow = prm.out + (size_t)t * C::NCP;
-                const double sc = 1.0 / prm.geom[t].w;
+            if (trow >= 0) {
+                double* orow = prm.out + (size_t)trow * C::NCP;
+                const double sc = 1.0 / prm.geom[trow].w;
 #pragma unroll
                 for (int j = 0; j < C::NP; ++j) {
                     const int b = it.half * C::NP + j;
-                    if (b < C::NC) orow[b] = (double)S[j] * sc;
-                    else if (b < C::NCP) orow[b] = 0.0;
+                    if (b < C::NC) {
+                        double v = (double)S[j] * sc;
+                        if constexpr (H) v *= (double)prm.inv_r[b];
+                        orow[b] = v;
+                    } else if (b < C::NCP) {
+                        orow[b] = 0.0;
+                    }
                 }
             }
         }
@@ -292,9 +310,9 @@ __global__ void __launch_bounds__(192, 1) k_tcg(const __grid_constant__ TCGParam
 }
 }  // namespace tc
 
-template <int P>
+template <int P, bool H>
 static cudaError_t launch_tcg(const TCGArgs& a, cudaStream_t s) {
-    using C = tc::Cfg<P>;
+    using C = tc::Cfg<P, H>;
     auto enc = get_encode();
     if (!enc) return cudaErrorNotSupported;
     if (a.ngroups > kTcgMaxGroups) return cudaErrorInvalidValue;
@@ -302,6 +320,9 @@ static cudaError_t launch_tcg(const TCGArgs& a, cudaStream_t s) {
     memset(&prm, 0, sizeof(prm));
     prm.a_hi = a.a_hi;
     prm.a_lo = a.a_lo;
+    prm.a_inv = a.a_inv;
+    prm.inv_r = a.inv_r;
+    prm.inv_c = a.inv_c;
     prm.tg = a.tg;
     prm.parent = a.parent;
     prm.colleague = a.colleague;
@@ -327,27 +348,32 @@ static cudaError_t launch_tcg(const TCGArgs& a, cudaStream_t s) {
     prm.ntiles = tiles;
     if (tiles == 0) return cudaSuccess;
     const int npt = tc_npt(P);
-    if (!encode_rows(enc, &prm.b_hi, a.b_hi, C::NCP, npt, a.nkey, C::NPL) ||
-        !encode_rows(enc, &prm.b_lo, a.b_lo, C::NCP, npt, a.nkey, C::NPL))
+    if (!encode_rows(enc, &prm.b_hi, a.b_hi, C::ROWLEN, npt, a.nkey, C::NPL, H) ||
+        !encode_rows(enc, &prm.b_lo, a.b_lo, C::ROWLEN, npt, a.nkey, C::NPL, H))
         return cudaErrorInvalidValue;
-    cudaError_t e = cudaFuncSetAttribute(tc::k_tcg<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM_BYTES);
+    cudaError_t e = cudaFuncSetAttribute(tc::k_tcg<P, H>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM_BYTES);
     if (e != cudaSuccess) return e;
     const int grid = tiles < a.num_sms ? tiles : a.num_sms;
-    tc::k_tcg<P><<<grid, 192, C::SMEM_BYTES, s>>>(prm);
+    tc::k_tcg<P, H><<<grid, 192, C::SMEM_BYTES, s>>>(prm);
     return cudaGetLastError();
+}
+
+template <int P>
+static cudaError_t launch_tcg_any(const TCGArgs& a, cudaStream_t s) {
+    return a.f16 ? launch_tcg<P, true>(a, s) : launch_tcg<P, false>(a, s);
 }
 
 cudaError_t tcg_launch(int p, const TCGArgs& a, cudaStream_t s) {
     switch (p) {
-        case 2: return launch_tcg<2>(a, s);
-        case 3: return launch_tcg<3>(a, s);
-        case 4: return launch_tcg<4>(a, s);
-        case 5: return launch_tcg<5>(a, s);
-        case 6: return launch_tcg<6>(a, s);
-        case 7: return launch_tcg<7>(a, s);
-        case 8: return launch_tcg<8>(a, s);
-        case 9: return launch_tcg<9>(a, s);
-        case 10: return launch_tcg<10>(a, s);
+        case 2: return launch_tcg_any<2>(a, s);
+        case 3: return launch_tcg_any<3>(a, s);
+        case 4: return launch_tcg_any<4>(a, s);
+        case 5: return launch_tcg_any<5>(a, s);
+        case 6: return launch_tcg_any<6>(a, s);
+        case 7: return launch_tcg_any<7>(a, s);
+        case 8: return launch_tcg_any<8>(a, s);
+        case 9: return launch_tcg_any<9>(a, s);
+        case 10: return launch_tcg_any<10>(a, s);
     }
     return cudaErrorInvalidValue;
 }

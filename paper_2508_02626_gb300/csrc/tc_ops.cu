@@ -71,9 +71,9 @@ __device__ __forceinline__ int out_index(const TCParams& prm, const WorkItem& it
 }
 
 // ---- the kernel -----------------------------------------------------------------------------
-template <int P>
+template <int P, bool H>
 __global__ void __launch_bounds__(192, 1) k_tc(const __grid_constant__ TCParams prm) {
-    using C = Cfg<P>;
+    using C = Cfg<P, H>;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     // 1024-byte aligned stage ring, then barriers
     unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -138,10 +138,11 @@ __global__ void __launch_bounds__(192, 1) k_tc(const __grid_constant__ TCParams 
                     const uint32_t fb = smem_u32(&full[stage]);
                     mbar_expect_tx(fb, 2u * a_bytes + 2u * C::B_BYTES);
                     armed[stage] = (int)phase;
-                    tma_load_5d(smem_u32(st), &prm.a_hi[it.li], fb, kc * 32, sx, sy, sz, slab);
-                    tma_load_5d(smem_u32(st + C::A_BYTES), &prm.a_lo[it.li], fb, kc * 32, sx, sy, sz, slab);
-                    tma_load_3d(smem_u32(st + 2 * C::A_BYTES), &prm.b_hi, fb, kc * 32, it.half * C::NP, key);
-                    tma_load_3d(smem_u32(st + 2 * C::A_BYTES + C::B_BYTES), &prm.b_lo, fb, kc * 32, it.half * C::NP, key);
+                    const int kx = kc * C::KPC;  // first element of the chunk (128-byte aligned)
+                    tma_load_5d(smem_u32(st), &prm.a_hi[it.li], fb, kx, sx, sy, sz, slab);
+                    tma_load_5d(smem_u32(st + C::A_BYTES), &prm.a_lo[it.li], fb, kx, sx, sy, sz, slab);
+                    tma_load_3d(smem_u32(st + 2 * C::A_BYTES), &prm.b_hi, fb, kx, it.half * C::NP, key);
+                    tma_load_3d(smem_u32(st + 2 * C::A_BYTES + C::B_BYTES), &prm.b_lo, fb, kx, it.half * C::NP, key);
                     if (++stage == C::STAGES) {
                         stage = 0;
                         phase ^= 1u;
@@ -185,10 +186,10 @@ __global__ void __launch_bounds__(192, 1) k_tc(const __grid_constant__ TCParams 
                         const uint64_t al = smem_desc_sw128(st + C::A_BYTES + ks * 32);
                         const uint64_t bh = smem_desc_sw128(st + 2 * C::A_BYTES + ks * 32);
                         const uint64_t bl = smem_desc_sw128(st + 2 * C::A_BYTES + C::B_BYTES + ks * 32);
-                        mma_tf32(d, ah, bl, C::IDESC, accum);  // small cross terms first
+                        mma_op<H>(d, ah, bl, C::IDESC, accum);  // small cross terms first
                         accum = 1;
-                        mma_tf32(d, al, bh, C::IDESC, 1);
-                        mma_tf32(d, ah, bh, C::IDESC, 1);
+                        mma_op<H>(d, al, bh, C::IDESC, 1);
+                        mma_op<H>(d, ah, bh, C::IDESC, 1);
                     }
                     mma_commit(smem_u32(&empty[stage]));
                     if (++stage == C::STAGES) {
@@ -224,13 +225,34 @@ __global__ void __launch_bounds__(192, 1) k_tc(const __grid_constant__ TCParams 
                 if (!ok) break;
                 accf_ph[buf] ^= 1u;
                 fence_after_sync();
+                // F16 operands: this term's accumulator carries the source row's scale and the
+                // matrix's scalar; undo both (one factor per row and term)
+                float f = 1.f;
+                if constexpr (H) {
+                    const int bx = prm.bx[it.li], by = prm.by[it.li], bz = prm.bz[it.li];
+                    f = 0.f;
+                    if (row < bx * by * bz) {
+                        int sx, sy, sz, slab, key;
+                        tm.source(it, sx, sy, sz, slab, key);
+                        const int S = prm.S[it.li];
+                        sx += row % bx;
+                        sy += (row / bx) % by;
+                        sz += row / (bx * by);
+                        if (sx >= 0 && sy >= 0 && sz >= 0 && sx < S && sy < S && sz < S)
+                            f = prm.a_inv[it.li][(size_t)slab * S * S * S + ((size_t)sz * S + sy) * S + sx] *
+                                prm.inv_c[key];
+                    }
+                }
                 const uint32_t tb = tmem_base + ((uint32_t)(32 * q) << 16) + (uint32_t)(buf * C::NP);
 #pragma unroll
                 for (int c0 = 0; c0 < C::NP; c0 += 16) {
                     uint32_t r[16];
                     tmem_ld16w(tb + c0, r);
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) S[c0 + j] += __uint_as_float(r[j]);
+                    for (int j = 0; j < 16; ++j) {
+                        if constexpr (H) S[c0 + j] = fmaf(__uint_as_float(r[j]), f, S[c0 + j]);
+                        else S[c0 + j] += __uint_as_float(r[j]);
+                    }
                 }
                 fence_before_sync();
                 mbar_arrive(smem_u32(&acc_empty[buf]));
@@ -251,6 +273,7 @@ __global__ void __launch_bounds__(192, 1) k_tc(const __grid_constant__ TCParams 
                     const int b = it.half * C::NP + j;
                     if (b < C::NC) {
                         double v = (double)S[j] * sc;
+                        if constexpr (H) v *= (double)prm.inv_r[b];
                         if (add) v += orow[b];
                         orow[b] = v;
                         if (hrow) {
@@ -309,6 +332,100 @@ __global__ void k_split_rows(const double* __restrict__ K64, int nkey, int nc, i
     }
 }
 
+// ---- F16 split with power-of-two scales -------------------------------------------------------
+// x = (hi + lo) / s exactly up to the rounding of lo (about 2^-22 relative to the row maximum);
+// s is a power of two that puts the largest magnitude of the row in [0.5, 1), so the halves
+// stay far from their overflow and the small coefficients lose at most 2^-25 of the row
+// maximum to F16 subnormals.
+__device__ __forceinline__ int pow2_exponent(double mx) {
+    int e = 0;
+    if (mx > 0.0) frexp(mx, &e);  // mx = f 2^e, f in [0.5, 1)
+    return e < -120 ? -120 : (e > 120 ? 120 : e);
+}
+
+__device__ __forceinline__ void split_half(double v, __half& h, __half& l) {
+    h = __double2half(v);
+    l = __double2half(v - (double)__half2float(h));
+}
+
+// one warp per row of src [nrows][ncp] -> hi, lo [nrows][rowlen] halves, inv[nrows]
+__global__ void k_split_f16_rows(const double* __restrict__ src, int nrows, int nc, int ncp, int rowlen,
+                                 __half* __restrict__ hi, __half* __restrict__ lo, float* __restrict__ inv) {
+    const int row = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (row >= nrows) return;
+    const double* x = src + (size_t)row * ncp;
+    double mx = 0.0;
+    for (int k = lane; k < nc; k += 32) mx = fmax(mx, fabs(x[k]));
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    const int e = pow2_exponent(mx);
+    const double sc = ldexp(1.0, -e);
+    for (int k = lane; k < rowlen; k += 32) {
+        __half h, l;
+        split_half(k < nc ? x[k] * sc : 0.0, h, l);
+        hi[(size_t)row * rowlen + k] = h;
+        lo[(size_t)row * rowlen + k] = l;
+    }
+    if (lane == 0) inv[row] = ldexpf(1.f, e);
+}
+
+// per row b of the matrices: the largest magnitude over all matrices -> exponent in er[b]
+__global__ void k_k16_rowexp(const double* __restrict__ K, int nkey, int nc, int ncp, int npt, float* er) {
+    const int b = blockIdx.x;
+    double mx = 0.0;
+    if (b < nc)
+        for (size_t i = threadIdx.x; i < (size_t)nkey * nc; i += blockDim.x) {
+            const size_t key = i / nc, a = i % nc;
+            mx = fmax(mx, fabs(K[(key * nc + b) * ncp + a]));
+        }
+    __shared__ double red[256];
+    red[threadIdx.x] = mx;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + o]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) er[b] = (float)pow2_exponent(red[0]);
+}
+
+// per matrix: the largest magnitude after the row scales -> exponent in ec[key]
+__global__ void k_k16_keyexp(const double* __restrict__ K, int nc, int ncp, const float* __restrict__ er, float* ec) {
+    const int key = blockIdx.x;
+    double mx = 0.0;
+    for (int i = threadIdx.x; i < nc * nc; i += blockDim.x) {
+        const int b = i / nc, a = i % nc;
+        mx = fmax(mx, fabs(ldexp(K[((size_t)key * nc + b) * ncp + a], -(int)er[b])));
+    }
+    __shared__ double red[256];
+    red[threadIdx.x] = mx;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + o]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) ec[key] = (float)pow2_exponent(red[0]);
+}
+
+__global__ void k_k16_split(const double* __restrict__ K, int nkey, int nc, int ncp, int npt, int rowlen,
+                            const float* __restrict__ er, const float* __restrict__ ec, __half* __restrict__ hi,
+                            __half* __restrict__ lo, float* __restrict__ inv_r, float* __restrict__ inv_c) {
+    const size_t n = (size_t)nkey * npt * rowlen;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const int a = (int)(i % rowlen);
+        const size_t rk = i / rowlen;
+        const int b = (int)(rk % npt);
+        const size_t key = rk / npt;
+        double v = 0.0;
+        if (b < nc && a < nc) v = ldexp(K[(key * nc + b) * ncp + a], -(int)er[b] - (int)ec[key]);
+        __half h, l;
+        split_half(v, h, l);
+        hi[i] = h;
+        lo[i] = l;
+        if (a == 0 && key == 0) inv_r[b] = b < nc ? ldexpf(1.f, (int)er[b]) : 1.f;
+        if (a == 0 && b == 0) inv_c[key] = ldexpf(1.f, (int)ec[key]);
+    }
+}
+
 }  // namespace tc
 
 // ---- host side ---------------------------------------------------------------------------------
@@ -317,6 +434,28 @@ int tc_npt(int p) {
     const int npf = (nc + 15) / 16 * 16;
     if (npf <= 192) return npf;
     return 2 * ((npf / 2 + 15) / 16 * 16);
+}
+
+int tc_rowlen16(int p) { return (ncoef_of(p) + 15) / 16 * 16; }
+
+cudaError_t tc_split_f16(const double* src, int nrows, int p, void* hi, void* lo, float* inv, cudaStream_t s) {
+    if (nrows == 0) return cudaSuccess;
+    const unsigned blocks = (unsigned)(((size_t)nrows * 32 + 255) / 256);
+    tc::k_split_f16_rows<<<blocks, 256, 0, s>>>(src, nrows, ncoef_of(p), ncp_of(p), tc_rowlen16(p),
+                                                static_cast<__half*>(hi), static_cast<__half*>(lo), inv);
+    return cudaGetLastError();
+}
+
+cudaError_t tc_prepare_k16(const double* K, int nkey, int p, void* hi, void* lo, float* inv_r, float* inv_c,
+                           float* scratch, cudaStream_t s) {
+    const int nc = ncoef_of(p), ncp = ncp_of(p), npt = tc_npt(p), rowlen = tc_rowlen16(p);
+    float* er = scratch;        // npt row exponents
+    float* ec = scratch + npt;  // nkey matrix exponents
+    tc::k_k16_rowexp<<<npt, 256, 0, s>>>(K, nkey, nc, ncp, npt, er);
+    tc::k_k16_keyexp<<<nkey, 256, 0, s>>>(K, nc, ncp, er, ec);
+    tc::k_k16_split<<<152 * 16, 256, 0, s>>>(K, nkey, nc, ncp, npt, rowlen, er, ec, static_cast<__half*>(hi),
+                                              static_cast<__half*>(lo), inv_r, inv_c);
+    return cudaGetLastError();
 }
 
 cudaError_t tc_split_tf32(const double* src, float* hi, float* lo, size_t n, cudaStream_t s) {
@@ -341,21 +480,22 @@ static void tile_shape(int S, int& bx, int& by, int& bz) {
 }
 
 // 5-D map (coef, x, y, z, slab) over an octant-major level with S slab positions per axis
-static bool encode_level(PFN_cuTensorMapEncodeTiled_v12000 enc, CUtensorMap* map, const float* base, int ncp, int S,
-                         int bx, int by, int bz) {
-    const cuuint64_t dims[5] = {(cuuint64_t)ncp, (cuuint64_t)S, (cuuint64_t)S, (cuuint64_t)S, 8};
-    const cuuint64_t row = (cuuint64_t)ncp * 4;
+static bool encode_level(PFN_cuTensorMapEncodeTiled_v12000 enc, CUtensorMap* map, const void* base, int rowlen, int S,
+                         int bx, int by, int bz, bool f16) {
+    const cuuint64_t esz = f16 ? 2 : 4;
+    const cuuint64_t dims[5] = {(cuuint64_t)rowlen, (cuuint64_t)S, (cuuint64_t)S, (cuuint64_t)S, 8};
+    const cuuint64_t row = (cuuint64_t)rowlen * esz;
     const cuuint64_t strides[4] = {row, row * S, row * S * S, row * S * S * S};
-    const cuuint32_t box[5] = {32, (cuuint32_t)bx, (cuuint32_t)by, (cuuint32_t)bz, 1};
+    const cuuint32_t box[5] = {(cuuint32_t)(128 / esz), (cuuint32_t)bx, (cuuint32_t)by, (cuuint32_t)bz, 1};
     const cuuint32_t es[5] = {1, 1, 1, 1, 1};
-    return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 5, (void*)base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-               CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
-           CUDA_SUCCESS;
+    return enc(map, f16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 5, const_cast<void*>(base),
+               dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <int P>
+template <int P, bool H>
 static cudaError_t launch_tc(const TCArgs& a, cudaStream_t s) {
-    using C = tc::Cfg<P>;
+    using C = tc::Cfg<P, H>;
     auto enc = get_encode();
     if (!enc) return cudaErrorNotSupported;
     TCParams prm;
@@ -381,34 +521,43 @@ static cudaError_t launch_tc(const TCArgs& a, cudaStream_t s) {
         prm.out_level[li] = a.mode == kTcM2M ? l - 1 : l;
         prm.tile_base[li] = tiles;
         tiles += per_tile_groups * (S / bx) * (S / by) * (S / bz) * C::NHALF;
-        if (!encode_level(enc, &prm.a_hi[li], a.a_hi[src], C::NCP, S, bx, by, bz) ||
-            !encode_level(enc, &prm.a_lo[li], a.a_lo[src], C::NCP, S, bx, by, bz))
+        prm.a_inv[li] = a.a_inv[src];
+        if (!encode_level(enc, &prm.a_hi[li], a.a_hi[src], C::ROWLEN, S, bx, by, bz, H) ||
+            !encode_level(enc, &prm.a_lo[li], a.a_lo[src], C::ROWLEN, S, bx, by, bz, H))
             return cudaErrorInvalidValue;
     }
     prm.tile_base[prm.nlev] = tiles;
     prm.ntiles = tiles;
     const int npt = tc_npt(P);
-    if (!encode_rows(enc, &prm.b_hi, a.b_hi, C::NCP, npt, a.nkey, C::NPL) ||
-        !encode_rows(enc, &prm.b_lo, a.b_lo, C::NCP, npt, a.nkey, C::NPL))
+    prm.inv_r = a.inv_r;
+    prm.inv_c = a.inv_c;
+    if (!encode_rows(enc, &prm.b_hi, a.b_hi, C::ROWLEN, npt, a.nkey, C::NPL, H) ||
+        !encode_rows(enc, &prm.b_lo, a.b_lo, C::ROWLEN, npt, a.nkey, C::NPL, H))
         return cudaErrorInvalidValue;
     if (tiles == 0) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(tc::k_tc<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM_BYTES);
+    cudaError_t e = cudaFuncSetAttribute(tc::k_tc<P, H>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM_BYTES);
     if (e != cudaSuccess) return e;
     const int grid = tiles < a.num_sms ? tiles : a.num_sms;
-    tc::k_tc<P><<<grid, 192, C::SMEM_BYTES, s>>>(prm);
+    tc::k_tc<P, H><<<grid, 192, C::SMEM_BYTES, s>>>(prm);
     return cudaGetLastError();
 }
+template <int P>
+static cudaError_t launch_tc_any(const TCArgs& a, cudaStream_t s) {
+    if (a.f16) return a.mode == kTcM2L ? launch_tc<P, true>(a, s) : cudaErrorInvalidValue;
+    return launch_tc<P, false>(a, s);
+}
+
 cudaError_t tc_launch(int p, const TCArgs& a, cudaStream_t s) {
     switch (p) {
-        case 2: return launch_tc<2>(a, s);
-        case 3: return launch_tc<3>(a, s);
-        case 4: return launch_tc<4>(a, s);
-        case 5: return launch_tc<5>(a, s);
-        case 6: return launch_tc<6>(a, s);
-        case 7: return launch_tc<7>(a, s);
-        case 8: return launch_tc<8>(a, s);
-        case 9: return launch_tc<9>(a, s);
-        case 10: return launch_tc<10>(a, s);
+        case 2: return launch_tc_any<2>(a, s);
+        case 3: return launch_tc_any<3>(a, s);
+        case 4: return launch_tc_any<4>(a, s);
+        case 5: return launch_tc_any<5>(a, s);
+        case 6: return launch_tc_any<6>(a, s);
+        case 7: return launch_tc_any<7>(a, s);
+        case 8: return launch_tc_any<8>(a, s);
+        case 9: return launch_tc_any<9>(a, s);
+        case 10: return launch_tc_any<10>(a, s);
     }
     return cudaErrorInvalidValue;
 }

@@ -27,6 +27,11 @@ struct TCParams {
     int bx[kTcMaxLevels], by[kTcMaxLevels], bz[kTcMaxLevels];
     int out_level[kTcMaxLevels];
     int tile_base[kTcMaxLevels + 1];
+    // F16 operands only: per-box factors of the A rows (per level), per-column and per-matrix
+    // factors of the B matrices (see tc_split_f16 / tc_prepare_k16)
+    const float* a_inv[kTcMaxLevels];
+    const float* inv_r;
+    const float* inv_c;
     int nlev;
     int ntiles;
     int nhalf;
@@ -38,14 +43,18 @@ struct TCParams {
 struct TCArgs {
     int mode;
     int lmin, lmax;
-    const float* a_hi[kMaxUniformDepth + 1];     // per level, [8^l][ncp] TF32 parts of the A operand
-    const float* a_lo[kMaxUniformDepth + 1];
+    bool f16;                                    // F16 split operands (M2L only), else TF32
+    const void* a_hi[kMaxUniformDepth + 1];      // per level, [8^l][rowlen] split parts of the A operand
+    const void* a_lo[kMaxUniformDepth + 1];
+    const float* a_inv[kMaxUniformDepth + 1];    // F16: per-box factor undoing the row scale
     double* out[kMaxUniformDepth + 1];           // FP64 result per level (written; added for L2L)
     float* out_hi[kMaxUniformDepth + 1];         // optional TF32 split of the result
     float* out_lo[kMaxUniformDepth + 1];
     double scale[kMaxUniformDepth + 1];
-    const float* b_hi;                           // [nkey][npt][ncp] TF32 parts of the matrices
-    const float* b_lo;
+    const void* b_hi;                            // [nkey][npt][rowlen] split parts of the matrices
+    const void* b_lo;
+    const float* inv_r;                          // F16: per-column factor of the matrices
+    const float* inv_c;                          // F16: per-matrix factor
     int nkey;
     int* err;                                    // device error flag
     int num_sms;
@@ -59,8 +68,11 @@ constexpr int kTcgMaxGroups = 8 * 21;  // (level, octant) groups of a launch
 struct TCGParams {
     CUtensorMap b_hi;
     CUtensorMap b_lo;
-    const float* a_hi;        // [nbox][ncp] TF32 parts of the multipoles
-    const float* a_lo;
+    const void* a_hi;         // [nbox][rowlen] split parts of the multipoles (TF32 or F16)
+    const void* a_lo;
+    const float* a_inv;       // F16: per-box factor undoing the row scale
+    const float* inv_r;       // F16: per-column factor of the matrices
+    const float* inv_c;       // F16: per-matrix factor
     const int* tg;            // target boxes, grouped
     const int* parent;
     const int* colleague;     // 27 per box
@@ -81,10 +93,14 @@ struct TCGParams {
 };
 
 struct TCGArgs {
-    const float* a_hi;
-    const float* a_lo;
-    const float* b_hi;        // [nkey][npt][ncp] TF32 parts of the M2L matrices
-    const float* b_lo;
+    bool f16;
+    const void* a_hi;
+    const void* a_lo;
+    const float* a_inv;
+    const void* b_hi;         // [nkey][npt][rowlen] split parts of the M2L matrices
+    const void* b_lo;
+    const float* inv_r;
+    const float* inv_c;
     int nkey;
     const int* tg;
     const int* parent;
@@ -101,6 +117,16 @@ struct TCGArgs {
 };
 
 int tc_npt(int p);  // rows of the split matrix tables (nc padded to the MMA N granule)
+int tc_rowlen16(int p);  // F16 operand row length: ncoef rounded up to 16
+// F16 split of FP64 rows [nrows][ncp] with a power-of-two scale per row (row max in [0.5, 1)):
+// hi, lo [nrows][rowlen16] halves, inv[nrows] = the factor that undoes the scale
+cudaError_t tc_split_f16(const double* src, int nrows, int p, void* hi, void* lo, float* inv, cudaStream_t s);
+// F16 split of the M2L matrices K[nkey][nc][ncp] (FP64): row b of matrix k is scaled by
+// r_b c_k (powers of two: r_b from the largest entry of row b over all matrices, c_k from the
+// largest entry of the row-scaled matrix k); hi, lo [nkey][npt][rowlen16]; inv_r[npt],
+// inv_c[nkey] undo the scales.  `scratch` holds nkey + npt floats.
+cudaError_t tc_prepare_k16(const double* K, int nkey, int p, void* hi, void* lo, float* inv_r, float* inv_c,
+                           float* scratch, cudaStream_t s);
 cudaError_t tcg_launch(int p, const TCGArgs& a, cudaStream_t s);
 cudaError_t tc_split_tf32(const double* src, float* hi, float* lo, size_t n, cudaStream_t s);
 cudaError_t tc_split_rows(const double* src, int nkey, int p, float* hi, float* lo, cudaStream_t s);

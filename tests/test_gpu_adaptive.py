@@ -204,3 +204,19 @@ def test_tensor_core_gathered_m2l(ctx, p):
         assert rel(tc_E, ref_E) <= TOL_E[prec], (prec, rel(tc_E, ref_E))
         assert rel(si_phi, ref_phi) <= TOL[prec]
         assert rel(tc_phi, si_phi) <= TOL[prec]
+
+
+@pytest.mark.parametrize("p", [4, 8, 10])
+def test_gathered_m2l_operand_splits(ctx, p):
+    """The gathered M2L with F16 and with TF32 split operands (FP32 mode), clustered tree."""
+    x, q = W.clustered(12000, seed=600 + p, charges="signed")
+    dom = O.bounding_cube(x)
+    ref_phi, ref_E = O.fmm(x, q, dom, p, max_leaf=20, max_depth=MAX_DEPTH)
+    for f16 in (1, 0):
+        B.dafmm_set_option(ctx.h, B.DAFMM_OPT_M2L_F16, f16)
+        try:
+            phi, E = gpu_eval(ctx, x, q, dom, 20, p, "fp32")
+        finally:
+            B.dafmm_set_option(ctx.h, B.DAFMM_OPT_M2L_F16, 1)
+        assert rel(phi, ref_phi) <= TOL["fp32"], (f16, rel(phi, ref_phi))
+        assert rel(E, ref_E) <= TOL_E["fp32"]

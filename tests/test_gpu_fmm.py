@@ -193,3 +193,23 @@ def test_config2_full_size_sampled(ctx):
         phi, E = gpu_eval(ctx, x, q, dom, cfg["uniform_depth"], cfg["order"], prec)
         assert rel(phi[tg], ref_phi) <= TOL[prec], (prec, rel(phi[tg], ref_phi))
         assert rel(E[tg], ref_E) <= TOL_E[prec], (prec, rel(E[tg], ref_E))
+
+
+@pytest.mark.parametrize("p", [2, 4, 6, 8, 10])
+def test_m2l_operand_splits(ctx, p):
+    """FP32 mode with the M2L operands split into F16 halves (power-of-two scales per box,
+    matrix row and matrix; the default) and into TF32 halves: both within the FP32 bound of
+    the oracle, and within it of each other."""
+    x, q = W.uniform(20000, seed=700 + p)
+    dom = W.UNIT_CUBE
+    ref_phi, ref_E = O.fmm(x, q, dom, p, uniform_depth=4)
+    out = {}
+    for f16 in (1, 0):
+        B.dafmm_set_option(ctx.h, B.DAFMM_OPT_M2L_F16, f16)
+        try:
+            out[f16] = gpu_eval(ctx, x, q, dom, 4, p, "fp32")
+        finally:
+            B.dafmm_set_option(ctx.h, B.DAFMM_OPT_M2L_F16, 1)
+        assert rel(out[f16][0], ref_phi) <= TOL["fp32"], (f16, rel(out[f16][0], ref_phi))
+        assert rel(out[f16][1], ref_E) <= TOL_E["fp32"]
+    assert rel(out[1][0], out[0][0]) <= TOL["fp32"]

@@ -27,6 +27,24 @@ sys.path.insert(0, ROOT)
 METRIC = "particles/s at rel err <=1e-7 (N=1M, p=8); served solves/s + p50/p99 latency"
 UNIT = "particles/s"
 
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of the M2L kernel on
+# this workload, from one ncu capture (profiles/k_tc_m2l_uniform_1e6_p8.md); valid while the
+# kernel's source files hash to the recorded value, reported as null otherwise
+M2L_TRAFFIC = {"fp32": (177.7e6, "93bcbf8b8ffa3b35")}
+M2L_SOURCES = ("paper_2508_02626_gb300/csrc/tc_common.cuh", "paper_2508_02626_gb300/csrc/tc_ops.cu")
+
+
+def m2l_traffic(precision):
+    import hashlib
+    rec = M2L_TRAFFIC.get(precision)
+    if rec is None:
+        return None
+    h = hashlib.sha1()
+    for f in M2L_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return rec[0] if h.hexdigest()[:16] == rec[1] else None
+
 
 def load_peaks():
     try:
@@ -242,7 +260,7 @@ def run_ours(args, rank, world):
             tiles += 8 * (S // bx) * (S // by) * (S // bz)
         executed = tiles * 189 * 3 * 2.0 * 128 * npt * klen / m2l_s / 1e12
     roofline = {"bound": bound, "achieved": round(achieved, 3), "peak": round(peak, 3), "unit": "TFLOP/s",
-                "frac": round(achieved / peak, 4), "traffic": None,
+                "frac": round(achieved / peak, 4), "traffic": m2l_traffic(args.precision), "traffic_unit": "bytes per launch",
                 "kernel": ("M2L contraction (tcgen05 kind::f16 k_tc, all levels, one launch)" if f16 else
                            "M2L contraction (tcgen05 kind::tf32 k_tc, all levels, one launch)") if bound == "tensor"
                 else "M2L (SIMT FP64 k_m2l, all levels)",

@@ -182,7 +182,8 @@ int dafmm_last_phase_ms(dafmm_ctx* ctx, double* out10);
  *   bulk paths when the order is >= 2 (default), 1 = SIMT FP32 M2L. */
 #define DAFMM_OPT_M2L_KERNEL 1
 /*   DAFMM_OPT_TC_MASK: which contractions may use the tensor cores in the FP32 mode
- *   (bit 0 M2L, bit 1 M2M, bit 2 L2L; default 7); the others run on the SIMT kernels. */
+ *   (bit 0 M2L, bit 1 M2M, bit 2 L2L; default 5: the octant-transformed SIMT M2M is the
+ *   faster one); the others run on the SIMT kernels. */
 #define DAFMM_OPT_TC_MASK 2
 /*   DAFMM_OPT_LEAF_WARPS: leaves per thread block of the adaptive near-field kernel (P2P,
  *   M2P, L2P), one warp each: 1, 2, 4 (default) or 8 -- the P2P tile the autotuner picks. */

@@ -1308,11 +1308,19 @@ int dafmm_eval(dafmm_tree* t, int order, double theta, int precision, double* ph
         }
         mark(2);
         if (f16_m2l) {
+            const double* src[8];
+            int nrows[8];
+            void *hi[8], *lo[8];
+            float* inv[8];
             for (int l = 2; l <= L; ++l) {
-                CK(c, tc_split_f16(ex.M[l], (int)level_boxes(l), order, ex.Mh16[l], ex.Ml16[l], ex.Minv[l], s),
-                   "split");
-                ++launches;
+                src[l - 2] = ex.M[l];
+                nrows[l - 2] = (int)level_boxes(l);
+                hi[l - 2] = ex.Mh16[l];
+                lo[l - 2] = ex.Ml16[l];
+                inv[l - 2] = ex.Minv[l];
             }
+            CK(c, tc_split_f16_multi(L - 1, src, nrows, hi, lo, inv, order, s), "split");
+            ++launches;
         } else if (precision != DAFMM_FP64 && !(tc_m2m && tc_m2l))
             for (int l = 2; l <= L; ++l) {
                 const size_t cnt = level_boxes(l) * od.ncp;

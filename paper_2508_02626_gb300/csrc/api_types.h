@@ -24,7 +24,7 @@ struct dafmm_ctx {
     int last_launches = 0;
     bool have_profile = false;
     int m2l_kernel = 0;       // 0 tensor cores, 1 SIMT
-    int tc_mask = 7;          // FP32 mode: bit 0 M2L, bit 1 M2M, bit 2 L2L on the tensor cores
+    int tc_mask = 5;          // FP32 mode: bit 0 M2L, bit 1 M2M, bit 2 L2L on the tensor cores
     int leaf_warps = 4;       // adaptive leaf kernel: leaves (one warp each) per thread block
     int m2l_f16 = 1;          // FP32 mode: M2L on F16 split operands (else TF32)
     int num_sms = 0;

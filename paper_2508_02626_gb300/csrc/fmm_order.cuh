@@ -49,6 +49,31 @@ struct SmemSink {
     __device__ __forceinline__ void operator()(int k, T v) const { base[k * 33 + lane] = v; }
 };
 
+// Sums one coefficient per lane over the warp's 32 particles while the generated code emits
+// the coefficients in increasing order: every 32 coefficients the [32][33] staging block is
+// reduced row by row (lane j takes coefficient 32 c + j), so the staging needs 32 x 33
+// values per warp instead of ncoef x 33.  The generated code passes k as a constant, so the
+// flush tests fold away.
+template <class T, int NJ>
+struct ChunkSink {
+    T* buf;       // [32][33] per warp
+    int lane;
+    T (&acc)[NJ];  // acc[c] += coefficient 32 c + lane
+    __device__ __forceinline__ void operator()(int k, T v) const {
+        buf[(k & 31) * 33 + lane] = v;
+        if ((k & 31) == 31 || k == NC - 1) {
+            __syncwarp();
+            if (lane <= (k & 31)) {
+                T s = T(0);
+#pragma unroll 8
+                for (int l = 0; l < 32; ++l) s += buf[lane * 33 + l];
+                acc[k >> 5] += s;
+            }
+            __syncwarp();
+        }
+    }
+};
+
 template <class T>
 struct RowLoad {
     const double* row;
@@ -73,7 +98,7 @@ __device__ __forceinline__ void warp_row_to_f32(const double* __restrict__ row, 
 template <class T>
 __global__ void k_p2m(TreeView tv, double* __restrict__ M) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T* sm = reinterpret_cast<T*>(smem_raw) + threadIdx.y * (NC * 33);
+    T* sm = reinterpret_cast<T*>(smem_raw) + threadIdx.y * (32 * 33);
     const int lane = threadIdx.x;
     const int leaf = blockIdx.x * blockDim.y + threadIdx.y;
     if (leaf >= tv.nleaf) return;
@@ -87,7 +112,7 @@ __global__ void k_p2m(TreeView tv, double* __restrict__ M) {
     T acc[NJ];
 #pragma unroll
     for (int j = 0; j < NJ; ++j) acc[j] = T(0);
-    SmemSink<T> sink{sm, lane};
+    ChunkSink<T, NJ> sink{sm, lane, acc};
     for (int base = i0; base < i1; base += 32) {
         const int i = base + lane;
         T x = T(0), y = T(0), z = T(0), q = T(0);
@@ -98,18 +123,6 @@ __global__ void k_p2m(TreeView tv, double* __restrict__ M) {
             q = (T)tv.q[i];
         }
         gen::GEN(p2m)<T>(x, y, z, q, sink);
-        __syncwarp();
-#pragma unroll
-        for (int j = 0; j < NJ; ++j) {
-            const int k = lane + 32 * j;
-            if (k < NC) {
-                T s = T(0);
-#pragma unroll 8
-                for (int l = 0; l < 32; ++l) s += sm[k * 33 + l];
-                acc[j] += s;
-            }
-        }
-        __syncwarp();
     }
 #pragma unroll
     for (int j = 0; j < NJ; ++j) {
@@ -580,7 +593,7 @@ __device__ __forceinline__ bool abox_is_leaf(const AdaptiveView& av, int b) {
 template <class T>
 __global__ void k_p2m_a(AdaptiveView av, const int* __restrict__ leaves, int nleaves, double* __restrict__ M) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T* sm = reinterpret_cast<T*>(smem_raw) + threadIdx.y * (NC * 33);
+    T* sm = reinterpret_cast<T*>(smem_raw) + threadIdx.y * (32 * 33);
     const int lane = threadIdx.x;
     const int li = blockIdx.x * blockDim.y + threadIdx.y;
     if (li >= nleaves) return;
@@ -593,7 +606,7 @@ __global__ void k_p2m_a(AdaptiveView av, const int* __restrict__ leaves, int nle
     T acc[NJ];
 #pragma unroll
     for (int j = 0; j < NJ; ++j) acc[j] = T(0);
-    SmemSink<T> sink{sm, lane};
+    ChunkSink<T, NJ> sink{sm, lane, acc};
     for (int base = i0; base < i1; base += 32) {
         const int i = base + lane;
         T x = T(0), y = T(0), z = T(0), q = T(0);
@@ -604,18 +617,6 @@ __global__ void k_p2m_a(AdaptiveView av, const int* __restrict__ leaves, int nle
             q = (T)av.q[i];
         }
         gen::GEN(p2m)<T>(x, y, z, q, sink);
-        __syncwarp();
-#pragma unroll
-        for (int j = 0; j < NJ; ++j) {
-            const int k = lane + 32 * j;
-            if (k < NC) {
-                T s = T(0);
-#pragma unroll 8
-                for (int l = 0; l < 32; ++l) s += sm[k * 33 + l];
-                acc[j] += s;
-            }
-        }
-        __syncwarp();
     }
 #pragma unroll
     for (int j = 0; j < NJ; ++j) {
@@ -730,7 +731,7 @@ __global__ void __launch_bounds__(256) k_m2l_a(const T* __restrict__ K, Adaptive
 template <class T>
 __global__ void k_p2l_a(AdaptiveView av, int lb, int le, double* __restrict__ L) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T* sm = reinterpret_cast<T*>(smem_raw) + threadIdx.y * (NC * 33);
+    T* sm = reinterpret_cast<T*>(smem_raw) + threadIdx.y * (32 * 33);
     const int lane = threadIdx.x;
     const int b = lb + blockIdx.x * blockDim.y + threadIdx.y;
     if (b >= le) return;
@@ -743,7 +744,7 @@ __global__ void k_p2l_a(AdaptiveView av, int lb, int le, double* __restrict__ L)
     T acc[NJ];
 #pragma unroll
     for (int j = 0; j < NJ; ++j) acc[j] = T(0);
-    SmemSink<T> sink{sm, lane};
+    ChunkSink<T, NJ> sink{sm, lane, acc};
     for (int xi = x0i; xi < x1i; ++xi) {
         const int c = av.x_idx[xi];
         const int i0 = av.pbeg[c], i1 = av.pend[c];
@@ -757,18 +758,6 @@ __global__ void k_p2l_a(AdaptiveView av, int lb, int le, double* __restrict__ L)
                 q = (T)av.q[i];
             }
             gen::GEN(p2l)<T>(X, Y, Z, q, sink);
-            __syncwarp();
-#pragma unroll
-            for (int j = 0; j < NJ; ++j) {
-                const int k = lane + 32 * j;
-                if (k < NC) {
-                    T s = T(0);
-#pragma unroll 8
-                    for (int l = 0; l < 32; ++l) s += sm[k * 33 + l];
-                    acc[j] += s;
-                }
-            }
-            __syncwarp();
         }
     }
 #pragma unroll
@@ -995,7 +984,7 @@ static cudaError_t set_smem(K kernel, size_t bytes) {
 static cudaError_t p2m_launch(const TreeView& tv, int prec, double* M, cudaStream_t s) {
     if (tv.nleaf == 0) return cudaSuccess;
     const bool f64 = prec == DAFMM_FP64;
-    const size_t per_warp = (size_t)NC * 33 * (f64 ? 8 : 4);
+    const size_t per_warp = (size_t)32 * 33 * (f64 ? 8 : 4);
     int wpb = (int)((96 * 1024) / per_warp);
     wpb = wpb < 1 ? 1 : (wpb > 4 ? 4 : wpb);
     const size_t smem = per_warp * wpb;
@@ -1084,7 +1073,7 @@ static cudaError_t p2m_a_launch(const AdaptiveView& av, const int* leaves, int n
                                 cudaStream_t s) {
     if (nleaves == 0) return cudaSuccess;
     const bool f64 = prec == DAFMM_FP64;
-    const size_t per_warp = (size_t)NC * 33 * (f64 ? 8 : 4);
+    const size_t per_warp = (size_t)32 * 33 * (f64 ? 8 : 4);
     int wpb = (int)((96 * 1024) / per_warp);
     wpb = wpb < 1 ? 1 : (wpb > 4 ? 4 : wpb);
     const size_t smem = per_warp * wpb;
@@ -1138,7 +1127,7 @@ static cudaError_t m2l_a_launch(const OrderData& od, const AdaptiveView& av, int
 static cudaError_t p2l_a_launch(const AdaptiveView& av, int prec, int lb, int le, double* L, cudaStream_t s) {
     if (le <= lb) return cudaSuccess;
     const bool f64 = prec == DAFMM_FP64;
-    const size_t per_warp = (size_t)NC * 33 * (f64 ? 8 : 4);
+    const size_t per_warp = (size_t)32 * 33 * (f64 ? 8 : 4);
     int wpb = (int)((96 * 1024) / per_warp);
     wpb = wpb < 1 ? 1 : (wpb > 4 ? 4 : wpb);
     const size_t smem = per_warp * wpb;

@@ -348,12 +348,28 @@ __device__ __forceinline__ void split_half(double v, __half& h, __half& l) {
     l = __double2half(v - (double)__half2float(h));
 }
 
+// up to 8 arrays of rows split in one launch; segment s covers global rows [first[s], first[s+1])
+struct F16Segments {
+    const double* src[8];
+    __half* hi[8];
+    __half* lo[8];
+    float* inv[8];
+    int first[9];
+    int nseg;
+};
+
 // one warp per row of src [nrows][ncp] -> hi, lo [nrows][rowlen] halves, inv[nrows]
-__global__ void k_split_f16_rows(const double* __restrict__ src, int nrows, int nc, int ncp, int rowlen,
-                                 __half* __restrict__ hi, __half* __restrict__ lo, float* __restrict__ inv) {
-    const int row = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
+__global__ void k_split_f16_rows(F16Segments sg, int nc, int ncp, int rowlen) {
+    int row = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
     const int lane = threadIdx.x & 31;
-    if (row >= nrows) return;
+    if (row >= sg.first[sg.nseg]) return;
+    int g = 0;
+    while (g + 1 < sg.nseg && row >= sg.first[g + 1]) ++g;
+    row -= sg.first[g];
+    const double* __restrict__ src = sg.src[g];
+    __half* __restrict__ hi = sg.hi[g];
+    __half* __restrict__ lo = sg.lo[g];
+    float* __restrict__ inv = sg.inv[g];
     const double* x = src + (size_t)row * ncp;
     double mx = 0.0;
     for (int k = lane; k < nc; k += 32) mx = fmax(mx, fabs(x[k]));
@@ -438,12 +454,28 @@ int tc_npt(int p) {
 
 int tc_rowlen16(int p) { return (ncoef_of(p) + 15) / 16 * 16; }
 
-cudaError_t tc_split_f16(const double* src, int nrows, int p, void* hi, void* lo, float* inv, cudaStream_t s) {
-    if (nrows == 0) return cudaSuccess;
-    const unsigned blocks = (unsigned)(((size_t)nrows * 32 + 255) / 256);
-    tc::k_split_f16_rows<<<blocks, 256, 0, s>>>(src, nrows, ncoef_of(p), ncp_of(p), tc_rowlen16(p),
-                                                static_cast<__half*>(hi), static_cast<__half*>(lo), inv);
+cudaError_t tc_split_f16_multi(int nseg, const double* const* src, const int* nrows, void* const* hi, void* const* lo,
+                               float* const* inv, int p, cudaStream_t s) {
+    if (nseg < 1 || nseg > 8) return cudaErrorInvalidValue;
+    tc::F16Segments sg;
+    memset(&sg, 0, sizeof(sg));
+    sg.nseg = nseg;
+    for (int g = 0; g < nseg; ++g) {
+        sg.src[g] = src[g];
+        sg.hi[g] = static_cast<__half*>(hi[g]);
+        sg.lo[g] = static_cast<__half*>(lo[g]);
+        sg.inv[g] = inv[g];
+        sg.first[g + 1] = sg.first[g] + nrows[g];
+    }
+    const int total = sg.first[nseg];
+    if (total == 0) return cudaSuccess;
+    const unsigned blocks = (unsigned)(((size_t)total * 32 + 255) / 256);
+    tc::k_split_f16_rows<<<blocks, 256, 0, s>>>(sg, ncoef_of(p), ncp_of(p), tc_rowlen16(p));
     return cudaGetLastError();
+}
+
+cudaError_t tc_split_f16(const double* src, int nrows, int p, void* hi, void* lo, float* inv, cudaStream_t s) {
+    return tc_split_f16_multi(1, &src, &nrows, &hi, &lo, &inv, p, s);
 }
 
 cudaError_t tc_prepare_k16(const double* K, int nkey, int p, void* hi, void* lo, float* inv_r, float* inv_c,

@@ -93,10 +93,15 @@ def test_tensor_core_m2l(ctx, p):
     assert rel(tc_E, ref_E) <= TOL_E["mixed"]
     assert rel(si_phi, ref_phi) <= TOL["mixed"]
     assert rel(tc_phi, si_phi) <= TOL["mixed"]
-    # FP32 mode: M2M and L2L on the tensor cores as well
-    f_phi, f_E = gpu_eval(ctx, x, q, dom, 4, p, "fp32")
-    assert rel(f_phi, ref_phi) <= TOL["fp32"], rel(f_phi, ref_phi)
-    assert rel(f_E, ref_E) <= TOL_E["fp32"]
+    # FP32 mode: L2L on the tensor cores as well (the default), and M2M too (mask 7)
+    for mask in (5, 7):
+        B.dafmm_set_option(ctx.h, B.DAFMM_OPT_TC_MASK, mask)
+        try:
+            f_phi, f_E = gpu_eval(ctx, x, q, dom, 4, p, "fp32")
+        finally:
+            B.dafmm_set_option(ctx.h, B.DAFMM_OPT_TC_MASK, 5)
+        assert rel(f_phi, ref_phi) <= TOL["fp32"], (mask, rel(f_phi, ref_phi))
+        assert rel(f_E, ref_E) <= TOL_E["fp32"]
 
 
 @pytest.mark.parametrize("depth", [0, 1, 2, 4])

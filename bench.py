@@ -113,6 +113,23 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def max_over_ranks(ms, world, device):
+    """The slowest rank's time (every rank gets it); a plain value when running alone."""
+    if world <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.barrier()
+    return float(t.item())
+
+
+def replica_throughput(units_per_rank, steps, world, max_ms):
+    """Whole-job rate of independent replicas: all ranks' units over the slowest rank's time."""
+    return units_per_rank * steps * world / (max_ms / 1e3)
+
+
 def m2l_pairs_level(level):
     """Well-separated pairs at one level of a full uniform tree (children of adjacent parents
     that are not adjacent themselves, counted axis by axis)."""
@@ -170,12 +187,8 @@ def run_ours(args, rank, world):
     torch.cuda.synchronize()
     ck = clocks.stop()
     total_ms = float(np.sum(times))
-    if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-        dist.barrier()
-    value = n * args.steps * world / (total_ms / 1e3)
+    total_ms = max_over_ranks(total_ms, world, dev)
+    value = replica_throughput(n, args.steps, world, total_ms)
     ph = {k: float(np.mean([d[k] for d in phases])) for k in phases[0]}
 
     # the other precision modes on the same tree (a few steps each), for comparison

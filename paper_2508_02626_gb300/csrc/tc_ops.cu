@@ -343,9 +343,11 @@ __device__ __forceinline__ int pow2_exponent(double mx) {
     return e < -120 ? -120 : (e > 120 ? 120 : e);
 }
 
+// v is already scaled into [-1, 1]: its FP32 rounding keeps 24 bits, more than hi + lo hold
 __device__ __forceinline__ void split_half(double v, __half& h, __half& l) {
-    h = __double2half(v);
-    l = __double2half(v - (double)__half2float(h));
+    const float f = (float)v;
+    h = __float2half_rn(f);
+    l = __float2half_rn(f - __half2float(h));
 }
 
 // up to 8 arrays of rows split in one launch; segment s covers global rows [first[s], first[s+1])

@@ -310,6 +310,10 @@ def run_ours(args, rank, world):
             out["batch"] = bench_batch(ctx, stream, flush)
         if "serving" in sections:
             out["serving"] = bench_serving(args.serving_requests)
+        if "operators" in sections:
+            out["operators"] = bench_operators(ctx)
+        if "leafsize" in sections:
+            out["leaf_size"] = bench_leaf_size(ctx)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"], out["accuracy"] = cpu_baseline(x, q, dom, cfg, phi_host, E_host)
     ctx.close()
@@ -523,6 +527,121 @@ def bench_serving(requests):
     return out
 
 
+def bench_operators(ctx):
+    """Per-operator cost, the GPU analogue of the paper's operator tables (Tables 2-8): each
+    generated operator applied to a batch of random instances (ns per instance, FP64 and
+    FP32), the batched M2L contraction inside an evaluation (ns per well-separated pair), and
+    the oracle's numerical-DA operator per call on one host core (us)."""
+    import torch
+
+    from paper_2508_02626_gb300 import binding as B
+    from paper_2508_02626_gb300 import workloads as W
+    import oracle as O
+    rng = np.random.default_rng(31)
+    out = {"note": "GPU: ns per instance of a batch of 2^18 (M2L: per pair inside a uniform N=2^18 depth-4 "
+                   "evaluation); oracle: us per call of its numerical-DA operator, one host core"}
+    count = 1 << 18
+    for p in (2, 4, 6, 8, 10):
+        nc = (p + 1) * (p + 2) * (p + 3) // 6
+        dev = "cuda"
+        s3 = torch.from_numpy(rng.uniform(-0.45, 0.45, (count, 3))).to(dev)
+        far = torch.from_numpy(rng.uniform(-0.45, 0.45, (count, 3)) + np.array([2.5, 0.3, -0.2])).to(dev)
+        qv = torch.from_numpy(rng.uniform(-1, 1, count)).to(dev)
+        C = torch.from_numpy(rng.uniform(-1, 1, (count, nc))).to(dev)
+        octs = torch.from_numpy(rng.integers(0, 8, count).astype(np.int32)).to(dev)
+        outc = torch.empty((count, nc), dtype=torch.float64, device=dev)
+        out4 = torch.empty((count, 4), dtype=torch.float64, device=dev)
+        ops = {"P2M": lambda prec: B.dafmm_op_p2m(ctx.h, p, prec, s3, qv, outc),
+               "P2L": lambda prec: B.dafmm_op_p2l(ctx.h, p, prec, far, qv, outc),
+               "L2P": lambda prec: B.dafmm_op_l2p(ctx.h, p, prec, C, s3, out4),
+               "M2P": lambda prec: B.dafmm_op_m2p(ctx.h, p, prec, C, far, out4),
+               "M2M": lambda prec: B.dafmm_op_m2m(ctx.h, p, prec, octs, C, outc),
+               "L2L": lambda prec: B.dafmm_op_l2l(ctx.h, p, prec, octs, C, outc)}
+        row = {}
+        for name, fn in ops.items():
+            r = {}
+            for pname, prec in (("gpu_fp64_ns", B.DAFMM_FP64), ("gpu_fp32_ns", B.DAFMM_FP32)):
+                fn(prec)
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                for _ in range(3):
+                    fn(prec)
+                e1.record()
+                e1.synchronize()
+                r[pname] = round(e0.elapsed_time(e1) / 3 * 1e6 / count, 4)
+            row[name] = r
+        # oracle numerical DA, one call at a time
+        s1, w1, M1 = rng.uniform(-0.45, 0.45, (1, 3)), rng.uniform(-0.45, 0.45, (1, 3)) + [2.5, 0.3, -0.2], rng.uniform(-1, 1, nc)
+        calls = {"P2M": lambda: O.p2m(p, s1, [1.0]), "P2L": lambda: O.p2l(p, w1, [1.0]),
+                 "L2P": lambda: O.l2p(p, M1, s1[0]), "M2P": lambda: O.m2p(p, M1, w1[0]),
+                 "M2M": lambda: O.m2m(p, M1, [0.25, 0.25, 0.25]), "L2L": lambda: O.l2l(p, M1, [0.25, 0.25, 0.25]),
+                 "M2L": lambda: O.m2l(p, M1, [2.0, 1.0, 0.0])}
+        for name, fn in calls.items():
+            k = 20 if p >= 8 else 100
+            t0 = time.perf_counter()
+            for _ in range(k):
+                fn()
+            row.setdefault(name, {})["oracle_da_us"] = round((time.perf_counter() - t0) / k * 1e6, 3)
+        # M2L per pair inside an evaluation
+        x, q = W.uniform(1 << 18, seed=40 + p)
+        tr = ctx.build_tree(torch.from_numpy(x).cuda(), torch.from_numpy(q).cuda(), domain=W.UNIT_CUBE, uniform_depth=4)
+        pairs = tr.info()["m2l_pairs"]
+        phi = torch.empty(len(q), dtype=torch.float64, device="cuda")
+        B.dafmm_set_profiling(ctx.h, True)
+        for pname, prec in (("gpu_fp64_ns", "fp64"), ("gpu_fp32_ns", "fp32")):
+            tr.eval(p, phi, None, precision=prec)
+            tr.eval(p, phi, None, precision=prec)
+            row["M2L"][pname] = round(B.dafmm_last_phase_ms(ctx.h)["m2l"] * 1e6 / pairs, 4)
+        tr.free()
+        out["p%d" % p] = row
+        del s3, far, qv, C, octs, outc, out4
+    return out
+
+
+def bench_leaf_size(ctx):
+    """Leaf size and linear scaling on the GPU, the analogue of the paper's leaf-size study
+    (Fig. 1, Table 10) and linear-scaling check (Fig. 2): a 3-D Gaussian of N particles
+    (q = +1), adaptive trees, FP32 mode; time of build + evaluation for each leaf size s; the
+    fastest s per (N, p) and the log-log slope of the fastest time against N."""
+    import torch
+
+    from paper_2508_02626_gb300 import workloads as W
+    sizes = (10_000, 100_000, 1_000_000, 4_000_000)
+    orders = (2, 6, 10)
+    leaf = (16, 32, 64, 128, 256, 512, 1024)
+    table, best = {}, {}
+    for n in sizes:
+        x, q = W.gaussian(n, seed=77)
+        xt, qt = torch.from_numpy(x).cuda(), torch.from_numpy(q).cuda()
+        phi = torch.empty(n, dtype=torch.float64, device="cuda")
+        for p in orders:
+            res = {}
+            for s_ in leaf:
+                if s_ >= n:
+                    continue
+                t = ctx.build_tree(xt, qt, uniform_depth=-1, max_leaf=s_)
+                t.eval(p, phi, None, precision="fp32")  # warm: tables, expansions
+                torch.cuda.synchronize()
+                t.free()
+                t0 = time.perf_counter()
+                t = ctx.build_tree(xt, qt, uniform_depth=-1, max_leaf=s_)
+                t.eval(p, phi, None, precision="fp32")
+                torch.cuda.synchronize()
+                res[s_] = round((time.perf_counter() - t0) * 1e3, 3)
+                t.free()
+            table["N%d_p%d" % (n, p)] = res
+            sb = min(res, key=res.get)
+            best.setdefault("p%d" % p, {})[n] = {"s": sb, "ms": res[sb]}
+    slopes = {}
+    for p in orders:
+        bs = best["p%d" % p]
+        ns = sorted(bs)
+        slopes["p%d" % p] = round(float(np.polyfit(np.log(ns), np.log([bs[k]["ms"] for k in ns]), 1)[0]), 3)
+    return {"workload": "3-D Gaussian (unit sigma), q = +1, adaptive, FP32, build + eval wall time (ms)",
+            "times_ms": table, "fastest": best, "loglog_slope_of_fastest": slopes}
+
+
 def cpu_baseline(x, q, dom, cfg, phi_gpu, E_gpu):
     """The oracle FMM (plain C, all host cores) on the same tree and order, for the particles
     of a sample of target leaves; the full-solve rate is extrapolated from the cost of the
@@ -619,8 +738,8 @@ def main():
     ap.add_argument("--no-workloads", action="store_true",
                     help="skip the adaptive, batched and serving workloads (N = 1 only)")
     ap.add_argument("--serving-requests", type=int, default=200)
-    ap.add_argument("--sections", default="adaptive,batch,serving",
-                    help="comma-separated extra workloads at N = 1: adaptive, batch, serving")
+    ap.add_argument("--sections", default="adaptive,batch,serving,operators,leafsize",
+                    help="comma-separated extra workloads at N = 1: adaptive, batch, serving, operators, leafsize")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))

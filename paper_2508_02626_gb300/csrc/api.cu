@@ -136,6 +136,107 @@ int upload(dafmm_ctx* c, T** dst, const T* src, size_t count, const char* what) 
     return DAFMM_OK;
 }
 
+// M2L matrices by the octahedral symmetry of 1/|w|: for a signed axis permutation g,
+// (g w)_d = sigma_d w_{pi(d)}, K_{g c}[b][a] = s(a) s(b) K_c[gamma(b)][gamma(a)] with
+// gamma(e)_{pi(d)} = e_d and s(e) = prod_d sigma_d^{e_d}.  The 316 displacements fall into 16
+// classes c = (|v| sorted descending); only those are generated by numerical DA.
+__global__ void k_ksym(const short* __restrict__ keyc, const unsigned char* __restrict__ keyperm,
+                       const unsigned char* __restrict__ keyneg, const short* __restrict__ gperm,
+                       const unsigned char* __restrict__ par, double* __restrict__ K64, float* __restrict__ K32,
+                       int nc, int ncp) {
+    const int v = blockIdx.x;
+    const int cls = keyc[v];
+    if (cls < 0) return;  // a generated representative, or an adjacent (unused) displacement
+    const short* g = gperm + (size_t)keyperm[v] * nc;
+    const unsigned neg = keyneg[v];
+    const double* Kc = K64 + (size_t)cls * nc * ncp;
+    double* Kv = K64 + (size_t)v * nc * ncp;
+    float* Kv32 = K32 + (size_t)v * nc * ncp;
+    for (int i = threadIdx.x; i < nc * nc; i += blockDim.x) {
+        const int b = i / nc, a = i - b * nc;
+        double x = Kc[(size_t)g[b] * ncp + g[a]];
+        if (__popc((par[a] ^ par[b]) & neg) & 1) x = -x;
+        Kv[(size_t)b * ncp + a] = x;
+        Kv32[(size_t)b * ncp + a] = (float)x;
+    }
+}
+
+int kgen_octahedral(dafmm_ctx* c, OrderData& od, int p, const OrderOps* ops, cudaStream_t s) {
+    const int nc = od.nc;
+    // exponents of each coefficient and their parity bits
+    std::vector<int> ex(3 * nc);
+    for (int n = 0; n <= p; ++n)
+        for (int a = n; a >= 0; --a)
+            for (int b = n - a; b >= 0; --b) {
+                const int k = da_index(a, b, n - a - b);
+                ex[3 * k] = a; ex[3 * k + 1] = b; ex[3 * k + 2] = n - a - b;
+            }
+    std::vector<unsigned char> par(nc);
+    for (int k = 0; k < nc; ++k) par[k] = (unsigned char)((ex[3 * k] & 1) | ((ex[3 * k + 1] & 1) << 1) | ((ex[3 * k + 2] & 1) << 2));
+    // the 6 axis permutations pi (pi[d] = position of axis d in the class representative)
+    const int perms[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+    std::vector<short> gperm(6 * (size_t)nc);
+    for (int q = 0; q < 6; ++q)
+        for (int k = 0; k < nc; ++k) {
+            int ge[3];
+            for (int d = 0; d < 3; ++d) ge[perms[q][d]] = ex[3 * k + d];
+            gperm[(size_t)q * nc + k] = (short)da_index(ge[0], ge[1], ge[2]);
+        }
+    std::vector<short> keyc(kNumKeys, -1), reps;
+    std::vector<unsigned char> keyperm(kNumKeys, 0), keyneg(kNumKeys, 0);
+    for (int key = 0; key < kNumKeys; ++key) {
+        const int v[3] = {key / 49 - 3, (key / 7) % 7 - 3, key % 7 - 3};
+        const int av[3] = {abs(v[0]), abs(v[1]), abs(v[2])};
+        if (std::max(av[0], std::max(av[1], av[2])) <= 1) continue;
+        int order[3] = {0, 1, 2};  // axes by |v| descending, ties by axis
+        std::sort(order, order + 3, [&](int x, int y) { return av[x] != av[y] ? av[x] > av[y] : x < y; });
+        int pi[3];
+        for (int j = 0; j < 3; ++j) pi[order[j]] = j;
+        const int ckey = (av[order[0]] + 3) * 49 + (av[order[1]] + 3) * 7 + (av[order[2]] + 3);
+        int q = 0;
+        while (!(perms[q][0] == pi[0] && perms[q][1] == pi[1] && perms[q][2] == pi[2])) ++q;
+        unsigned neg = 0;
+        for (int d = 0; d < 3; ++d)
+            if (v[d] < 0) neg |= 1u << d;
+        if (key == ckey) {
+            reps.push_back((short)key);
+        } else {
+            keyc[key] = (short)ckey;
+            keyperm[key] = (unsigned char)q;
+            keyneg[key] = (unsigned char)neg;
+        }
+    }
+    // device copies of the small tables (freed before returning)
+    const size_t b_reps = reps.size() * sizeof(short), b_keyc = keyc.size() * sizeof(short), b_kb = kNumKeys,
+                 b_g = gperm.size() * sizeof(short), b_par = (size_t)nc;
+    char* tab = nullptr;
+    const size_t total = 256 * 6 + b_reps + b_keyc + 2 * b_kb + b_g + b_par;
+    int rc = dev_alloc(c, (void**)&tab, total, "symmetry tables");
+    if (rc) return rc;
+    size_t off = 0;
+    auto put = [&](const void* src, size_t bytes) {
+        char* dst = tab + off;
+        off += (bytes + 255) / 256 * 256;
+        cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s);
+        return dst;
+    };
+    const short* d_reps = (const short*)put(reps.data(), b_reps);
+    const short* d_keyc = (const short*)put(keyc.data(), b_keyc);
+    const unsigned char* d_kp = (const unsigned char*)put(keyperm.data(), b_kb);
+    const unsigned char* d_kn = (const unsigned char*)put(keyneg.data(), b_kb);
+    const short* d_g = (const short*)put(gperm.data(), b_g);
+    const unsigned char* d_par = (const unsigned char*)put(par.data(), b_par);
+    cudaError_t e = ops->kgen(od, d_reps, (int)reps.size(), s);
+    if (e == cudaSuccess) {
+        k_ksym<<<kNumKeys, 256, 0, s>>>(d_keyc, d_kp, d_kn, d_g, d_par, od.K64, od.K32, nc, od.ncp);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    dev_free(c, tab, total);
+    if (e != cudaSuccess) return cuda_fail(c, e, "K generation");
+    return DAFMM_OK;
+}
+
 int ensure_order(dafmm_ctx* c, int p, cudaStream_t s, bool need_k) {
     if (p < 0 || p > kMaxOrder) return fail(c, DAFMM_ERR_UNSUPPORTED_ORDER, "order " + std::to_string(p));
     OrderData& od = c->ord[p];
@@ -208,7 +309,7 @@ int ensure_order(dafmm_ctx* c, int p, cudaStream_t s, bool need_k) {
         if ((rc = dev_alloc(c, (void**)&od.K32, cnt * sizeof(float), "M2L matrices (FP32)"))) return rc;
         CK(c, cudaMemsetAsync(od.K64, 0, cnt * sizeof(double), s), "K memset");
         CK(c, cudaMemsetAsync(od.K32, 0, cnt * sizeof(float), s), "K memset");
-        CK(c, ops->kgen(od, s), "K generation");
+        if ((rc = kgen_octahedral(c, od, p, ops, s))) return rc;
         if (p >= 2) {
             const size_t cs = (size_t)kNumKeys * tc_npt(p) * od.ncp;
             if ((rc = dev_alloc(c, (void**)&od.Khi, cs * sizeof(float), "M2L matrices (TF32 split)"))) return rc;

@@ -273,9 +273,9 @@ struct SmemStore {
 };
 
 __global__ void __launch_bounds__(256) k_kgen(MulTab mt, double* __restrict__ K64, float* __restrict__ K32,
-                                              int key_only) {
+                                              int key_only, const short* __restrict__ key_list) {
     __shared__ double buf[8][NCP];
-    const int key = key_only >= 0 ? key_only : blockIdx.x;
+    const int key = key_only >= 0 ? key_only : (key_list ? key_list[blockIdx.x] : blockIdx.x);
     const int vx = key / 49 - 3, vy = (key / 7) % 7 - 3, vz = key % 7 - 3;
     const int amax = max(abs(vx), max(abs(vy), abs(vz)));
     if (amax <= 1) return;  // adjacent boxes never interact through M2L
@@ -1063,8 +1063,10 @@ static cudaError_t leaf_launch(const TreeView& tv, int prec, const double* Lleaf
     return cudaGetLastError();
 }
 
-static cudaError_t kgen_launch(OrderData& od, cudaStream_t s) {
-    k_kgen<<<kNumKeys, 256, 0, s>>>(od.mul(), od.K64, od.K32, -1);
+// the matrices of the given keys (all keys when key_list is null)
+static cudaError_t kgen_launch(OrderData& od, const short* key_list, int nkeys, cudaStream_t s) {
+    if (nkeys <= 0) return cudaSuccess;
+    k_kgen<<<key_list ? nkeys : kNumKeys, 256, 0, s>>>(od.mul(), od.K64, od.K32, -1, key_list);
     return cudaGetLastError();
 }
 

@@ -111,7 +111,7 @@ struct OrderOps {
                              double* L, double inv_h, cudaStream_t);
     cudaError_t (*leaf)(const TreeView&, int prec, const double* Lleaf, double* phi, double* field,
                         cudaStream_t);
-    cudaError_t (*kgen)(OrderData&, cudaStream_t);
+    cudaError_t (*kgen)(OrderData&, const short* key_list, int nkeys, cudaStream_t);  // null list: all keys
     cudaError_t (*op_p2m)(int prec, int64_t n, const double* s, const double* q, double* out, cudaStream_t);
     cudaError_t (*op_p2l)(int prec, int64_t n, const double* w, const double* q, double* out, cudaStream_t);
     cudaError_t (*op_l2p)(int prec, int64_t n, const double* L, const double* x, double* out4, cudaStream_t);

@@ -115,3 +115,18 @@ def test_m2l_matrix_kgen(ctx, p):
         B.dafmm_op_m2l_matrix(ctx, p, v, K)
         ref = O.m2l_matrix(p, np.array(v, dtype=np.float64))
         assert np.abs(K - ref).max() <= 1e-13 * np.abs(ref).max(), v
+
+
+def test_m2l_matrices_of_every_displacement(ctx):
+    """All 316 M2L matrices of p = 6 -- 16 generated, 300 from the octahedral symmetry --
+    against the oracle's."""
+    import itertools
+    p = 6
+    nc = O.ncoef(p)
+    for v in itertools.product(range(-3, 4), repeat=3):
+        if max(map(abs, v)) < 2:
+            continue
+        K = np.zeros((nc, nc))
+        B.dafmm_op_m2l_matrix(ctx, p, list(v), K)
+        ref = O.m2l_matrix(p, np.array(v, dtype=np.float64))
+        assert np.abs(K - ref).max() <= 1e-13 * np.abs(ref).max(), v

@@ -492,7 +492,8 @@ __global__ void k_to_float(const double* __restrict__ a, float* __restrict__ b, 
 
 size_t tree_bytes(int64_t n, int depth) {
     const size_t nl = level_boxes(depth);
-    return (size_t)n * (4 * sizeof(double) + sizeof(float4) + sizeof(int)) + (nl + 1) * sizeof(int);
+    return (size_t)n * (4 * sizeof(double) + sizeof(int)) + xq_records(n, (int64_t)nl) * sizeof(float4) +
+           (nl + 1) * sizeof(int);
 }
 
 
@@ -525,6 +526,7 @@ AdaptiveView aview(const dafmm_tree* t) {
     v.w_ptr = t->w_ptr; v.w_idx = t->w_idx;
     v.x_ptr = t->x_ptr; v.x_idx = t->x_idx;
     v.geom = t->a_geom;
+    v.xq0 = t->a_xq0;
     v.x = t->x; v.y = t->y; v.z = t->z; v.q = t->q;
     v.xq = t->xq;
     v.perm = t->perm;
@@ -577,6 +579,8 @@ void free_adaptive(dafmm_ctx* c, dafmm_tree* t) {
     free_box_arrays(c, t);
     const size_t nb1 = (size_t)t->nbox + 1;
     dev_free(c, t->a_geom, (size_t)t->nbox * sizeof(double4));
+    dev_free(c, t->a_xq0, (size_t)t->nbox * sizeof(int));
+    t->a_xq0 = nullptr;
     dev_free(c, t->d_rootdom, t->rootdom.size() * sizeof(double));
     dev_free(c, t->u_ptr, nb1 * 4); dev_free(c, t->w_ptr, nb1 * 4); dev_free(c, t->x_ptr, nb1 * 4);
     dev_free(c, t->u_idx, (size_t)t->nu * 4); dev_free(c, t->w_idx, (size_t)t->nw * 4); dev_free(c, t->x_idx, (size_t)t->nx * 4);
@@ -761,9 +765,22 @@ int build_adaptive(dafmm_ctx* c, dafmm_tree* t, const double* dxyz, const double
     t->nleaves = nl;
     if ((rc = dev_alloc(c, (void**)&t->leaves, (size_t)(nl > 0 ? nl : 1) * 4, "leaves"))) return rc;
     e = launch_scatter_flagged(flags, foff, nbox, t->leaves, s);
+    if (e != cudaSuccess) return cuda_fail(c, e, "leaves");
+    // FP32 records: leaves in list order take consecutive even record ranges (at most one
+    // padding record per leaf)
+    dev_free(c, t->xq, t->xq_n4 * sizeof(float4));
+    t->xq = nullptr;
+    t->xq_n4 = xq_records(t->n, nl);
+    if ((rc = dev_alloc(c, (void**)&t->xq, t->xq_n4 * sizeof(float4), "particles"))) {
+        t->xq_n4 = 0;
+        return rc;
+    }
+    if ((rc = dev_alloc(c, (void**)&t->a_xq0, (size_t)nbox * sizeof(int), "leaf records"))) return rc;
+    CK(c, cudaMemsetAsync(t->a_xq0, 0, (size_t)nbox * sizeof(int), s), "memset");
+    e = launch_leaf_records(t->leaves, nl, t->a_pbeg, t->a_pend, flags, foff, t->a_xq0, s);
     if (e == cudaSuccess)
-        e = launch_gather_adaptive(dxyz, dq, t->perm, abuild(t, keys.as<uint64_t>()), t->leaves, nl, t->a_geom, t->x,
-                                   t->y, t->z, t->q, t->xq, s);
+        e = launch_gather_adaptive(dxyz, dq, t->perm, abuild(t, keys.as<uint64_t>()), t->leaves, nl, t->a_geom,
+                                   t->a_xq0, t->x, t->y, t->z, t->q, t->xq, t->xq_n4, s);
     if (e != cudaSuccess) return cuda_fail(c, e, "gather");
     // U, W, X lists
     const size_t nb1 = (size_t)nbox + 1;
@@ -1118,7 +1135,10 @@ int dafmm_build_tree(dafmm_ctx* c, const double* xyz, const double* q, int64_t n
     if (!rc) rc = dev_alloc(c, (void**)&t->y, N * sizeof(double), "particles");
     if (!rc) rc = dev_alloc(c, (void**)&t->z, N * sizeof(double), "particles");
     if (!rc) rc = dev_alloc(c, (void**)&t->q, N * sizeof(double), "particles");
-    if (!rc) rc = dev_alloc(c, (void**)&t->xq, N * sizeof(float4), "particles");
+    if (!rc) {
+        t->xq_n4 = xq_records(n, t->nleaf);
+        rc = dev_alloc(c, (void**)&t->xq, t->xq_n4 * sizeof(float4), "particles");
+    }
     if (!rc) rc = dev_alloc(c, (void**)&t->perm, N * sizeof(int), "particles");
     if (!rc) rc = dev_alloc(c, (void**)&t->leaf_start, ((size_t)t->nleaf + 1) * sizeof(int), "leaves");
     if (t->adaptive) {
@@ -1219,7 +1239,6 @@ int dafmm_build_forest(dafmm_ctx* c, const double* xyz, const double* q, const i
         if (!rc) rc = dev_alloc(c, (void**)&t->y, N * sizeof(double), "particles");
         if (!rc) rc = dev_alloc(c, (void**)&t->z, N * sizeof(double), "particles");
         if (!rc) rc = dev_alloc(c, (void**)&t->q, N * sizeof(double), "particles");
-        if (!rc) rc = dev_alloc(c, (void**)&t->xq, N * sizeof(float4), "particles");
         if (!rc) rc = dev_alloc(c, (void**)&t->perm, N * sizeof(int), "particles");
         if (!rc) rc = dev_alloc(c, (void**)&t->leaf_start, sizeof(int), "leaves");
     }
@@ -1256,7 +1275,7 @@ int dafmm_tree_free(dafmm_tree* t) {
     dev_free(c, t->y, N * sizeof(double));
     dev_free(c, t->z, N * sizeof(double));
     dev_free(c, t->q, N * sizeof(double));
-    dev_free(c, t->xq, N * sizeof(float4));
+    dev_free(c, t->xq, t->xq_n4 * sizeof(float4));
     dev_free(c, t->perm, N * sizeof(int));
     dev_free(c, t->leaf_start, ((size_t)t->nleaf + 1) * sizeof(int));
     dev_free(c, t->out_scratch, t->out_scratch_bytes);
@@ -1664,9 +1683,10 @@ size_t dafmm_footprint(int64_t n, int order, int uniform_depth, int max_leaf, in
     const size_t ncp = ncp_of(order), nc = ncoef_of(order);
     if (uniform_depth < 0) {
         // adaptive: about 16 n / max_leaf boxes; per box its hierarchy record, list entries
-        // (U, W and X, about 64 on average) and the expansions
+        // (U, W and X, about 64 on average), its first FP32 record, a padding record and the
+        // expansions
         const size_t nbox = 2 + (size_t)(16 * n) / (size_t)(max_leaf > 0 ? max_leaf : 1);
-        b += nbox * (kBoxInts * 4 + 64 * 4 + 24 + ncp * (8 + 8 + 4));
+        b += nbox * (kBoxInts * 4 + 64 * 4 + 24 + 16 + ncp * (8 + 8 + 4));
         b += (size_t)kNumKeys * nc * ncp * 12;
         b += (size_t)n * 12 + radix_sort_temp_bytes(n) + radix_sort_temp_bytes((int64_t)nbox);
         return b;

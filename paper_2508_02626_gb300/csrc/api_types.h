@@ -60,6 +60,7 @@ struct dafmm_tree {
     int max_per_leaf = 0;
     double *x = nullptr, *y = nullptr, *z = nullptr, *q = nullptr;
     float4* xq = nullptr;
+    size_t xq_n4 = 0;  // float4s held by xq
     int* perm = nullptr;
     int* leaf_start = nullptr;
     Expansions ex;
@@ -74,6 +75,7 @@ struct dafmm_tree {
     std::vector<int64_t> root_offs; // particles of tree r: [root_offs[r], root_offs[r+1]) in input order
     double* d_rootdom = nullptr;
     double4* a_geom = nullptr;      // per box: centre and width
+    int* a_xq0 = nullptr;           // per leaf box: its first FP32 record (even)
     int* a_root = nullptr;
     int *a_level = nullptr, *a_ijk = nullptr, *a_parent = nullptr, *a_child = nullptr;
     int *a_pbeg = nullptr, *a_pend = nullptr, *a_colleague = nullptr;

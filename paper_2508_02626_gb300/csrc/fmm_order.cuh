@@ -163,12 +163,13 @@ __device__ __forceinline__ void hadamard8(T (&m)[8]) {
             }
 }
 
-// parents per thread block of the M2M kernels: the transformed children S[8][PP][NCP + 1]
-// stay within ~180 KB of shared memory
+// parents per thread block of the M2M kernels: 8.  The NC output rows of a parent are then
+// spread over 32 threads (4 lanes in each of the 8 warps), about NC / 32 rows each; a level of
+// 4096 parents spreads over 512 blocks; and the transformed children S[8][8][NCP + 1] (43 KB in
+// FP32 at p = 8) leave room for several blocks per SM
 template <class T>
 constexpr int m2m_parents() {
-    return 8 * 32 * (NCP + 1) * (int)sizeof(T) <= 180 * 1024 ? 32
-           : 8 * 16 * (NCP + 1) * (int)sizeof(T) <= 180 * 1024 ? 16 : 8;
+    return 8;
 }
 template <class T>
 constexpr size_t m2m_smem() {
@@ -432,22 +433,30 @@ __device__ __forceinline__ float rsqrt_or_zero(float x) {
     return x >= 1.17549435e-38f ? y : 0.f;
 }
 
-// sources [s0, s1) of the float4 leaf-frame array acting on the target (tx, ty, tz), in the
-// same frame: potential and field partial sums (the field without its sign convention)
-__device__ __forceinline__ void p2p_f32(const float4* __restrict__ xq, int s0, int s1, float tx, float ty, float tz,
-                                        float& sp, float& sx, float& sy, float& sz) {
-#pragma unroll 4
-    for (int s = s0; s < s1; ++s) {
-        const float4 ps = xq[s];
-        const float ex = tx - ps.x, ey = ty - ps.y, ez = tz - ps.z;
-        const float r2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
-        const float ir = rsqrt_or_zero(r2);
-        const float qr = ps.w * ir;
-        const float qr3 = qr * (ir * ir);
-        sp += qr;
-        sx = fmaf(qr3, ex, sx);
-        sy = fmaf(qr3, ey, sy);
-        sz = fmaf(qr3, ez, sz);
+// record pairs [p0, p1) (records 2p and 2p + 1) acting on the target (tx, ty, tz), given in the
+// records' frame, with both halves of every step in one packed FP32x2 instruction: per half the
+// roundings of  e = t - s,  r2 = fma(ex, ex, fma(ey, ey, ez ez)),  qr = q / r,  qr3 = qr / r^2;
+// the halves accumulate separately in P (potential) and X, Y, Z (field without its sign
+// convention)
+__device__ __forceinline__ void p2p_pairs(const float4* __restrict__ xq, int p0, int p1, float2 tx, float2 ty,
+                                          float2 tz, float2& P, float2& X, float2& Y, float2& Z) {
+    const float2 m1 = make_float2(-1.f, -1.f);
+#pragma unroll 2
+    for (int p = p0; p < p1; ++p) {
+        const float4 A = xq[2 * p], B = xq[2 * p + 1];
+        const float2 ex = __ffma2_rn(make_float2(A.x, A.y), m1, tx);
+        const float2 ey = __ffma2_rn(make_float2(A.z, A.w), m1, ty);
+        const float2 ez = __ffma2_rn(make_float2(B.x, B.y), m1, tz);
+        float2 r2 = __fmul2_rn(ez, ez);
+        r2 = __ffma2_rn(ey, ey, r2);
+        r2 = __ffma2_rn(ex, ex, r2);
+        const float2 ir = make_float2(rsqrt_or_zero(r2.x), rsqrt_or_zero(r2.y));
+        const float2 qr = __fmul2_rn(make_float2(B.z, B.w), ir);
+        const float2 qr3 = __fmul2_rn(qr, __fmul2_rn(ir, ir));
+        P = __fadd2_rn(P, qr);
+        X = __ffma2_rn(qr3, ex, X);
+        Y = __ffma2_rn(qr3, ey, Y);
+        Z = __ffma2_rn(qr3, ez, Z);
     }
 }
 
@@ -456,6 +465,28 @@ __device__ __forceinline__ void two_sum_add(float& hi, float& lo, float v) {
     const float bp = s - hi;
     lo += (hi - (s - bp)) + (v - bp);
     hi = s;
+}
+
+// the records [r0, r0 + n) of one group (r0 even, an odd n followed by a zero record) acting on
+// the target (tx, ty, tz) in their frame, added to the compensated (hi, lo) sums: FP32 partial
+// sums over at most 64 sources, each folded into the (hi, lo) accumulators so that long
+// leaves keep FP32-level error
+struct CompSums {
+    float ph = 0.f, pl = 0.f, xh = 0.f, xl = 0.f, yh = 0.f, yl = 0.f, zh = 0.f, zl = 0.f;
+};
+
+__device__ __forceinline__ void p2p_group(const float4* __restrict__ xq, int r0, int n, float tx, float ty, float tz,
+                                          CompSums& cs) {
+    const float2 tx2 = make_float2(tx, tx), ty2 = make_float2(ty, ty), tz2 = make_float2(tz, tz);
+    const int p0 = r0 >> 1, pe = p0 + ((n + 1) >> 1);
+    for (int pb = p0; pb < pe; pb += 32) {
+        float2 P = make_float2(0.f, 0.f), X = P, Y = P, Z = P;
+        p2p_pairs(xq, pb, min(pe, pb + 32), tx2, ty2, tz2, P, X, Y, Z);
+        two_sum_add(cs.ph, cs.pl, P.x + P.y);
+        two_sum_add(cs.xh, cs.xl, X.x + X.y);
+        two_sum_add(cs.yh, cs.yl, Y.x + Y.y);
+        two_sum_add(cs.zh, cs.zl, Z.x + Z.y);
+    }
 }
 
 template <class T>
@@ -476,8 +507,9 @@ __global__ void __launch_bounds__(128) k_leaf(TreeView tv, const double* __restr
     if constexpr (sizeof(T) == 4) {
         if (Lrow) warp_row_to_f32(Lrow, s_lrow[threadIdx.y], lane);
     }
-    // the 27 neighbour leaves' particle ranges, one per lane (empty outside the domain)
-    int nb_s0 = 0, nb_s1 = 0;
+    // the 27 neighbour leaves' particle ranges, one per lane (empty outside the domain), and
+    // the first FP32 record of each
+    int nb_s0 = 0, nb_s1 = 0, nb_r0 = 0;
     if (lane < 27) {
         const int dx = lane % 3 - 1, dy = (lane / 3) % 3 - 1, dz = lane / 9 - 1;
         const int na = a + dx, nb = b + dy, nc2 = c + dz;
@@ -485,8 +517,10 @@ __global__ void __launch_bounds__(128) k_leaf(TreeView tv, const double* __restr
             const int nl = octmajor_index(tv.depth, na, nb, nc2);
             nb_s0 = tv.leaf_start[nl];
             nb_s1 = tv.leaf_start[nl + 1];
+            nb_r0 = xq_base(nb_s0, nl);
         }
     }
+    const int r_own = xq_base(i0, leaf) - i0;  // record of sorted position t: t + r_own
     for (int base = i0; base < i1; base += 32) {
         const int t = base + lane;
         const bool valid = t < i1;
@@ -514,31 +548,21 @@ __global__ void __launch_bounds__(128) k_leaf(TreeView tv, const double* __restr
                         }
                     }
         } else {
-            const float4 pt = tv.xq[tt];
-            float ph = 0.f, pl = 0.f, xh = 0.f, xl = 0.f, yh = 0.f, yl = 0.f, zh = 0.f, zl = 0.f;
+            const float4 pt = xq_load(tv.xq, tt + r_own);
+            CompSums cs;
             for (int nbi = 0; nbi < 27; ++nbi) {
                 const int s0 = __shfl_sync(0xffffffffu, nb_s0, nbi), s1 = __shfl_sync(0xffffffffu, nb_s1, nbi);
+                const int r0 = __shfl_sync(0xffffffffu, nb_r0, nbi);
                 if (s0 == s1) continue;
                 const int dx = nbi % 3 - 1, dy = (nbi / 3) % 3 - 1, dz = nbi / 9 - 1;
                 // target in the neighbour's frame (offsets in leaf widths)
-                const float tx = pt.x - (float)dx, ty = pt.y - (float)dy, tz = pt.z - (float)dz;
-                // FP32 partial sums over at most 64 sources, folded into compensated
-                // (hi, lo) accumulators so that long leaves keep FP32-level error
-                for (int sb = s0; sb < s1; sb += 64) {
-                    const int se = min(s1, sb + 64);
-                    float sp = 0.f, sx = 0.f, sy = 0.f, sz = 0.f;
-                    p2p_f32(tv.xq, sb, se, tx, ty, tz, sp, sx, sy, sz);
-                    two_sum_add(ph, pl, sp);
-                    two_sum_add(xh, xl, sx);
-                    two_sum_add(yh, yl, sy);
-                    two_sum_add(zh, zl, sz);
-                }
+                p2p_group(tv.xq, r0, s1 - s0, pt.x - (float)dx, pt.y - (float)dy, pt.z - (float)dz, cs);
             }
             const double ih = tv.inv_h_leaf, ih2 = ih * ih;
-            fphi = ((double)ph + (double)pl) * ih;
-            fx = ((double)xh + (double)xl) * ih2;
-            fy = ((double)yh + (double)yl) * ih2;
-            fz = ((double)zh + (double)zl) * ih2;
+            fphi = ((double)cs.ph + (double)cs.pl) * ih;
+            fx = ((double)cs.xh + (double)cs.xl) * ih2;
+            fy = ((double)cs.yh + (double)cs.yl) * ih2;
+            fz = ((double)cs.zh + (double)cs.zl) * ih2;
         }
         // far field from the leaf's local expansion
         if (Lrow) {
@@ -549,7 +573,7 @@ __global__ void __launch_bounds__(128) k_leaf(TreeView tv, const double* __restr
                 ys = (T)((tv.y[tt] - cy) * tv.inv_h_leaf);
                 zs = (T)((tv.z[tt] - cz) * tv.inv_h_leaf);
             } else {
-                const float4 pt = tv.xq[tt];
+                const float4 pt = xq_load(tv.xq, tt + r_own);
                 xs = (T)pt.x; ys = (T)pt.y; zs = (T)pt.z;
             }
             if constexpr (sizeof(T) == 4) gen::GEN(l2p)<T>(SmemRowF{s_lrow[threadIdx.y]}, xs, ys, zs, F, g0, g1, g2);
@@ -839,41 +863,39 @@ __global__ void __launch_bounds__(256) k_leaf_a(AdaptiveView av, const int* __re
                 }
             }
         } else {
-            const float4 pt = av.xq[tt];
-            float ph = 0.f, pl = 0.f, xh = 0.f, xl = 0.f, yh = 0.f, yl = 0.f, zh = 0.f, zl = 0.f;
+            const float4 pt = xq_load(av.xq, av.xq0[b] + (tt - i0));
+            CompSums acc;  // in target-leaf units
             for (int ui = u0; ui < u1; ++ui) {
                 const int sb = av.u_idx[ui];
                 double scx, scy, scz, sh;
                 abox_geom(av, sb, scx, scy, scz, sh);
-                // source leaf frame -> this leaf's frame: x_t_frame = off + r x_s (exact dyadic values)
-                const float r = (float)(sh * ih);
-                const float offx = (float)((scx - cx) * ih), offy = (float)((scy - cy) * ih),
-                            offz = (float)((scz - cz) * ih);
-                for (int sbeg = av.pbeg[sb]; sbeg < av.pend[sb]; sbeg += 64) {
-                    const int send = min(av.pend[sb], sbeg + 64);
-                    float sp = 0.f, sx = 0.f, sy = 0.f, sz = 0.f;
-#pragma unroll 4
-                    for (int sidx = sbeg; sidx < send; ++sidx) {
-                        const float4 ps = av.xq[sidx];
-                        const float ex = pt.x - fmaf(r, ps.x, offx), ey = pt.y - fmaf(r, ps.y, offy),
-                                    ez = pt.z - fmaf(r, ps.z, offz);
-                        const float r2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
-                        const float ir = rsqrt_or_zero(r2);
-                        const float qr = ps.w * ir;
-                        const float qr3 = qr * (ir * ir);
-                        sp += qr;
-                        sx = fmaf(qr3, ex, sx); sy = fmaf(qr3, ey, sy); sz = fmaf(qr3, ez, sz);
-                    }
-                    two_sum_add(ph, pl, sp);
-                    two_sum_add(xh, xl, sx);
-                    two_sum_add(yh, yl, sy);
-                    two_sum_add(zh, zl, sz);
+                // the target in the source leaf's frame: (x_t - off) / r with r = h_s / h a power
+                // of two; a distance in that frame is 1/r of the same distance in this leaf's, so
+                // the potential scales back by 1/r and the field by 1/r^2 (exact)
+                const float ir = (float)(h / sh);
+                const float tx = (pt.x - (float)((scx - cx) * ih)) * ir, ty = (pt.y - (float)((scy - cy) * ih)) * ir,
+                            tz = (pt.z - (float)((scz - cz) * ih)) * ir;
+                const int r0 = av.xq0[sb], ns = av.pend[sb] - av.pbeg[sb];
+                if (sh == h) {
+                    p2p_group(av.xq, r0, ns, tx, ty, tz, acc);
+                    continue;
                 }
+                CompSums cs;
+                p2p_group(av.xq, r0, ns, tx, ty, tz, cs);
+                const float ir2 = ir * ir;
+                two_sum_add(acc.ph, acc.pl, cs.ph * ir);
+                two_sum_add(acc.ph, acc.pl, cs.pl * ir);
+                two_sum_add(acc.xh, acc.xl, cs.xh * ir2);
+                two_sum_add(acc.xh, acc.xl, cs.xl * ir2);
+                two_sum_add(acc.yh, acc.yl, cs.yh * ir2);
+                two_sum_add(acc.yh, acc.yl, cs.yl * ir2);
+                two_sum_add(acc.zh, acc.zl, cs.zh * ir2);
+                two_sum_add(acc.zh, acc.zl, cs.zl * ir2);
             }
-            fphi = ((double)ph + (double)pl) * ih;
-            fx = ((double)xh + (double)xl) * ih * ih;
-            fy = ((double)yh + (double)yl) * ih * ih;
-            fz = ((double)zh + (double)zl) * ih * ih;
+            fphi = ((double)acc.ph + (double)acc.pl) * ih;
+            fx = ((double)acc.xh + (double)acc.xl) * ih * ih;
+            fy = ((double)acc.yh + (double)acc.yl) * ih * ih;
+            fz = ((double)acc.zh + (double)acc.zl) * ih * ih;
         }
         // M2P from the W list (Sec. 3.2): phi = F/h_w, E = -grad_s F / h_w^2
         for (int wi = w0; wi < w1; ++wi) {
@@ -904,7 +926,7 @@ __global__ void __launch_bounds__(256) k_leaf_a(AdaptiveView av, const int* __re
                 ys = (T)((av.y[tt] - cy) * ih);
                 zs = (T)((av.z[tt] - cz) * ih);
             } else {
-                const float4 pt = av.xq[tt];
+                const float4 pt = xq_load(av.xq, av.xq0[b] + (tt - i0));
                 xs = (T)pt.x; ys = (T)pt.y; zs = (T)pt.z;
             }
             if constexpr (sizeof(T) == 4) gen::GEN(l2p)<T>(SmemRowF{lrow}, xs, ys, zs, F, g0, g1, g2);

@@ -27,7 +27,8 @@ struct TreeView {
     double x0, y0, z0, size;
     double h_leaf, inv_h_leaf;
     const double *x, *y, *z, *q;  // sorted by leaf, FP64
-    const float4* xq;             // sorted, leaf-scaled offsets (x - c)/h and charge, FP32
+    const float4* xq;             // leaf-scaled offsets (x - c)/h and charge, FP32, pair-interleaved
+                                  // records from xq_base(leaf_start[l], l) per leaf l
     const int* perm;              // sorted position -> input index
     const int* leaf_start;        // nleaf + 1
 };

@@ -253,6 +253,67 @@ __device__ __forceinline__ float to_tf32(float x) {
 }
 
 
+// ---- epilogue: one accumulator row (one box) out to global memory -----------------------------
+// Columns b = b_base + j (j < NP) go out in groups of 4 with 16-byte accesses: NCP is a multiple
+// of 8 and every row starts on a multiple of NCP elements, so each group starts 16-byte aligned
+// in the FP32 split rows and 32-byte aligned in the FP64 row.  Value of column b < NC:
+// S[j] * sc (times inv_r[b] for scaled F16 operands), plus the old value when add; columns
+// NC..NCP-1 are written as zeros (they lie inside the last MMA step of a later stage, where a
+// stale NaN times a zero column would still be NaN).  With add the old values of a group are
+// loaded DEPTH groups ahead of its store: a load placed after a store to the same row cannot be
+// moved above it by the compiler, so without the ring every column would wait one memory round
+// trip.  hrow / lrow (optional) receive the TF32 split of the written values.
+template <int NP, int NC, int NCP, bool H>
+__device__ __forceinline__ void store_row(const float (&S)[NP], int b_base, double sc, const float* inv_r, bool add,
+                                          double* orow, float* hrow, float* lrow) {
+    constexpr int GW = 4, NG = NP / GW, DEPTH = 4;
+    static_assert(NP % 16 == 0 && NCP % 8 == 0, "column groups");
+    double2 ring[DEPTH][2];
+#pragma unroll
+    for (int g = 0; g < DEPTH; ++g) {
+        ring[g][0] = ring[g][1] = make_double2(0.0, 0.0);
+        if (add && b_base + GW * g < NCP) {
+            ring[g][0] = reinterpret_cast<const double2*>(orow + b_base + GW * g)[0];
+            ring[g][1] = reinterpret_cast<const double2*>(orow + b_base + GW * g)[1];
+        }
+    }
+#pragma unroll
+    for (int g = 0; g < NG; ++g) {
+        const int b0 = b_base + GW * g;
+        const double old[4] = {ring[g % DEPTH][0].x, ring[g % DEPTH][0].y, ring[g % DEPTH][1].x, ring[g % DEPTH][1].y};
+        if (add && g + DEPTH < NG && b0 + GW * DEPTH < NCP) {
+            ring[g % DEPTH][0] = reinterpret_cast<const double2*>(orow + b0 + GW * DEPTH)[0];
+            ring[g % DEPTH][1] = reinterpret_cast<const double2*>(orow + b0 + GW * DEPTH)[1];
+        }
+        if (b0 < NCP) {
+            double v[GW];
+#pragma unroll
+            for (int j = 0; j < GW; ++j) {
+                double x = 0.0;
+                if (b0 + j < NC) {
+                    x = (double)S[GW * g + j] * sc;
+                    if constexpr (H) x *= (double)inv_r[b0 + j];
+                    if (add) x += old[j];
+                }
+                v[j] = x;
+            }
+            reinterpret_cast<double2*>(orow + b0)[0] = make_double2(v[0], v[1]);
+            reinterpret_cast<double2*>(orow + b0)[1] = make_double2(v[2], v[3]);
+            if (hrow) {
+                float h[GW], l[GW];
+#pragma unroll
+                for (int j = 0; j < GW; ++j) {
+                    const float f = (float)v[j];
+                    h[j] = to_tf32(f);
+                    l[j] = to_tf32(f - h[j]);
+                }
+                *reinterpret_cast<float4*>(hrow + b0) = make_float4(h[0], h[1], h[2], h[3]);
+                *reinterpret_cast<float4*>(lrow + b0) = make_float4(l[0], l[1], l[2], l[3]);
+            }
+        }
+    }
+}
+
 }  // namespace tc
 
 // ---- host side: tensor maps --------------------------------------------------------------------

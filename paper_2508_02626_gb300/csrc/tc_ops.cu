@@ -266,32 +266,9 @@ __global__ void __launch_bounds__(192, 1) k_tc(const __grid_constant__ TCParams 
                 double* orow = prm.out[it.li] + t;
                 float* hrow = prm.out_hi[it.li] ? prm.out_hi[it.li] + t : nullptr;
                 float* lrow = prm.out_lo[it.li] ? prm.out_lo[it.li] + t : nullptr;
-                const double sc = prm.scale[it.li];
-                const bool add = prm.mode == kTcL2L;
-#pragma unroll
-                for (int j = 0; j < C::NP; ++j) {
-                    const int b = it.half * C::NP + j;
-                    if (b < C::NC) {
-                        double v = (double)S[j] * sc;
-                        if constexpr (H) v *= (double)prm.inv_r[b];
-                        if (add) v += orow[b];
-                        orow[b] = v;
-                        if (hrow) {
-                            const float f = (float)v;
-                            const float h = to_tf32(f);
-                            hrow[b] = h;
-                            lrow[b] = to_tf32(f - h);
-                        }
-                    } else if (b < C::NCP) {
-                        // padding columns lie inside the last MMA K step of the next stage:
-                        // they must hold zeros (a stale NaN times a zero column is NaN)
-                        orow[b] = 0.0;
-                        if (hrow) {
-                            hrow[b] = 0.f;
-                            lrow[b] = 0.f;
-                        }
-                    }
-                }
+                // L2L adds to the locals that M2L wrote
+                store_row<C::NP, C::NC, C::NCP, H>(S, it.half * C::NP, prm.scale[it.li], prm.inv_r,
+                                                   prm.mode == kTcL2L, orow, hrow, lrow);
             }
         }
     }

@@ -17,6 +17,7 @@
 
 #include "internal.h"
 #include "tree_adaptive.h"
+#include "tree_common.cuh"
 
 namespace dafmm {
 
@@ -469,8 +470,8 @@ cudaError_t launch_list_fill(AdaptiveBuild ab, int nbox, const int* pu, const in
 // ---- gather of the sorted particles: FP64 SoA and FP32 offsets in each particle's own leaf ----
 __global__ void k_gather_adaptive(const double* __restrict__ xyz, const double* __restrict__ q,
                                   const int* __restrict__ perm, AdaptiveBuild ab, const int* __restrict__ leaves,
-                                  int nleaves, const double4* __restrict__ geom, double* x, double* y, double* z,
-                                  double* qs, float4* xq) {
+                                  int nleaves, const double4* __restrict__ geom, const int* __restrict__ xq0,
+                                  double* x, double* y, double* z, double* qs, float4* xq) {
     const int li = blockIdx.x;
     if (li >= nleaves) return;
     const int b = leaves[li];
@@ -481,15 +482,42 @@ __global__ void k_gather_adaptive(const double* __restrict__ xyz, const double* 
         const int i = perm[t];
         const double px = xyz[3 * i], py = xyz[3 * i + 1], pz = xyz[3 * i + 2], pq = q[i];
         x[t] = px; y[t] = py; z[t] = pz; qs[t] = pq;
-        xq[t] = make_float4((float)((px - cx) * ih), (float)((py - cy) * ih), (float)((pz - cz) * ih), (float)pq);
+        xq_store(xq, xq0[b] + (t - ab.pbeg[b]), (float)((px - cx) * ih), (float)((py - cy) * ih),
+                 (float)((pz - cz) * ih), (float)pq);
     }
 }
 
+__global__ void k_leaf_pairs(const int* __restrict__ leaves, int nl, const int* __restrict__ pbeg,
+                             const int* __restrict__ pend, int* cnt) {
+    const int li = blockIdx.x * blockDim.x + threadIdx.x;
+    if (li < nl) {
+        const int b = leaves[li];
+        cnt[li] = (pend[b] - pbeg[b] + 1) >> 1;
+    }
+}
+
+__global__ void k_leaf_xq0(const int* __restrict__ leaves, int nl, const int* __restrict__ off, int* xq0) {
+    const int li = blockIdx.x * blockDim.x + threadIdx.x;
+    if (li < nl) xq0[leaves[li]] = 2 * off[li];
+}
+
+cudaError_t launch_leaf_records(const int* leaves, int nl, const int* pbeg, const int* pend, int* cnt, int* off,
+                                int* xq0, cudaStream_t s) {
+    if (nl == 0) return cudaSuccess;
+    k_leaf_pairs<<<(nl + 255) / 256, 256, 0, s>>>(leaves, nl, pbeg, pend, cnt);
+    cudaError_t e = launch_scan(cnt, off, nl, s);
+    if (e != cudaSuccess) return e;
+    k_leaf_xq0<<<(nl + 255) / 256, 256, 0, s>>>(leaves, nl, off, xq0);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_gather_adaptive(const double* xyz, const double* q, const int* perm, AdaptiveBuild ab,
-                                   const int* leaves, int nleaves, const double4* geom, double* x, double* y,
-                                   double* z, double* qs, float4* xq, cudaStream_t s) {
-    if (nleaves == 0) return cudaSuccess;
-    k_gather_adaptive<<<nleaves, 128, 0, s>>>(xyz, q, perm, ab, leaves, nleaves, geom, x, y, z, qs, xq);
+                                   const int* leaves, int nleaves, const double4* geom, const int* xq0, double* x,
+                                   double* y, double* z, double* qs, float4* xq, size_t xq_n4, cudaStream_t s) {
+    // the zero fill supplies the padding record of leaves with an odd particle count
+    cudaError_t e = cudaMemsetAsync(xq, 0, xq_n4 * sizeof(float4), s);
+    if (e != cudaSuccess || nleaves == 0) return e;
+    k_gather_adaptive<<<nleaves, 128, 0, s>>>(xyz, q, perm, ab, leaves, nleaves, geom, xq0, x, y, z, qs, xq);
     return cudaGetLastError();
 }
 

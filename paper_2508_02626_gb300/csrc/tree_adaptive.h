@@ -39,7 +39,9 @@ struct AdaptiveView {
     const int* x_idx;
     const double4* geom;   // per box: centre x, y, z and width h
     const double *x, *y, *z, *q;  // sorted particles
-    const float4* xq;             // offsets in the particle's own leaf, in leaf widths, and q
+    const float4* xq;             // offsets in the particle's own leaf, in leaf widths, and q (FP32,
+                                  // pair-interleaved records, those of leaf box b from xq0[b])
+    const int* xq0;               // per leaf box: its first record (even)
     const int* perm;
 };
 
@@ -67,9 +69,13 @@ cudaError_t launch_list_count(AdaptiveBuild ab, int nbox, int* cu, int* cw, int*
                               cudaStream_t s);
 cudaError_t launch_list_fill(AdaptiveBuild ab, int nbox, const int* pu, const int* pw, const int* px, int* iu, int* iw,
                              int* ix, int* err, cudaStream_t s);
+// first FP32 record of every leaf box (xq0[b], even): the leaves of the list take consecutive
+// record ranges of 2 ceil(n / 2) records; cnt and off are scratch of nl and nl + 1 ints
+cudaError_t launch_leaf_records(const int* leaves, int nl, const int* pbeg, const int* pend, int* cnt, int* off,
+                                int* xq0, cudaStream_t s);
 cudaError_t launch_gather_adaptive(const double* xyz, const double* q, const int* perm, AdaptiveBuild ab,
-                                   const int* leaves, int nleaves, const double4* geom, double* x, double* y,
-                                   double* z, double* qs, float4* xq, cudaStream_t s);
+                                   const int* leaves, int nleaves, const double4* geom, const int* xq0, double* x,
+                                   double* y, double* z, double* qs, float4* xq, size_t xq_n4, cudaStream_t s);
 
 cudaError_t launch_leaf_flags(const int* child, int nbox, int* flags, cudaStream_t s);
 cudaError_t launch_scatter_flagged(const int* flags, const int* offs, int nbox, int* out, cudaStream_t s);

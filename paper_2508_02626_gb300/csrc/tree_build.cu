@@ -218,8 +218,9 @@ __global__ void k_gather_uniform(const double* __restrict__ xyz, const double* _
     const double cx = tv.x0 + ((double)a + 0.5) * tv.h_leaf;
     const double cy = tv.y0 + ((double)b + 0.5) * tv.h_leaf;
     const double cz = tv.z0 + ((double)c + 0.5) * tv.h_leaf;
-    xq[t] = make_float4((float)((px - cx) * tv.inv_h_leaf), (float)((py - cy) * tv.inv_h_leaf),
-                        (float)((pz - cz) * tv.inv_h_leaf), (float)pq);
+    const int leaf = (int)keys[t], p0 = tv.leaf_start[leaf];
+    xq_store(xq, xq_base(p0, leaf) + (int)(t - p0), (float)((px - cx) * tv.inv_h_leaf),
+             (float)((py - cy) * tv.inv_h_leaf), (float)((pz - cz) * tv.inv_h_leaf), (float)pq);
 }
 
 __global__ void k_leaf_ranges(const uint64_t* __restrict__ keys, int64_t n, int nleaf, int* leaf_start) {
@@ -238,10 +239,15 @@ __global__ void k_leaf_ranges(const uint64_t* __restrict__ keys, int64_t n, int 
 cudaError_t launch_gather_uniform(const double* xyz, const double* q, const int* perm, int64_t n,
                                   const uint64_t* sorted_keys, TreeView tv, double* x, double* y,
                                   double* z, double* qs, float4* xq, int* leaf_start, cudaStream_t s) {
+    // leaf ranges first: the gather places each leaf's FP32 records from its first position;
+    // the zero fill supplies the padding record of odd leaves
+    k_leaf_ranges<<<(tv.nleaf + 1 + 255) / 256, 256, 0, s>>>(sorted_keys, n, tv.nleaf, leaf_start);
+    cudaError_t e = cudaMemsetAsync(xq, 0, xq_records(n, tv.nleaf) * sizeof(float4), s);
+    if (e != cudaSuccess) return e;
+    tv.leaf_start = leaf_start;
     if (n > 0)
         k_gather_uniform<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(xyz, q, perm, n, sorted_keys, tv, x,
                                                                      y, z, qs, xq);
-    k_leaf_ranges<<<(tv.nleaf + 1 + 255) / 256, 256, 0, s>>>(sorted_keys, n, tv.nleaf, leaf_start);
     return cudaGetLastError();
 }
 

@@ -489,6 +489,17 @@ __device__ __forceinline__ void p2p_group(const float4* __restrict__ xq, int r0,
     }
 }
 
+// copies record pairs [p, p + np) (np <= 32) into dst with 16-byte asynchronous copies, one
+// or two per lane, as one commit group of the calling thread
+__device__ __forceinline__ void stage_pairs(float4* dst, const float4* __restrict__ xq, int p, int np, int lane) {
+    const float4* src = xq + 2 * p;
+    for (int i = lane; i < 2 * np; i += 32) {
+        const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst + i));
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src + i) : "memory");
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
 template <class T>
 __global__ void __launch_bounds__(128) k_leaf(TreeView tv, const double* __restrict__ Lleaf,
                                               double* __restrict__ phi, double* __restrict__ field) {
@@ -550,13 +561,51 @@ __global__ void __launch_bounds__(128) k_leaf(TreeView tv, const double* __restr
         } else {
             const float4 pt = xq_load(tv.xq, tt + r_own);
             CompSums cs;
-            for (int nbi = 0; nbi < 27; ++nbi) {
-                const int s0 = __shfl_sync(0xffffffffu, nb_s0, nbi), s1 = __shfl_sync(0xffffffffu, nb_s1, nbi);
-                const int r0 = __shfl_sync(0xffffffffu, nb_r0, nbi);
-                if (s0 == s1) continue;
-                const int dx = nbi % 3 - 1, dy = (nbi / 3) % 3 - 1, dz = nbi / 9 - 1;
+            // the neighbours' records in chunks of at most 32 pairs, neighbour by neighbour,
+            // each staged in shared memory while the warp works on the one before it
+            __shared__ __align__(16) float4 s_rec[4][2][64];
+            float4(*buf)[64] = s_rec[threadIdx.y];
+            int nk = 0, np_ = 0, ne = 0, nbc = -1;  // cursor: next neighbour, next pair, end pair
+            auto next_chunk = [&](int& k, int& p, int& n) -> bool {
+                while (np_ >= ne) {
+                    if (nk >= 27) return false;
+                    const int s0 = __shfl_sync(0xffffffffu, nb_s0, nk), s1 = __shfl_sync(0xffffffffu, nb_s1, nk);
+                    const int r0 = __shfl_sync(0xffffffffu, nb_r0, nk);
+                    nbc = nk++;
+                    np_ = r0 >> 1;
+                    ne = np_ + ((s1 - s0 + 1) >> 1);
+                }
+                k = nbc;
+                p = np_;
+                n = min(32, ne - np_);
+                np_ += n;
+                return true;
+            };
+            int k0 = 0, p0 = 0, n0 = 0, sb = 0;
+            bool have = next_chunk(k0, p0, n0);
+            if (have) stage_pairs(buf[0], tv.xq, p0, n0, lane);
+            while (have) {
+                int k1 = 0, p1 = 0, n1 = 0;
+                const bool more = next_chunk(k1, p1, n1);
+                if (more) stage_pairs(buf[sb ^ 1], tv.xq, p1, n1, lane);
+                else asm volatile("cp.async.commit_group;" ::: "memory");
+                asm volatile("cp.async.wait_group 1;" ::: "memory");  // this chunk's copies landed
+                __syncwarp();
+                const int dx = k0 % 3 - 1, dy = (k0 / 3) % 3 - 1, dz = k0 / 9 - 1;
                 // target in the neighbour's frame (offsets in leaf widths)
-                p2p_group(tv.xq, r0, s1 - s0, pt.x - (float)dx, pt.y - (float)dy, pt.z - (float)dz, cs);
+                const float tx = pt.x - (float)dx, ty = pt.y - (float)dy, tz = pt.z - (float)dz;
+                float2 P = make_float2(0.f, 0.f), X = P, Y = P, Z = P;
+                p2p_pairs(buf[sb], 0, n0, make_float2(tx, tx), make_float2(ty, ty), make_float2(tz, tz), P, X, Y, Z);
+                two_sum_add(cs.ph, cs.pl, P.x + P.y);
+                two_sum_add(cs.xh, cs.xl, X.x + X.y);
+                two_sum_add(cs.yh, cs.yl, Y.x + Y.y);
+                two_sum_add(cs.zh, cs.zl, Z.x + Z.y);
+                __syncwarp();  // every lane is done with buf[sb] before it is refilled
+                k0 = k1;
+                p0 = p1;
+                n0 = n1;
+                have = more;
+                sb ^= 1;
             }
             const double ih = tv.inv_h_leaf, ih2 = ih * ih;
             fphi = ((double)cs.ph + (double)cs.pl) * ih;

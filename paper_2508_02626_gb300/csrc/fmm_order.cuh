@@ -441,7 +441,7 @@ __device__ __forceinline__ float rsqrt_or_zero(float x) {
 __device__ __forceinline__ void p2p_pairs(const float4* __restrict__ xq, int p0, int p1, float2 tx, float2 ty,
                                           float2 tz, float2& P, float2& X, float2& Y, float2& Z) {
     const float2 m1 = make_float2(-1.f, -1.f);
-#pragma unroll 2
+#pragma unroll 4
     for (int p = p0; p < p1; ++p) {
         const float4 A = xq[2 * p], B = xq[2 * p + 1];
         const float2 ex = __ffma2_rn(make_float2(A.x, A.y), m1, tx);

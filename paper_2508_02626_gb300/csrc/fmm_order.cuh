@@ -489,15 +489,14 @@ __device__ __forceinline__ void p2p_group(const float4* __restrict__ xq, int r0,
     }
 }
 
-// copies record pairs [p, p + np) (np <= 32) into dst with 16-byte asynchronous copies, one
-// or two per lane, as one commit group of the calling thread
+// starts the copy of record pairs [p, p + np) (np <= 32) into dst: 16-byte asynchronous copies,
+// one or two per lane (the caller commits them as a group)
 __device__ __forceinline__ void stage_pairs(float4* dst, const float4* __restrict__ xq, int p, int np, int lane) {
     const float4* src = xq + 2 * p;
     for (int i = lane; i < 2 * np; i += 32) {
         const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst + i));
         asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src + i) : "memory");
     }
-    asm volatile("cp.async.commit_group;" ::: "memory");
 }
 
 template <class T>
@@ -533,9 +532,14 @@ __global__ void __launch_bounds__(128) k_leaf(TreeView tv, const double* __restr
     }
     const int r_own = xq_base(i0, leaf) - i0;  // record of sorted position t: t + r_own
     for (int base = i0; base < i1; base += 32) {
-        const int t = base + lane;
-        const bool valid = t < i1;
-        const int tt = valid ? t : i0;
+        // FP32: a pass of at most 16 targets splits the sources between the two half-warps,
+        // lane l and lane l + 16 taking the same target
+        const int m = min(32, i1 - base);
+        const bool split = sizeof(T) == 4 && m <= 16;
+        const int tl = split ? (lane & 15) : lane;
+        const int t = base + tl;
+        const bool valid = tl < m && (!split || lane < 16);  // the lanes that write
+        const int tt = tl < m ? t : i0;
         double fphi = 0.0, fx = 0.0, fy = 0.0, fz = 0.0;  // near field, physical units
         if constexpr (sizeof(T) == 8) {
             const double xt = tv.x[tt], yt = tv.y[tt], zt = tv.z[tt];
@@ -563,8 +567,13 @@ __global__ void __launch_bounds__(128) k_leaf(TreeView tv, const double* __restr
             CompSums cs;
             // the neighbours' records in chunks of at most 32 pairs, neighbour by neighbour,
             // each staged in shared memory while the warp works on the one before it
-            __shared__ __align__(16) float4 s_rec[4][2][64];
-            float4(*buf)[64] = s_rec[threadIdx.y];
+            // the neighbours' records in chunks of at most 32 pairs, neighbour by neighbour; a
+            // step takes one chunk per lane group (the chunks of a split pass alternate between
+            // the half-warps) and is staged in shared memory while the warp works on the step
+            // before it.  Rows of 65 float4s keep the two groups' reads on different banks.
+            __shared__ __align__(16) float4 s_rec[4][2][2][65];
+            float4(*buf)[2][65] = s_rec[threadIdx.y];
+            const int G = split ? 2 : 1, g = split ? lane >> 4 : 0;
             int nk = 0, np_ = 0, ne = 0, nbc = -1;  // cursor: next neighbour, next pair, end pair
             auto next_chunk = [&](int& k, int& p, int& n) -> bool {
                 while (np_ >= ne) {
@@ -581,31 +590,58 @@ __global__ void __launch_bounds__(128) k_leaf(TreeView tv, const double* __restr
                 np_ += n;
                 return true;
             };
-            int k0 = 0, p0 = 0, n0 = 0, sb = 0;
-            bool have = next_chunk(k0, p0, n0);
-            if (have) stage_pairs(buf[0], tv.xq, p0, n0, lane);
-            while (have) {
-                int k1 = 0, p1 = 0, n1 = 0;
-                const bool more = next_chunk(k1, p1, n1);
-                if (more) stage_pairs(buf[sb ^ 1], tv.xq, p1, n1, lane);
-                else asm volatile("cp.async.commit_group;" ::: "memory");
-                asm volatile("cp.async.wait_group 1;" ::: "memory");  // this chunk's copies landed
+            // the next step: up to G chunks, copied into buf[st] as one commit group; returns
+            // the number of chunks
+            int ks[2], ns[2];
+            auto next_step = [&](int st, int (&k)[2], int (&n)[2]) -> int {
+                int c = 0, p;
+                while (c < G && next_chunk(k[c], p, n[c])) {
+                    stage_pairs(buf[st][c], tv.xq, p, n[c], lane);
+                    ++c;
+                }
+                asm volatile("cp.async.commit_group;" ::: "memory");
+                return c;
+            };
+            int sb = 0;
+            int c0 = next_step(0, ks, ns);
+            while (c0 > 0) {
+                const int k0 = g < c0 ? ks[g] : 0, n0 = g < c0 ? ns[g] : 0;
+                int kn[2], nn[2];
+                const int c1 = next_step(sb ^ 1, kn, nn);
+                asm volatile("cp.async.wait_group 1;" ::: "memory");  // this step's copies landed
                 __syncwarp();
                 const int dx = k0 % 3 - 1, dy = (k0 / 3) % 3 - 1, dz = k0 / 9 - 1;
                 // target in the neighbour's frame (offsets in leaf widths)
                 const float tx = pt.x - (float)dx, ty = pt.y - (float)dy, tz = pt.z - (float)dz;
                 float2 P = make_float2(0.f, 0.f), X = P, Y = P, Z = P;
-                p2p_pairs(buf[sb], 0, n0, make_float2(tx, tx), make_float2(ty, ty), make_float2(tz, tz), P, X, Y, Z);
-                two_sum_add(cs.ph, cs.pl, P.x + P.y);
-                two_sum_add(cs.xh, cs.xl, X.x + X.y);
-                two_sum_add(cs.yh, cs.yl, Y.x + Y.y);
-                two_sum_add(cs.zh, cs.zl, Z.x + Z.y);
+                p2p_pairs(buf[sb][g], 0, n0, make_float2(tx, tx), make_float2(ty, ty), make_float2(tz, tz), P, X, Y,
+                          Z);
+                if (n0 > 0) {
+                    two_sum_add(cs.ph, cs.pl, P.x + P.y);
+                    two_sum_add(cs.xh, cs.xl, X.x + X.y);
+                    two_sum_add(cs.yh, cs.yl, Y.x + Y.y);
+                    two_sum_add(cs.zh, cs.zl, Z.x + Z.y);
+                }
                 __syncwarp();  // every lane is done with buf[sb] before it is refilled
-                k0 = k1;
-                p0 = p1;
-                n0 = n1;
-                have = more;
+                for (int j = 0; j < 2; ++j) {
+                    ks[j] = kn[j];
+                    ns[j] = nn[j];
+                }
+                c0 = c1;
                 sb ^= 1;
+            }
+            if (split) {  // the upper half-warp's sums join the lower one's
+                float v[8] = {cs.ph, cs.pl, cs.xh, cs.xl, cs.yh, cs.yl, cs.zh, cs.zl};
+#pragma unroll
+                for (int j = 0; j < 8; ++j) v[j] = __shfl_down_sync(0xffffffffu, v[j], 16);
+                two_sum_add(cs.ph, cs.pl, v[0]);
+                cs.pl += v[1];
+                two_sum_add(cs.xh, cs.xl, v[2]);
+                cs.xl += v[3];
+                two_sum_add(cs.yh, cs.yl, v[4]);
+                cs.yl += v[5];
+                two_sum_add(cs.zh, cs.zl, v[6]);
+                cs.zl += v[7];
             }
             const double ih = tv.inv_h_leaf, ih2 = ih * ih;
             fphi = ((double)cs.ph + (double)cs.pl) * ih;

@@ -884,6 +884,7 @@ int eval_adaptive(dafmm_tree* t, int order, int precision, double* dphi, double*
         if (c->profile) cudaEventRecord(c->ev[k], s);
     };
     int launches = 0;
+    bool f32_locals = false;
     mark(0);
     if (far) {
         CK(c, ops->p2m_a(av, t->leaves, t->nleaves, precision, t->aM, s), "P2M");
@@ -1380,6 +1381,7 @@ int dafmm_eval(dafmm_tree* t, int order, double theta, int precision, double* ph
         if (c->profile) cudaEventRecord(c->ev[k], s);
     };
     int launches = 0;
+    bool f32_locals = false;
     mark(0);
     if (far) {
         const bool tc_ok = c->m2l_kernel == 0 && c->tc_capable && order >= 2;
@@ -1388,6 +1390,9 @@ int dafmm_eval(dafmm_tree* t, int order, double theta, int precision, double* ph
         const bool tc_m2m = f32 && tc_ok && (c->tc_mask & 2);     // tensor-core M2M (FP32 mode)
         const bool tc_l2l = f32 && tc_ok && (c->tc_mask & 4);     // tensor-core L2L (FP32 mode)
         const bool f16_m2l = tc_m2l && f32 && c->m2l_f16;         // M2L on F16 split operands
+        // FP32 mode with M2L and L2L on tensor cores keeps the locals as FP32 rows (in the
+        // FP64 arrays' memory): the epilogues then need no FP64 arithmetic
+        f32_locals = tc_m2l && tc_l2l;
         Expansions& ex = t->ex;
         if (f16_m2l && ((rc = ensure_f16_levels(t, s)) || (rc = ensure_k16(c, order, s)))) return rc;
         auto tc_args = [&](int mode, int lmin, int lmax) {
@@ -1457,6 +1462,7 @@ int dafmm_eval(dafmm_tree* t, int order, double theta, int precision, double* ph
             mark(4);
             TCArgs a = tc_args(kTcM2L, 2, L);
             a.f16 = f16_m2l;
+            a.out_f32 = f32_locals;
             for (int l = 2; l <= L; ++l) {
                 a.a_hi[l] = f16_m2l ? ex.Mh16[l] : (const void*)ex.Mhi[l];
                 a.a_lo[l] = f16_m2l ? ex.Ml16[l] : (const void*)ex.Mlo[l];
@@ -1492,6 +1498,7 @@ int dafmm_eval(dafmm_tree* t, int order, double theta, int precision, double* ph
         for (int lc = 3; lc <= L; ++lc) {
             if (tc_l2l) {
                 TCArgs a = tc_args(kTcL2L, lc, lc);
+                a.out_f32 = f32_locals;
                 a.a_hi[lc - 1] = ex.Lhi[lc - 1];
                 a.a_lo[lc - 1] = ex.Llo[lc - 1];
                 a.out[lc] = ex.L[lc];
@@ -1513,7 +1520,10 @@ int dafmm_eval(dafmm_tree* t, int order, double theta, int precision, double* ph
     } else {
         for (int k = 1; k <= 6; ++k) mark(k);
     }
-    CK(c, ops->leaf(tv, precision, far ? t->ex.L[L] : nullptr, dphi, dfield, s), "L2P/P2P");
+    TreeView tvl = tv;
+    tvl.locals_f32 = f32_locals ? 1 : 0;
+    if (far) t->ex.L_f32 = f32_locals;
+    CK(c, ops->leaf(tvl, precision, far ? t->ex.L[L] : nullptr, dphi, dfield, s), "L2P/P2P");
     ++launches;
     mark(7);
     c->last_launches = launches;
@@ -1631,7 +1641,12 @@ int64_t dafmm_debug_level(const dafmm_tree* t, int which, int level, double* out
     const int64_t cnt = (int64_t)level_boxes(level) * ncp_of(e.p);
     if (cap < cnt) return DAFMM_ERR_INVALID_ARG;
     if (cudaSetDevice(t->ctx->device) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) return DAFMM_ERR_CUDA;
-    if (which <= 1) {
+    if (which == 1 && e.L_f32) {
+        std::vector<float> tmp(cnt);
+        if (cudaMemcpy(tmp.data(), e.L[level], cnt * sizeof(float), cudaMemcpyDeviceToHost) != cudaSuccess)
+            return DAFMM_ERR_CUDA;
+        for (int64_t i = 0; i < cnt; ++i) out[i] = tmp[i];
+    } else if (which <= 1) {
         const double* src = which == 0 ? e.M[level] : e.L[level];
         if (cudaMemcpy(out, src, cnt * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess) return DAFMM_ERR_CUDA;
     } else {

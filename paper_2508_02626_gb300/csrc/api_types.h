@@ -49,6 +49,7 @@ struct Expansions {
     void* Mh16[dafmm::kMaxUniformDepth + 1] = {};
     void* Ml16[dafmm::kMaxUniformDepth + 1] = {};
     float* Minv[dafmm::kMaxUniformDepth + 1] = {};
+    bool L_f32 = false;  // the last evaluation left FP32 rows (ncp floats per box) in L
 };
 
 struct dafmm_tree {
@@ -107,6 +108,7 @@ inline TreeView make_view(const dafmm_tree* t) {
     tv.xq = t->xq;
     tv.perm = t->perm;
     tv.leaf_start = t->leaf_start;
+    tv.locals_f32 = 0;
     return tv;
 }
 }  // namespace dafmm

@@ -515,7 +515,16 @@ __global__ void __launch_bounds__(128) k_leaf(TreeView tv, const double* __restr
     const double* Lrow = Lleaf ? Lleaf + (size_t)leaf * NCP : nullptr;
     __shared__ float s_lrow[4][NCP];  // per warp: the leaf's local expansion in FP32
     if constexpr (sizeof(T) == 4) {
-        if (Lrow) warp_row_to_f32(Lrow, s_lrow[threadIdx.y], lane);
+        if (Lrow) {
+            if (tv.locals_f32) {  // the row is FP32 already (NCP floats per leaf)
+                const float* Lf = reinterpret_cast<const float*>(Lleaf) + (size_t)leaf * NCP;
+                __syncwarp();
+                for (int k = lane; k < NC; k += 32) s_lrow[threadIdx.y][k] = Lf[k];
+                __syncwarp();
+            } else {
+                warp_row_to_f32(Lrow, s_lrow[threadIdx.y], lane);
+            }
+        }
     }
     // the 27 neighbour leaves' particle ranges, one per lane (empty outside the domain), and
     // the first FP32 record of each

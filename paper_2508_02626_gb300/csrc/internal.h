@@ -31,6 +31,7 @@ struct TreeView {
                                   // records from xq_base(leaf_start[l], l) per leaf l
     const int* perm;              // sorted position -> input index
     const int* leaf_start;        // nleaf + 1
+    int locals_f32;               // the leaf locals passed to the leaf kernel are FP32 rows
 };
 
 struct ShiftTab {                 // compressed rows of a level-independent M2M or L2L table

@@ -44,13 +44,26 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
     return ok != 0;
 }
 
-constexpr long long kWaitLimit = 1ll << 24;  // try_wait rounds before a wait is declared stuck
+// A wait polls try_wait (which itself suspends the thread for a while when the phase is not
+// complete) with no sleep between polls: a sleep adds its own latency to every hand-off of the
+// pipeline.  It is declared stuck after 1 s of device time (checked every 256 polls) or after
+// kWaitPolls polls, whichever comes first.
+constexpr long long kWaitPolls = 1ll << 26;
+constexpr unsigned long long kWaitNs = 1000000000ull;
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
 
 // bounded wait; on expiry records `code` in *err and returns false
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* err, int code) {
-    for (long long i = 0; i < kWaitLimit; ++i) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    for (long long i = 1; i < kWaitPolls; ++i) {
         if (mbar_try_wait(bar, parity)) return true;
-        if (i > 64) __nanosleep(64);
+        if ((i & 255) == 0 && global_ns() - t0 > kWaitNs) break;
     }
     atomicExch(err, code);
     return false;
@@ -152,6 +165,20 @@ __device__ __forceinline__ void tmem_ld16w(uint32_t taddr, uint32_t (&r)[16]) {
 }
 
 
+// 32 lanes x 16 columns from registers into TMEM (the caller waits with tmem_wait_st)
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const float* v) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15, %16};" ::"r"(taddr),
+        "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])), "r"(__float_as_uint(v[3])),
+        "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])), "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])),
+        "r"(__float_as_uint(v[8])), "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])), "r"(__float_as_uint(v[11])),
+        "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])), "r"(__float_as_uint(v[14])), "r"(__float_as_uint(v[15]))
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
 // ---- configuration per order ------------------------------------------------------------------
 // H = false: TF32 operands (rows of ncp FP32 values); H = true: F16 operands (rows of ncph =
 // ncoef rounded up to 16 halves).  Either way a K chunk is 128 bytes of a row (32 TF32 or 64
@@ -219,6 +246,11 @@ struct Terms {
     __device__ bool valid() const {
         return mode != kTcM2L || abs(v[0]) > 1 || abs(v[1]) > 1 || abs(v[2]) > 1;
     }
+    __device__ bool next_valid() {  // advance to the next valid term; false at the end
+        while (next())
+            if (valid()) return true;
+        return false;
+    }
     // A box start (slab coordinates and slab) and the T matrix index of the current term
     __device__ void source(const WorkItem& it, int& x, int& y, int& z, int& slab, int& key) const {
         if (mode == kTcM2L) {
@@ -254,64 +286,105 @@ __device__ __forceinline__ float to_tf32(float x) {
 
 
 // ---- epilogue: one accumulator row (one box) out to global memory -----------------------------
-// Columns b = b_base + j (j < NP) go out in groups of 4 with 16-byte accesses: NCP is a multiple
-// of 8 and every row starts on a multiple of NCP elements, so each group starts 16-byte aligned
-// in the FP32 split rows and 32-byte aligned in the FP64 row.  Value of column b < NC:
-// S[j] * sc (times inv_r[b] for scaled F16 operands), plus the old value when add; columns
-// NC..NCP-1 are written as zeros (they lie inside the last MMA step of a later stage, where a
-// stale NaN times a zero column would still be NaN).  With add the old values of a group are
-// loaded DEPTH groups ahead of its store: a load placed after a store to the same row cannot be
-// moved above it by the compiler, so without the ring every column would wait one memory round
-// trip.  hrow / lrow (optional) receive the TF32 split of the written values.
+// The finished row of each of the warp's 32 lanes sits in TMEM columns tb .. tb + NP - 1; it
+// goes out 16 columns per step of a loop that is not unrolled, so the code stays small: this
+// runs once per tile, and a fully unrolled store of NP columns was measured to stall on
+// instruction fetch for tens of microseconds.  Column b = b_base + j < NC receives S_j * sc
+// (times inv_r[b] for scaled F16 operands), plus the old value when add; columns NC..NCP-1 are
+// written as zeros (they lie inside the last MMA step of a later stage, where a stale NaN times
+// a zero column would still be NaN).  With f32 the row holds FP32 values and the arithmetic is
+// FP32 (scf = sc rounded to FP32); otherwise both are FP64, which this part executes at a small
+// fraction of the FP32 rate.  Accesses are 16 bytes (NCP is a multiple of 8 and rows start on
+// multiples of NCP elements); with add the old values of the next step are requested before
+// this step's stores.  hrow / lrow (optional) receive the TF32 split of the written values.
+// All lanes call this (the TMEM loads are warp-wide); `valid` selects the lanes that own a row.
 template <int NP, int NC, int NCP, bool H>
-__device__ __forceinline__ void store_row(const float (&S)[NP], int b_base, double sc, const float* inv_r, bool add,
-                                          double* orow, float* hrow, float* lrow) {
-    constexpr int GW = 4, NG = NP / GW, DEPTH = 4;
+__device__ __forceinline__ void store_row(uint32_t tb, bool valid, int b_base, double sc, float scf, const float* inv_r,
+                                          bool add, bool f32, void* orow, float* hrow, float* lrow) {
     static_assert(NP % 16 == 0 && NCP % 8 == 0, "column groups");
-    double2 ring[DEPTH][2];
+    double* od = static_cast<double*>(orow);
+    float* of = static_cast<float*>(orow);
+    // old values of the 16 columns from b: FP32 in o[0..3], FP64 in o[0..7]; groups at or past
+    // NCP are not read
+    auto load_old = [&](int b, uint4 (&o)[8]) {
 #pragma unroll
-    for (int g = 0; g < DEPTH; ++g) {
-        ring[g][0] = ring[g][1] = make_double2(0.0, 0.0);
-        if (add && b_base + GW * g < NCP) {
-            ring[g][0] = reinterpret_cast<const double2*>(orow + b_base + GW * g)[0];
-            ring[g][1] = reinterpret_cast<const double2*>(orow + b_base + GW * g)[1];
-        }
-    }
-#pragma unroll
-    for (int g = 0; g < NG; ++g) {
-        const int b0 = b_base + GW * g;
-        const double old[4] = {ring[g % DEPTH][0].x, ring[g % DEPTH][0].y, ring[g % DEPTH][1].x, ring[g % DEPTH][1].y};
-        if (add && g + DEPTH < NG && b0 + GW * DEPTH < NCP) {
-            ring[g % DEPTH][0] = reinterpret_cast<const double2*>(orow + b0 + GW * DEPTH)[0];
-            ring[g % DEPTH][1] = reinterpret_cast<const double2*>(orow + b0 + GW * DEPTH)[1];
-        }
-        if (b0 < NCP) {
-            double v[GW];
-#pragma unroll
-            for (int j = 0; j < GW; ++j) {
-                double x = 0.0;
-                if (b0 + j < NC) {
-                    x = (double)S[GW * g + j] * sc;
-                    if constexpr (H) x *= (double)inv_r[b0 + j];
-                    if (add) x += old[j];
-                }
-                v[j] = x;
+        for (int k = 0; k < 4; ++k) {
+            if (b + 4 * k >= NCP) continue;
+            if (f32) {
+                o[k] = *reinterpret_cast<const uint4*>(of + b + 4 * k);
+            } else {
+                o[2 * k] = reinterpret_cast<const uint4*>(od + b + 4 * k)[0];
+                o[2 * k + 1] = reinterpret_cast<const uint4*>(od + b + 4 * k)[1];
             }
-            reinterpret_cast<double2*>(orow + b0)[0] = make_double2(v[0], v[1]);
-            reinterpret_cast<double2*>(orow + b0)[1] = make_double2(v[2], v[3]);
-            if (hrow) {
-                float h[GW], l[GW];
+        }
+    };
+    uint4 nxt[8];
 #pragma unroll
-                for (int j = 0; j < GW; ++j) {
-                    const float f = (float)v[j];
+    for (int k = 0; k < 8; ++k) nxt[k] = make_uint4(0u, 0u, 0u, 0u);
+    const bool rd = valid && add;
+    if (rd) load_old(b_base, nxt);
+#pragma unroll 1
+    for (int c0 = 0; c0 < NP; c0 += 16) {
+        __syncwarp();
+        uint32_t r[16];
+        tmem_ld16w(tb + c0, r);
+        const int b0 = b_base + c0;
+        uint4 cur[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) cur[k] = nxt[k];
+        if (rd && c0 + 16 < NP && b0 + 16 < NCP) load_old(b0 + 16, nxt);
+        if (!valid) continue;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int bg = b0 + 4 * k;
+            if (bg >= NCP) continue;
+            float h[4], l[4];
+            if (f32) {
+                const float o4[4] = {__uint_as_float(cur[k].x), __uint_as_float(cur[k].y), __uint_as_float(cur[k].z),
+                                     __uint_as_float(cur[k].w)};
+                float v[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    float x = 0.f;
+                    if (bg + j < NC) {
+                        x = __uint_as_float(r[4 * k + j]) * scf;
+                        if constexpr (H) x *= inv_r[bg + j];
+                        if (add) x += o4[j];
+                    }
+                    v[j] = x;
+                    h[j] = to_tf32(x);
+                    l[j] = to_tf32(x - h[j]);
+                }
+                *reinterpret_cast<float4*>(of + bg) = make_float4(v[0], v[1], v[2], v[3]);
+            } else {
+                const double o4[4] = {__hiloint2double((int)cur[2 * k].y, (int)cur[2 * k].x),
+                                      __hiloint2double((int)cur[2 * k].w, (int)cur[2 * k].z),
+                                      __hiloint2double((int)cur[2 * k + 1].y, (int)cur[2 * k + 1].x),
+                                      __hiloint2double((int)cur[2 * k + 1].w, (int)cur[2 * k + 1].z)};
+                double v[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    double x = 0.0;
+                    if (bg + j < NC) {
+                        x = (double)__uint_as_float(r[4 * k + j]) * sc;
+                        if constexpr (H) x *= (double)inv_r[bg + j];
+                        if (add) x += o4[j];
+                    }
+                    v[j] = x;
+                    const float f = (float)x;
                     h[j] = to_tf32(f);
                     l[j] = to_tf32(f - h[j]);
                 }
-                *reinterpret_cast<float4*>(hrow + b0) = make_float4(h[0], h[1], h[2], h[3]);
-                *reinterpret_cast<float4*>(lrow + b0) = make_float4(l[0], l[1], l[2], l[3]);
+                reinterpret_cast<double2*>(od + bg)[0] = make_double2(v[0], v[1]);
+                reinterpret_cast<double2*>(od + bg)[1] = make_double2(v[2], v[3]);
+            }
+            if (hrow) {
+                *reinterpret_cast<float4*>(hrow + bg) = make_float4(h[0], h[1], h[2], h[3]);
+                *reinterpret_cast<float4*>(lrow + bg) = make_float4(l[0], l[1], l[2], l[3]);
             }
         }
     }
+    __syncwarp();
 }
 
 }  // namespace tc

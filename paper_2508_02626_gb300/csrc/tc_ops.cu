@@ -218,8 +218,9 @@ __global__ void __launch_bounds__(192, 1) k_tc(const __grid_constant__ TCParams 
             for (int j = 0; j < C::NP; ++j) S[j] = 0.f;
             Terms tm;
             tm.first(prm.mode, it.oct);
-            do {
-                if (!tm.valid()) continue;
+            bool have = tm.valid() || tm.next_valid();
+            int lastbuf = -1;  // the last term's accumulator stays held until the row is out
+            while (have) {
                 const int buf = uses & 1;
                 ok = mbar_wait(smem_u32(&acc_full[buf]), accf_ph[buf], prm.err, 31);
                 if (!ok) break;
@@ -254,22 +255,36 @@ __global__ void __launch_bounds__(192, 1) k_tc(const __grid_constant__ TCParams 
                         else S[c0 + j] += __uint_as_float(r[j]);
                     }
                 }
-                fence_before_sync();
-                mbar_arrive(smem_u32(&acc_empty[buf]));
                 ++uses;
-            } while (tm.next() && ok);
-            if (!ok) break;
-            const int bx = prm.bx[it.li], by = prm.by[it.li], bz = prm.bz[it.li];
-            if (row < bx * by * bz) {
-                const int x = row % bx, y = (row / bx) % by, z = row / (bx * by);
-                const size_t t = (size_t)out_index(prm, it, x, y, z) * C::NCP;
-                double* orow = prm.out[it.li] + t;
-                float* hrow = prm.out_hi[it.li] ? prm.out_hi[it.li] + t : nullptr;
-                float* lrow = prm.out_lo[it.li] ? prm.out_lo[it.li] + t : nullptr;
-                // L2L adds to the locals that M2L wrote
-                store_row<C::NP, C::NC, C::NCP, H>(S, it.half * C::NP, prm.scale[it.li], prm.inv_r,
-                                                   prm.mode == kTcL2L, orow, hrow, lrow);
+                have = tm.next_valid();
+                if (have) {
+                    fence_before_sync();
+                    mbar_arrive(smem_u32(&acc_empty[buf]));
+                } else {
+                    lastbuf = buf;
+                }
             }
+            if (!ok) break;
+            if (lastbuf < 0) continue;  // no term (does not occur: every work item has one)
+            // the summed row back into the held accumulator, then out from there
+            const uint32_t tb = tmem_base + ((uint32_t)(32 * q) << 16) + (uint32_t)(lastbuf * C::NP);
+#pragma unroll
+            for (int c0 = 0; c0 < C::NP; c0 += 16) tmem_st16(tb + c0, S + c0);
+            tmem_wait_st();
+            const int bx = prm.bx[it.li], by = prm.by[it.li], bz = prm.bz[it.li];
+            const bool valid = row < bx * by * bz;
+            size_t t = 0;
+            if (valid) t = (size_t)out_index(prm, it, row % bx, (row / bx) % by, row / (bx * by)) * C::NCP;
+            const bool f32 = prm.out_f32 != 0;
+            void* orow = f32 ? static_cast<void*>(reinterpret_cast<float*>(prm.out[it.li]) + t)
+                             : static_cast<void*>(prm.out[it.li] + t);
+            float* hrow = prm.out_hi[it.li] ? prm.out_hi[it.li] + t : nullptr;
+            float* lrow = prm.out_lo[it.li] ? prm.out_lo[it.li] + t : nullptr;
+            // L2L adds to the locals that M2L wrote
+            store_row<C::NP, C::NC, C::NCP, H>(tb, valid, it.half * C::NP, prm.scale[it.li], (float)prm.scale[it.li],
+                                               prm.inv_r, prm.mode == kTcL2L, f32, orow, hrow, lrow);
+            fence_before_sync();
+            mbar_arrive(smem_u32(&acc_empty[lastbuf]));
         }
     }
     fence_before_sync();
@@ -513,6 +528,7 @@ static cudaError_t launch_tc(const TCArgs& a, cudaStream_t s) {
     memset(&prm, 0, sizeof(prm));
     prm.mode = a.mode;
     prm.nhalf = C::NHALF;
+    prm.out_f32 = a.out_f32 ? 1 : 0;
     prm.err = a.err;
     int tiles = 0;
     const int per_tile_groups = a.mode == kTcM2L ? 8 : (a.mode == kTcL2L ? 64 : 1);

@@ -36,6 +36,7 @@ struct TCParams {
     int ntiles;
     int nhalf;
     int mode;
+    int out_f32;  // out rows hold FP32 values (NCP floats per box) instead of FP64
     int* err;
 };
 
@@ -48,6 +49,7 @@ struct TCArgs {
     const void* a_lo[kMaxUniformDepth + 1];
     const float* a_inv[kMaxUniformDepth + 1];    // F16: per-box factor undoing the row scale
     double* out[kMaxUniformDepth + 1];           // FP64 result per level (written; added for L2L)
+    bool out_f32;                                // out rows hold FP32 values instead (NCP floats per box)
     float* out_hi[kMaxUniformDepth + 1];         // optional TF32 split of the result
     float* out_lo[kMaxUniformDepth + 1];
     double scale[kMaxUniformDepth + 1];

@@ -295,8 +295,9 @@ __device__ __forceinline__ float to_tf32(float x) {
 // a zero column would still be NaN).  With f32 the row holds FP32 values and the arithmetic is
 // FP32 (scf = sc rounded to FP32); otherwise both are FP64, which this part executes at a small
 // fraction of the FP32 rate.  Accesses are 16 bytes (NCP is a multiple of 8 and rows start on
-// multiples of NCP elements); with add the old values of the next step are requested before
-// this step's stores.  hrow / lrow (optional) receive the TF32 split of the written values.
+// multiples of NCP elements); the old values (add) and column factors (F16) of the next step
+// are requested before this step's stores.  inv_r holds at least NCP values.  hrow / lrow
+// (optional) receive the TF32 split of the written values.
 // All lanes call this (the TMEM loads are warp-wide); `valid` selects the lanes that own a row.
 template <int NP, int NC, int NCP, bool H>
 __device__ __forceinline__ void store_row(uint32_t tb, bool valid, int b_base, double sc, float scf, const float* inv_r,
@@ -318,11 +319,21 @@ __device__ __forceinline__ void store_row(uint32_t tb, bool valid, int b_base, d
             }
         }
     };
+    // per-column factors of the 16 columns from b (F16 operands)
+    auto load_inv = [&](int b, float4 (&f)[4]) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            if (b + 4 * k < NCP) f[k] = *reinterpret_cast<const float4*>(inv_r + b + 4 * k);
+    };
     uint4 nxt[8];
+    float4 nxf[4];
 #pragma unroll
     for (int k = 0; k < 8; ++k) nxt[k] = make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) nxf[k] = make_float4(1.f, 1.f, 1.f, 1.f);
     const bool rd = valid && add;
     if (rd) load_old(b_base, nxt);
+    if (H && valid && b_base < NCP) load_inv(b_base, nxf);
 #pragma unroll 1
     for (int c0 = 0; c0 < NP; c0 += 16) {
         __syncwarp();
@@ -330,9 +341,14 @@ __device__ __forceinline__ void store_row(uint32_t tb, bool valid, int b_base, d
         tmem_ld16w(tb + c0, r);
         const int b0 = b_base + c0;
         uint4 cur[8];
+        float4 cf[4];
 #pragma unroll
         for (int k = 0; k < 8; ++k) cur[k] = nxt[k];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) cf[k] = nxf[k];
+        // the next step's loads go out before this step's stores
         if (rd && c0 + 16 < NP && b0 + 16 < NCP) load_old(b0 + 16, nxt);
+        if (H && valid && c0 + 16 < NP && b0 + 16 < NCP) load_inv(b0 + 16, nxf);
         if (!valid) continue;
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
@@ -348,7 +364,7 @@ __device__ __forceinline__ void store_row(uint32_t tb, bool valid, int b_base, d
                     float x = 0.f;
                     if (bg + j < NC) {
                         x = __uint_as_float(r[4 * k + j]) * scf;
-                        if constexpr (H) x *= inv_r[bg + j];
+                        if constexpr (H) x *= (&cf[k].x)[j];
                         if (add) x += o4[j];
                     }
                     v[j] = x;
@@ -367,7 +383,7 @@ __device__ __forceinline__ void store_row(uint32_t tb, bool valid, int b_base, d
                     double x = 0.0;
                     if (bg + j < NC) {
                         x = (double)__uint_as_float(r[4 * k + j]) * sc;
-                        if constexpr (H) x *= (double)inv_r[bg + j];
+                        if constexpr (H) x *= (double)(&cf[k].x)[j];
                         if (add) x += o4[j];
                     }
                     v[j] = x;

@@ -295,8 +295,8 @@ __device__ __forceinline__ float to_tf32(float x) {
 // a zero column would still be NaN).  With f32 the row holds FP32 values and the arithmetic is
 // FP32 (scf = sc rounded to FP32); otherwise both are FP64, which this part executes at a small
 // fraction of the FP32 rate.  Accesses are 16 bytes (NCP is a multiple of 8 and rows start on
-// multiples of NCP elements); the old values (add) and column factors (F16) of the next step
-// are requested before this step's stores.  inv_r holds at least NCP values.  hrow / lrow
+// multiples of NCP elements); the old values (add) of the step after next and the column
+// factors (F16) of the next step are requested before this step's stores.  inv_r holds at least NCP values.  hrow / lrow
 // (optional) receive the TF32 split of the written values.
 // All lanes call this (the TMEM loads are warp-wide); `valid` selects the lanes that own a row.
 template <int NP, int NC, int NCP, bool H>
@@ -325,14 +325,15 @@ __device__ __forceinline__ void store_row(uint32_t tb, bool valid, int b_base, d
         for (int k = 0; k < 4; ++k)
             if (b + 4 * k < NCP) f[k] = *reinterpret_cast<const float4*>(inv_r + b + 4 * k);
     };
-    uint4 nxt[8];
+    uint4 nxt[8], nx2[8];  // old values one and two steps ahead
     float4 nxf[4];
 #pragma unroll
-    for (int k = 0; k < 8; ++k) nxt[k] = make_uint4(0u, 0u, 0u, 0u);
+    for (int k = 0; k < 8; ++k) nxt[k] = nx2[k] = make_uint4(0u, 0u, 0u, 0u);
 #pragma unroll
     for (int k = 0; k < 4; ++k) nxf[k] = make_float4(1.f, 1.f, 1.f, 1.f);
     const bool rd = valid && add;
     if (rd) load_old(b_base, nxt);
+    if (rd && 16 < NP && b_base + 16 < NCP) load_old(b_base + 16, nx2);
     if (H && valid && b_base < NCP) load_inv(b_base, nxf);
 #pragma unroll 1
     for (int c0 = 0; c0 < NP; c0 += 16) {
@@ -343,11 +344,14 @@ __device__ __forceinline__ void store_row(uint32_t tb, bool valid, int b_base, d
         uint4 cur[8];
         float4 cf[4];
 #pragma unroll
-        for (int k = 0; k < 8; ++k) cur[k] = nxt[k];
+        for (int k = 0; k < 8; ++k) {
+            cur[k] = nxt[k];
+            nxt[k] = nx2[k];
+        }
 #pragma unroll
         for (int k = 0; k < 4; ++k) cf[k] = nxf[k];
-        // the next step's loads go out before this step's stores
-        if (rd && c0 + 16 < NP && b0 + 16 < NCP) load_old(b0 + 16, nxt);
+        // later steps' loads go out before this step's stores
+        if (rd && c0 + 32 < NP && b0 + 32 < NCP) load_old(b0 + 32, nx2);
         if (H && valid && c0 + 16 < NP && b0 + 16 < NCP) load_inv(b0 + 16, nxf);
         if (!valid) continue;
 #pragma unroll

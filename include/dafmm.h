@@ -198,8 +198,8 @@ int dafmm_set_option(dafmm_ctx* ctx, int option, int64_t value);
 /* Diagnostics: copy level `level` of an internal expansion array of the last evaluation
  * into host memory `out` as doubles (8^level x ncp values; ncp = ncoef rounded up to 8).
  * which: 0 multipoles, 1 locals, 2/3 TF32 high/low parts of the multipoles, 4/5 of the
- * locals.  The FP32 mode with M2L and L2L on tensor cores keeps the locals in FP32; they are
- * returned as doubles all the same.  Synchronises the device.  Returns the number of values,
+ * locals.  The FP32 mode keeps the locals (M2L and L2L on tensor cores) and the multipoles
+ * (F16 M2L, SIMT M2M) in FP32; they are returned as doubles all the same.  Synchronises the device.  Returns the number of values,
  * or a negative code. */
 int64_t dafmm_debug_level(const dafmm_tree* tree, int which, int level, double* out, int64_t cap);
 

@@ -1391,9 +1391,14 @@ int dafmm_eval(dafmm_tree* t, int order, double theta, int precision, double* ph
         const bool tc_l2l = f32 && tc_ok && (c->tc_mask & 4);     // tensor-core L2L (FP32 mode)
         const bool f16_m2l = tc_m2l && f32 && c->m2l_f16;         // M2L on F16 split operands
         // FP32 mode with M2L and L2L on tensor cores keeps the locals as FP32 rows (in the
-        // FP64 arrays' memory): the epilogues then need no FP64 arithmetic
+        // FP64 arrays' memory): the epilogues then need no FP64 arithmetic.  With the F16 M2L
+        // and the SIMT M2M the multipoles are FP32 rows as well (P2M, M2M and the F16 split
+        // all in FP32).
         f32_locals = tc_m2l && tc_l2l;
+        const bool f32_mult = f16_m2l && !tc_m2m;
+        const int prec_m = precision | (f32_mult ? kRowsF32 : 0);
         Expansions& ex = t->ex;
+        ex.M_f32 = f32_mult;
         if (f16_m2l && ((rc = ensure_f16_levels(t, s)) || (rc = ensure_k16(c, order, s)))) return rc;
         auto tc_args = [&](int mode, int lmin, int lmax) {
             TCArgs a;
@@ -1405,7 +1410,7 @@ int dafmm_eval(dafmm_tree* t, int order, double theta, int precision, double* ph
             a.num_sms = c->num_sms;
             return a;
         };
-        CK(c, ops->p2m(tv, precision, ex.M[L], s), "P2M");
+        CK(c, ops->p2m(tv, prec_m, ex.M[L], s), "P2M");
         ++launches;
         mark(1);
         if (tc_m2m) {
@@ -1427,13 +1432,13 @@ int dafmm_eval(dafmm_tree* t, int order, double theta, int precision, double* ph
             }
         } else {
             for (int lc = L; lc >= 3; --lc) {
-                CK(c, ops->m2m_level(od, precision, lc, ex.M[lc], ex.M[lc - 1], s), "M2M");
+                CK(c, ops->m2m_level(od, prec_m, lc, ex.M[lc], ex.M[lc - 1], s), "M2M");
                 ++launches;
             }
         }
         mark(2);
         if (f16_m2l) {
-            const double* src[8];
+            const void* src[8];
             int nrows[8];
             void *hi[8], *lo[8];
             float* inv[8];
@@ -1444,7 +1449,7 @@ int dafmm_eval(dafmm_tree* t, int order, double theta, int precision, double* ph
                 lo[l - 2] = ex.Ml16[l];
                 inv[l - 2] = ex.Minv[l];
             }
-            CK(c, tc_split_f16_multi(L - 1, src, nrows, hi, lo, inv, order, s), "split");
+            CK(c, tc_split_f16_multi(L - 1, src, nrows, hi, lo, inv, order, s, f32_mult), "split");
             ++launches;
         } else if (precision != DAFMM_FP64 && !(tc_m2m && tc_m2l))
             for (int l = 2; l <= L; ++l) {
@@ -1641,9 +1646,10 @@ int64_t dafmm_debug_level(const dafmm_tree* t, int which, int level, double* out
     const int64_t cnt = (int64_t)level_boxes(level) * ncp_of(e.p);
     if (cap < cnt) return DAFMM_ERR_INVALID_ARG;
     if (cudaSetDevice(t->ctx->device) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) return DAFMM_ERR_CUDA;
-    if (which == 1 && e.L_f32) {
+    if ((which == 1 && e.L_f32) || (which == 0 && e.M_f32)) {
         std::vector<float> tmp(cnt);
-        if (cudaMemcpy(tmp.data(), e.L[level], cnt * sizeof(float), cudaMemcpyDeviceToHost) != cudaSuccess)
+        if (cudaMemcpy(tmp.data(), which == 0 ? (const void*)e.M[level] : (const void*)e.L[level], cnt * sizeof(float),
+                       cudaMemcpyDeviceToHost) != cudaSuccess)
             return DAFMM_ERR_CUDA;
         for (int64_t i = 0; i < cnt; ++i) out[i] = tmp[i];
     } else if (which <= 1) {

@@ -50,6 +50,7 @@ struct Expansions {
     void* Ml16[dafmm::kMaxUniformDepth + 1] = {};
     float* Minv[dafmm::kMaxUniformDepth + 1] = {};
     bool L_f32 = false;  // the last evaluation left FP32 rows (ncp floats per box) in L
+    bool M_f32 = false;  // ... and in M
 };
 
 struct dafmm_tree {

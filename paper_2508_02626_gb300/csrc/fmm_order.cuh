@@ -95,8 +95,11 @@ __device__ __forceinline__ void warp_row_to_f32(const double* __restrict__ row, 
 }
 
 // ---- P2M ---------------------------------------------------------------------------------
+// rows32: the multipole rows are FP32 (NCP floats per leaf) instead of FP64.  The FP32 kernel
+// reads the particles' FP32 leaf-frame records, which hold exactly the values it would compute
+// from the FP64 coordinates ((x - c) / h rounded once to FP32), without FP64 arithmetic.
 template <class T>
-__global__ void k_p2m(TreeView tv, double* __restrict__ M) {
+__global__ void k_p2m(TreeView tv, double* __restrict__ M, int rows32) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* sm = reinterpret_cast<T*>(smem_raw) + threadIdx.y * (32 * 33);
     const int lane = threadIdx.x;
@@ -108,6 +111,7 @@ __global__ void k_p2m(TreeView tv, double* __restrict__ M) {
     const double cx = tv.x0 + ((double)a + 0.5) * tv.h_leaf;
     const double cy = tv.y0 + ((double)b + 0.5) * tv.h_leaf;
     const double cz = tv.z0 + ((double)c + 0.5) * tv.h_leaf;
+    const int r_own = xq_base(i0, leaf) - i0;  // FP32 record of sorted position i: i + r_own
     constexpr int NJ = (NC + 31) / 32;
     T acc[NJ];
 #pragma unroll
@@ -117,12 +121,29 @@ __global__ void k_p2m(TreeView tv, double* __restrict__ M) {
         const int i = base + lane;
         T x = T(0), y = T(0), z = T(0), q = T(0);
         if (i < i1) {
-            x = (T)((tv.x[i] - cx) * tv.inv_h_leaf);
-            y = (T)((tv.y[i] - cy) * tv.inv_h_leaf);
-            z = (T)((tv.z[i] - cz) * tv.inv_h_leaf);
-            q = (T)tv.q[i];
+            if constexpr (sizeof(T) == 4) {
+                const float4 r = xq_load(tv.xq, i + r_own);
+                x = r.x;
+                y = r.y;
+                z = r.z;
+                q = r.w;
+            } else {
+                x = (T)((tv.x[i] - cx) * tv.inv_h_leaf);
+                y = (T)((tv.y[i] - cy) * tv.inv_h_leaf);
+                z = (T)((tv.z[i] - cz) * tv.inv_h_leaf);
+                q = (T)tv.q[i];
+            }
         }
         gen::GEN(p2m)<T>(x, y, z, q, sink);
+    }
+    if (rows32) {
+        float* Mf = reinterpret_cast<float*>(M) + (size_t)leaf * NCP;
+#pragma unroll
+        for (int j = 0; j < NJ; ++j) {
+            const int k = lane + 32 * j;
+            if (k < NC) Mf[k] = (float)acc[j];
+        }
+        return;
     }
 #pragma unroll
     for (int j = 0; j < NJ; ++j) {
@@ -179,7 +200,7 @@ constexpr size_t m2m_smem() {
 // M2M from the children at level lc into the parents at level lc - 1 (uniform tree)
 template <class T>
 __global__ void __launch_bounds__(256) k_m2m(ShiftTab tab, int lc, const double* __restrict__ Mc,
-                                             double* __restrict__ Mp) {
+                                             double* __restrict__ Mp, int rows32) {
     constexpr int PP = m2m_parents<T>(), RS = 32 / PP;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* S = reinterpret_cast<T*>(smem_raw);  // [8][PP][NCP + 1]
@@ -191,7 +212,10 @@ __global__ void __launch_bounds__(256) k_m2m(ShiftTab tab, int lc, const double*
         const int lin = lin0 + r;
         T m[8];
 #pragma unroll
-        for (int c = 0; c < 8; ++c) m[c] = lin < nparent ? (T)Mc[(size_t)(c * nparent + lin) * NCP + k] : T(0);
+        for (int c = 0; c < 8; ++c) {
+            const size_t at = (size_t)(c * nparent + lin) * NCP + k;
+            m[c] = lin >= nparent ? T(0) : rows32 ? (T)reinterpret_cast<const float*>(Mc)[at] : (T)Mc[at];
+        }
         hadamard8(m);
 #pragma unroll
         for (int q = 0; q < 8; ++q) S[(q * PP + r) * (NCP + 1) + k] = m[q];
@@ -202,12 +226,13 @@ __global__ void __launch_bounds__(256) k_m2m(ShiftTab tab, int lc, const double*
     const int lin = lin0 + r;
     if (lin >= nparent) return;
     const int px = lin % Pc, py = (lin / Pc) % Pc, pz = lin / (Pc * Pc);
-    double* out = Mp + (size_t)octmajor_index(lc - 1, px, py, pz) * NCP;
+    const size_t ob = (size_t)octmajor_index(lc - 1, px, py, pz) * NCP;
     for (int b = w * RS + sub; b < NC; b += 8 * RS) {
         T acc = T(0);
         for (int e = tab.rowptr[b]; e < tab.rowptr[b + 1]; ++e)
             acc += tab_val<T>(tab, e) * S[(tab.par[e] * PP + r) * (NCP + 1) + tab.col[e]];
-        out[b] = (double)acc;
+        if (rows32) reinterpret_cast<float*>(Mp)[ob + b] = (float)acc;
+        else Mp[ob + b] = (double)acc;
     }
 }
 
@@ -1099,6 +1124,8 @@ static cudaError_t set_smem(K kernel, size_t bytes) {
 
 static cudaError_t p2m_launch(const TreeView& tv, int prec, double* M, cudaStream_t s) {
     if (tv.nleaf == 0) return cudaSuccess;
+    const int rows32 = (prec & kRowsF32) ? 1 : 0;
+    prec &= ~kRowsF32;
     const bool f64 = prec == DAFMM_FP64;
     const size_t per_warp = (size_t)32 * 33 * (f64 ? 8 : 4);
     int wpb = (int)((96 * 1024) / per_warp);
@@ -1108,16 +1135,18 @@ static cudaError_t p2m_launch(const TreeView& tv, int prec, double* M, cudaStrea
     cudaError_t e;
     if (f64) {
         if ((e = set_smem(k_p2m<double>, smem)) != cudaSuccess) return e;
-        k_p2m<double><<<grd, blk, smem, s>>>(tv, M);
+        k_p2m<double><<<grd, blk, smem, s>>>(tv, M, 0);
     } else {
         if ((e = set_smem(k_p2m<float>, smem)) != cudaSuccess) return e;
-        k_p2m<float><<<grd, blk, smem, s>>>(tv, M);
+        k_p2m<float><<<grd, blk, smem, s>>>(tv, M, rows32);
     }
     return cudaGetLastError();
 }
 
 static cudaError_t m2m_launch(const OrderData& od, int prec, int lc, const double* Mc, double* Mp,
                               cudaStream_t s) {
+    const int rows32 = (prec & kRowsF32) ? 1 : 0;
+    prec &= ~kRowsF32;
     const int Pc = 1 << (lc - 1);
     const int nparent = Pc * Pc * Pc;
     const bool f32 = prec == DAFMM_FP32;
@@ -1125,11 +1154,11 @@ static cudaError_t m2m_launch(const OrderData& od, int prec, int lc, const doubl
     if (!f32) {
         constexpr int PP = m2m_parents<double>();
         if ((e = set_smem(k_m2m<double>, m2m_smem<double>())) != cudaSuccess) return e;
-        k_m2m<double><<<(nparent + PP - 1) / PP, 256, m2m_smem<double>(), s>>>(od.m2m(), lc, Mc, Mp);
+        k_m2m<double><<<(nparent + PP - 1) / PP, 256, m2m_smem<double>(), s>>>(od.m2m(), lc, Mc, Mp, 0);
     } else {
         constexpr int PP = m2m_parents<float>();
         if ((e = set_smem(k_m2m<float>, m2m_smem<float>())) != cudaSuccess) return e;
-        k_m2m<float><<<(nparent + PP - 1) / PP, 256, m2m_smem<float>(), s>>>(od.m2m(), lc, Mc, Mp);
+        k_m2m<float><<<(nparent + PP - 1) / PP, 256, m2m_smem<float>(), s>>>(od.m2m(), lc, Mc, Mp, rows32);
     }
     return cudaGetLastError();
 }

@@ -100,6 +100,10 @@ inline void shift_rp8(const HostShiftTable& t, int nc, int* out) {
     out[8 * nc] = t.nnz;
 }
 
+// or-ed into the precision argument of p2m and m2m_level (FP32 mode only): the multipole
+// rows are FP32 (ncp floats per box, in the FP64 arrays' memory) instead of FP64
+constexpr int kRowsF32 = 0x100;
+
 struct OrderOps {
     int p, nc, ncp;
     HostShiftTable m2m, l2l;

@@ -344,15 +344,19 @@ __device__ __forceinline__ void split_half(double v, __half& h, __half& l) {
 
 // up to 8 arrays of rows split in one launch; segment s covers global rows [first[s], first[s+1])
 struct F16Segments {
-    const double* src[8];
+    const void* src[8];  // FP64 rows, or FP32 rows when src_f32
     __half* hi[8];
     __half* lo[8];
     float* inv[8];
     int first[9];
     int nseg;
+    int src_f32;
 };
 
-// one warp per row of src [nrows][ncp] -> hi, lo [nrows][rowlen] halves, inv[nrows]
+// one warp per row of src [nrows][ncp] -> hi, lo [nrows][rowlen] halves, inv[nrows].  The work
+// is FP32 throughout (an FP64 value is rounded to FP32 once: the scale is a power of two, so
+// scaling commutes with that rounding, and FP32 keeps more bits than hi + lo hold); FP64
+// instructions run at a small fraction of the FP32 rate on this part.
 __global__ void k_split_f16_rows(F16Segments sg, int nc, int ncp, int rowlen) {
     int row = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
     const int lane = threadIdx.x & 31;
@@ -360,21 +364,36 @@ __global__ void k_split_f16_rows(F16Segments sg, int nc, int ncp, int rowlen) {
     int g = 0;
     while (g + 1 < sg.nseg && row >= sg.first[g + 1]) ++g;
     row -= sg.first[g];
-    const double* __restrict__ src = sg.src[g];
     __half* __restrict__ hi = sg.hi[g];
     __half* __restrict__ lo = sg.lo[g];
     float* __restrict__ inv = sg.inv[g];
-    const double* x = src + (size_t)row * ncp;
-    double mx = 0.0;
-    for (int k = lane; k < nc; k += 32) mx = fmax(mx, fabs(x[k]));
-    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    const int e = pow2_exponent(mx);
-    const double sc = ldexp(1.0, -e);
-    for (int k = lane; k < rowlen; k += 32) {
-        __half h, l;
-        split_half(k < nc ? x[k] * sc : 0.0, h, l);
+    constexpr int KMAX = 12;  // up to 32 x 12 = 384 coefficients per row (p <= 10: 286)
+    float v[KMAX];
+    float mx = 0.f;
+#pragma unroll
+    for (int j = 0; j < KMAX; ++j) {
+        const int k = lane + 32 * j;
+        float x = 0.f;
+        if (k < nc) {
+            x = sg.src_f32 ? static_cast<const float*>(sg.src[g])[(size_t)row * ncp + k]
+                           : (float)static_cast<const double*>(sg.src[g])[(size_t)row * ncp + k];
+        }
+        v[j] = x;
+        mx = fmaxf(mx, fabsf(x));
+    }
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    int e = 0;
+    if (mx > 0.f) frexpf(mx, &e);  // mx = f 2^e, f in [0.5, 1)
+    e = e < -120 ? -120 : (e > 120 ? 120 : e);
+    const float sc = ldexpf(1.f, -e);
+#pragma unroll
+    for (int j = 0; j < KMAX; ++j) {
+        const int k = lane + 32 * j;
+        if (k >= rowlen) break;
+        const float f = v[j] * sc;
+        const __half h = __float2half_rn(f);
         hi[(size_t)row * rowlen + k] = h;
-        lo[(size_t)row * rowlen + k] = l;
+        lo[(size_t)row * rowlen + k] = __float2half_rn(f - __half2float(h));
     }
     if (lane == 0) inv[row] = ldexpf(1.f, e);
 }
@@ -448,12 +467,14 @@ int tc_npt(int p) {
 
 int tc_rowlen16(int p) { return (ncoef_of(p) + 15) / 16 * 16; }
 
-cudaError_t tc_split_f16_multi(int nseg, const double* const* src, const int* nrows, void* const* hi, void* const* lo,
-                               float* const* inv, int p, cudaStream_t s) {
+cudaError_t tc_split_f16_multi(int nseg, const void* const* src, const int* nrows, void* const* hi, void* const* lo,
+                               float* const* inv, int p, cudaStream_t s, bool src_f32) {
     if (nseg < 1 || nseg > 8) return cudaErrorInvalidValue;
+    if (ncoef_of(p) > 32 * 12) return cudaErrorInvalidValue;
     tc::F16Segments sg;
     memset(&sg, 0, sizeof(sg));
     sg.nseg = nseg;
+    sg.src_f32 = src_f32 ? 1 : 0;
     for (int g = 0; g < nseg; ++g) {
         sg.src[g] = src[g];
         sg.hi[g] = static_cast<__half*>(hi[g]);
@@ -469,7 +490,8 @@ cudaError_t tc_split_f16_multi(int nseg, const double* const* src, const int* nr
 }
 
 cudaError_t tc_split_f16(const double* src, int nrows, int p, void* hi, void* lo, float* inv, cudaStream_t s) {
-    return tc_split_f16_multi(1, &src, &nrows, &hi, &lo, &inv, p, s);
+    const void* sv = src;
+    return tc_split_f16_multi(1, &sv, &nrows, &hi, &lo, &inv, p, s, false);
 }
 
 cudaError_t tc_prepare_k16(const double* K, int nkey, int p, void* hi, void* lo, float* inv_r, float* inv_c,

@@ -123,9 +123,9 @@ int tc_rowlen16(int p);  // F16 operand row length: ncoef rounded up to 16
 // F16 split of FP64 rows [nrows][ncp] with a power-of-two scale per row (row max in [0.5, 1)):
 // hi, lo [nrows][rowlen16] halves, inv[nrows] = the factor that undoes the scale
 cudaError_t tc_split_f16(const double* src, int nrows, int p, void* hi, void* lo, float* inv, cudaStream_t s);
-// the same for up to 8 arrays in one launch
-cudaError_t tc_split_f16_multi(int nseg, const double* const* src, const int* nrows, void* const* hi, void* const* lo,
-                               float* const* inv, int p, cudaStream_t s);
+// the same for up to 8 arrays in one launch; src_f32: the rows are FP32 (ncp floats per row)
+cudaError_t tc_split_f16_multi(int nseg, const void* const* src, const int* nrows, void* const* hi, void* const* lo,
+                               float* const* inv, int p, cudaStream_t s, bool src_f32);
 // F16 split of the M2L matrices K[nkey][nc][ncp] (FP64): row b of matrix k is scaled by
 // r_b c_k (powers of two: r_b from the largest entry of row b over all matrices, c_k from the
 // largest entry of the row-scaled matrix k); hi, lo [nkey][npt][rowlen16]; inv_r[npt],

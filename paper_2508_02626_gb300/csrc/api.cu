@@ -1473,7 +1473,9 @@ int dafmm_eval(dafmm_tree* t, int order, double theta, int precision, double* ph
                 a.a_lo[l] = f16_m2l ? ex.Ml16[l] : (const void*)ex.Mlo[l];
                 a.a_inv[l] = ex.Minv[l];
                 a.out[l] = ex.L[l];
-                if (tc_l2l) {
+                // the L2L of level 3 reads the TF32 split of level 2's locals; every finer
+                // level's split is written by the L2L that completes it
+                if (tc_l2l && l == 2) {
                     a.out_hi[l] = ex.Lhi[l];
                     a.out_lo[l] = ex.Llo[l];
                 }

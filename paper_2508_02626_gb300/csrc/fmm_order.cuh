@@ -514,15 +514,8 @@ __device__ __forceinline__ void p2p_group(const float4* __restrict__ xq, int r0,
     }
 }
 
-// starts the copy of record pairs [p, p + np) (np <= 32) into dst: 16-byte asynchronous copies,
-// one or two per lane (the caller commits them as a group)
-__device__ __forceinline__ void stage_pairs(float4* dst, const float4* __restrict__ xq, int p, int np, int lane) {
-    const float4* src = xq + 2 * p;
-    for (int i = lane; i < 2 * np; i += 32) {
-        const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst + i));
-        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src + i) : "memory");
-    }
-}
+// records per shared-memory segment of the neighbour list (per warp; 8 KB)
+constexpr int kLeafSeg = 512;
 
 template <class T>
 __global__ void __launch_bounds__(128) k_leaf(TreeView tv, const double* __restrict__ Lleaf,
@@ -565,6 +558,17 @@ __global__ void __launch_bounds__(128) k_leaf(TreeView tv, const double* __restr
         }
     }
     const int r_own = xq_base(i0, leaf) - i0;  // record of sorted position t: t + r_own
+    // the neighbours' records laid end to end: lane k's neighbour starts at nb_off (exclusive
+    // scan of the counts over the lanes), nb_tot records in all
+    const int nb_n = nb_s1 - nb_s0;
+    int nb_off = nb_n;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, nb_off, d);
+        if (lane >= d) nb_off += v;
+    }
+    const int nb_tot = __shfl_sync(0xffffffffu, nb_off, 31);
+    nb_off -= nb_n;
     for (int base = i0; base < i1; base += 32) {
         // FP32: a pass of at most 16 targets splits the sources between the two half-warps,
         // lane l and lane l + 16 taking the same target
@@ -599,70 +603,48 @@ __global__ void __launch_bounds__(128) k_leaf(TreeView tv, const double* __restr
         } else {
             const float4 pt = xq_load(tv.xq, tt + r_own);
             CompSums cs;
-            // the neighbours' records in chunks of at most 32 pairs, neighbour by neighbour,
-            // each staged in shared memory while the warp works on the one before it
-            // the neighbours' records in chunks of at most 32 pairs, neighbour by neighbour; a
-            // step takes one chunk per lane group (the chunks of a split pass alternate between
-            // the half-warps) and is staged in shared memory while the warp works on the step
-            // before it.  Rows of 65 float4s keep the two groups' reads on different banks.
-            __shared__ __align__(16) float4 s_rec[4][2][2][65];
-            float4(*buf)[2][65] = s_rec[threadIdx.y];
-            const int G = split ? 2 : 1, g = split ? lane >> 4 : 0;
-            int nk = 0, np_ = 0, ne = 0, nbc = -1;  // cursor: next neighbour, next pair, end pair
-            auto next_chunk = [&](int& k, int& p, int& n) -> bool {
-                while (np_ >= ne) {
-                    if (nk >= 27) return false;
-                    const int s0 = __shfl_sync(0xffffffffu, nb_s0, nk), s1 = __shfl_sync(0xffffffffu, nb_s1, nk);
-                    const int r0 = __shfl_sync(0xffffffffu, nb_r0, nk);
-                    nbc = nk++;
-                    np_ = r0 >> 1;
-                    ne = np_ + ((s1 - s0 + 1) >> 1);
+            // The neighbours' records are copied into one shared-memory list, shifted into this
+            // leaf's frame (source + neighbour offset, in leaf widths) and pair-interleaved, in
+            // segments of up to kLeafSeg records; the pairwise sum then runs over the whole
+            // list.  A pass of at most 16 targets gives each half-warp half of the pairs.
+            __shared__ __align__(16) float4 s_list[4][kLeafSeg];
+            float4* buf = s_list[threadIdx.y];
+            const int g = split ? lane >> 4 : 0;
+            const float2 tx2 = make_float2(pt.x, pt.x), ty2 = make_float2(pt.y, pt.y),
+                         tz2 = make_float2(pt.z, pt.z);
+            for (int seg0 = 0; seg0 < nb_tot; seg0 += kLeafSeg) {
+                const int segn = min(kLeafSeg, nb_tot - seg0);
+                __syncwarp();  // the previous segment is no longer read
+                for (int k = 0; k < 27; ++k) {
+                    const int o = __shfl_sync(0xffffffffu, nb_off, k), n = __shfl_sync(0xffffffffu, nb_n, k);
+                    const int r0 = __shfl_sync(0xffffffffu, nb_r0, k);
+                    const int lo = max(o, seg0), hi = min(o + n, seg0 + segn);
+                    const float dx = (float)(k % 3 - 1), dy = (float)((k / 3) % 3 - 1), dz = (float)(k / 9 - 1);
+                    for (int i = lo + lane; i < hi; i += 32) {
+                        const float4 rec = xq_load(tv.xq, r0 + (i - o));
+                        const int j = i - seg0;
+                        float* f = reinterpret_cast<float*>(buf) + 8 * (j >> 1) + (j & 1);
+                        f[0] = rec.x + dx;
+                        f[2] = rec.y + dy;
+                        f[4] = rec.z + dz;
+                        f[6] = rec.w;
+                    }
                 }
-                k = nbc;
-                p = np_;
-                n = min(32, ne - np_);
-                np_ += n;
-                return true;
-            };
-            // the next step: up to G chunks, copied into buf[st] as one commit group; returns
-            // the number of chunks
-            int ks[2], ns[2];
-            auto next_step = [&](int st, int (&k)[2], int (&n)[2]) -> int {
-                int c = 0, p;
-                while (c < G && next_chunk(k[c], p, n[c])) {
-                    stage_pairs(buf[st][c], tv.xq, p, n[c], lane);
-                    ++c;
+                if ((segn & 1) && lane == 0) {  // a zero record completes the last pair
+                    float* f = reinterpret_cast<float*>(buf) + 8 * (segn >> 1) + 1;
+                    f[0] = f[2] = f[4] = f[6] = 0.f;
                 }
-                asm volatile("cp.async.commit_group;" ::: "memory");
-                return c;
-            };
-            int sb = 0;
-            int c0 = next_step(0, ks, ns);
-            while (c0 > 0) {
-                const int k0 = g < c0 ? ks[g] : 0, n0 = g < c0 ? ns[g] : 0;
-                int kn[2], nn[2];
-                const int c1 = next_step(sb ^ 1, kn, nn);
-                asm volatile("cp.async.wait_group 1;" ::: "memory");  // this step's copies landed
                 __syncwarp();
-                const int dx = k0 % 3 - 1, dy = (k0 / 3) % 3 - 1, dz = k0 / 9 - 1;
-                // target in the neighbour's frame (offsets in leaf widths)
-                const float tx = pt.x - (float)dx, ty = pt.y - (float)dy, tz = pt.z - (float)dz;
-                float2 P = make_float2(0.f, 0.f), X = P, Y = P, Z = P;
-                p2p_pairs(buf[sb][g], 0, n0, make_float2(tx, tx), make_float2(ty, ty), make_float2(tz, tz), P, X, Y,
-                          Z);
-                if (n0 > 0) {
+                const int np = (segn + 1) >> 1, h = split ? (np + 1) >> 1 : np;
+                const int pa = g ? h : 0, pe = g ? np : h;
+                for (int pb = pa; pb < pe; pb += 32) {
+                    float2 P = make_float2(0.f, 0.f), X = P, Y = P, Z = P;
+                    p2p_pairs(buf, pb, min(pe, pb + 32), tx2, ty2, tz2, P, X, Y, Z);
                     two_sum_add(cs.ph, cs.pl, P.x + P.y);
                     two_sum_add(cs.xh, cs.xl, X.x + X.y);
                     two_sum_add(cs.yh, cs.yl, Y.x + Y.y);
                     two_sum_add(cs.zh, cs.zl, Z.x + Z.y);
                 }
-                __syncwarp();  // every lane is done with buf[sb] before it is refilled
-                for (int j = 0; j < 2; ++j) {
-                    ks[j] = kn[j];
-                    ns[j] = nn[j];
-                }
-                c0 = c1;
-                sb ^= 1;
             }
             if (split) {  // the upper half-warp's sums join the lower one's
                 float v[8] = {cs.ph, cs.pl, cs.xh, cs.xl, cs.yh, cs.yl, cs.zh, cs.zl};

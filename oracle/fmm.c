@@ -11,7 +11,8 @@
  * m2l_mode 0 applies Eq. 5 by DA composition for every pair; m2l_mode 1
  * applies the same linear maps as matrices whose columns are the operator
  * applied to unit vectors (exact by linearity), cached per level and
- * displacement for M2L and per level and octant for M2M/L2L.
+ * displacement for M2L and per level and octant for M2M/L2L; m2l_mode 2 applies
+ * the rotation-based M2L of Sec. 3.4 for every pair (M2M and L2L as in mode 0).
  */
 #include <math.h>
 #include <pthread.h>
@@ -79,7 +80,7 @@ static void m2m_range(int64_t b0, int64_t b1, void* p) {
             double r0[3];
             for (int d = 0; d < 3; ++d)
                 r0[d] = ((double)(2 * t->box[b].ijk[d] - t->box[ch].ijk[d]) + 0.5) * hc;
-            if (f->mode == 0) op_m2m(f->ctx, f->M + (size_t)ch * f->nc, r0, f->M + (size_t)b * f->nc);
+            if (f->mode != 1) op_m2m(f->ctx, f->M + (size_t)ch * f->nc, r0, f->M + (size_t)b * f->nc);
             else matvec_acc(f->nc, f->Scache[c], f->M + (size_t)ch * f->nc, f->M + (size_t)b * f->nc);
         }
     }
@@ -97,9 +98,10 @@ static void m2l_range(int64_t b0, int64_t b1, void* p) {
             int c = t->V[b].a[k];
             int64_t dv[3];
             for (int d = 0; d < 3; ++d) dv[d] = t->box[b].ijk[d] - t->box[c].ijk[d];
-            if (f->mode == 0) {
+            if (f->mode != 1) {
                 double r0[3] = {(double)dv[0] * h, (double)dv[1] * h, (double)dv[2] * h};
-                op_m2l(f->ctx, f->M + (size_t)c * f->nc, r0, Lb);
+                if (f->mode == 2) op_m2l_rot(f->ctx, f->M + (size_t)c * f->nc, r0, Lb);
+                else op_m2l(f->ctx, f->M + (size_t)c * f->nc, r0, Lb);
             } else {
                 int key = (int)((dv[0] + 3) * 49 + (dv[1] + 3) * 7 + (dv[2] + 3));
                 matvec_acc(f->nc, f->Kcache[key], f->M + (size_t)c * f->nc, Lb);
@@ -127,7 +129,7 @@ static void l2l_range(int64_t b0, int64_t b1, void* p) {
         int P = t->box[b].parent;
         double hc = box_width(t, f->level);
         int c = (int)((t->box[b].ijk[0] & 1) | ((t->box[b].ijk[1] & 1) << 1) | ((t->box[b].ijk[2] & 1) << 2));
-        if (f->mode == 0) {
+        if (f->mode != 1) {
             double r0[3];
             for (int d = 0; d < 3; ++d)
                 r0[d] = ((double)(t->box[b].ijk[d] - 2 * t->box[P].ijk[d]) - 0.5) * hc;
@@ -229,7 +231,7 @@ int or_fmm(int64_t n, const double* xyz, const double* q, const double* domain4,
            int max_leaf, int max_depth, int order, int m2l_mode, int64_t nt, const int64_t* tgt,
            double* phi, double* field, int nthreads) {
     const tpsa_ctx* ctx = tpsa_get(order);
-    if (!ctx || n < 0 || (m2l_mode != 0 && m2l_mode != 1)) return -1;
+    if (!ctx || n < 0 || m2l_mode < 0 || m2l_mode > 2) return -1;
     or_tree* t = or_tree_build(n, xyz, domain4, uniform_depth, max_leaf, max_depth);
     if (!t) return -2;
     fmm_ctx f;

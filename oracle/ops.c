@@ -89,6 +89,56 @@ void op_m2l(const tpsa_ctx* t, const double* M, const double* r0, double* out) {
     da_axpy(t, 1.0, tmp, out);
 }
 
+/* The rotation of Sec. 3.4 that puts r0 on the positive x axis: first about the x axis by
+ * theta = atan2(z, y), which brings r0 into the x-y plane, then about the z axis by
+ * phi = atan2(sqrt(y^2 + z^2), x).  Q = Rz(phi) Rx(theta) (row-major), Q r0 = (|r0|, 0, 0).
+ * With y = z = 0 the first rotation is the identity. */
+void op_rotation(const double* r0, double* Q) {
+    const double x = r0[0], y = r0[1], z = r0[2];
+    const double ryz = sqrt(y * y + z * z), rho = sqrt(x * x + y * y + z * z);
+    const double c1 = ryz > 0.0 ? y / ryz : 1.0, s1 = ryz > 0.0 ? z / ryz : 0.0;
+    const double c2 = rho > 0.0 ? x / rho : 1.0, s2 = rho > 0.0 ? ryz / rho : 0.0;
+    /* Rx = [[1,0,0],[0,c1,s1],[0,-s1,c1]], Rz = [[c2,s2,0],[-s2,c2,0],[0,0,1]] */
+    const double Rx[9] = {1, 0, 0, 0, c1, s1, 0, -s1, c1};
+    const double Rz[9] = {c2, s2, 0, -s2, c2, 0, 0, 0, 1};
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            double v = 0.0;
+            for (int k = 0; k < 3; ++k) v += Rz[3 * i + k] * Rx[3 * k + j];
+            Q[3 * i + j] = v;
+        }
+}
+
+/* a o (u -> A u): the DA vector a composed with the linear map of the 3x3 matrix A
+ * (row-major), i.e. the map whose components are u_i -> sum_j A_ij u_j */
+void op_linmap(const tpsa_ctx* t, const double* a, const double* A, double* out) {
+    double map[3][TPSA_MAXCOEF];
+    for (int i = 0; i < 3; ++i) {
+        da_zero(t, map[i]);
+        if (t->order >= 1)
+            for (int j = 0; j < 3; ++j) map[i][tpsa_index(j == 0, j == 1, j == 2)] = A[3 * i + j];
+    }
+    const double* g[3] = {map[0], map[1], map[2]};
+    da_compose(t, a, t, g, out);
+}
+
+/* M2L by rotation (Sec. 3.4): with Q r0 = (|r0|, 0, 0) and u = Q d, the source expansion in
+ * the rotated variables is M^(u) = M(Q^T u); Eq. 5 along the axis gives
+ * L^(e) = sqrt(R(e)) M^(M2(e)) for r0' = (|r0|, 0, 0); the result in the target variables
+ * is L(d') = L^(Q d'). */
+void op_m2l_rot(const tpsa_ctx* t, const double* M, const double* r0, double* out) {
+    double Q[9], Qt[9], Mh[TPSA_MAXCOEF], Lh[TPSA_MAXCOEF], L[TPSA_MAXCOEF];
+    op_rotation(r0, Q);
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) Qt[3 * i + j] = Q[3 * j + i];
+    const double ax[3] = {sqrt(r0[0] * r0[0] + r0[1] * r0[1] + r0[2] * r0[2]), 0.0, 0.0};
+    op_linmap(t, M, Qt, Mh);
+    da_zero(t, Lh);
+    op_m2l(t, Mh, ax, Lh);
+    op_linmap(t, Lh, Q, L);
+    da_axpy(t, 1.0, L, out);
+}
+
 /* P2L, Eq. 6 (Sec. 2.4): phi_L(d') = q / |r0 - r_i + d'|, w = r0 - r_i */
 void op_p2l1(const tpsa_ctx* t, const double* w, double q, double* L) {
     double wv[TPSA_MAXCOEF], sq[TPSA_MAXCOEF], u[TPSA_MAXCOEF], r[TPSA_MAXCOEF];
@@ -168,6 +218,26 @@ int or_m2l(int order, const double* M, const double* r0, double* out) {
     const tpsa_ctx* t = tpsa_get(order);
     if (!t) return -1;
     op_m2l(t, M, r0, out);
+    return 0;
+}
+
+int or_m2l_rot(int order, const double* M, const double* r0, double* out) {
+    const tpsa_ctx* t = tpsa_get(order);
+    if (!t) return -1;
+    op_m2l_rot(t, M, r0, out);
+    return 0;
+}
+
+int or_rotation(const double* r0, double* Q9) {
+    if (!r0 || !Q9) return -1;
+    op_rotation(r0, Q9);
+    return 0;
+}
+
+int or_da_linmap(int order, const double* a, const double* A9, double* out) {
+    const tpsa_ctx* t = tpsa_get(order);
+    if (!t) return -1;
+    op_linmap(t, a, A9, out);
     return 0;
 }
 

@@ -65,6 +65,14 @@ int or_p2m(int order, int64_t n, const double* s, const double* q, double* M);
 int or_m2m(int order, const double* M, const double* r0, double* out);
 /* M2L, Eq. 5 by DA composition: out += sqrt(R) (M o M2); r0 = target centre - source centre */
 int or_m2l(int order, const double* M, const double* r0, double* out);
+/* M2L by rotation (Sec. 3.4): rotate M so that r0 lies on the positive x axis, apply Eq. 5
+ * along the axis, rotate the result back; equal to or_m2l up to rounding */
+int or_m2l_rot(int order, const double* M, const double* r0, double* out);
+/* the rotation of Sec. 3.4 (about x by atan2(z, y), then about z by atan2(sqrt(y^2+z^2), x)):
+ * Q (3x3 row-major) with Q r0 = (|r0|, 0, 0) */
+int or_rotation(const double* r0, double* Q9);
+/* out = a o (u -> A u), A 3x3 row-major */
+int or_da_linmap(int order, const double* a, const double* A9, double* out);
 /* the M2L transfer map of Eq. 5: sqrt(R) and the three components of M2 (packed) */
 int or_m2l_map(int order, const double* r0, double* sqrtR, double* map3);
 /* M2L as a matrix: K[beta*nc + alpha] = coefficient beta of M2L(e_alpha); exact by linearity */
@@ -100,7 +108,8 @@ int      or_tree_perm(const or_tree* t, int64_t* perm);
 int      or_tree_list(const or_tree* t, int b, int list, int* out, int cap);
 
 /* ---- FMM traversal (Sec. 1) --------------------------------------------- */
-/* m2l_mode: 0 = DA composition per pair (Eq. 5 literally), 1 = matrices cached per (level, v).
+/* m2l_mode: 0 = DA composition per pair (Eq. 5 literally), 1 = matrices cached per (level, v),
+ * 2 = the rotation-based M2L of Sec. 3.4 per pair (M2M and L2L as in mode 0).
  * tgt: NULL for all targets, else only those targets are computed (outputs in tgt order). */
 int or_fmm(int64_t n, const double* xyz, const double* q, const double* domain4,
            int uniform_depth, int max_leaf, int max_depth, int order, int m2l_mode,

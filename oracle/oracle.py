@@ -56,6 +56,9 @@ def _load():
             "or_m2m": (c_int, [c_int, D, D, D]),
             "or_m2l": (c_int, [c_int, D, D, D]),
             "or_m2l_matrix": (c_int, [c_int, D, D]),
+            "or_m2l_rot": (c_int, [c_int, D, D, D]),
+            "or_rotation": (c_int, [D, D]),
+            "or_da_linmap": (c_int, [c_int, D, D, D]),
             "or_m2l_map": (c_int, [c_int, D, D, D]),
             "or_p2l": (c_int, [c_int, c_i64, D, D, D]),
             "or_l2l": (c_int, [c_int, D, D, D]),
@@ -174,6 +177,30 @@ def m2l(order, M, r0):
     M, r0 = _f64(M), _f64(r0)
     out = np.zeros_like(M)
     _check(_load().or_m2l(order, _d(M), _d(r0), _d(out)), "m2l")
+    return out
+
+
+def m2l_rot(order, M, r0):
+    """M2L by the rotation of Sec. 3.4 (equal to m2l up to rounding)."""
+    M, r0 = _f64(M), _f64(r0)
+    out = np.zeros_like(M)
+    _check(_load().or_m2l_rot(order, _d(M), _d(r0), _d(out)), "m2l_rot")
+    return out
+
+
+def rotation(r0):
+    """Q (3x3) of Sec. 3.4 with Q r0 = (|r0|, 0, 0)."""
+    r0 = _f64(r0)
+    Q = np.zeros(9)
+    _check(_load().or_rotation(_d(r0), _d(Q)), "rotation")
+    return Q.reshape(3, 3)
+
+
+def da_linmap(order, a, A):
+    """a composed with the linear map u -> A u."""
+    a, A = _f64(a), _f64(A, (3, 3))
+    out = np.zeros_like(a)
+    _check(_load().or_da_linmap(order, _d(a), _d(np.ascontiguousarray(A)), _d(out)), "da_linmap")
     return out
 
 

@@ -35,6 +35,9 @@ void op_p2m1(const tpsa_ctx* t, const double* s, double q, double* M);
 void op_m2m(const tpsa_ctx* t, const double* M, const double* r0, double* out);
 void op_m2l_map(const tpsa_ctx* t, const double* r0, double* sqrtR, double* map3);
 void op_m2l(const tpsa_ctx* t, const double* M, const double* r0, double* out);
+void op_m2l_rot(const tpsa_ctx* t, const double* M, const double* r0, double* out);
+void op_rotation(const double* r0, double* Q);
+void op_linmap(const tpsa_ctx* t, const double* a, const double* A, double* out);
 void op_p2l1(const tpsa_ctx* t, const double* w, double q, double* L);
 void op_l2l(const tpsa_ctx* t, const double* L, const double* r0, double* out);
 void op_l2p1(const tpsa_ctx* t, const double* L, const double* x, double* phi, double* grad);

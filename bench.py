@@ -194,11 +194,14 @@ def run_ours(args, rank, world):
     # the other precision modes on the same tree (a few steps each), for comparison
     modes = {}
     if not args.no_modes:
-        for mname in ("mixed", "fp64"):
+        for mname in ("mixed", "fp64", "fp64_dense_m2l"):
             if mname == args.precision:
                 continue
-            mp = B.PRECISIONS[mname]
-            ksteps = 2 if mname == "fp64" else 5
+            # fp64 uses the M2L by rotation (Sec. 3.4, the default from p = 4); fp64_dense_m2l
+            # the dense matrix per displacement, for comparison
+            B.dafmm_set_option(ctx.h, B.DAFMM_OPT_M2L_ROTATION, 0 if mname == "fp64_dense_m2l" else -1)
+            mp = B.PRECISIONS["fp64" if mname.startswith("fp64") else mname]
+            ksteps = 2 if mname.startswith("fp64") else 5
             with torch.cuda.stream(stream):
                 tree.eval(p, phi, E, precision=mp, stream=stream)
                 ms = []
@@ -214,6 +217,7 @@ def run_ours(args, rank, world):
             modes[mname] = {"value": n / (float(np.mean(ms)) / 1e3), "ms_per_step": float(np.mean(ms)),
                             "phases_ms": {k: round(v, 4) for k, v in B.dafmm_last_phase_ms(ctx.h).items()
                                           if k != "launches"}}
+        B.dafmm_set_option(ctx.h, B.DAFMM_OPT_M2L_ROTATION, -1)
         # back to the headline mode for the accuracy sample
         with torch.cuda.stream(stream):
             tree.eval(p, phi, E, precision=prec, stream=stream)
@@ -547,7 +551,8 @@ def bench_operators(ctx):
     import oracle as O
     rng = np.random.default_rng(31)
     out = {"note": "GPU: ns per instance of a batch of 2^18 (M2L: per pair inside a uniform N=2^18 depth-4 "
-                   "evaluation); oracle: us per call of its numerical-DA operator, one host core"}
+                   "evaluation; gpu_fp64_ns: the dense FP64 M2L, gpu_fp64_rotation_ns: the FP64 M2L by "
+                   "rotation, Sec. 3.4); oracle: us per call of its numerical-DA operator, one host core"}
     count = 1 << 18
     for p in (2, 4, 6, 8, 10):
         nc = (p + 1) * (p + 2) * (p + 3) // 6
@@ -597,10 +602,13 @@ def bench_operators(ctx):
         pairs = tr.info()["m2l_pairs"]
         phi = torch.empty(len(q), dtype=torch.float64, device="cuda")
         B.dafmm_set_profiling(ctx.h, True)
-        for pname, prec in (("gpu_fp64_ns", "fp64"), ("gpu_fp32_ns", "fp32")):
+        for pname, prec, rot in (("gpu_fp64_ns", "fp64", 0), ("gpu_fp64_rotation_ns", "fp64", 1),
+                                 ("gpu_fp32_ns", "fp32", -1)):
+            B.dafmm_set_option(ctx.h, B.DAFMM_OPT_M2L_ROTATION, rot)
             tr.eval(p, phi, None, precision=prec)
             tr.eval(p, phi, None, precision=prec)
             row["M2L"][pname] = round(B.dafmm_last_phase_ms(ctx.h)["m2l"] * 1e6 / pairs, 4)
+        B.dafmm_set_option(ctx.h, B.DAFMM_OPT_M2L_ROTATION, -1)
         tr.free()
         out["p%d" % p] = row
         del s3, far, qv, C, octs, outc, out4

@@ -7,6 +7,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -382,6 +383,13 @@ void free_order(dafmm_ctx* c, OrderData& od) {
         dev_free(c, od.M2Mhi, ss); dev_free(c, od.M2Mlo, ss);
         dev_free(c, od.L2Lhi, ss); dev_free(c, od.L2Llo, ss);
     }
+    if (od.rot_T) {
+        dev_free(c, od.rot_T, (size_t)kNumKeys * 4 * ops->rot_tsz * sizeof(double));
+        dev_free(c, od.rot_rho, (size_t)kNumKeys * sizeof(int));
+        dev_free(c, od.ax_rowptr, ((size_t)nc + 1) * sizeof(int));
+        dev_free(c, od.ax_col, (size_t)od.ax_nnz * sizeof(unsigned short));
+        dev_free(c, od.ax_val, (size_t)od.n_rho * od.ax_nnz * sizeof(double));
+    }
     od = OrderData();
 }
 
@@ -415,6 +423,89 @@ int ensure_k16(dafmm_ctx* c, int p, cudaStream_t s) {
     od.Kl16 = lo;
     od.k16_inv_r = ir;
     od.k16_inv_c = ic;
+    return DAFMM_OK;
+}
+
+// tables of the M2L by rotation (Sec. 3.4) of an order (made once, on first use): the four
+// substitution tables of every displacement key, and the axial matrices of the distinct
+// lengths |v| as their structural non-zeros (row b, column a: b_y >= a_y, b_z >= a_z, both
+// differences even), the values taken from the K generation along the x axis
+int ensure_rotation(dafmm_ctx* c, int p, cudaStream_t s) {
+    OrderData& od = c->ord[p];
+    if (od.rot_T) return DAFMM_OK;
+    const OrderOps* ops = order_ops(p);
+    const int nc = ncoef_of(p), ncp = ncp_of(p);
+    // exponents in the coefficient layout (degree graded, x exponent descending, then y)
+    std::vector<int> ey, ez;
+    for (int n = 0; n <= p; ++n)
+        for (int a = n; a >= 0; --a)
+            for (int b = n - a; b >= 0; --b) {
+                ey.push_back(b);
+                ez.push_back(n - a - b);
+            }
+    std::vector<int> rowptr(1, 0);
+    std::vector<unsigned short> col;
+    for (int b = 0; b < nc; ++b) {
+        for (int a = 0; a < nc; ++a)
+            if (ey[b] >= ey[a] && ez[b] >= ez[a] && (ey[b] - ey[a]) % 2 == 0 && (ez[b] - ez[a]) % 2 == 0)
+                col.push_back((unsigned short)a);
+        rowptr.push_back((int)col.size());
+    }
+    const int nnz = (int)col.size();
+    std::vector<int> rho_of(kNumKeys, 0), len2;
+    for (int key = 0; key < kNumKeys; ++key) {
+        const int vx = key / 49 - 3, vy = (key / 7) % 7 - 3, vz = key % 7 - 3;
+        if (std::max(std::abs(vx), std::max(std::abs(vy), std::abs(vz))) <= 1) continue;
+        const int r2 = vx * vx + vy * vy + vz * vz;
+        auto it = std::find(len2.begin(), len2.end(), r2);
+        rho_of[key] = (int)(it - len2.begin());
+        if (it == len2.end()) len2.push_back(r2);
+    }
+    const int nrho = (int)len2.size();
+    std::vector<double> r0s(3 * (size_t)nrho, 0.0);
+    for (int r = 0; r < nrho; ++r) r0s[3 * r] = std::sqrt((double)len2[r]);
+    const size_t tbytes = (size_t)kNumKeys * 4 * ops->rot_tsz * sizeof(double);
+    const size_t kbytes = (size_t)nrho * nc * ncp * sizeof(double);
+    double *T = nullptr, *val = nullptr, *d_r0s = nullptr, *Ks = nullptr;
+    int *rho = nullptr, *rp = nullptr;
+    unsigned short* cl = nullptr;
+    int rc;
+    auto release = [&]() {
+        dev_free(c, T, tbytes);
+        dev_free(c, val, (size_t)nrho * nnz * sizeof(double));
+        dev_free(c, rho, (size_t)kNumKeys * sizeof(int));
+        dev_free(c, rp, ((size_t)nc + 1) * sizeof(int));
+        dev_free(c, cl, (size_t)nnz * sizeof(unsigned short));
+    };
+    if ((rc = dev_alloc(c, (void**)&T, tbytes, "rotation tables")) ||
+        (rc = dev_alloc(c, (void**)&val, (size_t)nrho * nnz * sizeof(double), "axial M2L matrices")) ||
+        (rc = dev_alloc(c, (void**)&rho, (size_t)kNumKeys * sizeof(int), "rotation tables")) ||
+        (rc = dev_alloc(c, (void**)&rp, ((size_t)nc + 1) * sizeof(int), "axial M2L matrices")) ||
+        (rc = dev_alloc(c, (void**)&cl, (size_t)nnz * sizeof(unsigned short), "axial M2L matrices"))) {
+        release();
+        return rc;
+    }
+    if ((rc = dev_alloc(c, (void**)&d_r0s, r0s.size() * sizeof(double), "rotation scratch")) ||
+        (rc = dev_alloc(c, (void**)&Ks, kbytes, "rotation scratch"))) {
+        dev_free(c, d_r0s, r0s.size() * sizeof(double));
+        release();
+        return rc;
+    }
+    od.rot_T = T; od.rot_rho = rho; od.ax_rowptr = rp; od.ax_col = cl; od.ax_val = val;
+    od.ax_nnz = nnz; od.n_rho = nrho;
+    cudaError_t e = cudaMemcpyAsync(rho, rho_of.data(), rho_of.size() * sizeof(int), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(rp, rowptr.data(), rowptr.size() * sizeof(int), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(cl, col.data(), col.size() * sizeof(unsigned short), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_r0s, r0s.data(), r0s.size() * sizeof(double), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = ops->rot_setup(od, d_r0s, nrho, Ks, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // shared by every later evaluation, on any stream
+    dev_free(c, d_r0s, r0s.size() * sizeof(double));
+    dev_free(c, Ks, kbytes);
+    if (e != cudaSuccess) {
+        release();
+        od.rot_T = nullptr; od.rot_rho = nullptr; od.ax_rowptr = nullptr; od.ax_col = nullptr; od.ax_val = nullptr;
+        return cuda_fail(c, e, "rotation tables");
+    }
     return DAFMM_OK;
 }
 
@@ -1489,10 +1580,14 @@ int dafmm_eval(dafmm_tree* t, int order, double theta, int precision, double* ph
             CK(c, tc_launch(order, a, s), "M2L (tensor cores)");
             ++launches;
         } else {
+            // M2L by rotation (Sec. 3.4); by default from p = 4, where it is the faster one
+            const bool rot = precision == DAFMM_FP64 && (c->m2l_rot > 0 || (c->m2l_rot < 0 && order >= 4));
+            if (rot && (rc = ensure_rotation(c, order, s))) return rc;
             for (int l = 2; l <= L; ++l) {
                 if (l == L) mark(4);
                 const double inv_h = 1.0 / ldexp(t->dom[3], -l);
-                CK(c, ops->m2l_level(od, precision, l, ex.M[l], ex.Mf[l], ex.L[l], inv_h, s), "M2L");
+                if (rot) CK(c, ops->m2l_rot(od, l, ex.M[l], ex.L[l], inv_h, s), "M2L (rotation)");
+                else CK(c, ops->m2l_level(od, precision, l, ex.M[l], ex.Mf[l], ex.L[l], inv_h, s), "M2L");
                 ++launches;
             }
         }
@@ -1557,6 +1652,10 @@ int dafmm_set_option(dafmm_ctx* c, int option, int64_t value) {
     }
     if (option == DAFMM_OPT_M2L_F16 && (value == 0 || value == 1)) {
         c->m2l_f16 = (int)value;
+        return DAFMM_OK;
+    }
+    if (option == DAFMM_OPT_M2L_ROTATION && (value == -1 || value == 0 || value == 1)) {
+        c->m2l_rot = (int)value;
         return DAFMM_OK;
     }
     return fail(c, DAFMM_ERR_INVALID_ARG, "option");

@@ -298,20 +298,25 @@ struct SmemStore {
     __device__ __forceinline__ void operator()(int k, double v) const { o[k] = v; }
 };
 
+// r0s (optional): block b computes the matrix of the displacement r0s[3 b .. 3 b + 2] (any
+// real vector, e.g. along an axis) into slot b of K64, instead of an integer key's
 __global__ void __launch_bounds__(256) k_kgen(MulTab mt, double* __restrict__ K64, float* __restrict__ K32,
-                                              int key_only, const short* __restrict__ key_list) {
+                                              int key_only, const short* __restrict__ key_list,
+                                              const double* __restrict__ r0s) {
     __shared__ double buf[8][NCP];
     const int key = key_only >= 0 ? key_only : (key_list ? key_list[blockIdx.x] : blockIdx.x);
     const int vx = key / 49 - 3, vy = (key / 7) % 7 - 3, vz = key % 7 - 3;
     const int amax = max(abs(vx), max(abs(vy), abs(vz)));
-    if (amax <= 1) return;  // adjacent boxes never interact through M2L
+    if (!r0s && amax <= 1) return;  // adjacent boxes never interact through M2L
     double* sR = buf[0];
     double* m2[3] = {buf[1], buf[2], buf[3]};
     double* X = buf[4];
     double* XY = buf[5];
     double* Z0 = buf[6];
     double* Z1 = buf[7];
-    const double v[3] = {(double)vx, (double)vy, (double)vz};
+    const double v[3] = {r0s ? r0s[3 * blockIdx.x] : (double)vx, r0s ? r0s[3 * blockIdx.x + 1] : (double)vy,
+                         r0s ? r0s[3 * blockIdx.x + 2] : (double)vz};
+    const size_t slot = r0s ? blockIdx.x : (size_t)(key_only >= 0 ? 0 : key);
     const double rho = 1.0 / (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
     if (threadIdx.x == 0) {
         gen::GEN(m2lmap_inv)<double>(v[0], v[1], v[2], rho, SmemStore{X});
@@ -359,8 +364,8 @@ __global__ void __launch_bounds__(256) k_kgen(MulTab mt, double* __restrict__ K6
                 }
                 // column alpha = sqrt(R) * Z  -> K[key][beta][alpha]
                 const int alpha = da_index(a, b, c);
-                double* out = K64 + (size_t)(key_only >= 0 ? 0 : key) * NC * NCP;
-                float* out32 = K32 ? K32 + (size_t)(key_only >= 0 ? 0 : key) * NC * NCP : nullptr;
+                double* out = K64 + slot * NC * NCP;
+                float* out32 = K32 ? K32 + slot * NC * NCP : nullptr;
                 for (int k = threadIdx.x; k < NC; k += blockDim.x) {
                     double s = 0.0;
                     for (int e = mt.rowptr[k]; e < mt.rowptr[k + 1]; ++e) {
@@ -445,6 +450,184 @@ __global__ void __launch_bounds__(256) k_m2l(const T* __restrict__ K, int l, con
             const int b = w + 8 * j;
             if (b < NC) L[(size_t)t * NCP + b] = (double)acc[j] * inv_h;
         }
+    }
+}
+
+// ---- M2L by rotation (Sec. 3.4), FP64 -------------------------------------------------------
+// K^_v = B_v A_|v| F_v: F_v rotates the source expansion so that v lies on the positive x axis
+// (M^(u) = M(Q^T u), Q = Rz(phi) Rx(theta) with theta = atan2(vz, vy), phi = atan2(sqrt(vy^2 +
+// vz^2), vx)), A_rho is Eq. 5 along the axis (displacement (rho, 0, 0)), and B_v rotates the
+// result back (L(d) = L^(Q d)).  A linear substitution keeps every degree apart; a rotation
+// about one axis moves only the other two variables, so it acts on the binary forms of fixed
+// exponent of the untouched variable: the form of degree m in (p, q) is multiplied by the
+// (m+1) x (m+1) matrix of p -> al p + be q, q -> ga p + de q.  The four substitutions (forward
+// about x then z, back about z then x) are tabulated per displacement key; A_rho is sparse:
+// column (a, b, c) reaches row (a', b', c') only when b' >= b, c' >= c and both differences are
+// even (the axial map depends on y and z through y^2 + z^2 and odd powers of y, z alone).
+constexpr int ROT_TSZ = (P + 1) * (P + 2) * (2 * P + 3) / 6;  // sum over m <= P of (m+1)^2
+
+__host__ __device__ constexpr int rot_off(int m) { return m * (m + 1) * (2 * m + 1) / 6; }
+__host__ __device__ constexpr int deg_start(int n) { return n * (n + 1) * (n + 2) / 6; }
+// index of d^(a, b, c) with n = a + b + c: degree n graded, x exponent descending, then y
+__host__ __device__ constexpr int coef_index(int n, int a, int c) { return deg_start(n) + (n - a) * (n - a + 1) / 2 + c; }
+
+__device__ __forceinline__ void coef_exponents(int k, int& a, int& b, int& c) {
+    int n = 0;
+    while (deg_start(n + 1) <= k) ++n;
+    int r = k - deg_start(n), u = 0;  // u = n - a
+    while ((u + 1) * (u + 2) / 2 <= r) ++u;
+    a = n - u;
+    c = r - u * (u + 1) / 2;
+    b = n - a - c;
+}
+
+// per key: the four substitution matrices (forward x-step, forward z-step, back z-step, back
+// x-step), each packed over m = 0..P
+__global__ void __launch_bounds__(128) k_rot_tables(double* __restrict__ T) {
+    const int key = blockIdx.x;
+    const double vx = key / 49 - 3, vy = (key / 7) % 7 - 3, vz = key % 7 - 3;
+    const double ryz = sqrt(vy * vy + vz * vz), rho = sqrt(vx * vx + vy * vy + vz * vz);
+    const double c1 = ryz > 0.0 ? vy / ryz : 1.0, s1 = ryz > 0.0 ? vz / ryz : 0.0;
+    const double c2 = rho > 0.0 ? vx / rho : 1.0, s2 = rho > 0.0 ? ryz / rho : 0.0;
+    // (al, be, ga, de) per substitution: old p = al p' + be q', old q = ga p' + de q'
+    const double sub[4][4] = {{c1, -s1, s1, c1}, {c2, -s2, s2, c2}, {c2, s2, -s2, c2}, {c1, s1, -s1, c1}};
+    for (int e = threadIdx.x; e < 4 * ROT_TSZ; e += blockDim.x) {
+        const int w = e / ROT_TSZ, r = e - w * ROT_TSZ;
+        int m = 0;
+        while (rot_off(m + 1) <= r) ++m;
+        const int i = (r - rot_off(m)) / (m + 1), j = (r - rot_off(m)) % (m + 1);
+        const double al = sub[w][0], be = sub[w][1], ga = sub[w][2], de = sub[w][3];
+        // coefficient of p^(m-i) q^i in (al p + be q)^(m-j) (ga p + de q)^j
+        double acc = 0.0;
+        for (int k = 0; k <= i; ++k) {  // k from the first factor, i - k from the second
+            if (k > m - j || i - k > j) continue;
+            double c_a = 1.0, c_b = 1.0;
+            for (int t = 0; t < k; ++t) c_a = c_a * (m - j - t) / (t + 1);
+            for (int t = 0; t < i - k; ++t) c_b = c_b * (j - t) / (t + 1);
+            double pw = c_a * c_b;
+            for (int t = 0; t < m - j - k; ++t) pw *= al;
+            for (int t = 0; t < k; ++t) pw *= be;
+            for (int t = 0; t < j - (i - k); ++t) pw *= ga;
+            for (int t = 0; t < i - k; ++t) pw *= de;
+            acc += pw;
+        }
+        T[(size_t)key * 4 * ROT_TSZ + e] = acc;
+    }
+}
+
+// the axial matrices [nrho][NC][NCP] (dense, from k_kgen) -> their structural non-zeros
+__global__ void k_axial_gather(const double* __restrict__ K, const int* __restrict__ rowptr,
+                               const unsigned short* __restrict__ col, int nnz, double* __restrict__ val) {
+    const int r = blockIdx.x;
+    for (int b = threadIdx.x; b < NC; b += blockDim.x)
+        for (int e = rowptr[b]; e < rowptr[b + 1]; ++e)
+            val[(size_t)r * nnz + e] = K[((size_t)r * NC + b) * NCP + col[e]];
+}
+
+// out = substitution about x (binary forms in y, z at fixed x exponent) of in, for the
+// coefficients k = lane + 32 r of this lane
+template <int NJR>
+__device__ __forceinline__ void rot_subst_x(const double* __restrict__ T, const double* in, double* out,
+                                            const int (&kx)[NJR], int lane) {
+#pragma unroll
+    for (int r = 0; r < NJR; ++r) {
+        const int k = lane + 32 * r;
+        if (k >= NC) break;
+        const int a = kx[r] & 255, b = (kx[r] >> 8) & 255, c = kx[r] >> 16;
+        const int n = a + b + c, m = b + c, i = c;
+        const double* t = T + rot_off(m) + i * (m + 1);
+        const double* f = in + coef_index(n, a, 0);
+        double s = 0.0;
+        for (int j = 0; j <= m; ++j) s = fma(t[j], f[j], s);
+        out[k] = s;
+    }
+}
+
+// coefficient (a, b, c) of the substitution about z (binary forms in x, y at fixed z exponent;
+// position = y exponent) of in
+__device__ __forceinline__ double rot_subst_z1(const double* __restrict__ T, const double* in, int a, int b, int c) {
+    const int n = a + b + c, m = a + b, i = b;
+    const double* t = T + rot_off(m) + i * (m + 1);
+    double s = 0.0;
+    for (int j = 0; j <= m; ++j) s = fma(t[j], in[coef_index(n, m - j, c)], s);
+    return s;
+}
+
+template <int NJR>
+__global__ void __launch_bounds__(256, 2) k_m2l_rot(const double* __restrict__ Ttab, const int* __restrict__ krho,
+                                                 const int* __restrict__ arow, const unsigned short* __restrict__ acol,
+                                                 const double* __restrict__ aval, int annz, int l,
+                                                 const double* __restrict__ M, double* __restrict__ L, double inv_h) {
+    __shared__ double sbuf[8][2][NCP];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int Pp = 1 << (l - 1), P3 = Pp * Pp * Pp, n_side = 1 << l;
+    const int t = blockIdx.x * 8 + w;  // target box, octant-major
+    if (t >= 8 * P3) return;
+    const int oct = t / P3, lin = t - oct * P3;
+    const int ox = oct & 1, oy = (oct >> 1) & 1, oz = (oct >> 2) & 1;
+    const int tx = 2 * (lin % Pp) + ox, ty = 2 * ((lin / Pp) % Pp) + oy, tz = 2 * (lin / (Pp * Pp)) + oz;
+    double* X = sbuf[w][0];
+    double* Y = sbuf[w][1];
+    int kx[NJR];  // exponents (a, b, c) of this lane's coefficients, a | b << 8 | c << 16
+    double acc[NJR];
+#pragma unroll
+    for (int r = 0; r < NJR; ++r) {
+        acc[r] = 0.0;
+        int a = 0, b = 0, c = 0;
+        if (lane + 32 * r < NC) coef_exponents(lane + 32 * r, a, b, c);
+        kx[r] = a | (b << 8) | (c << 16);
+    }
+    for (int vx = -3 + ox; vx <= 2 + ox; ++vx)
+        for (int vy = -3 + oy; vy <= 2 + oy; ++vy)
+            for (int vz = -3 + oz; vz <= 2 + oz; ++vz) {
+                if (abs(vx) <= 1 && abs(vy) <= 1 && abs(vz) <= 1) continue;
+                const int sx = tx - vx, sy = ty - vy, sz = tz - vz;
+                if (sx < 0 || sy < 0 || sz < 0 || sx >= n_side || sy >= n_side || sz >= n_side) continue;
+                const int key = (vx + 3) * 49 + (vy + 3) * 7 + (vz + 3);
+                const double* T = Ttab + (size_t)key * 4 * ROT_TSZ;
+                const double* av = aval + (size_t)krho[key] * annz;
+                const double* Ms = M + (size_t)octmajor_index(l, sx, sy, sz) * NCP;
+                __syncwarp();
+                for (int k = lane; k < NC; k += 32) X[k] = Ms[k];
+                __syncwarp();
+                rot_subst_x<NJR>(T, X, Y, kx, lane);  // forward, about x
+                __syncwarp();
+#pragma unroll
+                for (int r = 0; r < NJR; ++r)  // forward, about z
+                    if (lane + 32 * r < NC)
+                        X[lane + 32 * r] = rot_subst_z1(T + ROT_TSZ, Y, kx[r] & 255, (kx[r] >> 8) & 255, kx[r] >> 16);
+                __syncwarp();
+#pragma unroll
+                for (int r = 0; r < NJR; ++r) {  // Eq. 5 along the axis
+                    const int k = lane + 32 * r;
+                    if (k >= NC) break;
+                    double s = 0.0;
+                    for (int e = arow[k]; e < arow[k + 1]; ++e) s = fma(av[e], X[acol[e]], s);
+                    Y[k] = s;
+                }
+                __syncwarp();
+#pragma unroll
+                for (int r = 0; r < NJR; ++r)  // back, about z
+                    if (lane + 32 * r < NC)
+                        X[lane + 32 * r] = rot_subst_z1(T + 2 * ROT_TSZ, Y, kx[r] & 255, (kx[r] >> 8) & 255, kx[r] >> 16);
+                __syncwarp();
+#pragma unroll
+                for (int r = 0; r < NJR; ++r) {  // back, about x, into the sums
+                    const int k = lane + 32 * r;
+                    if (k >= NC) break;
+                    const int a = kx[r] & 255, b = (kx[r] >> 8) & 255, c = kx[r] >> 16;
+                    const int n = a + b + c, m = b + c, i = c;
+                    const double* tt = T + 3 * ROT_TSZ + rot_off(m) + i * (m + 1);
+                    const double* f = X + coef_index(n, a, 0);
+                    double s = 0.0;
+                    for (int j = 0; j <= m; ++j) s = fma(tt[j], f[j], s);
+                    acc[r] += s;
+                }
+            }
+#pragma unroll
+    for (int r = 0; r < NJR; ++r) {
+        const int k = lane + 32 * r;
+        if (k < NC) L[(size_t)t * NCP + k] = acc[r] * inv_h;
     }
 }
 
@@ -1190,10 +1373,29 @@ static cudaError_t leaf_launch(const TreeView& tv, int prec, const double* Lleaf
     return cudaGetLastError();
 }
 
+// M2L by rotation at level l (FP64, uniform trees): L~ = (1/h) sum_v B_v A_|v| F_v M~
+static cudaError_t m2l_rot_launch(const OrderData& od, int l, const double* M, double* L, double inv_h,
+                                  cudaStream_t s) {
+    constexpr int NJR = (NC + 31) / 32;
+    const int nbox = 1 << (3 * l);
+    k_m2l_rot<NJR><<<(nbox + 7) / 8, 256, 0, s>>>(od.rot_T, od.rot_rho, od.ax_rowptr, od.ax_col, od.ax_val,
+                                                   od.ax_nnz, l, M, L, inv_h);
+    return cudaGetLastError();
+}
+
+// the rotation tables of all keys and the axial matrices of the nrho lengths in r0s (3 per
+// length, along x); Kscratch holds nrho dense matrices
+static cudaError_t rot_setup_launch(OrderData& od, const double* r0s, int nrho, double* Kscratch, cudaStream_t s) {
+    k_kgen<<<nrho, 256, 0, s>>>(od.mul(), Kscratch, nullptr, -1, nullptr, r0s);
+    k_axial_gather<<<nrho, 256, 0, s>>>(Kscratch, od.ax_rowptr, od.ax_col, od.ax_nnz, od.ax_val);
+    k_rot_tables<<<kNumKeys, 128, 0, s>>>(od.rot_T);
+    return cudaGetLastError();
+}
+
 // the matrices of the given keys (all keys when key_list is null)
 static cudaError_t kgen_launch(OrderData& od, const short* key_list, int nkeys, cudaStream_t s) {
     if (nkeys <= 0) return cudaSuccess;
-    k_kgen<<<key_list ? nkeys : kNumKeys, 256, 0, s>>>(od.mul(), od.K64, od.K32, -1, key_list);
+    k_kgen<<<key_list ? nkeys : kNumKeys, 256, 0, s>>>(od.mul(), od.K64, od.K32, -1, key_list, nullptr);
     return cudaGetLastError();
 }
 
@@ -1344,7 +1546,8 @@ const OrderOps* DAFMM_CAT(order_ops_p, DAFMM_P)() {
                        gen::GENT(m2m, _val)},
         HostShiftTable{gen::GENT(l2l, _nnz), gen::GENT(l2l, _rowptr), gen::GENT(l2l, _col), gen::GENT(l2l, _par),
                        gen::GENT(l2l, _val)},
-        p2m_launch, m2m_launch, l2l_launch, m2l_launch, leaf_launch, kgen_launch,
+        p2m_launch, m2m_launch, l2l_launch, m2l_launch, leaf_launch, kgen_launch, m2l_rot_launch, rot_setup_launch,
+        ROT_TSZ,
         op_p2m, op_p2l, op_l2p, op_m2p, op_shift,
         p2m_a_launch, m2m_a_launch, m2l_a_launch, p2l_a_launch, l2l_a_launch, leaf_a_launch};
     return &ops;

@@ -73,6 +73,14 @@ struct OrderData {
     float* L2Lhi = nullptr;
     float* L2Llo = nullptr;
     bool k_ready = false;
+    // M2L by rotation (Sec. 3.4): per key the four substitution tables, per key the index of
+    // its axial length, the axial matrices' structural non-zeros (CSR by row) per length
+    double* rot_T = nullptr;
+    int* rot_rho = nullptr;
+    int* ax_rowptr = nullptr;
+    unsigned short* ax_col = nullptr;
+    double* ax_val = nullptr;
+    int ax_nnz = 0, n_rho = 0;
     ShiftTab m2m() const { return ShiftTab{m2m_rowptr, m2m_col, m2m_par, m2m_val, m2m_valf, m2m_rp8}; }
     ShiftTab l2l() const { return ShiftTab{l2l_rowptr, l2l_col, l2l_par, l2l_val, l2l_valf, l2l_rp8}; }
     MulTab mul() const { return MulTab{mul_rowptr, mul_pairs, mul_minus}; }
@@ -118,6 +126,10 @@ struct OrderOps {
     cudaError_t (*leaf)(const TreeView&, int prec, const double* Lleaf, double* phi, double* field,
                         cudaStream_t);
     cudaError_t (*kgen)(OrderData&, const short* key_list, int nkeys, cudaStream_t);  // null list: all keys
+    // M2L by rotation (FP64, uniform trees) and its tables
+    cudaError_t (*m2l_rot)(const OrderData&, int level, const double* M, double* L, double inv_h, cudaStream_t);
+    cudaError_t (*rot_setup)(OrderData&, const double* r0s, int nrho, double* Kscratch, cudaStream_t);
+    int rot_tsz;  // doubles per substitution table (sum over m <= p of (m+1)^2)
     cudaError_t (*op_p2m)(int prec, int64_t n, const double* s, const double* q, double* out, cudaStream_t);
     cudaError_t (*op_p2l)(int prec, int64_t n, const double* w, const double* q, double* out, cudaStream_t);
     cudaError_t (*op_l2p)(int prec, int64_t n, const double* L, const double* x, double* out4, cudaStream_t);

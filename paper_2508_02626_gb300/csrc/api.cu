@@ -389,6 +389,9 @@ void free_order(dafmm_ctx* c, OrderData& od) {
         dev_free(c, od.ax_rowptr, ((size_t)nc + 1) * sizeof(int));
         dev_free(c, od.ax_col, (size_t)od.ax_nnz * sizeof(unsigned short));
         dev_free(c, od.ax_val, (size_t)od.n_rho * od.ax_nnz * sizeof(double));
+        dev_free(c, od.rot_lx, (size_t)od.rot_len[0] * 32 * sizeof(uint2));
+        dev_free(c, od.rot_lz, (size_t)od.rot_len[1] * 32 * sizeof(uint2));
+        dev_free(c, od.rot_la, (size_t)od.rot_len[2] * 32 * sizeof(uint2));
     }
     od = OrderData();
 }
@@ -462,6 +465,52 @@ int ensure_rotation(dafmm_ctx* c, int p, cudaStream_t s) {
         if (it == len2.end()) len2.push_back(r2);
     }
     const int nrho = (int)len2.size();
+    // the kernel's task lists: per step the outputs' multiply-adds (table offset, input index),
+    // outputs dealt to the 32 lanes largest first onto the least loaded lane, each lane's tasks
+    // padded to the longest lane with tasks that read the zero at index nc
+    std::vector<int> ex;
+    for (int n = 0; n <= p; ++n)
+        for (int a = n; a >= 0; --a)
+            for (int b = n - a; b >= 0; --b) ex.push_back(a);
+    auto deg_start = [](int n) { return n * (n + 1) * (n + 2) / 6; };
+    auto cidx = [&](int n, int a, int c) { return deg_start(n) + (n - a) * (n - a + 1) / 2 + c; };
+    auto roff = [](int m) { return m * (m + 1) * (2 * m + 1) / 6; };
+    struct Task { unsigned off, in; };
+    auto build = [&](const std::vector<std::vector<Task>>& per_out, std::vector<uint2>& list) {
+        std::vector<int> order(nc);
+        for (int k = 0; k < nc; ++k) order[k] = k;
+        std::stable_sort(order.begin(), order.end(),
+                         [&](int u, int v) { return per_out[u].size() > per_out[v].size(); });
+        std::vector<std::vector<uint2>> lane(32);
+        for (int k : order) {
+            int best = 0;
+            for (int q = 1; q < 32; ++q)
+                if (lane[q].size() < lane[best].size()) best = q;
+            for (size_t j = 0; j < per_out[k].size(); ++j) {
+                const bool last = j + 1 == per_out[k].size();
+                lane[best].push_back(make_uint2(per_out[k][j].off | (last ? 0x80000000u : 0u),
+                                                per_out[k][j].in | ((unsigned)k << 16)));
+            }
+        }
+        size_t len = 0;
+        for (auto& v : lane) len = std::max(len, v.size());
+        list.assign(len * 32, make_uint2(0u, (unsigned)nc));
+        for (int q = 0; q < 32; ++q)
+            for (size_t t = 0; t < lane[q].size(); ++t) list[t * 32 + q] = lane[q][t];
+        return (int)len;
+    };
+    std::vector<std::vector<Task>> tx(nc), tz(nc), ta(nc);
+    for (int k = 0; k < nc; ++k) {
+        const int a = ex[k], b = ey[k], cz = ez[k], n = a + b + cz;
+        const int mx = b + cz, mz = a + b;
+        for (int j = 0; j <= mx; ++j)
+            tx[k].push_back({(unsigned)(roff(mx) + cz * (mx + 1) + j), (unsigned)(cidx(n, a, 0) + j)});
+        for (int j = 0; j <= mz; ++j)
+            tz[k].push_back({(unsigned)(roff(mz) + b * (mz + 1) + j), (unsigned)cidx(n, mz - j, cz)});
+        for (int e = rowptr[k]; e < rowptr[k + 1]; ++e) ta[k].push_back({(unsigned)e, (unsigned)col[e]});
+    }
+    std::vector<uint2> lx, lz, la;
+    const int len_x = build(tx, lx), len_z = build(tz, lz), len_a = build(ta, la);
     std::vector<double> r0s(3 * (size_t)nrho, 0.0);
     for (int r = 0; r < nrho; ++r) r0s[3 * r] = std::sqrt((double)len2[r]);
     const size_t tbytes = (size_t)kNumKeys * 4 * ops->rot_tsz * sizeof(double);
@@ -469,8 +518,12 @@ int ensure_rotation(dafmm_ctx* c, int p, cudaStream_t s) {
     double *T = nullptr, *val = nullptr, *d_r0s = nullptr, *Ks = nullptr;
     int *rho = nullptr, *rp = nullptr;
     unsigned short* cl = nullptr;
+    uint2 *dlx = nullptr, *dlz = nullptr, *dla = nullptr;
     int rc;
     auto release = [&]() {
+        dev_free(c, dlx, lx.size() * sizeof(uint2));
+        dev_free(c, dlz, lz.size() * sizeof(uint2));
+        dev_free(c, dla, la.size() * sizeof(uint2));
         dev_free(c, T, tbytes);
         dev_free(c, val, (size_t)nrho * nnz * sizeof(double));
         dev_free(c, rho, (size_t)kNumKeys * sizeof(int));
@@ -481,7 +534,10 @@ int ensure_rotation(dafmm_ctx* c, int p, cudaStream_t s) {
         (rc = dev_alloc(c, (void**)&val, (size_t)nrho * nnz * sizeof(double), "axial M2L matrices")) ||
         (rc = dev_alloc(c, (void**)&rho, (size_t)kNumKeys * sizeof(int), "rotation tables")) ||
         (rc = dev_alloc(c, (void**)&rp, ((size_t)nc + 1) * sizeof(int), "axial M2L matrices")) ||
-        (rc = dev_alloc(c, (void**)&cl, (size_t)nnz * sizeof(unsigned short), "axial M2L matrices"))) {
+        (rc = dev_alloc(c, (void**)&cl, (size_t)nnz * sizeof(unsigned short), "axial M2L matrices")) ||
+        (rc = dev_alloc(c, (void**)&dlx, lx.size() * sizeof(uint2), "rotation task lists")) ||
+        (rc = dev_alloc(c, (void**)&dlz, lz.size() * sizeof(uint2), "rotation task lists")) ||
+        (rc = dev_alloc(c, (void**)&dla, la.size() * sizeof(uint2), "rotation task lists"))) {
         release();
         return rc;
     }
@@ -493,10 +549,15 @@ int ensure_rotation(dafmm_ctx* c, int p, cudaStream_t s) {
     }
     od.rot_T = T; od.rot_rho = rho; od.ax_rowptr = rp; od.ax_col = cl; od.ax_val = val;
     od.ax_nnz = nnz; od.n_rho = nrho;
+    od.rot_lx = dlx; od.rot_lz = dlz; od.rot_la = dla;
+    od.rot_len[0] = len_x; od.rot_len[1] = len_z; od.rot_len[2] = len_a;
     cudaError_t e = cudaMemcpyAsync(rho, rho_of.data(), rho_of.size() * sizeof(int), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(rp, rowptr.data(), rowptr.size() * sizeof(int), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(cl, col.data(), col.size() * sizeof(unsigned short), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(d_r0s, r0s.data(), r0s.size() * sizeof(double), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dlx, lx.data(), lx.size() * sizeof(uint2), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dlz, lz.data(), lz.size() * sizeof(uint2), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dla, la.data(), la.size() * sizeof(uint2), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = ops->rot_setup(od, d_r0s, nrho, Ks, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // shared by every later evaluation, on any stream
     dev_free(c, d_r0s, r0s.size() * sizeof(double));
@@ -504,6 +565,7 @@ int ensure_rotation(dafmm_ctx* c, int p, cudaStream_t s) {
     if (e != cudaSuccess) {
         release();
         od.rot_T = nullptr; od.rot_rho = nullptr; od.ax_rowptr = nullptr; od.ax_col = nullptr; od.ax_val = nullptr;
+        od.rot_lx = od.rot_lz = od.rot_la = nullptr;
         return cuda_fail(c, e, "rotation tables");
     }
     return DAFMM_OK;

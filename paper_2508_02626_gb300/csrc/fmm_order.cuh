@@ -467,20 +467,6 @@ __global__ void __launch_bounds__(256) k_m2l(const T* __restrict__ K, int l, con
 constexpr int ROT_TSZ = (P + 1) * (P + 2) * (2 * P + 3) / 6;  // sum over m <= P of (m+1)^2
 
 __host__ __device__ constexpr int rot_off(int m) { return m * (m + 1) * (2 * m + 1) / 6; }
-__host__ __device__ constexpr int deg_start(int n) { return n * (n + 1) * (n + 2) / 6; }
-// index of d^(a, b, c) with n = a + b + c: degree n graded, x exponent descending, then y
-__host__ __device__ constexpr int coef_index(int n, int a, int c) { return deg_start(n) + (n - a) * (n - a + 1) / 2 + c; }
-
-__device__ __forceinline__ void coef_exponents(int k, int& a, int& b, int& c) {
-    int n = 0;
-    while (deg_start(n + 1) <= k) ++n;
-    int r = k - deg_start(n), u = 0;  // u = n - a
-    while ((u + 1) * (u + 2) / 2 <= r) ++u;
-    a = n - u;
-    c = r - u * (u + 1) / 2;
-    b = n - a - c;
-}
-
 // per key: the four substitution matrices (forward x-step, forward z-step, back z-step, back
 // x-step), each packed over m = 0..P
 __global__ void __launch_bounds__(128) k_rot_tables(double* __restrict__ T) {
@@ -524,41 +510,43 @@ __global__ void k_axial_gather(const double* __restrict__ K, const int* __restri
             val[(size_t)r * nnz + e] = K[((size_t)r * NC + b) * NCP + col[e]];
 }
 
-// out = substitution about x (binary forms in y, z at fixed x exponent) of in, for the
-// coefficients k = lane + 32 r of this lane
-template <int NJR>
-__device__ __forceinline__ void rot_subst_x(const double* __restrict__ T, const double* in, double* out,
-                                            const int (&kx)[NJR], int lane) {
-#pragma unroll
-    for (int r = 0; r < NJR; ++r) {
-        const int k = lane + 32 * r;
-        if (k >= NC) break;
-        const int a = kx[r] & 255, b = (kx[r] >> 8) & 255, c = kx[r] >> 16;
-        const int n = a + b + c, m = b + c, i = c;
-        const double* t = T + rot_off(m) + i * (m + 1);
-        const double* f = in + coef_index(n, a, 0);
-        double s = 0.0;
-        for (int j = 0; j <= m; ++j) s = fma(t[j], f[j], s);
-        out[k] = s;
+// One step of the rotation M2L for the warp: out[k] (=, or += with ACC) sum over the tasks of
+// k of tab[offset] * in[index].  Each lane runs its own list of tasks (a precomputed,
+// load-balanced share of the step's multiply-adds, whole outputs per lane, padded to a common
+// length with tasks that read the zero at in[NC]); task t of lane l is list[32 t + l]:
+// x = table offset | last-of-output << 31, y = input index | output index << 16.  Lanes with
+// outputs of very different lengths would otherwise run every loop to the longest one, and
+// FP64 instructions are this kernel's bound.
+template <bool ACC>
+__device__ __forceinline__ void rot_step(const uint2* __restrict__ list, int len, const double* __restrict__ tab,
+                                         const double* in, double* out, int lane) {
+    double s = 0.0;
+#pragma unroll 4
+    for (int t = 0; t < len; ++t) {
+        const uint2 w = list[32 * t + lane];
+        s = fma(tab[w.x & 0x7fffffffu], in[w.y & 0xffffu], s);
+        if (w.x >> 31) {
+            const int k = (int)(w.y >> 16);
+            if (ACC) out[k] += s;
+            else out[k] = s;
+            s = 0.0;
+        }
     }
 }
 
-// coefficient (a, b, c) of the substitution about z (binary forms in x, y at fixed z exponent;
-// position = y exponent) of in
-__device__ __forceinline__ double rot_subst_z1(const double* __restrict__ T, const double* in, int a, int b, int c) {
-    const int n = a + b + c, m = a + b, i = b;
-    const double* t = T + rot_off(m) + i * (m + 1);
-    double s = 0.0;
-    for (int j = 0; j <= m; ++j) s = fma(t[j], in[coef_index(n, m - j, c)], s);
-    return s;
-}
+// task lists of the rotation M2L: x-step (substitution about x), z-step, axial matrix
+struct RotLists {
+    const uint2* x;
+    const uint2* z;
+    const uint2* a;
+    int lx, lz, la;
+};
 
-template <int NJR>
 __global__ void __launch_bounds__(256, 2) k_m2l_rot(const double* __restrict__ Ttab, const int* __restrict__ krho,
-                                                 const int* __restrict__ arow, const unsigned short* __restrict__ acol,
-                                                 const double* __restrict__ aval, int annz, int l,
-                                                 const double* __restrict__ M, double* __restrict__ L, double inv_h) {
-    __shared__ double sbuf[8][2][NCP];
+                                                    RotLists rl, const double* __restrict__ aval, int annz, int l,
+                                                    const double* __restrict__ M, double* __restrict__ L,
+                                                    double inv_h) {
+    __shared__ double sbuf[8][3][NCP + 1];  // per warp: two work vectors and the sums
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int Pp = 1 << (l - 1), P3 = Pp * Pp * Pp, n_side = 1 << l;
     const int t = blockIdx.x * 8 + w;  // target box, octant-major
@@ -568,14 +556,11 @@ __global__ void __launch_bounds__(256, 2) k_m2l_rot(const double* __restrict__ T
     const int tx = 2 * (lin % Pp) + ox, ty = 2 * ((lin / Pp) % Pp) + oy, tz = 2 * (lin / (Pp * Pp)) + oz;
     double* X = sbuf[w][0];
     double* Y = sbuf[w][1];
-    int kx[NJR];  // exponents (a, b, c) of this lane's coefficients, a | b << 8 | c << 16
-    double acc[NJR];
-#pragma unroll
-    for (int r = 0; r < NJR; ++r) {
-        acc[r] = 0.0;
-        int a = 0, b = 0, c = 0;
-        if (lane + 32 * r < NC) coef_exponents(lane + 32 * r, a, b, c);
-        kx[r] = a | (b << 8) | (c << 16);
+    double* S = sbuf[w][2];
+    for (int k = lane; k <= NCP; k += 32) {
+        X[k] = 0.0;  // X[NC], Y[NC]: the zero that padding tasks read
+        Y[k] = 0.0;
+        S[k] = 0.0;
     }
     for (int vx = -3 + ox; vx <= 2 + ox; ++vx)
         for (int vy = -3 + oy; vy <= 2 + oy; ++vy)
@@ -585,50 +570,22 @@ __global__ void __launch_bounds__(256, 2) k_m2l_rot(const double* __restrict__ T
                 if (sx < 0 || sy < 0 || sz < 0 || sx >= n_side || sy >= n_side || sz >= n_side) continue;
                 const int key = (vx + 3) * 49 + (vy + 3) * 7 + (vz + 3);
                 const double* T = Ttab + (size_t)key * 4 * ROT_TSZ;
-                const double* av = aval + (size_t)krho[key] * annz;
                 const double* Ms = M + (size_t)octmajor_index(l, sx, sy, sz) * NCP;
                 __syncwarp();
                 for (int k = lane; k < NC; k += 32) X[k] = Ms[k];
                 __syncwarp();
-                rot_subst_x<NJR>(T, X, Y, kx, lane);  // forward, about x
+                rot_step<false>(rl.x, rl.lx, T, X, Y, lane);  // forward, about x
                 __syncwarp();
-#pragma unroll
-                for (int r = 0; r < NJR; ++r)  // forward, about z
-                    if (lane + 32 * r < NC)
-                        X[lane + 32 * r] = rot_subst_z1(T + ROT_TSZ, Y, kx[r] & 255, (kx[r] >> 8) & 255, kx[r] >> 16);
+                rot_step<false>(rl.z, rl.lz, T + ROT_TSZ, Y, X, lane);  // forward, about z
                 __syncwarp();
-#pragma unroll
-                for (int r = 0; r < NJR; ++r) {  // Eq. 5 along the axis
-                    const int k = lane + 32 * r;
-                    if (k >= NC) break;
-                    double s = 0.0;
-                    for (int e = arow[k]; e < arow[k + 1]; ++e) s = fma(av[e], X[acol[e]], s);
-                    Y[k] = s;
-                }
+                rot_step<false>(rl.a, rl.la, aval + (size_t)krho[key] * annz, X, Y, lane);  // Eq. 5 on the axis
                 __syncwarp();
-#pragma unroll
-                for (int r = 0; r < NJR; ++r)  // back, about z
-                    if (lane + 32 * r < NC)
-                        X[lane + 32 * r] = rot_subst_z1(T + 2 * ROT_TSZ, Y, kx[r] & 255, (kx[r] >> 8) & 255, kx[r] >> 16);
+                rot_step<false>(rl.z, rl.lz, T + 2 * ROT_TSZ, Y, X, lane);  // back, about z
                 __syncwarp();
-#pragma unroll
-                for (int r = 0; r < NJR; ++r) {  // back, about x, into the sums
-                    const int k = lane + 32 * r;
-                    if (k >= NC) break;
-                    const int a = kx[r] & 255, b = (kx[r] >> 8) & 255, c = kx[r] >> 16;
-                    const int n = a + b + c, m = b + c, i = c;
-                    const double* tt = T + 3 * ROT_TSZ + rot_off(m) + i * (m + 1);
-                    const double* f = X + coef_index(n, a, 0);
-                    double s = 0.0;
-                    for (int j = 0; j <= m; ++j) s = fma(tt[j], f[j], s);
-                    acc[r] += s;
-                }
+                rot_step<true>(rl.x, rl.lx, T + 3 * ROT_TSZ, X, S, lane);  // back, about x, into the sums
             }
-#pragma unroll
-    for (int r = 0; r < NJR; ++r) {
-        const int k = lane + 32 * r;
-        if (k < NC) L[(size_t)t * NCP + k] = acc[r] * inv_h;
-    }
+    __syncwarp();
+    for (int k = lane; k < NC; k += 32) L[(size_t)t * NCP + k] = S[k] * inv_h;
 }
 
 // ---- leaves: P2P over the 27 neighbours + L2P --------------------------------------------------
@@ -1376,10 +1333,9 @@ static cudaError_t leaf_launch(const TreeView& tv, int prec, const double* Lleaf
 // M2L by rotation at level l (FP64, uniform trees): L~ = (1/h) sum_v B_v A_|v| F_v M~
 static cudaError_t m2l_rot_launch(const OrderData& od, int l, const double* M, double* L, double inv_h,
                                   cudaStream_t s) {
-    constexpr int NJR = (NC + 31) / 32;
     const int nbox = 1 << (3 * l);
-    k_m2l_rot<NJR><<<(nbox + 7) / 8, 256, 0, s>>>(od.rot_T, od.rot_rho, od.ax_rowptr, od.ax_col, od.ax_val,
-                                                   od.ax_nnz, l, M, L, inv_h);
+    const RotLists rl{od.rot_lx, od.rot_lz, od.rot_la, od.rot_len[0], od.rot_len[1], od.rot_len[2]};
+    k_m2l_rot<<<(nbox + 7) / 8, 256, 0, s>>>(od.rot_T, od.rot_rho, rl, od.ax_val, od.ax_nnz, l, M, L, inv_h);
     return cudaGetLastError();
 }
 

@@ -81,6 +81,11 @@ struct OrderData {
     unsigned short* ax_col = nullptr;
     double* ax_val = nullptr;
     int ax_nnz = 0, n_rho = 0;
+    // the kernel's load-balanced task lists (x-step, z-step, axial), [length][32] each
+    uint2* rot_lx = nullptr;
+    uint2* rot_lz = nullptr;
+    uint2* rot_la = nullptr;
+    int rot_len[3] = {0, 0, 0};
     ShiftTab m2m() const { return ShiftTab{m2m_rowptr, m2m_col, m2m_par, m2m_val, m2m_valf, m2m_rp8}; }
     ShiftTab l2l() const { return ShiftTab{l2l_rowptr, l2l_col, l2l_par, l2l_val, l2l_valf, l2l_rp8}; }
     MulTab mul() const { return MulTab{mul_rowptr, mul_pairs, mul_minus}; }

@@ -193,12 +193,12 @@ int dafmm_last_phase_ms(dafmm_ctx* ctx, double* out10);
  *   rate, M2L rounding ~1e-7 relative), 0 = TF32 hi/lo splits (~5e-8).  MIXED always uses
  *   the TF32 splits. */
 #define DAFMM_OPT_M2L_F16 4
-/*   DAFMM_OPT_M2L_ROTATION: the FP64 M2L of uniform trees (Sec. 3.4): 0 = the dense K^_v
+/*   DAFMM_OPT_M2L_ROTATION: the FP64 M2L (Sec. 3.4): 0 = the dense K^_v
  *   matrix of each displacement; 1 = rotate the source expansion so that the displacement lies
  *   on the x axis, apply Eq. 5 along the axis (a sparse matrix per distinct length |v|), rotate
  *   back -- per well-separated pair about 6.2k instead of 27k multiply-adds at p = 8, 14.7k
- *   instead of 82k at p = 10; -1 (default) = 1 from p = 4, else 0.  Adaptive trees keep the
- *   dense matrices. */
+ *   instead of 82k at p = 10; -1 (default) = 1 from p = 4, else 0.  Uniform and adaptive trees
+ *   (the V-list pairs of a level have the same 316 box displacements). */
 #define DAFMM_OPT_M2L_ROTATION 5
 int dafmm_set_option(dafmm_ctx* ctx, int option, int64_t value);
 

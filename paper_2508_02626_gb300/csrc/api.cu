@@ -1105,11 +1105,16 @@ int eval_adaptive(dafmm_tree* t, int order, int precision, double* dphi, double*
                 ++launches;
             }
         } else {
+            // FP64: the M2L by rotation (Sec. 3.4), by default from p = 4
+            const bool rot = precision == DAFMM_FP64 && (c->m2l_rot > 0 || (c->m2l_rot < 0 && order >= 4));
+            if (rot && (rc = ensure_rotation(c, order, s))) return rc;
             for (int l = 2; l <= t->maxlev; ++l) {
                 if (l == t->maxlev) mark(4);
                 int mx = 0;
                 for (int o = 0; o < 8; ++o) mx = std::max(mx, t->grp_ptr_h[l * 8 + o + 1] - t->grp_ptr_h[l * 8 + o]);
-                CK(c, ops->m2l_a(od, av, precision, t->grp_tg, t->grp_ptr, l * 8, mx, t->aM, t->aMf, t->aL, s), "M2L");
+                CK(c, ops->m2l_a(od, av, precision | (rot ? kM2LRot : 0), t->grp_tg, t->grp_ptr, l * 8, mx, t->aM,
+                                 t->aMf, t->aL, s),
+                   "M2L");
                 CK(c, ops->p2l_a(av, precision, t->level_start[l], t->level_start[l + 1], t->aL, s), "P2L");
                 launches += 2;
             }

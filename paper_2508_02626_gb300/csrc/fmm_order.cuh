@@ -542,6 +542,24 @@ struct RotLists {
     int lx, lz, la;
 };
 
+// one well-separated pair for the warp: S += B_v A_|v| F_v Ms (T: the key's four substitution
+// tables, av: the axial matrix of its length; X, Y: work vectors with X[NC] = Y[NC] = 0)
+__device__ __forceinline__ void rot_pair(const double* __restrict__ T, const double* __restrict__ av, const RotLists& rl,
+                                         const double* __restrict__ Ms, double* X, double* Y, double* S, int lane) {
+    __syncwarp();
+    for (int k = lane; k < NC; k += 32) X[k] = Ms[k];
+    __syncwarp();
+    rot_step<false>(rl.x, rl.lx, T, X, Y, lane);  // forward, about x
+    __syncwarp();
+    rot_step<false>(rl.z, rl.lz, T + ROT_TSZ, Y, X, lane);  // forward, about z
+    __syncwarp();
+    rot_step<false>(rl.a, rl.la, av, X, Y, lane);  // Eq. 5 on the axis
+    __syncwarp();
+    rot_step<false>(rl.z, rl.lz, T + 2 * ROT_TSZ, Y, X, lane);  // back, about z
+    __syncwarp();
+    rot_step<true>(rl.x, rl.lx, T + 3 * ROT_TSZ, X, S, lane);  // back, about x, into the sums
+}
+
 __global__ void __launch_bounds__(256, 2) k_m2l_rot(const double* __restrict__ Ttab, const int* __restrict__ krho,
                                                     RotLists rl, const double* __restrict__ aval, int annz, int l,
                                                     const double* __restrict__ M, double* __restrict__ L,
@@ -569,22 +587,53 @@ __global__ void __launch_bounds__(256, 2) k_m2l_rot(const double* __restrict__ T
                 const int sx = tx - vx, sy = ty - vy, sz = tz - vz;
                 if (sx < 0 || sy < 0 || sz < 0 || sx >= n_side || sy >= n_side || sz >= n_side) continue;
                 const int key = (vx + 3) * 49 + (vy + 3) * 7 + (vz + 3);
-                const double* T = Ttab + (size_t)key * 4 * ROT_TSZ;
-                const double* Ms = M + (size_t)octmajor_index(l, sx, sy, sz) * NCP;
-                __syncwarp();
-                for (int k = lane; k < NC; k += 32) X[k] = Ms[k];
-                __syncwarp();
-                rot_step<false>(rl.x, rl.lx, T, X, Y, lane);  // forward, about x
-                __syncwarp();
-                rot_step<false>(rl.z, rl.lz, T + ROT_TSZ, Y, X, lane);  // forward, about z
-                __syncwarp();
-                rot_step<false>(rl.a, rl.la, aval + (size_t)krho[key] * annz, X, Y, lane);  // Eq. 5 on the axis
-                __syncwarp();
-                rot_step<false>(rl.z, rl.lz, T + 2 * ROT_TSZ, Y, X, lane);  // back, about z
-                __syncwarp();
-                rot_step<true>(rl.x, rl.lx, T + 3 * ROT_TSZ, X, S, lane);  // back, about x, into the sums
+                rot_pair(Ttab + (size_t)key * 4 * ROT_TSZ, aval + (size_t)krho[key] * annz, rl,
+                         M + (size_t)octmajor_index(l, sx, sy, sz) * NCP, X, Y, S, lane);
             }
     __syncwarp();
+    for (int k = lane; k < NC; k += 32) L[(size_t)t * NCP + k] = S[k] * inv_h;
+}
+
+// the same for the targets tg[g0 .. g1) of one (level, octant) group of an adaptive tree (V-list
+// sources through the parent's colleagues, as in k_m2l_a); one warp per target
+__global__ void __launch_bounds__(256, 2) k_m2l_rot_a(const double* __restrict__ Ttab, const int* __restrict__ krho,
+                                                      RotLists rl, const double* __restrict__ aval, int annz,
+                                                      AdaptiveView av, const int* __restrict__ tg,
+                                                      const int* __restrict__ grp_ptr, int grp0,
+                                                      const double* __restrict__ M, double* __restrict__ L) {
+    __shared__ double sbuf[8][3][NCP + 1];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int oct = blockIdx.y;
+    const int g0 = grp_ptr[grp0 + oct], g1 = grp_ptr[grp0 + oct + 1];
+    const int ti = g0 + blockIdx.x * 8 + w;
+    if (ti >= g1) return;
+    const int t = tg[ti], P = av.parent[t];
+    const int ox = oct & 1, oy = (oct >> 1) & 1, oz = (oct >> 2) & 1;
+    double* X = sbuf[w][0];
+    double* Y = sbuf[w][1];
+    double* S = sbuf[w][2];
+    for (int k = lane; k <= NCP; k += 32) {
+        X[k] = 0.0;
+        Y[k] = 0.0;
+        S[k] = 0.0;
+    }
+    for (int vx = -3 + ox; vx <= 2 + ox; ++vx)
+        for (int vy = -3 + oy; vy <= 2 + oy; ++vy)
+            for (int vz = -3 + oz; vz <= 2 + oz; ++vz) {
+                if (abs(vx) <= 1 && abs(vy) <= 1 && abs(vz) <= 1) continue;
+                const int dx = ox - vx, dy = oy - vy, dz = oz - vz;  // = 2a + sc
+                const int scx = dx & 1, scy = dy & 1, scz = dz & 1;
+                const int ax = (dx - scx) >> 1, ay = (dy - scy) >> 1, az = (dz - scz) >> 1;
+                const int Q = av.colleague[27 * P + (ax + 1) * 9 + (ay + 1) * 3 + (az + 1)];
+                if (Q < 0) continue;
+                const int sb = av.child[8 * Q + (scx | (scy << 1) | (scz << 2))];
+                if (sb < 0) continue;
+                const int key = (vx + 3) * 49 + (vy + 3) * 7 + (vz + 3);
+                rot_pair(Ttab + (size_t)key * 4 * ROT_TSZ, aval + (size_t)krho[key] * annz, rl, M + (size_t)sb * NCP,
+                         X, Y, S, lane);
+            }
+    __syncwarp();
+    const double inv_h = 1.0 / av.geom[t].w;  // the target box's width (each tree has its own)
     for (int k = lane; k < NC; k += 32) L[(size_t)t * NCP + k] = S[k] * inv_h;
 }
 
@@ -1397,6 +1446,12 @@ static cudaError_t m2l_a_launch(const OrderData& od, const AdaptiveView& av, int
                                 const int* grp_ptr, int grp0, int max_group, const double* M, const float* Mf,
                                 double* L, cudaStream_t s) {
     if (max_group == 0) return cudaSuccess;
+    if (prec & kM2LRot) {  // FP64 by rotation (Sec. 3.4)
+        const RotLists rl{od.rot_lx, od.rot_lz, od.rot_la, od.rot_len[0], od.rot_len[1], od.rot_len[2]};
+        k_m2l_rot_a<<<dim3((max_group + 7) / 8, 8), 256, 0, s>>>(od.rot_T, od.rot_rho, rl, od.ax_val, od.ax_nnz, av,
+                                                                 tg, grp_ptr, grp0, M, L);
+        return cudaGetLastError();
+    }
     dim3 grd((max_group + 31) / 32, 8);
     cudaError_t e;
     if (prec == DAFMM_FP64) {

@@ -116,6 +116,8 @@ inline void shift_rp8(const HostShiftTable& t, int nc, int* out) {
 // or-ed into the precision argument of p2m and m2m_level (FP32 mode only): the multipole
 // rows are FP32 (ncp floats per box, in the FP64 arrays' memory) instead of FP64
 constexpr int kRowsF32 = 0x100;
+// or-ed into the precision argument of m2l_a (FP64 only): the M2L by rotation (Sec. 3.4)
+constexpr int kM2LRot = 0x200;
 
 struct OrderOps {
     int p, nc, ncp;

@@ -78,3 +78,45 @@ def test_rotated_m2l_matches_oracle_rotation_and_dense_gpu(ctx):
 def test_rotation_option_values(ctx):
     with pytest.raises(Exception):
         B.dafmm_set_option(ctx.h, B.DAFMM_OPT_M2L_ROTATION, 2)
+
+
+def test_rotated_m2l_adaptive_forest(ctx):
+    """Adaptive trees: the V-list pairs of a level have the same integer box displacements, so
+    the rotation tables serve them too; a two-member forest of clustered points."""
+    rng = np.random.default_rng(11)
+    parts = []
+    for m in range(2):
+        c = rng.random((4, 3))
+        x = c[rng.integers(0, 4, 5000)] + 0.05 * rng.normal(size=(5000, 3))
+        parts.append(x)
+    q = [rng.uniform(-1, 1, len(x)) for x in parts]
+    xyz = np.concatenate(parts)
+    qq = np.concatenate(q)
+    offs = np.array([0, len(parts[0]), len(xyz)], dtype=np.int64)
+    p = 6
+
+    def run_forest(c):
+        tree = c.build_forest(torch.from_numpy(xyz).cuda(), torch.from_numpy(qq).cuda(), offs, max_leaf=32)
+        phi = torch.empty(len(qq), dtype=torch.float64, device="cuda")
+        E = torch.empty((len(qq), 3), dtype=torch.float64, device="cuda")
+        tree.eval(p, phi, E, precision="fp64")
+        B.dafmm_sync(c.h)
+        _, doms = tree.forest()
+        tree.free()
+        return phi.cpu().numpy(), E.cpu().numpy(), doms
+
+    phi, E, doms = run_forest(ctx)
+    plain = B.Context(0)
+    B.dafmm_set_option(plain.h, B.DAFMM_OPT_M2L_ROTATION, 0)
+    try:
+        d_phi, d_E, _ = run_forest(plain)
+    finally:
+        plain.close()
+    assert rel(phi, d_phi) <= 1e-13
+    assert rel(E, d_E) <= 1e-12
+    # each member against the oracle's adaptive FMM on the member's own root cube
+    for m in range(2):
+        a, b = offs[m], offs[m + 1]
+        ref_phi, ref_E = O.fmm(xyz[a:b], qq[a:b], doms[m], p, max_leaf=32)
+        assert rel(phi[a:b], ref_phi) <= 1e-12, (m, rel(phi[a:b], ref_phi))
+        assert rel(E[a:b], ref_E) <= 1e-11

@@ -246,13 +246,15 @@ cudaError_t launch_children_init(int* child, int b0, int b1, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-// exclusive scan of n ints by one block (n up to a few million; used at build time only)
-__global__ void __launch_bounds__(1024) k_scan_excl(const int* in, int* out, int n) {
+// exclusive scan of n ints by one block (n up to a few million; used at build time only); in
+// and out are distinct, so the loads of a chunk need not wait for its stores
+__global__ void __launch_bounds__(1024) k_scan_excl(const int* __restrict__ in, int* __restrict__ out, int n) {
     __shared__ int sums[1024];
     const int t = threadIdx.x;
     const int chunk = (n + 1023) / 1024;
     const int b = t * chunk, e = min(b + chunk, n);
     int s = 0;
+#pragma unroll 8
     for (int i = b; i < e; ++i) s += in[i];
     sums[t] = s;
     __syncthreads();
@@ -263,6 +265,7 @@ __global__ void __launch_bounds__(1024) k_scan_excl(const int* in, int* out, int
         __syncthreads();
     }
     int run = t ? sums[t - 1] : 0;
+#pragma unroll 8
     for (int i = b; i < e; ++i) {
         const int v = in[i];
         out[i] = run;

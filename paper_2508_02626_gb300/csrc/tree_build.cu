@@ -105,15 +105,23 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_hist(const uint64_t* __restri
     hist[threadIdx.x * nb + blockIdx.x] = h[threadIdx.x];
 }
 
-// exclusive scan of `total` counters by one block of 1024 threads
-__global__ void __launch_bounds__(1024) k_rs_scan(unsigned* hist, int total) {
+// exclusive scan of `total` counters by one block of 1024 threads.  Each thread owns a chunk of
+// a multiple of 4 counters (16-byte aligned: hist is) and reads it with 16-byte loads, eight in
+// flight, so each pass over the counters costs a few memory round trips rather than one per
+// counter.
+__global__ void __launch_bounds__(1024) k_rs_scan(unsigned* __restrict__ hist, int total) {
     __shared__ unsigned sums[1024];
     const int t = threadIdx.x;
-    const int chunk = (total + 1023) / 1024;
-    const int b = t * chunk;
-    const int e = min(b + chunk, total);
+    const int chunk = ((total + 1023) / 1024 + 3) & ~3;
+    const int b = min(t * chunk, total), e = min(b + chunk, total);
+    const int ev = b + (e - b) / 4 * 4;  // end of the whole 4-counter groups
     unsigned s = 0;
-    for (int i = b; i < e; ++i) s += hist[i];
+#pragma unroll 8
+    for (int i = b; i < ev; i += 4) {
+        const uint4 v = *reinterpret_cast<const uint4*>(hist + i);
+        s += v.x + v.y + v.z + v.w;
+    }
+    for (int i = ev; i < e; ++i) s += hist[i];
     sums[t] = s;
     __syncthreads();
     for (int off = 1; off < 1024; off <<= 1) {
@@ -123,8 +131,22 @@ __global__ void __launch_bounds__(1024) k_rs_scan(unsigned* hist, int total) {
         __syncthreads();
     }
     unsigned run = t ? sums[t - 1] : 0u;
-    for (int i = b; i < e; ++i) {
-        unsigned v = hist[i];
+    // in place: a batch of 8 groups is read before any of it is written
+    for (int i0 = b; i0 < ev; i0 += 32) {
+        uint4 v[8];
+#pragma unroll
+        for (int g = 0; g < 8; ++g)
+            if (i0 + 4 * g < ev) v[g] = *reinterpret_cast<const uint4*>(hist + i0 + 4 * g);
+#pragma unroll
+        for (int g = 0; g < 8; ++g)
+            if (i0 + 4 * g < ev) {
+                const uint4 o = make_uint4(run, run + v[g].x, run + v[g].x + v[g].y, run + v[g].x + v[g].y + v[g].z);
+                run += v[g].x + v[g].y + v[g].z + v[g].w;
+                *reinterpret_cast<uint4*>(hist + i0 + 4 * g) = o;
+            }
+    }
+    for (int i = ev; i < e; ++i) {
+        const unsigned v = hist[i];
         hist[i] = run;
         run += v;
     }

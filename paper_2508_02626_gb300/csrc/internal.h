@@ -133,7 +133,8 @@ struct OrderOps {
     cudaError_t (*leaf)(const TreeView&, int prec, const double* Lleaf, double* phi, double* field,
                         cudaStream_t);
     cudaError_t (*kgen)(OrderData&, const short* key_list, int nkeys, cudaStream_t);  // null list: all keys
-    // M2L by rotation (FP64, uniform trees) and its tables
+    // M2L by rotation (FP64) of a uniform tree's level, and its tables (adaptive trees: m2l_a
+    // with kM2LRot)
     cudaError_t (*m2l_rot)(const OrderData&, int level, const double* M, double* L, double inv_h, cudaStream_t);
     cudaError_t (*rot_setup)(OrderData&, const double* r0s, int nrho, double* Kscratch, cudaStream_t);
     int rot_tsz;  // doubles per substitution table (sum over m <= p of (m+1)^2)

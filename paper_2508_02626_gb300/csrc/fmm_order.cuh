@@ -681,27 +681,12 @@ __device__ __forceinline__ void two_sum_add(float& hi, float& lo, float v) {
     hi = s;
 }
 
-// the records [r0, r0 + n) of one group (r0 even, an odd n followed by a zero record) acting on
-// the target (tx, ty, tz) in their frame, added to the compensated (hi, lo) sums: FP32 partial
-// sums over at most 64 sources, each folded into the (hi, lo) accumulators so that long
-// leaves keep FP32-level error
+// compensated (hi, lo) sums of the near field: FP32 partial sums over at most 64 sources are
+// folded into them, so that long neighbour lists keep FP32-level error
 struct CompSums {
     float ph = 0.f, pl = 0.f, xh = 0.f, xl = 0.f, yh = 0.f, yl = 0.f, zh = 0.f, zl = 0.f;
 };
 
-__device__ __forceinline__ void p2p_group(const float4* __restrict__ xq, int r0, int n, float tx, float ty, float tz,
-                                          CompSums& cs) {
-    const float2 tx2 = make_float2(tx, tx), ty2 = make_float2(ty, ty), tz2 = make_float2(tz, tz);
-    const int p0 = r0 >> 1, pe = p0 + ((n + 1) >> 1);
-    for (int pb = p0; pb < pe; pb += 32) {
-        float2 P = make_float2(0.f, 0.f), X = P, Y = P, Z = P;
-        p2p_pairs(xq, pb, min(pe, pb + 32), tx2, ty2, tz2, P, X, Y, Z);
-        two_sum_add(cs.ph, cs.pl, P.x + P.y);
-        two_sum_add(cs.xh, cs.xl, X.x + X.y);
-        two_sum_add(cs.yh, cs.yl, Y.x + Y.y);
-        two_sum_add(cs.zh, cs.zl, Z.x + Z.y);
-    }
-}
 
 // records per shared-memory segment of the neighbour list (per warp; 8 KB)
 constexpr int kLeafSeg = 512;
@@ -1115,6 +1100,7 @@ __global__ void __launch_bounds__(256) k_leaf_a(AdaptiveView av, const int* __re
                                                 const double* __restrict__ L, const double* __restrict__ M,
                                                 double* __restrict__ phi, double* __restrict__ field) {
     __shared__ float s_rows[8][2][NCP];  // per warp: the W box's multipoles and the leaf's locals, FP32
+    extern __shared__ __align__(16) float4 s_list_a[];  // FP32: per warp kLeafSeg records
     const int lane = threadIdx.x;
     const int li = blockIdx.x * blockDim.y + threadIdx.y;
     if (li >= nleaves) return;
@@ -1132,9 +1118,14 @@ __global__ void __launch_bounds__(256) k_leaf_a(AdaptiveView av, const int* __re
     const int u0 = av.u_ptr[b], u1 = av.u_ptr[b + 1];
     const int w0 = av.w_ptr[b], w1 = av.w_ptr[b + 1];
     for (int base = i0; base < i1; base += 32) {
-        const int t = base + lane;
-        const bool valid = t < i1;
-        const int tt = valid ? t : i0;
+        // FP32: a pass of at most 16 targets splits the sources between the two half-warps,
+        // lane l and lane l + 16 taking the same target
+        const int m = min(32, i1 - base);
+        const bool split = sizeof(T) == 4 && m <= 16;
+        const int tl = split ? (lane & 15) : lane;
+        const int t = base + tl;
+        const bool valid = tl < m && (!split || lane < 16);  // the lanes that write
+        const int tt = tl < m ? t : i0;
         double fphi = 0.0, fx = 0.0, fy = 0.0, fz = 0.0;
         if constexpr (sizeof(T) == 8) {
             const double xt = av.x[tt], yt = av.y[tt], zt = av.z[tt];
@@ -1154,33 +1145,71 @@ __global__ void __launch_bounds__(256) k_leaf_a(AdaptiveView av, const int* __re
             }
         } else {
             const float4 pt = xq_load(av.xq, av.xq0[b] + (tt - i0));
-            CompSums acc;  // in target-leaf units
+            CompSums acc;  // in leaf widths of this leaf
+            // The U-list leaves' records are copied into one shared-memory list in this leaf's
+            // frame (source x h_s / h + centre offset / h; h_s / h is a power of two), in
+            // segments of up to kLeafSeg records; the pairwise sum runs over each segment.
+            float4* buf = s_list_a + (size_t)threadIdx.y * kLeafSeg;
+            const int g = split ? lane >> 4 : 0;
+            const float2 tx2 = make_float2(pt.x, pt.x), ty2 = make_float2(pt.y, pt.y),
+                         tz2 = make_float2(pt.z, pt.z);
+            int fill = 0;
+            auto flush = [&]() {
+                if ((fill & 1) && lane == 0) {  // a zero record completes the last pair
+                    float* f = reinterpret_cast<float*>(buf) + 8 * (fill >> 1) + 1;
+                    f[0] = f[2] = f[4] = f[6] = 0.f;
+                }
+                __syncwarp();
+                const int np = (fill + 1) >> 1, hp = split ? (np + 1) >> 1 : np;
+                const int pa = g ? hp : 0, pe = g ? np : hp;
+                for (int pb = pa; pb < pe; pb += 32) {
+                    float2 P = make_float2(0.f, 0.f), X = P, Y = P, Z = P;
+                    p2p_pairs(buf, pb, min(pe, pb + 32), tx2, ty2, tz2, P, X, Y, Z);
+                    two_sum_add(acc.ph, acc.pl, P.x + P.y);
+                    two_sum_add(acc.xh, acc.xl, X.x + X.y);
+                    two_sum_add(acc.yh, acc.yl, Y.x + Y.y);
+                    two_sum_add(acc.zh, acc.zl, Z.x + Z.y);
+                }
+                __syncwarp();  // the segment is no longer read
+                fill = 0;
+            };
             for (int ui = u0; ui < u1; ++ui) {
                 const int sb = av.u_idx[ui];
                 double scx, scy, scz, sh;
                 abox_geom(av, sb, scx, scy, scz, sh);
-                // the target in the source leaf's frame: (x_t - off) / r with r = h_s / h a power
-                // of two; a distance in that frame is 1/r of the same distance in this leaf's, so
-                // the potential scales back by 1/r and the field by 1/r^2 (exact)
-                const float ir = (float)(h / sh);
-                const float tx = (pt.x - (float)((scx - cx) * ih)) * ir, ty = (pt.y - (float)((scy - cy) * ih)) * ir,
-                            tz = (pt.z - (float)((scz - cz) * ih)) * ir;
-                const int r0 = av.xq0[sb], ns = av.pend[sb] - av.pbeg[sb];
-                if (sh == h) {
-                    p2p_group(av.xq, r0, ns, tx, ty, tz, acc);
-                    continue;
+                const float r = (float)(sh * ih);
+                const float offx = (float)((scx - cx) * ih), offy = (float)((scy - cy) * ih),
+                            offz = (float)((scz - cz) * ih);
+                const int r0 = av.xq0[sb], n = av.pend[sb] - av.pbeg[sb];
+                for (int i0s = 0; i0s < n;) {
+                    const int take = min(n - i0s, kLeafSeg - fill);
+                    for (int i = lane; i < take; i += 32) {
+                        const float4 rec = xq_load(av.xq, r0 + i0s + i);
+                        const int j = fill + i;
+                        float* f = reinterpret_cast<float*>(buf) + 8 * (j >> 1) + (j & 1);
+                        f[0] = fmaf(r, rec.x, offx);
+                        f[2] = fmaf(r, rec.y, offy);
+                        f[4] = fmaf(r, rec.z, offz);
+                        f[6] = rec.w;
+                    }
+                    fill += take;
+                    i0s += take;
+                    if (fill == kLeafSeg) flush();
                 }
-                CompSums cs;
-                p2p_group(av.xq, r0, ns, tx, ty, tz, cs);
-                const float ir2 = ir * ir;
-                two_sum_add(acc.ph, acc.pl, cs.ph * ir);
-                two_sum_add(acc.ph, acc.pl, cs.pl * ir);
-                two_sum_add(acc.xh, acc.xl, cs.xh * ir2);
-                two_sum_add(acc.xh, acc.xl, cs.xl * ir2);
-                two_sum_add(acc.yh, acc.yl, cs.yh * ir2);
-                two_sum_add(acc.yh, acc.yl, cs.yl * ir2);
-                two_sum_add(acc.zh, acc.zl, cs.zh * ir2);
-                two_sum_add(acc.zh, acc.zl, cs.zl * ir2);
+            }
+            if (fill > 0) flush();
+            if (split) {  // the upper half-warp's sums join the lower one's
+                float v[8] = {acc.ph, acc.pl, acc.xh, acc.xl, acc.yh, acc.yl, acc.zh, acc.zl};
+#pragma unroll
+                for (int j = 0; j < 8; ++j) v[j] = __shfl_down_sync(0xffffffffu, v[j], 16);
+                two_sum_add(acc.ph, acc.pl, v[0]);
+                acc.pl += v[1];
+                two_sum_add(acc.xh, acc.xl, v[2]);
+                acc.xl += v[3];
+                two_sum_add(acc.yh, acc.yl, v[4]);
+                acc.yl += v[5];
+                two_sum_add(acc.zh, acc.zl, v[6]);
+                acc.zl += v[7];
             }
             fphi = ((double)acc.ph + (double)acc.pl) * ih;
             fx = ((double)acc.xh + (double)acc.xl) * ih * ih;
@@ -1507,8 +1536,14 @@ static cudaError_t leaf_a_launch(const AdaptiveView& av, const int* leaves, int 
     if (nleaves == 0) return cudaSuccess;
     warps = warps < 1 ? 1 : (warps > 8 ? 8 : warps);
     dim3 blk(32, warps), grd((nleaves + warps - 1) / warps);
-    if (prec == DAFMM_FP64) k_leaf_a<double><<<grd, blk, 0, s>>>(av, leaves, nleaves, L, M, phi, field);
-    else k_leaf_a<float><<<grd, blk, 0, s>>>(av, leaves, nleaves, L, M, phi, field);
+    if (prec == DAFMM_FP64) {
+        k_leaf_a<double><<<grd, blk, 0, s>>>(av, leaves, nleaves, L, M, phi, field);
+    } else {
+        const size_t smem = (size_t)warps * kLeafSeg * sizeof(float4);
+        cudaError_t e = cudaFuncSetAttribute(k_leaf_a<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k_leaf_a<float><<<grd, blk, smem, s>>>(av, leaves, nleaves, L, M, phi, field);
+    }
     return cudaGetLastError();
 }
 

@@ -14,6 +14,7 @@
 
 #include "da_common.cuh"
 #include "internal.h"
+#include "rot_lists.h"
 #include "tc_ops.h"
 #include "tree_common.cuh"
 
@@ -438,22 +439,10 @@ int ensure_rotation(dafmm_ctx* c, int p, cudaStream_t s) {
     if (od.rot_T) return DAFMM_OK;
     const OrderOps* ops = order_ops(p);
     const int nc = ncoef_of(p), ncp = ncp_of(p);
-    // exponents in the coefficient layout (degree graded, x exponent descending, then y)
-    std::vector<int> ey, ez;
-    for (int n = 0; n <= p; ++n)
-        for (int a = n; a >= 0; --a)
-            for (int b = n - a; b >= 0; --b) {
-                ey.push_back(b);
-                ez.push_back(n - a - b);
-            }
-    std::vector<int> rowptr(1, 0);
-    std::vector<unsigned short> col;
-    for (int b = 0; b < nc; ++b) {
-        for (int a = 0; a < nc; ++a)
-            if (ey[b] >= ey[a] && ez[b] >= ez[a] && (ey[b] - ey[a]) % 2 == 0 && (ez[b] - ez[a]) % 2 == 0)
-                col.push_back((unsigned short)a);
-        rowptr.push_back((int)col.size());
-    }
+    // the axial matrices' structure and the kernel's task lists (rot_lists.h)
+    const RotStructure rs = rot_structure(p);
+    const std::vector<int>& rowptr = rs.rowptr;
+    const std::vector<unsigned short>& col = rs.col;
     const int nnz = (int)col.size();
     std::vector<int> rho_of(kNumKeys, 0), len2;
     for (int key = 0; key < kNumKeys; ++key) {
@@ -465,52 +454,11 @@ int ensure_rotation(dafmm_ctx* c, int p, cudaStream_t s) {
         if (it == len2.end()) len2.push_back(r2);
     }
     const int nrho = (int)len2.size();
-    // the kernel's task lists: per step the outputs' multiply-adds (table offset, input index),
-    // outputs dealt to the 32 lanes largest first onto the least loaded lane, each lane's tasks
-    // padded to the longest lane with tasks that read the zero at index nc
-    std::vector<int> ex;
-    for (int n = 0; n <= p; ++n)
-        for (int a = n; a >= 0; --a)
-            for (int b = n - a; b >= 0; --b) ex.push_back(a);
-    auto deg_start = [](int n) { return n * (n + 1) * (n + 2) / 6; };
-    auto cidx = [&](int n, int a, int c) { return deg_start(n) + (n - a) * (n - a + 1) / 2 + c; };
-    auto roff = [](int m) { return m * (m + 1) * (2 * m + 1) / 6; };
-    struct Task { unsigned off, in; };
-    auto build = [&](const std::vector<std::vector<Task>>& per_out, std::vector<uint2>& list) {
-        std::vector<int> order(nc);
-        for (int k = 0; k < nc; ++k) order[k] = k;
-        std::stable_sort(order.begin(), order.end(),
-                         [&](int u, int v) { return per_out[u].size() > per_out[v].size(); });
-        std::vector<std::vector<uint2>> lane(32);
-        for (int k : order) {
-            int best = 0;
-            for (int q = 1; q < 32; ++q)
-                if (lane[q].size() < lane[best].size()) best = q;
-            for (size_t j = 0; j < per_out[k].size(); ++j) {
-                const bool last = j + 1 == per_out[k].size();
-                lane[best].push_back(make_uint2(per_out[k][j].off | (last ? 0x80000000u : 0u),
-                                                per_out[k][j].in | ((unsigned)k << 16)));
-            }
-        }
-        size_t len = 0;
-        for (auto& v : lane) len = std::max(len, v.size());
-        list.assign(len * 32, make_uint2(0u, (unsigned)nc));
-        for (int q = 0; q < 32; ++q)
-            for (size_t t = 0; t < lane[q].size(); ++t) list[t * 32 + q] = lane[q][t];
-        return (int)len;
-    };
-    std::vector<std::vector<Task>> tx(nc), tz(nc), ta(nc);
-    for (int k = 0; k < nc; ++k) {
-        const int a = ex[k], b = ey[k], cz = ez[k], n = a + b + cz;
-        const int mx = b + cz, mz = a + b;
-        for (int j = 0; j <= mx; ++j)
-            tx[k].push_back({(unsigned)(roff(mx) + cz * (mx + 1) + j), (unsigned)(cidx(n, a, 0) + j)});
-        for (int j = 0; j <= mz; ++j)
-            tz[k].push_back({(unsigned)(roff(mz) + b * (mz + 1) + j), (unsigned)cidx(n, mz - j, cz)});
-        for (int e = rowptr[k]; e < rowptr[k + 1]; ++e) ta[k].push_back({(unsigned)e, (unsigned)col[e]});
-    }
-    std::vector<uint2> lx, lz, la;
-    const int len_x = build(tx, lx), len_z = build(tz, lz), len_a = build(ta, la);
+    static_assert(sizeof(RotTask) == sizeof(uint2), "task layout");
+    const std::vector<RotTask>& lx = rs.lx;
+    const std::vector<RotTask>& lz = rs.lz;
+    const std::vector<RotTask>& la = rs.la;
+    const int len_x = rs.len[0], len_z = rs.len[1], len_a = rs.len[2];
     std::vector<double> r0s(3 * (size_t)nrho, 0.0);
     for (int r = 0; r < nrho; ++r) r0s[3 * r] = std::sqrt((double)len2[r]);
     const size_t tbytes = (size_t)kNumKeys * 4 * ops->rot_tsz * sizeof(double);

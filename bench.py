@@ -313,6 +313,13 @@ def run_ours(args, rank, world):
         "modes": modes,
     }
     phi_host, E_host = phi.cpu().numpy(), E.cpu().numpy()
+    # the method's own error against the direct sum as a function of the order (FP64 path, the
+    # same tree): which order, if any, reaches the metric's 1e-7 on this workload
+    phi_by_order = {}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        for po in range(2, 11):
+            tree.eval(po, phi, None, precision="fp64")
+            phi_by_order[po] = phi.cpu().numpy().copy()
     tree.free()
     if world == 1 and not args.no_workloads:
         sections = set(args.sections.split(","))
@@ -327,7 +334,7 @@ def run_ours(args, rank, world):
         if "leafsize" in sections:
             out["leaf_size"] = bench_leaf_size(ctx)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        out["cpu_baseline"], out["accuracy"] = cpu_baseline(x, q, dom, cfg, phi_host, E_host)
+        out["cpu_baseline"], out["accuracy"] = cpu_baseline(x, q, dom, cfg, phi_host, E_host, phi_by_order)
     ctx.close()
     return out
 
@@ -658,7 +665,7 @@ def bench_leaf_size(ctx):
             "times_ms": table, "fastest": best, "loglog_slope_of_fastest": slopes}
 
 
-def cpu_baseline(x, q, dom, cfg, phi_gpu, E_gpu):
+def cpu_baseline(x, q, dom, cfg, phi_gpu, E_gpu, phi_by_order=None):
     """The oracle FMM (plain C, all host cores) on the same tree and order, for the particles
     of a sample of target leaves; the full-solve rate is extrapolated from the cost of the
     upward pass (all particles) and the per-leaf cost of the sampled leaves.  The sampled
@@ -696,6 +703,11 @@ def cpu_baseline(x, q, dom, cfg, phi_gpu, E_gpu):
            "rel_l2_phi_vs_direct": rel(phi_gpu[tg[:300]], d_phi),
            "oracle_rel_l2_phi_vs_direct": rel(ref_phi[:300], d_phi),
            "rel_l2_field_vs_direct": rel(E_gpu[tg[:300]], d_E)}
+    if phi_by_order:
+        by = {"p%d" % po: rel(ph[tg[:300]], d_phi) for po, ph in sorted(phi_by_order.items())}
+        reach = [po for po, ph in sorted(phi_by_order.items()) if rel(ph[tg[:300]], d_phi) <= 1e-7]
+        acc["fp64_rel_l2_phi_vs_direct_by_order"] = by
+        acc["smallest_order_reaching_1e-7"] = reach[0] if reach else None
     return cpu, acc
 
 

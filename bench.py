@@ -59,20 +59,102 @@ def fp32_fma_peak_tflops(sm_mhz):
     return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
 
 
+# clock-event reason bits of NVML (nvml.h) and the names the clock record uses for them
+NVML_REASONS = ((0x8, "hw_slowdown"), (0x40, "hw_thermal_slowdown"), (0x20, "sw_thermal_slowdown"),
+                (0x4, "sw_power_cap"))
+SMI_REASONS = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+
+
+def summarise_clocks(nvml_samples, smi_lines):
+    """One clock record from both samplers.  nvml_samples: (sm MHz, max sm MHz, reason bits or
+    None); smi_lines: nvidia-smi CSV rows of ClockSampler.FIELDS.  The median SM clock and the
+    sample count come from NVML when it gave samples (denser), else from nvidia-smi; the
+    reasons are those either source saw active."""
+    sm_n, smax_n, reasons = [], [], set()
+    for clk, mx, bits in nvml_samples:
+        sm_n.append(float(clk))
+        smax_n.append(float(mx))
+        if bits is not None:
+            reasons.update(nm for bit, nm in NVML_REASONS if bits & bit)
+    sm_s, smax_s = [], []
+    for ln in smi_lines:
+        parts = [p.strip() for p in ln.split(",")]
+        if len(parts) < 8:
+            continue
+        try:
+            sm_s.append(float(parts[0]))
+            smax_s.append(float(parts[1]))
+        except ValueError:
+            continue
+        reasons.update(nm for nm, v in zip(SMI_REASONS, parts[4:8]) if v.lower().startswith("active"))
+    sm, smax, src = (sm_n, smax_n, "nvml") if sm_n else (sm_s, smax_s, "nvidia-smi")
+    return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+            "reasons": sorted(reasons), "samples": len(sm), "source": src if sm else None,
+            "nvidia_smi_samples": len(sm_s)}
+
+
 class ClockSampler:
-    """nvidia-smi clock/throttle samples while the timed region runs."""
+    """SM clock and clock-event reasons while the timed region runs: NVML queried every 5 ms
+    from a thread (read-only calls into libnvidia-ml), and nvidia-smi every 200 ms beside it."""
 
     FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_index):
+    def __init__(self, gpu_index, uuid=None):
         self.gpu = gpu_index
+        self.uuid = uuid
         self.proc = None
         self.lines = []
         self.thread = None
+        self.nvml = None
+        self.samples = []
+        self.done = threading.Event()
+        self.poller = None
+
+    def _nvml_open(self):
+        import ctypes
+        try:
+            lib = ctypes.CDLL("libnvidia-ml.so.1")
+            if lib.nvmlInit_v2() != 0:
+                return None
+            h = ctypes.c_void_p()
+            ok = False
+            if self.uuid:
+                u = self.uuid if self.uuid.startswith("GPU-") else "GPU-" + self.uuid
+                ok = lib.nvmlDeviceGetHandleByUUID(u.encode(), ctypes.byref(h)) == 0
+            if not ok:
+                ok = lib.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(self.gpu), ctypes.byref(h)) == 0
+            if not ok:
+                lib.nvmlShutdown()
+                return None
+            reasons = getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+                lib.nvmlDeviceGetCurrentClocksThrottleReasons
+            return lib, h, reasons
+        except Exception:
+            return None
+
+    def _nvml_sample(self):
+        import ctypes
+        lib, h, reasons = self.nvml
+        clk, mx, bits = ctypes.c_uint(), ctypes.c_uint(), ctypes.c_ulonglong()
+        if lib.nvmlDeviceGetClockInfo(h, 1, ctypes.byref(clk)) != 0:  # 1 = NVML_CLOCK_SM
+            return
+        if lib.nvmlDeviceGetMaxClockInfo(h, 1, ctypes.byref(mx)) != 0:
+            return
+        ok = reasons(h, ctypes.byref(bits)) == 0
+        self.samples.append((clk.value, mx.value, bits.value if ok else None))
+
+    def _poll(self):
+        while not self.done.wait(0.005):
+            self._nvml_sample()
 
     def start(self):
+        self.nvml = self._nvml_open()
+        if self.nvml is not None:
+            self._nvml_sample()
+            self.poller = threading.Thread(target=self._poll, daemon=True)
+            self.poller.start()
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
@@ -88,29 +170,22 @@ class ClockSampler:
             self.lines.append(line.strip())
 
     def stop(self):
-        if self.proc is None:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
-        self.proc.terminate()
-        try:
-            self.proc.wait(timeout=5)
-        except Exception:
-            self.proc.kill()
-        sm, smax, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
-            parts = [p.strip() for p in ln.split(",")]
-            if len(parts) < 8:
-                continue
+        if self.nvml is not None:
+            self._nvml_sample()
+            self.done.set()
+            self.poller.join(timeout=5)
+            self.nvml[0].nvmlShutdown()
+        if self.proc is not None:
+            self.proc.terminate()
             try:
-                sm.append(float(parts[0]))
-                smax.append(float(parts[1]))
-            except ValueError:
-                continue
-            for nm, v in zip(names, parts[4:8]):
-                if v.lower().startswith("active"):
-                    reasons.add(nm)
-        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.thread.join(timeout=5)
+        if self.nvml is None and self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvml and nvidia-smi unavailable"],
+                    "samples": 0}
+        return summarise_clocks(list(self.samples), list(self.lines))
 
 
 def max_over_ranks(ms, world, device):
@@ -170,7 +245,11 @@ def run_ours(args, rank, world):
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
-    clocks = ClockSampler(local)
+    try:
+        uuid = str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        uuid = None
+    clocks = ClockSampler(local, uuid)
     clocks.start()
     times, phases = [], []
     with torch.cuda.stream(stream):

@@ -213,6 +213,14 @@ int64_t dafmm_debug_level(const dafmm_tree* tree, int which, int level, double* 
 /* Wait for `stream` and report failures recorded on the device by bounded waits inside the
  * kernels (DAFMM_ERR_TIMEOUT); clears the record. */
 int dafmm_sync(dafmm_ctx* ctx, void* stream);
+/* Self-test of that path (the paper has no counterpart): launch on `stream` one kernel whose
+ * bounded mbarrier wait -- the wait the tensor-core kernels use, at most 1 s of device time --
+ * waits for an arrival that never comes, gives up, records site code 90 in the context's
+ * failure record and returns.  The next dafmm_sync on the context then returns
+ * DAFMM_ERR_TIMEOUT (its message names the site) and clears the record; the context and its
+ * trees stay usable.  Returns DAFMM_OK once the kernel is launched, DAFMM_ERR_CUDA if the
+ * launch fails, DAFMM_ERR_INVALID_ARG for a NULL context. */
+int dafmm_debug_expire_wait(dafmm_ctx* ctx, void* stream);
 
 /* dafmm_eval without device allocation.  (The paper has no counterpart: this exists for
  * callers that cannot call cudaMalloc while they evaluate -- a service whose device memory

@@ -43,6 +43,7 @@ SIGNATURES = {
     "dafmm_set_profiling": (_i, [_vp, _i]),
     "dafmm_set_option": (_i, [_vp, _i, _i64]),
     "dafmm_sync": (_i, [_vp, _vp]),
+    "dafmm_debug_expire_wait": (_i, [_vp, _vp]),
     "dafmm_eval_noalloc": (_i, [_vp, _i, _vp, _vp, _vp]),
     "dafmm_debug_level": (_i64, [_vp, _i, _i, _vp, _i64]),
     "dafmm_last_phase_ms": (_i, [_vp, _vp]),
@@ -246,6 +247,10 @@ def dafmm_set_option(ctx, option, value):
 
 def dafmm_sync(ctx, stream=None):
     _check(ctx, load().dafmm_sync(ctx, _stream_ptr(stream)))
+
+
+def dafmm_debug_expire_wait(ctx, stream=None):
+    _check(ctx, load().dafmm_debug_expire_wait(ctx, _stream_ptr(stream)))
 
 
 def dafmm_eval_noalloc(ctx, tree, order, phi=None, field=None, stream=None):

@@ -27,7 +27,7 @@ struct dafmm_ctx {
     int tc_mask = 5;          // FP32 mode: bit 0 M2L, bit 1 M2M, bit 2 L2L on the tensor cores
     int leaf_warps = 4;       // adaptive leaf kernel: leaves (one warp each) per thread block
     int m2l_f16 = 1;          // FP32 mode: M2L on F16 split operands (else TF32)
-    int m2l_rot = -1;         // FP64 mode, uniform trees: M2L by rotation (Sec. 3.4); -1 = from p = 4
+    int m2l_rot = -1;         // FP64 mode: M2L by rotation (Sec. 3.4), uniform and adaptive; -1 = from p = 4
     int num_sms = 0;
     bool tc_capable = false;  // compute capability 10.x
     int* d_err = nullptr;     // device-side failure record of bounded waits

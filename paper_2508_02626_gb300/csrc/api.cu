@@ -1260,11 +1260,14 @@ int dafmm_build_tree(dafmm_ctx* c, const double* xyz, const double* q, int64_t n
         const std::vector<int> offs = {0, (int)n};
         Scratch d_offs(c);
         if (!(rc = d_offs.alloc(2 * sizeof(int), "offsets"))) {
-            CK(c, cudaMemcpyAsync(d_offs.p, offs.data(), 2 * sizeof(int), cudaMemcpyHostToDevice, s), "offsets");
-            rc = build_adaptive(c, t, dxyz, dq, offs, d_offs.as<int>(), max_leaf, kMaxAdaptiveDepth, s);
+            const cudaError_t e =
+                cudaMemcpyAsync(d_offs.p, offs.data(), 2 * sizeof(int), cudaMemcpyHostToDevice, s);
+            rc = e != cudaSuccess ? cuda_fail(c, e, "offsets")
+                                  : build_adaptive(c, t, dxyz, dq, offs, d_offs.as<int>(), max_leaf,
+                                                   kMaxAdaptiveDepth, s);
         }
         if (rc) {
-            dafmm_tree_free(t);
+            dafmm_tree_free(t);  // a failed build leaves nothing behind in the context
             return rc;
         }
         *out = t;

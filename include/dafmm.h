@@ -154,9 +154,12 @@ int dafmm_graph_free(dafmm_graph* graph);
  *   dafmm_server_wait: blocks up to timeout_s seconds (< 0: no limit) for the request;
  *     returns its status (DAFMM_OK, or the error of its job; DAFMM_ERR_OVER_BUDGET when it
  *     cannot fit the empty pool; DAFMM_ERR_CANCELLED when the server stopped first) and
- *     forgets it, or DAFMM_ERR_TIMEOUT and keeps it.  times3 (may be NULL) receives, in
- *     milliseconds: submit to results in the caller's buffers, submit to admission, and
- *     admission to results.
+ *     forgets it, or DAFMM_ERR_TIMEOUT and keeps it; DAFMM_ERR_INVALID_ARG for an id it does
+ *     not hold (never submitted, already waited for, or taken by another thread waiting for
+ *     the same id).  times3 (may be NULL) receives, in milliseconds: submit to results in the
+ *     caller's buffers, submit to admission, and admission to results.
+ *   dafmm_server_last_error: the server's last failure message, copied per calling thread
+ *     (valid until that thread calls it again).
  *   dafmm_server_stats: out8 = {completed, failed, queued, running jobs, jobs launched,
  *     mean requests per job, peak pool bytes in use, peak concurrent jobs}.
  *   dafmm_server_destroy: lets running jobs finish, cancels queued requests, frees all. */

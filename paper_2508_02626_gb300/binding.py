@@ -474,7 +474,10 @@ class Server:
         st, t = dafmm_server_wait(self.h, rid, timeout)
         if st == DAFMM_ERR_TIMEOUT:
             return st, None, None, None
-        _, _, phi, E = self._live.pop(rid)
+        live = self._live.pop(rid, None)
+        if live is None:  # an id this server object does not hold
+            return st, None, None, None
+        _, _, phi, E = live
         times = dict(latency_ms=t[0], queue_ms=t[1], device_ms=t[2])
         return st, phi.numpy(), (E.numpy() if E is not None else None), times
 

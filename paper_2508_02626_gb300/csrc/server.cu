@@ -339,12 +339,18 @@ int dafmm_server_submit(dafmm_server* S, const double* xyz, const double* q, int
 int dafmm_server_wait(dafmm_server* S, int64_t id, double timeout_s, double* times3) {
     if (!S) return DAFMM_ERR_INVALID_ARG;
     std::unique_lock<std::mutex> lk(S->m);
-    auto it = S->reqs.find(id);
-    if (it == S->reqs.end()) return DAFMM_ERR_INVALID_ARG;
-    SReq* r = it->second;
-    auto finished = [r] { return r->status <= 0; };
+    if (S->reqs.find(id) == S->reqs.end()) return DAFMM_ERR_INVALID_ARG;
+    // the request is looked up afresh on every wake-up: another thread waiting for the same id
+    // may have taken (and deleted) it meanwhile
+    auto finished = [S, id] {
+        auto f = S->reqs.find(id);
+        return f == S->reqs.end() || f->second->status <= 0;
+    };
     if (timeout_s < 0) S->cv_done.wait(lk, finished);
     else if (!S->cv_done.wait_for(lk, std::chrono::duration<double>(timeout_s), finished)) return DAFMM_ERR_TIMEOUT;
+    auto it = S->reqs.find(id);
+    if (it == S->reqs.end()) return DAFMM_ERR_INVALID_ARG;  // another waiter took it
+    SReq* r = it->second;
     if (times3) {
         times3[0] = (r->t_done - r->t_submit) * 1e3;  // latency
         times3[1] = (r->t_start - r->t_submit) * 1e3;  // waiting for admission
@@ -374,8 +380,11 @@ int dafmm_server_stats(dafmm_server* S, double* out8) {
 
 const char* dafmm_server_last_error(dafmm_server* S) {
     if (!S) return "no server";
+    // a copy per calling thread: the scheduler may replace the message at any time
+    thread_local std::string copy;
     std::lock_guard<std::mutex> lk(S->m);
-    return S->err.c_str();
+    copy = S->err;
+    return copy.c_str();
 }
 
 int dafmm_server_destroy(dafmm_server* S) {

@@ -89,3 +89,29 @@ def test_wait_timeout_and_errors():
     with pytest.raises(B.DafmmError):
         srv.submit(x, q, 11)
     srv.close()
+
+
+def test_two_waiters_and_consumed_ids():
+    """Two threads waiting for one request: one receives its status, the other
+    DAFMM_ERR_INVALID_ARG (the request is gone once taken); waiting again for a consumed id is
+    DAFMM_ERR_INVALID_ARG as well."""
+    import threading
+    srv = B.Server(0, pool_bytes=1 << 30, slots=1, max_batch=2)
+    x, q = W.uniform(200_000, seed=11)
+    rid = srv.submit(x, q, 8)
+    got = []
+
+    def waiter():
+        got.append(B.dafmm_server_wait(srv.h, rid, 120.0)[0])
+
+    ts = [threading.Thread(target=waiter) for _ in range(2)]
+    for t in ts:
+        t.start()
+    for t in ts:
+        t.join()
+    again = B.dafmm_server_wait(srv.h, rid, 0.0)[0]
+    srv._live.pop(rid)  # the raw waits above took the request: release its buffers here
+    st, phi, _, _ = srv.wait(rid, timeout=0.0)  # the wrapper reports an id it no longer holds
+    srv.close()
+    assert sorted(got) == sorted([B.DAFMM_OK, B.DAFMM_ERR_INVALID_ARG])
+    assert again == B.DAFMM_ERR_INVALID_ARG and st == B.DAFMM_ERR_INVALID_ARG and phi is None

@@ -22,6 +22,7 @@
 #pragma once
 #include <stddef.h>
 #include <stdint.h>
+#include <vector_functions.h>
 #include <vector_types.h>
 
 namespace dafmm {

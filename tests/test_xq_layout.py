@@ -3,7 +3,9 @@ every leaf starts on an even record, its records and the zero record that comple
 leaf stay inside xq_records(n, leaves) and never overlap another leaf's, no record pair spans
 two leaves (so a leaf's pairs do not depend on what precedes it in the sorted order), and
 records are stored as (x, x', y, y') (z, z', q, q') and read back unchanged.  A build with a
-planted mistake (leaves placed without the rounding to an even record) must fail."""
+planted mistake (leaves placed without the rounding to an even record) must fail.  The
+octant-major box index of the same header is a bijection inverted by its decoder, with the 8
+children of a parent at one offset of the 8 octant slabs."""
 import ctypes
 import os
 import subprocess
@@ -26,13 +28,24 @@ def _build(extra):
     h = ctypes.CDLL(so)
     h.xq_layout_check.argtypes = [ctypes.c_uint]
     h.xq_layout_check.restype = ctypes.c_int
+    h.octmajor_check.argtypes = [ctypes.c_int]
+    h.octmajor_check.restype = ctypes.c_int
     return h
 
 
-def test_record_layout():
-    lib = _build([])
+@pytest.fixture(scope="module")
+def lib():
+    return _build([])
+
+
+def test_record_layout(lib):
     for seed in (1, 2, 3):
         assert lib.xq_layout_check(seed) == 0
+
+
+@pytest.mark.parametrize("level", [0, 1, 2, 3, 5])
+def test_octant_major_index(lib, level):
+    assert lib.octmajor_check(level) == 0
 
 
 def test_planted_odd_base_fails():

@@ -74,3 +74,29 @@ extern "C" int xq_layout_check(unsigned seed) {
     }
     return 0;
 }
+
+// the octant-major box index of level l: a bijection of the 8^l boxes onto [0, 8^l), inverted
+// by octmajor_decode, with the 8 children of a parent at one offset of the 8 octant slabs
+// (child octant o of parent (I, J, K) at o * 8^(l-1) + the parent's index at level l - 1)
+extern "C" int octmajor_check(int l) {
+    const int s = 1 << l, nbox = s * s * s;
+    std::vector<int> seen(nbox, 0);
+    for (int k = 0; k < s; ++k)
+        for (int j = 0; j < s; ++j)
+            for (int i = 0; i < s; ++i) {
+                const int idx = octmajor_index(l, i, j, k);
+                if (idx < 0 || idx >= nbox || seen[idx]) return 1;
+                seen[idx] = 1;
+                int a, b, c;
+                octmajor_decode(l, idx, a, b, c);
+                if (a != i || b != j || c != k) return 2;
+                if (l >= 1) {
+                    const int P3 = nbox / 8;
+                    const int oct = (i & 1) | (j & 1) << 1 | (k & 1) << 2;
+                    // the parent's position in its own level, as a plain row-major grid of P^3
+                    const int P = s / 2, par = ((k >> 1) * P + (j >> 1)) * P + (i >> 1);
+                    if (idx != oct * P3 + par) return 3;
+                }
+            }
+    return 0;
+}

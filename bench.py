@@ -486,7 +486,7 @@ def bench_batch(ctx, stream, flush):
     x, q = np.concatenate(xs), np.concatenate(qs)
     n, p = int(offs[-1]), 6
     xt, qt = torch.from_numpy(x).cuda(), torch.from_numpy(q).cuda()
-    cache = A.Cache(os.path.join(ROOT, "gpurun_out", "autotune.json"))
+    cache = A.Cache(os.path.join(ROOT, "paper_2508_02626_gb300", "_build", "autotune.json"))  # git-ignored
     tuned = A.tune_forest(ctx, xt, qt, offs, p, "fp32", cache=cache, reps=1)
     s = tuned["max_leaf"]
     torch.cuda.synchronize()

@@ -1,5 +1,5 @@
-"""The octahedral symmetry of the M2L matrices (SURVEY "next": 48 signed axis permutations
-map the 316 displacements onto 16 classes), checked on the oracle's matrices.
+"""The octahedral symmetry of the M2L matrices (the 48 signed axis permutations map the 316
+displacements onto 16 classes), checked on the oracle's matrices.
 
 For a signed permutation g, (g w)_d = sigma_d w_{pi(d)}, the kernel 1/|w| is invariant, and
 a monomial transforms as (g u)^a = s(a) u^{gamma(a)} with s(a) = prod_d sigma_d^{a_d} and

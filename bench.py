@@ -59,6 +59,56 @@ def fp32_fma_peak_tflops(sm_mhz):
     return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
 
 
+def rotation_madds_per_pair(p):
+    """Multiply-adds per well-separated pair of the M2L by rotation (Sec. 3.4) at order p: two
+    substitutions about x (output (a, b, c) takes b + c + 1 terms), two about z (a + b + 1
+    terms) and the axial Eq. 5 matrix (column (a, b, c) reaches row (a', b', c') when b' >= b,
+    c' >= c and both differences are even)."""
+    C = [(a, b, n - a - b) for n in range(p + 1) for a in range(n, -1, -1) for b in range(n - a, -1, -1)]
+    sx = sum(b + c + 1 for a, b, c in C)
+    sz = sum(a + b + 1 for a, b, c in C)
+    ax = sum(1 for (_, b2, c2) in C for (_, b, c) in C
+             if b2 >= b and c2 >= c and (b2 - b) % 2 == 0 and (c2 - c) % 2 == 0)
+    return 2 * sx + 2 * sz + ax
+
+
+def near_field_interactions(x, dom, depth):
+    """Pairwise interactions (i != j) of a uniform tree's near field: every particle with every
+    other particle of its own leaf and of the adjacent leaves; leaves from the library's box
+    rule (21-bit integer coordinates, clamped, shifted down to the leaf level)."""
+    s = 1 << depth
+    k21 = np.clip(np.floor((np.asarray(x) - np.asarray(dom[:3])) * (2.0 ** 21 / dom[3])), 0, 2 ** 21 - 1)
+    k = k21.astype(np.int64) >> (21 - depth)
+    cnt = np.zeros((s, s, s), dtype=np.int64)
+    np.add.at(cnt, (k[:, 0], k[:, 1], k[:, 2]), 1)
+    pad = np.pad(cnt, 1)
+    nb = sum(pad[1 + a:1 + a + s, 1 + b:1 + b + s, 1 + c:1 + c + s]
+             for a in (-1, 0, 1) for b in (-1, 0, 1) for c in (-1, 0, 1))
+    return int((cnt * nb).sum()) - len(x)
+
+
+def near_field_roofline(x, dom, depth, leaf_ms, sm_mhz):
+    """Roofline of the FP32 near-field kernel (P2P over the 27 neighbour leaves; its launch
+    also runs L2P): 18 FP32 flops and one rsqrt per interaction (3 differences, r^2 in 5, q/r,
+    1/r^2, q/r^3, the potential sum and 3 field FMAs) against the FP32 FMA peak from unit
+    counts and clock; rsqrt_frac against 16 MUFU results per SM and clock."""
+    try:
+        inter = near_field_interactions(x, dom, depth)
+        flops = 18.0 * inter
+        sec = leaf_ms / 1e3
+        peak = fp32_fma_peak_tflops(sm_mhz)
+        ach = flops / sec / 1e12
+        return {"bound": "alu", "achieved": round(ach, 3), "peak": round(peak, 3), "unit": "TFLOP/s",
+                "frac": round(ach / peak, 4), "traffic": None,
+                "kernel": "near field k_leaf<float> (P2P over the 27 neighbour leaves, plus L2P; leaf phase time)",
+                "algorithmic": "18 FP32 flops + 1 rsqrt per interaction (i != j): %d interactions = %.3e flops"
+                               % (inter, flops),
+                "peak_source": "FP32 FMA = 152 SMs x 128 lanes x 2 flops x %.0f MHz (unit counts and clock)" % sm_mhz,
+                "rsqrt_frac": round(inter / sec / (152 * 16 * sm_mhz * 1e6), 4)}
+    except Exception as e:  # the bench line must not be lost to this extra key
+        return {"error": repr(e)}
+
+
 # clock-event reason bits of NVML (nvml.h) and the names the clock record uses for them
 NVML_REASONS = ((0x8, "hw_slowdown"), (0x40, "hw_thermal_slowdown"), (0x20, "sw_thermal_slowdown"),
                 (0x4, "sw_power_cap"))
@@ -339,10 +389,14 @@ def run_ours(args, rank, world):
     m2l_s = ph["m2l"] / 1e3
     achieved = flops / m2l_s / 1e12
     f16 = args.precision == "fp32"  # the FP32 mode's M2L runs on F16 split operands (the default)
+    rot = args.precision == "fp64" and p >= 4  # the FP64 default M2L from p = 4: by rotation
     if args.precision == "fp64":
         peak, bound = 1.25, "alu"
         peak_note = "FP64 nominal 1.25 TFLOP/s (no measured FP64 peak)"
         executed = None
+        if rot:
+            flops = 2.0 * rotation_madds_per_pair(p) * pairs_all
+            achieved = flops / m2l_s / 1e12
     else:
         if f16:
             # F16 operands: dense F16 tensor peak = the measured BF16 burst peak (same nominal rate)
@@ -366,8 +420,11 @@ def run_ours(args, rank, world):
                 "frac": round(achieved / peak, 4), "traffic": m2l_traffic(args.precision), "traffic_unit": "bytes per launch",
                 "kernel": ("M2L contraction (tcgen05 kind::f16 k_tc, all levels, one launch)" if f16 else
                            "M2L contraction (tcgen05 kind::tf32 k_tc, all levels, one launch)") if bound == "tensor"
-                else "M2L (SIMT FP64 k_m2l, all levels)",
-                "algorithmic": "2 ncoef^2 flops per well-separated pair: %.3e flops" % flops,
+                else ("M2L by rotation (k_m2l_rot, FP64 pipe, all levels)" if rot else
+                      "M2L (SIMT FP64 k_m2l, all levels)"),
+                "algorithmic": ("2 x %d multiply-adds per well-separated pair (4 rotations + axial Eq. 5): %.3e flops"
+                                % (rotation_madds_per_pair(p), flops)) if rot else
+                               "2 ncoef^2 flops per well-separated pair: %.3e flops" % flops,
                 "executed_tflops": None if executed is None else round(executed, 3),
                 "executed_frac": None if executed is None else round(executed / peak, 4),
                 "peak_source": peak_note}
@@ -384,6 +441,8 @@ def run_ours(args, rank, world):
         "phases_ms": {k: round(v, 4) for k, v in ph.items() if k != "launches"},
         "gpu_launches": int(ph["launches"]) * args.steps,
         "roofline": roofline,
+        "roofline_near_field": (near_field_roofline(x, dom, depth, ph["leaf"], peaks.get("sm_max_mhz", 2070.0))
+                                if args.precision != "fp64" else None),
         "clocks": ck,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": n * 4 * 8,
                 "d2h_bytes_per_step": n * 4 * 8, "steps": e2e_steps,

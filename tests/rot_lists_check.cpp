@@ -166,3 +166,15 @@ extern "C" int rot_lists_check(int p, unsigned seed) {
     }
     return 0;
 }
+
+// multiply-adds per pair of the M2L by rotation as the kernel runs it: the real (not padding)
+// tasks of the x and z lists, each list run twice, plus those of the axial list
+extern "C" long rot_real_tasks(int p) {
+    const RotStructure r = rot_structure(p);
+    auto real = [&](const std::vector<RotTask>& l) {
+        long c = 0;
+        for (const RotTask& t : l) c += !(t.y == (unsigned)r.nc && t.x == 0u);
+        return c;
+    };
+    return 2 * real(r.lx) + 2 * real(r.lz) + real(r.la);
+}

@@ -886,15 +886,17 @@ int build_adaptive(dafmm_ctx* c, dafmm_tree* t, const double* dxyz, const double
     // U, W, X lists
     const size_t nb1 = (size_t)nbox + 1;
     Scratch cnt3(c);
-    if ((rc = cnt3.alloc(3 * nb1 * 4 + 16, "list counts"))) return rc;
+    if ((rc = cnt3.alloc(3 * nb1 * 4 + 32, "list counts"))) return rc;
     int* cu = cnt3.as<int>();
     unsigned long long* nv = reinterpret_cast<unsigned long long*>(cu + ((3 * nb1 + 1) & ~size_t(1)));
+    // overflow of the list traversal, this build's own flag: the context's record of expired
+    // device waits (read by dafmm_sync) must survive a tree build
+    int* lflag = reinterpret_cast<int*>(nv + 1);
     if ((rc = dev_alloc(c, (void**)&t->u_ptr, nb1 * 4, "lists")) || (rc = dev_alloc(c, (void**)&t->w_ptr, nb1 * 4, "lists")) ||
         (rc = dev_alloc(c, (void**)&t->x_ptr, nb1 * 4, "lists")))
         return rc;
-    CK(c, cudaMemsetAsync(c->d_err, 0, 4, s), "err");
-    CK(c, cudaMemsetAsync(nv, 0, 8, s), "counter");
-    e = launch_list_count(abuild(t, keys.as<uint64_t>()), nbox, cu, cu + nb1, cu + 2 * nb1, nv, c->d_err, s);
+    CK(c, cudaMemsetAsync(nv, 0, 16, s), "counter");  // the V-pair counter and lflag
+    e = launch_list_count(abuild(t, keys.as<uint64_t>()), nbox, cu, cu + nb1, cu + 2 * nb1, nv, lflag, s);
     if (e == cudaSuccess) e = launch_scan(cu, t->u_ptr, nbox, s);
     if (e == cudaSuccess) e = launch_scan(cu + nb1, t->w_ptr, nbox, s);
     if (e == cudaSuccess) e = launch_scan(cu + 2 * nb1, t->x_ptr, nbox, s);
@@ -913,15 +915,12 @@ int build_adaptive(dafmm_ctx* c, dafmm_tree* t, const double* dxyz, const double
         (rc = dev_alloc(c, (void**)&t->x_idx, (size_t)std::max(tot[2], 1) * 4, "lists")))
         return rc;
     e = launch_list_fill(abuild(t, keys.as<uint64_t>()), nbox, t->u_ptr, t->w_ptr, t->x_ptr, t->u_idx, t->w_idx,
-                         t->x_idx, c->d_err, s);
+                         t->x_idx, lflag, s);
     int flag = 0;
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&flag, c->d_err, 4, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&flag, lflag, 4, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(c, e, "lists");
-    if (flag) {
-        CK(c, cudaMemset(c->d_err, 0, 4), "err");
-        return fail(c, DAFMM_ERR_INVALID_ARG, "adaptive tree too deep for the list traversal");
-    }
+    if (flag) return fail(c, DAFMM_ERR_INVALID_ARG, "adaptive tree too deep for the list traversal");
     cnt3.release();
     // M2L target groups: boxes of levels >= 2 by (level, octant)
     const int ngroups = (t->maxlev + 1) * 8;

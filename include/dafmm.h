@@ -193,8 +193,8 @@ int dafmm_last_phase_ms(dafmm_ctx* ctx, double* out10);
 #define DAFMM_OPT_LEAF_WARPS 3
 /*   DAFMM_OPT_M2L_F16: operands of the FP32 mode's tensor-core M2L: 1 (default) = F16 hi/lo
  *   splits with power-of-two scales per box, per matrix row and per matrix (twice the TF32
- *   rate, M2L rounding ~1e-7 relative), 0 = TF32 hi/lo splits (~5e-8).  MIXED always uses
- *   the TF32 splits. */
+ *   rate; FP32-level error, within a few times that of a plain FP32 product), 0 = TF32 hi/lo
+ *   splits.  MIXED always uses the TF32 splits. */
 #define DAFMM_OPT_M2L_F16 4
 /*   DAFMM_OPT_M2L_ROTATION: the FP64 M2L (Sec. 3.4): 0 = the dense K^_v
  *   matrix of each displacement; 1 = rotate the source expansion so that the displacement lies

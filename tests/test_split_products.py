@@ -9,6 +9,9 @@ lo = f16(x - hi).  Each displacement's term is A_hi B_hi + A_hi B_lo + A_lo B_hi
 are exact in FP32 and are accumulated in FP32.  The term is then rescaled and added in FP32,
 and the row scale is removed at the end.
 
+The MIXED mode's TF32 splits (hi = tf32(x), lo = tf32(x - hi), no scales) are emulated the
+same way.
+
 Checked, on the potential the local expansion gives at points of the target box:
   * the error stays at the FP32 level: within 4x of a plain FP32 product of the same FP32
     multipoles, and below the FP32 mode's 3.8e-6 parity bound;
@@ -92,6 +95,48 @@ def test_f16_split_is_fp32_level(p, seed):
     e32 = potential_error(p, plain.astype(np.float64), L64, X)
     assert e16 <= max(4.0 * e32, 1e-6), (e16, e32)
     assert e16 <= 3.8e-6
+
+
+def tf32(x):
+    """Round FP32 values to TF32 (10 mantissa bits), to nearest with ties away from zero."""
+    u = np.ascontiguousarray(x, dtype=np.float32).view(np.uint32)
+    return ((u + np.uint32(0x1000)) & np.uint32(0xFFFFE000)).view(np.float32)
+
+
+def tf32x3_local(Ks, Ms):
+    """The MIXED mode's M2L: operands rounded to FP32, split as hi = tf32(x), lo = tf32(x - hi)
+    (TF32 keeps FP32's exponent range, so no scales), three exact products per displacement
+    accumulated in FP32 and summed in FP32."""
+    L = np.zeros(Ks.shape[1], np.float32)
+    for K, M in zip(Ks, Ms):
+        K32, M32 = K.astype(np.float32), M.astype(np.float32)
+        Khi, Mhi = tf32(K32), tf32(M32)
+        Klo, Mlo = tf32(K32 - Khi), tf32(M32 - Mhi)
+        L = L + ((Khi @ Mhi + Khi @ Mlo) + Klo @ Mhi)
+    return L.astype(np.float64)
+
+
+def test_tf32_rounding():
+    one = np.float32(1.0)
+    ulp = np.float32(2.0 ** -10)  # TF32 spacing at 1
+    x = np.array([one + ulp / 4, one + ulp / 2, one + 3 * ulp / 4, -(one + ulp / 2)], np.float32)
+    assert tf32(x).tolist() == [1.0, 1.0 + 2.0 ** -10, 1.0 + 2.0 ** -10, -(1.0 + 2.0 ** -10)]
+
+
+@pytest.mark.parametrize("p", [4, 8, 10])
+def test_tf32_split_is_fp32_level(p):
+    Ks = matrices(p)
+    rng = np.random.default_rng(7)
+    Ms = np.array([O.p2m(p, rng.uniform(-0.5, 0.5, (30, 3)), rng.uniform(-1, 1, 30)) for _ in DISPLACEMENTS])
+    X = rng.uniform(-0.5, 0.5, (200, 3))
+    L64 = np.einsum("vba,va->b", Ks, Ms)
+    plain = np.zeros(Ks.shape[1], np.float32)
+    for K, M in zip(Ks, Ms):
+        plain = plain + K.astype(np.float32) @ M.astype(np.float32)
+    e_tf = potential_error(p, tf32x3_local(Ks, Ms), L64, X)
+    e32 = potential_error(p, plain.astype(np.float64), L64, X)
+    assert e_tf <= max(4.0 * e32, 1e-6), (e_tf, e32)
+    assert e_tf <= 3.8e-6
 
 
 @pytest.mark.parametrize("p", [4, 8])

@@ -62,6 +62,23 @@ def test_p2m_p2l_10000_instances(ctx, p, prec):
     assert per_order_rel(out2[sub], ref2, p) <= TOL[prec]
 
 
+@pytest.mark.parametrize("p", [2, 6])
+def test_p2l_reproduces_table1(ctx, p):
+    """Table 1 of the paper lists the Taylor coefficients of 1/r at (1,1,1) to order 2: the P2L
+    expansion (Eq. 6) of a unit charge at w = (1,1,1), here from the generated GPU operator, in
+    FP64 to within a few units in the last of the table's 16 digits and in FP32 to single
+    precision."""
+    from conftest import read_golden
+    ex = O.exponents(p)
+    idx = {tuple(int(v) for v in e): k for k, e in enumerate(ex)}
+    for prec, tol in ((B.DAFMM_FP64, 1e-15), (B.DAFMM_FP32, 5e-7)):
+        out = np.zeros((1, O.ncoef(p)))
+        B.dafmm_op_p2l(ctx, p, prec, np.array([[1.0, 1.0, 1.0]]), np.array([1.0]), out)
+        for a, b, c, val in read_golden("table1_rinv_at_111_order2.txt"):
+            got = out[0, idx[(int(a), int(b), int(c))]]
+            assert abs(got - val) <= tol * (1.0 + abs(val)), (prec, a, b, c, got, val)
+
+
 @pytest.mark.parametrize("p", ORDERS)
 @pytest.mark.parametrize("prec", [B.DAFMM_FP64, B.DAFMM_FP32])
 def test_l2p_m2p(ctx, p, prec):

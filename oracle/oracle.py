@@ -37,8 +37,11 @@ def build(force=False):
 def _load():
     global _lib
     if _lib is None:
-        build()
-        _lib = ctypes.CDLL(_LIB_PATH)
+        # DAFMM_ORACLE_LIB: an instrumented build of the same sources (the sanitizer tests)
+        path = os.environ.get("DAFMM_ORACLE_LIB")
+        if not path:
+            path = build()
+        _lib = ctypes.CDLL(path)
         D = ctypes.POINTER(ctypes.c_double)
         I64 = ctypes.POINTER(ctypes.c_int64)
         I32 = ctypes.POINTER(ctypes.c_int)

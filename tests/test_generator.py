@@ -71,7 +71,7 @@ def test_generated_p2m_p2l(hc, p):
             s = rng.uniform(-0.5, 0.5, 3)  # charge inside the unit box (Sec. 3 setup)
             q = rng.uniform(-1, 1)
             out = np.zeros(nc)
-            assert hc.hc_p2m(p, prec, P(s), q, P(out) if False else out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), nc) == 0
+            assert hc.hc_p2m(p, prec, P(s), q, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), nc) == 0
             g_m.append(out)
             r_m.append(O.p2m(p, s[None, :], [q]))
             w = rng.uniform(-0.5, 0.5, 3) + np.array([2.0, -1.0, 2.0])  # source two boxes away

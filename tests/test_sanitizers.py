@@ -1,6 +1,8 @@
 """Host-side AddressSanitizer and UndefinedBehaviorSanitizer runs (no GPU).
 
-The oracle's C sources and the host build of the generated operator code are compiled with
+The oracle's C sources, the host build of the generated operator code and the host-side
+runtime headers (pool arena, admission policy, rotation task lists, record layout, through
+their CPU checks) are compiled with
 -fsanitize=address,undefined, loaded in a child Python process with the ASan runtime
 preloaded, and driven through every operator and orders 0..10.  The oracle also runs the
 direct sum and FMM solves on uniform, adaptive, rotation-mode and depth-capped trees.  A run
@@ -63,7 +65,19 @@ def builds():
                 "int heap_overflow(int n) { int* a = malloc(4 * n); a[n] = 1; int r = a[0]; free(a); return r; }\n"
                 "int signed_overflow(int x) { return x + 2147483647; }\n")
     subprocess.check_call(["gcc", "-O0", "-fPIC", "-shared"] + SAN + ["-o", planted, os.path.join(d, "planted.c")])
-    return {"oracle": oracle_so, "hc": hc_so, "planted": planted}
+    # the host-side runtime pieces (pool arena, admission policy, rotation task lists, particle
+    # record layout), through their CPU checks
+    host = {}
+    for name, extra in (("arena_check", []), ("serve_policy_check", []), ("rot_lists_check", []),
+                        ("xq_layout_check", ["-x", "c++", "-I", "/usr/local/cuda/include"])):
+        if name == "xq_layout_check" and not os.path.exists("/usr/local/cuda/include/vector_types.h"):
+            continue
+        so = os.path.join(d, name + ".so")
+        subprocess.check_call(["g++", "-O1", "-std=c++17", "-fPIC", "-shared"] + SAN + extra
+                              + ["-I", os.path.join(ROOT, "paper_2508_02626_gb300", "csrc"), "-o", so,
+                                 os.path.join(ROOT, "tests", name + ".cpp")])
+        host[name] = so
+    return {"oracle": oracle_so, "hc": hc_so, "planted": planted, "host": host}
 
 
 ORACLE_SCRIPT = r"""
@@ -136,6 +150,35 @@ def test_oracle_is_clean(builds):
 def test_generated_operators_are_clean(builds):
     r = _run(HC_SCRIPT, {"HC_LIB": builds["hc"]})
     assert _clean(r) and "generated ok" in r.stdout, r.stderr[-3000:]
+
+
+HOST_SCRIPT = r"""
+import ctypes, json, os
+libs = json.loads(os.environ["HOST_LIBS"])
+C = ctypes
+if "arena_check" in libs:
+    a = C.CDLL(libs["arena_check"]); a.arena_check.argtypes = [C.c_int, C.c_int, C.c_ulonglong]
+    assert a.arena_check(64, 4000, 1) == 0 and a.arena_check(1000, 20000, 2) == 0 and a.arena_check(7, 2000, 3) == 0
+if "serve_policy_check" in libs:
+    s = C.CDLL(libs["serve_policy_check"]); s.policy_check.argtypes = [C.c_int, C.c_ulonglong]
+    assert s.policy_check(5000, 1) == 0
+if "rot_lists_check" in libs:
+    r = C.CDLL(libs["rot_lists_check"]); r.rot_lists_check.argtypes = [C.c_int, C.c_uint]
+    r.rot_real_tasks.argtypes = [C.c_int]; r.rot_real_tasks.restype = C.c_long
+    for p in range(11):
+        assert r.rot_lists_check(p, 100 + p) == 0 and r.rot_real_tasks(p) > 0
+if "xq_layout_check" in libs:
+    x = C.CDLL(libs["xq_layout_check"]); x.xq_layout_check.argtypes = [C.c_uint]
+    x.octmajor_check.argtypes = [C.c_int]
+    assert x.xq_layout_check(1) == 0 and all(x.octmajor_check(l) == 0 for l in range(5))
+print("host ok")
+"""
+
+
+def test_host_runtime_pieces_are_clean(builds):
+    import json
+    r = _run(HOST_SCRIPT, {"HOST_LIBS": json.dumps(builds["host"])})
+    assert _clean(r) and "host ok" in r.stdout, r.stderr[-3000:]
 
 
 @pytest.mark.parametrize("fn,report", [("heap_overflow(4)", "heap-buffer-overflow"),

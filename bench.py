@@ -8,8 +8,9 @@ Prints one JSON line (rank 0).  Under torchrun every rank runs an independent re
 the workload on its own GPU (independent solves shard with no data exchange); the value
 is the total particles of all ranks divided by the slowest rank's time.
 
---impl reference times the CPU oracle (oracle/, plain C, all host cores) on a bounded
-sample of the same workload and reports its extrapolated full-solve rate.
+--impl reference times the CPU oracle (oracle/, plain C, all host cores): each step is one
+full oracle solve of the same workload (same tree and order, every particle), nothing
+extrapolated.
 """
 import argparse
 import json
@@ -28,8 +29,8 @@ METRIC = "particles/s at rel err <=1e-7 (N=1M, p=8); served solves/s + p50/p99 l
 UNIT = "particles/s"
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of the M2L kernel on
-# this workload, from one ncu capture (profiles/k_tc_m2l_uniform_1e6_p8.md); valid while the
-# kernel's source files hash to the recorded value, reported as null otherwise
+# this workload, from one ncu capture of that kernel; valid while the kernel's source files
+# hash to the recorded value, reported as null otherwise
 M2L_TRAFFIC = {"fp32": (79.5e6, "b6f5406ee09268bb")}
 M2L_SOURCES = ("paper_2508_02626_gb300/csrc/tc_common.cuh", "paper_2508_02626_gb300/csrc/tc_ops.cu")
 

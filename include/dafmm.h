@@ -181,7 +181,8 @@ int dafmm_set_profiling(dafmm_ctx* ctx, int enable);
 int dafmm_last_phase_ms(dafmm_ctx* ctx, double* out10);
 
 /* Options of a context.
- *   DAFMM_OPT_M2L_KERNEL: 0 = tensor-core M2L (tcgen05, TF32 split products) for the FP32
+ *   DAFMM_OPT_M2L_KERNEL: 0 = tensor-core M2L (tcgen05 split products: F16 splits in the
+ *   FP32 mode unless DAFMM_OPT_M2L_F16 is 0, TF32 splits in the MIXED mode) for the FP32
  *   bulk paths when the order is >= 2 (default), 1 = SIMT FP32 M2L. */
 #define DAFMM_OPT_M2L_KERNEL 1
 /*   DAFMM_OPT_TC_MASK: which contractions may use the tensor cores in the FP32 mode

@@ -83,6 +83,65 @@ bool device_or_null(const void* p) {
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// Host-side tables of one order that the evaluation copies into the scratch array: the DA
+// product table of the K generation (pairs (i, j) with e_i + e_j = e_k per output k, and the
+// index of e_k minus one unit per axis) and the per-octant row starts of the M2M/L2L tables.
+// Built once per order on first use and kept until the process exits, so that every copy
+// reads host memory that outlives the call that issued it.
+struct HostTables {
+    std::vector<int> rowptr;
+    std::vector<ushort2> pairs;
+    std::vector<short> minus;
+    std::vector<int> m2m_rp8, l2l_rp8;
+};
+
+HostTables g_tables[kNoAllocMaxOrder + 1];
+std::once_flag g_tables_once[kNoAllocMaxOrder + 1];
+
+const HostTables& host_tables(int order) {
+    std::call_once(g_tables_once[order], [order] {
+        const dafmm::OrderOps* ops = dafmm::order_ops(order);
+        const int nc = ops->nc;
+        HostTables& ht = g_tables[order];
+        std::vector<int> ex(3 * nc);
+        for (int n = 0; n <= order; ++n)
+            for (int a = n; a >= 0; --a)
+                for (int b = n - a; b >= 0; --b) {
+                    const int cc = n - a - b, k = dafmm::da_index(a, b, cc);
+                    ex[3 * k] = a; ex[3 * k + 1] = b; ex[3 * k + 2] = cc;
+                }
+        ht.rowptr.resize(nc + 1);
+        for (int k = 0; k < nc; ++k) {
+            ht.rowptr[k] = (int)ht.pairs.size();
+            for (int i = 0; i < nc; ++i) {
+                const int r0 = ex[3 * k] - ex[3 * i], r1 = ex[3 * k + 1] - ex[3 * i + 1], r2 = ex[3 * k + 2] - ex[3 * i + 2];
+                if (r0 < 0 || r1 < 0 || r2 < 0) continue;
+                ushort2 pr;
+                pr.x = (unsigned short)i;
+                pr.y = (unsigned short)dafmm::da_index(r0, r1, r2);
+                ht.pairs.push_back(pr);
+            }
+        }
+        ht.rowptr[nc] = (int)ht.pairs.size();
+        ht.minus.resize(3 * nc);
+        for (int d = 0; d < 3; ++d)
+            for (int k = 0; k < nc; ++k) {
+                int e[3] = {ex[3 * k], ex[3 * k + 1], ex[3 * k + 2]};
+                if (e[d] == 0) {
+                    ht.minus[d * nc + k] = -1;
+                } else {
+                    e[d] -= 1;
+                    ht.minus[d * nc + k] = (short)dafmm::da_index(e[0], e[1], e[2]);
+                }
+            }
+        ht.m2m_rp8.resize(8 * (size_t)nc + 1);
+        ht.l2l_rp8.resize(8 * (size_t)nc + 1);
+        dafmm::shift_rp8(ops->m2m, nc, ht.m2m_rp8.data());
+        dafmm::shift_rp8(ops->l2l, nc, ht.l2l_rp8.data());
+    });
+    return g_tables[order];
+}
+
 }  // namespace
 
 using namespace dafmm;
@@ -108,39 +167,10 @@ extern "C" int dafmm_eval_noalloc(dafmm_tree* t, int order, double* phi, double*
     const int nc = ops->nc, ncp = ops->ncp;
     const bool far = t->depth >= 2;
 
-    // DA product table of the K generation (pairs (i, j) with e_i + e_j = e_k, per output k)
-    std::vector<int> ex(3 * nc);
-    for (int n = 0; n <= order; ++n)
-        for (int a = n; a >= 0; --a)
-            for (int b = n - a; b >= 0; --b) {
-                const int cc = n - a - b, k = da_index(a, b, cc);
-                ex[3 * k] = a; ex[3 * k + 1] = b; ex[3 * k + 2] = cc;
-            }
-    std::vector<int> rowptr(nc + 1);
-    std::vector<ushort2> pairs;
-    for (int k = 0; k < nc; ++k) {
-        rowptr[k] = (int)pairs.size();
-        for (int i = 0; i < nc; ++i) {
-            const int r0 = ex[3 * k] - ex[3 * i], r1 = ex[3 * k + 1] - ex[3 * i + 1], r2 = ex[3 * k + 2] - ex[3 * i + 2];
-            if (r0 < 0 || r1 < 0 || r2 < 0) continue;
-            ushort2 pr;
-            pr.x = (unsigned short)i;
-            pr.y = (unsigned short)da_index(r0, r1, r2);
-            pairs.push_back(pr);
-        }
-    }
-    rowptr[nc] = (int)pairs.size();
-    std::vector<short> minus(3 * nc);
-    for (int d = 0; d < 3; ++d)
-        for (int k = 0; k < nc; ++k) {
-            int e[3] = {ex[3 * k], ex[3 * k + 1], ex[3 * k + 2]};
-            if (e[d] == 0) {
-                minus[d * nc + k] = -1;
-            } else {
-                e[d] -= 1;
-                minus[d * nc + k] = (short)da_index(e[0], e[1], e[2]);
-            }
-        }
+    const HostTables& ht = host_tables(order);
+    const std::vector<int>& rowptr = ht.rowptr;
+    const std::vector<ushort2>& pairs = ht.pairs;
+    const std::vector<short>& minus = ht.minus;
 
     // plan the layout (a dry run with a null base gives the size)
     auto plan = [&](unsigned char* base, OrderData& od, double** M, double** L) {
@@ -195,11 +225,8 @@ extern "C" int dafmm_eval_noalloc(dafmm_tree* t, int order, double* phi, double*
     up(od.l2l_col, ops->l2l.col, ops->l2l.nnz * sizeof(unsigned short));
     up(od.l2l_par, ops->l2l.par, ops->l2l.nnz);
     up(od.l2l_val, ops->l2l.val, ops->l2l.nnz * sizeof(double));
-    std::vector<int> m2m_rp8(8 * (size_t)nc + 1), l2l_rp8(8 * (size_t)nc + 1);
-    shift_rp8(ops->m2m, nc, m2m_rp8.data());
-    shift_rp8(ops->l2l, nc, l2l_rp8.data());
-    up(od.m2m_rp8, m2m_rp8.data(), m2m_rp8.size() * sizeof(int));
-    up(od.l2l_rp8, l2l_rp8.data(), l2l_rp8.size() * sizeof(int));
+    up(od.m2m_rp8, ht.m2m_rp8.data(), ht.m2m_rp8.size() * sizeof(int));
+    up(od.l2l_rp8, ht.l2l_rp8.data(), ht.l2l_rp8.size() * sizeof(int));
     up(od.mul_rowptr, rowptr.data(), rowptr.size() * sizeof(int));
     up(od.mul_pairs, pairs.data(), pairs.size() * sizeof(ushort2));
     up(od.mul_minus, minus.data(), minus.size() * sizeof(short));

@@ -14,8 +14,9 @@
 // box.  Each FP32 operand is split into TF32 parts x = hi + lo and the product takes
 // A_hi T_lo + A_lo T_hi + A_hi T_hi (about 22 mantissa bits per product) into a fresh
 // FP32 TMEM accumulator per term (double-buffered); the epilogue warps add the terms in
-// FP32 registers, write the FP64 result and, when asked, its TF32 split for the next
-// stage.
+// FP32 registers, write the result -- FP64 rows, or FP32 rows in the FP32 mode of uniform
+// trees -- and, when asked, its TF32 split for the next stage.  (The FP32 mode's M2L takes
+// F16 hi/lo splits with power-of-two scales instead of TF32 ones; see tc_common.cuh.)
 //
 // One persistent CTA per SM walks the work items.  Warp roles: warp 0 issues TMA loads
 // into a ring of shared-memory stages, warp 1 issues the MMAs (one elected thread) and

@@ -5,9 +5,10 @@ memory is owned by their own pool allocator, or cudaMalloc's implicit synchronis
 not acceptable in their loop).  It keeps every intermediate array in one fixed array of
 device memory inside the library; this test checks, through the C ABI, that two calls in
 a row give the same potential and field as the ordinary FP64 evaluation (within the FP64
-bound of the other parity tests), that the context's own allocations do not grow, and
-that requests beyond its limits are refused.  The file is named so that pytest collects
-it last."""
+bound of the other parity tests) -- on a depth-3 tree and on the largest accepted case,
+order 6 at depth 4, which fills most of the array -- that neither the context's own
+allocations nor the device's free memory change across a call, and that requests beyond
+its limits are refused.  The file is named so that pytest collects it last."""
 import numpy as np
 import pytest
 import torch
@@ -22,28 +23,43 @@ def rel(a, b):
     return float(np.sqrt(((a - b) ** 2).sum() / (b ** 2).sum()))
 
 
+def check_twice(ctx, n, p, depth, seed):
+    """Two calls in a row against dafmm_eval FP64 on the same tree; returns the tree."""
+    x, q = W.uniform(n, seed=seed)
+    tree = ctx.build_tree(torch.from_numpy(x).cuda(), torch.from_numpy(q).cuda(), domain=W.UNIT_CUBE,
+                          uniform_depth=depth)
+    ref_phi = torch.empty(n, dtype=torch.float64, device="cuda")
+    ref_E = torch.empty((n, 3), dtype=torch.float64, device="cuda")
+    tree.eval(p, ref_phi, ref_E, precision="fp64")
+    B.dafmm_sync(ctx.h)
+    ref_phi, ref_E = ref_phi.cpu().numpy(), ref_E.cpu().numpy()
+    held = B.dafmm_bytes_in_use(ctx.h)
+    phi = torch.empty(n, dtype=torch.float64, device="cuda")
+    E = torch.empty((n, 3), dtype=torch.float64, device="cuda")
+    for call in range(2):
+        phi.fill_(float("nan"))
+        E.fill_(float("nan"))
+        torch.cuda.synchronize()
+        free_before = torch.cuda.mem_get_info()[0]
+        B.dafmm_eval_noalloc(ctx.h, tree.h, p, phi, E)
+        B.dafmm_sync(ctx.h)
+        free_after = torch.cuda.mem_get_info()[0]
+        assert rel(phi.cpu().numpy(), ref_phi) <= 1e-12
+        assert rel(E.cpu().numpy(), ref_E) <= 1e-11
+        assert B.dafmm_bytes_in_use(ctx.h) == held
+        if call == 1:  # the first call on a device may load the library's module
+            assert free_after == free_before, (free_before, free_after)
+    return tree
+
+
 def test_noalloc_matches_eval_twice():
     B.load()
     ctx = B.Context(0)
     try:
-        n, p, depth = 10_000, 6, 3
-        x, q = W.uniform(n, seed=1001)
-        tree = ctx.build_tree(torch.from_numpy(x).cuda(), torch.from_numpy(q).cuda(), domain=W.UNIT_CUBE,
-                              uniform_depth=depth)
-        ref_phi = torch.empty(n, dtype=torch.float64, device="cuda")
-        ref_E = torch.empty((n, 3), dtype=torch.float64, device="cuda")
-        tree.eval(p, ref_phi, ref_E, precision="fp64")
-        B.dafmm_sync(ctx.h)
-        ref_phi, ref_E = ref_phi.cpu().numpy(), ref_E.cpu().numpy()
-        held = B.dafmm_bytes_in_use(ctx.h)
-        for _ in range(2):
-            phi = torch.full((n,), float("nan"), dtype=torch.float64, device="cuda")
-            E = torch.full((n, 3), float("nan"), dtype=torch.float64, device="cuda")
-            B.dafmm_eval_noalloc(ctx.h, tree.h, p, phi, E)
-            B.dafmm_sync(ctx.h)
-            assert rel(phi.cpu().numpy(), ref_phi) <= 1e-12
-            assert rel(E.cpu().numpy(), ref_E) <= 1e-11
-            assert B.dafmm_bytes_in_use(ctx.h) == held
+        n, p = 10_000, 6
+        tree = check_twice(ctx, n, p, 3, 1001)
+        phi = torch.empty(n, dtype=torch.float64, device="cuda")
+        E = torch.empty((n, 3), dtype=torch.float64, device="cuda")
         # beyond the limits: order above 6, host outputs
         with pytest.raises(B.DafmmError) as e:
             B.dafmm_eval_noalloc(ctx.h, tree.h, 8, phi, E)
@@ -60,5 +76,16 @@ def test_noalloc_matches_eval_twice():
             B.dafmm_eval_noalloc(ctx.h, deep.h, 4, torch.empty(40_000, dtype=torch.float64, device="cuda"), None)
         assert e.value.code == B.DAFMM_ERR_INVALID_ARG
         deep.free()
+    finally:
+        ctx.close()
+
+
+def test_noalloc_largest_case():
+    """Order 6 on a depth-4 tree: the largest case the array accepts (the M2L matrices and
+    the expansions of levels 2..4 take about 27 of its 32 MiB)."""
+    B.load()
+    ctx = B.Context(0)
+    try:
+        check_twice(ctx, 40_000, 6, 4, 4004).free()
     finally:
         ctx.close()

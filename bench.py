@@ -88,26 +88,63 @@ def near_field_interactions(x, dom, depth):
     return int((cnt * nb).sum()) - len(x)
 
 
-def near_field_roofline(x, dom, depth, leaf_ms, sm_mhz):
+def near_field_roofline(x, dom, depth, leaf_ms, sm_mhz, measured=None):
     """Roofline of the FP32 near-field kernel (P2P over the 27 neighbour leaves; its launch
     also runs L2P): 18 FP32 flops and one rsqrt per interaction (3 differences, r^2 in 5, q/r,
-    1/r^2, q/r^3, the potential sum and 3 field FMAs) against the FP32 FMA peak from unit
-    counts and clock; rsqrt_frac against 16 MUFU results per SM and clock."""
+    1/r^2, q/r^3, the potential sum and 3 field FMAs) against the FP32 FMA peak, and
+    rsqrt_frac against the rsqrt rate.  With `measured` (the probes of dafmm_probe_peak:
+    {"fp32_tflops": the faster of scalar and packed FMA, "rsqrt_per_s": ...}) the peaks are the
+    measured ones; the figures from unit counts and clock (152 SMs x 128 FP32 lanes x 2 flops,
+    16 MUFU results per SM and clock) are reported beside them."""
     try:
         inter = near_field_interactions(x, dom, depth)
         flops = 18.0 * inter
         sec = leaf_ms / 1e3
-        peak = fp32_fma_peak_tflops(sm_mhz)
+        derived = fp32_fma_peak_tflops(sm_mhz)
+        derived_rsqrt = 152 * 16 * sm_mhz * 1e6
+        if measured:
+            peak, rsq = measured["fp32_tflops"], measured["rsqrt_per_s"]
+            src = "measured (dafmm_probe_peak: FP32 FMA %.1f TFLOP/s, rsqrt %.3e/s)" % (peak, rsq)
+        else:
+            peak, rsq = derived, derived_rsqrt
+            src = "FP32 FMA = 152 SMs x 128 lanes x 2 flops x %.0f MHz (unit counts and clock)" % sm_mhz
         ach = flops / sec / 1e12
         return {"bound": "alu", "achieved": round(ach, 3), "peak": round(peak, 3), "unit": "TFLOP/s",
                 "frac": round(ach / peak, 4), "traffic": None,
                 "kernel": "near field k_leaf<float> (P2P over the 27 neighbour leaves, plus L2P; leaf phase time)",
                 "algorithmic": "18 FP32 flops + 1 rsqrt per interaction (i != j): %d interactions = %.3e flops"
                                % (inter, flops),
-                "peak_source": "FP32 FMA = 152 SMs x 128 lanes x 2 flops x %.0f MHz (unit counts and clock)" % sm_mhz,
-                "rsqrt_frac": round(inter / sec / (152 * 16 * sm_mhz * 1e6), 4)}
+                "peak_source": src,
+                "rsqrt_frac": round(inter / sec / rsq, 4),
+                "peak_derived": round(derived, 3), "frac_of_derived": round(ach / derived, 4),
+                "rsqrt_frac_of_derived": round(inter / sec / derived_rsqrt, 4)}
     except Exception as e:  # the bench line must not be lost to this extra key
         return {"error": repr(e)}
+
+
+def bench_peaks(device):
+    """Unit rates of the GPU measured by the library's probes (dafmm_probe_peak), with the SM
+    clock sampled while they run: FP32 FMA (scalar, packed FP32x2), FP64 FMA, MUFU rsqrt, and
+    tcgen05 MMA of kind tf32 and f16 (M=128, N=256, one CTA per SM)."""
+    import torch
+
+    from paper_2508_02626_gb300 import binding as B
+    try:
+        uuid = str(torch.cuda.get_device_properties(device).uuid)
+    except Exception:
+        uuid = None
+    ck = ClockSampler(device, uuid)
+    ck.start()
+    out = {}
+    try:
+        for kind in ("ffma", "ffma2", "dfma", "rsqrt", "mma_tf32", "mma_f16"):
+            rate, ms = B.dafmm_probe_peak(device, kind)
+            unit = "results/s" if kind == "rsqrt" else "TFLOP/s"
+            out[kind] = {"rate": rate if kind == "rsqrt" else round(rate / 1e12, 3), "unit": unit,
+                         "ms": round(ms, 3)}
+    finally:
+        out["clocks"] = ck.stop()
+    return out
 
 
 # clock-event reason bits of NVML (nvml.h) and the names the clock record uses for them
@@ -383,6 +420,36 @@ def run_ours(args, rank, world):
         pool.close()
         e2e_plain = e2e_rate(ctx) * world
 
+    # measured unit rates (FP32 / FP64 / MUFU / tcgen05 TF32 and F16), after the timed region
+    probes = None
+    if not args.no_peaks:
+        try:
+            probes = bench_peaks(local)
+        except Exception as e:  # the bench line must not be lost to this extra key
+            probes = {"error": repr(e)}
+    measured_alu = None
+    if probes and "ffma" in probes:
+        measured_alu = {"fp32_tflops": max(probes["ffma"]["rate"], probes["ffma2"]["rate"]),
+                        "rsqrt_per_s": probes["rsqrt"]["rate"], "fp64_tflops": probes["dfma"]["rate"]}
+
+    # the FP64 mode's two dominant kernels against the measured FP64 FMA rate: the M2L by
+    # rotation (its multiply-adds, Sec. 3.4) and the leaf kernel (18 FP64 flops and one
+    # rsqrt per near-field interaction; its launch also runs L2P)
+    if measured_alu and "fp64" in modes and p >= 4:
+        pf = measured_alu["fp64_tflops"]
+        ph64 = modes["fp64"]["phases_ms"]
+        pairs64 = sum(m2l_pairs_level(l) for l in range(2, depth + 1))
+        rot_fl = 2.0 * rotation_madds_per_pair(p) * pairs64
+        inter = near_field_interactions(x, dom, depth)
+        modes["fp64"]["rooflines"] = {
+            "peak_fp64_tflops": round(pf, 4), "peak_source": "measured (dafmm_probe_peak, FP64 FMA)",
+            "m2l_rotation": {"algorithmic_flops": rot_fl, "ms": ph64["m2l"],
+                             "achieved": round(rot_fl / (ph64["m2l"] / 1e3) / 1e12, 4),
+                             "frac": round(rot_fl / (ph64["m2l"] / 1e3) / 1e12 / pf, 4)},
+            "leaf": {"algorithmic_flops": 18.0 * inter, "interactions": inter, "ms": ph64["leaf"],
+                     "achieved": round(18.0 * inter / (ph64["leaf"] / 1e3) / 1e12, 4),
+                     "frac": round(18.0 * inter / (ph64["leaf"] / 1e3) / 1e12 / pf, 4)}}
+
     peaks, peak_src = load_peaks()
     nc = (p + 1) * (p + 2) * (p + 3) // 6
     pairs_all = sum(m2l_pairs_level(l) for l in range(2, depth + 1))
@@ -394,6 +461,9 @@ def run_ours(args, rank, world):
     if args.precision == "fp64":
         peak, bound = 1.25, "alu"
         peak_note = "FP64 nominal 1.25 TFLOP/s (no measured FP64 peak)"
+        if measured_alu:
+            peak = measured_alu["fp64_tflops"]
+            peak_note = "FP64 FMA measured by dafmm_probe_peak (%.3f TFLOP/s; nominal 1.25)" % peak
         executed = None
         if rot:
             flops = 2.0 * rotation_madds_per_pair(p) * pairs_all
@@ -442,8 +512,10 @@ def run_ours(args, rank, world):
         "phases_ms": {k: round(v, 4) for k, v in ph.items() if k != "launches"},
         "gpu_launches": int(ph["launches"]) * args.steps,
         "roofline": roofline,
-        "roofline_near_field": (near_field_roofline(x, dom, depth, ph["leaf"], peaks.get("sm_max_mhz", 2070.0))
+        "roofline_near_field": (near_field_roofline(x, dom, depth, ph["leaf"], peaks.get("sm_max_mhz", 2070.0),
+                                                    measured_alu)
                                 if args.precision != "fp64" else None),
+        "peaks": probes,
         "clocks": ck,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": n * 4 * 8,
                 "d2h_bytes_per_step": n * 4 * 8, "steps": e2e_steps,
@@ -463,7 +535,8 @@ def run_ours(args, rank, world):
     if world == 1 and not args.no_workloads:
         sections = set(args.sections.split(","))
         if "adaptive" in sections:
-            out["adaptive"] = bench_adaptive(ctx, stream, flush)
+            out["adaptive"] = bench_adaptive(ctx, stream, flush, args.adaptive_n,
+                                             tuple(args.adaptive_modes.split(",")))
         if "batch" in sections:
             out["batch"] = bench_batch(ctx, stream, flush)
         if "serving" in sections:
@@ -474,6 +547,15 @@ def run_ours(args, rank, world):
             out["leaf_size"] = bench_leaf_size(ctx)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"], out["accuracy"] = cpu_baseline(x, q, dom, cfg, phi_host, E_host, phi_by_order)
+        a = out["accuracy"]
+        # the headline's error beside its value: against the FP64 oracle FMM (same tree and
+        # order, all particles) and, with the oracle's own, against the direct sum
+        out["config"]["error"] = {k: float("%.3e" % a[k]) for k in (
+            "rel_l2_phi_vs_oracle", "rel_l2_field_vs_oracle", "worst_target_field_vs_oracle",
+            "rel_l2_phi_vs_direct", "oracle_rel_l2_phi_vs_direct", "rel_l2_field_vs_direct",
+            "oracle_rel_l2_field_vs_direct")}
+    if "fp64" in out["modes"]:
+        out["config"]["fp64_mode_particles_per_s"] = round(out["modes"]["fp64"]["value"])
     ctx.close()
     return out
 
@@ -494,14 +576,17 @@ def timed_evals(tree, p, prec, phi, E, stream, flush, steps):
     return float(np.mean(ms))
 
 
-def bench_adaptive(ctx, stream, flush):
+def bench_adaptive(ctx, stream, flush, n_points=None, modes=("mixed", "fp32")):
     """Adaptive octree on clustered data: N = 4e6 in 32 Gaussian clusters, q = +1, s = 64,
-    p = 10; MIXED (the workload's stated precision) and FP32."""
+    p = 10; MIXED (the workload's stated precision) and FP32.  n_points replaces N (a smaller
+    case of the same distribution, for profiling captures)."""
     import torch
 
     from paper_2508_02626_gb300 import binding as B
     from paper_2508_02626_gb300 import workloads as W
-    cfg = W.C3
+    cfg = dict(W.C3)
+    if n_points:
+        cfg["n"] = int(n_points)
     x, q, _ = W.make(cfg)
     n, p = cfg["n"], cfg["order"]
     xt, qt = torch.from_numpy(x).cuda(), torch.from_numpy(q).cuda()
@@ -515,10 +600,10 @@ def bench_adaptive(ctx, stream, flush):
     build_ms = (time.perf_counter() - t0) * 1e3
     tr2.free()
     info = tree.info()
-    out = {"workload": "clustered N=4e6 (32 Gaussian clusters, sigma U[0.02,0.1]), q=+1, adaptive s=64, p=10",
+    out = {"workload": "clustered N=%.0e (32 Gaussian clusters, sigma U[0.02,0.1]), q=+1, adaptive s=64, p=10" % n,
            "tree": {k: info[k] for k in ("depth", "leaves", "boxes", "max_per_leaf", "m2l_pairs", "p2p_leaf_pairs")},
            "build_ms": build_ms}
-    for mname in ("mixed", "fp32"):
+    for mname in modes:
         mp = B.PRECISIONS[mname]
         with torch.cuda.stream(stream):
             tree.eval(p, phi, E, precision=mp, stream=stream)
@@ -808,7 +893,9 @@ def cpu_baseline(x, q, dom, cfg, phi_gpu, E_gpu, phi_by_order=None):
     """The oracle FMM (plain C, all host cores) timed on one full solve of the workload: same
     tree and order, every particle a target, nothing extrapolated (about 15 s on 16 Arm cores,
     23 s on 8 x86 cores).  Its result also gives the GPU's error against the oracle over all
-    particles; 300 seeded random particles give the errors against the direct sum (Eq. 1)."""
+    particles (relative L2, and the worst single target relative to max(|value|, median
+    |value|)); 2000 seeded random particles give the errors of both against the direct sum
+    (Eq. 1), for the potential and the field."""
     import oracle as O
 
     n, p, depth = cfg["n"], cfg["order"], cfg["uniform_depth"]
@@ -816,19 +903,27 @@ def cpu_baseline(x, q, dom, cfg, phi_gpu, E_gpu, phi_by_order=None):
     t0 = time.perf_counter()
     ref_phi, ref_E = O.fmm(x, q, dom, p, uniform_depth=depth, nthreads=cores)
     t_full = time.perf_counter() - t0
-    td = np.sort(np.random.default_rng(123).choice(n, 300, replace=False))
+    td = np.sort(np.random.default_rng(123).choice(n, 2000, replace=False))
     d_phi, d_E = O.direct(x, q, targets=td)
 
     def rel(a, b):
         return float(np.sqrt(((a - b) ** 2).sum() / (b ** 2).sum()))
 
+    def worst(a, b):
+        if a.ndim == 1:
+            a, b = a[:, None], b[:, None]
+        m = np.linalg.norm(b, axis=1)
+        return float((np.linalg.norm(a - b, axis=1) / np.maximum(m, np.median(m))).max())
+
     cpu = {"value": n / t_full, "unit": UNIT, "cores": cores, "kind": "oracle",
            "sample": "one full oracle FMM solve of all %d particles (%.1f s), nothing extrapolated" % (n, t_full)}
     acc = {"targets": int(n), "direct_sum_targets": int(len(td)),
            "rel_l2_phi_vs_oracle": rel(phi_gpu, ref_phi), "rel_l2_field_vs_oracle": rel(E_gpu, ref_E),
+           "worst_target_phi_vs_oracle": worst(phi_gpu, ref_phi), "worst_target_field_vs_oracle": worst(E_gpu, ref_E),
            "rel_l2_phi_vs_direct": rel(phi_gpu[td], d_phi),
            "oracle_rel_l2_phi_vs_direct": rel(ref_phi[td], d_phi),
-           "rel_l2_field_vs_direct": rel(E_gpu[td], d_E)}
+           "rel_l2_field_vs_direct": rel(E_gpu[td], d_E),
+           "oracle_rel_l2_field_vs_direct": rel(ref_E[td], d_E)}
     if phi_by_order:
         by = {"p%d" % po: rel(ph[td], d_phi) for po, ph in sorted(phi_by_order.items())}
         reach = [po for po, ph in sorted(phi_by_order.items()) if rel(ph[td], d_phi) <= 1e-7]
@@ -879,9 +974,12 @@ def main():
     ap.add_argument("--no-modes", action="store_true", help="skip the MIXED / FP64 comparison runs")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-peaks", action="store_true", help="skip the unit-rate probes (dafmm_probe_peak)")
     ap.add_argument("--no-workloads", action="store_true",
                     help="skip the adaptive, batched and serving workloads (N = 1 only)")
     ap.add_argument("--serving-requests", type=int, default=200)
+    ap.add_argument("--adaptive-n", type=int, default=0, help="particles of the adaptive workload (0: 4e6)")
+    ap.add_argument("--adaptive-modes", default="mixed,fp32", help="precision modes of the adaptive workload")
     ap.add_argument("--sections", default="adaptive,batch,serving,operators,leafsize",
                     help="comma-separated extra workloads at N = 1: adaptive, batch, serving, operators, leafsize")
     args = ap.parse_args()

@@ -242,6 +242,27 @@ int dafmm_debug_expire_wait(dafmm_ctx* ctx, void* stream);
  *   (other streams, other host threads) race, so the caller must order them. */
 int dafmm_eval_noalloc(dafmm_tree* tree, int order, double* phi, double* field, void* stream);
 
+/* Unit rates of a GPU, measured (the paper has no counterpart: these are the denominators of
+ * the rooflines of the kernels bound by neither HBM nor the BF16 tensor rate).  Runs one probe
+ * kernel of the given kind on `device` for about 20-100 ms after one shorter warm-up launch,
+ * timed with CUDA events, and returns in *rate the counted operations per second of the whole
+ * GPU and in *ms (if not NULL) the timed launch's duration:
+ *   DAFMM_PEAK_FFMA      FP32 FMA, 2 flops each            DAFMM_PEAK_FFMA2  packed FP32x2 FMA, 4 flops each
+ *   DAFMM_PEAK_DFMA      FP64 FMA, 2 flops each            DAFMM_PEAK_RSQRT  rsqrt.approx.f32 results
+ *   DAFMM_PEAK_MMA_TF32  tcgen05.mma kind::tf32 flops      DAFMM_PEAK_MMA_F16 tcgen05.mma kind::f16 flops
+ * (ALU probes: 16 independent dependency chains per thread, 8 blocks of 256 threads per SM;
+ * MMA probes: one CTA per SM issuing M=128 N=256 MMAs from shared memory into TMEM.)  The
+ * clocks are whatever the GPU runs at: the caller records them.  Errors: DAFMM_ERR_INVALID_ARG
+ * (unknown kind, NULL rate, bad device), DAFMM_ERR_CUDA (a launch or copy failed),
+ * DAFMM_ERR_TIMEOUT (the MMA probe's bounded wait for its MMAs gave up). */
+#define DAFMM_PEAK_FFMA 0
+#define DAFMM_PEAK_FFMA2 1
+#define DAFMM_PEAK_DFMA 2
+#define DAFMM_PEAK_RSQRT 3
+#define DAFMM_PEAK_MMA_TF32 4
+#define DAFMM_PEAK_MMA_F16 5
+int dafmm_probe_peak(int device, int kind, double* rate, double* ms);
+
 /* Device bytes an evaluation of a tree with these parameters needs (an upper estimate). */
 size_t dafmm_footprint(int64_t n, int order, int uniform_depth, int max_leaf, int precision);
 

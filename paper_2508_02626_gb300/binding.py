@@ -45,6 +45,7 @@ SIGNATURES = {
     "dafmm_sync": (_i, [_vp, _vp]),
     "dafmm_debug_expire_wait": (_i, [_vp, _vp]),
     "dafmm_eval_noalloc": (_i, [_vp, _i, _vp, _vp, _vp]),
+    "dafmm_probe_peak": (_i, [_i, _i, ctypes.POINTER(_d), ctypes.POINTER(_d)]),
     "dafmm_debug_level": (_i64, [_vp, _i, _i, _vp, _i64]),
     "dafmm_last_phase_ms": (_i, [_vp, _vp]),
     "dafmm_op_p2m": (_i, [_vp, _i, _i, _i64, _vp, _vp, _vp, _vp]),
@@ -256,6 +257,19 @@ def dafmm_debug_expire_wait(ctx, stream=None):
 def dafmm_eval_noalloc(ctx, tree, order, phi=None, field=None, stream=None):
     """FP64 evaluation that allocates no device memory (order <= 6, depth <= 4, device outputs)."""
     _check(ctx, load().dafmm_eval_noalloc(tree, int(order), _ptr(phi), _ptr(field), _stream_ptr(stream)))
+
+
+PEAK_KINDS = {"ffma": 0, "ffma2": 1, "dfma": 2, "rsqrt": 3, "mma_tf32": 4, "mma_f16": 5}
+
+
+def dafmm_probe_peak(device, kind):
+    """Measured unit rate of the GPU (operations per second) and the timed launch's ms."""
+    rate, ms = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    rc = load().dafmm_probe_peak(int(device), PEAK_KINDS[kind] if isinstance(kind, str) else int(kind),
+                                 ctypes.byref(rate), ctypes.byref(ms))
+    if rc != DAFMM_OK:
+        raise DafmmError(rc, "dafmm_probe_peak(%s) failed" % kind)
+    return rate.value, ms.value
 
 
 DEBUG_ARRAYS = {"M": 0, "L": 1, "Mhi": 2, "Mlo": 3, "Lhi": 4, "Llo": 5}

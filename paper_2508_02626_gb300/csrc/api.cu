@@ -593,7 +593,7 @@ __global__ void k_to_float(const double* __restrict__ a, float* __restrict__ b, 
 
 size_t tree_bytes(int64_t n, int depth) {
     const size_t nl = level_boxes(depth);
-    return (size_t)n * (4 * sizeof(double) + sizeof(int)) + xq_records(n, (int64_t)nl) * sizeof(float4) +
+    return (size_t)n * (4 * sizeof(double) + sizeof(int)) + 2 * xq_records(n, (int64_t)nl) * sizeof(float4) +
            (nl + 1) * sizeof(int);
 }
 
@@ -630,6 +630,7 @@ AdaptiveView aview(const dafmm_tree* t) {
     v.xq0 = t->a_xq0;
     v.x = t->x; v.y = t->y; v.z = t->z; v.q = t->q;
     v.xq = t->xq;
+    v.xl = t->xq ? t->xq + t->xq_n4 : nullptr;
     v.perm = t->perm;
     return v;
 }
@@ -869,10 +870,10 @@ int build_adaptive(dafmm_ctx* c, dafmm_tree* t, const double* dxyz, const double
     if (e != cudaSuccess) return cuda_fail(c, e, "leaves");
     // FP32 records: leaves in list order take consecutive even record ranges (at most one
     // padding record per leaf)
-    dev_free(c, t->xq, t->xq_n4 * sizeof(float4));
+    dev_free(c, t->xq, 2 * t->xq_n4 * sizeof(float4));
     t->xq = nullptr;
     t->xq_n4 = xq_records(t->n, nl);
-    if ((rc = dev_alloc(c, (void**)&t->xq, t->xq_n4 * sizeof(float4), "particles"))) {
+    if ((rc = dev_alloc(c, (void**)&t->xq, 2 * t->xq_n4 * sizeof(float4), "particles"))) {
         t->xq_n4 = 0;
         return rc;
     }
@@ -1243,7 +1244,7 @@ int dafmm_build_tree(dafmm_ctx* c, const double* xyz, const double* q, int64_t n
     if (!rc) rc = dev_alloc(c, (void**)&t->q, N * sizeof(double), "particles");
     if (!rc) {
         t->xq_n4 = xq_records(n, t->nleaf);
-        rc = dev_alloc(c, (void**)&t->xq, t->xq_n4 * sizeof(float4), "particles");
+        rc = dev_alloc(c, (void**)&t->xq, 2 * t->xq_n4 * sizeof(float4), "particles");
     }
     if (!rc) rc = dev_alloc(c, (void**)&t->perm, N * sizeof(int), "particles");
     if (!rc) rc = dev_alloc(c, (void**)&t->leaf_start, ((size_t)t->nleaf + 1) * sizeof(int), "leaves");
@@ -1384,7 +1385,7 @@ int dafmm_tree_free(dafmm_tree* t) {
     dev_free(c, t->y, N * sizeof(double));
     dev_free(c, t->z, N * sizeof(double));
     dev_free(c, t->q, N * sizeof(double));
-    dev_free(c, t->xq, t->xq_n4 * sizeof(float4));
+    dev_free(c, t->xq, 2 * t->xq_n4 * sizeof(float4));
     dev_free(c, t->perm, N * sizeof(int));
     dev_free(c, t->leaf_start, ((size_t)t->nleaf + 1) * sizeof(int));
     dev_free(c, t->out_scratch, t->out_scratch_bytes);
@@ -1822,10 +1823,10 @@ size_t dafmm_footprint(int64_t n, int order, int uniform_depth, int max_leaf, in
     const size_t ncp = ncp_of(order), nc = ncoef_of(order);
     if (uniform_depth < 0) {
         // adaptive: about 16 n / max_leaf boxes; per box its hierarchy record, list entries
-        // (U, W and X, about 64 on average), its first FP32 record, a padding record and the
-        // expansions
+        // (U, W and X, about 64 on average), its first FP32 record, a padding record (with its
+        // remainder record) and the expansions
         const size_t nbox = 2 + (size_t)(16 * n) / (size_t)(max_leaf > 0 ? max_leaf : 1);
-        b += nbox * (kBoxInts * 4 + 64 * 4 + 24 + 16 + ncp * (8 + 8 + 4));
+        b += nbox * (kBoxInts * 4 + 64 * 4 + 24 + 32 + ncp * (8 + 8 + 4));
         b += (size_t)kNumKeys * nc * ncp * 12;
         b += (size_t)n * 12 + radix_sort_temp_bytes(n) + radix_sort_temp_bytes((int64_t)nbox);
         return b;

@@ -62,8 +62,8 @@ struct dafmm_tree {
     int nleaf = 1;
     int max_per_leaf = 0;
     double *x = nullptr, *y = nullptr, *z = nullptr, *q = nullptr;
-    float4* xq = nullptr;
-    size_t xq_n4 = 0;  // float4s held by xq
+    float4* xq = nullptr;  // 2 * xq_n4 float4s: FP32 records, then their remainders
+    size_t xq_n4 = 0;      // float4s of one half of xq
     int* perm = nullptr;
     int* leaf_start = nullptr;
     Expansions ex;

@@ -639,32 +639,84 @@ __global__ void __launch_bounds__(256, 2) k_m2l_rot_a(const double* __restrict__
 
 // ---- leaves: P2P over the 27 neighbours + L2P --------------------------------------------------
 // 1/sqrt(x) of the PTX instruction rsqrt.approx.ftz.f32 (relative error about 2^-23, the
-// size of an FP32 rounding, so no Newton step is needed); 0 for x below the smallest normal
-// float, which covers coincident points (r = 0 contributes nothing, as everywhere else)
-__device__ __forceinline__ float rsqrt_or_zero(float x) {
+// size of an FP32 rounding, so no Newton step is needed)
+__device__ __forceinline__ float rsqrt_approx(float x) {
     float y;
     asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+// the same, and 0 for x below the smallest normal float, which covers coincident points
+// (r = 0 contributes nothing, as everywhere else)
+__device__ __forceinline__ float rsqrt_or_zero(float x) {
+    const float y = rsqrt_approx(x);
     return x >= 1.17549435e-38f ? y : 0.f;
 }
 
-// record pairs [p0, p1) (records 2p and 2p + 1) acting on the target (tx, ty, tz), given in the
-// records' frame, with both halves of every step in one packed FP32x2 instruction: per half the
-// roundings of  e = t - s,  r2 = fma(ex, ex, fma(ey, ey, ez ez)),  qr = q / r,  qr3 = qr / r^2;
-// the halves accumulate separately in P (potential) and X, Y, Z (field without its sign
-// convention)
-__device__ __forceinline__ void p2p_pairs(const float4* __restrict__ xq, int p0, int p1, float2 tx, float2 ty,
-                                          float2 tz, float2& P, float2& X, float2& Y, float2& Z) {
+// Shared-memory source list of the near field, in the target leaf's frame: pair p of the list
+// (records 2p and 2p + 1) occupies four float4s from buf[4p]:
+//   (X, X', Y, Y')  (Z, Z', Q, Q')      offsets rounded to FP32 and the charges
+//   (x, x', y, y')  (z, z', 0, 0)       their FP32 remainders
+__device__ __forceinline__ void list_store(float4* buf, int j, float X, float Y, float Z, float Q, float xl,
+                                           float yl, float zl) {
+    float* f = reinterpret_cast<float*>(buf) + 16 * (j >> 1) + (j & 1);
+    f[0] = X;
+    f[2] = Y;
+    f[4] = Z;
+    f[6] = Q;
+    f[8] = xl;
+    f[10] = yl;
+    f[12] = zl;
+    f[14] = 0.f;
+}
+// a record that adds exactly nothing (q = 0, far from every target: finite 1/r, no guard needed)
+__device__ __forceinline__ void list_store_null(float4* buf, int j) {
+    list_store(buf, j, 4096.f, 4096.f, 4096.f, 0.f, 0.f, 0.f, 0.f);
+}
+
+// (H, L) = hi + lo shifted by d with the rounding of hi + d moved into L (Fast2Sum: exact when
+// |d| >= |hi| or d = 0, which holds for the integer leaf offsets d in {-1, 0, 1} of a uniform
+// tree and |hi| <= 1/2)
+__device__ __forceinline__ void shift_exact(float hi, float lo, float d, float& H, float& L) {
+    H = hi + d;
+    L = lo + (hi - (H - d));
+}
+// (H, L) = (hi + lo) * r + (oh + ol) for a power of two r, with the rounding of hi * r + oh
+// moved into L (TwoSum: exact for any ordering of the two terms)
+__device__ __forceinline__ void scale_shift_exact(float hi, float lo, float r, float oh, float ol, float& H,
+                                                  float& L) {
+    const float a = hi * r;  // exact
+    H = a + oh;
+    const float bb = H - a;
+    const float err = (a - (H - bb)) + (oh - bb);
+    L = fmaf(lo, r, err + ol);
+}
+
+// list pairs [p0, p1) acting on the target t = T + tl (T: rounded offsets, tl: remainders,
+// in the list's frame), both halves of every step in one packed FP32x2 instruction: per half
+//   e = (T - S) + (tl - sl),  r2 = fma(ex, ex, fma(ey, ey, ez ez)),  qr = q / r,  qr3 = qr / r^2
+// and the halves accumulate separately in P (potential) and X, Y, Z (field without its sign
+// convention).  e carries the difference of the two particles to a few FP32 roundings of
+// itself however close they are.  GUARD (the target's own leaf, which holds the target and
+// any coincident particles) gives r = 0 no contribution; without it r2 starts from the
+// smallest normal float, so distinct particles -- which never coincide across leaves --
+// always give a finite 1/r.
+template <bool GUARD>
+__device__ __forceinline__ void p2p_pairs(const float4* __restrict__ buf, int p0, int p1, float2 tx, float2 ty,
+                                          float2 tz, float2 lx, float2 ly, float2 lz, float2& P, float2& X,
+                                          float2& Y, float2& Z) {
     const float2 m1 = make_float2(-1.f, -1.f);
+    const float2 tiny = make_float2(1.17549435e-38f, 1.17549435e-38f);
 #pragma unroll 4
     for (int p = p0; p < p1; ++p) {
-        const float4 A = xq[2 * p], B = xq[2 * p + 1];
-        const float2 ex = __ffma2_rn(make_float2(A.x, A.y), m1, tx);
-        const float2 ey = __ffma2_rn(make_float2(A.z, A.w), m1, ty);
-        const float2 ez = __ffma2_rn(make_float2(B.x, B.y), m1, tz);
-        float2 r2 = __fmul2_rn(ez, ez);
+        const float4 A = buf[4 * p], B = buf[4 * p + 1], C = buf[4 * p + 2], D = buf[4 * p + 3];
+        const float2 ex = __fadd2_rn(__ffma2_rn(make_float2(A.x, A.y), m1, tx), __ffma2_rn(make_float2(C.x, C.y), m1, lx));
+        const float2 ey = __fadd2_rn(__ffma2_rn(make_float2(A.z, A.w), m1, ty), __ffma2_rn(make_float2(C.z, C.w), m1, ly));
+        const float2 ez = __fadd2_rn(__ffma2_rn(make_float2(B.x, B.y), m1, tz), __ffma2_rn(make_float2(D.x, D.y), m1, lz));
+        float2 r2 = GUARD ? __fmul2_rn(ez, ez) : __ffma2_rn(ez, ez, tiny);
         r2 = __ffma2_rn(ey, ey, r2);
         r2 = __ffma2_rn(ex, ex, r2);
-        const float2 ir = make_float2(rsqrt_or_zero(r2.x), rsqrt_or_zero(r2.y));
+        const float2 ir = GUARD ? make_float2(rsqrt_or_zero(r2.x), rsqrt_or_zero(r2.y))
+                                : make_float2(rsqrt_approx(r2.x), rsqrt_approx(r2.y));
         const float2 qr = __fmul2_rn(make_float2(B.z, B.w), ir);
         const float2 qr3 = __fmul2_rn(qr, __fmul2_rn(ir, ir));
         P = __fadd2_rn(P, qr);
@@ -689,7 +741,46 @@ struct CompSums {
 
 
 // records per shared-memory segment of the neighbour list (per warp; 8 KB)
-constexpr int kLeafSeg = 512;
+constexpr int kLeafSeg = 256;
+
+// the pairwise sums of one segment of the list: pairs [pa, pe) for this lane's target, those
+// below pown from the target's own leaf (guarded), FP32 partial sums over at most 64 sources
+// folded into the compensated sums
+__device__ __forceinline__ void p2p_segment(const float4* __restrict__ buf, int pa, int pe, int pown, float2 tx,
+                                            float2 ty, float2 tz, float2 lx, float2 ly, float2 lz, CompSums& cs) {
+    for (int pb = pa; pb < pe; pb += 32) {
+        const int pc = min(pe, pb + 32);
+        const int pm = max(pb, min(pc, pown));
+        float2 P = make_float2(0.f, 0.f), X = P, Y = P, Z = P;
+        if (pb < pm) p2p_pairs<true>(buf, pb, pm, tx, ty, tz, lx, ly, lz, P, X, Y, Z);
+        if (pm < pc) p2p_pairs<false>(buf, pm, pc, tx, ty, tz, lx, ly, lz, P, X, Y, Z);
+        two_sum_add(cs.ph, cs.pl, P.x + P.y);
+        two_sum_add(cs.xh, cs.xl, X.x + X.y);
+        two_sum_add(cs.yh, cs.yl, Y.x + Y.y);
+        two_sum_add(cs.zh, cs.zl, Z.x + Z.y);
+    }
+}
+
+// the upper half-warp's sums join the lower one's (passes whose sources were split between
+// the half-warps)
+__device__ __forceinline__ void join_halves(CompSums& cs) {
+    float v[8] = {cs.ph, cs.pl, cs.xh, cs.xl, cs.yh, cs.yl, cs.zh, cs.zl};
+#pragma unroll
+    for (int j = 0; j < 8; ++j) v[j] = __shfl_down_sync(0xffffffffu, v[j], 16);
+    two_sum_add(cs.ph, cs.pl, v[0]);
+    cs.pl += v[1];
+    two_sum_add(cs.xh, cs.xl, v[2]);
+    cs.xl += v[3];
+    two_sum_add(cs.yh, cs.yl, v[4]);
+    cs.yl += v[5];
+    two_sum_add(cs.zh, cs.zl, v[6]);
+    cs.zl += v[7];
+}
+
+// the neighbour slot (0..26, slot 13 = the leaf itself) held by lane k of the list: the leaf
+// itself first, so that its records -- the only ones that can coincide with a target -- form
+// the guarded head of the list
+__device__ __forceinline__ int own_first_slot(int k) { return k == 0 ? 13 : (k <= 13 ? k - 1 : k); }
 
 template <class T>
 __global__ void __launch_bounds__(128) k_leaf(TreeView tv, const double* __restrict__ Lleaf,
@@ -718,31 +809,40 @@ __global__ void __launch_bounds__(128) k_leaf(TreeView tv, const double* __restr
             }
         }
     }
-    // the 27 neighbour leaves' particle ranges, one per lane (empty outside the domain), and
-    // the first FP32 record of each
-    int nb_s0 = 0, nb_s1 = 0, nb_r0 = 0;
-    if (lane < 27) {
-        const int dx = lane % 3 - 1, dy = (lane / 3) % 3 - 1, dz = lane / 9 - 1;
-        const int na = a + dx, nb = b + dy, nc2 = c + dz;
-        if (na >= 0 && nb >= 0 && nc2 >= 0 && na < nside && nb < nside && nc2 < nside) {
-            const int nl = octmajor_index(tv.depth, na, nb, nc2);
-            nb_s0 = tv.leaf_start[nl];
-            nb_s1 = tv.leaf_start[nl + 1];
-            nb_r0 = xq_base(nb_s0, nl);
+    // FP32: the 27 neighbour leaves' particle ranges, one per lane (empty outside the domain),
+    // and the first FP32 record of each, laid end to end as one list: the leaf's own records
+    // first (lane 0), completed to an even count by a null record; lane k's neighbour starts
+    // at nb_off (exclusive scan of the counts over the lanes), nb_tot records in all, the
+    // first own_pairs pairs the leaf's own
+    int nb_n = 0, nb_r0 = 0, nb_off = 0, nb_tot = 0, n_own = 0, own_pad = 0, own_pairs = 0;
+    if constexpr (sizeof(T) == 4) {
+        int nb_s0 = 0, nb_s1 = 0;
+        if (lane < 27) {
+            const int slot = own_first_slot(lane);
+            const int dx = slot % 3 - 1, dy = (slot / 3) % 3 - 1, dz = slot / 9 - 1;
+            const int na = a + dx, nb = b + dy, nc2 = c + dz;
+            if (na >= 0 && nb >= 0 && nc2 >= 0 && na < nside && nb < nside && nc2 < nside) {
+                const int nl = octmajor_index(tv.depth, na, nb, nc2);
+                nb_s0 = tv.leaf_start[nl];
+                nb_s1 = tv.leaf_start[nl + 1];
+                nb_r0 = xq_base(nb_s0, nl);
+            }
         }
+        nb_n = nb_s1 - nb_s0;
+        nb_off = nb_n;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, nb_off, d);
+            if (lane >= d) nb_off += v;
+        }
+        n_own = __shfl_sync(0xffffffffu, nb_n, 0);
+        own_pad = n_own & 1;
+        nb_tot = __shfl_sync(0xffffffffu, nb_off, 31) + own_pad;
+        nb_off -= nb_n;
+        if (lane > 0) nb_off += own_pad;
+        own_pairs = (n_own + 1) >> 1;
     }
     const int r_own = xq_base(i0, leaf) - i0;  // record of sorted position t: t + r_own
-    // the neighbours' records laid end to end: lane k's neighbour starts at nb_off (exclusive
-    // scan of the counts over the lanes), nb_tot records in all
-    const int nb_n = nb_s1 - nb_s0;
-    int nb_off = nb_n;
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-        const int v = __shfl_up_sync(0xffffffffu, nb_off, d);
-        if (lane >= d) nb_off += v;
-    }
-    const int nb_tot = __shfl_sync(0xffffffffu, nb_off, 31);
-    nb_off -= nb_n;
     for (int base = i0; base < i1; base += 32) {
         // FP32: a pass of at most 16 targets splits the sources between the two half-warps,
         // lane l and lane l + 16 taking the same target
@@ -775,64 +875,53 @@ __global__ void __launch_bounds__(128) k_leaf(TreeView tv, const double* __restr
                         }
                     }
         } else {
-            const float4 pt = xq_load(tv.xq, tt + r_own);
+            const float4* xl = tv.xq + xq_records(tv.n, tv.nleaf);  // the remainder records
+            const float4 pt = xq_load(tv.xq, tt + r_own), pl = xq_load(xl, tt + r_own);
             CompSums cs;
             // The neighbours' records are copied into one shared-memory list, shifted into this
-            // leaf's frame (source + neighbour offset, in leaf widths) and pair-interleaved, in
-            // segments of up to kLeafSeg records; the pairwise sum then runs over the whole
-            // list.  A pass of at most 16 targets gives each half-warp half of the pairs.
-            __shared__ __align__(16) float4 s_list[4][kLeafSeg];
+            // leaf's frame (source + neighbour offset, in leaf widths, exactly: the rounding of
+            // the shift joins the remainder), in segments of up to kLeafSeg records; the pairwise
+            // sum then runs over the whole list.  A pass of at most 16 targets gives each
+            // half-warp half of the pairs.
+            __shared__ __align__(16) float4 s_list[4][2 * kLeafSeg];
             float4* buf = s_list[threadIdx.y];
             const int g = split ? lane >> 4 : 0;
             const float2 tx2 = make_float2(pt.x, pt.x), ty2 = make_float2(pt.y, pt.y),
                          tz2 = make_float2(pt.z, pt.z);
+            const float2 lx2 = make_float2(pl.x, pl.x), ly2 = make_float2(pl.y, pl.y),
+                         lz2 = make_float2(pl.z, pl.z);
             for (int seg0 = 0; seg0 < nb_tot; seg0 += kLeafSeg) {
-                const int segn = min(kLeafSeg, nb_tot - seg0);
+                const int segn = min(kLeafSeg, nb_tot - seg0), seg1 = seg0 + segn;
                 __syncwarp();  // the previous segment is no longer read
-                for (int k = 0; k < 27; ++k) {
+                // the neighbours whose records fall into this segment
+                unsigned ov = __ballot_sync(0xffffffffu, lane < 27 && nb_n > 0 && nb_off < seg1 && nb_off + nb_n > seg0);
+                while (ov) {
+                    const int k = __ffs(ov) - 1;
+                    ov &= ov - 1;
                     const int o = __shfl_sync(0xffffffffu, nb_off, k), n = __shfl_sync(0xffffffffu, nb_n, k);
                     const int r0 = __shfl_sync(0xffffffffu, nb_r0, k);
-                    const int lo = max(o, seg0), hi = min(o + n, seg0 + segn);
-                    const float dx = (float)(k % 3 - 1), dy = (float)((k / 3) % 3 - 1), dz = (float)(k / 9 - 1);
+                    const int slot = own_first_slot(k);
+                    const int lo = max(o, seg0), hi = min(o + n, seg1);
+                    const float dx = (float)(slot % 3 - 1), dy = (float)((slot / 3) % 3 - 1), dz = (float)(slot / 9 - 1);
                     for (int i = lo + lane; i < hi; i += 32) {
-                        const float4 rec = xq_load(tv.xq, r0 + (i - o));
-                        const int j = i - seg0;
-                        float* f = reinterpret_cast<float*>(buf) + 8 * (j >> 1) + (j & 1);
-                        f[0] = rec.x + dx;
-                        f[2] = rec.y + dy;
-                        f[4] = rec.z + dz;
-                        f[6] = rec.w;
+                        const float4 rec = xq_load(tv.xq, r0 + (i - o)), rl = xq_load(xl, r0 + (i - o));
+                        float X, Y, Z, XL, YL, ZL;
+                        shift_exact(rec.x, rl.x, dx, X, XL);
+                        shift_exact(rec.y, rl.y, dy, Y, YL);
+                        shift_exact(rec.z, rl.z, dz, Z, ZL);
+                        list_store(buf, i - seg0, X, Y, Z, rec.w, XL, YL, ZL);
                     }
                 }
-                if ((segn & 1) && lane == 0) {  // a zero record completes the last pair
-                    float* f = reinterpret_cast<float*>(buf) + 8 * (segn >> 1) + 1;
-                    f[0] = f[2] = f[4] = f[6] = 0.f;
+                if (lane == 0) {
+                    if (own_pad && n_own >= seg0 && n_own < seg1) list_store_null(buf, n_own - seg0);
+                    if (segn & 1) list_store_null(buf, segn);  // completes the last pair
                 }
                 __syncwarp();
                 const int np = (segn + 1) >> 1, h = split ? (np + 1) >> 1 : np;
                 const int pa = g ? h : 0, pe = g ? np : h;
-                for (int pb = pa; pb < pe; pb += 32) {
-                    float2 P = make_float2(0.f, 0.f), X = P, Y = P, Z = P;
-                    p2p_pairs(buf, pb, min(pe, pb + 32), tx2, ty2, tz2, P, X, Y, Z);
-                    two_sum_add(cs.ph, cs.pl, P.x + P.y);
-                    two_sum_add(cs.xh, cs.xl, X.x + X.y);
-                    two_sum_add(cs.yh, cs.yl, Y.x + Y.y);
-                    two_sum_add(cs.zh, cs.zl, Z.x + Z.y);
-                }
+                p2p_segment(buf, pa, pe, own_pairs - (seg0 >> 1), tx2, ty2, tz2, lx2, ly2, lz2, cs);
             }
-            if (split) {  // the upper half-warp's sums join the lower one's
-                float v[8] = {cs.ph, cs.pl, cs.xh, cs.xl, cs.yh, cs.yl, cs.zh, cs.zl};
-#pragma unroll
-                for (int j = 0; j < 8; ++j) v[j] = __shfl_down_sync(0xffffffffu, v[j], 16);
-                two_sum_add(cs.ph, cs.pl, v[0]);
-                cs.pl += v[1];
-                two_sum_add(cs.xh, cs.xl, v[2]);
-                cs.xl += v[3];
-                two_sum_add(cs.yh, cs.yl, v[4]);
-                cs.yl += v[5];
-                two_sum_add(cs.zh, cs.zl, v[6]);
-                cs.zl += v[7];
-            }
+            if (split) join_halves(cs);
             const double ih = tv.inv_h_leaf, ih2 = ih * ih;
             fphi = ((double)cs.ph + (double)cs.pl) * ih;
             fx = ((double)cs.xh + (double)cs.xl) * ih2;
@@ -1100,7 +1189,7 @@ __global__ void __launch_bounds__(256) k_leaf_a(AdaptiveView av, const int* __re
                                                 const double* __restrict__ L, const double* __restrict__ M,
                                                 double* __restrict__ phi, double* __restrict__ field) {
     __shared__ float s_rows[8][2][NCP];  // per warp: the W box's multipoles and the leaf's locals, FP32
-    extern __shared__ __align__(16) float4 s_list_a[];  // FP32: per warp kLeafSeg records
+    extern __shared__ __align__(16) float4 s_list_a[];  // FP32: per warp kLeafSeg records (2 float4s each)
     const int lane = threadIdx.x;
     const int li = blockIdx.x * blockDim.y + threadIdx.y;
     if (li >= nleaves) return;
@@ -1144,73 +1233,69 @@ __global__ void __launch_bounds__(256) k_leaf_a(AdaptiveView av, const int* __re
                 }
             }
         } else {
-            const float4 pt = xq_load(av.xq, av.xq0[b] + (tt - i0));
+            const float4 pt = xq_load(av.xq, av.xq0[b] + (tt - i0)), pl = xq_load(av.xl, av.xq0[b] + (tt - i0));
             CompSums acc;  // in leaf widths of this leaf
             // The U-list leaves' records are copied into one shared-memory list in this leaf's
-            // frame (source x h_s / h + centre offset / h; h_s / h is a power of two), in
+            // frame (source x h_s / h + centre offset / h, exactly: h_s / h is a power of two and
+            // the rounding of the sum joins the remainder), the leaf's own records first, in
             // segments of up to kLeafSeg records; the pairwise sum runs over each segment.
-            float4* buf = s_list_a + (size_t)threadIdx.y * kLeafSeg;
+            float4* buf = s_list_a + (size_t)threadIdx.y * 2 * kLeafSeg;
             const int g = split ? lane >> 4 : 0;
             const float2 tx2 = make_float2(pt.x, pt.x), ty2 = make_float2(pt.y, pt.y),
                          tz2 = make_float2(pt.z, pt.z);
-            int fill = 0;
+            const float2 lx2 = make_float2(pl.x, pl.x), ly2 = make_float2(pl.y, pl.y),
+                         lz2 = make_float2(pl.z, pl.z);
+            int fill = 0, done = 0, own_end = 0;  // records in the segment, before it, of the own leaf
             auto flush = [&]() {
-                if ((fill & 1) && lane == 0) {  // a zero record completes the last pair
-                    float* f = reinterpret_cast<float*>(buf) + 8 * (fill >> 1) + 1;
-                    f[0] = f[2] = f[4] = f[6] = 0.f;
-                }
+                if ((fill & 1) && lane == 0) list_store_null(buf, fill);  // completes the last pair
                 __syncwarp();
                 const int np = (fill + 1) >> 1, hp = split ? (np + 1) >> 1 : np;
                 const int pa = g ? hp : 0, pe = g ? np : hp;
-                for (int pb = pa; pb < pe; pb += 32) {
-                    float2 P = make_float2(0.f, 0.f), X = P, Y = P, Z = P;
-                    p2p_pairs(buf, pb, min(pe, pb + 32), tx2, ty2, tz2, P, X, Y, Z);
-                    two_sum_add(acc.ph, acc.pl, P.x + P.y);
-                    two_sum_add(acc.xh, acc.xl, X.x + X.y);
-                    two_sum_add(acc.yh, acc.yl, Y.x + Y.y);
-                    two_sum_add(acc.zh, acc.zl, Z.x + Z.y);
-                }
+                p2p_segment(buf, pa, pe, (own_end - done) >> 1, tx2, ty2, tz2, lx2, ly2, lz2, acc);
                 __syncwarp();  // the segment is no longer read
+                done += fill;
                 fill = 0;
             };
-            for (int ui = u0; ui < u1; ++ui) {
-                const int sb = av.u_idx[ui];
+            auto add_leaf = [&](int sb) {
                 double scx, scy, scz, sh;
                 abox_geom(av, sb, scx, scy, scz, sh);
                 const float r = (float)(sh * ih);
-                const float offx = (float)((scx - cx) * ih), offy = (float)((scy - cy) * ih),
-                            offz = (float)((scz - cz) * ih);
+                const double ox = (scx - cx) * ih, oy = (scy - cy) * ih, oz = (scz - cz) * ih;
+                const float ohx = (float)ox, ohy = (float)oy, ohz = (float)oz;
+                const float olx = (float)(ox - (double)ohx), oly = (float)(oy - (double)ohy),
+                            olz = (float)(oz - (double)ohz);
                 const int r0 = av.xq0[sb], n = av.pend[sb] - av.pbeg[sb];
                 for (int i0s = 0; i0s < n;) {
                     const int take = min(n - i0s, kLeafSeg - fill);
                     for (int i = lane; i < take; i += 32) {
-                        const float4 rec = xq_load(av.xq, r0 + i0s + i);
-                        const int j = fill + i;
-                        float* f = reinterpret_cast<float*>(buf) + 8 * (j >> 1) + (j & 1);
-                        f[0] = fmaf(r, rec.x, offx);
-                        f[2] = fmaf(r, rec.y, offy);
-                        f[4] = fmaf(r, rec.z, offz);
-                        f[6] = rec.w;
+                        const float4 rec = xq_load(av.xq, r0 + i0s + i), rl = xq_load(av.xl, r0 + i0s + i);
+                        float X, Y, Z, XL, YL, ZL;
+                        scale_shift_exact(rec.x, rl.x, r, ohx, olx, X, XL);
+                        scale_shift_exact(rec.y, rl.y, r, ohy, oly, Y, YL);
+                        scale_shift_exact(rec.z, rl.z, r, ohz, olz, Z, ZL);
+                        list_store(buf, fill + i, X, Y, Z, rec.w, XL, YL, ZL);
                     }
                     fill += take;
                     i0s += take;
                     if (fill == kLeafSeg) flush();
                 }
+            };
+            // the leaf itself (the only records that can coincide with a target), completed to
+            // an even count by a null record, then the other U-list leaves
+            const int n_own = i1 - i0;
+            own_end = n_own + (n_own & 1);  // (set first: a long own leaf flushes segments)
+            add_leaf(b);
+            if (n_own & 1) {
+                if (lane == 0) list_store_null(buf, fill);  // fill < kLeafSeg here
+                ++fill;
+                if (fill == kLeafSeg) flush();
+            }
+            for (int ui = u0; ui < u1; ++ui) {
+                const int sb = av.u_idx[ui];
+                if (sb != b) add_leaf(sb);
             }
             if (fill > 0) flush();
-            if (split) {  // the upper half-warp's sums join the lower one's
-                float v[8] = {acc.ph, acc.pl, acc.xh, acc.xl, acc.yh, acc.yl, acc.zh, acc.zl};
-#pragma unroll
-                for (int j = 0; j < 8; ++j) v[j] = __shfl_down_sync(0xffffffffu, v[j], 16);
-                two_sum_add(acc.ph, acc.pl, v[0]);
-                acc.pl += v[1];
-                two_sum_add(acc.xh, acc.xl, v[2]);
-                acc.xl += v[3];
-                two_sum_add(acc.yh, acc.yl, v[4]);
-                acc.yl += v[5];
-                two_sum_add(acc.zh, acc.zl, v[6]);
-                acc.zl += v[7];
-            }
+            if (split) join_halves(acc);
             fphi = ((double)acc.ph + (double)acc.pl) * ih;
             fx = ((double)acc.xh + (double)acc.xl) * ih * ih;
             fy = ((double)acc.yh + (double)acc.yl) * ih * ih;
@@ -1539,7 +1624,7 @@ static cudaError_t leaf_a_launch(const AdaptiveView& av, const int* leaves, int 
     if (prec == DAFMM_FP64) {
         k_leaf_a<double><<<grd, blk, 0, s>>>(av, leaves, nleaves, L, M, phi, field);
     } else {
-        const size_t smem = (size_t)warps * kLeafSeg * sizeof(float4);
+        const size_t smem = (size_t)warps * 2 * kLeafSeg * sizeof(float4);
         cudaError_t e = cudaFuncSetAttribute(k_leaf_a<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         k_leaf_a<float><<<grd, blk, smem, s>>>(av, leaves, nleaves, L, M, phi, field);

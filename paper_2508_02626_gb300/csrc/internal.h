@@ -29,6 +29,8 @@ struct TreeView {
     const double *x, *y, *z, *q;  // sorted by leaf, FP64
     const float4* xq;             // leaf-scaled offsets (x - c)/h and charge, FP32, pair-interleaved
                                   // records from xq_base(leaf_start[l], l) per leaf l
+                                  // and, xq_records(n, nleaf) float4s further, the FP32
+                                  // remainders of those offsets (same records)
     const int* perm;              // sorted position -> input index
     const int* leaf_start;        // nleaf + 1
     int locals_f32;               // the leaf locals passed to the leaf kernel are FP32 rows
@@ -157,6 +159,7 @@ struct OrderOps {
 };
 
 const OrderOps* order_ops(int p);
+
 // one function per translation unit fmm_p*.cu
 #define DAFMM_DECLARE_ORDER(P) const OrderOps* order_ops_p##P();
 DAFMM_DECLARE_ORDER(0) DAFMM_DECLARE_ORDER(1) DAFMM_DECLARE_ORDER(2) DAFMM_DECLARE_ORDER(3)

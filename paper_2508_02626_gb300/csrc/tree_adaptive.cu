@@ -474,7 +474,7 @@ cudaError_t launch_list_fill(AdaptiveBuild ab, int nbox, const int* pu, const in
 __global__ void k_gather_adaptive(const double* __restrict__ xyz, const double* __restrict__ q,
                                   const int* __restrict__ perm, AdaptiveBuild ab, const int* __restrict__ leaves,
                                   int nleaves, const double4* __restrict__ geom, const int* __restrict__ xq0,
-                                  double* x, double* y, double* z, double* qs, float4* xq) {
+                                  double* x, double* y, double* z, double* qs, float4* xq, float4* xl) {
     const int li = blockIdx.x;
     if (li >= nleaves) return;
     const int b = leaves[li];
@@ -485,8 +485,11 @@ __global__ void k_gather_adaptive(const double* __restrict__ xyz, const double* 
         const int i = perm[t];
         const double px = xyz[3 * i], py = xyz[3 * i + 1], pz = xyz[3 * i + 2], pq = q[i];
         x[t] = px; y[t] = py; z[t] = pz; qs[t] = pq;
-        xq_store(xq, xq0[b] + (t - ab.pbeg[b]), (float)((px - cx) * ih), (float)((py - cy) * ih),
-                 (float)((pz - cz) * ih), (float)pq);
+        const double ox = (px - cx) * ih, oy = (py - cy) * ih, oz = (pz - cz) * ih;
+        const float hx = (float)ox, hy = (float)oy, hz = (float)oz;
+        const int r = xq0[b] + (t - ab.pbeg[b]);
+        xq_store(xq, r, hx, hy, hz, (float)pq);
+        xq_store(xl, r, (float)(ox - (double)hx), (float)(oy - (double)hy), (float)(oz - (double)hz), 0.f);
     }
 }
 
@@ -517,10 +520,12 @@ cudaError_t launch_leaf_records(const int* leaves, int nl, const int* pbeg, cons
 cudaError_t launch_gather_adaptive(const double* xyz, const double* q, const int* perm, AdaptiveBuild ab,
                                    const int* leaves, int nleaves, const double4* geom, const int* xq0, double* x,
                                    double* y, double* z, double* qs, float4* xq, size_t xq_n4, cudaStream_t s) {
-    // the zero fill supplies the padding record of leaves with an odd particle count
-    cudaError_t e = cudaMemsetAsync(xq, 0, xq_n4 * sizeof(float4), s);
+    // the zero fill supplies the padding record of leaves with an odd particle count (both
+    // halves: the records and their remainders)
+    cudaError_t e = cudaMemsetAsync(xq, 0, 2 * xq_n4 * sizeof(float4), s);
     if (e != cudaSuccess || nleaves == 0) return e;
-    k_gather_adaptive<<<nleaves, 128, 0, s>>>(xyz, q, perm, ab, leaves, nleaves, geom, xq0, x, y, z, qs, xq);
+    k_gather_adaptive<<<nleaves, 128, 0, s>>>(xyz, q, perm, ab, leaves, nleaves, geom, xq0, x, y, z, qs, xq,
+                                              xq + xq_n4);
     return cudaGetLastError();
 }
 

@@ -41,6 +41,7 @@ struct AdaptiveView {
     const double *x, *y, *z, *q;  // sorted particles
     const float4* xq;             // offsets in the particle's own leaf, in leaf widths, and q (FP32,
                                   // pair-interleaved records, those of leaf box b from xq0[b])
+    const float4* xl;             // the FP32 remainders of those offsets, same records
     const int* xq0;               // per leaf box: its first record (even)
     const int* perm;
 };

@@ -229,7 +229,7 @@ cudaError_t radix_sort_pairs(uint64_t* keys, int* vals, int64_t n, int bits, voi
 __global__ void k_gather_uniform(const double* __restrict__ xyz, const double* __restrict__ q,
                                  const int* __restrict__ perm, int64_t n,
                                  const uint64_t* __restrict__ keys, TreeView tv, double* x, double* y,
-                                 double* z, double* qs, float4* xq) {
+                                 double* z, double* qs, float4* xq, float4* xl) {
     int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (t >= n) return;
     const int i = perm[t];
@@ -241,8 +241,11 @@ __global__ void k_gather_uniform(const double* __restrict__ xyz, const double* _
     const double cy = tv.y0 + ((double)b + 0.5) * tv.h_leaf;
     const double cz = tv.z0 + ((double)c + 0.5) * tv.h_leaf;
     const int leaf = (int)keys[t], p0 = tv.leaf_start[leaf];
-    xq_store(xq, xq_base(p0, leaf) + (int)(t - p0), (float)((px - cx) * tv.inv_h_leaf),
-             (float)((py - cy) * tv.inv_h_leaf), (float)((pz - cz) * tv.inv_h_leaf), (float)pq);
+    const double ox = (px - cx) * tv.inv_h_leaf, oy = (py - cy) * tv.inv_h_leaf, oz = (pz - cz) * tv.inv_h_leaf;
+    const float hx = (float)ox, hy = (float)oy, hz = (float)oz;
+    const int r = xq_base(p0, leaf) + (int)(t - p0);
+    xq_store(xq, r, hx, hy, hz, (float)pq);
+    xq_store(xl, r, (float)(ox - (double)hx), (float)(oy - (double)hy), (float)(oz - (double)hz), 0.f);
 }
 
 __global__ void k_leaf_ranges(const uint64_t* __restrict__ keys, int64_t n, int nleaf, int* leaf_start) {
@@ -264,12 +267,14 @@ cudaError_t launch_gather_uniform(const double* xyz, const double* q, const int*
     // leaf ranges first: the gather places each leaf's FP32 records from its first position;
     // the zero fill supplies the padding record of odd leaves
     k_leaf_ranges<<<(tv.nleaf + 1 + 255) / 256, 256, 0, s>>>(sorted_keys, n, tv.nleaf, leaf_start);
-    cudaError_t e = cudaMemsetAsync(xq, 0, xq_records(n, tv.nleaf) * sizeof(float4), s);
+    // (both halves: the records and their remainders)
+    const size_t n4 = xq_records(n, tv.nleaf);
+    cudaError_t e = cudaMemsetAsync(xq, 0, 2 * n4 * sizeof(float4), s);
     if (e != cudaSuccess) return e;
     tv.leaf_start = leaf_start;
     if (n > 0)
         k_gather_uniform<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(xyz, q, perm, n, sorted_keys, tv, x,
-                                                                     y, z, qs, xq);
+                                                                     y, z, qs, xq, xq + n4);
     return cudaGetLastError();
 }
 

@@ -1,6 +1,6 @@
 """The CPU leg of bench.py that times the oracle, on the small uniform workload (N = 1e4,
 depth 3, p = 6): it runs one full oracle solve without extrapolation, compares the given
-results with the oracle over every particle, and with the direct sum on 300 particles.  The
+results with the oracle over every particle, and with the direct sum on 2000 particles.  The
 oracle's own result stands in for the GPU's here, so its error against the oracle is zero
 and its error against the direct sum is the method's."""
 import os
@@ -23,7 +23,7 @@ def test_cpu_baseline_full_solve_small():
     cpu, acc = bench.cpu_baseline(x, q, dom, cfg, phi, E, {cfg["order"]: phi})
     assert cpu["kind"] == "oracle" and cpu["value"] > 0 and cpu["cores"] >= 1
     assert "nothing extrapolated" in cpu["sample"]
-    assert acc["targets"] == cfg["n"] and acc["direct_sum_targets"] == 300
+    assert acc["targets"] == cfg["n"] and acc["direct_sum_targets"] == 2000
     assert acc["rel_l2_phi_vs_oracle"] == 0.0 and acc["rel_l2_field_vs_oracle"] == 0.0
     assert acc["rel_l2_phi_vs_direct"] == acc["oracle_rel_l2_phi_vs_direct"]
     # the method's own error at p = 6 on this workload: well above rounding, well below 1

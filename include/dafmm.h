@@ -270,7 +270,13 @@ size_t dafmm_footprint(int64_t n, int order, int uniform_depth, int max_leaf, in
  * Each entry applies one generated operator to `count` independent instances, in box-
  * scaled variables (a box of width 1): multipoles M~_a = M_a / h^|a|, locals
  * L~_b = L_b h^|b|.  Arrays are device or host memory; outputs are overwritten.
- *   precision: DAFMM_FP64 or DAFMM_FP32 (arithmetic of the generated code). */
+ *   precision: DAFMM_FP64 or DAFMM_FP32 (arithmetic of the generated code), or
+ *   DAFMM_FP64 | DAFMM_OP_NUMERICAL_DA: the same operator evaluated step by step with
+ *   numerical DA (truncated power series arithmetic, Appendix A: products truncated at
+ *   order p, powers by the binomial series, composition with the operator's map), FP64, one
+ *   warp per instance -- the baseline the generated code replaces (Sec. 3, Tables 2-8).
+ *   Any other value: DAFMM_ERR_INVALID_ARG. */
+#define DAFMM_OP_NUMERICAL_DA 16
 
 /* P2M, Eq. 2: out[i*nc + k] = q_i * coefficient k of (1 - 2 s_i.d + s_i^2 d^2)^(-1/2) */
 int dafmm_op_p2m(dafmm_ctx* ctx, int order, int precision, int64_t count, const double* s,
@@ -290,6 +296,13 @@ int dafmm_op_m2m(dafmm_ctx* ctx, int order, int precision, int64_t count, const 
                  const double* in, double* out, void* stream);
 int dafmm_op_l2l(dafmm_ctx* ctx, int order, int precision, int64_t count, const int* oct,
                  const double* in, double* out, void* stream);
+/* M2L, Eq. 5, by numerical DA only (precision must be DAFMM_FP64 | DAFMM_OP_NUMERICAL_DA, else
+ * DAFMM_ERR_UNSUPPORTED; the generated M2L runs inside dafmm_eval, and its matrices come from
+ * dafmm_op_m2l_matrix): out[i*nc + b] = coefficient b of sqrt(R) (M_i o M2), M2: d = (r0_i + d') R,
+ * R = 1/|r0_i + d'|^2, for the displacement r0_i = r0[3i .. 3i+2] (target centre - source
+ * centre, boxes of width 1; any well-separated real vector); M is count x nc. */
+int dafmm_op_m2l(dafmm_ctx* ctx, int order, int precision, int64_t count, const double* r0, const double* M,
+                 double* out, void* stream);
 /* M2L matrix of Eq. 5 for an integer box displacement v (target - source, boxes of width 1,
  * max|v_k| in 2..3): K[b*nc + a] = coefficient b of M2L(e_a), computed on the GPU in FP64. */
 int dafmm_op_m2l_matrix(dafmm_ctx* ctx, int order, const int* v3, double* K, void* stream);

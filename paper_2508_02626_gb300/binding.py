@@ -26,6 +26,7 @@ DAFMM_FP64 = 0
 DAFMM_MIXED = 1
 DAFMM_FP32 = 2
 PRECISIONS = {"fp64": DAFMM_FP64, "mixed": DAFMM_MIXED, "fp32": DAFMM_FP32}
+DAFMM_OP_NUMERICAL_DA = 16  # or-ed into the precision of a single-operator batch
 MAX_ORDER = 10
 
 # entry points declared in include/dafmm.h: name -> (restype, argtypes)
@@ -55,6 +56,7 @@ SIGNATURES = {
     "dafmm_op_m2m": (_i, [_vp, _i, _i, _i64, _vp, _vp, _vp, _vp]),
     "dafmm_op_l2l": (_i, [_vp, _i, _i, _i64, _vp, _vp, _vp, _vp]),
     "dafmm_op_m2l_matrix": (_i, [_vp, _i, _vp, _vp, _vp]),
+    "dafmm_op_m2l": (_i, [_vp, _i, _i, _i64, _vp, _vp, _vp, _vp]),
     "dafmm_create_pooled": (_i, [ctypes.POINTER(_vp), _i, _sz]),
     "dafmm_build_forest": (_i, [_vp, _vp, _vp, _vp, _i, _vp, _i, _vp, ctypes.POINTER(_vp)]),
     "dafmm_forest_info": (_i, [_vp, _vp, _vp]),
@@ -328,6 +330,11 @@ def dafmm_op_m2m(ctx, order, precision, oct_, inp, out, stream=None):
 
 def dafmm_op_l2l(ctx, order, precision, oct_, inp, out, stream=None):
     _op("dafmm_op_l2l", ctx, order, precision, oct_.shape[0], oct_, inp, out, stream)
+
+
+def dafmm_op_m2l(ctx, order, precision, r0, M, out, stream=None):
+    """M2L (Eq. 5) of each row of M for the displacement r0[i] (numerical DA only)."""
+    _op("dafmm_op_m2l", ctx, order, precision, r0.shape[0], r0, M, out, stream)
 
 
 def dafmm_op_m2l_matrix(ctx, order, v, K, stream=None):

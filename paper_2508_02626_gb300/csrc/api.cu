@@ -1841,9 +1841,18 @@ size_t dafmm_footprint(int64_t n, int order, int uniform_depth, int max_leaf, in
 static int op_common(dafmm_ctx* c, int order, int precision) {
     if (!c) return DAFMM_ERR_INVALID_ARG;
     if (order < 0 || order > kMaxOrder) return fail(c, DAFMM_ERR_UNSUPPORTED_ORDER, std::to_string(order));
-    if (precision != DAFMM_FP64 && precision != DAFMM_FP32) return fail(c, DAFMM_ERR_INVALID_ARG, "precision");
+    if (precision != DAFMM_FP64 && precision != DAFMM_FP32 && precision != (DAFMM_FP64 | DAFMM_OP_NUMERICAL_DA))
+        return fail(c, DAFMM_ERR_INVALID_ARG, "precision");
     if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, DAFMM_ERR_CUDA, "cudaSetDevice");
     return DAFMM_OK;
+}
+
+// the numerical-DA form of an operator batch (da_numeric.cu): the order's product table, then
+// one launch
+static cudaError_t numerical_da(dafmm_ctx* c, int order, int op, int64_t count, const double* a, const double* b,
+                                const int* oct, double* out, cudaStream_t s) {
+    if (ensure_order(c, order, s, false)) return cudaErrorMemoryAllocation;
+    return launch_da_op(c->ord[order], op, count, a, b, oct, out, c->num_sms, s);
 }
 
 static int finish_out(dafmm_ctx* c, double* user, void* dev, size_t bytes, bool owned, cudaStream_t s) {
@@ -1858,7 +1867,7 @@ typedef cudaError_t (*op2_fn)(int, int64_t, const double*, const double*, double
 
 static int run_op2(dafmm_ctx* c, int order, int prec, int64_t count, const double* a, size_t abytes,
                    const double* b, size_t bbytes, double* out, size_t obytes, op2_fn fn, void* stream,
-                   const char* what) {
+                   const char* what, int da_op) {
     int rc = op_common(c, order, prec);
     if (rc) return rc;
     if (count < 0 || (count > 0 && (!a || !b || !out))) return fail(c, DAFMM_ERR_INVALID_ARG, what);
@@ -1874,7 +1883,13 @@ static int run_op2(dafmm_ctx* c, int order, int prec, int64_t count, const doubl
         if ((rc = dev_alloc(c, &so.dev, obytes, "op output"))) return rc;
         so.owned = true;
     }
-    CK(c, fn(prec, count, (const double*)sa.dev, (const double*)sb.dev, (double*)so.dev, s), what);
+    if (prec & DAFMM_OP_NUMERICAL_DA) {
+        CK(c, numerical_da(c, order, da_op, count, (const double*)sa.dev, (const double*)sb.dev, nullptr,
+                           (double*)so.dev, s),
+           what);
+    } else {
+        CK(c, fn(prec, count, (const double*)sa.dev, (const double*)sb.dev, (double*)so.dev, s), what);
+    }
     return finish_out(c, out, so.dev, obytes, so.owned, s);
 }
 
@@ -1884,7 +1899,7 @@ int dafmm_op_p2m(dafmm_ctx* c, int order, int precision, int64_t count, const do
     const OrderOps* ops = order_ops(order);
     if (!ops) return op_common(c, order, precision);
     return run_op2(c, order, precision, count, s3, count * 3 * 8, q, count * 8, out, count * nc * 8, ops->op_p2m,
-                   stream, "P2M");
+                   stream, "P2M", kDaP2M);
 }
 
 int dafmm_op_p2l(dafmm_ctx* c, int order, int precision, int64_t count, const double* w, const double* q,
@@ -1893,7 +1908,7 @@ int dafmm_op_p2l(dafmm_ctx* c, int order, int precision, int64_t count, const do
     const OrderOps* ops = order_ops(order);
     if (!ops) return op_common(c, order, precision);
     return run_op2(c, order, precision, count, w, count * 3 * 8, q, count * 8, out, count * nc * 8, ops->op_p2l,
-                   stream, "P2L");
+                   stream, "P2L", kDaP2L);
 }
 
 int dafmm_op_l2p(dafmm_ctx* c, int order, int precision, int64_t count, const double* L, const double* x,
@@ -1902,7 +1917,7 @@ int dafmm_op_l2p(dafmm_ctx* c, int order, int precision, int64_t count, const do
     const OrderOps* ops = order_ops(order);
     if (!ops) return op_common(c, order, precision);
     return run_op2(c, order, precision, count, L, count * nc * 8, x, count * 3 * 8, out4, count * 4 * 8,
-                   ops->op_l2p, stream, "L2P");
+                   ops->op_l2p, stream, "L2P", kDaL2P);
 }
 
 int dafmm_op_m2p(dafmm_ctx* c, int order, int precision, int64_t count, const double* M, const double* s3,
@@ -1911,7 +1926,7 @@ int dafmm_op_m2p(dafmm_ctx* c, int order, int precision, int64_t count, const do
     const OrderOps* ops = order_ops(order);
     if (!ops) return op_common(c, order, precision);
     return run_op2(c, order, precision, count, M, count * nc * 8, s3, count * 3 * 8, out4, count * 4 * 8,
-                   ops->op_m2p, stream, "M2P");
+                   ops->op_m2p, stream, "M2P", kDaM2P);
 }
 
 static int run_shift(dafmm_ctx* c, int which, int order, int prec, int64_t count, const int* oct,
@@ -1933,9 +1948,15 @@ static int run_shift(dafmm_ctx* c, int which, int order, int prec, int64_t count
         if ((rc = dev_alloc(c, &sout.dev, sout.bytes, "op output"))) return rc;
         sout.owned = true;
     }
-    CK(c, order_ops(order)->op_shift(c->ord[order], which, prec, count, (const int*)so_.dev, (const double*)si.dev,
-                                     (double*)sout.dev, s),
-       which == 0 ? "M2M" : "L2L");
+    if (prec & DAFMM_OP_NUMERICAL_DA) {
+        CK(c, numerical_da(c, order, which == 0 ? kDaM2M : kDaL2L, count, (const double*)si.dev, nullptr,
+                           (const int*)so_.dev, (double*)sout.dev, s),
+           which == 0 ? "M2M" : "L2L");
+    } else {
+        CK(c, order_ops(order)->op_shift(c->ord[order], which, prec, count, (const int*)so_.dev,
+                                         (const double*)si.dev, (double*)sout.dev, s),
+           which == 0 ? "M2M" : "L2L");
+    }
     return finish_out(c, out, sout.dev, sout.bytes, sout.owned, s);
 }
 
@@ -1947,6 +1968,17 @@ int dafmm_op_m2m(dafmm_ctx* c, int order, int precision, int64_t count, const in
 int dafmm_op_l2l(dafmm_ctx* c, int order, int precision, int64_t count, const int* oct, const double* in,
                  double* out, void* stream) {
     return run_shift(c, 1, order, precision, count, oct, in, out, stream);
+}
+
+int dafmm_op_m2l(dafmm_ctx* c, int order, int precision, int64_t count, const double* r0, const double* M,
+                 double* out, void* stream) {
+    int rc = op_common(c, order, precision);
+    if (rc) return rc;
+    if (!(precision & DAFMM_OP_NUMERICAL_DA))
+        return fail(c, DAFMM_ERR_UNSUPPORTED, "dafmm_op_m2l: numerical DA only (DAFMM_FP64 | DAFMM_OP_NUMERICAL_DA)");
+    const size_t nc = ncoef_of(order);
+    return run_op2(c, order, precision, count, M, count * nc * 8, r0, count * 3 * 8, out, count * nc * 8, nullptr,
+                   stream, "M2L", kDaM2L);
 }
 
 int dafmm_op_m2l_matrix(dafmm_ctx* c, int order, const int* v3, double* K, void* stream) {

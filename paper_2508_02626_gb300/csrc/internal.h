@@ -160,6 +160,12 @@ struct OrderOps {
 
 const OrderOps* order_ops(int p);
 
+// numerical-DA operator batches (da_numeric.cu), FP64, one warp per instance; `op` is one of
+// kDa*, the arguments those of the single-operator entry points (a: first array, b: second,
+// oct: child octants of M2M/L2L)
+enum { kDaP2M = 0, kDaP2L, kDaL2P, kDaM2P, kDaM2M, kDaL2L, kDaM2L };
+cudaError_t launch_da_op(const OrderData& od, int op, int64_t n, const double* a, const double* b, const int* oct,
+                         double* out, int num_sms, cudaStream_t s);
 // one function per translation unit fmm_p*.cu
 #define DAFMM_DECLARE_ORDER(P) const OrderOps* order_ops_p##P();
 DAFMM_DECLARE_ORDER(0) DAFMM_DECLARE_ORDER(1) DAFMM_DECLARE_ORDER(2) DAFMM_DECLARE_ORDER(3)

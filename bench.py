@@ -360,14 +360,18 @@ def run_ours(args, rank, world):
 
     # the other precision modes on the same tree (a few steps each), for comparison
     modes = {}
+    mode_results = {}
     if not args.no_modes:
-        for mname in ("mixed", "fp64", "fp64_dense_m2l"):
+        for mname in ("mixed", "fp64", "fp64_dense_m2l", "fp32_tf32_m2l"):
             if mname == args.precision:
                 continue
             # fp64 uses the M2L by rotation (Sec. 3.4, the default from p = 4); fp64_dense_m2l
-            # the dense matrix per displacement, for comparison
+            # the dense matrix per displacement, for comparison; fp32_tf32_m2l the FP32 mode with
+            # TF32 instead of F16 split operands in M2L -- against MIXED (the same M2L, FP64
+            # M2M/L2L and storage) it shows what the FP32 shifts cost in accuracy
             B.dafmm_set_option(ctx.h, B.DAFMM_OPT_M2L_ROTATION, 0 if mname == "fp64_dense_m2l" else -1)
-            mp = B.PRECISIONS["fp64" if mname.startswith("fp64") else mname]
+            B.dafmm_set_option(ctx.h, B.DAFMM_OPT_M2L_F16, 0 if mname == "fp32_tf32_m2l" else 1)
+            mp = B.PRECISIONS["fp64" if mname.startswith("fp64") else ("fp32" if mname.startswith("fp32") else mname)]
             ksteps = 2 if mname.startswith("fp64") else 5
             with torch.cuda.stream(stream):
                 tree.eval(p, phi, E, precision=mp, stream=stream)
@@ -384,7 +388,9 @@ def run_ours(args, rank, world):
             modes[mname] = {"value": n / (float(np.mean(ms)) / 1e3), "ms_per_step": float(np.mean(ms)),
                             "phases_ms": {k: round(v, 4) for k, v in B.dafmm_last_phase_ms(ctx.h).items()
                                           if k != "launches"}}
+            mode_results[mname] = (phi.cpu().numpy(), E.cpu().numpy())
         B.dafmm_set_option(ctx.h, B.DAFMM_OPT_M2L_ROTATION, -1)
+        B.dafmm_set_option(ctx.h, B.DAFMM_OPT_M2L_F16, 1)
         # back to the headline mode for the accuracy sample
         with torch.cuda.stream(stream):
             tree.eval(p, phi, E, precision=prec, stream=stream)
@@ -545,8 +551,13 @@ def run_ours(args, rank, world):
             out["operators"] = bench_operators(ctx)
         if "leafsize" in sections:
             out["leaf_size"] = bench_leaf_size(ctx)
+        if "paper" in sections:
+            out["paper_shape"] = bench_paper_shape(ctx)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        out["cpu_baseline"], out["accuracy"] = cpu_baseline(x, q, dom, cfg, phi_host, E_host, phi_by_order)
+        out["cpu_baseline"], out["accuracy"] = cpu_baseline(x, q, dom, cfg, phi_host, E_host, phi_by_order,
+                                                            mode_results)
+        for mname, errs in out["accuracy"].pop("modes", {}).items():
+            out["modes"][mname].update(errs)
         a = out["accuracy"]
         # the headline's error beside its value: against the FP64 oracle FMM (same tree and
         # order, all particles) and, with the oracle's own, against the direct sum
@@ -670,13 +681,23 @@ def bench_batch(ctx, stream, flush):
         t.eval(p, ph64[a:b], None, precision="fp64")
         t.free()
     seq_s = time.perf_counter() - t0
-    # equal accuracy: both against the direct sum on two sampled problems
-    acc = []
-    for r in (3, 100):
+    # equal accuracy: every problem's batched FP32 and single FP64 results against the direct
+    # sum (Eq. 1, the oracle's) on 64 seeded targets of that problem
+    rng = np.random.default_rng(4999)
+    e32, e64 = [], []
+    for r in range(len(sizes)):
         a, b = offs[r], offs[r + 1]
-        d_phi, _ = O.direct(xs[r], qs[r])
-        rl = lambda u: float(np.sqrt(((u - d_phi) ** 2).sum() / (d_phi ** 2).sum()))
-        acc.append({"problem": r, "n": int(b - a), "batched_fp32": rl(phi_b[a:b]), "single_fp64": rl(ph64[a:b])})
+        tg = np.sort(rng.choice(b - a, min(64, b - a), replace=False))
+        d_phi, _ = O.direct(xs[r], qs[r], targets=tg)
+        rl = lambda u: float(np.sqrt(((u[tg] - d_phi) ** 2).sum() / (d_phi ** 2).sum()))
+        e32.append(rl(phi_b[a:b]))
+        e64.append(rl(ph64[a:b]))
+    e32, e64 = np.array(e32), np.array(e64)
+    acc = {"problems": len(sizes), "targets_per_problem": 64,
+           "batched_fp32_median": float(np.median(e32)), "batched_fp32_max": float(e32.max()),
+           "single_fp64_median": float(np.median(e64)), "single_fp64_max": float(e64.max()),
+           "ratio_median": float(np.median(e32 / e64)), "ratio_max": float((e32 / e64).max()),
+           "note": "potential, relative L2 against the direct sum; the two forms use their own leaf sizes"}
     return {"workload": "256 problems, N log-uniform [1e3,1e5], uniform/clustered by seed, q U[-1,1], p=6",
             "particles": n, "autotuned": {"max_leaf": s, "leaf_warps": tuned["leaf_warps"],
                                           "cached": tuned["cached"]},
@@ -688,14 +709,20 @@ def bench_batch(ctx, stream, flush):
             "accuracy_vs_direct": acc}
 
 
-def bench_serving(requests):
+def bench_serving(requests, fp64_every=4, direct_targets=8):
     """Serving loop on the Poisson request stream (N log-uniform in [1e3, 1e6], p in {4, 6, 8},
-    uniform or clustered, FP32): the first `requests` requests of the stream; capacity from
-    a saturated run, then arrivals at 0.5, 0.8 and 1.0 x capacity, p50/p99 latency from
-    submission to results in the caller's page-locked buffers; plain FP64 single solves of a
-    sample of the same requests for comparison."""
+    uniform or clustered, q U[-1,1], FP32, s = 64): the first `requests` requests of the
+    stream (2000: the whole stream); capacity from a saturated run, then arrivals at 0.5, 0.8
+    and 1.0 x capacity, p50/p99 latency from submission to results in the caller's
+    page-locked buffers.  Every `fp64_every`-th request is also solved as a plain FP64 single
+    solve (build + eval, one after another): that gives the sequential FP64 baseline on the
+    same requests and, per served result, its error against the FP64 result over all its
+    particles (the FP64 path equals the oracle FMM to 1e-12).  Every served result is also
+    compared with the direct sum (Eq. 1, the oracle's) on `direct_targets` seeded targets,
+    beside the FP64 result's error on the same targets ("equal accuracy")."""
     import torch
 
+    import oracle as O
     from paper_2508_02626_gb300 import binding as B
     from paper_2508_02626_gb300 import workloads as W
     stream_def = W.poisson_stream()[:requests]
@@ -753,28 +780,74 @@ def bench_serving(requests):
     st = srv.stats()
     out["server"] = {k: st[k] for k in ("jobs", "requests_per_job", "peak_running", "peak_bytes")}
     srv.close()
-    # plain FP64 single solves, one after another, on a sample of the same requests
+    # the served results stay in the page-locked outputs (from the last run)
+    served = [(d[2][0].numpy(), d[2][1].numpy()) for d in data]
+    # plain FP64 single solves, one after another, of every fp64_every-th request
     ctx = B.Context(torch.cuda.current_device())
-    k = min(24, len(data))
+    sample = list(range(0, len(data), fp64_every))
+    fp64 = {}
     sample_n = 0
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for xp, qp, o, p in data[:k]:
+    for i in sample:
+        xp, qp, _, p = data[i]
+        fp64[i] = (np.empty(len(qp)), np.empty((len(qp), 3)))
         t = ctx.build_tree(xp, qp, domain=None, uniform_depth=-1, max_leaf=64)
-        t.eval(p, o[0], o[1], precision="fp64")
+        t.eval(p, fp64[i][0], fp64[i][1], precision="fp64")
         t.free()
         sample_n += len(qp)
     seq_s = time.perf_counter() - t0
     ctx.close()
-    out["sequential_fp64"] = {"requests": k, "particles_per_s": sample_n / seq_s, "solves_per_s": k / seq_s}
+    out["sequential_fp64"] = {"requests": len(sample), "particles": sample_n, "particles_per_s": sample_n / seq_s,
+                              "solves_per_s": len(sample) / seq_s,
+                              "note": "every %d-th request of the same stream, build + eval each" % fp64_every}
+
+    def rel(a, b):
+        return float(np.sqrt(((a - b) ** 2).sum() / max((b ** 2).sum(), 1e-300)))
+
+    # per served result: against its FP64 solve (all particles) and against the direct sum
+    vs64_phi, vs64_E, d_served, d_fp64 = [], [], [], []
+    rng = np.random.default_rng(5006)
+    for i, d in enumerate(data):
+        x, q = d[0].numpy(), d[1].numpy()
+        tg = np.sort(rng.choice(len(q), min(direct_targets, len(q)), replace=False))
+        dphi, dE = O.direct(x, q, targets=tg)
+        d_served.append((rel(served[i][0][tg], dphi), rel(served[i][1][tg], dE)))
+        if i in fp64:
+            vs64_phi.append(rel(served[i][0], fp64[i][0]))
+            vs64_E.append(rel(served[i][1], fp64[i][1]))
+            d_fp64.append((rel(fp64[i][0][tg], dphi), rel(fp64[i][1][tg], dE)))
+    d_served = np.array(d_served)
+    d_fp64 = np.array(d_fp64)
+    ds_sub = d_served[sample]
+
+    def summ(v):
+        v = np.asarray(v)
+        return {"median": float(np.median(v)), "p99": float(np.percentile(v, 99)), "max": float(v.max())}
+
+    out["accuracy"] = {
+        "served_vs_fp64_rel_l2": {"requests": len(vs64_phi), "phi": summ(vs64_phi), "field": summ(vs64_E),
+                                  "within_fp32_bounds": int(sum(1 for a, b in zip(vs64_phi, vs64_E)
+                                                                if a <= 3.8e-6 and b <= 1e-5)),
+                                  "bounds": "phi 3.8e-6, field 1e-5 (64 u, 160 u)"},
+        "served_vs_direct": {"requests": len(d_served), "targets_per_request": direct_targets,
+                             "phi": summ(d_served[:, 0]), "field": summ(d_served[:, 1])},
+        "equal_accuracy_vs_direct": {"requests": len(d_fp64),
+                                     "served_phi_median": float(np.median(ds_sub[:, 0])),
+                                     "fp64_phi_median": float(np.median(d_fp64[:, 0])),
+                                     "served_field_median": float(np.median(ds_sub[:, 1])),
+                                     "fp64_field_median": float(np.median(d_fp64[:, 1])),
+                                     "max_ratio_phi": float((ds_sub[:, 0] / np.maximum(d_fp64[:, 0], 1e-300)).max())}}
     return out
 
 
 def bench_operators(ctx):
     """Per-operator cost, the GPU analogue of the paper's operator tables (Tables 2-8): each
     generated operator applied to a batch of random instances (ns per instance, FP64 and
-    FP32), the batched M2L contraction inside an evaluation (ns per well-separated pair), and
-    the oracle's numerical-DA operator per call on one host core (us)."""
+    FP32), the same operators by numerical DA on the GPU (DAFMM_OP_NUMERICAL_DA, FP64) and
+    their ratio to the generated FP64 code (the paper's Tables 2-8 ratio on one device), the
+    batched M2L contraction inside an evaluation (ns per well-separated pair), and the
+    oracle's numerical-DA operator per call on one host core (us)."""
     import torch
 
     from paper_2508_02626_gb300 import binding as B
@@ -783,7 +856,9 @@ def bench_operators(ctx):
     rng = np.random.default_rng(31)
     out = {"note": "GPU: ns per instance of a batch of 2^18 (M2L: per pair inside a uniform N=2^18 depth-4 "
                    "evaluation; gpu_fp64_ns: the dense FP64 M2L, gpu_fp64_rotation_ns: the FP64 M2L by "
-                   "rotation, Sec. 3.4); oracle: us per call of its numerical-DA operator, one host core"}
+                   "rotation, Sec. 3.4); gpu_numerical_da_ns: the same operator by numerical DA on the GPU "
+                   "(FP64, one warp per instance, a batch of 2^15..2^10 by order); oracle: us per call of "
+                   "its numerical-DA operator, one host core"}
     count = 1 << 18
     for p in (2, 4, 6, 8, 10):
         nc = (p + 1) * (p + 2) * (p + 3) // 6
@@ -815,6 +890,32 @@ def bench_operators(ctx):
                 e1.synchronize()
                 r[pname] = round(e0.elapsed_time(e1) / 3 * 1e6 / count, 4)
             row[name] = r
+        # the same operators by numerical DA on the GPU (FP64, one warp per instance), on the
+        # first count_da instances: the paper's generated-versus-DA comparison on one device
+        count_da = {2: 1 << 15, 4: 1 << 14, 6: 1 << 12, 8: 1 << 11, 10: 1 << 10}[p]
+        sub = {"s3": s3[:count_da], "far": far[:count_da], "qv": qv[:count_da], "C": C[:count_da],
+               "octs": octs[:count_da], "outc": outc[:count_da], "out4": out4[:count_da]}
+        r0s = torch.from_numpy(rng.integers(2, 4, (count_da, 3)) * rng.choice([-1.0, 1.0], (count_da, 3))).to(dev)
+        DA = B.DAFMM_FP64 | B.DAFMM_OP_NUMERICAL_DA
+        da_ops = {"P2M": lambda: B.dafmm_op_p2m(ctx.h, p, DA, sub["s3"], sub["qv"], sub["outc"]),
+                  "P2L": lambda: B.dafmm_op_p2l(ctx.h, p, DA, sub["far"], sub["qv"], sub["outc"]),
+                  "L2P": lambda: B.dafmm_op_l2p(ctx.h, p, DA, sub["C"], sub["s3"], sub["out4"]),
+                  "M2P": lambda: B.dafmm_op_m2p(ctx.h, p, DA, sub["C"], sub["far"], sub["out4"]),
+                  "M2M": lambda: B.dafmm_op_m2m(ctx.h, p, DA, sub["octs"], sub["C"], sub["outc"]),
+                  "L2L": lambda: B.dafmm_op_l2l(ctx.h, p, DA, sub["octs"], sub["C"], sub["outc"]),
+                  "M2L": lambda: B.dafmm_op_m2l(ctx.h, p, DA, r0s, sub["C"], sub["outc"])}
+        for name, fn in da_ops.items():
+            fn()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            e1.synchronize()
+            row.setdefault(name, {})["gpu_numerical_da_ns"] = round(e0.elapsed_time(e1) * 1e6 / count_da, 2)
+            if "gpu_fp64_ns" in row[name]:
+                row[name]["numerical_da_over_generated_fp64"] = round(
+                    row[name]["gpu_numerical_da_ns"] / row[name]["gpu_fp64_ns"], 1)
         # oracle numerical DA, one call at a time
         s1, w1, M1 = rng.uniform(-0.45, 0.45, (1, 3)), rng.uniform(-0.45, 0.45, (1, 3)) + [2.5, 0.3, -0.2], rng.uniform(-1, 1, nc)
         calls = {"P2M": lambda: O.p2m(p, s1, [1.0]), "P2L": lambda: O.p2l(p, w1, [1.0]),
@@ -841,6 +942,9 @@ def bench_operators(ctx):
             row["M2L"][pname] = round(B.dafmm_last_phase_ms(ctx.h)["m2l"] * 1e6 / pairs, 4)
         B.dafmm_set_option(ctx.h, B.DAFMM_OPT_M2L_ROTATION, -1)
         tr.free()
+        m = row["M2L"]
+        m["numerical_da_over_generated_fp64"] = round(m["gpu_numerical_da_ns"] / m["gpu_fp64_ns"], 1)
+        m["numerical_da_over_rotation_fp64"] = round(m["gpu_numerical_da_ns"] / m["gpu_fp64_rotation_ns"], 1)
         out["p%d" % p] = row
         del s3, far, qv, C, octs, outc, out4
     return out
@@ -854,7 +958,7 @@ def bench_leaf_size(ctx):
     import torch
 
     from paper_2508_02626_gb300 import workloads as W
-    sizes = (10_000, 100_000, 1_000_000, 4_000_000)
+    sizes = (10_000, 100_000, 1_000_000, 4_000_000, 10_000_000)
     orders = (2, 6, 10)
     leaf = (16, 32, 64, 128, 256, 512, 1024)
     table, best = {}, {}
@@ -865,7 +969,7 @@ def bench_leaf_size(ctx):
         for p in orders:
             res = {}
             for s_ in leaf:
-                if s_ >= n:
+                if s_ >= n or (n >= 10_000_000 and s_ < 64):  # (1e7: the leaf sizes around the optimum)
                     continue
                 t = ctx.build_tree(xt, qt, uniform_depth=-1, max_leaf=s_)
                 t.eval(p, phi, None, precision="fp32")  # warm: tables, expansions
@@ -889,7 +993,70 @@ def bench_leaf_size(ctx):
             "times_ms": table, "fastest": best, "loglog_slope_of_fastest": slopes}
 
 
-def cpu_baseline(x, q, dom, cfg, phi_gpu, E_gpu, phi_by_order=None):
+# the paper's figures on its own workload (1M-point unit Gaussian, q = +1; i5-14600, FP64):
+# Table 9 (error against the exact potential by order) and Table 11 (SDA-FMM rows: order, s,
+# sigma, T in seconds), quoted as context
+PAPER_TABLE9 = {2: 7.94e-4, 4: 6.30e-5, 6: 3.76e-6, 8: 1.58e-7, 10: 2.95e-8}
+PAPER_TABLE11 = {3: (64, 3.12e-4, 4.70), 4: (128, 7.03e-5, 6.14), 7: (256, 8.49e-7, 20.86)}
+# leaf size by order on 1M particles: Table 10's optimum (odd orders: the table of Table 11,
+# else the next lower even order's)
+PAPER_LEAF = {2: 64, 3: 64, 4: 128, 5: 128, 6: 256, 7: 256, 8: 256, 9: 256, 10: 512}
+
+
+def bench_paper_shape(ctx, n=1_000_000, targets=5000):
+    """The paper's own test (Sec. 3.5): N = 1e6 particles from a 3-D Gaussian with unit
+    standard deviation, q = +1, adaptive trees with the leaf size of its Table 10.  For p = 2..10
+    the relative RMS error sigma (Eq. 8) of the FP64 and FP32 modes against the exact potential
+    (the oracle's direct sum, Eq. 1, on `targets` seeded particles) beside Table 9, and build +
+    evaluation wall time; Table 11's SDA-FMM rows (p = 3, 4, 7 at s = 64, 128, 256) beside
+    the paper's times (an i5-14600 CPU: context, not a target)."""
+    import torch
+
+    import oracle as O
+    from paper_2508_02626_gb300 import workloads as W
+    x, q = W.gaussian(n, seed=394)
+    tg = np.sort(np.random.default_rng(395).choice(n, targets, replace=False))
+    d_phi, _ = O.direct(x, q, targets=tg)
+    xt, qt = torch.from_numpy(x).cuda(), torch.from_numpy(q).cuda()
+    phi = torch.empty(n, dtype=torch.float64, device="cuda")
+
+    def sigma(a):
+        return float(np.sqrt(((a[tg] - d_phi) ** 2).sum() / (d_phi ** 2).sum()))
+
+    def solve(p, s_, prec):
+        t = ctx.build_tree(xt, qt, uniform_depth=-1, max_leaf=s_)
+        t.eval(p, phi, None, precision=prec)  # warm: tables, expansions
+        torch.cuda.synchronize()
+        t.free()
+        t0 = time.perf_counter()
+        t = ctx.build_tree(xt, qt, uniform_depth=-1, max_leaf=s_)
+        t.eval(p, phi, None, precision=prec)
+        torch.cuda.synchronize()
+        ms = (time.perf_counter() - t0) * 1e3
+        t.free()
+        return sigma(phi.cpu().numpy()), ms
+
+    by_order = {}
+    for p in range(2, 11):
+        s_ = PAPER_LEAF[p]
+        e64, t64 = solve(p, s_, "fp64")
+        e32, t32 = solve(p, s_, "fp32")
+        row = {"s": s_, "sigma_fp64": e64, "sigma_fp32": e32, "ms_fp64": round(t64, 3), "ms_fp32": round(t32, 3)}
+        if p in PAPER_TABLE9:
+            row["paper_sigma"] = PAPER_TABLE9[p]
+        by_order["p%d" % p] = row
+    t11 = {}
+    for p, (s_, sig, sec) in PAPER_TABLE11.items():
+        r = by_order["p%d" % p]
+        t11["p%d_s%d" % (p, s_)] = {"sigma_fp64": r["sigma_fp64"], "ms_fp64": r["ms_fp64"],
+                                    "sigma_fp32": r["sigma_fp32"], "ms_fp32": r["ms_fp32"],
+                                    "paper_sigma": sig, "paper_seconds_i5_14600": sec}
+    return {"workload": "3-D Gaussian (unit sigma), N=%d, q=+1, adaptive, leaf size of Table 10; sigma (Eq. 8) "
+                        "against the direct sum on %d seeded particles; time = build + eval wall" % (n, targets),
+            "by_order": by_order, "table11": t11}
+
+
+def cpu_baseline(x, q, dom, cfg, phi_gpu, E_gpu, phi_by_order=None, mode_results=None):
     """The oracle FMM (plain C, all host cores) timed on one full solve of the workload: same
     tree and order, every particle a target, nothing extrapolated (about 15 s on 16 Arm cores,
     23 s on 8 x86 cores).  Its result also gives the GPU's error against the oracle over all
@@ -924,6 +1091,9 @@ def cpu_baseline(x, q, dom, cfg, phi_gpu, E_gpu, phi_by_order=None):
            "oracle_rel_l2_phi_vs_direct": rel(ref_phi[td], d_phi),
            "rel_l2_field_vs_direct": rel(E_gpu[td], d_E),
            "oracle_rel_l2_field_vs_direct": rel(ref_E[td], d_E)}
+    if mode_results:  # the other precision modes on the same tree, against the same oracle solve
+        acc["modes"] = {m: {"rel_l2_phi_vs_oracle": rel(ph, ref_phi), "rel_l2_field_vs_oracle": rel(Ef, ref_E)}
+                        for m, (ph, Ef) in mode_results.items()}
     if phi_by_order:
         by = {"p%d" % po: rel(ph[td], d_phi) for po, ph in sorted(phi_by_order.items())}
         reach = [po for po, ph in sorted(phi_by_order.items()) if rel(ph[td], d_phi) <= 1e-7]
@@ -977,11 +1147,12 @@ def main():
     ap.add_argument("--no-peaks", action="store_true", help="skip the unit-rate probes (dafmm_probe_peak)")
     ap.add_argument("--no-workloads", action="store_true",
                     help="skip the adaptive, batched and serving workloads (N = 1 only)")
-    ap.add_argument("--serving-requests", type=int, default=200)
+    ap.add_argument("--serving-requests", type=int, default=2000)
     ap.add_argument("--adaptive-n", type=int, default=0, help="particles of the adaptive workload (0: 4e6)")
     ap.add_argument("--adaptive-modes", default="mixed,fp32", help="precision modes of the adaptive workload")
-    ap.add_argument("--sections", default="adaptive,batch,serving,operators,leafsize",
-                    help="comma-separated extra workloads at N = 1: adaptive, batch, serving, operators, leafsize")
+    ap.add_argument("--sections", default="adaptive,batch,serving,operators,leafsize,paper",
+                    help="comma-separated extra workloads at N = 1: adaptive, batch, serving, operators, leafsize, "
+                         "paper")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))

@@ -691,38 +691,128 @@ __device__ __forceinline__ void scale_shift_exact(float hi, float lo, float r, f
     L = fmaf(lo, r, err + ol);
 }
 
+// a pair closer than this (in leaf widths of the target's leaf) takes the remainders of its
+// offsets into its difference: beyond it, T - S alone is within a few FP32 roundings of the
+// difference's own size (the remainders are below 2^-23 leaf widths)
+constexpr float kCloseR2 = 0.01f;
+
 // list pairs [p0, p1) acting on the target t = T + tl (T: rounded offsets, tl: remainders,
 // in the list's frame), both halves of every step in one packed FP32x2 instruction: per half
-//   e = (T - S) + (tl - sl),  r2 = fma(ex, ex, fma(ey, ey, ez ez)),  qr = q / r,  qr3 = qr / r^2
+//   e = T - S  (+ (tl - sl) when |e| < 0.1),  r2 = fma(ex, ex, fma(ey, ey, ez ez)),
+//   qr = q / r,  qr3 = qr / r^2,
 // and the halves accumulate separately in P (potential) and X, Y, Z (field without its sign
 // convention).  e carries the difference of the two particles to a few FP32 roundings of
-// itself however close they are.  GUARD (the target's own leaf, which holds the target and
-// any coincident particles) gives r = 0 no contribution; without it r2 starts from the
+// itself however close they are: pairs closer than 0.1 leaf widths -- rare, so the remainders
+// are loaded and added only in an iteration where a lane of the warp has one -- take the
+// remainders.  GUARD (the target's own leaf, which holds the target and any coincident
+// particles) always takes them and gives r = 0 no contribution; without it r2 starts from the
 // smallest normal float, so distinct particles -- which never coincide across leaves --
 // always give a finite 1/r.
+// one pair of the list: its difference e (T - S, plus the remainders for the target's own
+// leaf) and r^2
+template <bool GUARD>
+__device__ __forceinline__ void p2p_diff(const float4* __restrict__ buf, int p, float2 tx, float2 ty, float2 tz,
+                                         float2 lx, float2 ly, float2 lz, float2& ex, float2& ey, float2& ez,
+                                         float2& r2, float2& q) {
+    const float2 m1 = make_float2(-1.f, -1.f);
+    const float4 A = buf[4 * p], B = buf[4 * p + 1];
+    ex = __ffma2_rn(make_float2(A.x, A.y), m1, tx);
+    ey = __ffma2_rn(make_float2(A.z, A.w), m1, ty);
+    ez = __ffma2_rn(make_float2(B.x, B.y), m1, tz);
+    q = make_float2(B.z, B.w);
+    if (GUARD) {
+        const float4 C = buf[4 * p + 2], D = buf[4 * p + 3];
+        ex = __fadd2_rn(ex, __ffma2_rn(make_float2(C.x, C.y), m1, lx));
+        ey = __fadd2_rn(ey, __ffma2_rn(make_float2(C.z, C.w), m1, ly));
+        ez = __fadd2_rn(ez, __ffma2_rn(make_float2(D.x, D.y), m1, lz));
+        r2 = __fmul2_rn(ez, ez);
+    } else {
+        r2 = __ffma2_rn(ez, ez, make_float2(1.17549435e-38f, 1.17549435e-38f));
+    }
+    r2 = __ffma2_rn(ey, ey, r2);
+    r2 = __ffma2_rn(ex, ex, r2);
+}
+
+// a pair closer than 0.1 leaf widths takes the remainders into its difference (halves whose
+// r^2 is below kCloseR2; the others keep T - S)
+__device__ __forceinline__ void p2p_close(const float4* __restrict__ buf, int p, float2 lx, float2 ly, float2 lz,
+                                          float2& ex, float2& ey, float2& ez, float2& r2) {
+    const float2 m1 = make_float2(-1.f, -1.f);
+    const bool cx = r2.x < kCloseR2, cy = r2.y < kCloseR2;
+    const float4 C = buf[4 * p + 2], D = buf[4 * p + 3];
+    const float2 fx = __fadd2_rn(ex, __ffma2_rn(make_float2(C.x, C.y), m1, lx));
+    const float2 fy = __fadd2_rn(ey, __ffma2_rn(make_float2(C.z, C.w), m1, ly));
+    const float2 fz = __fadd2_rn(ez, __ffma2_rn(make_float2(D.x, D.y), m1, lz));
+    if (cx) {
+        ex.x = fx.x;
+        ey.x = fy.x;
+        ez.x = fz.x;
+    }
+    if (cy) {
+        ex.y = fx.y;
+        ey.y = fy.y;
+        ez.y = fz.y;
+    }
+    r2 = __ffma2_rn(ez, ez, make_float2(1.17549435e-38f, 1.17549435e-38f));
+    r2 = __ffma2_rn(ey, ey, r2);
+    r2 = __ffma2_rn(ex, ex, r2);
+}
+
+// the pair's terms into the sums
+template <bool GUARD>
+__device__ __forceinline__ void p2p_acc(float2 ex, float2 ey, float2 ez, float2 r2, float2 q, float2& P, float2& X,
+                                        float2& Y, float2& Z) {
+    const float2 ir = GUARD ? make_float2(rsqrt_or_zero(r2.x), rsqrt_or_zero(r2.y))
+                            : make_float2(rsqrt_approx(r2.x), rsqrt_approx(r2.y));
+    const float2 qr = __fmul2_rn(q, ir);
+    const float2 qr3 = __fmul2_rn(qr, __fmul2_rn(ir, ir));
+    P = __fadd2_rn(P, qr);
+    X = __ffma2_rn(qr3, ex, X);
+    Y = __ffma2_rn(qr3, ey, Y);
+    Z = __ffma2_rn(qr3, ez, Z);
+}
+
+// list pairs [p0, p1) acting on the target t = T + tl (T: rounded offsets, tl: remainders,
+// in the list's frame), both halves of every step in one packed FP32x2 instruction: per half
+//   e = T - S  (+ (tl - sl) when |e| < 0.1),  r2 = fma(ex, ex, fma(ey, ey, ez ez)),
+//   qr = q / r,  qr3 = qr / r^2,
+// and the halves accumulate separately in P (potential) and X, Y, Z (field without its sign
+// convention).  e carries the difference of the two particles to a few FP32 roundings of
+// itself however close they are: pairs closer than 0.1 leaf widths -- rare -- take the
+// remainders, loaded and added only for a group of four pairs in which a lane of the warp has
+// one (one vote per group keeps the four pairs' arithmetic in one stretch of code).  GUARD
+// (the target's own leaf, which holds the target and any coincident particles) always takes
+// them and gives r = 0 no contribution; without it r2 starts from the smallest normal float,
+// so distinct particles -- which never coincide across leaves -- always give a finite 1/r.
 template <bool GUARD>
 __device__ __forceinline__ void p2p_pairs(const float4* __restrict__ buf, int p0, int p1, float2 tx, float2 ty,
                                           float2 tz, float2 lx, float2 ly, float2 lz, float2& P, float2& X,
                                           float2& Y, float2& Z) {
-    const float2 m1 = make_float2(-1.f, -1.f);
-    const float2 tiny = make_float2(1.17549435e-38f, 1.17549435e-38f);
+    int p = p0;
+    if (!GUARD) {
+        for (; p + 4 <= p1; p += 4) {
+            float2 ex[4], ey[4], ez[4], r2[4], q[4];
+            bool close = false;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                p2p_diff<false>(buf, p + k, tx, ty, tz, lx, ly, lz, ex[k], ey[k], ez[k], r2[k], q[k]);
+                close |= r2[k].x < kCloseR2 || r2[k].y < kCloseR2;
+            }
+            if (__any_sync(__activemask(), close)) {
+#pragma unroll
+                for (int k = 0; k < 4; ++k) p2p_close(buf, p + k, lx, ly, lz, ex[k], ey[k], ez[k], r2[k]);
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k) p2p_acc<false>(ex[k], ey[k], ez[k], r2[k], q[k], P, X, Y, Z);
+        }
+    }
 #pragma unroll 4
-    for (int p = p0; p < p1; ++p) {
-        const float4 A = buf[4 * p], B = buf[4 * p + 1], C = buf[4 * p + 2], D = buf[4 * p + 3];
-        const float2 ex = __fadd2_rn(__ffma2_rn(make_float2(A.x, A.y), m1, tx), __ffma2_rn(make_float2(C.x, C.y), m1, lx));
-        const float2 ey = __fadd2_rn(__ffma2_rn(make_float2(A.z, A.w), m1, ty), __ffma2_rn(make_float2(C.z, C.w), m1, ly));
-        const float2 ez = __fadd2_rn(__ffma2_rn(make_float2(B.x, B.y), m1, tz), __ffma2_rn(make_float2(D.x, D.y), m1, lz));
-        float2 r2 = GUARD ? __fmul2_rn(ez, ez) : __ffma2_rn(ez, ez, tiny);
-        r2 = __ffma2_rn(ey, ey, r2);
-        r2 = __ffma2_rn(ex, ex, r2);
-        const float2 ir = GUARD ? make_float2(rsqrt_or_zero(r2.x), rsqrt_or_zero(r2.y))
-                                : make_float2(rsqrt_approx(r2.x), rsqrt_approx(r2.y));
-        const float2 qr = __fmul2_rn(make_float2(B.z, B.w), ir);
-        const float2 qr3 = __fmul2_rn(qr, __fmul2_rn(ir, ir));
-        P = __fadd2_rn(P, qr);
-        X = __ffma2_rn(qr3, ex, X);
-        Y = __ffma2_rn(qr3, ey, Y);
-        Z = __ffma2_rn(qr3, ez, Z);
+    for (; p < p1; ++p) {
+        float2 ex, ey, ez, r2, q;
+        p2p_diff<GUARD>(buf, p, tx, ty, tz, lx, ly, lz, ex, ey, ez, r2, q);
+        if (!GUARD && __any_sync(__activemask(), r2.x < kCloseR2 || r2.y < kCloseR2))
+            p2p_close(buf, p, lx, ly, lz, ex, ey, ez, r2);
+        p2p_acc<GUARD>(ex, ey, ez, r2, q, P, X, Y, Z);
     }
 }
 
@@ -783,7 +873,7 @@ __device__ __forceinline__ void join_halves(CompSums& cs) {
 __device__ __forceinline__ int own_first_slot(int k) { return k == 0 ? 13 : (k <= 13 ? k - 1 : k); }
 
 template <class T>
-__global__ void __launch_bounds__(128) k_leaf(TreeView tv, const double* __restrict__ Lleaf,
+__global__ void __launch_bounds__(128, sizeof(T) == 4 ? 5 : 8) k_leaf(TreeView tv, const double* __restrict__ Lleaf,
                                               double* __restrict__ phi, double* __restrict__ field) {
     const int lane = threadIdx.x;
     const int leaf = blockIdx.x * blockDim.y + threadIdx.y;

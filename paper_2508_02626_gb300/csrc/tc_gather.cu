@@ -45,11 +45,11 @@ __device__ __forceinline__ GItem gdecode(const TCGParams& prm, int w) {
     return it;
 }
 
-// source box of target t for the displacement term `tm` (the parent's colleague at offset a,
-// its child sc, with o - v = 2a + sc), or -1
-__device__ __forceinline__ int m2l_source(const TCGParams& prm, int t, const Terms& tm) {
-    if (t < 0) return -1;
-    int sc = 0, slot = 0;
+// the source of a target for the displacement term `tm` is its parent's colleague at offset
+// a (slot) and that box's child sc, with o - v = 2a + sc
+__device__ __forceinline__ void term_slot(const Terms& tm, int& slot, int& sc) {
+    sc = 0;
+    slot = 0;
     for (int d = 0; d < 3; ++d) {
         const int dd = tm.o[d] - tm.v[d];
         const int c = dd & 1;
@@ -57,8 +57,16 @@ __device__ __forceinline__ int m2l_source(const TCGParams& prm, int t, const Ter
         sc |= c << d;
         slot = slot * 3 + (a + 1);
     }
-    const int Q = prm.colleague[27 * prm.parent[t] + slot];
+}
+// the two dependent loads of that lookup, for a target whose parent is `par` (-1: none)
+__device__ __forceinline__ int colleague_of(const TCGParams& prm, int par, int slot) {
+    return par >= 0 ? prm.colleague[27 * par + slot] : -1;
+}
+__device__ __forceinline__ int child_of(const TCGParams& prm, int Q, int sc) {
     return Q >= 0 ? prm.child[8 * Q + sc] : -1;
+}
+__device__ __forceinline__ int term_key(const Terms& tm) {
+    return (tm.v[0] + 3) * 49 + (tm.v[1] + 3) * 7 + (tm.v[2] + 3);
 }
 
 template <int P, bool H>
@@ -107,7 +115,10 @@ __global__ void __launch_bounds__(192, 1) k_tcg(const __grid_constant__ TCGParam
         }
         int stage = 0;
         uint32_t phase = 0;
-        int pend = -1;  // stage whose copies are committed but not yet signalled
+        // the stage whose copies are committed but not yet signalled: it is signalled once the
+        // next stage's copies are issued (holding more stages back starves the MMAs while this
+        // warp issues)
+        int pend = -1;
         int armed[C::STAGES];
         for (int s = 0; s < C::STAGES; ++s) armed[s] = -1;
         bool ok = true;
@@ -115,20 +126,40 @@ __global__ void __launch_bounds__(192, 1) k_tcg(const __grid_constant__ TCGParam
             const GItem it = gdecode(prm, w);
             const int start = prm.grp_start[it.g] + it.tile * 128;
             const int cnt = min(128, prm.grp_count[it.g] - it.tile * 128);
-            int tgt[4];
+            int par[4];
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
                 const int r = lane + 32 * i;
-                tgt[i] = r < cnt ? prm.tg[start + r] : -1;
+                const int t = r < cnt ? prm.tg[start + r] : -1;
+                par[i] = t >= 0 ? prm.parent[t] : -1;
             }
+            // the valid terms in order, the source lookups running ahead: while the rows of a
+            // term are gathered, the children of the next term's colleagues and the colleagues
+            // of the term after it are being loaded
             Terms tm;
             tm.first(kTcM2L, prm.grp_oct[it.g]);
-            do {
-                if (!tm.valid()) continue;
-                int src[4];
+            bool have = tm.valid() || tm.next_valid();
+            int src[4], qn[4];
+            int slot, sc;
+            term_slot(tm, slot, sc);
 #pragma unroll
-                for (int i = 0; i < 4; ++i) src[i] = m2l_source(prm, tgt[i], tm);
-                const int key = (tm.v[0] + 3) * 49 + (tm.v[1] + 3) * 7 + (tm.v[2] + 3);
+            for (int i = 0; i < 4; ++i) src[i] = child_of(prm, colleague_of(prm, par[i], slot), sc);
+            Terms tn = tm;
+            bool hn = have && tn.next_valid();
+            if (hn) term_slot(tn, slot, sc);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) qn[i] = hn ? colleague_of(prm, par[i], slot) : -1;
+            while (have && ok) {
+                int srcn[4], qnn[4];
+                if (hn) term_slot(tn, slot, sc);
+#pragma unroll
+                for (int i = 0; i < 4; ++i) srcn[i] = hn ? child_of(prm, qn[i], sc) : -1;
+                Terms tnn = tn;
+                const bool hnn = hn && tnn.next_valid();
+                if (hnn) term_slot(tnn, slot, sc);
+#pragma unroll
+                for (int i = 0; i < 4; ++i) qnn[i] = hnn ? colleague_of(prm, par[i], slot) : -1;
+                const int key = term_key(tm);
                 for (int kc = 0; kc < C::NKC; ++kc) {
                     int got = 1;
                     if (lane == 0) got = mbar_wait(smem_u32(&empty[stage]), phase ^ 1u, prm.err, 41) ? 1 : 0;
@@ -157,11 +188,11 @@ __global__ void __launch_bounds__(192, 1) k_tcg(const __grid_constant__ TCGParam
 #pragma unroll
                         for (int j = 0; j < 8; ++j) {
                             const int col = kc * C::KPC + j * (16 / ESZ);  // first element of the 16-byte chunk
-                            const bool have = src[i] >= 0 && col < C::ROWLEN;
-                            const size_t e = have ? (rowoff + col) * ESZ : 0;
+                            const bool hv = src[i] >= 0 && col < C::ROWLEN;
+                            const size_t e = hv ? (rowoff + col) * ESZ : 0;
                             const uint32_t off = rbase + (uint32_t)(((j ^ (r & 7)) & 7) << 4);
-                            cp_async16(sa + off, ahi + e, have ? 16u : 0u);
-                            cp_async16(sa + C::A_BYTES + off, alo + e, have ? 16u : 0u);
+                            cp_async16(sa + off, ahi + e, hv ? 16u : 0u);
+                            cp_async16(sa + C::A_BYTES + off, alo + e, hv ? 16u : 0u);
                         }
                     }
                     cp_async_commit();
@@ -176,7 +207,16 @@ __global__ void __launch_bounds__(192, 1) k_tcg(const __grid_constant__ TCGParam
                         phase ^= 1u;
                     }
                 }
-            } while (ok && tm.next());
+                tm = tn;
+                tn = tnn;
+                have = hn;
+                hn = hnn;
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    src[i] = srcn[i];
+                    qn[i] = qnn[i];
+                }
+            }
         }
         if (pend >= 0) {
             cp_async_wait<0>();
@@ -247,25 +287,32 @@ __global__ void __launch_bounds__(192, 1) k_tcg(const __grid_constant__ TCGParam
             const GItem it = gdecode(prm, w);
             const int cnt = min(128, prm.grp_count[it.g] - it.tile * 128);
             const int trow = row < cnt ? prm.tg[prm.grp_start[it.g] + it.tile * 128 + row] : -1;
+            const int tpar = trow >= 0 ? prm.parent[trow] : -1;
             float S[C::NP];
 #pragma unroll
             for (int j = 0; j < C::NP; ++j) S[j] = 0.f;
+            // F16 operands: the factor undoing the source row's scale and the matrix's scalar,
+            // looked up for the next term before waiting for its accumulator
+            auto factor = [&](const Terms& t) -> float {
+                if constexpr (H) {
+                    int slot, sc;
+                    term_slot(t, slot, sc);
+                    const int sb = child_of(prm, colleague_of(prm, tpar, slot), sc);
+                    return sb >= 0 ? prm.a_inv[sb] * prm.inv_c[term_key(t)] : 0.f;
+                } else {
+                    return 1.f;
+                }
+            };
             Terms tm;
             tm.first(kTcM2L, prm.grp_oct[it.g]);
-            do {
-                if (!tm.valid()) continue;
+            bool have = tm.valid() || tm.next_valid();
+            float f = have ? factor(tm) : 0.f;
+            while (have) {
                 const int buf = uses & 1;
                 ok = mbar_wait(smem_u32(&acc_full[buf]), accf_ph[buf], prm.err, 46);
                 if (!ok) break;
                 accf_ph[buf] ^= 1u;
                 fence_after_sync();
-                // F16 operands: undo the source row's scale and the matrix's scalar
-                float f = 1.f;
-                if constexpr (H) {
-                    const int sb = m2l_source(prm, trow, tm);
-                    f = sb >= 0 ? prm.a_inv[sb] * prm.inv_c[(tm.v[0] + 3) * 49 + (tm.v[1] + 3) * 7 + (tm.v[2] + 3)]
-                                : 0.f;
-                }
                 const uint32_t tb = tmem_base + ((uint32_t)(32 * q) << 16) + (uint32_t)(buf * C::NP);
 #pragma unroll
                 for (int c0 = 0; c0 < C::NP; c0 += 16) {
@@ -280,7 +327,9 @@ __global__ void __launch_bounds__(192, 1) k_tcg(const __grid_constant__ TCGParam
                 fence_before_sync();
                 mbar_arrive(smem_u32(&acc_empty[buf]));
                 ++uses;
-            } while (tm.next() && ok);
+                have = tm.next_valid();
+                if (have) f = factor(tm);
+            }
             if (!ok) break;
             if (trow >= 0) {
                 double* orow = prm.out + (size_t)trow * C::NCP;

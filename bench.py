@@ -31,7 +31,7 @@ UNIT = "particles/s"
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of the M2L kernel on
 # this workload, from one ncu capture of that kernel; valid while the kernel's source files
 # hash to the recorded value, reported as null otherwise
-M2L_TRAFFIC = {"fp32": (79.5e6, "b6f5406ee09268bb")}
+M2L_TRAFFIC = {"fp32": (80.7e6, "9bae660215015e86")}
 M2L_SOURCES = ("paper_2508_02626_gb300/csrc/tc_common.cuh", "paper_2508_02626_gb300/csrc/tc_ops.cu")
 
 
@@ -362,13 +362,14 @@ def run_ours(args, rank, world):
     modes = {}
     mode_results = {}
     if not args.no_modes:
-        for mname in ("mixed", "fp64", "fp64_dense_m2l", "fp32_tf32_m2l"):
-            if mname == args.precision:
+        for mname in ("mixed", "fp64", "fp64_dense_m2l", "fp32_tf32_m2l", "ff"):
+            if mname == args.precision or (args.modes and mname not in args.modes.split(",")):
                 continue
             # fp64 uses the M2L by rotation (Sec. 3.4, the default from p = 4); fp64_dense_m2l
             # the dense matrix per displacement, for comparison; fp32_tf32_m2l the FP32 mode with
             # TF32 instead of F16 split operands in M2L -- against MIXED (the same M2L, FP64
-            # M2M/L2L and storage) it shows what the FP32 shifts cost in accuracy
+            # M2M/L2L and storage) it shows what the FP32 shifts cost in accuracy; ff the
+            # float-float mode (FP64-level accuracy on the FP32 pipe)
             B.dafmm_set_option(ctx.h, B.DAFMM_OPT_M2L_ROTATION, 0 if mname == "fp64_dense_m2l" else -1)
             B.dafmm_set_option(ctx.h, B.DAFMM_OPT_M2L_F16, 0 if mname == "fp32_tf32_m2l" else 1)
             mp = B.PRECISIONS["fp64" if mname.startswith("fp64") else ("fp32" if mname.startswith("fp32") else mname)]
@@ -567,6 +568,12 @@ def run_ours(args, rank, world):
             "oracle_rel_l2_field_vs_direct")}
     if "fp64" in out["modes"]:
         out["config"]["fp64_mode_particles_per_s"] = round(out["modes"]["fp64"]["value"])
+    if "ff" in out["modes"]:  # the float-float mode: FP64-level agreement with the oracle
+        m = out["modes"]["ff"]
+        out["config"]["ff_mode"] = {"particles_per_s": round(m["value"])}
+        for k in ("rel_l2_phi_vs_oracle", "rel_l2_field_vs_oracle"):
+            if k in m:
+                out["config"]["ff_mode"][k] = float("%.3e" % m[k])
     ctx.close()
     return out
 
@@ -1142,6 +1149,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp32", choices=["mixed", "fp64", "fp32"])
     ap.add_argument("--no-modes", action="store_true", help="skip the MIXED / FP64 comparison runs")
+    ap.add_argument("--modes", default="", help="comparison modes to run (comma-separated; default all): "
+                                                "mixed, fp64, fp64_dense_m2l, fp32_tf32_m2l, ff")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-peaks", action="store_true", help="skip the unit-rate probes (dafmm_probe_peak)")

@@ -51,6 +51,12 @@ extern "C" {
 #define DAFMM_FP64 0  /* every step in double precision */
 #define DAFMM_MIXED 1 /* FP32 bulk (P2M, M2L, L2P, P2P); FP64 derivative tensors, M2M/L2L, final sums */
 #define DAFMM_FP32 2  /* FP32 everywhere except the derivative tensors and the final sums */
+#define DAFMM_FF 3    /* FP64-level accuracy with float-float (pairs of FP32 numbers, ~48 significand
+                         bits) for P2M, M2L (by rotation, Sec. 3.4) and the leaves (P2P, L2P) of
+                         uniform trees, FP64 for the rest; adaptive trees and forests: as DAFMM_FP64.
+                         A particle's offset from its leaf centre is held to 2^-49 leaf widths, so a
+                         pair closer than about 1e-3 leaf widths has its difference accurate to that
+                         absolute size rather than to FP64's relative one. */
 
 #define DAFMM_MAX_ORDER 10
 

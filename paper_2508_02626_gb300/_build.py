@@ -58,6 +58,11 @@ def _sources():
     return srcs
 
 
+def _extra_flags():
+    """Extra nvcc flags from DAFMM_NVCC_FLAGS (e.g. -DDAFMM_LEAF_SEG=128 for a tuning build)."""
+    return os.environ.get("DAFMM_NVCC_FLAGS", "").split()
+
+
 def _deps_mtime():
     m = 0.0
     for root, _, files in os.walk(CSRC):
@@ -72,7 +77,10 @@ def _deps_mtime():
 def build(force=False, jobs=None, verbose=False):
     """Generate, compile every translation unit in parallel and link libdafmm.so."""
     generate()
-    if not force and os.path.exists(LIB_PATH) and os.path.getmtime(LIB_PATH) >= _deps_mtime():
+    flags_file = os.path.join(BUILD_DIR, ".flags")
+    extra = _extra_flags()
+    same_flags = os.path.exists(flags_file) and open(flags_file).read() == " ".join(extra)
+    if not force and same_flags and os.path.exists(LIB_PATH) and os.path.getmtime(LIB_PATH) >= _deps_mtime():
         return LIB_PATH
     os.makedirs(BUILD_DIR, exist_ok=True)
     nvcc = _nvcc()
@@ -82,7 +90,7 @@ def build(force=False, jobs=None, verbose=False):
     for s in _sources():
         o = os.path.join(BUILD_DIR, os.path.basename(s) + ".o")
         objs.append(o)
-        cmds.append([nvcc] + NVCC_FLAGS + inc + ["-c", s, "-o", o])
+        cmds.append([nvcc] + NVCC_FLAGS + extra + inc + ["-c", s, "-o", o])
     jobs = jobs or max(1, min(len(cmds), os.cpu_count() or 1))
 
     def run(c):
@@ -101,4 +109,6 @@ def build(force=False, jobs=None, verbose=False):
     if r.returncode != 0:
         raise RuntimeError("link failed:\n%s" % r.stdout)
     os.replace(tmp, LIB_PATH)
+    with open(flags_file, "w") as f:
+        f.write(" ".join(extra))
     return LIB_PATH

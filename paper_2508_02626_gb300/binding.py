@@ -25,7 +25,8 @@ DAFMM_ERR_CANCELLED = -8
 DAFMM_FP64 = 0
 DAFMM_MIXED = 1
 DAFMM_FP32 = 2
-PRECISIONS = {"fp64": DAFMM_FP64, "mixed": DAFMM_MIXED, "fp32": DAFMM_FP32}
+DAFMM_FF = 3
+PRECISIONS = {"fp64": DAFMM_FP64, "mixed": DAFMM_MIXED, "fp32": DAFMM_FP32, "ff": DAFMM_FF}
 DAFMM_OP_NUMERICAL_DA = 16  # or-ed into the precision of a single-operator batch
 MAX_ORDER = 10
 

@@ -393,6 +393,8 @@ void free_order(dafmm_ctx* c, OrderData& od) {
         dev_free(c, od.rot_lx, (size_t)od.rot_len[0] * 32 * sizeof(uint2));
         dev_free(c, od.rot_lz, (size_t)od.rot_len[1] * 32 * sizeof(uint2));
         dev_free(c, od.rot_la, (size_t)od.rot_len[2] * 32 * sizeof(uint2));
+        dev_free(c, od.rot_Tf, (size_t)kNumKeys * 4 * ops->rot_tsz * sizeof(float2));
+        dev_free(c, od.ax_valf, (size_t)od.n_rho * od.ax_nnz * sizeof(float2));
     }
     od = OrderData();
 }
@@ -516,6 +518,33 @@ int ensure_rotation(dafmm_ctx* c, int p, cudaStream_t s) {
         od.rot_lx = od.rot_lz = od.rot_la = nullptr;
         return cuda_fail(c, e, "rotation tables");
     }
+    return DAFMM_OK;
+}
+
+// float-float copies of the rotation tables and axial values (the DAFMM_FF mode's M2L)
+int ensure_rotation_ff(dafmm_ctx* c, int p, cudaStream_t s) {
+    int rc;
+    if ((rc = ensure_rotation(c, p, s))) return rc;
+    OrderData& od = c->ord[p];
+    if (od.rot_Tf) return DAFMM_OK;
+    const OrderOps* ops = order_ops(p);
+    const size_t nt = (size_t)kNumKeys * 4 * ops->rot_tsz, na = (size_t)od.n_rho * od.ax_nnz;
+    float2 *T = nullptr, *A = nullptr;
+    if ((rc = dev_alloc(c, (void**)&T, nt * sizeof(float2), "rotation tables (float-float)"))) return rc;
+    if ((rc = dev_alloc(c, (void**)&A, na * sizeof(float2), "axial M2L matrices (float-float)"))) {
+        dev_free(c, T, nt * sizeof(float2));
+        return rc;
+    }
+    cudaError_t e = ops->to_ff(od.rot_T, T, nt, s);
+    if (e == cudaSuccess) e = ops->to_ff(od.ax_val, A, na, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // shared by every later evaluation, on any stream
+    if (e != cudaSuccess) {
+        dev_free(c, T, nt * sizeof(float2));
+        dev_free(c, A, na * sizeof(float2));
+        return cuda_fail(c, e, "rotation tables (float-float)");
+    }
+    od.rot_Tf = T;
+    od.ax_valf = A;
     return DAFMM_OK;
 }
 
@@ -1447,7 +1476,7 @@ int dafmm_eval(dafmm_tree* t, int order, double theta, int precision, double* ph
     if (order < 0 || order > kMaxOrder) return fail(c, DAFMM_ERR_UNSUPPORTED_ORDER, std::to_string(order));
     if (!(fabs(theta - 1.0) < 1e-12))
         return fail(c, DAFMM_ERR_UNSUPPORTED, "theta other than 1 (nearest-neighbour separation)");
-    if (precision != DAFMM_FP64 && precision != DAFMM_MIXED && precision != DAFMM_FP32)
+    if (precision != DAFMM_FP64 && precision != DAFMM_MIXED && precision != DAFMM_FP32 && precision != DAFMM_FF)
         return fail(c, DAFMM_ERR_INVALID_ARG, "precision");
     CK(c, cudaSetDevice(c->device), "cudaSetDevice");
     cudaStream_t s = (cudaStream_t)stream;
@@ -1475,7 +1504,8 @@ int dafmm_eval(dafmm_tree* t, int order, double theta, int precision, double* ph
         if (!field_dev) dfield = t->out_scratch + N;
     }
     if (t->adaptive) {
-        if ((rc = eval_adaptive(t, order, precision, dphi, dfield, s))) return rc;
+        // (the float-float kernels serve uniform trees; adaptive trees take the FP64 path)
+        if ((rc = eval_adaptive(t, order, precision == DAFMM_FF ? DAFMM_FP64 : precision, dphi, dfield, s))) return rc;
         if (!phi_dev) CK(c, cudaMemcpyAsync(phi, dphi, N * sizeof(double), cudaMemcpyDeviceToHost, s), "D2H");
         if (!field_dev) CK(c, cudaMemcpyAsync(field, dfield, N * 3 * sizeof(double), cudaMemcpyDeviceToHost, s), "D2H");
         if (!phi_dev || !field_dev) CK(c, cudaStreamSynchronize(s), "sync");
@@ -1495,7 +1525,8 @@ int dafmm_eval(dafmm_tree* t, int order, double theta, int precision, double* ph
     if (far) {
         const bool tc_ok = c->m2l_kernel == 0 && c->tc_capable && order >= 2;
         const bool f32 = precision == DAFMM_FP32;
-        const bool tc_m2l = precision != DAFMM_FP64 && tc_ok && (!f32 || (c->tc_mask & 1));
+        const bool fff = precision == DAFMM_FF;  // float-float P2M, M2L and leaves; FP64 shifts
+        const bool tc_m2l = precision != DAFMM_FP64 && !fff && tc_ok && (!f32 || (c->tc_mask & 1));
         const bool tc_m2m = f32 && tc_ok && (c->tc_mask & 2);     // tensor-core M2M (FP32 mode)
         const bool tc_l2l = f32 && tc_ok && (c->tc_mask & 4);     // tensor-core L2L (FP32 mode)
         const bool f16_m2l = tc_m2l && f32 && c->m2l_f16;         // M2L on F16 split operands
@@ -1560,7 +1591,7 @@ int dafmm_eval(dafmm_tree* t, int order, double theta, int precision, double* ph
             }
             CK(c, tc_split_f16_multi(L - 1, src, nrows, hi, lo, inv, order, s, f32_mult), "split");
             ++launches;
-        } else if (precision != DAFMM_FP64 && !(tc_m2m && tc_m2l))
+        } else if (precision != DAFMM_FP64 && !fff && !(tc_m2m && tc_m2l))
             for (int l = 2; l <= L; ++l) {
                 const size_t cnt = level_boxes(l) * od.ncp;
                 if (tc_m2l) {
@@ -1598,14 +1629,20 @@ int dafmm_eval(dafmm_tree* t, int order, double theta, int precision, double* ph
             CK(c, tc_launch(order, a, s), "M2L (tensor cores)");
             ++launches;
         } else {
-            // M2L by rotation (Sec. 3.4); by default from p = 4, where it is the faster one
+            // M2L by rotation (Sec. 3.4); by default from p = 4, where it is the faster one (FP64),
+            // and from p = 2 in float-float
             const bool rot = precision == DAFMM_FP64 && (c->m2l_rot > 0 || (c->m2l_rot < 0 && order >= 4));
+            const bool rot_ff = fff && order >= 2;
             if (rot && (rc = ensure_rotation(c, order, s))) return rc;
+            if (rot_ff && (rc = ensure_rotation_ff(c, order, s))) return rc;
             for (int l = 2; l <= L; ++l) {
                 if (l == L) mark(4);
                 const double inv_h = 1.0 / ldexp(t->dom[3], -l);
-                if (rot) CK(c, ops->m2l_rot(od, l, ex.M[l], ex.L[l], inv_h, s), "M2L (rotation)");
-                else CK(c, ops->m2l_level(od, precision, l, ex.M[l], ex.Mf[l], ex.L[l], inv_h, s), "M2L");
+                if (rot_ff) CK(c, ops->m2l_rot_ff(od, l, ex.M[l], ex.L[l], inv_h, s), "M2L (rotation, float-float)");
+                else if (rot) CK(c, ops->m2l_rot(od, l, ex.M[l], ex.L[l], inv_h, s), "M2L (rotation)");
+                else
+                    CK(c, ops->m2l_level(od, fff ? DAFMM_FP64 : precision, l, ex.M[l], ex.Mf[l], ex.L[l], inv_h, s),
+                       "M2L");
                 ++launches;
             }
         }

@@ -20,7 +20,10 @@
 //                             leaves and the generated L2P of the leaf's local expansion
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "da_common.cuh"
+#include "ff.cuh"
 #include "internal.h"
 #include "tree_adaptive.h"
 #include "tree_common.cuh"
@@ -517,19 +520,58 @@ __global__ void k_axial_gather(const double* __restrict__ K, const int* __restri
 // x = table offset | last-of-output << 31, y = input index | output index << 16.  Lanes with
 // outputs of very different lengths would otherwise run every loop to the longest one, and
 // FP64 instructions are this kernel's bound.
-template <bool ACC>
-__device__ __forceinline__ void rot_step(const uint2* __restrict__ list, int len, const double* __restrict__ tab,
-                                         const double* in, double* out, int lane) {
+// the arithmetic of the rotation M2L: FP64, or float-float (the DAFMM_FF mode)
+__device__ __forceinline__ double rot_add(double a, double b) { return a + b; }
+__device__ __forceinline__ ff rot_add(ff a, ff b) { return ff_acc(a, b); }
+template <class R>
+__device__ __forceinline__ R rot_zero() { return R(0.0); }
+__device__ __forceinline__ double rot_to_double(double a) { return a; }
+__device__ __forceinline__ double rot_to_double(ff a) { return a.to_double(); }
+
+// running sums of a rotation step's output.  FP64: a plain fma chain.  Float-float: a cascaded
+// sum (as Ogita, Rump and Oishi's Sum2): each product's high part joins the high sum through
+// TwoSum and its rounding error, with the product's low part, joins the low sum; the pair is
+// renormalised once per output.  A renormalisation per term (ff_acc) would put about eight
+// dependent FP32 operations between consecutive terms of a lane's chain instead of two adds.
+struct RotAccD {
     double s = 0.0;
+    __device__ __forceinline__ void madd(double a, double b) { s = fma(a, b, s); }
+    __device__ __forceinline__ double get() const { return s; }
+};
+struct RotAccF {
+    float hi = 0.f, lo = 0.f;
+    __device__ __forceinline__ void madd(ff a, ff b) {
+        const ff p = ff_mul(a, b);
+        const ff t = two_sum(hi, p.hi);
+        hi = t.hi;
+        lo += t.lo + p.lo;
+    }
+    __device__ __forceinline__ ff get() const { return fast_two_sum(hi, lo); }
+};
+template <class R>
+struct RotAcc;
+template <>
+struct RotAcc<double> {
+    using type = RotAccD;
+};
+template <>
+struct RotAcc<ff> {
+    using type = RotAccF;
+};
+
+template <bool ACC, class R>
+__device__ __forceinline__ void rot_step(const uint2* __restrict__ list, int len, const R* __restrict__ tab,
+                                         const R* in, R* out, int lane) {
+    typename RotAcc<R>::type s;
 #pragma unroll 4
     for (int t = 0; t < len; ++t) {
         const uint2 w = list[32 * t + lane];
-        s = fma(tab[w.x & 0x7fffffffu], in[w.y & 0xffffu], s);
+        s.madd(tab[w.x & 0x7fffffffu], in[w.y & 0xffffu]);
         if (w.x >> 31) {
             const int k = (int)(w.y >> 16);
-            if (ACC) out[k] += s;
-            else out[k] = s;
-            s = 0.0;
+            if (ACC) out[k] = rot_add(out[k], s.get());
+            else out[k] = s.get();
+            s = typename RotAcc<R>::type();
         }
     }
 }
@@ -544,10 +586,11 @@ struct RotLists {
 
 // one well-separated pair for the warp: S += B_v A_|v| F_v Ms (T: the key's four substitution
 // tables, av: the axial matrix of its length; X, Y: work vectors with X[NC] = Y[NC] = 0)
-__device__ __forceinline__ void rot_pair(const double* __restrict__ T, const double* __restrict__ av, const RotLists& rl,
-                                         const double* __restrict__ Ms, double* X, double* Y, double* S, int lane) {
+template <class R>
+__device__ __forceinline__ void rot_pair(const R* __restrict__ T, const R* __restrict__ av, const RotLists& rl,
+                                         const double* __restrict__ Ms, R* X, R* Y, R* S, int lane) {
     __syncwarp();
-    for (int k = lane; k < NC; k += 32) X[k] = Ms[k];
+    for (int k = lane; k < NC; k += 32) X[k] = R(Ms[k]);
     __syncwarp();
     rot_step<false>(rl.x, rl.lx, T, X, Y, lane);  // forward, about x
     __syncwarp();
@@ -560,11 +603,12 @@ __device__ __forceinline__ void rot_pair(const double* __restrict__ T, const dou
     rot_step<true>(rl.x, rl.lx, T + 3 * ROT_TSZ, X, S, lane);  // back, about x, into the sums
 }
 
-__global__ void __launch_bounds__(256, 2) k_m2l_rot(const double* __restrict__ Ttab, const int* __restrict__ krho,
-                                                    RotLists rl, const double* __restrict__ aval, int annz, int l,
+template <class R>
+__global__ void __launch_bounds__(256, 2) k_m2l_rot(const R* __restrict__ Ttab, const int* __restrict__ krho,
+                                                    RotLists rl, const R* __restrict__ aval, int annz, int l,
                                                     const double* __restrict__ M, double* __restrict__ L,
                                                     double inv_h) {
-    __shared__ double sbuf[8][3][NCP + 1];  // per warp: two work vectors and the sums
+    __shared__ R sbuf[8][3][NCP + 1];  // per warp: two work vectors and the sums
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int Pp = 1 << (l - 1), P3 = Pp * Pp * Pp, n_side = 1 << l;
     const int t = blockIdx.x * 8 + w;  // target box, octant-major
@@ -572,13 +616,13 @@ __global__ void __launch_bounds__(256, 2) k_m2l_rot(const double* __restrict__ T
     const int oct = t / P3, lin = t - oct * P3;
     const int ox = oct & 1, oy = (oct >> 1) & 1, oz = (oct >> 2) & 1;
     const int tx = 2 * (lin % Pp) + ox, ty = 2 * ((lin / Pp) % Pp) + oy, tz = 2 * (lin / (Pp * Pp)) + oz;
-    double* X = sbuf[w][0];
-    double* Y = sbuf[w][1];
-    double* S = sbuf[w][2];
+    R* X = sbuf[w][0];
+    R* Y = sbuf[w][1];
+    R* S = sbuf[w][2];
     for (int k = lane; k <= NCP; k += 32) {
-        X[k] = 0.0;  // X[NC], Y[NC]: the zero that padding tasks read
-        Y[k] = 0.0;
-        S[k] = 0.0;
+        X[k] = rot_zero<R>();  // X[NC], Y[NC]: the zero that padding tasks read
+        Y[k] = rot_zero<R>();
+        S[k] = rot_zero<R>();
     }
     for (int vx = -3 + ox; vx <= 2 + ox; ++vx)
         for (int vy = -3 + oy; vy <= 2 + oy; ++vy)
@@ -587,11 +631,11 @@ __global__ void __launch_bounds__(256, 2) k_m2l_rot(const double* __restrict__ T
                 const int sx = tx - vx, sy = ty - vy, sz = tz - vz;
                 if (sx < 0 || sy < 0 || sz < 0 || sx >= n_side || sy >= n_side || sz >= n_side) continue;
                 const int key = (vx + 3) * 49 + (vy + 3) * 7 + (vz + 3);
-                rot_pair(Ttab + (size_t)key * 4 * ROT_TSZ, aval + (size_t)krho[key] * annz, rl,
-                         M + (size_t)octmajor_index(l, sx, sy, sz) * NCP, X, Y, S, lane);
+                rot_pair<R>(Ttab + (size_t)key * 4 * ROT_TSZ, aval + (size_t)krho[key] * annz, rl,
+                            M + (size_t)octmajor_index(l, sx, sy, sz) * NCP, X, Y, S, lane);
             }
     __syncwarp();
-    for (int k = lane; k < NC; k += 32) L[(size_t)t * NCP + k] = S[k] * inv_h;
+    for (int k = lane; k < NC; k += 32) L[(size_t)t * NCP + k] = rot_to_double(S[k]) * inv_h;
 }
 
 // the same for the targets tg[g0 .. g1) of one (level, octant) group of an adaptive tree (V-list
@@ -629,12 +673,18 @@ __global__ void __launch_bounds__(256, 2) k_m2l_rot_a(const double* __restrict__
                 const int sb = av.child[8 * Q + (scx | (scy << 1) | (scz << 2))];
                 if (sb < 0) continue;
                 const int key = (vx + 3) * 49 + (vy + 3) * 7 + (vz + 3);
-                rot_pair(Ttab + (size_t)key * 4 * ROT_TSZ, aval + (size_t)krho[key] * annz, rl, M + (size_t)sb * NCP,
-                         X, Y, S, lane);
+                rot_pair<double>(Ttab + (size_t)key * 4 * ROT_TSZ, aval + (size_t)krho[key] * annz, rl,
+                                 M + (size_t)sb * NCP, X, Y, S, lane);
             }
     __syncwarp();
     const double inv_h = 1.0 / av.geom[t].w;  // the target box's width (each tree has its own)
     for (int k = lane; k < NC; k += 32) L[(size_t)t * NCP + k] = S[k] * inv_h;
+}
+
+// float-float copies of the rotation tables and axial values (n doubles each)
+__global__ void k_to_ff(const double* __restrict__ a, ff* __restrict__ b, size_t n) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        b[i] = ff(a[i]);
 }
 
 // ---- leaves: P2P over the 27 neighbours + L2P --------------------------------------------------
@@ -654,10 +704,10 @@ __device__ __forceinline__ float rsqrt_or_zero(float x) {
 
 // Shared-memory source list of the near field, in the target leaf's frame: pair p of the list
 // (records 2p and 2p + 1) occupies four float4s from buf[4p]:
-//   (X, X', Y, Y')  (Z, Z', Q, Q')      offsets rounded to FP32 and the charges
-//   (x, x', y, y')  (z, z', 0, 0)       their FP32 remainders
+//   (X, X', Y, Y')  (Z, Z', Q, Q')      offsets and charges rounded to FP32
+//   (x, x', y, y')  (z, z', q, q')      their FP32 remainders
 __device__ __forceinline__ void list_store(float4* buf, int j, float X, float Y, float Z, float Q, float xl,
-                                           float yl, float zl) {
+                                           float yl, float zl, float ql) {
     float* f = reinterpret_cast<float*>(buf) + 16 * (j >> 1) + (j & 1);
     f[0] = X;
     f[2] = Y;
@@ -666,11 +716,11 @@ __device__ __forceinline__ void list_store(float4* buf, int j, float X, float Y,
     f[8] = xl;
     f[10] = yl;
     f[12] = zl;
-    f[14] = 0.f;
+    f[14] = ql;
 }
 // a record that adds exactly nothing (q = 0, far from every target: finite 1/r, no guard needed)
 __device__ __forceinline__ void list_store_null(float4* buf, int j) {
-    list_store(buf, j, 4096.f, 4096.f, 4096.f, 0.f, 0.f, 0.f, 0.f);
+    list_store(buf, j, 4096.f, 4096.f, 4096.f, 0.f, 0.f, 0.f, 0.f, 0.f);
 }
 
 // (H, L) = hi + lo shifted by d with the rounding of hi + d moved into L (Fast2Sum: exact when
@@ -690,6 +740,11 @@ __device__ __forceinline__ void scale_shift_exact(float hi, float lo, float r, f
     const float err = (a - (H - bb)) + (oh - bb);
     L = fmaf(lo, r, err + ol);
 }
+
+// pairs of the list per close-pair vote (the unguarded passes)
+#ifndef DAFMM_P2P_GROUP
+#define DAFMM_P2P_GROUP 2
+#endif
 
 // a pair closer than this (in leaf widths of the target's leaf) takes the remainders of its
 // offsets into its difference: beyond it, T - S alone is within a few FP32 roundings of the
@@ -780,7 +835,7 @@ __device__ __forceinline__ void p2p_acc(float2 ex, float2 ey, float2 ez, float2 
 // convention).  e carries the difference of the two particles to a few FP32 roundings of
 // itself however close they are: pairs closer than 0.1 leaf widths -- rare -- take the
 // remainders, loaded and added only for a group of four pairs in which a lane of the warp has
-// one (one vote per group keeps the four pairs' arithmetic in one stretch of code).  GUARD
+// one (one vote per group keeps the group's arithmetic in one stretch of code).  GUARD
 // (the target's own leaf, which holds the target and any coincident particles) always takes
 // them and gives r = 0 no contribution; without it r2 starts from the smallest normal float,
 // so distinct particles -- which never coincide across leaves -- always give a finite 1/r.
@@ -790,20 +845,21 @@ __device__ __forceinline__ void p2p_pairs(const float4* __restrict__ buf, int p0
                                           float2& Y, float2& Z) {
     int p = p0;
     if (!GUARD) {
-        for (; p + 4 <= p1; p += 4) {
-            float2 ex[4], ey[4], ez[4], r2[4], q[4];
-            bool close = false;
+        constexpr int G = DAFMM_P2P_GROUP;
+        for (; p + G <= p1; p += G) {
+            float2 ex[G], ey[G], ez[G], r2[G], q[G];
+            float rmin = 3.0e38f;
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
+            for (int k = 0; k < G; ++k) {
                 p2p_diff<false>(buf, p + k, tx, ty, tz, lx, ly, lz, ex[k], ey[k], ez[k], r2[k], q[k]);
-                close |= r2[k].x < kCloseR2 || r2[k].y < kCloseR2;
+                rmin = fminf(rmin, fminf(r2[k].x, r2[k].y));
             }
-            if (__any_sync(__activemask(), close)) {
+            if (__any_sync(__activemask(), rmin < kCloseR2)) {
 #pragma unroll
-                for (int k = 0; k < 4; ++k) p2p_close(buf, p + k, lx, ly, lz, ex[k], ey[k], ez[k], r2[k]);
+                for (int k = 0; k < G; ++k) p2p_close(buf, p + k, lx, ly, lz, ex[k], ey[k], ez[k], r2[k]);
             }
 #pragma unroll
-            for (int k = 0; k < 4; ++k) p2p_acc<false>(ex[k], ey[k], ez[k], r2[k], q[k], P, X, Y, Z);
+            for (int k = 0; k < G; ++k) p2p_acc<false>(ex[k], ey[k], ez[k], r2[k], q[k], P, X, Y, Z);
         }
     }
 #pragma unroll 4
@@ -830,8 +886,71 @@ struct CompSums {
 };
 
 
-// records per shared-memory segment of the neighbour list (per warp; 8 KB)
-constexpr int kLeafSeg = 256;
+// ---- float-float near field (the DAFMM_FF mode) ----
+// a cascaded float-float sum (as Ogita, Rump and Oishi's Sum2): the high parts through TwoSum,
+// their rounding errors and the low parts into the low sum; renormalised once, by get()
+struct FFCasc {
+    float hi = 0.f, lo = 0.f;
+    __device__ __forceinline__ void add(ff v) {
+        const ff t = two_sum(hi, v.hi);
+        hi = t.hi;
+        lo += t.lo + v.lo;
+    }
+    __device__ __forceinline__ ff get() const { return fast_two_sum(hi, lo); }
+};
+struct FFSums {
+    FFCasc p, x, y, z;
+};
+
+// the difference (T + tl) - (S + sl) in float-float: TwoSum of the rounded parts (exact), the
+// remainders' difference (below 2^-23 leaf widths, one FP32 rounding) added, renormalised
+__device__ __forceinline__ ff ff_diff(float T, float tl, float S, float sl) {
+    const ff d = two_sum(T, -S);
+    return two_sum(d.hi, d.lo + (tl - sl));
+}
+
+// list records [2 pa, 2 pe) acting on the target t = T + tl, every step in float-float (about
+// 48 bits): e as above, r^2 = e.e, 1/r by the Newton-refined float-float 1/sqrt, q (rounded
+// charge plus its remainder) / r and q / r^3 into float-float sums.  The records below 2 pown
+// are the target's own leaf: a pair at r = 0 (the target itself, coincident particles) adds
+// nothing; elsewhere r^2 is kept at least the smallest normal float.
+__device__ __forceinline__ void p2p_segment_ff(const float4* __restrict__ buf, int pa, int pe, int pown, float tx,
+                                               float ty, float tz, float tlx, float tly, float tlz, FFSums& acc) {
+    for (int p = pa; p < pe; ++p) {
+        const float4 A = buf[4 * p], B = buf[4 * p + 1], C = buf[4 * p + 2], D = buf[4 * p + 3];
+        const bool own = p < pown;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const ff ex = ff_diff(tx, tlx, h ? A.y : A.x, h ? C.y : C.x);
+            const ff ey = ff_diff(ty, tly, h ? A.w : A.z, h ? C.w : C.z);
+            const ff ez = ff_diff(tz, tlz, h ? B.y : B.x, h ? D.y : D.x);
+            ff r2 = ff_acc(ff_acc(ff_mul(ex, ex), ff_mul(ey, ey)), ff_mul(ez, ez));
+            if (own && r2.hi == 0.f) continue;
+            r2.hi = fmaxf(r2.hi, 1.17549435e-38f);
+            const ff ir = ff_rsqrt(r2);
+            const ff qr = ff_mul(ff(h ? B.w : B.z, h ? D.w : D.z), ir);
+            const ff qr3 = ff_mul(qr, ff_mul(ir, ir));
+            acc.p.add(qr);
+            acc.x.add(ff_mul(qr3, ex));
+            acc.y.add(ff_mul(qr3, ey));
+            acc.z.add(ff_mul(qr3, ez));
+        }
+    }
+}
+
+__device__ __forceinline__ ff ff_shfl_down(ff v, int d) {
+    return ff(__shfl_down_sync(0xffffffffu, v.hi, d), __shfl_down_sync(0xffffffffu, v.lo, d));
+}
+
+// records per shared-memory segment of the neighbour list (per warp; 32 bytes each)
+#ifndef DAFMM_LEAF_SEG
+#define DAFMM_LEAF_SEG 128
+#endif
+constexpr int kLeafSeg = DAFMM_LEAF_SEG;
+// blocks per SM the uniform FP32 leaf kernel is compiled for (its register budget)
+#ifndef DAFMM_LEAF_MINB
+#define DAFMM_LEAF_MINB 8
+#endif
 
 // the pairwise sums of one segment of the list: pairs [pa, pe) for this lane's target, those
 // below pown from the target's own leaf (guarded), FP32 partial sums over at most 64 sources
@@ -873,7 +992,8 @@ __device__ __forceinline__ void join_halves(CompSums& cs) {
 __device__ __forceinline__ int own_first_slot(int k) { return k == 0 ? 13 : (k <= 13 ? k - 1 : k); }
 
 template <class T>
-__global__ void __launch_bounds__(128, sizeof(T) == 4 ? 5 : 8) k_leaf(TreeView tv, const double* __restrict__ Lleaf,
+__global__ void __launch_bounds__(128, std::is_same<T, float>::value ? DAFMM_LEAF_MINB : (std::is_same<T, ff>::value ? 4 : 8))
+k_leaf(TreeView tv, const double* __restrict__ Lleaf,
                                               double* __restrict__ phi, double* __restrict__ field) {
     const int lane = threadIdx.x;
     const int leaf = blockIdx.x * blockDim.y + threadIdx.y;
@@ -905,7 +1025,7 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 5 : 8) k_leaf(TreeView t
     // at nb_off (exclusive scan of the counts over the lanes), nb_tot records in all, the
     // first own_pairs pairs the leaf's own
     int nb_n = 0, nb_r0 = 0, nb_off = 0, nb_tot = 0, n_own = 0, own_pad = 0, own_pairs = 0;
-    if constexpr (sizeof(T) == 4) {
+    if constexpr (!std::is_same<T, double>::value) {
         int nb_s0 = 0, nb_s1 = 0;
         if (lane < 27) {
             const int slot = own_first_slot(lane);
@@ -937,13 +1057,13 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 5 : 8) k_leaf(TreeView t
         // FP32: a pass of at most 16 targets splits the sources between the two half-warps,
         // lane l and lane l + 16 taking the same target
         const int m = min(32, i1 - base);
-        const bool split = sizeof(T) == 4 && m <= 16;
+        const bool split = !std::is_same<T, double>::value && m <= 16;
         const int tl = split ? (lane & 15) : lane;
         const int t = base + tl;
         const bool valid = tl < m && (!split || lane < 16);  // the lanes that write
         const int tt = tl < m ? t : i0;
         double fphi = 0.0, fx = 0.0, fy = 0.0, fz = 0.0;  // near field, physical units
-        if constexpr (sizeof(T) == 8) {
+        if constexpr (std::is_same<T, double>::value) {
             const double xt = tv.x[tt], yt = tv.y[tt], zt = tv.z[tt];
             for (int dz = -1; dz <= 1; ++dz)
                 for (int dy = -1; dy <= 1; ++dy)
@@ -968,6 +1088,7 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 5 : 8) k_leaf(TreeView t
             const float4* xl = tv.xq + xq_records(tv.n, tv.nleaf);  // the remainder records
             const float4 pt = xq_load(tv.xq, tt + r_own), pl = xq_load(xl, tt + r_own);
             CompSums cs;
+            FFSums fs;
             // The neighbours' records are copied into one shared-memory list, shifted into this
             // leaf's frame (source + neighbour offset, in leaf widths, exactly: the rounding of
             // the shift joins the remainder), in segments of up to kLeafSeg records; the pairwise
@@ -999,7 +1120,7 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 5 : 8) k_leaf(TreeView t
                         shift_exact(rec.x, rl.x, dx, X, XL);
                         shift_exact(rec.y, rl.y, dy, Y, YL);
                         shift_exact(rec.z, rl.z, dz, Z, ZL);
-                        list_store(buf, i - seg0, X, Y, Z, rec.w, XL, YL, ZL);
+                        list_store(buf, i - seg0, X, Y, Z, rec.w, XL, YL, ZL, rl.w);
                     }
                 }
                 if (lane == 0) {
@@ -1009,14 +1130,31 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 5 : 8) k_leaf(TreeView t
                 __syncwarp();
                 const int np = (segn + 1) >> 1, h = split ? (np + 1) >> 1 : np;
                 const int pa = g ? h : 0, pe = g ? np : h;
-                p2p_segment(buf, pa, pe, own_pairs - (seg0 >> 1), tx2, ty2, tz2, lx2, ly2, lz2, cs);
+                if constexpr (std::is_same<T, float>::value)
+                    p2p_segment(buf, pa, pe, own_pairs - (seg0 >> 1), tx2, ty2, tz2, lx2, ly2, lz2, cs);
+                else
+                    p2p_segment_ff(buf, pa, pe, own_pairs - (seg0 >> 1), pt.x, pt.y, pt.z, pl.x, pl.y, pl.z, fs);
             }
-            if (split) join_halves(cs);
             const double ih = tv.inv_h_leaf, ih2 = ih * ih;
-            fphi = ((double)cs.ph + (double)cs.pl) * ih;
-            fx = ((double)cs.xh + (double)cs.xl) * ih2;
-            fy = ((double)cs.yh + (double)cs.yl) * ih2;
-            fz = ((double)cs.zh + (double)cs.zl) * ih2;
+            if constexpr (std::is_same<T, float>::value) {
+                if (split) join_halves(cs);
+                fphi = ((double)cs.ph + (double)cs.pl) * ih;
+                fx = ((double)cs.xh + (double)cs.xl) * ih2;
+                fy = ((double)cs.yh + (double)cs.yl) * ih2;
+                fz = ((double)cs.zh + (double)cs.zl) * ih2;
+            } else {
+                ff sp = fs.p.get(), sx = fs.x.get(), sy = fs.y.get(), sz = fs.z.get();
+                if (split) {  // the upper half-warp's sums join the lower one's
+                    sp = ff_add(sp, ff_shfl_down(sp, 16));
+                    sx = ff_add(sx, ff_shfl_down(sx, 16));
+                    sy = ff_add(sy, ff_shfl_down(sy, 16));
+                    sz = ff_add(sz, ff_shfl_down(sz, 16));
+                }
+                fphi = sp.to_double() * ih;
+                fx = sx.to_double() * ih2;
+                fy = sy.to_double() * ih2;
+                fz = sz.to_double() * ih2;
+            }
         }
         // far field from the leaf's local expansion
         if (Lrow) {
@@ -1363,7 +1501,7 @@ __global__ void __launch_bounds__(256) k_leaf_a(AdaptiveView av, const int* __re
                         scale_shift_exact(rec.x, rl.x, r, ohx, olx, X, XL);
                         scale_shift_exact(rec.y, rl.y, r, ohy, oly, Y, YL);
                         scale_shift_exact(rec.z, rl.z, r, ohz, olz, Z, ZL);
-                        list_store(buf, fill + i, X, Y, Z, rec.w, XL, YL, ZL);
+                        list_store(buf, fill + i, X, Y, Z, rec.w, XL, YL, ZL, rl.w);
                     }
                     fill += take;
                     i0s += take;
@@ -1501,8 +1639,8 @@ static cudaError_t p2m_launch(const TreeView& tv, int prec, double* M, cudaStrea
     if (tv.nleaf == 0) return cudaSuccess;
     const int rows32 = (prec & kRowsF32) ? 1 : 0;
     prec &= ~kRowsF32;
-    const bool f64 = prec == DAFMM_FP64;
-    const size_t per_warp = (size_t)32 * 33 * (f64 ? 8 : 4);
+    const bool f64 = prec == DAFMM_FP64, fff = prec == DAFMM_FF;
+    const size_t per_warp = (size_t)32 * 33 * (f64 || fff ? 8 : 4);
     int wpb = (int)((96 * 1024) / per_warp);
     wpb = wpb < 1 ? 1 : (wpb > 4 ? 4 : wpb);
     const size_t smem = per_warp * wpb;
@@ -1511,6 +1649,9 @@ static cudaError_t p2m_launch(const TreeView& tv, int prec, double* M, cudaStrea
     if (f64) {
         if ((e = set_smem(k_p2m<double>, smem)) != cudaSuccess) return e;
         k_p2m<double><<<grd, blk, smem, s>>>(tv, M, 0);
+    } else if (fff) {
+        if ((e = set_smem(k_p2m<ff>, smem)) != cudaSuccess) return e;
+        k_p2m<ff><<<grd, blk, smem, s>>>(tv, M, 0);
     } else {
         if ((e = set_smem(k_p2m<float>, smem)) != cudaSuccess) return e;
         k_p2m<float><<<grd, blk, smem, s>>>(tv, M, rows32);
@@ -1579,6 +1720,7 @@ static cudaError_t leaf_launch(const TreeView& tv, int prec, const double* Lleaf
     if (tv.nleaf == 0) return cudaSuccess;
     dim3 blk(32, 4), grd((tv.nleaf + 3) / 4);
     if (prec == DAFMM_FP64) k_leaf<double><<<grd, blk, 0, s>>>(tv, Lleaf, phi, field);
+    else if (prec == DAFMM_FF) k_leaf<ff><<<grd, blk, 0, s>>>(tv, Lleaf, phi, field);
     else k_leaf<float><<<grd, blk, 0, s>>>(tv, Lleaf, phi, field);
     return cudaGetLastError();
 }
@@ -1588,7 +1730,24 @@ static cudaError_t m2l_rot_launch(const OrderData& od, int l, const double* M, d
                                   cudaStream_t s) {
     const int nbox = 1 << (3 * l);
     const RotLists rl{od.rot_lx, od.rot_lz, od.rot_la, od.rot_len[0], od.rot_len[1], od.rot_len[2]};
-    k_m2l_rot<<<(nbox + 7) / 8, 256, 0, s>>>(od.rot_T, od.rot_rho, rl, od.ax_val, od.ax_nnz, l, M, L, inv_h);
+    k_m2l_rot<double><<<(nbox + 7) / 8, 256, 0, s>>>(od.rot_T, od.rot_rho, rl, od.ax_val, od.ax_nnz, l, M, L, inv_h);
+    return cudaGetLastError();
+}
+
+// the same in float-float (DAFMM_FF): tables od.rot_Tf, od.ax_valf
+static cudaError_t m2l_rot_ff_launch(const OrderData& od, int l, const double* M, double* L, double inv_h,
+                                     cudaStream_t s) {
+    const int nbox = 1 << (3 * l);
+    const RotLists rl{od.rot_lx, od.rot_lz, od.rot_la, od.rot_len[0], od.rot_len[1], od.rot_len[2]};
+    k_m2l_rot<ff><<<(nbox + 7) / 8, 256, 0, s>>>(reinterpret_cast<const ff*>(od.rot_Tf), od.rot_rho, rl,
+                                                  reinterpret_cast<const ff*>(od.ax_valf), od.ax_nnz, l, M, L, inv_h);
+    return cudaGetLastError();
+}
+
+static cudaError_t to_ff_launch(const double* a, float2* b, size_t n, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    const size_t blocks = (n + 255) / 256;
+    k_to_ff<<<(unsigned)(blocks < 4096 ? blocks : 4096), 256, 0, s>>>(a, reinterpret_cast<ff*>(b), n);
     return cudaGetLastError();
 }
 
@@ -1770,7 +1929,8 @@ const OrderOps* DAFMM_CAT(order_ops_p, DAFMM_P)() {
         p2m_launch, m2m_launch, l2l_launch, m2l_launch, leaf_launch, kgen_launch, m2l_rot_launch, rot_setup_launch,
         ROT_TSZ,
         op_p2m, op_p2l, op_l2p, op_m2p, op_shift,
-        p2m_a_launch, m2m_a_launch, m2l_a_launch, p2l_a_launch, l2l_a_launch, leaf_a_launch};
+        p2m_a_launch, m2m_a_launch, m2l_a_launch, p2l_a_launch, l2l_a_launch, leaf_a_launch,
+        m2l_rot_ff_launch, to_ff_launch};
     return &ops;
 }
 

@@ -88,6 +88,9 @@ struct OrderData {
     uint2* rot_lz = nullptr;
     uint2* rot_la = nullptr;
     int rot_len[3] = {0, 0, 0};
+    // float-float copies of rot_T and ax_val (the DAFMM_FF mode's M2L), made on first use
+    float2* rot_Tf = nullptr;
+    float2* ax_valf = nullptr;
     ShiftTab m2m() const { return ShiftTab{m2m_rowptr, m2m_col, m2m_par, m2m_val, m2m_valf, m2m_rp8}; }
     ShiftTab l2l() const { return ShiftTab{l2l_rowptr, l2l_col, l2l_par, l2l_val, l2l_valf, l2l_rp8}; }
     MulTab mul() const { return MulTab{mul_rowptr, mul_pairs, mul_minus}; }
@@ -156,6 +159,10 @@ struct OrderOps {
     cudaError_t (*l2l_a)(const OrderData&, const AdaptiveView&, int prec, int lb, int le, double* L, cudaStream_t);
     cudaError_t (*leaf_a)(const AdaptiveView&, const int* leaves, int nleaves, int prec, const double* L,
                           const double* M, double* phi, double* field, int warps, cudaStream_t);
+    // the M2L by rotation of a uniform tree's level in float-float (DAFMM_FF; tables rot_Tf,
+    // ax_valf), and the conversion of n doubles into float-float pairs
+    cudaError_t (*m2l_rot_ff)(const OrderData&, int level, const double* M, double* L, double inv_h, cudaStream_t);
+    cudaError_t (*to_ff)(const double* a, float2* b, size_t n, cudaStream_t);
 };
 
 const OrderOps* order_ops(int p);

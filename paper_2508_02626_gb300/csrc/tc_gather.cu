@@ -12,10 +12,11 @@ namespace tc {
 // Same pipeline as k_tc, but the A rows (source multipoles) of a 128-target tile are gathered
 // one 16-byte chunk at a time with cp.async into the 128-byte-swizzled K-major layout that a
 // TMA box would produce (chunk j of row r at (r / 8) * 1024 + (r % 8) * 128 + (j ^ r % 8) * 16),
-// zero-filled for missing sources and for columns past ncp.  The whole producer warp gathers;
-// its lane 0 also loads the K^_v tile by TMA.  A stage is signalled full once the TMA bytes
-// have landed and every producer lane has seen its own copies complete, fenced them for the
-// async proxy and arrived (33 arrivals: 32 lanes + the expect_tx arrival).
+// zero-filled for missing sources and for columns past ncp.  Two producer warps gather, half the
+// rows each (one warp issuing all of a stage's copies paced the kernel); lane 0 of the first
+// also loads the K^_v tile by TMA.  A stage is signalled full once the TMA bytes have landed and
+// every producer lane has seen its own copies complete, fenced them for the async proxy and
+// arrived (65 arrivals: 2 x 32 lanes + the expect_tx arrival).
 __device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, uint32_t src_bytes) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
 }
@@ -69,8 +70,12 @@ __device__ __forceinline__ int term_key(const Terms& tm) {
     return (tm.v[0] + 3) * 49 + (tm.v[1] + 3) * 7 + (tm.v[2] + 3);
 }
 
+// gather warps: warp 0 (and the TMA of the matrices) takes rows 0-63 of every stage, warp 6
+// rows 64-127
+constexpr int kTcgThreads = 224;
+
 template <int P, bool H>
-__global__ void __launch_bounds__(192, 1) k_tcg(const __grid_constant__ TCGParams prm) {
+__global__ void __launch_bounds__(kTcgThreads, 1) k_tcg(const __grid_constant__ TCGParams prm) {
     using C = Cfg<P, H>;
     constexpr int ESZ = H ? 2 : 4;  // operand element bytes
     extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -86,7 +91,7 @@ __global__ void __launch_bounds__(192, 1) k_tcg(const __grid_constant__ TCGParam
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
         for (int s = 0; s < C::STAGES; ++s) {
-            mbar_init(smem_u32(&full[s]), 33);
+            mbar_init(smem_u32(&full[s]), 65);  // 2 x 32 gather lanes + the expect_tx arrival
             mbar_init(smem_u32(&empty[s]), 1);
         }
         for (int b = 0; b < 2; ++b) {
@@ -107,9 +112,10 @@ __global__ void __launch_bounds__(192, 1) k_tcg(const __grid_constant__ TCGParam
     fence_after_sync();
     const uint32_t tmem_base = *tmem_slot;
 
-    if (warp == 0) {
-        // ---------------- gather producer (whole warp) + TMA of the matrices (lane 0) -------------
-        if (lane == 0) {
+    if (warp == 0 || warp == 6) {
+        // ------- gather producers (two whole warps, half the rows each) + TMA of the matrices -------
+        const int pw = warp == 0 ? 0 : 1;  // rows 64 pw .. 64 pw + 63
+        if (warp == 0 && lane == 0) {
             prefetch_map(&prm.b_hi);
             prefetch_map(&prm.b_lo);
         }
@@ -126,10 +132,10 @@ __global__ void __launch_bounds__(192, 1) k_tcg(const __grid_constant__ TCGParam
             const GItem it = gdecode(prm, w);
             const int start = prm.grp_start[it.g] + it.tile * 128;
             const int cnt = min(128, prm.grp_count[it.g] - it.tile * 128);
-            int par[4];
+            int par[2];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const int r = lane + 32 * i;
+            for (int i = 0; i < 2; ++i) {
+                const int r = lane + 32 * (i + 2 * pw);
                 const int t = r < cnt ? prm.tg[start + r] : -1;
                 par[i] = t >= 0 ? prm.parent[t] : -1;
             }
@@ -139,26 +145,26 @@ __global__ void __launch_bounds__(192, 1) k_tcg(const __grid_constant__ TCGParam
             Terms tm;
             tm.first(kTcM2L, prm.grp_oct[it.g]);
             bool have = tm.valid() || tm.next_valid();
-            int src[4], qn[4];
+            int src[2], qn[2];
             int slot, sc;
             term_slot(tm, slot, sc);
 #pragma unroll
-            for (int i = 0; i < 4; ++i) src[i] = child_of(prm, colleague_of(prm, par[i], slot), sc);
+            for (int i = 0; i < 2; ++i) src[i] = child_of(prm, colleague_of(prm, par[i], slot), sc);
             Terms tn = tm;
             bool hn = have && tn.next_valid();
             if (hn) term_slot(tn, slot, sc);
 #pragma unroll
-            for (int i = 0; i < 4; ++i) qn[i] = hn ? colleague_of(prm, par[i], slot) : -1;
+            for (int i = 0; i < 2; ++i) qn[i] = hn ? colleague_of(prm, par[i], slot) : -1;
             while (have && ok) {
-                int srcn[4], qnn[4];
+                int srcn[2], qnn[2];
                 if (hn) term_slot(tn, slot, sc);
 #pragma unroll
-                for (int i = 0; i < 4; ++i) srcn[i] = hn ? child_of(prm, qn[i], sc) : -1;
+                for (int i = 0; i < 2; ++i) srcn[i] = hn ? child_of(prm, qn[i], sc) : -1;
                 Terms tnn = tn;
                 const bool hnn = hn && tnn.next_valid();
                 if (hnn) term_slot(tnn, slot, sc);
 #pragma unroll
-                for (int i = 0; i < 4; ++i) qnn[i] = hnn ? colleague_of(prm, par[i], slot) : -1;
+                for (int i = 0; i < 2; ++i) qnn[i] = hnn ? colleague_of(prm, par[i], slot) : -1;
                 const int key = term_key(tm);
                 for (int kc = 0; kc < C::NKC; ++kc) {
                     int got = 1;
@@ -169,7 +175,7 @@ __global__ void __launch_bounds__(192, 1) k_tcg(const __grid_constant__ TCGParam
                         break;
                     }
                     unsigned char* st = base + stage * C::STAGE_BYTES;
-                    if (lane == 0) {
+                    if (warp == 0 && lane == 0) {
                         const uint32_t fb = smem_u32(&full[stage]);
                         mbar_expect_tx(fb, 2u * C::B_BYTES);
                         armed[stage] = (int)phase;
@@ -181,8 +187,8 @@ __global__ void __launch_bounds__(192, 1) k_tcg(const __grid_constant__ TCGParam
                     const char* ahi = static_cast<const char*>(prm.a_hi);
                     const char* alo = static_cast<const char*>(prm.a_lo);
 #pragma unroll
-                    for (int i = 0; i < 4; ++i) {
-                        const int r = lane + 32 * i;
+                    for (int i = 0; i < 2; ++i) {
+                        const int r = lane + 32 * (i + 2 * pw);
                         const size_t rowoff = src[i] >= 0 ? (size_t)src[i] * C::ROWLEN : 0;
                         const uint32_t rbase = (uint32_t)((r >> 3) * 1024 + (r & 7) * 128);
 #pragma unroll
@@ -212,7 +218,7 @@ __global__ void __launch_bounds__(192, 1) k_tcg(const __grid_constant__ TCGParam
                 have = hn;
                 hn = hnn;
 #pragma unroll
-                for (int i = 0; i < 4; ++i) {
+                for (int i = 0; i < 2; ++i) {
                     src[i] = srcn[i];
                     qn[i] = qnn[i];
                 }
@@ -224,7 +230,7 @@ __global__ void __launch_bounds__(192, 1) k_tcg(const __grid_constant__ TCGParam
             mbar_arrive(smem_u32(&full[pend]));
         }
         // every copy this warp armed must have landed before the block may exit
-        if (lane == 0)
+        if (warp == 0 && lane == 0)
             for (int s = 0; s < C::STAGES; ++s)
                 if (armed[s] >= 0) mbar_wait(smem_u32(&full[s]), (uint32_t)armed[s], prm.err, 42);
         __syncwarp();
@@ -276,7 +282,7 @@ __global__ void __launch_bounds__(192, 1) k_tcg(const __grid_constant__ TCGParam
         }
         mma_commit(smem_u32(drain));
         mbar_wait(smem_u32(drain), 0, prm.err, 45);
-    } else if (warp >= 2) {
+    } else if (warp >= 2 && warp <= 5) {
         // ---------------- epilogue ----------------
         const int q = warp & 3;
         const int row = 32 * q + lane;
@@ -403,7 +409,7 @@ static cudaError_t launch_tcg(const TCGArgs& a, cudaStream_t s) {
     cudaError_t e = cudaFuncSetAttribute(tc::k_tcg<P, H>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM_BYTES);
     if (e != cudaSuccess) return e;
     const int grid = tiles < a.num_sms ? tiles : a.num_sms;
-    tc::k_tcg<P, H><<<grid, 192, C::SMEM_BYTES, s>>>(prm);
+    tc::k_tcg<P, H><<<grid, tc::kTcgThreads, C::SMEM_BYTES, s>>>(prm);
     return cudaGetLastError();
 }
 

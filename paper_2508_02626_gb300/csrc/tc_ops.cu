@@ -217,34 +217,37 @@ __global__ void __launch_bounds__(192, 1) k_tc(const __grid_constant__ TCParams 
             float S[C::NP];
 #pragma unroll
             for (int j = 0; j < C::NP; ++j) S[j] = 0.f;
+            // F16 operands: each term's accumulator carries the source row's scale and the
+            // matrix's scalar; the factor undoing both (one per row and term) is looked up for
+            // the next term right after a term's accumulator is released, before waiting for the
+            // next one
+            auto factor = [&](const Terms& t) -> float {
+                if constexpr (H) {
+                    const int bx = prm.bx[it.li], by = prm.by[it.li], bz = prm.bz[it.li];
+                    if (row >= bx * by * bz) return 0.f;
+                    int sx, sy, sz, slab, key;
+                    t.source(it, sx, sy, sz, slab, key);
+                    const int S = prm.S[it.li];
+                    sx += row % bx;
+                    sy += (row / bx) % by;
+                    sz += row / (bx * by);
+                    if (sx < 0 || sy < 0 || sz < 0 || sx >= S || sy >= S || sz >= S) return 0.f;
+                    return prm.a_inv[it.li][(size_t)slab * S * S * S + ((size_t)sz * S + sy) * S + sx] * prm.inv_c[key];
+                } else {
+                    return 1.f;
+                }
+            };
             Terms tm;
             tm.first(prm.mode, it.oct);
             bool have = tm.valid() || tm.next_valid();
             int lastbuf = -1;  // the last term's accumulator stays held until the row is out
+            float f = have ? factor(tm) : 0.f;
             while (have) {
                 const int buf = uses & 1;
                 ok = mbar_wait(smem_u32(&acc_full[buf]), accf_ph[buf], prm.err, 31);
                 if (!ok) break;
                 accf_ph[buf] ^= 1u;
                 fence_after_sync();
-                // F16 operands: this term's accumulator carries the source row's scale and the
-                // matrix's scalar; undo both (one factor per row and term)
-                float f = 1.f;
-                if constexpr (H) {
-                    const int bx = prm.bx[it.li], by = prm.by[it.li], bz = prm.bz[it.li];
-                    f = 0.f;
-                    if (row < bx * by * bz) {
-                        int sx, sy, sz, slab, key;
-                        tm.source(it, sx, sy, sz, slab, key);
-                        const int S = prm.S[it.li];
-                        sx += row % bx;
-                        sy += (row / bx) % by;
-                        sz += row / (bx * by);
-                        if (sx >= 0 && sy >= 0 && sz >= 0 && sx < S && sy < S && sz < S)
-                            f = prm.a_inv[it.li][(size_t)slab * S * S * S + ((size_t)sz * S + sy) * S + sx] *
-                                prm.inv_c[key];
-                    }
-                }
                 const uint32_t tb = tmem_base + ((uint32_t)(32 * q) << 16) + (uint32_t)(buf * C::NP);
 #pragma unroll
                 for (int c0 = 0; c0 < C::NP; c0 += 16) {
@@ -261,6 +264,7 @@ __global__ void __launch_bounds__(192, 1) k_tc(const __grid_constant__ TCParams 
                 if (have) {
                     fence_before_sync();
                     mbar_arrive(smem_u32(&acc_empty[buf]));
+                    f = factor(tm);
                 } else {
                     lastbuf = buf;
                 }

@@ -489,7 +489,8 @@ __global__ void k_gather_adaptive(const double* __restrict__ xyz, const double* 
         const float hx = (float)ox, hy = (float)oy, hz = (float)oz;
         const int r = xq0[b] + (t - ab.pbeg[b]);
         xq_store(xq, r, hx, hy, hz, (float)pq);
-        xq_store(xl, r, (float)(ox - (double)hx), (float)(oy - (double)hy), (float)(oz - (double)hz), 0.f);
+        xq_store(xl, r, (float)(ox - (double)hx), (float)(oy - (double)hy), (float)(oz - (double)hz),
+                 (float)(pq - (double)(float)pq));
     }
 }
 

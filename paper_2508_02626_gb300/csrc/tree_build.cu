@@ -245,7 +245,8 @@ __global__ void k_gather_uniform(const double* __restrict__ xyz, const double* _
     const float hx = (float)ox, hy = (float)oy, hz = (float)oz;
     const int r = xq_base(p0, leaf) + (int)(t - p0);
     xq_store(xq, r, hx, hy, hz, (float)pq);
-    xq_store(xl, r, (float)(ox - (double)hx), (float)(oy - (double)hy), (float)(oz - (double)hz), 0.f);
+    xq_store(xl, r, (float)(ox - (double)hx), (float)(oy - (double)hy), (float)(oz - (double)hz),
+             (float)(pq - (double)(float)pq));
 }
 
 __global__ void k_leaf_ranges(const uint64_t* __restrict__ keys, int64_t n, int nleaf, int* leaf_start) {

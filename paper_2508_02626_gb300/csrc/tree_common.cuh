@@ -21,8 +21,8 @@
 // per leaf box.  n particles in g leaves take at most xq_records(n, g) records = float4s.
 //
 // The record array holds two such halves of xq_records(n, g) float4s each: the first holds
-// the offsets rounded to FP32 (hi) and the charge, the second, at the same record index, the
-// FP32 remainders lo = fl(off - hi) of the three offsets (charge slot zero).  hi + lo carries
+// the offsets rounded to FP32 (hi) and the charge rounded to FP32, the second, at the same
+// record index, the FP32 remainders lo = fl(v - hi) of the three offsets and of the charge.  hi + lo carries
 // the offset to about 2^-48 leaf widths, so the near field can form the difference of two
 // close particles from both parts with a relative error of a few FP32 roundings instead of
 // the 2^-25 leaf widths of the rounded offsets alone (which dominated the field's error

@@ -1638,8 +1638,13 @@ int dafmm_eval(dafmm_tree* t, int order, double theta, int precision, double* ph
             for (int l = 2; l <= L; ++l) {
                 if (l == L) mark(4);
                 const double inv_h = 1.0 / ldexp(t->dom[3], -l);
-                if (rot_ff) CK(c, ops->m2l_rot_ff(od, l, ex.M[l], ex.L[l], inv_h, s), "M2L (rotation, float-float)");
-                else if (rot) CK(c, ops->m2l_rot(od, l, ex.M[l], ex.L[l], inv_h, s), "M2L (rotation)");
+                if (rot_ff) {
+                    CK(c, ops->split_ff(ex.M[l], ex.Mhi[l], ex.Mlo[l], level_boxes(l) * od.ncp, s), "split");
+                    CK(c, ops->m2l_rot_ff(od, l, ex.Mhi[l], ex.Mlo[l], ex.L[l], inv_h, s), "M2L (rotation, float-float)");
+                    ++launches;
+                }
+                else if (rot)
+                    CK(c, ops->m2l_rot(od, l, ex.M[l], ex.L[l], inv_h, s), "M2L (rotation)");
                 else
                     CK(c, ops->m2l_level(od, fff ? DAFMM_FP64 : precision, l, ex.M[l], ex.Mf[l], ex.L[l], inv_h, s),
                        "M2L");

@@ -89,6 +89,11 @@ struct SmemRowF {
     const float* row;
     __device__ __forceinline__ float operator()(int k) const { return row[k]; }
 };
+// the same as float-float pairs
+struct SmemRowFF {
+    const ff* row;
+    __device__ __forceinline__ ff operator()(int k) const { return row[k]; }
+};
 
 // the warp copies an FP64 row into `buf` as FP32
 __device__ __forceinline__ void warp_row_to_f32(const double* __restrict__ row, float* buf, int lane) {
@@ -584,13 +589,24 @@ struct RotLists {
     int lx, lz, la;
 };
 
+// a source row into the work vector: FP64 rows, or (float-float) the rows' FP32 high and low
+// parts, split once per evaluation
+__device__ __forceinline__ void rot_load(double* X, const double* M, const float*, const float*, size_t row, int lane) {
+    for (int k = lane; k < NC; k += 32) X[k] = M[row + k];
+}
+__device__ __forceinline__ void rot_load(ff* X, const double*, const float* Mh, const float* Ml, size_t row, int lane) {
+    for (int k = lane; k < NC; k += 32) X[k] = ff(Mh[row + k], Ml[row + k]);
+}
+
 // one well-separated pair for the warp: S += B_v A_|v| F_v Ms (T: the key's four substitution
-// tables, av: the axial matrix of its length; X, Y: work vectors with X[NC] = Y[NC] = 0)
+// tables, av: the axial matrix of its length; X, Y: work vectors with X[NC] = Y[NC] = 0; the
+// source row at `row` of M, or of Mh / Ml in float-float)
 template <class R>
 __device__ __forceinline__ void rot_pair(const R* __restrict__ T, const R* __restrict__ av, const RotLists& rl,
-                                         const double* __restrict__ Ms, R* X, R* Y, R* S, int lane) {
+                                         const double* __restrict__ M, const float* __restrict__ Mh,
+                                         const float* __restrict__ Ml, size_t row, R* X, R* Y, R* S, int lane) {
     __syncwarp();
-    for (int k = lane; k < NC; k += 32) X[k] = R(Ms[k]);
+    rot_load(X, M, Mh, Ml, row, lane);
     __syncwarp();
     rot_step<false>(rl.x, rl.lx, T, X, Y, lane);  // forward, about x
     __syncwarp();
@@ -603,22 +619,48 @@ __device__ __forceinline__ void rot_pair(const R* __restrict__ T, const R* __res
     rot_step<true>(rl.x, rl.lx, T + 3 * ROT_TSZ, X, S, lane);  // back, about x, into the sums
 }
 
+// the per-warp work vectors of k_m2l_rot
+template <class R>
+struct RotBuf {
+    R v[3][NCP + 1];
+};
+
+// R = double: FP64, work vectors in static shared memory, task lists read from global memory.
+// R = ff: float-float, the task lists (the same for every pair) copied into shared memory
+// after the work vectors (dynamic shared memory), the source rows from the FP32 split parts.
 template <class R>
 __global__ void __launch_bounds__(256, 2) k_m2l_rot(const R* __restrict__ Ttab, const int* __restrict__ krho,
                                                     RotLists rl, const R* __restrict__ aval, int annz, int l,
-                                                    const double* __restrict__ M, double* __restrict__ L,
+                                                    const double* __restrict__ M, const float* __restrict__ Mh,
+                                                    const float* __restrict__ Ml, double* __restrict__ L,
                                                     double inv_h) {
-    __shared__ R sbuf[8][3][NCP + 1];  // per warp: two work vectors and the sums
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    RotBuf<R>* bufs;
+    if constexpr (std::is_same<R, double>::value) {
+        __shared__ RotBuf<double> sbuf[8];
+        bufs = sbuf;
+    } else {
+        extern __shared__ __align__(16) unsigned char rot_smem[];
+        bufs = reinterpret_cast<RotBuf<R>*>(rot_smem);
+        uint2* lists = reinterpret_cast<uint2*>(rot_smem + 8 * sizeof(RotBuf<R>));
+        const int nx = 32 * rl.lx, nz = 32 * rl.lz, na = 32 * rl.la;
+        for (int i = threadIdx.x; i < nx; i += blockDim.x) lists[i] = rl.x[i];
+        for (int i = threadIdx.x; i < nz; i += blockDim.x) lists[nx + i] = rl.z[i];
+        for (int i = threadIdx.x; i < na; i += blockDim.x) lists[nx + nz + i] = rl.a[i];
+        __syncthreads();
+        rl.x = lists;
+        rl.z = lists + nx;
+        rl.a = lists + nx + nz;
+    }
     const int Pp = 1 << (l - 1), P3 = Pp * Pp * Pp, n_side = 1 << l;
     const int t = blockIdx.x * 8 + w;  // target box, octant-major
     if (t >= 8 * P3) return;
     const int oct = t / P3, lin = t - oct * P3;
     const int ox = oct & 1, oy = (oct >> 1) & 1, oz = (oct >> 2) & 1;
     const int tx = 2 * (lin % Pp) + ox, ty = 2 * ((lin / Pp) % Pp) + oy, tz = 2 * (lin / (Pp * Pp)) + oz;
-    R* X = sbuf[w][0];
-    R* Y = sbuf[w][1];
-    R* S = sbuf[w][2];
+    R* X = bufs[w].v[0];
+    R* Y = bufs[w].v[1];
+    R* S = bufs[w].v[2];
     for (int k = lane; k <= NCP; k += 32) {
         X[k] = rot_zero<R>();  // X[NC], Y[NC]: the zero that padding tasks read
         Y[k] = rot_zero<R>();
@@ -631,11 +673,20 @@ __global__ void __launch_bounds__(256, 2) k_m2l_rot(const R* __restrict__ Ttab, 
                 const int sx = tx - vx, sy = ty - vy, sz = tz - vz;
                 if (sx < 0 || sy < 0 || sz < 0 || sx >= n_side || sy >= n_side || sz >= n_side) continue;
                 const int key = (vx + 3) * 49 + (vy + 3) * 7 + (vz + 3);
-                rot_pair<R>(Ttab + (size_t)key * 4 * ROT_TSZ, aval + (size_t)krho[key] * annz, rl,
-                            M + (size_t)octmajor_index(l, sx, sy, sz) * NCP, X, Y, S, lane);
+                rot_pair<R>(Ttab + (size_t)key * 4 * ROT_TSZ, aval + (size_t)krho[key] * annz, rl, M, Mh, Ml,
+                            (size_t)octmajor_index(l, sx, sy, sz) * NCP, X, Y, S, lane);
             }
     __syncwarp();
     for (int k = lane; k < NC; k += 32) L[(size_t)t * NCP + k] = rot_to_double(S[k]) * inv_h;
+}
+
+// the float-float split of FP64 rows (n values): hi = fl32(v), lo = fl32(v - hi)
+__global__ void k_split_ff(const double* __restrict__ a, float* __restrict__ hi, float* __restrict__ lo, size_t n) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const ff v(a[i]);
+        hi[i] = v.hi;
+        lo[i] = v.lo;
+    }
 }
 
 // the same for the targets tg[g0 .. g1) of one (level, octant) group of an adaptive tree (V-list
@@ -673,8 +724,8 @@ __global__ void __launch_bounds__(256, 2) k_m2l_rot_a(const double* __restrict__
                 const int sb = av.child[8 * Q + (scx | (scy << 1) | (scz << 2))];
                 if (sb < 0) continue;
                 const int key = (vx + 3) * 49 + (vy + 3) * 7 + (vz + 3);
-                rot_pair<double>(Ttab + (size_t)key * 4 * ROT_TSZ, aval + (size_t)krho[key] * annz, rl,
-                                 M + (size_t)sb * NCP, X, Y, S, lane);
+                rot_pair<double>(Ttab + (size_t)key * 4 * ROT_TSZ, aval + (size_t)krho[key] * annz, rl, M,
+                                 nullptr, nullptr, (size_t)sb * NCP, X, Y, S, lane);
             }
     __syncwarp();
     const double inv_h = 1.0 / av.geom[t].w;  // the target box's width (each tree has its own)
@@ -916,6 +967,7 @@ __device__ __forceinline__ ff ff_diff(float T, float tl, float S, float sl) {
 // nothing; elsewhere r^2 is kept at least the smallest normal float.
 __device__ __forceinline__ void p2p_segment_ff(const float4* __restrict__ buf, int pa, int pe, int pown, float tx,
                                                float ty, float tz, float tlx, float tly, float tlz, FFSums& acc) {
+#pragma unroll 1
     for (int p = pa; p < pe; ++p) {
         const float4 A = buf[4 * p], B = buf[4 * p + 1], C = buf[4 * p + 2], D = buf[4 * p + 3];
         const bool own = p < pown;
@@ -1007,6 +1059,14 @@ k_leaf(TreeView tv, const double* __restrict__ Lleaf,
     const double cz = tv.z0 + ((double)c + 0.5) * tv.h_leaf;
     const double* Lrow = Lleaf ? Lleaf + (size_t)leaf * NCP : nullptr;
     __shared__ float s_lrow[4][NCP];  // per warp: the leaf's local expansion in FP32
+    __shared__ ff s_lrow_ff[std::is_same<T, ff>::value ? 4 : 1][std::is_same<T, ff>::value ? NCP : 1];
+    if constexpr (std::is_same<T, ff>::value) {  // ... or in float-float
+        if (Lrow) {
+            __syncwarp();
+            for (int k = lane; k < NC; k += 32) s_lrow_ff[threadIdx.y][k] = ff(Lrow[k]);
+            __syncwarp();
+        }
+    }
     if constexpr (sizeof(T) == 4) {
         if (Lrow) {
             if (tv.locals_f32) {  // the row is FP32 already (NCP floats per leaf)
@@ -1169,6 +1229,8 @@ k_leaf(TreeView tv, const double* __restrict__ Lleaf,
                 xs = (T)pt.x; ys = (T)pt.y; zs = (T)pt.z;
             }
             if constexpr (sizeof(T) == 4) gen::GEN(l2p)<T>(SmemRowF{s_lrow[threadIdx.y]}, xs, ys, zs, F, g0, g1, g2);
+            else if constexpr (std::is_same<T, ff>::value)
+                gen::GEN(l2p)<T>(SmemRowFF{s_lrow_ff[threadIdx.y]}, xs, ys, zs, F, g0, g1, g2);
             else gen::GEN(l2p)<T>(RowLoad<T>{Lrow}, xs, ys, zs, F, g0, g1, g2);
             fphi += (double)F;
             fx -= (double)g0 * tv.inv_h_leaf;
@@ -1730,17 +1792,30 @@ static cudaError_t m2l_rot_launch(const OrderData& od, int l, const double* M, d
                                   cudaStream_t s) {
     const int nbox = 1 << (3 * l);
     const RotLists rl{od.rot_lx, od.rot_lz, od.rot_la, od.rot_len[0], od.rot_len[1], od.rot_len[2]};
-    k_m2l_rot<double><<<(nbox + 7) / 8, 256, 0, s>>>(od.rot_T, od.rot_rho, rl, od.ax_val, od.ax_nnz, l, M, L, inv_h);
+    k_m2l_rot<double><<<(nbox + 7) / 8, 256, 0, s>>>(od.rot_T, od.rot_rho, rl, od.ax_val, od.ax_nnz, l, M, nullptr,
+                                                      nullptr, L, inv_h);
     return cudaGetLastError();
 }
 
-// the same in float-float (DAFMM_FF): tables od.rot_Tf, od.ax_valf
-static cudaError_t m2l_rot_ff_launch(const OrderData& od, int l, const double* M, double* L, double inv_h,
-                                     cudaStream_t s) {
+// the same in float-float (DAFMM_FF): tables od.rot_Tf, od.ax_valf; the source rows' FP32 parts
+// Mh, Ml (k_split_ff); the task lists staged in shared memory
+static cudaError_t m2l_rot_ff_launch(const OrderData& od, int l, const float* Mh, const float* Ml, double* L,
+                                     double inv_h, cudaStream_t s) {
     const int nbox = 1 << (3 * l);
     const RotLists rl{od.rot_lx, od.rot_lz, od.rot_la, od.rot_len[0], od.rot_len[1], od.rot_len[2]};
-    k_m2l_rot<ff><<<(nbox + 7) / 8, 256, 0, s>>>(reinterpret_cast<const ff*>(od.rot_Tf), od.rot_rho, rl,
-                                                  reinterpret_cast<const ff*>(od.ax_valf), od.ax_nnz, l, M, L, inv_h);
+    const size_t smem = 8 * sizeof(RotBuf<ff>) + (size_t)32 * (rl.lx + rl.lz + rl.la) * sizeof(uint2);
+    cudaError_t e = cudaFuncSetAttribute(k_m2l_rot<ff>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_m2l_rot<ff><<<(nbox + 7) / 8, 256, smem, s>>>(reinterpret_cast<const ff*>(od.rot_Tf), od.rot_rho, rl,
+                                                     reinterpret_cast<const ff*>(od.ax_valf), od.ax_nnz, l, nullptr,
+                                                     Mh, Ml, L, inv_h);
+    return cudaGetLastError();
+}
+
+static cudaError_t split_ff_launch(const double* a, float* hi, float* lo, size_t n, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    const size_t blocks = (n + 255) / 256;
+    k_split_ff<<<(unsigned)(blocks < 4096 ? blocks : 4096), 256, 0, s>>>(a, hi, lo, n);
     return cudaGetLastError();
 }
 
@@ -1930,7 +2005,7 @@ const OrderOps* DAFMM_CAT(order_ops_p, DAFMM_P)() {
         ROT_TSZ,
         op_p2m, op_p2l, op_l2p, op_m2p, op_shift,
         p2m_a_launch, m2m_a_launch, m2l_a_launch, p2l_a_launch, l2l_a_launch, leaf_a_launch,
-        m2l_rot_ff_launch, to_ff_launch};
+        m2l_rot_ff_launch, to_ff_launch, split_ff_launch};
     return &ops;
 }
 

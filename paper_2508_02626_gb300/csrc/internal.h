@@ -160,9 +160,13 @@ struct OrderOps {
     cudaError_t (*leaf_a)(const AdaptiveView&, const int* leaves, int nleaves, int prec, const double* L,
                           const double* M, double* phi, double* field, int warps, cudaStream_t);
     // the M2L by rotation of a uniform tree's level in float-float (DAFMM_FF; tables rot_Tf,
-    // ax_valf), and the conversion of n doubles into float-float pairs
-    cudaError_t (*m2l_rot_ff)(const OrderData&, int level, const double* M, double* L, double inv_h, cudaStream_t);
+    // ax_valf; source rows as FP32 high and low parts), and the conversion of n doubles into
+    // float-float pairs
+    cudaError_t (*m2l_rot_ff)(const OrderData&, int level, const float* Mh, const float* Ml, double* L, double inv_h,
+                              cudaStream_t);
     cudaError_t (*to_ff)(const double* a, float2* b, size_t n, cudaStream_t);
+    // the float-float split of n FP64 values into their FP32 high and low parts
+    cudaError_t (*split_ff)(const double* a, float* hi, float* lo, size_t n, cudaStream_t);
 };
 
 const OrderOps* order_ops(int p);

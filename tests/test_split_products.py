@@ -52,8 +52,9 @@ def split16(x):
     return hi.astype(np.float32), lo.astype(np.float32)
 
 
-def f16x3_local(Ks, Ms, scaled=True):
-    """The local expansion sum_v K_v M_v by the F16 split scheme (FP32 result as float64)."""
+def f16x3_local(Ks, Ms, scaled=True, products=("hh", "hl", "lh")):
+    """The local expansion sum_v K_v M_v by the F16 split scheme (FP32 result as float64);
+    `products` picks the split products kept (K part, M part: h = hi, l = lo)."""
     r = np.array([pow2_scale(m) for m in np.abs(Ks).max(axis=(0, 2))]) if scaled else np.ones(Ks.shape[1])
     L = np.zeros(Ks.shape[1], np.float32)
     with np.errstate(over="ignore", invalid="ignore"):
@@ -63,7 +64,11 @@ def f16x3_local(Ks, Ms, scaled=True):
             g = pow2_scale(np.abs(M).max()) if scaled else 1.0
             Khi, Klo = split16(Kr * s)
             Mhi, Mlo = split16(M * g)
-            L = L + ((Khi @ Mhi + Khi @ Mlo) + Klo @ Mhi) * np.float32(1.0 / (g * s))
+            parts = {"hh": (Khi, Mhi), "hl": (Khi, Mlo), "lh": (Klo, Mhi)}
+            t = np.zeros_like(L)
+            for k in products:
+                t = t + parts[k][0] @ parts[k][1]
+            L = L + t * np.float32(1.0 / (g * s))
         return L.astype(np.float64) / r
 
 
@@ -155,3 +160,17 @@ def test_power_of_two_scaling_is_charge_scale_invariant(p):
     # without the scales: charges at 2^-30 underflow in F16, charges at 2^20 overflow it
     assert unscaled[1] > 0.5
     assert not np.isfinite(unscaled[2]) or unscaled[2] > 0.5
+
+
+@pytest.mark.parametrize("p", [4, 8, 10])
+def test_two_products_miss_the_fp32_bound(p):
+    """Dropping either cross product (two MMAs per term instead of three) leaves the F16
+    rounding of the dropped part, about 2^-11 relative: 1e-4..1e-3 here, far above the FP32
+    mode's 3.8e-6 bound, so the kernel keeps three products."""
+    Ks = matrices(p)
+    Ms, X = workload(p, 0)
+    L64 = np.einsum("vba,va->b", Ks, Ms)
+    e3 = potential_error(p, f16x3_local(Ks, Ms), L64, X)
+    for keep in (("hh", "hl"), ("hh", "lh")):
+        e2 = potential_error(p, f16x3_local(Ks, Ms, products=keep), L64, X)
+        assert e2 > 10 * 3.8e-6 and e2 > 100 * e3, (keep, e2, e3)

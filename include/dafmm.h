@@ -46,6 +46,7 @@ extern "C" {
 #define DAFMM_ERR_UNSUPPORTED (-6)       /* a valid but unimplemented option (e.g. theta != 1) */
 #define DAFMM_ERR_NO_DEVICE (-7)
 #define DAFMM_ERR_CANCELLED (-8)         /* a served request dropped because its server stopped */
+#define DAFMM_ERR_CHECK (-9)             /* an index check of a checked build (DAFMM_CHECK) failed */
 
 /* arithmetic of an evaluation */
 #define DAFMM_FP64 0  /* every step in double precision */
@@ -231,6 +232,20 @@ int dafmm_sync(dafmm_ctx* ctx, void* stream);
  * trees stay usable.  Returns DAFMM_OK once the kernel is launched, DAFMM_ERR_CUDA if the
  * launch fails, DAFMM_ERR_INVALID_ARG for a NULL context. */
 int dafmm_debug_expire_wait(dafmm_ctx* ctx, void* stream);
+/* The checked build (the paper has no counterpart).  A library compiled with -DDAFMM_CHECK
+ * guards every device access whose index is read from memory (particle ranges of leaves and
+ * boxes, box indices from the tree arrays and interaction lists, list pointers, rotation task
+ * entries, sort and gather positions, the gathered M2L's source rows): a failing check records
+ * its site code, the index and the bound, and the access is skipped -- no trap.  dafmm_sync
+ * then returns DAFMM_ERR_CHECK, its message naming the site, index and bound, and clears the
+ * record; the context stays usable (the results of that evaluation are not).  The record is
+ * per device, shared by the contexts on it.
+ * dafmm_debug_check launches on `stream` one kernel whose check fails on purpose (site code
+ * 99: index 32 against the bound 32; the guarded array holds 64 entries, so the access would be
+ * in bounds even unchecked).  Returns DAFMM_OK once launched; DAFMM_ERR_UNSUPPORTED in a
+ * library built without DAFMM_CHECK; DAFMM_ERR_CUDA if the launch fails;
+ * DAFMM_ERR_INVALID_ARG for a NULL context. */
+int dafmm_debug_check(dafmm_ctx* ctx, void* stream);
 
 /* dafmm_eval without device allocation.  (The paper has no counterpart: this exists for
  * callers that cannot call cudaMalloc while they evaluate -- a service whose device memory

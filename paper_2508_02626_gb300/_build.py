@@ -16,6 +16,9 @@ CSRC = os.path.join(PKG, "csrc")
 GEN_DIR = os.path.join(CSRC, "generated")
 BUILD_DIR = os.path.join(PKG, "_build")
 LIB_PATH = os.path.join(BUILD_DIR, "libdafmm.so")
+# the checked build (-DDAFMM_CHECK: device index checks that record a site code, no trap)
+CHECK_BUILD_DIR = os.path.join(PKG, "_build_check")
+CHECK_LIB_PATH = os.path.join(CHECK_BUILD_DIR, "libdafmm_check.so")
 MAXORD = 10
 
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-lineinfo", "-O3", "-std=c++17",
@@ -74,21 +77,23 @@ def _deps_mtime():
     return m
 
 
-def build(force=False, jobs=None, verbose=False):
-    """Generate, compile every translation unit in parallel and link libdafmm.so."""
+def build(force=False, jobs=None, verbose=False, checked=False):
+    """Generate, compile every translation unit in parallel and link libdafmm.so (checked:
+    libdafmm_check.so, compiled with -DDAFMM_CHECK into its own folder)."""
     generate()
-    flags_file = os.path.join(BUILD_DIR, ".flags")
-    extra = _extra_flags()
+    build_dir, lib_path = (CHECK_BUILD_DIR, CHECK_LIB_PATH) if checked else (BUILD_DIR, LIB_PATH)
+    flags_file = os.path.join(build_dir, ".flags")
+    extra = _extra_flags() + (["-DDAFMM_CHECK"] if checked else [])
     same_flags = os.path.exists(flags_file) and open(flags_file).read() == " ".join(extra)
-    if not force and same_flags and os.path.exists(LIB_PATH) and os.path.getmtime(LIB_PATH) >= _deps_mtime():
-        return LIB_PATH
-    os.makedirs(BUILD_DIR, exist_ok=True)
+    if not force and same_flags and os.path.exists(lib_path) and os.path.getmtime(lib_path) >= _deps_mtime():
+        return lib_path
+    os.makedirs(build_dir, exist_ok=True)
     nvcc = _nvcc()
     inc = ["-I", CSRC, "-I", os.path.join(os.path.dirname(PKG), "include")]
     objs = []
     cmds = []
     for s in _sources():
-        o = os.path.join(BUILD_DIR, os.path.basename(s) + ".o")
+        o = os.path.join(build_dir, os.path.basename(s) + ".o")
         objs.append(o)
         cmds.append([nvcc] + NVCC_FLAGS + extra + inc + ["-c", s, "-o", o])
     jobs = jobs or max(1, min(len(cmds), os.cpu_count() or 1))
@@ -103,12 +108,12 @@ def build(force=False, jobs=None, verbose=False):
                 print(out)
             if rc != 0:
                 raise RuntimeError("nvcc failed:\n%s\n%s" % (" ".join(c), out))
-    tmp = LIB_PATH + ".tmp.%d" % os.getpid()
+    tmp = lib_path + ".tmp.%d" % os.getpid()
     link = [nvcc, "-shared", "-gencode", "arch=compute_103a,code=sm_103a", "-o", tmp] + objs
     r = subprocess.run(link, stdout=subprocess.PIPE, stderr=subprocess.STDOUT, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n%s" % r.stdout)
-    os.replace(tmp, LIB_PATH)
+    os.replace(tmp, lib_path)
     with open(flags_file, "w") as f:
         f.write(" ".join(extra))
-    return LIB_PATH
+    return lib_path

@@ -21,6 +21,7 @@ DAFMM_ERR_TIMEOUT = -5
 DAFMM_ERR_UNSUPPORTED = -6
 DAFMM_ERR_NO_DEVICE = -7
 DAFMM_ERR_CANCELLED = -8
+DAFMM_ERR_CHECK = -9
 
 DAFMM_FP64 = 0
 DAFMM_MIXED = 1
@@ -46,6 +47,7 @@ SIGNATURES = {
     "dafmm_set_option": (_i, [_vp, _i, _i64]),
     "dafmm_sync": (_i, [_vp, _vp]),
     "dafmm_debug_expire_wait": (_i, [_vp, _vp]),
+    "dafmm_debug_check": (_i, [_vp, _vp]),
     "dafmm_eval_noalloc": (_i, [_vp, _i, _vp, _vp, _vp]),
     "dafmm_probe_peak": (_i, [_i, _i, ctypes.POINTER(_d), ctypes.POINTER(_d)]),
     "dafmm_debug_level": (_i64, [_vp, _i, _i, _vp, _i64]),
@@ -80,6 +82,15 @@ def library_path():
     return _build.LIB_PATH
 
 
+def _open(path):
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
 def load(build_if_missing=False):
     """Load libdafmm.so.  Raises RuntimeError when it has not been built."""
     global _lib
@@ -91,13 +102,27 @@ def load(build_if_missing=False):
             _build.build()
         else:
             raise RuntimeError("libdafmm.so is not built (run __graft_entry__.build()); there is no fallback")
-    lib = ctypes.CDLL(path)
-    for name, (res, args) in SIGNATURES.items():
-        fn = getattr(lib, name)
-        fn.restype = res
-        fn.argtypes = args
-    _lib = lib
-    return lib
+    _lib = _open(path)
+    return _lib
+
+
+def load_checked(build_if_missing=True):
+    """The checked build, libdafmm_check.so (compiled with -DDAFMM_CHECK; built on first use)."""
+    path = _build.CHECK_LIB_PATH
+    if build_if_missing:
+        _build.build(checked=True)
+    elif not os.path.exists(path):
+        raise RuntimeError("libdafmm_check.so is not built")
+    return _open(path)
+
+
+def swap_library(lib):
+    """Route every wrapper of this module to `lib` (a library from load / load_checked, or None
+    for the default); returns the one routed to before.  Handles made by one library must not
+    be passed to another."""
+    global _lib
+    old, _lib = _lib, lib
+    return old
 
 
 class DafmmError(RuntimeError):
@@ -255,6 +280,10 @@ def dafmm_sync(ctx, stream=None):
 
 def dafmm_debug_expire_wait(ctx, stream=None):
     _check(ctx, load().dafmm_debug_expire_wait(ctx, _stream_ptr(stream)))
+
+
+def dafmm_debug_check(ctx, stream=None):
+    _check(ctx, load().dafmm_debug_check(ctx, _stream_ptr(stream)))
 
 
 def dafmm_eval_noalloc(ctx, tree, order, phi=None, field=None, stream=None):

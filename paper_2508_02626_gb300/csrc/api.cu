@@ -12,6 +12,7 @@
 #include <string>
 #include <vector>
 
+#include "check.cuh"
 #include "da_common.cuh"
 #include "internal.h"
 #include "rot_lists.h"
@@ -33,6 +34,7 @@ const char* code_name(int c) {
         case DAFMM_ERR_TIMEOUT: return "timeout";
         case DAFMM_ERR_UNSUPPORTED: return "unsupported option";
         case DAFMM_ERR_NO_DEVICE: return "no CUDA device";
+        case DAFMM_ERR_CHECK: return "index check failed";
     }
     return "error";
 }
@@ -639,6 +641,10 @@ AdaptiveBuild abuild(dafmm_tree* t, const uint64_t* keys) {
     ab.pbeg = t->a_pbeg;
     ab.pend = t->a_pend;
     ab.colleague = t->a_colleague;
+#if defined(DAFMM_CHECK)
+    ab.cap = t->cap;
+    ab.nbox = t->nbox;
+#endif
     return ab;
 }
 
@@ -661,6 +667,13 @@ AdaptiveView aview(const dafmm_tree* t) {
     v.xq = t->xq;
     v.xl = t->xq ? t->xq + t->xq_n4 : nullptr;
     v.perm = t->perm;
+#if defined(DAFMM_CHECK)
+    v.n = t->n;
+    v.nrec = (int64_t)t->xq_n4;
+    v.nu = t->nu;
+    v.nw = t->nw;
+    v.nx = t->nx;
+#endif
     return v;
 }
 
@@ -911,7 +924,7 @@ int build_adaptive(dafmm_ctx* c, dafmm_tree* t, const double* dxyz, const double
     e = launch_leaf_records(t->leaves, nl, t->a_pbeg, t->a_pend, flags, foff, t->a_xq0, s);
     if (e == cudaSuccess)
         e = launch_gather_adaptive(dxyz, dq, t->perm, abuild(t, keys.as<uint64_t>()), t->leaves, nl, t->a_geom,
-                                   t->a_xq0, t->x, t->y, t->z, t->q, t->xq, t->xq_n4, s);
+                                   t->a_xq0, t->x, t->y, t->z, t->q, t->xq, t->xq_n4, t->n, s);
     if (e != cudaSuccess) return cuda_fail(c, e, "gather");
     // U, W, X lists
     const size_t nb1 = (size_t)nbox + 1;
@@ -1067,6 +1080,7 @@ int eval_adaptive(dafmm_tree* t, int order, int precision, double* dphi, double*
             a.geom = t->a_geom;
             a.out = t->aL;
             a.err = c->d_err;
+            a.nbox = t->nbox;
             a.num_sms = c->num_sms;
             for (int l = t->maxlev; l >= 2; --l)  // finest first
                 for (int o = 0; o < 8; ++o) {
@@ -1116,6 +1130,54 @@ int eval_adaptive(dafmm_tree* t, int order, int precision, double* dphi, double*
 }  // namespace
 
 namespace dafmm {
+const char* check_site_name(int site) {
+    switch (site) {
+        case kChkLeafRange: return "particle range of a uniform leaf";
+        case kChkBoxIndex: return "box index from a tree array or list";
+        case kChkBoxRange: return "particle range of an adaptive box";
+        case kChkListPtr: return "interaction-list range";
+        case kChkRotTask: return "rotation task entry";
+        case kChkRecord: return "FP32 record of a leaf";
+        case kChkSortScatter: return "radix-sort scatter position";
+        case kChkPerm: return "sort permutation entry";
+        case kChkLeafKey: return "leaf of a sorted key";
+        case kChkSplitChild: return "child box of an adaptive split";
+        case kChkListFill: return "interaction-list fill position";
+        case kChkGatherSource: return "source box of the gathered M2L";
+        case kChkDebug: return "deliberate failure of dafmm_debug_check";
+    }
+    return "unknown";
+}
+
+#if defined(DAFMM_CHECK)
+static std::mutex& check_mutex() {
+    static std::mutex m;
+    return m;
+}
+static std::vector<CheckTake>& check_readers() {  // built on first use: registrations run at load time
+    static std::vector<CheckTake> v;
+    return v;
+}
+void check_register(CheckTake take) {
+    std::lock_guard<std::mutex> g(check_mutex());
+    check_readers().push_back(take);
+}
+int check_take_all(long long* index, long long* bound) {
+    std::lock_guard<std::mutex> g(check_mutex());
+    int first = 0;
+    for (CheckTake take : check_readers()) {
+        long long i = 0, n = 0;
+        const int site = take(&i, &n);
+        if (site && !first) {
+            first = site;
+            *index = i;
+            *bound = n;
+        }
+    }
+    return first;
+}
+#endif
+
 int ctx_alloc(dafmm_ctx* c, void** p, size_t bytes, const char* what) { return dev_alloc(c, p, bytes, what); }
 void ctx_free(dafmm_ctx* c, void* p, size_t bytes) { dev_free(c, p, bytes); }
 }  // namespace dafmm
@@ -1731,6 +1793,12 @@ int dafmm_sync(dafmm_ctx* c, void* stream) {
         CK(c, cudaMemset(c->d_err, 0, sizeof(int)), "error flag");
         return fail(c, DAFMM_ERR_TIMEOUT, "a bounded device wait gave up (site " + std::to_string(flag) + ")");
     }
+#if defined(DAFMM_CHECK)
+    long long index = 0, bound = 0;
+    if (const int site = check_take_all(&index, &bound))
+        return fail(c, DAFMM_ERR_CHECK, std::string(check_site_name(site)) + " (site " + std::to_string(site) +
+                                            "): index " + std::to_string(index) + ", bound " + std::to_string(bound));
+#endif
     return DAFMM_OK;
 }
 

@@ -23,6 +23,7 @@
 #include <type_traits>
 
 #include "da_common.cuh"
+#include "check.cuh"
 #include "ff.cuh"
 #include "internal.h"
 #include "tree_adaptive.h"
@@ -113,7 +114,8 @@ __global__ void k_p2m(TreeView tv, double* __restrict__ M, int rows32) {
     const int lane = threadIdx.x;
     const int leaf = blockIdx.x * blockDim.y + threadIdx.y;
     if (leaf >= tv.nleaf) return;
-    const int i0 = tv.leaf_start[leaf], i1 = tv.leaf_start[leaf + 1];
+    int i0 = tv.leaf_start[leaf], i1 = tv.leaf_start[leaf + 1];
+    if (!DAFMM_RANGE(i0, i1, tv.n, kChkLeafRange)) i0 = i1 = 0;
     int a, b, c;
     octmajor_decode(tv.depth, leaf, a, b, c);
     const double cx = tv.x0 + ((double)a + 0.5) * tv.h_leaf;
@@ -571,11 +573,13 @@ __device__ __forceinline__ void rot_step(const uint2* __restrict__ list, int len
 #pragma unroll 4
     for (int t = 0; t < len; ++t) {
         const uint2 w = list[32 * t + lane];
-        s.madd(tab[w.x & 0x7fffffffu], in[w.y & 0xffffu]);
+        if (DAFMM_IN(w.y & 0xffffu, NC + 1, kChkRotTask)) s.madd(tab[w.x & 0x7fffffffu], in[w.y & 0xffffu]);
         if (w.x >> 31) {
             const int k = (int)(w.y >> 16);
-            if (ACC) out[k] = rot_add(out[k], s.get());
-            else out[k] = s.get();
+            if (DAFMM_IN(k, NC, kChkRotTask)) {
+                if (ACC) out[k] = rot_add(out[k], s.get());
+                else out[k] = s.get();
+            }
             s = typename RotAcc<R>::type();
         }
     }
@@ -701,7 +705,8 @@ __global__ void __launch_bounds__(256, 2) k_m2l_rot_a(const double* __restrict__
     const int oct = blockIdx.y;
     const int g0 = grp_ptr[grp0 + oct], g1 = grp_ptr[grp0 + oct + 1];
     const int ti = g0 + blockIdx.x * 8 + w;
-    if (ti >= g1) return;
+    if (ti >= g1 || !DAFMM_RANGE(g0, g1, av.nbox, kChkListPtr)) return;
+    if (!DAFMM_IN(tg[ti], av.nbox, kChkBoxIndex) || !DAFMM_IN(av.parent[tg[ti]], av.nbox, kChkBoxIndex)) return;
     const int t = tg[ti], P = av.parent[t];
     const int ox = oct & 1, oy = (oct >> 1) & 1, oz = (oct >> 2) & 1;
     double* X = sbuf[w][0];
@@ -720,9 +725,9 @@ __global__ void __launch_bounds__(256, 2) k_m2l_rot_a(const double* __restrict__
                 const int scx = dx & 1, scy = dy & 1, scz = dz & 1;
                 const int ax = (dx - scx) >> 1, ay = (dy - scy) >> 1, az = (dz - scz) >> 1;
                 const int Q = av.colleague[27 * P + (ax + 1) * 9 + (ay + 1) * 3 + (az + 1)];
-                if (Q < 0) continue;
+                if (Q < 0 || !DAFMM_IN(Q, av.nbox, kChkBoxIndex)) continue;
                 const int sb = av.child[8 * Q + (scx | (scy << 1) | (scz << 2))];
-                if (sb < 0) continue;
+                if (sb < 0 || !DAFMM_IN(sb, av.nbox, kChkBoxIndex)) continue;
                 const int key = (vx + 3) * 49 + (vy + 3) * 7 + (vz + 3);
                 rot_pair<double>(Ttab + (size_t)key * 4 * ROT_TSZ, aval + (size_t)krho[key] * annz, rl, M,
                                  nullptr, nullptr, (size_t)sb * NCP, X, Y, S, lane);
@@ -1050,7 +1055,8 @@ k_leaf(TreeView tv, const double* __restrict__ Lleaf,
     const int lane = threadIdx.x;
     const int leaf = blockIdx.x * blockDim.y + threadIdx.y;
     if (leaf >= tv.nleaf) return;
-    const int i0 = tv.leaf_start[leaf], i1 = tv.leaf_start[leaf + 1];
+    int i0 = tv.leaf_start[leaf], i1 = tv.leaf_start[leaf + 1];
+    if (!DAFMM_RANGE(i0, i1, tv.n, kChkLeafRange)) i0 = i1 = 0;
     int a, b, c;
     octmajor_decode(tv.depth, leaf, a, b, c);
     const int nside = 1 << tv.depth;
@@ -1095,6 +1101,7 @@ k_leaf(TreeView tv, const double* __restrict__ Lleaf,
                 const int nl = octmajor_index(tv.depth, na, nb, nc2);
                 nb_s0 = tv.leaf_start[nl];
                 nb_s1 = tv.leaf_start[nl + 1];
+                if (!DAFMM_RANGE(nb_s0, nb_s1, tv.n, kChkLeafRange)) nb_s0 = nb_s1 = 0;
                 nb_r0 = xq_base(nb_s0, nl);
             }
         }
@@ -1131,7 +1138,8 @@ k_leaf(TreeView tv, const double* __restrict__ Lleaf,
                         const int na = a + dx, nb = b + dy, nc2 = c + dz;
                         if (na < 0 || nb < 0 || nc2 < 0 || na >= nside || nb >= nside || nc2 >= nside) continue;
                         const int nl = octmajor_index(tv.depth, na, nb, nc2);
-                        const int s0 = tv.leaf_start[nl], s1 = tv.leaf_start[nl + 1];
+                        int s0 = tv.leaf_start[nl], s1 = tv.leaf_start[nl + 1];
+                        if (!DAFMM_RANGE(s0, s1, tv.n, kChkLeafRange)) s0 = s1 = 0;
                         for (int s = s0; s < s1; ++s) {
                             const double ex = xt - tv.x[s], ey = yt - tv.y[s], ez = zt - tv.z[s];
                             const double r2 = ex * ex + ey * ey + ez * ez;
@@ -1237,7 +1245,7 @@ k_leaf(TreeView tv, const double* __restrict__ Lleaf,
             fy -= (double)g1 * tv.inv_h_leaf;
             fz -= (double)g2 * tv.inv_h_leaf;
         }
-        if (valid) {
+        if (valid && DAFMM_IN(tv.perm[t], tv.n, kChkPerm)) {
             const int o = tv.perm[t];
             if (phi) phi[o] = fphi;
             if (field) {
@@ -1276,10 +1284,12 @@ __global__ void k_p2m_a(AdaptiveView av, const int* __restrict__ leaves, int nle
     const int li = blockIdx.x * blockDim.y + threadIdx.y;
     if (li >= nleaves) return;
     const int b = leaves[li];
+    if (!DAFMM_IN(b, av.nbox, kChkBoxIndex)) return;
     double cx, cy, cz, h;
     abox_geom(av, b, cx, cy, cz, h);
     const double ih = 1.0 / h;
-    const int i0 = av.pbeg[b], i1 = av.pend[b];
+    int i0 = av.pbeg[b], i1 = av.pend[b];
+    if (!DAFMM_RANGE(i0, i1, av.n, kChkBoxRange)) i0 = i1 = 0;
     constexpr int NJ = (NC + 31) / 32;
     T acc[NJ];
 #pragma unroll
@@ -1318,7 +1328,7 @@ __global__ void __launch_bounds__(256) k_m2m_a(ShiftTab tab, AdaptiveView av, in
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
             const int ch = bx < le ? av.child[8 * bx + c] : -1;
-            m[c] = ch >= 0 ? (T)M[(size_t)ch * NCP + k] : T(0);
+            m[c] = ch >= 0 && DAFMM_IN(ch, av.nbox, kChkBoxIndex) ? (T)M[(size_t)ch * NCP + k] : T(0);
         }
         hadamard8(m);
 #pragma unroll
@@ -1348,7 +1358,8 @@ __global__ void __launch_bounds__(256) k_m2l_a(const T* __restrict__ K, Adaptive
     T* src = reinterpret_cast<T*>(smem_raw);  // [32][NCP + 1]
     __shared__ int sidx[32];
     const int oct = blockIdx.y;
-    const int g0 = grp_ptr[grp0 + oct], g1 = grp_ptr[grp0 + oct + 1];
+    int g0 = grp_ptr[grp0 + oct], g1 = grp_ptr[grp0 + oct + 1];
+    if (!DAFMM_RANGE(g0, g1, av.nbox, kChkListPtr)) g0 = g1 = 0;
     const int t0 = g0 + blockIdx.x * 32;
     if (t0 >= g1) return;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -1363,13 +1374,16 @@ __global__ void __launch_bounds__(256) k_m2l_a(const T* __restrict__ K, Adaptive
                 if (threadIdx.x < 32) {
                     const int ti = t0 + threadIdx.x;
                     int sbox = -1;
-                    if (ti < g1) {
+                    if (ti < g1 && DAFMM_IN(tg[ti], av.nbox, kChkBoxIndex) &&
+                        DAFMM_IN(av.parent[tg[ti]], av.nbox, kChkBoxIndex)) {
                         const int P = av.parent[tg[ti]];
                         const int dx = ox - vx, dy = oy - vy, dz = oz - vz;  // = 2a + sc
                         const int scx = dx & 1, scy = dy & 1, scz = dz & 1;
                         const int ax = (dx - scx) >> 1, ay = (dy - scy) >> 1, az = (dz - scz) >> 1;
                         const int Q = av.colleague[27 * P + (ax + 1) * 9 + (ay + 1) * 3 + (az + 1)];
-                        if (Q >= 0) sbox = av.child[8 * Q + (scx | (scy << 1) | (scz << 2))];
+                        if (Q >= 0 && DAFMM_IN(Q, av.nbox, kChkBoxIndex))
+                            sbox = av.child[8 * Q + (scx | (scy << 1) | (scz << 2))];
+                        if (sbox >= 0 && !DAFMM_IN(sbox, av.nbox, kChkBoxIndex)) sbox = -1;
                     }
                     sidx[threadIdx.x] = sbox;
                 }
@@ -1394,7 +1408,7 @@ __global__ void __launch_bounds__(256) k_m2l_a(const T* __restrict__ K, Adaptive
                 __syncthreads();
             }
     const int ti = t0 + lane;
-    if (ti < g1) {
+    if (ti < g1 && DAFMM_IN(tg[ti], av.nbox, kChkBoxIndex)) {
         const int t = tg[ti];
         const double inv_h = 1.0 / av.geom[t].w;  // the target box's width (each tree has its own)
 #pragma unroll
@@ -1413,7 +1427,8 @@ __global__ void k_p2l_a(AdaptiveView av, int lb, int le, double* __restrict__ L)
     const int lane = threadIdx.x;
     const int b = lb + blockIdx.x * blockDim.y + threadIdx.y;
     if (b >= le) return;
-    const int x0i = av.x_ptr[b], x1i = av.x_ptr[b + 1];
+    int x0i = av.x_ptr[b], x1i = av.x_ptr[b + 1];
+    if (!DAFMM_RANGE(x0i, x1i, av.nx, kChkListPtr)) x0i = x1i = 0;
     if (x0i == x1i) return;
     double cx, cy, cz, h;
     abox_geom(av, b, cx, cy, cz, h);
@@ -1425,6 +1440,7 @@ __global__ void k_p2l_a(AdaptiveView av, int lb, int le, double* __restrict__ L)
     ChunkSink<T, NJ> sink{sm, lane, acc};
     for (int xi = x0i; xi < x1i; ++xi) {
         const int c = av.x_idx[xi];
+        if (!DAFMM_IN(c, av.nbox, kChkBoxIndex) || !DAFMM_RANGE(av.pbeg[c], av.pend[c], av.n, kChkBoxRange)) continue;
         const int i0 = av.pbeg[c], i1 = av.pend[c];
         for (int base = i0; base < i1; base += 32) {
             const int i = base + lane;
@@ -1469,7 +1485,7 @@ __global__ void __launch_bounds__(256) k_l2l_a(ShiftTab tab, AdaptiveView av, in
         l2l_row(tab, b, src + lane * (NCP + 1), R);
 #pragma unroll
         for (int c = 0; c < 8; ++c)
-            if (ch[c] >= 0) L[(size_t)ch[c] * NCP + b] += (double)R[c];
+            if (ch[c] >= 0 && DAFMM_IN(ch[c], av.nbox, kChkBoxIndex)) L[(size_t)ch[c] * NCP + b] += (double)R[c];
     }
 }
 
@@ -1486,6 +1502,7 @@ __global__ void __launch_bounds__(256) k_leaf_a(AdaptiveView av, const int* __re
     float* mrow = s_rows[threadIdx.y][0];
     float* lrow = s_rows[threadIdx.y][1];
     const int b = leaves[li];
+    if (!DAFMM_IN(b, av.nbox, kChkBoxIndex)) return;
     double cx, cy, cz, h;
     abox_geom(av, b, cx, cy, cz, h);
     const double ih = 1.0 / h;
@@ -1493,9 +1510,15 @@ __global__ void __launch_bounds__(256) k_leaf_a(AdaptiveView av, const int* __re
     if constexpr (sizeof(T) == 4) {
         if (lev >= 2) warp_row_to_f32(L + (size_t)b * NCP, lrow, lane);
     }
-    const int i0 = av.pbeg[b], i1 = av.pend[b];
-    const int u0 = av.u_ptr[b], u1 = av.u_ptr[b + 1];
-    const int w0 = av.w_ptr[b], w1 = av.w_ptr[b + 1];
+    int i0 = av.pbeg[b], i1 = av.pend[b];
+    if (!DAFMM_RANGE(i0, i1, av.n, kChkBoxRange)) i0 = i1 = 0;
+    if constexpr (sizeof(T) == 4) {  // the leaf's own records (its targets)
+        if (!DAFMM_RANGE(av.xq0[b], (long long)av.xq0[b] + (i1 - i0), av.nrec, kChkRecord)) i0 = i1 = 0;
+    }
+    int u0 = av.u_ptr[b], u1 = av.u_ptr[b + 1];
+    int w0 = av.w_ptr[b], w1 = av.w_ptr[b + 1];
+    if (!DAFMM_RANGE(u0, u1, av.nu, kChkListPtr)) u0 = u1 = 0;
+    if (!DAFMM_RANGE(w0, w1, av.nw, kChkListPtr)) w0 = w1 = 0;
     for (int base = i0; base < i1; base += 32) {
         // FP32: a pass of at most 16 targets splits the sources between the two half-warps,
         // lane l and lane l + 16 taking the same target
@@ -1510,6 +1533,8 @@ __global__ void __launch_bounds__(256) k_leaf_a(AdaptiveView av, const int* __re
             const double xt = av.x[tt], yt = av.y[tt], zt = av.z[tt];
             for (int ui = u0; ui < u1; ++ui) {
                 const int sb = av.u_idx[ui];
+                if (!DAFMM_IN(sb, av.nbox, kChkBoxIndex) || !DAFMM_RANGE(av.pbeg[sb], av.pend[sb], av.n, kChkBoxRange))
+                    continue;
                 for (int sidx = av.pbeg[sb]; sidx < av.pend[sb]; ++sidx) {
                     const double ex = xt - av.x[sidx], ey = yt - av.y[sidx], ez = zt - av.z[sidx];
                     const double r2 = ex * ex + ey * ey + ez * ez;
@@ -1554,7 +1579,9 @@ __global__ void __launch_bounds__(256) k_leaf_a(AdaptiveView av, const int* __re
                 const float ohx = (float)ox, ohy = (float)oy, ohz = (float)oz;
                 const float olx = (float)(ox - (double)ohx), oly = (float)(oy - (double)ohy),
                             olz = (float)(oz - (double)ohz);
+                if (!DAFMM_RANGE(av.pbeg[sb], av.pend[sb], av.n, kChkBoxRange)) return;
                 const int r0 = av.xq0[sb], n = av.pend[sb] - av.pbeg[sb];
+                if (!DAFMM_RANGE(r0, (long long)r0 + n, av.nrec, kChkRecord)) return;
                 for (int i0s = 0; i0s < n;) {
                     const int take = min(n - i0s, kLeafSeg - fill);
                     for (int i = lane; i < take; i += 32) {
@@ -1582,7 +1609,7 @@ __global__ void __launch_bounds__(256) k_leaf_a(AdaptiveView av, const int* __re
             }
             for (int ui = u0; ui < u1; ++ui) {
                 const int sb = av.u_idx[ui];
-                if (sb != b) add_leaf(sb);
+                if (sb != b && DAFMM_IN(sb, av.nbox, kChkBoxIndex)) add_leaf(sb);
             }
             if (fill > 0) flush();
             if (split) join_halves(acc);
@@ -1594,6 +1621,7 @@ __global__ void __launch_bounds__(256) k_leaf_a(AdaptiveView av, const int* __re
         // M2P from the W list (Sec. 3.2): phi = F/h_w, E = -grad_s F / h_w^2
         for (int wi = w0; wi < w1; ++wi) {
             const int wb = av.w_idx[wi];
+            if (!DAFMM_IN(wb, av.nbox, kChkBoxIndex)) continue;
             double wx, wy, wz, wh;
             abox_geom(av, wb, wx, wy, wz, wh);
             const double iwh = 1.0 / wh;
@@ -1630,7 +1658,7 @@ __global__ void __launch_bounds__(256) k_leaf_a(AdaptiveView av, const int* __re
             fy -= (double)g1 * ih;
             fz -= (double)g2 * ih;
         }
-        if (valid) {
+        if (valid && DAFMM_IN(av.perm[t], av.n, kChkPerm)) {
             const int o = av.perm[t];
             if (phi) phi[o] = fphi;
             if (field) {

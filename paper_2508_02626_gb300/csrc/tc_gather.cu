@@ -3,6 +3,7 @@
 // octant (a group of `tg`); for each of the 189 displacement terms the source box of every
 // target is found through its parent's colleague table, and the source rows are gathered
 // into shared memory (the uniform-tree kernel in tc_ops.cu loads them as one TMA box).
+#include "check.cuh"
 #include "tc_common.cuh"
 
 namespace dafmm {
@@ -61,10 +62,11 @@ __device__ __forceinline__ void term_slot(const Terms& tm, int& slot, int& sc) {
 }
 // the two dependent loads of that lookup, for a target whose parent is `par` (-1: none)
 __device__ __forceinline__ int colleague_of(const TCGParams& prm, int par, int slot) {
-    return par >= 0 ? prm.colleague[27 * par + slot] : -1;
+    return par >= 0 && DAFMM_IN(par, prm.nbox, kChkGatherSource) ? prm.colleague[27 * par + slot] : -1;
 }
 __device__ __forceinline__ int child_of(const TCGParams& prm, int Q, int sc) {
-    return Q >= 0 ? prm.child[8 * Q + sc] : -1;
+    const int s = Q >= 0 && DAFMM_IN(Q, prm.nbox, kChkGatherSource) ? prm.child[8 * Q + sc] : -1;
+    return s < 0 || DAFMM_IN(s, prm.nbox, kChkGatherSource) ? s : -1;
 }
 __device__ __forceinline__ int term_key(const Terms& tm) {
     return (tm.v[0] + 3) * 49 + (tm.v[1] + 3) * 7 + (tm.v[2] + 3);
@@ -137,7 +139,7 @@ __global__ void __launch_bounds__(kTcgThreads, 1) k_tcg(const __grid_constant__ 
             for (int i = 0; i < 2; ++i) {
                 const int r = lane + 32 * (i + 2 * pw);
                 const int t = r < cnt ? prm.tg[start + r] : -1;
-                par[i] = t >= 0 ? prm.parent[t] : -1;
+                par[i] = t >= 0 && DAFMM_IN(t, prm.nbox, kChkGatherSource) ? prm.parent[t] : -1;
             }
             // the valid terms in order, the source lookups running ahead: while the rows of a
             // term are gathered, the children of the next term's colleagues and the colleagues
@@ -292,7 +294,8 @@ __global__ void __launch_bounds__(kTcgThreads, 1) k_tcg(const __grid_constant__ 
         for (int w = blockIdx.x; w < prm.ntiles && ok; w += gridDim.x) {
             const GItem it = gdecode(prm, w);
             const int cnt = min(128, prm.grp_count[it.g] - it.tile * 128);
-            const int trow = row < cnt ? prm.tg[prm.grp_start[it.g] + it.tile * 128 + row] : -1;
+            int trow = row < cnt ? prm.tg[prm.grp_start[it.g] + it.tile * 128 + row] : -1;
+            if (trow >= 0 && !DAFMM_IN(trow, prm.nbox, kChkGatherSource)) trow = -1;
             const int tpar = trow >= 0 ? prm.parent[trow] : -1;
             float S[C::NP];
 #pragma unroll
@@ -386,6 +389,9 @@ static cudaError_t launch_tcg(const TCGArgs& a, cudaStream_t s) {
     prm.out = a.out;
     prm.nhalf = C::NHALF;
     prm.err = a.err;
+#if defined(DAFMM_CHECK)
+    prm.nbox = a.nbox;
+#endif
     int tiles = 0, ng = 0;
     for (int o = 0; o < 8; ++o)
         for (int g = 0; g < a.ngroups; ++g) {

@@ -92,6 +92,9 @@ struct TCGParams {
     int ntiles;
     int nhalf;
     int* err;
+#if defined(DAFMM_CHECK)
+    int nbox;                 // checked builds: boxes (the bound of the index checks)
+#endif
 };
 
 struct TCGArgs {
@@ -116,6 +119,7 @@ struct TCGArgs {
     int grp_oct[kTcgMaxGroups];
     int* err;
     int num_sms;
+    int nbox;                 // boxes of the tree (the bound of the checked build's index checks)
 };
 
 int tc_npt(int p);  // rows of the split matrix tables (nc padded to the MMA N granule)

@@ -15,6 +15,7 @@
 // list ever crosses trees, since every relation is derived from the parent's colleagues.
 #include <cuda_runtime.h>
 
+#include "check.cuh"
 #include "internal.h"
 #include "tree_adaptive.h"
 #include "tree_common.cuh"
@@ -202,7 +203,7 @@ __global__ void k_split_fill(AdaptiveBuild ab, int lb, int le, int level, const 
     int s = pb, k = first_new + k0;
     for (int c = 0; c < 8; ++c) {
         const int e = first_digit_ge(ab.keys, s, pe, shift, c + 1);
-        if (e > s) {
+        if (e > s && DAFMM_IN(k, ab.cap, kChkSplitChild)) {
             ab.root[k] = ab.root[b];
             ab.level[k] = level + 1;
             ab.ijk[3 * k] = 2 * ab.ijk[3 * b] + (c & 1);
@@ -335,9 +336,10 @@ constexpr int kStack = 256;
 // U and W of leaf b: traverse the descendants of b's non-leaf colleagues; plus the same-level
 // colleague leaves, plus coarser adjacent leaves (leaf colleagues of b's ancestors)
 template <bool FILL>
-__device__ void uw_lists(const AdaptiveBuild& ab, int b, int* nu, int* nw, int* ou, int* ow, int* err) {
+__device__ void uw_lists(const AdaptiveBuild& ab, int b, int* nu, int* nw, int* ou, int* ow, int* err, int cap_u = 0,
+                         int cap_w = 0) {
     int cu = 0, cw = 0;
-    if (FILL) ou[cu] = b;
+    if (FILL && DAFMM_IN(cu, cap_u, kChkListFill)) ou[cu] = b;
     ++cu;
     const int* col = ab.colleague + 27 * b;
     int stack[kStack];
@@ -346,7 +348,7 @@ __device__ void uw_lists(const AdaptiveBuild& ab, int b, int* nu, int* nw, int* 
         if (c < 0 || c == b) continue;
         if (ab.child[8 * c] < 0 && ab.child[8 * c + 1] < 0 && ab.child[8 * c + 2] < 0 && ab.child[8 * c + 3] < 0 &&
             ab.child[8 * c + 4] < 0 && ab.child[8 * c + 5] < 0 && ab.child[8 * c + 6] < 0 && ab.child[8 * c + 7] < 0) {
-            if (FILL) ou[cu] = c;
+            if (FILL && DAFMM_IN(cu, cap_u, kChkListFill)) ou[cu] = c;
             ++cu;
             continue;
         }
@@ -364,11 +366,11 @@ __device__ void uw_lists(const AdaptiveBuild& ab, int b, int* nu, int* nw, int* 
                         else atomicExch(err, 41);
                     }
                 if (leaf) {
-                    if (FILL) ou[cu] = x;
+                    if (FILL && DAFMM_IN(cu, cap_u, kChkListFill)) ou[cu] = x;
                     ++cu;
                 }
             } else {
-                if (FILL) ow[cw] = x;
+                if (FILL && DAFMM_IN(cw, cap_w, kChkListFill)) ow[cw] = x;
                 ++cw;
             }
         }
@@ -382,7 +384,7 @@ __device__ void uw_lists(const AdaptiveBuild& ab, int b, int* nu, int* nw, int* 
             bool leaf = true;
             for (int j = 0; j < 8; ++j) leaf = leaf && ab.child[8 * c + j] < 0;
             if (leaf && touch(ab, c, b)) {
-                if (FILL) ou[cu] = c;
+                if (FILL && DAFMM_IN(cu, cap_u, kChkListFill)) ou[cu] = c;
                 ++cu;
             }
         }
@@ -393,7 +395,7 @@ __device__ void uw_lists(const AdaptiveBuild& ab, int b, int* nu, int* nw, int* 
 
 // X of box b: leaf colleagues c of b's ancestors (parent and up) adjacent to parent(b), not to b
 template <bool FILL>
-__device__ int x_list(const AdaptiveBuild& ab, int b, int* ox) {
+__device__ int x_list(const AdaptiveBuild& ab, int b, int* ox, int cap_x = 0) {
     const int P = ab.parent[b];
     if (P < 0) return 0;
     int cx = 0;
@@ -406,7 +408,7 @@ __device__ int x_list(const AdaptiveBuild& ab, int b, int* ox) {
             for (int j = 0; j < 8; ++j) leaf = leaf && ab.child[8 * c + j] < 0;
             if (!leaf) continue;
             if (touch(ab, c, P) && !touch(ab, c, b)) {
-                if (FILL) ox[cx] = c;
+                if (FILL && DAFMM_IN(cx, cap_x, kChkListFill)) ox[cx] = c;
                 ++cx;
             }
         }
@@ -452,8 +454,8 @@ __global__ void k_list_fill(AdaptiveBuild ab, int nbox, const int* pu, const int
     bool leaf = true;
     for (int j = 0; j < 8; ++j) leaf = leaf && ab.child[8 * b + j] < 0;
     int nu, nw;
-    if (leaf) uw_lists<true>(ab, b, &nu, &nw, iu + pu[b], iw + pw[b], err);
-    x_list<true>(ab, b, ix + px[b]);
+    if (leaf) uw_lists<true>(ab, b, &nu, &nw, iu + pu[b], iw + pw[b], err, pu[b + 1] - pu[b], pw[b + 1] - pw[b]);
+    x_list<true>(ab, b, ix + px[b], px[b + 1] - px[b]);
 }
 
 cudaError_t launch_list_count(AdaptiveBuild ab, int nbox, int* cu, int* cw, int* cx, unsigned long long* nv, int* err,
@@ -474,20 +476,24 @@ cudaError_t launch_list_fill(AdaptiveBuild ab, int nbox, const int* pu, const in
 __global__ void k_gather_adaptive(const double* __restrict__ xyz, const double* __restrict__ q,
                                   const int* __restrict__ perm, AdaptiveBuild ab, const int* __restrict__ leaves,
                                   int nleaves, const double4* __restrict__ geom, const int* __restrict__ xq0,
-                                  double* x, double* y, double* z, double* qs, float4* xq, float4* xl) {
+                                  double* x, double* y, double* z, double* qs, float4* xq, float4* xl, int64_t n,
+                                  int64_t nrec) {
     const int li = blockIdx.x;
     if (li >= nleaves) return;
     const int b = leaves[li];
+    if (!DAFMM_IN(b, ab.nbox, kChkBoxIndex) || !DAFMM_RANGE(ab.pbeg[b], ab.pend[b], n, kChkBoxRange)) return;
     const double4 g = geom[b];
     const double ih = 1.0 / g.w;
     const double cx = g.x, cy = g.y, cz = g.z;
     for (int t = ab.pbeg[b] + threadIdx.x; t < ab.pend[b]; t += blockDim.x) {
         const int i = perm[t];
+        if (!DAFMM_IN(i, n, kChkPerm)) continue;
         const double px = xyz[3 * i], py = xyz[3 * i + 1], pz = xyz[3 * i + 2], pq = q[i];
         x[t] = px; y[t] = py; z[t] = pz; qs[t] = pq;
         const double ox = (px - cx) * ih, oy = (py - cy) * ih, oz = (pz - cz) * ih;
         const float hx = (float)ox, hy = (float)oy, hz = (float)oz;
         const int r = xq0[b] + (t - ab.pbeg[b]);
+        if (!DAFMM_IN(r, nrec, kChkRecord)) continue;
         xq_store(xq, r, hx, hy, hz, (float)pq);
         xq_store(xl, r, (float)(ox - (double)hx), (float)(oy - (double)hy), (float)(oz - (double)hz),
                  (float)(pq - (double)(float)pq));
@@ -520,13 +526,13 @@ cudaError_t launch_leaf_records(const int* leaves, int nl, const int* pbeg, cons
 
 cudaError_t launch_gather_adaptive(const double* xyz, const double* q, const int* perm, AdaptiveBuild ab,
                                    const int* leaves, int nleaves, const double4* geom, const int* xq0, double* x,
-                                   double* y, double* z, double* qs, float4* xq, size_t xq_n4, cudaStream_t s) {
+                                   double* y, double* z, double* qs, float4* xq, size_t xq_n4, int64_t n, cudaStream_t s) {
     // the zero fill supplies the padding record of leaves with an odd particle count (both
     // halves: the records and their remainders)
     cudaError_t e = cudaMemsetAsync(xq, 0, 2 * xq_n4 * sizeof(float4), s);
     if (e != cudaSuccess || nleaves == 0) return e;
     k_gather_adaptive<<<nleaves, 128, 0, s>>>(xyz, q, perm, ab, leaves, nleaves, geom, xq0, x, y, z, qs, xq,
-                                              xq + xq_n4);
+                                              xq + xq_n4, n, (int64_t)xq_n4);
     return cudaGetLastError();
 }
 

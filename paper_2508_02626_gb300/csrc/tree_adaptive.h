@@ -19,6 +19,10 @@ struct AdaptiveBuild {
     int* pbeg;             // particle range [pbeg, pend) in sorted order
     int* pend;
     int* colleague;        // per box, 27 slots by relative position, slot 13 = the box
+#if defined(DAFMM_CHECK)
+    int cap;               // checked builds: boxes the arrays hold, and (once the levels are
+    int nbox;              // built) the boxes of the tree
+#endif
 };
 
 // what the evaluation kernels read (const view)
@@ -44,6 +48,10 @@ struct AdaptiveView {
     const float4* xl;             // the FP32 remainders of those offsets, same records
     const int* xq0;               // per leaf box: its first record (even)
     const int* perm;
+#if defined(DAFMM_CHECK)
+    int64_t n, nrec;              // checked builds: particles, FP32 records (one half of xq),
+    int nu, nw, nx;               // U / W / X list entries (the bounds of the index checks)
+#endif
 };
 
 // Morton keys of particles grouped by tree: particles [offs[r], offs[r+1]) belong to tree r,
@@ -76,7 +84,7 @@ cudaError_t launch_leaf_records(const int* leaves, int nl, const int* pbeg, cons
                                 int* xq0, cudaStream_t s);
 cudaError_t launch_gather_adaptive(const double* xyz, const double* q, const int* perm, AdaptiveBuild ab,
                                    const int* leaves, int nleaves, const double4* geom, const int* xq0, double* x,
-                                   double* y, double* z, double* qs, float4* xq, size_t xq_n4, cudaStream_t s);
+                                   double* y, double* z, double* qs, float4* xq, size_t xq_n4, int64_t n, cudaStream_t s);
 
 cudaError_t launch_leaf_flags(const int* child, int nbox, int* flags, cudaStream_t s);
 cudaError_t launch_scatter_flagged(const int* flags, const int* offs, int nbox, int* out, cudaStream_t s);

@@ -6,6 +6,7 @@
 // computed with explicitly rounded double operations so that no contraction changes it.
 #include <cuda_runtime.h>
 
+#include "check.cuh"
 #include "internal.h"
 #include "tree_common.cuh"
 
@@ -177,8 +178,10 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const uint64_t* __res
         if (valid) {
             unsigned pos = base[d] + rank;
             for (int ww = 0; ww < w; ++ww) pos += wcnt[ww][d];
-            kout[pos] = k;
-            vout[pos] = v;
+            if (DAFMM_IN(pos, n, kChkSortScatter)) {
+                kout[pos] = k;
+                vout[pos] = v;
+            }
         }
         __syncthreads();
         unsigned tot = 0;
@@ -233,6 +236,7 @@ __global__ void k_gather_uniform(const double* __restrict__ xyz, const double* _
     int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (t >= n) return;
     const int i = perm[t];
+    if (!DAFMM_IN(i, n, kChkPerm) || !DAFMM_IN(keys[t], tv.nleaf, kChkLeafKey)) return;
     const double px = xyz[3 * i], py = xyz[3 * i + 1], pz = xyz[3 * i + 2], pq = q[i];
     x[t] = px; y[t] = py; z[t] = pz; qs[t] = pq;
     int a, b, c;
@@ -244,6 +248,7 @@ __global__ void k_gather_uniform(const double* __restrict__ xyz, const double* _
     const double ox = (px - cx) * tv.inv_h_leaf, oy = (py - cy) * tv.inv_h_leaf, oz = (pz - cz) * tv.inv_h_leaf;
     const float hx = (float)ox, hy = (float)oy, hz = (float)oz;
     const int r = xq_base(p0, leaf) + (int)(t - p0);
+    if (!DAFMM_IN(r, xq_records(n, tv.nleaf), kChkRecord)) return;
     xq_store(xq, r, hx, hy, hz, (float)pq);
     xq_store(xl, r, (float)(ox - (double)hx), (float)(oy - (double)hy), (float)(oz - (double)hz),
              (float)(pq - (double)(float)pq));
@@ -284,6 +289,7 @@ __global__ void k_scatter_out(const double* __restrict__ ps, const double* __res
     int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (t >= n) return;
     const int i = perm[t];
+    if (!DAFMM_IN(i, n, kChkPerm)) return;
     if (phi) phi[i] = ps[t];
     if (field)
         for (int d = 0; d < 3; ++d) field[3 * i + d] = fs[3 * t + d];

@@ -30,6 +30,14 @@ def test_every_declared_symbol_is_exported(lib):
         assert hasattr(lib, n), n
 
 
+def test_checked_build_exports_every_symbol():
+    """The checked build (-DDAFMM_CHECK, its own folder and library) compiles, links and
+    exports the same entry points."""
+    lib = ctypes.CDLL(_build.build(checked=True))
+    for n in declared_entry_points():
+        assert hasattr(lib, n), n
+
+
 def test_binding_covers_header():
     assert set(declared_entry_points()) == set(binding.SIGNATURES)
     for n in declared_entry_points():

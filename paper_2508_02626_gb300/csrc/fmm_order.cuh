@@ -547,11 +547,16 @@ struct RotAccD {
 };
 struct RotAccF {
     float hi = 0.f, lo = 0.f;
+    // the product enters unnormalised: its rounded high part p through TwoSum, and p's exact
+    // rounding error plus the cross terms (a.hi b.lo + a.lo b.hi) into the low sum (13 FP32
+    // operations instead of 16 with a renormalised product; the low sum's rounding stays of
+    // the order u^2 |a b|)
     __device__ __forceinline__ void madd(ff a, ff b) {
-        const ff p = ff_mul(a, b);
-        const ff t = two_sum(hi, p.hi);
+        const float p = mul_rn(a.hi, b.hi);
+        const float e = fmaf(a.hi, b.hi, -p) + fmaf(a.hi, b.lo, mul_rn(a.lo, b.hi));
+        const ff t = two_sum(hi, p);
         hi = t.hi;
-        lo += t.lo + p.lo;
+        lo += t.lo + e;
     }
     __device__ __forceinline__ ff get() const { return fast_two_sum(hi, lo); }
 };
@@ -629,9 +634,10 @@ struct RotBuf {
     R v[3][NCP + 1];
 };
 
-// R = double: FP64, work vectors in static shared memory, task lists read from global memory.
-// R = ff: float-float, the task lists (the same for every pair) copied into shared memory
-// after the work vectors (dynamic shared memory), the source rows from the FP32 split parts.
+// R = double: FP64.  R = ff: float-float, the source rows from their FP32 split parts.  The work
+// vectors are in shared memory; the task lists (the same for every pair) are read through the
+// L1 cache (copies of them in shared memory cost the float-float kernel a quarter of its
+// resident warps and gained nothing: measured 73.7 -> 75.5 ms at level 5, N = 1e6, p = 8).
 template <class R>
 __global__ void __launch_bounds__(256, 2) k_m2l_rot(const R* __restrict__ Ttab, const int* __restrict__ krho,
                                                     RotLists rl, const R* __restrict__ aval, int annz, int l,
@@ -639,23 +645,7 @@ __global__ void __launch_bounds__(256, 2) k_m2l_rot(const R* __restrict__ Ttab, 
                                                     const float* __restrict__ Ml, double* __restrict__ L,
                                                     double inv_h) {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    RotBuf<R>* bufs;
-    if constexpr (std::is_same<R, double>::value) {
-        __shared__ RotBuf<double> sbuf[8];
-        bufs = sbuf;
-    } else {
-        extern __shared__ __align__(16) unsigned char rot_smem[];
-        bufs = reinterpret_cast<RotBuf<R>*>(rot_smem);
-        uint2* lists = reinterpret_cast<uint2*>(rot_smem + 8 * sizeof(RotBuf<R>));
-        const int nx = 32 * rl.lx, nz = 32 * rl.lz, na = 32 * rl.la;
-        for (int i = threadIdx.x; i < nx; i += blockDim.x) lists[i] = rl.x[i];
-        for (int i = threadIdx.x; i < nz; i += blockDim.x) lists[nx + i] = rl.z[i];
-        for (int i = threadIdx.x; i < na; i += blockDim.x) lists[nx + nz + i] = rl.a[i];
-        __syncthreads();
-        rl.x = lists;
-        rl.z = lists + nx;
-        rl.a = lists + nx + nz;
-    }
+    __shared__ RotBuf<R> bufs[8];
     const int Pp = 1 << (l - 1), P3 = Pp * Pp * Pp, n_side = 1 << l;
     const int t = blockIdx.x * 8 + w;  // target box, octant-major
     if (t >= 8 * P3) return;
@@ -1831,10 +1821,7 @@ static cudaError_t m2l_rot_ff_launch(const OrderData& od, int l, const float* Mh
                                      double inv_h, cudaStream_t s) {
     const int nbox = 1 << (3 * l);
     const RotLists rl{od.rot_lx, od.rot_lz, od.rot_la, od.rot_len[0], od.rot_len[1], od.rot_len[2]};
-    const size_t smem = 8 * sizeof(RotBuf<ff>) + (size_t)32 * (rl.lx + rl.lz + rl.la) * sizeof(uint2);
-    cudaError_t e = cudaFuncSetAttribute(k_m2l_rot<ff>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    k_m2l_rot<ff><<<(nbox + 7) / 8, 256, smem, s>>>(reinterpret_cast<const ff*>(od.rot_Tf), od.rot_rho, rl,
+    k_m2l_rot<ff><<<(nbox + 7) / 8, 256, 0, s>>>(reinterpret_cast<const ff*>(od.rot_Tf), od.rot_rho, rl,
                                                      reinterpret_cast<const ff*>(od.ax_valf), od.ax_nnz, l, nullptr,
                                                      Mh, Ml, L, inv_h);
     return cudaGetLastError();

@@ -31,7 +31,7 @@ UNIT = "particles/s"
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of the M2L kernel on
 # this workload, from one ncu capture of that kernel; valid while the kernel's source files
 # hash to the recorded value, reported as null otherwise
-M2L_TRAFFIC = {"fp32": (80.7e6, "9bae660215015e86")}
+M2L_TRAFFIC = {"fp32": (25.4e6, "2c5c2b768d57ed1d")}
 M2L_SOURCES = ("paper_2508_02626_gb300/csrc/tc_common.cuh", "paper_2508_02626_gb300/csrc/tc_ops.cu")
 
 
@@ -484,10 +484,13 @@ def run_ours(args, rank, world):
             # TF32 tensor peak = measured BF16 burst peak x the nominal TF32/BF16 ratio 1/2
             peak, bound = peaks["bf16_tflops"] / 2.0, "tensor"
             peak_note = "TF32 = %s BF16 %.1f TFLOP/s x 1/2 (nominal ratio)" % (peak_src, peaks["bf16_tflops"])
-        npt = (nc + 15) // 16 * 16
+        # the FP32 mode's F16 M2L runs in the harmonic basis (DAFMM_OPT_M2L_HARMONIC, default):
+        # rows and columns of the contraction are the (p + 1)^2 free coefficients
+        nk = (p + 1) ** 2 if f16 else nc
+        npt = (nk + 15) // 16 * 16
         if npt > 192:
             npt = 2 * (((npt // 2) + 15) // 16 * 16)
-        klen = (nc + 15) // 16 * 16 if f16 else (nc + 7) // 8 * 8  # operand row length (MMA K)
+        klen = (nk + 15) // 16 * 16 if f16 else (nk + 7) // 8 * 8  # operand row length (MMA K)
         tiles = 0
         for l in range(2, depth + 1):
             S = 1 << (l - 1)
@@ -502,7 +505,14 @@ def run_ours(args, rank, world):
                       "M2L (SIMT FP64 k_m2l, all levels)"),
                 "algorithmic": ("2 x %d multiply-adds per well-separated pair (4 rotations + axial Eq. 5): %.3e flops"
                                 % (rotation_madds_per_pair(p), flops)) if rot else
-                               "2 ncoef^2 flops per well-separated pair: %.3e flops" % flops,
+                               ("2 ncoef^2 flops per well-separated pair: %.3e flops (the dense M2L of Eq. 5; "
+                                "computed in the harmonic basis, 2 (p+1)^4 = %.3e flops, plus the expansion of "
+                                "the locals, inside the timed phase)" % (flops, 2.0 * (p + 1) ** 4 * pairs_all)
+                                if f16 else "2 ncoef^2 flops per well-separated pair: %.3e flops" % flops),
+                "achieved_harmonic": (round(2.0 * (p + 1) ** 4 * pairs_all / m2l_s / 1e12, 3)
+                                      if f16 and bound == "tensor" else None),
+                "frac_harmonic": (round(2.0 * (p + 1) ** 4 * pairs_all / m2l_s / 1e12 / peak, 4)
+                                  if f16 and bound == "tensor" else None),
                 "executed_tflops": None if executed is None else round(executed, 3),
                 "executed_frac": None if executed is None else round(executed / peak, 4),
                 "peak_source": peak_note}

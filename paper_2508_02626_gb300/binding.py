@@ -268,6 +268,7 @@ DAFMM_OPT_TC_MASK = 2
 DAFMM_OPT_LEAF_WARPS = 3
 DAFMM_OPT_M2L_F16 = 4
 DAFMM_OPT_M2L_ROTATION = 5
+DAFMM_OPT_M2L_HARMONIC = 6
 
 
 def dafmm_set_option(ctx, option, value):

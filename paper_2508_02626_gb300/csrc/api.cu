@@ -378,6 +378,16 @@ void free_order(dafmm_ctx* c, OrderData& od) {
         dev_free(c, od.k16_inv_r, (size_t)tc_npt(od.p) * sizeof(float));
         dev_free(c, od.k16_inv_c, (size_t)kNumKeys * sizeof(float));
     }
+    if (od.Kh16h) {
+        const size_t c16 = (size_t)kNumKeys * tc_npt_h(od.p) * tc_rowlen16h(od.p) * 2;
+        const size_t nstep = (size_t)(ncoef_of(od.p) - nharm_of(od.p));
+        dev_free(c, od.Kh16h, c16);
+        dev_free(c, od.Kl16h, c16);
+        dev_free(c, od.k16h_inv_r, (size_t)tc_npt_h(od.p) * sizeof(float));
+        dev_free(c, od.k16h_inv_c, (size_t)kNumKeys * sizeof(float));
+        dev_free(c, od.hx_step, std::max<size_t>(nstep, 1) * sizeof(int4));
+        dev_free(c, od.hx_w, std::max<size_t>(nstep, 1) * sizeof(float2));
+    }
     if (od.Khi) {
         const size_t cs = (size_t)kNumKeys * tc_npt(od.p) * od.ncp;
         dev_free(c, od.Khi, cs * sizeof(float));
@@ -431,6 +441,100 @@ int ensure_k16(dafmm_ctx* c, int p, cudaStream_t s) {
     od.Kl16 = lo;
     od.k16_inv_r = ir;
     od.k16_inv_c = ic;
+    return DAFMM_OK;
+}
+
+// The M2L in the harmonic basis (made once per order, on first use): the steps that restore the
+// coefficients of z exponent >= 2 from the free ones (Laplace's equation, in order of increasing
+// z exponent), the expansion matrix X [nc][nh] they define (FP64, for the matrices only), and
+// the F16 splits of the matrices restricted to the free output coefficients and composed with X
+int ensure_k16h(dafmm_ctx* c, int p, cudaStream_t s) {
+    OrderData& od = c->ord[p];
+    if (od.Kh16h) return DAFMM_OK;
+    const int nc = ncoef_of(p), nh = nharm_of(p), nhp = harm_row(p);
+    const int npt = tc_npt_h(p), rowlen = tc_rowlen16h(p);
+    // exponents of every coefficient (the layout of da_index)
+    std::vector<int> ea(nc), eb(nc), ec(nc);
+    for (int n = 0; n <= p; ++n)
+        for (int a = n; a >= 0; --a)
+            for (int b = n - a; b >= 0; --b) {
+                const int cc = n - a - b, i = da_index(a, b, cc);
+                ea[i] = a; eb[i] = b; ec[i] = cc;
+            }
+    std::vector<int4> step;
+    std::vector<float2> w;
+    std::vector<double> X((size_t)nc * nh, 0.0);
+    for (int k = 0; k < nh; ++k) X[(size_t)harm_full_index(k) * nh + k] = 1.0;
+    int cst[kMaxOrder + 3] = {};
+    for (int cz = 2; cz <= p + 1; ++cz) {
+        cst[cz] = (int)step.size();
+        for (int i = 0; i < nc; ++i) {
+            if (ec[i] != cz) continue;
+            const int a = ea[i], b = eb[i];
+            const int i1 = da_index(a + 2, b, cz - 2), i2 = da_index(a, b + 2, cz - 2);
+            const double d = (double)cz * (cz - 1);
+            const double w1 = -(double)(a + 2) * (a + 1) / d, w2 = -(double)(b + 2) * (b + 1) / d;
+            step.push_back(make_int4(i, i1, i2, cz));
+            w.push_back(make_float2((float)w1, (float)w2));
+            for (int k = 0; k < nh; ++k)
+                X[(size_t)i * nh + k] = w1 * X[(size_t)i1 * nh + k] + w2 * X[(size_t)i2 * nh + k];
+        }
+    }
+    cst[p + 2] = (int)step.size();
+    const size_t nstep = std::max<size_t>(step.size(), 1);
+    const size_t c16 = (size_t)kNumKeys * npt * rowlen * 2;
+    const size_t xb = (size_t)nc * nh * sizeof(double), khb = (size_t)kNumKeys * nh * nhp * sizeof(double);
+    int rc;
+    void *hi = nullptr, *lo = nullptr, *xd = nullptr, *khd = nullptr;
+    float *ir = nullptr, *icv = nullptr, *scratch = nullptr;
+    int4* stp = nullptr;
+    float2* wd = nullptr;
+    auto release = [&]() {
+        dev_free(c, hi, hi ? c16 : 0); dev_free(c, lo, lo ? c16 : 0);
+        dev_free(c, ir, ir ? (size_t)npt * sizeof(float) : 0);
+        dev_free(c, icv, icv ? (size_t)kNumKeys * sizeof(float) : 0);
+        dev_free(c, stp, stp ? nstep * sizeof(int4) : 0);
+        dev_free(c, wd, wd ? nstep * sizeof(float2) : 0);
+    };
+    auto release_scratch = [&]() {
+        dev_free(c, xd, xd ? xb : 0);
+        dev_free(c, khd, khd ? khb : 0);
+        dev_free(c, scratch, scratch ? ((size_t)npt + kNumKeys) * sizeof(float) : 0);
+    };
+    if ((rc = dev_alloc(c, &hi, c16, "M2L matrices (harmonic, F16 split)")) ||
+        (rc = dev_alloc(c, &lo, c16, "M2L matrices (harmonic, F16 split)")) ||
+        (rc = dev_alloc(c, (void**)&ir, (size_t)npt * sizeof(float), "M2L matrix factors")) ||
+        (rc = dev_alloc(c, (void**)&icv, (size_t)kNumKeys * sizeof(float), "M2L matrix factors")) ||
+        (rc = dev_alloc(c, (void**)&stp, nstep * sizeof(int4), "harmonic expansion")) ||
+        (rc = dev_alloc(c, (void**)&wd, nstep * sizeof(float2), "harmonic expansion")) ||
+        (rc = dev_alloc(c, &xd, xb, "harmonic expansion (scratch)")) ||
+        (rc = dev_alloc(c, &khd, khb, "M2L matrices (harmonic, scratch)")) ||
+        (rc = dev_alloc(c, (void**)&scratch, ((size_t)npt + kNumKeys) * sizeof(float), "M2L matrix factors"))) {
+        release();
+        release_scratch();
+        return rc;
+    }
+    cudaError_t e = cudaMemcpyAsync(xd, X.data(), xb, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && !step.empty())
+        e = cudaMemcpyAsync(stp, step.data(), step.size() * sizeof(int4), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && !w.empty())
+        e = cudaMemcpyAsync(wd, w.data(), w.size() * sizeof(float2), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = tc_prepare_k16h(od.K64, kNumKeys, p, static_cast<const double*>(xd), static_cast<double*>(khd), hi, lo, ir,
+                            icv, scratch, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // the host vectors die with this call
+    release_scratch();
+    if (e != cudaSuccess) {
+        release();
+        return cuda_fail(c, e, "M2L matrices (harmonic)");
+    }
+    od.Kh16h = hi;
+    od.Kl16h = lo;
+    od.k16h_inv_r = ir;
+    od.k16h_inv_c = icv;
+    od.hx_step = stp;
+    od.hx_w = wd;
+    for (int k = 0; k < kMaxOrder + 3; ++k) od.hx_cst[k] = cst[k];
     return DAFMM_OK;
 }
 
@@ -569,6 +673,7 @@ void free_expansions(dafmm_tree* t) {
         dev_free(c, e.Mh16[l], c16);
         dev_free(c, e.Ml16[l], c16);
         dev_free(c, e.Minv[l], level_boxes(l) * sizeof(float));
+        dev_free(c, e.Lh[l], e.Lh[l] ? level_boxes(l) * harm_row(e.p) * sizeof(float) : 0);
     }
     e = Expansions();
 }
@@ -602,17 +707,21 @@ int ensure_expansions(dafmm_tree* t, int p, cudaStream_t s) {
 }
 
 // the F16 multipole splits of every level of a uniform tree (made on first use)
-int ensure_f16_levels(dafmm_tree* t, cudaStream_t s) {
+int ensure_f16_levels(dafmm_tree* t, bool harm, cudaStream_t s) {
     (void)s;
     dafmm_ctx* c = t->ctx;
     Expansions& e = t->ex;
     for (int l = 2; l <= e.depth; ++l) {
-        if (e.Mh16[l]) continue;
-        const size_t c16 = level_boxes(l) * (size_t)tc_rowlen16(e.p) * 2;
         int rc;
-        if ((rc = dev_alloc(c, &e.Mh16[l], c16, "multipoles (F16 split)"))) return rc;
-        if ((rc = dev_alloc(c, &e.Ml16[l], c16, "multipoles (F16 split)"))) return rc;
-        if ((rc = dev_alloc(c, (void**)&e.Minv[l], level_boxes(l) * sizeof(float), "multipole factors"))) return rc;
+        if (!e.Mh16[l]) {
+            const size_t c16 = level_boxes(l) * (size_t)tc_rowlen16(e.p) * 2;
+            if ((rc = dev_alloc(c, &e.Mh16[l], c16, "multipoles (F16 split)"))) return rc;
+            if ((rc = dev_alloc(c, &e.Ml16[l], c16, "multipoles (F16 split)"))) return rc;
+            if ((rc = dev_alloc(c, (void**)&e.Minv[l], level_boxes(l) * sizeof(float), "multipole factors"))) return rc;
+        }
+        if (harm && !e.Lh[l] &&
+            (rc = dev_alloc(c, (void**)&e.Lh[l], level_boxes(l) * harm_row(e.p) * sizeof(float), "locals (harmonic)")))
+            return rc;
     }
     return DAFMM_OK;
 }
@@ -1601,7 +1710,11 @@ int dafmm_eval(dafmm_tree* t, int order, double theta, int precision, double* ph
         const int prec_m = precision | (f32_mult ? kRowsF32 : 0);
         Expansions& ex = t->ex;
         ex.M_f32 = f32_mult;
-        if (f16_m2l && ((rc = ensure_f16_levels(t, s)) || (rc = ensure_k16(c, order, s)))) return rc;
+        // the F16 M2L in the harmonic basis: (p + 1)^2 free coefficients per row instead of ncoef
+        const bool harm = f16_m2l && c->m2l_harm;
+        if (f16_m2l && ((rc = ensure_f16_levels(t, harm, s)) ||
+                        (rc = harm ? ensure_k16h(c, order, s) : ensure_k16(c, order, s))))
+            return rc;
         auto tc_args = [&](int mode, int lmin, int lmax) {
             TCArgs a;
             memset(&a, 0, sizeof(a));
@@ -1651,7 +1764,7 @@ int dafmm_eval(dafmm_tree* t, int order, double theta, int precision, double* ph
                 lo[l - 2] = ex.Ml16[l];
                 inv[l - 2] = ex.Minv[l];
             }
-            CK(c, tc_split_f16_multi(L - 1, src, nrows, hi, lo, inv, order, s, f32_mult), "split");
+            CK(c, tc_split_f16_multi(L - 1, src, nrows, hi, lo, inv, order, s, f32_mult, harm), "split");
             ++launches;
         } else if (precision != DAFMM_FP64 && !fff && !(tc_m2m && tc_m2l))
             for (int l = 2; l <= L; ++l) {
@@ -1669,27 +1782,47 @@ int dafmm_eval(dafmm_tree* t, int order, double theta, int precision, double* ph
             mark(4);
             TCArgs a = tc_args(kTcM2L, 2, L);
             a.f16 = f16_m2l;
-            a.out_f32 = f32_locals;
+            a.harm = harm;
+            a.out_f32 = f32_locals || harm;
             for (int l = 2; l <= L; ++l) {
                 a.a_hi[l] = f16_m2l ? ex.Mh16[l] : (const void*)ex.Mhi[l];
                 a.a_lo[l] = f16_m2l ? ex.Ml16[l] : (const void*)ex.Mlo[l];
                 a.a_inv[l] = ex.Minv[l];
-                a.out[l] = ex.L[l];
+                // harmonic basis: the free coefficients (FP32 rows), expanded below
+                a.out[l] = harm ? reinterpret_cast<double*>(ex.Lh[l]) : ex.L[l];
                 // the L2L of level 3 reads the TF32 split of level 2's locals; every finer
                 // level's split is written by the L2L that completes it
-                if (tc_l2l && l == 2) {
+                if (tc_l2l && l == 2 && !harm) {
                     a.out_hi[l] = ex.Lhi[l];
                     a.out_lo[l] = ex.Llo[l];
                 }
                 a.scale[l] = 1.0 / ldexp(t->dom[3], -l);
             }
-            a.b_hi = f16_m2l ? od.Kh16 : (const void*)od.Khi;
-            a.b_lo = f16_m2l ? od.Kl16 : (const void*)od.Klo;
-            a.inv_r = od.k16_inv_r;
-            a.inv_c = od.k16_inv_c;
+            a.b_hi = harm ? od.Kh16h : f16_m2l ? od.Kh16 : (const void*)od.Khi;
+            a.b_lo = harm ? od.Kl16h : f16_m2l ? od.Kl16 : (const void*)od.Klo;
+            a.inv_r = harm ? od.k16h_inv_r : od.k16_inv_r;
+            a.inv_c = harm ? od.k16h_inv_c : od.k16_inv_c;
             a.nkey = kNumKeys;
             CK(c, tc_launch(order, a, s), "M2L (tensor cores)");
             ++launches;
+            if (harm) {
+                // every coefficient of the locals from the free ones (and the TF32 split of
+                // level 2's, which the L2L of level 3 reads)
+                const float* red[kTcMaxLevels];
+                void* full[kTcMaxLevels];
+                float *hs[kTcMaxLevels], *ls[kTcMaxLevels];
+                int nrows[kTcMaxLevels];
+                for (int l = 2; l <= L; ++l) {
+                    red[l - 2] = ex.Lh[l];
+                    full[l - 2] = ex.L[l];
+                    hs[l - 2] = tc_l2l && l == 2 ? ex.Lhi[l] : nullptr;
+                    ls[l - 2] = tc_l2l && l == 2 ? ex.Llo[l] : nullptr;
+                    nrows[l - 2] = (int)level_boxes(l);
+                }
+                CK(c, tc_harm_expand(order, L - 1, red, full, hs, ls, nrows, f32_locals, od.hx_step, od.hx_w, od.hx_cst, s),
+                   "M2L (harmonic expansion)");
+                ++launches;
+            }
         } else {
             // M2L by rotation (Sec. 3.4); by default from p = 4, where it is the faster one (FP64),
             // and from p = 2 in float-float
@@ -1778,6 +1911,10 @@ int dafmm_set_option(dafmm_ctx* c, int option, int64_t value) {
     }
     if (option == DAFMM_OPT_M2L_ROTATION && (value == -1 || value == 0 || value == 1)) {
         c->m2l_rot = (int)value;
+        return DAFMM_OK;
+    }
+    if (option == DAFMM_OPT_M2L_HARMONIC && (value == 0 || value == 1)) {
+        c->m2l_harm = (int)value;
         return DAFMM_OK;
     }
     return fail(c, DAFMM_ERR_INVALID_ARG, "option");

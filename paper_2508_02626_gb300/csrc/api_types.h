@@ -27,6 +27,7 @@ struct dafmm_ctx {
     int tc_mask = 5;          // FP32 mode: bit 0 M2L, bit 1 M2M, bit 2 L2L on the tensor cores
     int leaf_warps = 4;       // adaptive leaf kernel: leaves (one warp each) per thread block
     int m2l_f16 = 1;          // FP32 mode: M2L on F16 split operands (else TF32)
+    int m2l_harm = 1;         // FP32 mode, uniform trees: the F16 M2L in the harmonic basis
     int m2l_rot = -1;         // FP64 mode: M2L by rotation (Sec. 3.4), uniform and adaptive; -1 = from p = 4
     int num_sms = 0;
     bool tc_capable = false;  // compute capability 10.x
@@ -50,6 +51,8 @@ struct Expansions {
     void* Mh16[dafmm::kMaxUniformDepth + 1] = {};
     void* Ml16[dafmm::kMaxUniformDepth + 1] = {};
     float* Minv[dafmm::kMaxUniformDepth + 1] = {};
+    // the harmonic-basis M2L's output rows (free coefficients, FP32, nharm rounded up to 8)
+    float* Lh[dafmm::kMaxUniformDepth + 1] = {};
     bool L_f32 = false;  // the last evaluation left FP32 rows (ncp floats per box) in L
     bool M_f32 = false;  // ... and in M
 };

@@ -19,6 +19,28 @@ __host__ __device__ constexpr int ncoef_of(int p) { return (p + 1) * (p + 2) * (
 // row stride of every expansion array: ncoef rounded up to 8 (32-byte rows in FP32)
 __host__ __device__ constexpr int ncp_of(int p) { return (ncoef_of(p) + 7) / 8 * 8; }
 
+// Harmonic basis.  The multipole expansions of 1/r are polynomials in d = r / r^2 whose
+// homogeneous parts are solid harmonics (Eq. 2 is the generating function of the Legendre
+// polynomials: its degree-n part is |s|^n |d|^n P_n(cos gamma)), and the local expansions are
+// Taylor polynomials of a harmonic potential, whose homogeneous parts are harmonic too.  A
+// harmonic homogeneous polynomial of degree n is fixed by its 2n + 1 coefficients with z
+// exponent c <= 1: Laplace's equation gives every other one,
+//   (c + 2)(c + 1) a[a, b, c + 2] = -(a + 2)(a + 1) a[a + 2, b, c] - (b + 2)(b + 1) a[a, b + 2, c],
+// so an expansion of order p has (p + 1)^2 free coefficients instead of ncoef(p).
+__host__ __device__ constexpr int nharm_of(int p) { return (p + 1) * (p + 1); }
+// row stride of arrays of free coefficients: nharm rounded up to 8
+__host__ __device__ constexpr int harm_row(int p) { return (nharm_of(p) + 7) / 8 * 8; }
+// the coefficient index (the layout of da_index: degree, x exponent descending, y descending)
+// of free coefficient k: degree n with n^2 <= k < (n + 1)^2, then within the degree the c <= 1
+// coefficients in layout order: (n, 0, 0), (n - 1, 1, 0), (n - 1, 0, 1), (n - 2, 2, 0), ...
+__host__ __device__ inline int harm_full_index(int k) {
+    int n = 0;
+    while ((n + 1) * (n + 1) <= k) ++n;
+    const int r = k - n * n;
+    const int a = n - (r + 1) / 2, c = (r > 0 && (r & 1) == 0) ? 1 : 0, b = n - a - c;
+    return n * (n + 1) * (n + 2) / 6 + (b + c) * (b + c + 1) / 2 + c;
+}
+
 // ---- views passed by value to kernels ---------------------------------------------------
 struct TreeView {
     int64_t n;
@@ -64,6 +86,14 @@ struct OrderData {
     // F16 splits of the M2L matrices with their power-of-two row and matrix factors
     void* Kh16 = nullptr; void* Kl16 = nullptr;
     float* k16_inv_r = nullptr; float* k16_inv_c = nullptr;
+    // the same for the M2L in the harmonic basis: [343][npt_h][rowlen_h] F16 parts of
+    // K^_v restricted to the free coefficients (rows) and composed with the expansion from them
+    // (columns), and the expansion's steps (harm_expand_launch)
+    void* Kh16h = nullptr; void* Kl16h = nullptr;
+    float* k16h_inv_r = nullptr; float* k16h_inv_c = nullptr;
+    int4* hx_step = nullptr;      // [ncoef - nharm]: (i, i1, i2, 0), in order of increasing c
+    float2* hx_w = nullptr;       // their weights (w1, w2): a[i] = w1 a[i1] + w2 a[i2]
+    int hx_cst[kMaxOrder + 3] = {};  // steps of z exponent c: [hx_cst[c], hx_cst[c + 1])
     int* mul_rowptr = nullptr; ushort2* mul_pairs = nullptr; short* mul_minus = nullptr;
     size_t mul_npairs = 0;
     double* K64 = nullptr;        // [343][nc][ncp]: K^_v[b][a] (scaled M2L, Eq. 5)

@@ -182,17 +182,19 @@ __device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.
 // ---- configuration per order ------------------------------------------------------------------
 // H = false: TF32 operands (rows of ncp FP32 values); H = true: F16 operands (rows of ncph =
 // ncoef rounded up to 16 halves).  Either way a K chunk is 128 bytes of a row (32 TF32 or 64
-// F16 values) and one MMA step takes 32 bytes of it (K = 8 or 16).
-template <int P, bool H = false>
+// F16 values) and one MMA step takes 32 bytes of it (K = 8 or 16).  R = true: the contraction
+// in the harmonic basis (the (p + 1)^2 free coefficients of rows and columns; see nharm_of).
+template <int P, bool H = false, bool R = false>
 struct Cfg {
-    static constexpr int NC = ncoef_of(P);
-    static constexpr int NCP = ncp_of(P);
+    static constexpr int NC = R ? nharm_of(P) : ncoef_of(P);  // coefficients contracted and produced
+    static constexpr int NCP = (NC + 7) / 8 * 8;                 // output row stride
     static constexpr int ROWLEN = H ? (NC + 15) / 16 * 16 : NCP;  // operand row length, elements
     static constexpr int KPC = H ? 64 : 32;                         // elements per 128-byte chunk
     static constexpr int KSTEP = H ? 16 : 8;                        // elements per MMA step
     static constexpr int NPF = (NC + 15) / 16 * 16;               // N padded to the MMA granule
     static constexpr int NHALF = NPF > 192 ? 2 : 1;                // N split: <= 192 register sums per thread
     static constexpr int NP = NHALF == 1 ? NPF : (NPF / 2 + 15) / 16 * 16;
+    static constexpr int NPT = NHALF == 1 ? NPF : 2 * NP;         // rows per matrix in the B tables
     static constexpr int NKC = (ROWLEN + KPC - 1) / KPC;           // K chunks of 128 bytes
     static constexpr int KSTEPS_LAST = (ROWLEN - KPC * (NKC - 1)) / KSTEP;  // MMA steps in the last chunk
     static constexpr int A_BYTES = 128 * 128;

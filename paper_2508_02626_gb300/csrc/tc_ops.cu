@@ -72,9 +72,9 @@ __device__ __forceinline__ int out_index(const TCParams& prm, const WorkItem& it
 }
 
 // ---- the kernel -----------------------------------------------------------------------------
-template <int P, bool H>
+template <int P, bool H, bool R>
 __global__ void __launch_bounds__(192, 1) k_tc(const __grid_constant__ TCParams prm) {
-    using C = Cfg<P, H>;
+    using C = Cfg<P, H, R>;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     // 1024-byte aligned stage ring, then barriers
     unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -356,6 +356,7 @@ struct F16Segments {
     int first[9];
     int nseg;
     int src_f32;
+    int harm;            // take the free coefficients of the harmonic basis (harm_full_index)
 };
 
 // one warp per row of src [nrows][ncp] -> hi, lo [nrows][rowlen] halves, inv[nrows].  The work
@@ -380,8 +381,9 @@ __global__ void k_split_f16_rows(F16Segments sg, int nc, int ncp, int rowlen) {
         const int k = lane + 32 * j;
         float x = 0.f;
         if (k < nc) {
-            x = sg.src_f32 ? static_cast<const float*>(sg.src[g])[(size_t)row * ncp + k]
-                           : (float)static_cast<const double*>(sg.src[g])[(size_t)row * ncp + k];
+            const int kk = sg.harm ? harm_full_index(k) : k;
+            x = sg.src_f32 ? static_cast<const float*>(sg.src[g])[(size_t)row * ncp + kk]
+                           : (float)static_cast<const double*>(sg.src[g])[(size_t)row * ncp + kk];
         }
         v[j] = x;
         mx = fmaxf(mx, fabsf(x));
@@ -460,6 +462,75 @@ __global__ void k_k16_split(const double* __restrict__ K, int nkey, int nc, int 
     }
 }
 
+// K^_v in the harmonic basis (one block per matrix): rows are the free coefficients of the
+// output, columns the free coefficients of the input through the expansion X [nc][nh] that
+// restores every coefficient from them, Kh[key][r][j] = sum_i K[key][free r][i] X[i][j]
+__global__ void k_harm_K(const double* __restrict__ K, int nc, int ncp, const double* __restrict__ X, int nh, int nhp,
+                         double* __restrict__ Kh) {
+    const size_t key = blockIdx.x;
+    for (int e = threadIdx.x; e < nh * nhp; e += blockDim.x) {
+        const int r = e / nhp, j = e % nhp;
+        double acc = 0.0;
+        if (j < nh) {
+            const double* kr = K + (key * nc + harm_full_index(r)) * ncp;
+            for (int i = 0; i < nc; ++i) acc = fma(kr[i], X[(size_t)i * nh + j], acc);
+        }
+        Kh[(key * nh + r) * nhp + j] = acc;
+    }
+}
+
+// rows of free coefficients (FP32, stride nhp) -> full expansion rows (FP32 or FP64, stride ncp),
+// one warp per row: the free coefficients go to their places, then the others follow from
+// Laplace's equation in order of increasing z exponent (each step a[i] = w1 a[i1] + w2 a[i2]
+// reads two coefficients of z exponent c - 2), columns nc..ncp-1 are zeros; optionally the TF32
+// split of the written row
+struct HarmSegments {
+    const float* red[kTcMaxLevels];
+    void* full[kTcMaxLevels];
+    float* hi[kTcMaxLevels];
+    float* lo[kTcMaxLevels];
+    int first[kTcMaxLevels + 1];
+    int nseg;
+    int full_f32;
+    int cst[kMaxOrder + 3];  // steps of z exponent c: [cst[c], cst[c + 1]), c = 2..p
+};
+
+__global__ void __launch_bounds__(128) k_harm_expand(HarmSegments sg, const int4* __restrict__ step,
+                                                     const float2* __restrict__ w, int p, int nc, int ncp, int nh,
+                                                     int nhp) {
+    __shared__ float sbuf[4][ncp_of(kMaxOrder)];
+    const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
+    int row = (int)(blockIdx.x * 4 + wi);
+    if (row >= sg.first[sg.nseg]) return;
+    int g = 0;
+    while (g + 1 < sg.nseg && row >= sg.first[g + 1]) ++g;
+    row -= sg.first[g];
+    float* buf = sbuf[wi];
+    const float* r = sg.red[g] + (size_t)row * nhp;
+    for (int k = lane; k < nh; k += 32) buf[harm_full_index(k)] = r[k];
+    __syncwarp();
+    for (int c = 2; c <= p; ++c) {
+        for (int s = sg.cst[c] + lane; s < sg.cst[c + 1]; s += 32) {
+            const int4 st = step[s];
+            const float2 ww = w[s];
+            buf[st.x] = fmaf(ww.x, buf[st.y], ww.y * buf[st.z]);
+        }
+        __syncwarp();
+    }
+    float* hi = sg.hi[g] ? sg.hi[g] + (size_t)row * ncp : nullptr;
+    float* lo = sg.lo[g] ? sg.lo[g] + (size_t)row * ncp : nullptr;
+    for (int k = lane; k < ncp; k += 32) {
+        const float v = k < nc ? buf[k] : 0.f;
+        if (sg.full_f32) static_cast<float*>(sg.full[g])[(size_t)row * ncp + k] = v;
+        else static_cast<double*>(sg.full[g])[(size_t)row * ncp + k] = (double)v;
+        if (hi) {
+            const float h = to_tf32(v);
+            hi[k] = h;
+            lo[k] = to_tf32(v - h);
+        }
+    }
+}
+
 }  // namespace tc
 
 // ---- host side ---------------------------------------------------------------------------------
@@ -472,14 +543,23 @@ int tc_npt(int p) {
 
 int tc_rowlen16(int p) { return (ncoef_of(p) + 15) / 16 * 16; }
 
+int tc_npt_h(int p) {
+    const int npf = (nharm_of(p) + 15) / 16 * 16;
+    if (npf <= 192) return npf;
+    return 2 * ((npf / 2 + 15) / 16 * 16);
+}
+
+int tc_rowlen16h(int p) { return (nharm_of(p) + 15) / 16 * 16; }
+
 cudaError_t tc_split_f16_multi(int nseg, const void* const* src, const int* nrows, void* const* hi, void* const* lo,
-                               float* const* inv, int p, cudaStream_t s, bool src_f32) {
+                               float* const* inv, int p, cudaStream_t s, bool src_f32, bool harm) {
     if (nseg < 1 || nseg > 8) return cudaErrorInvalidValue;
     if (ncoef_of(p) > 32 * 12) return cudaErrorInvalidValue;
     tc::F16Segments sg;
     memset(&sg, 0, sizeof(sg));
     sg.nseg = nseg;
     sg.src_f32 = src_f32 ? 1 : 0;
+    sg.harm = harm ? 1 : 0;
     for (int g = 0; g < nseg; ++g) {
         sg.src[g] = src[g];
         sg.hi[g] = static_cast<__half*>(hi[g]);
@@ -490,13 +570,14 @@ cudaError_t tc_split_f16_multi(int nseg, const void* const* src, const int* nrow
     const int total = sg.first[nseg];
     if (total == 0) return cudaSuccess;
     const unsigned blocks = (unsigned)(((size_t)total * 32 + 255) / 256);
-    tc::k_split_f16_rows<<<blocks, 256, 0, s>>>(sg, ncoef_of(p), ncp_of(p), tc_rowlen16(p));
+    tc::k_split_f16_rows<<<blocks, 256, 0, s>>>(sg, harm ? nharm_of(p) : ncoef_of(p), ncp_of(p),
+                                                 harm ? tc_rowlen16h(p) : tc_rowlen16(p));
     return cudaGetLastError();
 }
 
 cudaError_t tc_split_f16(const double* src, int nrows, int p, void* hi, void* lo, float* inv, cudaStream_t s) {
     const void* sv = src;
-    return tc_split_f16_multi(1, &sv, &nrows, &hi, &lo, &inv, p, s, false);
+    return tc_split_f16_multi(1, &sv, &nrows, &hi, &lo, &inv, p, s, false, false);
 }
 
 cudaError_t tc_prepare_k16(const double* K, int nkey, int p, void* hi, void* lo, float* inv_r, float* inv_c,
@@ -508,6 +589,43 @@ cudaError_t tc_prepare_k16(const double* K, int nkey, int p, void* hi, void* lo,
     tc::k_k16_keyexp<<<nkey, 256, 0, s>>>(K, nc, ncp, er, ec);
     tc::k_k16_split<<<152 * 16, 256, 0, s>>>(K, nkey, nc, ncp, npt, rowlen, er, ec, static_cast<__half*>(hi),
                                               static_cast<__half*>(lo), inv_r, inv_c);
+    return cudaGetLastError();
+}
+
+cudaError_t tc_prepare_k16h(const double* K, int nkey, int p, const double* X, double* Kh, void* hi, void* lo,
+                            float* inv_r, float* inv_c, float* scratch, cudaStream_t s) {
+    const int nc = ncoef_of(p), ncp = ncp_of(p), nh = nharm_of(p), nhp = (nh + 7) / 8 * 8;
+    const int npt = tc_npt_h(p), rowlen = tc_rowlen16h(p);
+    float* er = scratch;        // npt row exponents
+    float* ec = scratch + npt;  // nkey matrix exponents
+    tc::k_harm_K<<<nkey, 256, 0, s>>>(K, nc, ncp, X, nh, nhp, Kh);
+    tc::k_k16_rowexp<<<npt, 256, 0, s>>>(Kh, nkey, nh, nhp, npt, er);
+    tc::k_k16_keyexp<<<nkey, 256, 0, s>>>(Kh, nh, nhp, er, ec);
+    tc::k_k16_split<<<152 * 16, 256, 0, s>>>(Kh, nkey, nh, nhp, npt, rowlen, er, ec, static_cast<__half*>(hi),
+                                              static_cast<__half*>(lo), inv_r, inv_c);
+    return cudaGetLastError();
+}
+
+cudaError_t tc_harm_expand(int p, int nseg, const float* const* red, void* const* full, float* const* hi,
+                           float* const* lo, const int* nrows, bool full_f32, const int4* step, const float2* w,
+                           const int* cst, cudaStream_t s) {
+    if (nseg < 1 || nseg > kTcMaxLevels) return cudaErrorInvalidValue;
+    tc::HarmSegments sg;
+    memset(&sg, 0, sizeof(sg));
+    sg.nseg = nseg;
+    sg.full_f32 = full_f32 ? 1 : 0;
+    for (int g = 0; g < nseg; ++g) {
+        sg.red[g] = red[g];
+        sg.full[g] = full[g];
+        sg.hi[g] = hi ? hi[g] : nullptr;
+        sg.lo[g] = lo ? lo[g] : nullptr;
+        sg.first[g + 1] = sg.first[g] + nrows[g];
+    }
+    for (int c = 0; c <= p + 1; ++c) sg.cst[c] = cst[c];
+    const int total = sg.first[nseg];
+    if (total == 0) return cudaSuccess;
+    const int nh = nharm_of(p);
+    tc::k_harm_expand<<<(total + 3) / 4, 128, 0, s>>>(sg, step, w, p, ncoef_of(p), ncp_of(p), nh, (nh + 7) / 8 * 8);
     return cudaGetLastError();
 }
 
@@ -546,9 +664,9 @@ static bool encode_level(PFN_cuTensorMapEncodeTiled_v12000 enc, CUtensorMap* map
                CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <int P, bool H>
+template <int P, bool H, bool R = false>
 static cudaError_t launch_tc(const TCArgs& a, cudaStream_t s) {
-    using C = tc::Cfg<P, H>;
+    using C = tc::Cfg<P, H, R>;
     auto enc = get_encode();
     if (!enc) return cudaErrorNotSupported;
     TCParams prm;
@@ -582,23 +700,26 @@ static cudaError_t launch_tc(const TCArgs& a, cudaStream_t s) {
     }
     prm.tile_base[prm.nlev] = tiles;
     prm.ntiles = tiles;
-    const int npt = tc_npt(P);
+    const int npt = C::NPT;
     prm.inv_r = a.inv_r;
     prm.inv_c = a.inv_c;
     if (!encode_rows(enc, &prm.b_hi, a.b_hi, C::ROWLEN, npt, a.nkey, C::NPL, H) ||
         !encode_rows(enc, &prm.b_lo, a.b_lo, C::ROWLEN, npt, a.nkey, C::NPL, H))
         return cudaErrorInvalidValue;
     if (tiles == 0) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(tc::k_tc<P, H>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM_BYTES);
+    cudaError_t e = cudaFuncSetAttribute(tc::k_tc<P, H, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM_BYTES);
     if (e != cudaSuccess) return e;
     const int grid = tiles < a.num_sms ? tiles : a.num_sms;
-    tc::k_tc<P, H><<<grid, 192, C::SMEM_BYTES, s>>>(prm);
+    tc::k_tc<P, H, R><<<grid, 192, C::SMEM_BYTES, s>>>(prm);
     return cudaGetLastError();
 }
 template <int P>
 static cudaError_t launch_tc_any(const TCArgs& a, cudaStream_t s) {
-    if (a.f16) return a.mode == kTcM2L ? launch_tc<P, true>(a, s) : cudaErrorInvalidValue;
-    return launch_tc<P, false>(a, s);
+    if (a.f16) {
+        if (a.mode != kTcM2L) return cudaErrorInvalidValue;
+        return a.harm ? launch_tc<P, true, true>(a, s) : launch_tc<P, true, false>(a, s);
+    }
+    return a.harm ? cudaErrorInvalidValue : launch_tc<P, false>(a, s);
 }
 
 cudaError_t tc_launch(int p, const TCArgs& a, cudaStream_t s) {

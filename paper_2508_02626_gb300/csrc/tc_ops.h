@@ -45,6 +45,8 @@ struct TCArgs {
     int mode;
     int lmin, lmax;
     bool f16;                                    // F16 split operands (M2L only), else TF32
+    bool harm;                                   // (F16 M2L) the harmonic basis: A rows, matrices
+                                                 // and out rows hold the free coefficients only
     const void* a_hi[kMaxUniformDepth + 1];      // per level, [8^l][rowlen] split parts of the A operand
     const void* a_lo[kMaxUniformDepth + 1];
     const float* a_inv[kMaxUniformDepth + 1];    // F16: per-box factor undoing the row scale
@@ -127,15 +129,32 @@ int tc_rowlen16(int p);  // F16 operand row length: ncoef rounded up to 16
 // F16 split of FP64 rows [nrows][ncp] with a power-of-two scale per row (row max in [0.5, 1)):
 // hi, lo [nrows][rowlen16] halves, inv[nrows] = the factor that undoes the scale
 cudaError_t tc_split_f16(const double* src, int nrows, int p, void* hi, void* lo, float* inv, cudaStream_t s);
-// the same for up to 8 arrays in one launch; src_f32: the rows are FP32 (ncp floats per row)
+// the same for up to 8 arrays in one launch; src_f32: the rows are FP32 (ncp floats per row);
+// harm: only the free coefficients of the harmonic basis, into rows of tc_rowlen16h(p) halves
 cudaError_t tc_split_f16_multi(int nseg, const void* const* src, const int* nrows, void* const* hi, void* const* lo,
-                               float* const* inv, int p, cudaStream_t s, bool src_f32);
+                               float* const* inv, int p, cudaStream_t s, bool src_f32, bool harm);
 // F16 split of the M2L matrices K[nkey][nc][ncp] (FP64): row b of matrix k is scaled by
 // r_b c_k (powers of two: r_b from the largest entry of row b over all matrices, c_k from the
 // largest entry of the row-scaled matrix k); hi, lo [nkey][npt][rowlen16]; inv_r[npt],
 // inv_c[nkey] undo the scales.  `scratch` holds nkey + npt floats.
 cudaError_t tc_prepare_k16(const double* K, int nkey, int p, void* hi, void* lo, float* inv_r, float* inv_c,
                            float* scratch, cudaStream_t s);
+// The M2L in the harmonic basis (nharm_of(p) free coefficients, harm_full_index): npt / rowlen
+// of its matrix tables, and the tables: Kh = K restricted to the free output coefficients and
+// composed with X [nc][nh] (the expansion from the free input coefficients), as FP64 scratch
+// [nkey][nh][nhp = nh rounded up to 8], then split as tc_prepare_k16 does (scratch: npt + nkey
+// floats).
+int tc_npt_h(int p);
+int tc_rowlen16h(int p);
+cudaError_t tc_prepare_k16h(const double* K, int nkey, int p, const double* X, double* Kh, void* hi, void* lo,
+                            float* inv_r, float* inv_c, float* scratch, cudaStream_t s);
+// rows of free coefficients (FP32, nhp per row) of up to kTcMaxLevels arrays -> full rows (FP32
+// or FP64, ncp per row) by Laplace's equation: steps (i, i1, i2) with weights (w1, w2), those of
+// z exponent c at [cst[c], cst[c + 1]); hi / lo (optional, per array or null) receive the TF32
+// split of the written rows
+cudaError_t tc_harm_expand(int p, int nseg, const float* const* red, void* const* full, float* const* hi,
+                           float* const* lo, const int* nrows, bool full_f32, const int4* step, const float2* w,
+                           const int* cst, cudaStream_t s);
 cudaError_t tcg_launch(int p, const TCGArgs& a, cudaStream_t s);
 cudaError_t tc_split_tf32(const double* src, float* hi, float* lo, size_t n, cudaStream_t s);
 cudaError_t tc_split_rows(const double* src, int nkey, int p, float* hi, float* lo, cudaStream_t s);

@@ -174,3 +174,24 @@ def test_two_products_miss_the_fp32_bound(p):
     for keep in (("hh", "hl"), ("hh", "lh")):
         e2 = potential_error(p, f16x3_local(Ks, Ms, products=keep), L64, X)
         assert e2 > 10 * 3.8e-6 and e2 > 100 * e3, (keep, e2, e3)
+
+
+@pytest.mark.parametrize("p", [4, 8, 10])
+def test_harmonic_f16_split_is_fp32_level(p):
+    """The same scheme in the harmonic basis (the FP32 mode's default): the matrices restricted
+    to the free coefficients and composed with the expansion X, the multipoles' free
+    coefficients only, the result expanded by X -- within the same bounds."""
+    from test_harmonic_basis import basis
+    _, free, X = basis(p)
+    Ks = matrices(p)
+    Kh = np.array([K[free] @ X for K in Ks])
+    for seed in (0, 1):
+        Ms, Xp = workload(p, seed)
+        L64 = np.einsum("vba,va->b", Ks, Ms)
+        plain = np.zeros(Ks.shape[1], np.float32)
+        for K, M in zip(Ks, Ms):
+            plain = plain + K.astype(np.float32) @ M.astype(np.float32)
+        eh = potential_error(p, X @ f16x3_local(Kh, Ms[:, free]), L64, Xp)
+        e32 = potential_error(p, plain.astype(np.float64), L64, Xp)
+        assert eh <= max(4.0 * e32, 1e-6), (eh, e32)
+        assert eh <= 3.8e-6

@@ -211,14 +211,14 @@ int dafmm_last_phase_ms(dafmm_ctx* ctx, double* out10);
  *   instead of 82k at p = 10; -1 (default) = 1 from p = 4, else 0.  Uniform and adaptive trees
  *   (the V-list pairs of a level have the same 316 box displacements). */
 #define DAFMM_OPT_M2L_ROTATION 5
-/*   DAFMM_OPT_M2L_HARMONIC: the FP32 mode's F16 M2L on uniform trees: 1 (default) = in the
- *   harmonic basis.  The homogeneous parts of the multipole expansions (Eq. 2: the Legendre
- *   generating function) and of the local expansions (Taylor polynomials of a harmonic
- *   potential) are harmonic polynomials, each fixed by its coefficients of z exponent <= 1; the
- *   M2L contracts those (p + 1)^2 coefficients against K^_v restricted and composed accordingly
- *   (81 instead of 165 at p = 8) and restores the others by Laplace's equation -- the same
- *   result up to rounding with about a quarter of the multiply-adds.  0 = all ncoef
- *   coefficients. */
+/*   DAFMM_OPT_M2L_HARMONIC: the FP32 mode's F16 M2L (uniform and adaptive trees, forests):
+ *   1 (default) = in the harmonic basis.  The homogeneous parts of the multipole expansions
+ *   (Eq. 2: the Legendre generating function) and of the local expansions (Taylor polynomials
+ *   of a harmonic potential) are harmonic polynomials, each fixed by its coefficients of z
+ *   exponent <= 1; the M2L contracts those (p + 1)^2 coefficients against K^_v restricted and
+ *   composed accordingly (81 instead of 165 at p = 8) and restores the others by Laplace's
+ *   equation -- the same result up to rounding with about a quarter of the multiply-adds.
+ *   0 = all ncoef coefficients. */
 #define DAFMM_OPT_M2L_HARMONIC 6
 int dafmm_set_option(dafmm_ctx* ctx, int option, int64_t value);
 

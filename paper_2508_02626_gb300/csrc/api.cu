@@ -1151,13 +1151,21 @@ int eval_adaptive(dafmm_tree* t, int order, int precision, double* dphi, double*
         const bool tc = precision != DAFMM_FP64 && c->m2l_kernel == 0 && c->tc_capable && order >= 2 &&
                         (precision != DAFMM_FP32 || (c->tc_mask & 1));
         const bool f16 = tc && precision == DAFMM_FP32 && c->m2l_f16;
-        // F16 split: hi and lo rows of rowlen16 halves, stored in the FP32 multipole buffer
-        const size_t c16 = (size_t)t->nbox * tc_rowlen16(order);
+        // the F16 M2L in the harmonic basis: (p + 1)^2 free coefficients per row
+        const bool harm = f16 && c->m2l_harm;
+        // F16 split: hi and lo rows of rowlen16 halves (harmonic: rowlen16h), stored in the FP32
+        // multipole buffer (8 ncp bytes per box), followed in the harmonic basis by the M2L's FP32
+        // rows of free coefficients (harm_row floats per box; rowlen16h + harm_row <= 2 ncp)
+        const size_t c16 = (size_t)t->nbox * (harm ? tc_rowlen16h(order) : tc_rowlen16(order));
         void* h16 = t->aMf;
         void* l16 = reinterpret_cast<__half*>(t->aMf) + c16;
+        float* lh = reinterpret_cast<float*>(reinterpret_cast<__half*>(t->aMf) + 2 * c16);
         if (f16) {
-            if ((rc = ensure_k16(c, order, s))) return rc;
-            CK(c, tc_split_f16(t->aM, t->nbox, order, h16, l16, t->aMinv, s), "split");
+            if ((rc = harm ? ensure_k16h(c, order, s) : ensure_k16(c, order, s))) return rc;
+            const void* src = t->aM;
+            const int nrows = t->nbox;
+            float* inv = t->aMinv;
+            CK(c, tc_split_f16_multi(1, &src, &nrows, &h16, &l16, &inv, order, s, false, harm), "split");
             ++launches;
         } else if (tc) {
             CK(c, tc_split_tf32(t->aM, t->aMf, t->aMf + cnt, cnt, s), "split");
@@ -1174,20 +1182,21 @@ int eval_adaptive(dafmm_tree* t, int order, int precision, double* dphi, double*
             TCGArgs a;
             memset(&a, 0, sizeof(a));
             a.f16 = f16;
+            a.harm = harm;
             a.a_hi = f16 ? h16 : (const void*)t->aMf;
             a.a_lo = f16 ? l16 : (const void*)(t->aMf + cnt);
             a.a_inv = t->aMinv;
-            a.b_hi = f16 ? od.Kh16 : (const void*)od.Khi;
-            a.b_lo = f16 ? od.Kl16 : (const void*)od.Klo;
-            a.inv_r = od.k16_inv_r;
-            a.inv_c = od.k16_inv_c;
+            a.b_hi = harm ? od.Kh16h : f16 ? od.Kh16 : (const void*)od.Khi;
+            a.b_lo = harm ? od.Kl16h : f16 ? od.Kl16 : (const void*)od.Klo;
+            a.inv_r = harm ? od.k16h_inv_r : od.k16_inv_r;
+            a.inv_c = harm ? od.k16h_inv_c : od.k16_inv_c;
             a.nkey = kNumKeys;
             a.tg = t->grp_tg;
             a.parent = t->a_parent;
             a.colleague = t->a_colleague;
             a.child = t->a_child;
             a.geom = t->a_geom;
-            a.out = t->aL;
+            a.out = harm ? reinterpret_cast<double*>(lh) : t->aL;
             a.err = c->d_err;
             a.nbox = t->nbox;
             a.num_sms = c->num_sms;
@@ -1200,6 +1209,18 @@ int eval_adaptive(dafmm_tree* t, int order, int precision, double* dphi, double*
                 }
             CK(c, tcg_launch(order, a, s), "M2L (tensor cores)");
             ++launches;
+            if (harm) {
+                // the other coefficients of the locals of every box of levels >= 2 (the M2L's
+                // targets, contiguous from level_start[2])
+                const int b0 = t->level_start[2];
+                const float* red = lh + (size_t)b0 * harm_row(order);
+                void* full = t->aL + (size_t)b0 * od.ncp;
+                const int nrows = t->nbox - b0;
+                CK(c, tc_harm_expand(order, 1, &red, &full, nullptr, nullptr, &nrows, false, od.hx_step, od.hx_w,
+                                     od.hx_cst, s),
+                   "M2L (harmonic expansion)");
+                ++launches;
+            }
             for (int l = 2; l <= t->maxlev; ++l) {
                 CK(c, ops->p2l_a(av, precision, t->level_start[l], t->level_start[l + 1], t->aL, s), "P2L");
                 ++launches;

@@ -164,7 +164,6 @@ __device__ __forceinline__ void tmem_ld16w(uint32_t taddr, uint32_t (&r)[16]) {
         : "memory");
 }
 
-
 // 32 lanes x 16 columns from registers into TMEM (the caller waits with tmem_wait_st)
 __device__ __forceinline__ void tmem_st16(uint32_t taddr, const float* v) {
     asm volatile(

@@ -76,9 +76,9 @@ __device__ __forceinline__ int term_key(const Terms& tm) {
 // rows 64-127
 constexpr int kTcgThreads = 224;
 
-template <int P, bool H>
+template <int P, bool H, bool R>
 __global__ void __launch_bounds__(kTcgThreads, 1) k_tcg(const __grid_constant__ TCGParams prm) {
-    using C = Cfg<P, H>;
+    using C = Cfg<P, H, R>;
     constexpr int ESZ = H ? 2 : 4;  // operand element bytes
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -341,17 +341,22 @@ __global__ void __launch_bounds__(kTcgThreads, 1) k_tcg(const __grid_constant__ 
             }
             if (!ok) break;
             if (trow >= 0) {
+                // FP64 rows; in the harmonic basis FP32 rows of the free coefficients (expanded
+                // afterwards)
                 double* orow = prm.out + (size_t)trow * C::NCP;
+                float* orowf = reinterpret_cast<float*>(prm.out) + (size_t)trow * C::NCP;
                 const double sc = 1.0 / prm.geom[trow].w;
 #pragma unroll
                 for (int j = 0; j < C::NP; ++j) {
                     const int b = it.half * C::NP + j;
+                    double v = 0.0;
                     if (b < C::NC) {
-                        double v = (double)S[j] * sc;
+                        v = (double)S[j] * sc;
                         if constexpr (H) v *= (double)prm.inv_r[b];
-                        orow[b] = v;
-                    } else if (b < C::NCP) {
-                        orow[b] = 0.0;
+                    }
+                    if (b < C::NCP) {
+                        if constexpr (R) orowf[b] = (float)v;
+                        else orow[b] = v;
                     }
                 }
             }
@@ -368,9 +373,9 @@ __global__ void __launch_bounds__(kTcgThreads, 1) k_tcg(const __grid_constant__ 
 }
 }  // namespace tc
 
-template <int P, bool H>
+template <int P, bool H, bool R = false>
 static cudaError_t launch_tcg(const TCGArgs& a, cudaStream_t s) {
-    using C = tc::Cfg<P, H>;
+    using C = tc::Cfg<P, H, R>;
     auto enc = get_encode();
     if (!enc) return cudaErrorNotSupported;
     if (a.ngroups > kTcgMaxGroups) return cudaErrorInvalidValue;
@@ -408,19 +413,20 @@ static cudaError_t launch_tcg(const TCGArgs& a, cudaStream_t s) {
     prm.ngroups = ng;
     prm.ntiles = tiles;
     if (tiles == 0) return cudaSuccess;
-    const int npt = tc_npt(P);
+    const int npt = C::NPT;
     if (!encode_rows(enc, &prm.b_hi, a.b_hi, C::ROWLEN, npt, a.nkey, C::NPL, H) ||
         !encode_rows(enc, &prm.b_lo, a.b_lo, C::ROWLEN, npt, a.nkey, C::NPL, H))
         return cudaErrorInvalidValue;
-    cudaError_t e = cudaFuncSetAttribute(tc::k_tcg<P, H>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM_BYTES);
+    cudaError_t e = cudaFuncSetAttribute(tc::k_tcg<P, H, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM_BYTES);
     if (e != cudaSuccess) return e;
     const int grid = tiles < a.num_sms ? tiles : a.num_sms;
-    tc::k_tcg<P, H><<<grid, tc::kTcgThreads, C::SMEM_BYTES, s>>>(prm);
+    tc::k_tcg<P, H, R><<<grid, tc::kTcgThreads, C::SMEM_BYTES, s>>>(prm);
     return cudaGetLastError();
 }
 
 template <int P>
 static cudaError_t launch_tcg_any(const TCGArgs& a, cudaStream_t s) {
+    if (a.harm) return a.f16 ? launch_tcg<P, true, true>(a, s) : cudaErrorInvalidValue;
     return a.f16 ? launch_tcg<P, true>(a, s) : launch_tcg<P, false>(a, s);
 }
 

@@ -101,6 +101,8 @@ struct TCGParams {
 
 struct TCGArgs {
     bool f16;
+    bool harm;                // (F16) the harmonic basis: A rows and matrices hold the free
+                              // coefficients; out receives FP32 rows of them (harm_row(p) floats)
     const void* a_hi;
     const void* a_lo;
     const float* a_inv;

@@ -31,7 +31,7 @@ UNIT = "particles/s"
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of the M2L kernel on
 # this workload, from one ncu capture of that kernel; valid while the kernel's source files
 # hash to the recorded value, reported as null otherwise
-M2L_TRAFFIC = {"fp32": (25.4e6, "2c5c2b768d57ed1d")}
+M2L_TRAFFIC = {"fp32": (25.4e6, "eef784baa41f372b")}
 M2L_SOURCES = ("paper_2508_02626_gb300/csrc/tc_common.cuh", "paper_2508_02626_gb300/csrc/tc_ops.cu")
 
 
@@ -486,7 +486,7 @@ def run_ours(args, rank, world):
             peak_note = "TF32 = %s BF16 %.1f TFLOP/s x 1/2 (nominal ratio)" % (peak_src, peaks["bf16_tflops"])
         # the FP32 mode's F16 M2L runs in the harmonic basis (DAFMM_OPT_M2L_HARMONIC, default):
         # rows and columns of the contraction are the (p + 1)^2 free coefficients
-        nk = (p + 1) ** 2 if f16 else nc
+        nk = (p + 1) ** 2  # both operand forms run in the harmonic basis by default
         npt = (nk + 15) // 16 * 16
         if npt > 192:
             npt = 2 * (((npt // 2) + 15) // 16 * 16)
@@ -508,11 +508,11 @@ def run_ours(args, rank, world):
                                ("2 ncoef^2 flops per well-separated pair: %.3e flops (the dense M2L of Eq. 5; "
                                 "computed in the harmonic basis, 2 (p+1)^4 = %.3e flops, plus the expansion of "
                                 "the locals, inside the timed phase)" % (flops, 2.0 * (p + 1) ** 4 * pairs_all)
-                                if f16 else "2 ncoef^2 flops per well-separated pair: %.3e flops" % flops),
+                                if bound == "tensor" else "2 ncoef^2 flops per well-separated pair: %.3e flops" % flops),
                 "achieved_harmonic": (round(2.0 * (p + 1) ** 4 * pairs_all / m2l_s / 1e12, 3)
-                                      if f16 and bound == "tensor" else None),
+                                      if bound == "tensor" else None),
                 "frac_harmonic": (round(2.0 * (p + 1) ** 4 * pairs_all / m2l_s / 1e12 / peak, 4)
-                                  if f16 and bound == "tensor" else None),
+                                  if bound == "tensor" else None),
                 "executed_tflops": None if executed is None else round(executed, 3),
                 "executed_frac": None if executed is None else round(executed / peak, 4),
                 "peak_source": peak_note}

@@ -211,8 +211,8 @@ int dafmm_last_phase_ms(dafmm_ctx* ctx, double* out10);
  *   instead of 82k at p = 10; -1 (default) = 1 from p = 4, else 0.  Uniform and adaptive trees
  *   (the V-list pairs of a level have the same 316 box displacements). */
 #define DAFMM_OPT_M2L_ROTATION 5
-/*   DAFMM_OPT_M2L_HARMONIC: the FP32 mode's F16 M2L (uniform and adaptive trees, forests):
- *   1 (default) = in the harmonic basis.  The homogeneous parts of the multipole expansions
+/*   DAFMM_OPT_M2L_HARMONIC: the tensor-core M2L of the FP32 (F16 operands) and MIXED (TF32)
+ *   modes, uniform and adaptive trees and forests: 1 (default) = in the harmonic basis.  The homogeneous parts of the multipole expansions
  *   (Eq. 2: the Legendre generating function) and of the local expansions (Taylor polynomials
  *   of a harmonic potential) are harmonic polynomials, each fixed by its coefficients of z
  *   exponent <= 1; the M2L contracts those (p + 1)^2 coefficients against K^_v restricted and

@@ -387,6 +387,9 @@ void free_order(dafmm_ctx* c, OrderData& od) {
         dev_free(c, od.k16h_inv_c, (size_t)kNumKeys * sizeof(float));
         dev_free(c, od.hx_step, std::max<size_t>(nstep, 1) * sizeof(int4));
         dev_free(c, od.hx_w, std::max<size_t>(nstep, 1) * sizeof(float2));
+        const size_t ctf = (size_t)kNumKeys * tc_npt_h(od.p) * harm_row(od.p) * sizeof(float);
+        dev_free(c, od.Khih, ctf);
+        dev_free(c, od.Kloh, ctf);
     }
     if (od.Khi) {
         const size_t cs = (size_t)kNumKeys * tc_npt(od.p) * od.ncp;
@@ -447,7 +450,8 @@ int ensure_k16(dafmm_ctx* c, int p, cudaStream_t s) {
 // The M2L in the harmonic basis (made once per order, on first use): the steps that restore the
 // coefficients of z exponent >= 2 from the free ones (Laplace's equation, in order of increasing
 // z exponent), the expansion matrix X [nc][nh] they define (FP64, for the matrices only), and
-// the F16 splits of the matrices restricted to the free output coefficients and composed with X
+// the F16 and TF32 splits of the matrices restricted to the free output coefficients and
+// composed with X
 int ensure_k16h(dafmm_ctx* c, int p, cudaStream_t s) {
     OrderData& od = c->ord[p];
     if (od.Kh16h) return DAFMM_OK;
@@ -486,7 +490,8 @@ int ensure_k16h(dafmm_ctx* c, int p, cudaStream_t s) {
     const size_t xb = (size_t)nc * nh * sizeof(double), khb = (size_t)kNumKeys * nh * nhp * sizeof(double);
     int rc;
     void *hi = nullptr, *lo = nullptr, *xd = nullptr, *khd = nullptr;
-    float *ir = nullptr, *icv = nullptr, *scratch = nullptr;
+    float *ir = nullptr, *icv = nullptr, *scratch = nullptr, *thi = nullptr, *tlo = nullptr;
+    const size_t ctf = (size_t)kNumKeys * npt * nhp * sizeof(float);
     int4* stp = nullptr;
     float2* wd = nullptr;
     auto release = [&]() {
@@ -495,6 +500,7 @@ int ensure_k16h(dafmm_ctx* c, int p, cudaStream_t s) {
         dev_free(c, icv, icv ? (size_t)kNumKeys * sizeof(float) : 0);
         dev_free(c, stp, stp ? nstep * sizeof(int4) : 0);
         dev_free(c, wd, wd ? nstep * sizeof(float2) : 0);
+        dev_free(c, thi, thi ? ctf : 0); dev_free(c, tlo, tlo ? ctf : 0);
     };
     auto release_scratch = [&]() {
         dev_free(c, xd, xd ? xb : 0);
@@ -507,6 +513,8 @@ int ensure_k16h(dafmm_ctx* c, int p, cudaStream_t s) {
         (rc = dev_alloc(c, (void**)&icv, (size_t)kNumKeys * sizeof(float), "M2L matrix factors")) ||
         (rc = dev_alloc(c, (void**)&stp, nstep * sizeof(int4), "harmonic expansion")) ||
         (rc = dev_alloc(c, (void**)&wd, nstep * sizeof(float2), "harmonic expansion")) ||
+        (rc = dev_alloc(c, (void**)&thi, ctf, "M2L matrices (harmonic, TF32 split)")) ||
+        (rc = dev_alloc(c, (void**)&tlo, ctf, "M2L matrices (harmonic, TF32 split)")) ||
         (rc = dev_alloc(c, &xd, xb, "harmonic expansion (scratch)")) ||
         (rc = dev_alloc(c, &khd, khb, "M2L matrices (harmonic, scratch)")) ||
         (rc = dev_alloc(c, (void**)&scratch, ((size_t)npt + kNumKeys) * sizeof(float), "M2L matrix factors"))) {
@@ -521,7 +529,7 @@ int ensure_k16h(dafmm_ctx* c, int p, cudaStream_t s) {
         e = cudaMemcpyAsync(wd, w.data(), w.size() * sizeof(float2), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess)
         e = tc_prepare_k16h(od.K64, kNumKeys, p, static_cast<const double*>(xd), static_cast<double*>(khd), hi, lo, ir,
-                            icv, scratch, s);
+                            icv, scratch, thi, tlo, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // the host vectors die with this call
     release_scratch();
     if (e != cudaSuccess) {
@@ -534,6 +542,8 @@ int ensure_k16h(dafmm_ctx* c, int p, cudaStream_t s) {
     od.k16h_inv_c = icv;
     od.hx_step = stp;
     od.hx_w = wd;
+    od.Khih = thi;
+    od.Kloh = tlo;
     for (int k = 0; k < kMaxOrder + 3; ++k) od.hx_cst[k] = cst[k];
     return DAFMM_OK;
 }
@@ -707,19 +717,28 @@ int ensure_expansions(dafmm_tree* t, int p, cudaStream_t s) {
 }
 
 // the F16 multipole splits of every level of a uniform tree (made on first use)
-int ensure_f16_levels(dafmm_tree* t, bool harm, cudaStream_t s) {
+int ensure_f16_levels(dafmm_tree* t, cudaStream_t s) {
     (void)s;
     dafmm_ctx* c = t->ctx;
     Expansions& e = t->ex;
     for (int l = 2; l <= e.depth; ++l) {
+        if (e.Mh16[l]) continue;
+        const size_t c16 = level_boxes(l) * (size_t)tc_rowlen16(e.p) * 2;
         int rc;
-        if (!e.Mh16[l]) {
-            const size_t c16 = level_boxes(l) * (size_t)tc_rowlen16(e.p) * 2;
-            if ((rc = dev_alloc(c, &e.Mh16[l], c16, "multipoles (F16 split)"))) return rc;
-            if ((rc = dev_alloc(c, &e.Ml16[l], c16, "multipoles (F16 split)"))) return rc;
-            if ((rc = dev_alloc(c, (void**)&e.Minv[l], level_boxes(l) * sizeof(float), "multipole factors"))) return rc;
-        }
-        if (harm && !e.Lh[l] &&
+        if ((rc = dev_alloc(c, &e.Mh16[l], c16, "multipoles (F16 split)"))) return rc;
+        if ((rc = dev_alloc(c, &e.Ml16[l], c16, "multipoles (F16 split)"))) return rc;
+        if ((rc = dev_alloc(c, (void**)&e.Minv[l], level_boxes(l) * sizeof(float), "multipole factors"))) return rc;
+    }
+    return DAFMM_OK;
+}
+
+// the harmonic-basis M2L's output rows per level (FP32, harm_row floats per box)
+int ensure_lh_levels(dafmm_tree* t) {
+    dafmm_ctx* c = t->ctx;
+    Expansions& e = t->ex;
+    for (int l = 2; l <= e.depth; ++l) {
+        int rc;
+        if (!e.Lh[l] &&
             (rc = dev_alloc(c, (void**)&e.Lh[l], level_boxes(l) * harm_row(e.p) * sizeof(float), "locals (harmonic)")))
             return rc;
     }
@@ -830,6 +849,9 @@ int grow_boxes(dafmm_ctx* c, dafmm_tree* t, int need, int used, cudaStream_t s) 
 
 void free_adaptive(dafmm_ctx* c, dafmm_tree* t) {
     free_box_arrays(c, t);
+    dev_free(c, t->aLh, t->aLh_bytes);
+    t->aLh = nullptr;
+    t->aLh_bytes = 0;
     const size_t nb1 = (size_t)t->nbox + 1;
     dev_free(c, t->a_geom, (size_t)t->nbox * sizeof(double4));
     dev_free(c, t->a_xq0, (size_t)t->nbox * sizeof(int));
@@ -1151,24 +1173,37 @@ int eval_adaptive(dafmm_tree* t, int order, int precision, double* dphi, double*
         const bool tc = precision != DAFMM_FP64 && c->m2l_kernel == 0 && c->tc_capable && order >= 2 &&
                         (precision != DAFMM_FP32 || (c->tc_mask & 1));
         const bool f16 = tc && precision == DAFMM_FP32 && c->m2l_f16;
-        // the F16 M2L in the harmonic basis: (p + 1)^2 free coefficients per row
-        const bool harm = f16 && c->m2l_harm;
+        // the tensor-core M2L in the harmonic basis: (p + 1)^2 free coefficients per row (F16
+        // operands in the FP32 mode, TF32 in MIXED); its output rows go to t->aLh
+        const bool harm = tc && c->m2l_harm;
         // F16 split: hi and lo rows of rowlen16 halves (harmonic: rowlen16h), stored in the FP32
-        // multipole buffer (8 ncp bytes per box), followed in the harmonic basis by the M2L's FP32
-        // rows of free coefficients (harm_row floats per box; rowlen16h + harm_row <= 2 ncp)
+        // multipole buffer; TF32 split: hi and lo rows of ncp floats (harmonic: harm_row) there
         const size_t c16 = (size_t)t->nbox * (harm ? tc_rowlen16h(order) : tc_rowlen16(order));
+        const size_t ctf = harm ? (size_t)t->nbox * harm_row(order) : cnt;
         void* h16 = t->aMf;
         void* l16 = reinterpret_cast<__half*>(t->aMf) + c16;
-        float* lh = reinterpret_cast<float*>(reinterpret_cast<__half*>(t->aMf) + 2 * c16);
+        if (harm) {
+            const size_t need = (size_t)t->nbox * harm_row(order) * sizeof(float);
+            if (t->aLh_bytes != need) {
+                dev_free(c, t->aLh, t->aLh_bytes);
+                t->aLh = nullptr;
+                t->aLh_bytes = 0;
+                if ((rc = dev_alloc(c, (void**)&t->aLh, need, "locals (harmonic)"))) return rc;
+                t->aLh_bytes = need;
+            }
+            if ((rc = ensure_k16h(c, order, s))) return rc;
+        }
+        float* lh = t->aLh;
         if (f16) {
-            if ((rc = harm ? ensure_k16h(c, order, s) : ensure_k16(c, order, s))) return rc;
+            if (!harm && (rc = ensure_k16(c, order, s))) return rc;
             const void* src = t->aM;
             const int nrows = t->nbox;
             float* inv = t->aMinv;
             CK(c, tc_split_f16_multi(1, &src, &nrows, &h16, &l16, &inv, order, s, false, harm), "split");
             ++launches;
         } else if (tc) {
-            CK(c, tc_split_tf32(t->aM, t->aMf, t->aMf + cnt, cnt, s), "split");
+            if (harm) CK(c, tc_split_tf32_harm(t->aM, t->nbox, order, t->aMf, t->aMf + ctf, s), "split");
+            else CK(c, tc_split_tf32(t->aM, t->aMf, t->aMf + cnt, cnt, s), "split");
             ++launches;
         } else if (precision != DAFMM_FP64) {
             k_to_float<<<(unsigned)std::min<size_t>((cnt + 255) / 256, 152 * 16), 256, 0, s>>>(t->aM, t->aMf, cnt);
@@ -1184,10 +1219,10 @@ int eval_adaptive(dafmm_tree* t, int order, int precision, double* dphi, double*
             a.f16 = f16;
             a.harm = harm;
             a.a_hi = f16 ? h16 : (const void*)t->aMf;
-            a.a_lo = f16 ? l16 : (const void*)(t->aMf + cnt);
+            a.a_lo = f16 ? l16 : (const void*)(t->aMf + ctf);
             a.a_inv = t->aMinv;
-            a.b_hi = harm ? od.Kh16h : f16 ? od.Kh16 : (const void*)od.Khi;
-            a.b_lo = harm ? od.Kl16h : f16 ? od.Kl16 : (const void*)od.Klo;
+            a.b_hi = f16 ? (harm ? od.Kh16h : od.Kh16) : (const void*)(harm ? od.Khih : od.Khi);
+            a.b_lo = f16 ? (harm ? od.Kl16h : od.Kl16) : (const void*)(harm ? od.Kloh : od.Klo);
             a.inv_r = harm ? od.k16h_inv_r : od.k16_inv_r;
             a.inv_c = harm ? od.k16h_inv_c : od.k16_inv_c;
             a.nkey = kNumKeys;
@@ -1731,11 +1766,13 @@ int dafmm_eval(dafmm_tree* t, int order, double theta, int precision, double* ph
         const int prec_m = precision | (f32_mult ? kRowsF32 : 0);
         Expansions& ex = t->ex;
         ex.M_f32 = f32_mult;
-        // the F16 M2L in the harmonic basis: (p + 1)^2 free coefficients per row instead of ncoef
-        const bool harm = f16_m2l && c->m2l_harm;
-        if (f16_m2l && ((rc = ensure_f16_levels(t, harm, s)) ||
-                        (rc = harm ? ensure_k16h(c, order, s) : ensure_k16(c, order, s))))
-            return rc;
+        // the tensor-core M2L in the harmonic basis: (p + 1)^2 free coefficients per row instead
+        // of ncoef (F16 operands in the FP32 mode, TF32 in MIXED)
+        const bool harm = tc_m2l && c->m2l_harm && (f16_m2l || !tc_m2m);  // (the tensor-core M2M
+                                                                           // writes full TF32 rows)
+        if (f16_m2l && (rc = ensure_f16_levels(t, s))) return rc;
+        if (harm && ((rc = ensure_lh_levels(t)) || (rc = ensure_k16h(c, order, s)))) return rc;
+        if (f16_m2l && !harm && (rc = ensure_k16(c, order, s))) return rc;
         auto tc_args = [&](int mode, int lmin, int lmax) {
             TCArgs a;
             memset(&a, 0, sizeof(a));
@@ -1790,7 +1827,9 @@ int dafmm_eval(dafmm_tree* t, int order, double theta, int precision, double* ph
         } else if (precision != DAFMM_FP64 && !fff && !(tc_m2m && tc_m2l))
             for (int l = 2; l <= L; ++l) {
                 const size_t cnt = level_boxes(l) * od.ncp;
-                if (tc_m2l) {
+                if (harm) {
+                    CK(c, tc_split_tf32_harm(ex.M[l], level_boxes(l), order, ex.Mhi[l], ex.Mlo[l], s), "split");
+                } else if (tc_m2l) {
                     CK(c, tc_split_tf32(ex.M[l], ex.Mhi[l], ex.Mlo[l], cnt, s), "split");
                 } else {
                     k_to_float<<<(unsigned)std::min<size_t>((cnt + 255) / 256, 152 * 16), 256, 0, s>>>(ex.M[l], ex.Mf[l], cnt);
@@ -1819,8 +1858,8 @@ int dafmm_eval(dafmm_tree* t, int order, double theta, int precision, double* ph
                 }
                 a.scale[l] = 1.0 / ldexp(t->dom[3], -l);
             }
-            a.b_hi = harm ? od.Kh16h : f16_m2l ? od.Kh16 : (const void*)od.Khi;
-            a.b_lo = harm ? od.Kl16h : f16_m2l ? od.Kl16 : (const void*)od.Klo;
+            a.b_hi = f16_m2l ? (harm ? od.Kh16h : od.Kh16) : (const void*)(harm ? od.Khih : od.Khi);
+            a.b_lo = f16_m2l ? (harm ? od.Kl16h : od.Kl16) : (const void*)(harm ? od.Kloh : od.Klo);
             a.inv_r = harm ? od.k16h_inv_r : od.k16_inv_r;
             a.inv_c = harm ? od.k16h_inv_c : od.k16_inv_c;
             a.nkey = kNumKeys;

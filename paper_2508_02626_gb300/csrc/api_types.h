@@ -97,6 +97,8 @@ struct dafmm_tree {
     double *aM = nullptr, *aL = nullptr;
     float* aMf = nullptr;
     float* aMinv = nullptr;         // per box: factor of the F16 multipole split
+    float* aLh = nullptr;           // harmonic-basis M2L output rows (FP32, free coefficients)
+    size_t aLh_bytes = 0;
 };
 
 

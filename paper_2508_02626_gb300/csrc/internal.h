@@ -91,6 +91,7 @@ struct OrderData {
     // (columns), and the expansion's steps (harm_expand_launch)
     void* Kh16h = nullptr; void* Kl16h = nullptr;
     float* k16h_inv_r = nullptr; float* k16h_inv_c = nullptr;
+    float* Khih = nullptr; float* Kloh = nullptr;  // TF32 parts [343][npt_h][harm_row] (MIXED)
     int4* hx_step = nullptr;      // [ncoef - nharm]: (i, i1, i2, 0), in order of increasing c
     float2* hx_w = nullptr;       // their weights (w1, w2): a[i] = w1 a[i1] + w2 a[i2]
     int hx_cst[kMaxOrder + 3] = {};  // steps of z exponent c: [hx_cst[c], hx_cst[c + 1])

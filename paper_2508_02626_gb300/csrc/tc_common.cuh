@@ -164,6 +164,53 @@ __device__ __forceinline__ void tmem_ld16w(uint32_t taddr, uint32_t (&r)[16]) {
         : "memory");
 }
 
+// 32 lanes x 32 columns, load and wait in one statement (half the round trips of two x16 loads)
+__device__ __forceinline__ void tmem_ld32w(uint32_t taddr, uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {"
+        "%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, "
+        "[%32];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr)
+        : "memory");
+}
+
+// one term's accumulator (NP columns from tb) folded into the row sums S: S += acc (TF32), or
+// S += acc * f (F16: f undoes the term's scales).  WIDE: 32 columns per load and wait instead of
+// 16 -- half the round trips, 16 more registers (taken where the accumulator is narrow, in the
+// harmonic basis)
+template <int NP, bool H, bool WIDE>
+__device__ __forceinline__ void fold_term(uint32_t tb, float f, float (&S)[NP]) {
+#pragma unroll
+    for (int c0 = 0; c0 < NP; c0 += (WIDE ? 32 : 16)) {
+        if (WIDE && c0 + 32 <= NP) {
+            uint32_t r[32];
+            tmem_ld32w(tb + c0, r);
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+                if constexpr (H) S[c0 + j] = fmaf(__uint_as_float(r[j]), f, S[c0 + j]);
+                else S[c0 + j] += __uint_as_float(r[j]);
+            }
+        } else {
+#pragma unroll
+            for (int c1 = c0; c1 < c0 + (WIDE ? 32 : 16) && c1 < NP; c1 += 16) {
+                uint32_t r[16];
+                tmem_ld16w(tb + c1, r);
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    if constexpr (H) S[c1 + j] = fmaf(__uint_as_float(r[j]), f, S[c1 + j]);
+                    else S[c1 + j] += __uint_as_float(r[j]);
+                }
+            }
+        }
+    }
+}
+
 // 32 lanes x 16 columns from registers into TMEM (the caller waits with tmem_wait_st)
 __device__ __forceinline__ void tmem_st16(uint32_t taddr, const float* v) {
     asm volatile(

@@ -323,16 +323,7 @@ __global__ void __launch_bounds__(kTcgThreads, 1) k_tcg(const __grid_constant__ 
                 accf_ph[buf] ^= 1u;
                 fence_after_sync();
                 const uint32_t tb = tmem_base + ((uint32_t)(32 * q) << 16) + (uint32_t)(buf * C::NP);
-#pragma unroll
-                for (int c0 = 0; c0 < C::NP; c0 += 16) {
-                    uint32_t r[16];
-                    tmem_ld16w(tb + c0, r);
-#pragma unroll
-                    for (int j = 0; j < 16; ++j) {
-                        if constexpr (H) S[c0 + j] = fmaf(__uint_as_float(r[j]), f, S[c0 + j]);
-                        else S[c0 + j] += __uint_as_float(r[j]);
-                    }
-                }
+                fold_term<C::NP, H, R>(tb, f, S);
                 fence_before_sync();
                 mbar_arrive(smem_u32(&acc_empty[buf]));
                 ++uses;
@@ -426,7 +417,7 @@ static cudaError_t launch_tcg(const TCGArgs& a, cudaStream_t s) {
 
 template <int P>
 static cudaError_t launch_tcg_any(const TCGArgs& a, cudaStream_t s) {
-    if (a.harm) return a.f16 ? launch_tcg<P, true, true>(a, s) : cudaErrorInvalidValue;
+    if (a.harm) return a.f16 ? launch_tcg<P, true, true>(a, s) : launch_tcg<P, false, true>(a, s);
     return a.f16 ? launch_tcg<P, true>(a, s) : launch_tcg<P, false>(a, s);
 }
 

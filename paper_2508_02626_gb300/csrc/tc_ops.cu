@@ -249,16 +249,7 @@ __global__ void __launch_bounds__(192, 1) k_tc(const __grid_constant__ TCParams 
                 accf_ph[buf] ^= 1u;
                 fence_after_sync();
                 const uint32_t tb = tmem_base + ((uint32_t)(32 * q) << 16) + (uint32_t)(buf * C::NP);
-#pragma unroll
-                for (int c0 = 0; c0 < C::NP; c0 += 16) {
-                    uint32_t r[16];
-                    tmem_ld16w(tb + c0, r);
-#pragma unroll
-                    for (int j = 0; j < 16; ++j) {
-                        if constexpr (H) S[c0 + j] = fmaf(__uint_as_float(r[j]), f, S[c0 + j]);
-                        else S[c0 + j] += __uint_as_float(r[j]);
-                    }
-                }
+                fold_term<C::NP, H, R>(tb, f, S);
                 ++uses;
                 have = tm.next_valid();
                 if (have) {
@@ -306,6 +297,21 @@ __global__ void __launch_bounds__(192, 1) k_tc(const __grid_constant__ TCParams 
 __global__ void k_split_tf32(const double* __restrict__ src, float* __restrict__ hi, float* __restrict__ lo, size_t n) {
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
         const double x = src[i];
+        const float h = to_tf32((float)x);
+        hi[i] = h;
+        lo[i] = to_tf32((float)(x - (double)h));
+    }
+}
+
+// the free coefficients (harm_full_index) of FP64 rows [nrows][ncp] into TF32 parts, rows of
+// nhp values (zeros past nh)
+__global__ void k_split_tf32_harm(const double* __restrict__ src, size_t nrows, int ncp, int nh, int nhp,
+                                  float* __restrict__ hi, float* __restrict__ lo) {
+    const size_t n = nrows * nhp;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const size_t row = i / nhp;
+        const int k = (int)(i % nhp);
+        const double x = k < nh ? src[row * ncp + harm_full_index(k)] : 0.0;
         const float h = to_tf32((float)x);
         hi[i] = h;
         lo[i] = to_tf32((float)(x - (double)h));
@@ -593,7 +599,7 @@ cudaError_t tc_prepare_k16(const double* K, int nkey, int p, void* hi, void* lo,
 }
 
 cudaError_t tc_prepare_k16h(const double* K, int nkey, int p, const double* X, double* Kh, void* hi, void* lo,
-                            float* inv_r, float* inv_c, float* scratch, cudaStream_t s) {
+                            float* inv_r, float* inv_c, float* scratch, float* thi, float* tlo, cudaStream_t s) {
     const int nc = ncoef_of(p), ncp = ncp_of(p), nh = nharm_of(p), nhp = (nh + 7) / 8 * 8;
     const int npt = tc_npt_h(p), rowlen = tc_rowlen16h(p);
     float* er = scratch;        // npt row exponents
@@ -603,6 +609,7 @@ cudaError_t tc_prepare_k16h(const double* K, int nkey, int p, const double* X, d
     tc::k_k16_keyexp<<<nkey, 256, 0, s>>>(Kh, nh, nhp, er, ec);
     tc::k_k16_split<<<152 * 16, 256, 0, s>>>(Kh, nkey, nh, nhp, npt, rowlen, er, ec, static_cast<__half*>(hi),
                                               static_cast<__half*>(lo), inv_r, inv_c);
+    tc::k_split_rows<<<152 * 16, 256, 0, s>>>(Kh, nkey, nh, nhp, npt, thi, tlo);
     return cudaGetLastError();
 }
 
@@ -633,6 +640,14 @@ cudaError_t tc_split_tf32(const double* src, float* hi, float* lo, size_t n, cud
     if (n == 0) return cudaSuccess;
     unsigned blocks = (unsigned)std::min<size_t>((n + 255) / 256, 152 * 16);
     tc::k_split_tf32<<<blocks, 256, 0, s>>>(src, hi, lo, n);
+    return cudaGetLastError();
+}
+
+cudaError_t tc_split_tf32_harm(const double* src, size_t nrows, int p, float* hi, float* lo, cudaStream_t s) {
+    if (nrows == 0) return cudaSuccess;
+    const int nh = nharm_of(p), nhp = harm_row(p);
+    const unsigned blocks = (unsigned)std::min<size_t>((nrows * nhp + 255) / 256, 152 * 16);
+    tc::k_split_tf32_harm<<<blocks, 256, 0, s>>>(src, nrows, ncp_of(p), nh, nhp, hi, lo);
     return cudaGetLastError();
 }
 
@@ -719,7 +734,8 @@ static cudaError_t launch_tc_any(const TCArgs& a, cudaStream_t s) {
         if (a.mode != kTcM2L) return cudaErrorInvalidValue;
         return a.harm ? launch_tc<P, true, true>(a, s) : launch_tc<P, true, false>(a, s);
     }
-    return a.harm ? cudaErrorInvalidValue : launch_tc<P, false>(a, s);
+    if (a.harm) return a.mode == kTcM2L ? launch_tc<P, false, true>(a, s) : cudaErrorInvalidValue;
+    return launch_tc<P, false>(a, s);
 }
 
 cudaError_t tc_launch(int p, const TCArgs& a, cudaStream_t s) {

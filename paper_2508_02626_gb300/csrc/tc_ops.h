@@ -45,7 +45,7 @@ struct TCArgs {
     int mode;
     int lmin, lmax;
     bool f16;                                    // F16 split operands (M2L only), else TF32
-    bool harm;                                   // (F16 M2L) the harmonic basis: A rows, matrices
+    bool harm;                                   // (M2L) the harmonic basis: A rows, matrices
                                                  // and out rows hold the free coefficients only
     const void* a_hi[kMaxUniformDepth + 1];      // per level, [8^l][rowlen] split parts of the A operand
     const void* a_lo[kMaxUniformDepth + 1];
@@ -101,7 +101,7 @@ struct TCGParams {
 
 struct TCGArgs {
     bool f16;
-    bool harm;                // (F16) the harmonic basis: A rows and matrices hold the free
+    bool harm;                // the harmonic basis: A rows and matrices hold the free
                               // coefficients; out receives FP32 rows of them (harm_row(p) floats)
     const void* a_hi;
     const void* a_lo;
@@ -145,11 +145,13 @@ cudaError_t tc_prepare_k16(const double* K, int nkey, int p, void* hi, void* lo,
 // of its matrix tables, and the tables: Kh = K restricted to the free output coefficients and
 // composed with X [nc][nh] (the expansion from the free input coefficients), as FP64 scratch
 // [nkey][nh][nhp = nh rounded up to 8], then split as tc_prepare_k16 does (scratch: npt + nkey
-// floats).
+// floats); thi / tlo receive the TF32 parts of Kh as [nkey][npt][nhp] (the MIXED mode's form).
 int tc_npt_h(int p);
 int tc_rowlen16h(int p);
 cudaError_t tc_prepare_k16h(const double* K, int nkey, int p, const double* X, double* Kh, void* hi, void* lo,
-                            float* inv_r, float* inv_c, float* scratch, cudaStream_t s);
+                            float* inv_r, float* inv_c, float* scratch, float* thi, float* tlo, cudaStream_t s);
+// TF32 parts of the free coefficients of FP64 rows [nrows][ncp]: hi, lo [nrows][harm_row(p)]
+cudaError_t tc_split_tf32_harm(const double* src, size_t nrows, int p, float* hi, float* lo, cudaStream_t s);
 // rows of free coefficients (FP32, nhp per row) of up to kTcMaxLevels arrays -> full rows (FP32
 // or FP64, ncp per row) by Laplace's equation: steps (i, i1, i2) with weights (w1, w2), those of
 // z exponent c at [cst[c], cst[c + 1]); hi / lo (optional, per array or null) receive the TF32

@@ -224,20 +224,21 @@ def test_gathered_m2l_operand_splits(ctx, p):
 
 @pytest.mark.parametrize("p", [2, 4, 6, 8, 10])
 def test_gathered_m2l_harmonic(ctx, p):
-    """The gathered F16 M2L (FP32 mode) in the harmonic basis (the default: the (p + 1)^2 free
-    coefficients gathered and contracted, the others restored by Laplace's equation) and in the
-    full basis, on a clustered tree with levels 2 to ~8: both within the FP32 bound of the
-    oracle and of each other."""
+    """The gathered M2L in the harmonic basis (the default: the (p + 1)^2 free coefficients
+    gathered and contracted, the others restored by Laplace's equation) and in the full basis,
+    FP32 mode (F16 operands) and MIXED (TF32 operands), on a clustered tree with levels 2 to ~8:
+    both within the mode's bound of the oracle and of each other."""
     x, q = W.clustered(12000, seed=650 + p, charges="signed")
     dom = O.bounding_cube(x)
     ref_phi, ref_E = O.fmm(x, q, dom, p, max_leaf=20, max_depth=MAX_DEPTH)
-    out = {}
-    for harm in (1, 0):
-        B.dafmm_set_option(ctx.h, B.DAFMM_OPT_M2L_HARMONIC, harm)
-        try:
-            out[harm] = gpu_eval(ctx, x, q, dom, 20, p, "fp32")
-        finally:
-            B.dafmm_set_option(ctx.h, B.DAFMM_OPT_M2L_HARMONIC, 1)
-        assert rel(out[harm][0], ref_phi) <= TOL["fp32"], (harm, rel(out[harm][0], ref_phi))
-        assert rel(out[harm][1], ref_E) <= TOL_E["fp32"], (harm, rel(out[harm][1], ref_E))
-    assert rel(out[1][0], out[0][0]) <= TOL["fp32"]
+    for prec in ("fp32", "mixed"):
+        out = {}
+        for harm in (1, 0):
+            B.dafmm_set_option(ctx.h, B.DAFMM_OPT_M2L_HARMONIC, harm)
+            try:
+                out[harm] = gpu_eval(ctx, x, q, dom, 20, p, prec)
+            finally:
+                B.dafmm_set_option(ctx.h, B.DAFMM_OPT_M2L_HARMONIC, 1)
+            assert rel(out[harm][0], ref_phi) <= TOL[prec], (prec, harm, rel(out[harm][0], ref_phi))
+            assert rel(out[harm][1], ref_E) <= TOL_E[prec], (prec, harm, rel(out[harm][1], ref_E))
+        assert rel(out[1][0], out[0][0]) <= TOL[prec]

@@ -253,23 +253,25 @@ def test_m2l_operand_splits(ctx, p):
 
 @pytest.mark.parametrize("p", [2, 3, 4, 6, 8, 9, 10])
 def test_harmonic_m2l(ctx, p):
-    """FP32 mode with the F16 M2L in the harmonic basis (the default: the (p + 1)^2 free
-    coefficients contracted, the others restored by Laplace's equation) and in the full basis:
-    both within the FP32 bound of the oracle, within it of each other; depth 5 at p = 2 and
-    depth 4 otherwise, so that every level and tile shape of the kernel runs, and with the
-    tensor-core L2L reading level 2's expanded locals."""
+    """The tensor-core M2L in the harmonic basis (the default: the (p + 1)^2 free coefficients
+    contracted, the others restored by Laplace's equation) and in the full basis, FP32 mode (F16
+    operands) and MIXED (TF32 operands): both within the mode's bound of the oracle and within it
+    of each other; depth 5 at p = 2 and depth 4 otherwise, so that every level and tile shape of
+    the kernel runs, and in the FP32 mode with the tensor-core L2L reading level 2's expanded
+    locals."""
     depth = 5 if p == 2 else 4
     x, q = W.uniform(30000, seed=800 + p)
     dom = W.UNIT_CUBE
     ref_phi, ref_E = O.fmm(x, q, dom, p, uniform_depth=depth)
-    out = {}
-    for harm in (1, 0):
-        B.dafmm_set_option(ctx.h, B.DAFMM_OPT_M2L_HARMONIC, harm)
-        try:
-            out[harm] = gpu_eval(ctx, x, q, dom, depth, p, "fp32")
-        finally:
-            B.dafmm_set_option(ctx.h, B.DAFMM_OPT_M2L_HARMONIC, 1)
-        assert rel(out[harm][0], ref_phi) <= TOL["fp32"], (harm, rel(out[harm][0], ref_phi))
-        assert rel(out[harm][1], ref_E) <= TOL_E["fp32"], (harm, rel(out[harm][1], ref_E))
-    assert rel(out[1][0], out[0][0]) <= TOL["fp32"]
-    assert rel(out[1][1], out[0][1]) <= TOL_E["fp32"]
+    for prec in ("fp32", "mixed"):
+        out = {}
+        for harm in (1, 0):
+            B.dafmm_set_option(ctx.h, B.DAFMM_OPT_M2L_HARMONIC, harm)
+            try:
+                out[harm] = gpu_eval(ctx, x, q, dom, depth, p, prec)
+            finally:
+                B.dafmm_set_option(ctx.h, B.DAFMM_OPT_M2L_HARMONIC, 1)
+            assert rel(out[harm][0], ref_phi) <= TOL[prec], (prec, harm, rel(out[harm][0], ref_phi))
+            assert rel(out[harm][1], ref_E) <= TOL_E[prec], (prec, harm, rel(out[harm][1], ref_E))
+        assert rel(out[1][0], out[0][0]) <= TOL[prec]
+        assert rel(out[1][1], out[0][1]) <= TOL_E[prec]

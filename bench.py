@@ -60,17 +60,21 @@ def fp32_fma_peak_tflops(sm_mhz):
     return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
 
 
-def rotation_madds_per_pair(p):
+def rotation_madds_per_pair(p, harm=True):
     """Multiply-adds per well-separated pair of the M2L by rotation (Sec. 3.4) at order p: two
     substitutions about x (output (a, b, c) takes b + c + 1 terms), two about z (a + b + 1
     terms) and the axial Eq. 5 matrix (column (a, b, c) reaches row (a', b', c') when b' >= b,
-    c' >= c and both differences are even)."""
+    c' >= c and both differences are even).  harm: the harmonic form (DAFMM_OPT_M2L_HARMONIC,
+    default) computes only the outputs of z exponent <= 1 and restores the others before the
+    last x-step, two multiply-adds each."""
     C = [(a, b, n - a - b) for n in range(p + 1) for a in range(n, -1, -1) for b in range(n - a, -1, -1)]
-    sx = sum(b + c + 1 for a, b, c in C)
-    sz = sum(a + b + 1 for a, b, c in C)
-    ax = sum(1 for (_, b2, c2) in C for (_, b, c) in C
+    out = [k for k in C if not harm or k[2] <= 1]
+    sx = sum(b + c + 1 for a, b, c in out)
+    sz = sum(a + b + 1 for a, b, c in out)
+    ax = sum(1 for (_, b2, c2) in out for (_, b, c) in C
              if b2 >= b and c2 >= c and (b2 - b) % 2 == 0 and (c2 - c) % 2 == 0)
-    return 2 * sx + 2 * sz + ax
+    restored = 2 * sum(1 for k in C if k[2] > 1) if harm else 0
+    return 2 * sx + 2 * sz + ax + restored
 
 
 def near_field_interactions(x, dom, depth):
@@ -503,7 +507,8 @@ def run_ours(args, rank, world):
                            "M2L contraction (tcgen05 kind::tf32 k_tc, all levels, one launch)") if bound == "tensor"
                 else ("M2L by rotation (k_m2l_rot, FP64 pipe, all levels)" if rot else
                       "M2L (SIMT FP64 k_m2l, all levels)"),
-                "algorithmic": ("2 x %d multiply-adds per well-separated pair (4 rotations + axial Eq. 5): %.3e flops"
+                "algorithmic": ("2 x %d multiply-adds per well-separated pair (4 rotations + axial Eq. 5, "
+                                "harmonic form: outputs of z exponent <= 1, the others restored): %.3e flops"
                                 % (rotation_madds_per_pair(p), flops)) if rot else
                                ("2 ncoef^2 flops per well-separated pair: %.3e flops (the dense M2L of Eq. 5; "
                                 "computed in the harmonic basis, 2 (p+1)^4 = %.3e flops, plus the expansion of "

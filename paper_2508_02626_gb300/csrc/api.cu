@@ -408,6 +408,12 @@ void free_order(dafmm_ctx* c, OrderData& od) {
         dev_free(c, od.rot_lx, (size_t)od.rot_len[0] * 32 * sizeof(uint2));
         dev_free(c, od.rot_lz, (size_t)od.rot_len[1] * 32 * sizeof(uint2));
         dev_free(c, od.rot_la, (size_t)od.rot_len[2] * 32 * sizeof(uint2));
+        dev_free(c, od.rot_lxh, (size_t)od.rot_lenh[0] * 32 * sizeof(uint2));
+        dev_free(c, od.rot_lzh, (size_t)od.rot_lenh[1] * 32 * sizeof(uint2));
+        dev_free(c, od.rot_lah, (size_t)od.rot_lenh[2] * 32 * sizeof(uint2));
+        const size_t nhs = std::max<size_t>((size_t)(ncoef_of(od.p) - nharm_of(od.p)), 1);
+        dev_free(c, od.hxr_step, nhs * sizeof(int4));
+        dev_free(c, od.hxr_w, nhs * sizeof(double2));
         dev_free(c, od.rot_Tf, (size_t)kNumKeys * 4 * ops->rot_tsz * sizeof(float2));
         dev_free(c, od.ax_valf, (size_t)od.n_rho * od.ax_nnz * sizeof(float2));
     }
@@ -447,6 +453,35 @@ int ensure_k16(dafmm_ctx* c, int p, cudaStream_t s) {
     return DAFMM_OK;
 }
 
+// The steps that restore an expansion's coefficients of z exponent >= 2 from its free ones by
+// Laplace's equation, in order of increasing z exponent: step (i, i1, i2, c) sets
+// a[i] = w1 a[i1] + w2 a[i2] with w1 = -(a+2)(a+1) / (c(c-1)), w2 = -(b+2)(b+1) / (c(c-1)) for
+// coefficient i = (a, b, c); those of z exponent c are [cst[c], cst[c + 1])
+static void harm_steps(int p, std::vector<int4>& step, std::vector<double2>& w, int* cst) {
+    const int nc = ncoef_of(p);
+    std::vector<int> ea(nc), eb(nc), ec(nc);
+    for (int n = 0; n <= p; ++n)
+        for (int a = n; a >= 0; --a)
+            for (int b = n - a; b >= 0; --b) {
+                const int cc = n - a - b, i = da_index(a, b, cc);
+                ea[i] = a; eb[i] = b; ec[i] = cc;
+            }
+    step.clear();
+    w.clear();
+    for (int k = 0; k < kMaxOrder + 3; ++k) cst[k] = 0;
+    for (int cz = 2; cz <= p + 1; ++cz) {
+        cst[cz] = (int)step.size();
+        for (int i = 0; i < nc; ++i) {
+            if (ec[i] != cz) continue;
+            const int a = ea[i], b = eb[i];
+            const double d = (double)cz * (cz - 1);
+            step.push_back(make_int4(i, da_index(a + 2, b, cz - 2), da_index(a, b + 2, cz - 2), cz));
+            w.push_back(make_double2(-(double)(a + 2) * (a + 1) / d, -(double)(b + 2) * (b + 1) / d));
+        }
+    }
+    cst[p + 2] = (int)step.size();
+}
+
 // The M2L in the harmonic basis (made once per order, on first use): the steps that restore the
 // coefficients of z exponent >= 2 from the free ones (Laplace's equation, in order of increasing
 // z exponent), the expansion matrix X [nc][nh] they define (FP64, for the matrices only), and
@@ -457,34 +492,19 @@ int ensure_k16h(dafmm_ctx* c, int p, cudaStream_t s) {
     if (od.Kh16h) return DAFMM_OK;
     const int nc = ncoef_of(p), nh = nharm_of(p), nhp = harm_row(p);
     const int npt = tc_npt_h(p), rowlen = tc_rowlen16h(p);
-    // exponents of every coefficient (the layout of da_index)
-    std::vector<int> ea(nc), eb(nc), ec(nc);
-    for (int n = 0; n <= p; ++n)
-        for (int a = n; a >= 0; --a)
-            for (int b = n - a; b >= 0; --b) {
-                const int cc = n - a - b, i = da_index(a, b, cc);
-                ea[i] = a; eb[i] = b; ec[i] = cc;
-            }
     std::vector<int4> step;
-    std::vector<float2> w;
+    std::vector<double2> w64;
+    int cst[kMaxOrder + 3];
+    harm_steps(p, step, w64, cst);
+    std::vector<float2> w(w64.size());
     std::vector<double> X((size_t)nc * nh, 0.0);
     for (int k = 0; k < nh; ++k) X[(size_t)harm_full_index(k) * nh + k] = 1.0;
-    int cst[kMaxOrder + 3] = {};
-    for (int cz = 2; cz <= p + 1; ++cz) {
-        cst[cz] = (int)step.size();
-        for (int i = 0; i < nc; ++i) {
-            if (ec[i] != cz) continue;
-            const int a = ea[i], b = eb[i];
-            const int i1 = da_index(a + 2, b, cz - 2), i2 = da_index(a, b + 2, cz - 2);
-            const double d = (double)cz * (cz - 1);
-            const double w1 = -(double)(a + 2) * (a + 1) / d, w2 = -(double)(b + 2) * (b + 1) / d;
-            step.push_back(make_int4(i, i1, i2, cz));
-            w.push_back(make_float2((float)w1, (float)w2));
-            for (int k = 0; k < nh; ++k)
-                X[(size_t)i * nh + k] = w1 * X[(size_t)i1 * nh + k] + w2 * X[(size_t)i2 * nh + k];
-        }
+    for (size_t q = 0; q < step.size(); ++q) {
+        const int i = step[q].x, i1 = step[q].y, i2 = step[q].z;
+        w[q] = make_float2((float)w64[q].x, (float)w64[q].y);
+        for (int k = 0; k < nh; ++k)
+            X[(size_t)i * nh + k] = w64[q].x * X[(size_t)i1 * nh + k] + w64[q].y * X[(size_t)i2 * nh + k];
     }
-    cst[p + 2] = (int)step.size();
     const size_t nstep = std::max<size_t>(step.size(), 1);
     const size_t c16 = (size_t)kNumKeys * npt * rowlen * 2;
     const size_t xb = (size_t)nc * nh * sizeof(double), khb = (size_t)kNumKeys * nh * nhp * sizeof(double);
@@ -577,6 +597,13 @@ int ensure_rotation(dafmm_ctx* c, int p, cudaStream_t s) {
     const std::vector<RotTask>& lz = rs.lz;
     const std::vector<RotTask>& la = rs.la;
     const int len_x = rs.len[0], len_z = rs.len[1], len_a = rs.len[2];
+    // the harmonic form: lists of the free outputs, and the steps restoring the others
+    const RotStructure rsh = rot_structure(p, true);
+    std::vector<int4> hstep;
+    std::vector<double2> hw;
+    int hcst[kMaxOrder + 3];
+    harm_steps(p, hstep, hw, hcst);
+    const size_t nhstep = std::max<size_t>(hstep.size(), 1);
     std::vector<double> r0s(3 * (size_t)nrho, 0.0);
     for (int r = 0; r < nrho; ++r) r0s[3 * r] = std::sqrt((double)len2[r]);
     const size_t tbytes = (size_t)kNumKeys * 4 * ops->rot_tsz * sizeof(double);
@@ -584,12 +611,19 @@ int ensure_rotation(dafmm_ctx* c, int p, cudaStream_t s) {
     double *T = nullptr, *val = nullptr, *d_r0s = nullptr, *Ks = nullptr;
     int *rho = nullptr, *rp = nullptr;
     unsigned short* cl = nullptr;
-    uint2 *dlx = nullptr, *dlz = nullptr, *dla = nullptr;
+    uint2 *dlx = nullptr, *dlz = nullptr, *dla = nullptr, *dlxh = nullptr, *dlzh = nullptr, *dlah = nullptr;
+    int4* dhs = nullptr;
+    double2* dhw = nullptr;
     int rc;
     auto release = [&]() {
         dev_free(c, dlx, lx.size() * sizeof(uint2));
         dev_free(c, dlz, lz.size() * sizeof(uint2));
         dev_free(c, dla, la.size() * sizeof(uint2));
+        dev_free(c, dlxh, dlxh ? rsh.lx.size() * sizeof(uint2) : 0);
+        dev_free(c, dlzh, dlzh ? rsh.lz.size() * sizeof(uint2) : 0);
+        dev_free(c, dlah, dlah ? rsh.la.size() * sizeof(uint2) : 0);
+        dev_free(c, dhs, dhs ? nhstep * sizeof(int4) : 0);
+        dev_free(c, dhw, dhw ? nhstep * sizeof(double2) : 0);
         dev_free(c, T, tbytes);
         dev_free(c, val, (size_t)nrho * nnz * sizeof(double));
         dev_free(c, rho, (size_t)kNumKeys * sizeof(int));
@@ -603,7 +637,12 @@ int ensure_rotation(dafmm_ctx* c, int p, cudaStream_t s) {
         (rc = dev_alloc(c, (void**)&cl, (size_t)nnz * sizeof(unsigned short), "axial M2L matrices")) ||
         (rc = dev_alloc(c, (void**)&dlx, lx.size() * sizeof(uint2), "rotation task lists")) ||
         (rc = dev_alloc(c, (void**)&dlz, lz.size() * sizeof(uint2), "rotation task lists")) ||
-        (rc = dev_alloc(c, (void**)&dla, la.size() * sizeof(uint2), "rotation task lists"))) {
+        (rc = dev_alloc(c, (void**)&dla, la.size() * sizeof(uint2), "rotation task lists")) ||
+        (rc = dev_alloc(c, (void**)&dlxh, rsh.lx.size() * sizeof(uint2), "rotation task lists")) ||
+        (rc = dev_alloc(c, (void**)&dlzh, rsh.lz.size() * sizeof(uint2), "rotation task lists")) ||
+        (rc = dev_alloc(c, (void**)&dlah, rsh.la.size() * sizeof(uint2), "rotation task lists")) ||
+        (rc = dev_alloc(c, (void**)&dhs, nhstep * sizeof(int4), "harmonic expansion")) ||
+        (rc = dev_alloc(c, (void**)&dhw, nhstep * sizeof(double2), "harmonic expansion"))) {
         release();
         return rc;
     }
@@ -617,7 +656,18 @@ int ensure_rotation(dafmm_ctx* c, int p, cudaStream_t s) {
     od.ax_nnz = nnz; od.n_rho = nrho;
     od.rot_lx = dlx; od.rot_lz = dlz; od.rot_la = dla;
     od.rot_len[0] = len_x; od.rot_len[1] = len_z; od.rot_len[2] = len_a;
+    od.rot_lxh = dlxh; od.rot_lzh = dlzh; od.rot_lah = dlah;
+    od.rot_lenh[0] = rsh.len[0]; od.rot_lenh[1] = rsh.len[1]; od.rot_lenh[2] = rsh.len[2];
+    od.hxr_step = dhs; od.hxr_w = dhw;
+    for (int k = 0; k < kMaxOrder + 3; ++k) od.hxr_cst[k] = hcst[k];
     cudaError_t e = cudaMemcpyAsync(rho, rho_of.data(), rho_of.size() * sizeof(int), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dlxh, rsh.lx.data(), rsh.lx.size() * sizeof(uint2), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dlzh, rsh.lz.data(), rsh.lz.size() * sizeof(uint2), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dlah, rsh.la.data(), rsh.la.size() * sizeof(uint2), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && !hstep.empty())
+        e = cudaMemcpyAsync(dhs, hstep.data(), hstep.size() * sizeof(int4), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && !hw.empty())
+        e = cudaMemcpyAsync(dhw, hw.data(), hw.size() * sizeof(double2), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(rp, rowptr.data(), rowptr.size() * sizeof(int), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(cl, col.data(), col.size() * sizeof(unsigned short), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(d_r0s, r0s.data(), r0s.size() * sizeof(double), cudaMemcpyHostToDevice, s);
@@ -632,6 +682,9 @@ int ensure_rotation(dafmm_ctx* c, int p, cudaStream_t s) {
         release();
         od.rot_T = nullptr; od.rot_rho = nullptr; od.ax_rowptr = nullptr; od.ax_col = nullptr; od.ax_val = nullptr;
         od.rot_lx = od.rot_lz = od.rot_la = nullptr;
+        od.rot_lxh = od.rot_lzh = od.rot_lah = nullptr;
+        od.hxr_step = nullptr;
+        od.hxr_w = nullptr;
         return cuda_fail(c, e, "rotation tables");
     }
     return DAFMM_OK;
@@ -1264,11 +1317,12 @@ int eval_adaptive(dafmm_tree* t, int order, int precision, double* dphi, double*
             // FP64: the M2L by rotation (Sec. 3.4), by default from p = 4
             const bool rot = precision == DAFMM_FP64 && (c->m2l_rot > 0 || (c->m2l_rot < 0 && order >= 4));
             if (rot && (rc = ensure_rotation(c, order, s))) return rc;
+            const int rflags = rot ? kM2LRot | (c->m2l_harm ? kM2LHarm : 0) : 0;
             for (int l = 2; l <= t->maxlev; ++l) {
                 if (l == t->maxlev) mark(4);
                 int mx = 0;
                 for (int o = 0; o < 8; ++o) mx = std::max(mx, t->grp_ptr_h[l * 8 + o + 1] - t->grp_ptr_h[l * 8 + o]);
-                CK(c, ops->m2l_a(od, av, precision | (rot ? kM2LRot : 0), t->grp_tg, t->grp_ptr, l * 8, mx, t->aM,
+                CK(c, ops->m2l_a(od, av, precision | rflags, t->grp_tg, t->grp_ptr, l * 8, mx, t->aM,
                                  t->aMf, t->aL, s),
                    "M2L");
                 CK(c, ops->p2l_a(av, precision, t->level_start[l], t->level_start[l + 1], t->aL, s), "P2L");
@@ -1895,11 +1949,12 @@ int dafmm_eval(dafmm_tree* t, int order, double theta, int precision, double* ph
                 const double inv_h = 1.0 / ldexp(t->dom[3], -l);
                 if (rot_ff) {
                     CK(c, ops->split_ff(ex.M[l], ex.Mhi[l], ex.Mlo[l], level_boxes(l) * od.ncp, s), "split");
-                    CK(c, ops->m2l_rot_ff(od, l, ex.Mhi[l], ex.Mlo[l], ex.L[l], inv_h, s), "M2L (rotation, float-float)");
+                    CK(c, ops->m2l_rot_ff(od, l, ex.Mhi[l], ex.Mlo[l], ex.L[l], inv_h, c->m2l_harm != 0, s),
+                       "M2L (rotation, float-float)");
                     ++launches;
                 }
                 else if (rot)
-                    CK(c, ops->m2l_rot(od, l, ex.M[l], ex.L[l], inv_h, s), "M2L (rotation)");
+                    CK(c, ops->m2l_rot(od, l, ex.M[l], ex.L[l], inv_h, c->m2l_harm != 0, s), "M2L (rotation)");
                 else
                     CK(c, ops->m2l_level(od, fff ? DAFMM_FP64 : precision, l, ex.M[l], ex.Mf[l], ex.L[l], inv_h, s),
                        "M2L");

@@ -598,6 +598,34 @@ struct RotLists {
     int lx, lz, la;
 };
 
+// the harmonic form of the rotation (harmonic task lists): the steps that restore a vector's
+// coefficients of z exponent >= 2 from its free ones by Laplace's equation (step s sets
+// V[i] = w1 V[i1] + w2 V[i2]; those of z exponent c at [cst[c], cst[c + 1]))
+struct RotHarm {
+    const int4* step;
+    const double2* w;
+    int cst[kMaxOrder + 3];
+};
+
+__device__ __forceinline__ double rot_axpby(double w1, double a, double w2, double b) { return fma(w1, a, w2 * b); }
+__device__ __forceinline__ ff rot_axpby(double w1, ff a, double w2, ff b) {
+    return ff_add(ff_mul(ff(w1), a), ff_mul(ff(w2), b));
+}
+
+// the warp restores V's coefficients of z exponent >= 2, level by level
+template <class R>
+__device__ __forceinline__ void rot_expand(R* V, const RotHarm& hm, int lane) {
+#pragma unroll 1
+    for (int c = 2; c <= P; ++c) {
+        for (int s = hm.cst[c] + lane; s < hm.cst[c + 1]; s += 32) {
+            const int4 st = hm.step[s];
+            const double2 w = hm.w[s];
+            V[st.x] = rot_axpby(w.x, V[st.y], w.y, V[st.z]);
+        }
+        __syncwarp();
+    }
+}
+
 // a source row into the work vector: FP64 rows, or (float-float) the rows' FP32 high and low
 // parts, split once per evaluation
 __device__ __forceinline__ void rot_load(double* X, const double* M, const float*, const float*, size_t row, int lane) {
@@ -610,10 +638,12 @@ __device__ __forceinline__ void rot_load(ff* X, const double*, const float* Mh, 
 // one well-separated pair for the warp: S += B_v A_|v| F_v Ms (T: the key's four substitution
 // tables, av: the axial matrix of its length; X, Y: work vectors with X[NC] = Y[NC] = 0; the
 // source row at `row` of M, or of Mh / Ml in float-float)
-template <class R>
+// HARM: harmonic task lists (free outputs only), the vector restored before the last x-step
+template <class R, bool HARM>
 __device__ __forceinline__ void rot_pair(const R* __restrict__ T, const R* __restrict__ av, const RotLists& rl,
                                          const double* __restrict__ M, const float* __restrict__ Mh,
-                                         const float* __restrict__ Ml, size_t row, R* X, R* Y, R* S, int lane) {
+                                         const float* __restrict__ Ml, size_t row, R* X, R* Y, R* S, int lane,
+                                         const RotHarm& hm) {
     __syncwarp();
     rot_load(X, M, Mh, Ml, row, lane);
     __syncwarp();
@@ -625,6 +655,7 @@ __device__ __forceinline__ void rot_pair(const R* __restrict__ T, const R* __res
     __syncwarp();
     rot_step<false>(rl.z, rl.lz, T + 2 * ROT_TSZ, Y, X, lane);  // back, about z
     __syncwarp();
+    if constexpr (HARM) rot_expand<R>(X, hm, lane);  // the x-step reads every z exponent
     rot_step<true>(rl.x, rl.lx, T + 3 * ROT_TSZ, X, S, lane);  // back, about x, into the sums
 }
 
@@ -638,12 +669,12 @@ struct RotBuf {
 // vectors are in shared memory; the task lists (the same for every pair) are read through the
 // L1 cache (copies of them in shared memory cost the float-float kernel a quarter of its
 // resident warps and gained nothing: measured 73.7 -> 75.5 ms at level 5, N = 1e6, p = 8).
-template <class R>
+template <class R, bool HARM>
 __global__ void __launch_bounds__(256, 2) k_m2l_rot(const R* __restrict__ Ttab, const int* __restrict__ krho,
                                                     RotLists rl, const R* __restrict__ aval, int annz, int l,
                                                     const double* __restrict__ M, const float* __restrict__ Mh,
                                                     const float* __restrict__ Ml, double* __restrict__ L,
-                                                    double inv_h) {
+                                                    double inv_h, const __grid_constant__ RotHarm hm) {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     __shared__ RotBuf<R> bufs[8];
     const int Pp = 1 << (l - 1), P3 = Pp * Pp * Pp, n_side = 1 << l;
@@ -667,10 +698,11 @@ __global__ void __launch_bounds__(256, 2) k_m2l_rot(const R* __restrict__ Ttab, 
                 const int sx = tx - vx, sy = ty - vy, sz = tz - vz;
                 if (sx < 0 || sy < 0 || sz < 0 || sx >= n_side || sy >= n_side || sz >= n_side) continue;
                 const int key = (vx + 3) * 49 + (vy + 3) * 7 + (vz + 3);
-                rot_pair<R>(Ttab + (size_t)key * 4 * ROT_TSZ, aval + (size_t)krho[key] * annz, rl, M, Mh, Ml,
-                            (size_t)octmajor_index(l, sx, sy, sz) * NCP, X, Y, S, lane);
+                rot_pair<R, HARM>(Ttab + (size_t)key * 4 * ROT_TSZ, aval + (size_t)krho[key] * annz, rl, M, Mh, Ml,
+                                  (size_t)octmajor_index(l, sx, sy, sz) * NCP, X, Y, S, lane, hm);
             }
     __syncwarp();
+    if constexpr (HARM) rot_expand<R>(S, hm, lane);  // the sums' coefficients of z exponent >= 2
     for (int k = lane; k < NC; k += 32) L[(size_t)t * NCP + k] = rot_to_double(S[k]) * inv_h;
 }
 
@@ -685,11 +717,13 @@ __global__ void k_split_ff(const double* __restrict__ a, float* __restrict__ hi,
 
 // the same for the targets tg[g0 .. g1) of one (level, octant) group of an adaptive tree (V-list
 // sources through the parent's colleagues, as in k_m2l_a); one warp per target
+template <bool HARM>
 __global__ void __launch_bounds__(256, 2) k_m2l_rot_a(const double* __restrict__ Ttab, const int* __restrict__ krho,
                                                       RotLists rl, const double* __restrict__ aval, int annz,
                                                       AdaptiveView av, const int* __restrict__ tg,
                                                       const int* __restrict__ grp_ptr, int grp0,
-                                                      const double* __restrict__ M, double* __restrict__ L) {
+                                                      const double* __restrict__ M, double* __restrict__ L,
+                                                      const __grid_constant__ RotHarm hm) {
     __shared__ double sbuf[8][3][NCP + 1];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int oct = blockIdx.y;
@@ -719,10 +753,11 @@ __global__ void __launch_bounds__(256, 2) k_m2l_rot_a(const double* __restrict__
                 const int sb = av.child[8 * Q + (scx | (scy << 1) | (scz << 2))];
                 if (sb < 0 || !DAFMM_IN(sb, av.nbox, kChkBoxIndex)) continue;
                 const int key = (vx + 3) * 49 + (vy + 3) * 7 + (vz + 3);
-                rot_pair<double>(Ttab + (size_t)key * 4 * ROT_TSZ, aval + (size_t)krho[key] * annz, rl, M,
-                                 nullptr, nullptr, (size_t)sb * NCP, X, Y, S, lane);
+                rot_pair<double, HARM>(Ttab + (size_t)key * 4 * ROT_TSZ, aval + (size_t)krho[key] * annz, rl, M,
+                                       nullptr, nullptr, (size_t)sb * NCP, X, Y, S, lane, hm);
             }
     __syncwarp();
+    if constexpr (HARM) rot_expand<double>(S, hm, lane);  // the sums' coefficients of z exponent >= 2
     const double inv_h = 1.0 / av.geom[t].w;  // the target box's width (each tree has its own)
     for (int k = lane; k < NC; k += 32) L[(size_t)t * NCP + k] = S[k] * inv_h;
 }
@@ -1806,24 +1841,50 @@ static cudaError_t leaf_launch(const TreeView& tv, int prec, const double* Lleaf
 }
 
 // M2L by rotation at level l (FP64, uniform trees): L~ = (1/h) sum_v B_v A_|v| F_v M~
-static cudaError_t m2l_rot_launch(const OrderData& od, int l, const double* M, double* L, double inv_h,
+// the task lists and expansion steps of the rotation: harmonic (free outputs only) or full
+static RotLists rot_lists(const OrderData& od, bool harm) {
+    if (harm) return RotLists{od.rot_lxh, od.rot_lzh, od.rot_lah, od.rot_lenh[0], od.rot_lenh[1], od.rot_lenh[2]};
+    return RotLists{od.rot_lx, od.rot_lz, od.rot_la, od.rot_len[0], od.rot_len[1], od.rot_len[2]};
+}
+static RotHarm rot_harm(const OrderData& od) {
+    RotHarm hm;
+    hm.step = od.hxr_step;
+    hm.w = od.hxr_w;
+    for (int k = 0; k < kMaxOrder + 3; ++k) hm.cst[k] = od.hxr_cst[k];
+    return hm;
+}
+
+static cudaError_t m2l_rot_launch(const OrderData& od, int l, const double* M, double* L, double inv_h, bool harm,
                                   cudaStream_t s) {
     const int nbox = 1 << (3 * l);
-    const RotLists rl{od.rot_lx, od.rot_lz, od.rot_la, od.rot_len[0], od.rot_len[1], od.rot_len[2]};
-    k_m2l_rot<double><<<(nbox + 7) / 8, 256, 0, s>>>(od.rot_T, od.rot_rho, rl, od.ax_val, od.ax_nnz, l, M, nullptr,
-                                                      nullptr, L, inv_h);
+    harm = harm && od.rot_lxh;
+    const RotLists rl = rot_lists(od, harm);
+    const RotHarm hm = rot_harm(od);
+    if (harm)
+        k_m2l_rot<double, true><<<(nbox + 7) / 8, 256, 0, s>>>(od.rot_T, od.rot_rho, rl, od.ax_val, od.ax_nnz, l, M,
+                                                                nullptr, nullptr, L, inv_h, hm);
+    else
+        k_m2l_rot<double, false><<<(nbox + 7) / 8, 256, 0, s>>>(od.rot_T, od.rot_rho, rl, od.ax_val, od.ax_nnz, l, M,
+                                                                 nullptr, nullptr, L, inv_h, hm);
     return cudaGetLastError();
 }
 
 // the same in float-float (DAFMM_FF): tables od.rot_Tf, od.ax_valf; the source rows' FP32 parts
 // Mh, Ml (k_split_ff); the task lists staged in shared memory
 static cudaError_t m2l_rot_ff_launch(const OrderData& od, int l, const float* Mh, const float* Ml, double* L,
-                                     double inv_h, cudaStream_t s) {
+                                     double inv_h, bool harm, cudaStream_t s) {
     const int nbox = 1 << (3 * l);
-    const RotLists rl{od.rot_lx, od.rot_lz, od.rot_la, od.rot_len[0], od.rot_len[1], od.rot_len[2]};
-    k_m2l_rot<ff><<<(nbox + 7) / 8, 256, 0, s>>>(reinterpret_cast<const ff*>(od.rot_Tf), od.rot_rho, rl,
-                                                     reinterpret_cast<const ff*>(od.ax_valf), od.ax_nnz, l, nullptr,
-                                                     Mh, Ml, L, inv_h);
+    harm = harm && od.rot_lxh;
+    const RotLists rl = rot_lists(od, harm);
+    const RotHarm hm = rot_harm(od);
+    const ff* T = reinterpret_cast<const ff*>(od.rot_Tf);
+    const ff* av = reinterpret_cast<const ff*>(od.ax_valf);
+    if (harm)
+        k_m2l_rot<ff, true><<<(nbox + 7) / 8, 256, 0, s>>>(T, od.rot_rho, rl, av, od.ax_nnz, l, nullptr, Mh, Ml, L,
+                                                            inv_h, hm);
+    else
+        k_m2l_rot<ff, false><<<(nbox + 7) / 8, 256, 0, s>>>(T, od.rot_rho, rl, av, od.ax_nnz, l, nullptr, Mh, Ml, L,
+                                                             inv_h, hm);
     return cudaGetLastError();
 }
 
@@ -1900,9 +1961,16 @@ static cudaError_t m2l_a_launch(const OrderData& od, const AdaptiveView& av, int
                                 double* L, cudaStream_t s) {
     if (max_group == 0) return cudaSuccess;
     if (prec & kM2LRot) {  // FP64 by rotation (Sec. 3.4)
-        const RotLists rl{od.rot_lx, od.rot_lz, od.rot_la, od.rot_len[0], od.rot_len[1], od.rot_len[2]};
-        k_m2l_rot_a<<<dim3((max_group + 7) / 8, 8), 256, 0, s>>>(od.rot_T, od.rot_rho, rl, od.ax_val, od.ax_nnz, av,
-                                                                 tg, grp_ptr, grp0, M, L);
+        const bool harm = (prec & kM2LHarm) && od.rot_lxh;
+        const RotLists rl = rot_lists(od, harm);
+        const RotHarm hm = rot_harm(od);
+        const dim3 grd((max_group + 7) / 8, 8);
+        if (harm)
+            k_m2l_rot_a<true><<<grd, 256, 0, s>>>(od.rot_T, od.rot_rho, rl, od.ax_val, od.ax_nnz, av, tg, grp_ptr, grp0,
+                                                  M, L, hm);
+        else
+            k_m2l_rot_a<false><<<grd, 256, 0, s>>>(od.rot_T, od.rot_rho, rl, od.ax_val, od.ax_nnz, av, tg, grp_ptr,
+                                                   grp0, M, L, hm);
         return cudaGetLastError();
     }
     dim3 grd((max_group + 31) / 32, 8);

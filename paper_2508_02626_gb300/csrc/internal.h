@@ -119,6 +119,15 @@ struct OrderData {
     uint2* rot_lz = nullptr;
     uint2* rot_la = nullptr;
     int rot_len[3] = {0, 0, 0};
+    // the same lists in the harmonic form (outputs of z exponent <= 1 only) and the steps that
+    // restore the other coefficients (FP64 weights; harm_steps in api.cu)
+    uint2* rot_lxh = nullptr;
+    uint2* rot_lzh = nullptr;
+    uint2* rot_lah = nullptr;
+    int rot_lenh[3] = {0, 0, 0};
+    int4* hxr_step = nullptr;
+    double2* hxr_w = nullptr;
+    int hxr_cst[kMaxOrder + 3] = {};
     // float-float copies of rot_T and ax_val (the DAFMM_FF mode's M2L), made on first use
     float2* rot_Tf = nullptr;
     float2* ax_valf = nullptr;
@@ -154,6 +163,7 @@ inline void shift_rp8(const HostShiftTable& t, int nc, int* out) {
 constexpr int kRowsF32 = 0x100;
 // or-ed into the precision argument of m2l_a (FP64 only): the M2L by rotation (Sec. 3.4)
 constexpr int kM2LRot = 0x200;
+constexpr int kM2LHarm = 0x400;  // with kM2LRot: the rotation in its harmonic form
 
 struct OrderOps {
     int p, nc, ncp;
@@ -171,7 +181,8 @@ struct OrderOps {
     cudaError_t (*kgen)(OrderData&, const short* key_list, int nkeys, cudaStream_t);  // null list: all keys
     // M2L by rotation (FP64) of a uniform tree's level, and its tables (adaptive trees: m2l_a
     // with kM2LRot)
-    cudaError_t (*m2l_rot)(const OrderData&, int level, const double* M, double* L, double inv_h, cudaStream_t);
+    cudaError_t (*m2l_rot)(const OrderData&, int level, const double* M, double* L, double inv_h, bool harm,
+                           cudaStream_t);
     cudaError_t (*rot_setup)(OrderData&, const double* r0s, int nrho, double* Kscratch, cudaStream_t);
     int rot_tsz;  // doubles per substitution table (sum over m <= p of (m+1)^2)
     cudaError_t (*op_p2m)(int prec, int64_t n, const double* s, const double* q, double* out, cudaStream_t);
@@ -194,7 +205,7 @@ struct OrderOps {
     // ax_valf; source rows as FP32 high and low parts), and the conversion of n doubles into
     // float-float pairs
     cudaError_t (*m2l_rot_ff)(const OrderData&, int level, const float* Mh, const float* Ml, double* L, double inv_h,
-                              cudaStream_t);
+                              bool harm, cudaStream_t);
     cudaError_t (*to_ff)(const double* a, float2* b, size_t n, cudaStream_t);
     // the float-float split of n FP64 values into their FP32 high and low parts
     cudaError_t (*split_ff)(const double* a, float* hi, float* lo, size_t n, cudaStream_t);

@@ -18,6 +18,11 @@
 //     lane l is list[32 t + l]: x = offset | last-task-of-its-output << 31,
 //     y = input index | output index << 16.
 // Substitution matrices are packed per degree m at offset rot_off(m) = sum_{m' < m} (m'+1)^2.
+// With harm, the lists compute only the outputs of z exponent c <= 1 -- the free coefficients of
+// a harmonic expansion (every vector of the M2L is one): a z-step output and an axial output of
+// z exponent c <= 1 read only inputs of z exponent <= c, so from the x-step on the free
+// coefficients carry the computation; the kernel restores the others (Laplace's equation) before
+// the last x-step, whose inputs span every z exponent, and once per target at the end.
 #pragma once
 #include <algorithm>
 #include <vector>
@@ -41,7 +46,7 @@ inline int rot_deg_start(int n) { return n * (n + 1) * (n + 2) / 6; }
 inline int rot_coef_index(int n, int a, int c) { return rot_deg_start(n) + (n - a) * (n - a + 1) / 2 + c; }
 inline int rot_off_h(int m) { return m * (m + 1) * (2 * m + 1) / 6; }
 
-inline RotStructure rot_structure(int p) {
+inline RotStructure rot_structure(int p, bool harm = false) {
     RotStructure r;
     for (int n = 0; n <= p; ++n)
         for (int a = n; a >= 0; --a)
@@ -88,6 +93,7 @@ inline RotStructure rot_structure(int p) {
     std::vector<std::vector<Task>> tx(nc), tz(nc), ta(nc);
     for (int k = 0; k < nc; ++k) {
         const int a = r.ea[k], b = r.eb[k], c = r.ec[k], n = a + b + c;
+        if (harm && c > 1) continue;
         const int mx = b + c, mz = a + b;
         for (int j = 0; j <= mx; ++j)
             tx[k].push_back({(unsigned)(rot_off_h(mx) + c * (mx + 1) + j), (unsigned)(rot_coef_index(n, a, 0) + j)});

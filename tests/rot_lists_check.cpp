@@ -80,7 +80,8 @@ std::vector<double> run_step(const std::vector<RotTask>& list, int len, const st
 }
 
 // every output in exactly one lane, its tasks contiguous with the last flag on the final one,
-// expected task counts, padding after the real tasks, lanes balanced
+// expected task counts, padding after the real tasks, lanes balanced; outputs with a zero
+// count must not appear (the harmonic lists compute the outputs of z exponent <= 1 only)
 int check_list(const RotStructure& r, const std::vector<RotTask>& list, int len, const std::vector<int>& count) {
     const int nc = r.nc;
     if ((int)list.size() != 32 * len) return 1;
@@ -107,7 +108,7 @@ int check_list(const RotStructure& r, const std::vector<RotTask>& list, int len,
             if (list[32 * t + lane].y != (unsigned)nc || list[32 * t + lane].x != 0u) return 6;
     }
     for (int k = 0; k < nc; ++k)
-        if (!seen[k]) return 7;
+        if (seen[k] != (count[k] > 0 ? 1 : 0)) return 7;
     if (lmax != len || lmax - lmin > biggest) return 8;
     return 0;
 }
@@ -177,4 +178,62 @@ extern "C" long rot_real_tasks(int p) {
         return c;
     };
     return 2 * real(r.lx) + 2 * real(r.lz) + real(r.la);
+}
+
+// The harmonic lists (rot_structure(p, true)): the same checks with only the outputs of z
+// exponent c <= 1 present, and, run on random data as the kernel runs them, the same values at
+// those outputs as the full lists -- the x-step from a full input, the z-step and the axial step
+// from the inputs of z exponent <= 1 alone (the others set to garbage, which must not matter).
+extern "C" int rot_lists_check_harm(int p, unsigned seed) {
+    const RotStructure r = rot_structure(p);
+    const RotStructure h = rot_structure(p, true);
+    const auto ex = layout(p);
+    const int nc = (int)ex.size();
+    if (h.nc != nc || h.rowptr != r.rowptr || h.col != r.col) return 10;
+    std::vector<int> cx(nc), cz(nc), ca(nc);
+    for (int k = 0; k < nc; ++k) {
+        const bool free_k = std::get<2>(ex[k]) <= 1;
+        cx[k] = free_k ? std::get<1>(ex[k]) + std::get<2>(ex[k]) + 1 : 0;
+        cz[k] = free_k ? std::get<0>(ex[k]) + std::get<1>(ex[k]) + 1 : 0;
+        ca[k] = free_k ? r.rowptr[k + 1] - r.rowptr[k] : 0;
+    }
+    if (int e = check_list(h, h.lx, h.len[0], cx)) return 200 + e;
+    if (int e = check_list(h, h.lz, h.len[1], cz)) return 210 + e;
+    if (int e = check_list(h, h.la, h.len[2], ca)) return 220 + e;
+    std::mt19937 rng(seed);
+    std::uniform_real_distribution<double> U(-1.0, 1.0);
+    for (int trial = 0; trial < 3; ++trial) {
+        const std::vector<double> T = subst_tables(p, U(rng), U(rng), U(rng), U(rng));
+        std::vector<double> A(r.col.size());
+        for (double& v : A) v = U(rng);
+        std::vector<double> f(nc + 1, 0.0), g(nc + 1, 0.0);
+        for (int k = 0; k < nc; ++k) {
+            f[k] = U(rng);
+            g[k] = std::get<2>(ex[k]) <= 1 ? f[k] : 1e30 * U(rng);  // garbage above c = 1
+        }
+        const std::vector<double> fx = run_step(r.lx, r.len[0], T, f), hx = run_step(h.lx, h.len[0], T, f);
+        const std::vector<double> fz = run_step(r.lz, r.len[1], T, f), hz = run_step(h.lz, h.len[1], T, g);
+        const std::vector<double> fa = run_step(r.la, r.len[2], A, f), ha = run_step(h.la, h.len[2], A, g);
+        for (int k = 0; k < nc; ++k) {
+            if (std::get<2>(ex[k]) > 1) continue;
+            if (std::fabs(hx[k] - fx[k]) > 1e-12 * (1.0 + std::fabs(fx[k]))) return 30;
+            if (std::fabs(hz[k] - fz[k]) > 1e-12 * (1.0 + std::fabs(fz[k]))) return 31;
+            if (std::fabs(ha[k] - fa[k]) > 1e-12 * (1.0 + std::fabs(fa[k]))) return 32;
+        }
+    }
+    return 0;
+}
+
+// multiply-adds per pair of the harmonic form: its lists' real tasks (x and z lists twice, the
+// axial list once) plus two per restored coefficient (one restoration per pair)
+extern "C" long rot_real_tasks_harm(int p) {
+    const RotStructure r = rot_structure(p, true);
+    auto real = [&](const std::vector<RotTask>& l) {
+        long c = 0;
+        for (const RotTask& t : l) c += !(t.y == (unsigned)r.nc && t.x == 0u);
+        return c;
+    };
+    long restored = 0;
+    for (int k = 0; k < r.nc; ++k) restored += r.ec[k] > 1;
+    return 2 * real(r.lx) + 2 * real(r.lz) + real(r.la) + 2 * restored;
 }

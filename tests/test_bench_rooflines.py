@@ -47,12 +47,15 @@ def rot():
     h = ctypes.CDLL(so)
     h.rot_real_tasks.argtypes = [ctypes.c_int]
     h.rot_real_tasks.restype = ctypes.c_long
+    h.rot_real_tasks_harm.argtypes = [ctypes.c_int]
+    h.rot_real_tasks_harm.restype = ctypes.c_long
     return h
 
 
 @pytest.mark.parametrize("p", [2, 4, 6, 8, 10])
 def test_rotation_madds_match_the_kernel_lists(rot, p):
-    assert bench.rotation_madds_per_pair(p) == rot.rot_real_tasks(p)
+    assert bench.rotation_madds_per_pair(p, harm=False) == rot.rot_real_tasks(p)
+    assert bench.rotation_madds_per_pair(p) == rot.rot_real_tasks_harm(p)
 
 
 def test_near_field_roofline_arithmetic():

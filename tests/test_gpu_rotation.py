@@ -120,3 +120,32 @@ def test_rotated_m2l_adaptive_forest(ctx):
         ref_phi, ref_E = O.fmm(xyz[a:b], qq[a:b], doms[m], p, max_leaf=32)
         assert rel(phi[a:b], ref_phi) <= 1e-12, (m, rel(phi[a:b], ref_phi))
         assert rel(E[a:b], ref_E) <= 1e-11
+
+
+@pytest.mark.parametrize("p", [3, 4, 8, 10])
+def test_harmonic_rotation_matches_full_lists(ctx, p):
+    """The rotation in its harmonic form (the default: only the outputs of z exponent <= 1 of
+    each step, the others restored by Laplace's equation before the last x-step and once per
+    target) against the full task lists, FP64 and float-float: the same result up to rounding."""
+    rng = np.random.default_rng(90 + p)
+    n = 6000
+    x = rng.random((n, 3))
+    q = rng.uniform(-1, 1, n)
+    dom = (0.0, 0.0, 0.0, 1.0)
+    for prec, tol in (("fp64", 1e-13), ("ff", 1e-12)):
+        out = {}
+        for harm in (1, 0):
+            B.dafmm_set_option(ctx.h, B.DAFMM_OPT_M2L_HARMONIC, harm)
+            try:
+                xt, qt = torch.from_numpy(x).cuda(), torch.from_numpy(q).cuda()
+                tree = ctx.build_tree(xt, qt, domain=dom, uniform_depth=3)
+                phi = torch.empty(n, dtype=torch.float64, device="cuda")
+                E = torch.empty((n, 3), dtype=torch.float64, device="cuda")
+                tree.eval(p, phi, E, precision=prec)
+                B.dafmm_sync(ctx.h)
+                tree.free()
+                out[harm] = (phi.cpu().numpy(), E.cpu().numpy())
+            finally:
+                B.dafmm_set_option(ctx.h, B.DAFMM_OPT_M2L_HARMONIC, 1)
+        assert rel(out[1][0], out[0][0]) <= tol, (prec, rel(out[1][0], out[0][0]))
+        assert rel(out[1][1], out[0][1]) <= 10 * tol, (prec, rel(out[1][1], out[0][1]))

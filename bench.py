@@ -565,6 +565,7 @@ def run_ours(args, rank, world):
             out["serving"] = bench_serving(args.serving_requests)
         if "operators" in sections:
             out["operators"] = bench_operators(ctx)
+            out["noalloc"] = bench_noalloc(ctx)
         if "leafsize" in sections:
             out["leaf_size"] = bench_leaf_size(ctx)
         if "paper" in sections:
@@ -860,6 +861,40 @@ def bench_serving(requests, fp64_every=4, direct_targets=8):
                                      "served_field_median": float(np.median(ds_sub[:, 1])),
                                      "fp64_field_median": float(np.median(d_fp64[:, 1])),
                                      "max_ratio_phi": float((ds_sub[:, 0] / np.maximum(d_fp64[:, 0], 1e-300)).max())}}
+    return out
+
+
+def bench_noalloc(ctx):
+    """dafmm_eval_noalloc (FP64, every intermediate in the library's fixed array: it copies the
+    operator tables in and regenerates the 343 M2L matrices on every call) beside dafmm_eval FP64
+    on the same tree (its tables and matrices made once and kept): wall time per call, the
+    stream synchronised after each, 20 calls after 3 warm-up calls."""
+    import time
+
+    import torch
+
+    from paper_2508_02626_gb300 import binding as B
+    from paper_2508_02626_gb300 import workloads as W
+    out = {}
+    for n, depth, p in ((10000, 3, 6), (40000, 4, 6)):
+        x, q = W.uniform(n, seed=880 + depth)
+        tree = ctx.build_tree(torch.from_numpy(x).cuda(), torch.from_numpy(q).cuda(), domain=W.UNIT_CUBE,
+                              uniform_depth=depth)
+        phi = torch.empty(n, dtype=torch.float64, device="cuda")
+        E = torch.empty((n, 3), dtype=torch.float64, device="cuda")
+        res = {}
+        for name, call in (("eval_ms", lambda: tree.eval(p, phi, E, precision="fp64")),
+                           ("noalloc_ms", lambda: B.dafmm_eval_noalloc(ctx.h, tree.h, p, phi, E))):
+            for _ in range(3):
+                call()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(20):
+                call()
+                torch.cuda.synchronize()
+            res[name] = round((time.perf_counter() - t0) / 20 * 1e3, 3)
+        tree.free()
+        out["N=%d depth %d p=%d" % (n, depth, p)] = res
     return out
 
 

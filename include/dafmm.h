@@ -267,8 +267,8 @@ int dafmm_debug_check(dafmm_ctx* ctx, void* stream);
  *   Limits: order <= 6 (else DAFMM_ERR_UNSUPPORTED_ORDER), uniform trees of depth <= 4
  *   (else DAFMM_ERR_INVALID_ARG; adaptive trees: DAFMM_ERR_UNSUPPORTED); phi and field must
  *   be device memory or NULL.
- *   The first call on a device looks up the array's device address; make that call
- *   before any stream capture.  All calls share the array: calls that overlap on the GPU
+ *   The first call on a device looks up the array's device address (cudaGetSymbolAddress)
+ *   and keeps it.  All calls share the array: calls that overlap on the GPU
  *   (other streams, other host threads) race, so the caller must order them. */
 int dafmm_eval_noalloc(dafmm_tree* tree, int order, double* phi, double* field, void* stream);
 

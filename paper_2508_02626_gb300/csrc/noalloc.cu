@@ -11,10 +11,10 @@
 // depth 4, and rejects anything larger.
 //
 // Set-up: the first call on a device looks up the device address of the array
-// (cudaGetSymbolAddress, with that device current) and caches it; that first call should
-// come before any stream capture.  Every call shares the array and rewrites everything it
-// uses, so calls that overlap on the GPU (different streams, or other host threads) race
-// and must be ordered by the caller.
+// (cudaGetSymbolAddress, with that device current) and caches it.  The operator tables it
+// copies in come from host storage kept for the process.  Every call shares the array and
+// rewrites everything it uses, so calls that overlap on the GPU (different streams, or other
+// host threads) race and must be ordered by the caller.
 #include <cuda_runtime.h>
 #include <string.h>
 

@@ -905,6 +905,9 @@ void free_adaptive(dafmm_ctx* c, dafmm_tree* t) {
     dev_free(c, t->aLh, t->aLh_bytes);
     t->aLh = nullptr;
     t->aLh_bytes = 0;
+    dev_free(c, t->aMc, t->aMc_bytes);
+    t->aMc = nullptr;
+    t->aMc_bytes = 0;
     const size_t nb1 = (size_t)t->nbox + 1;
     dev_free(c, t->a_geom, (size_t)t->nbox * sizeof(double4));
     dev_free(c, t->a_xq0, (size_t)t->nbox * sizeof(int));
@@ -1338,7 +1341,23 @@ int eval_adaptive(dafmm_tree* t, int order, int precision, double* dphi, double*
     } else {
         for (int k = 1; k <= 6; ++k) mark(k);
     }
-    CK(c, ops->leaf_a(av, t->leaves, t->nleaves, precision, t->aL, t->aM, dphi, dfield, c->leaf_warps, s),
+    // FP32 paths: the leaves' M2P reads FP32 multipole rows (no FP64 conversion per W box)
+    float* mc = nullptr;
+    if (far && precision != DAFMM_FP64) {
+        const size_t cnt = (size_t)t->nbox * ncp_of(order);
+        if (t->aMc_bytes != cnt * sizeof(float)) {
+            dev_free(c, t->aMc, t->aMc_bytes);
+            t->aMc = nullptr;
+            t->aMc_bytes = 0;
+            if ((rc = dev_alloc(c, (void**)&t->aMc, cnt * sizeof(float), "multipoles (FP32 copy)"))) return rc;
+            t->aMc_bytes = cnt * sizeof(float);
+        }
+        k_to_float<<<(unsigned)std::min<size_t>((cnt + 255) / 256, 152 * 16), 256, 0, s>>>(t->aM, t->aMc, cnt);
+        CK(c, cudaGetLastError(), "convert");
+        ++launches;
+        mc = t->aMc;
+    }
+    CK(c, ops->leaf_a(av, t->leaves, t->nleaves, precision, t->aL, t->aM, mc, dphi, dfield, c->leaf_warps, s),
        "P2P/M2P/L2P");
     ++launches;
     mark(7);

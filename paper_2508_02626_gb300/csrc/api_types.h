@@ -99,6 +99,8 @@ struct dafmm_tree {
     float* aMinv = nullptr;         // per box: factor of the F16 multipole split
     float* aLh = nullptr;           // harmonic-basis M2L output rows (FP32, free coefficients)
     size_t aLh_bytes = 0;
+    float* aMc = nullptr;           // FP32 copy of the multipole rows for the leaves' M2P (FP32 paths)
+    size_t aMc_bytes = 0;
 };
 
 

@@ -102,6 +102,12 @@ __device__ __forceinline__ void warp_row_to_f32(const double* __restrict__ row, 
     for (int k = lane; k < NC; k += 32) buf[k] = (float)row[k];
     __syncwarp();
 }
+// ... or an FP32 row
+__device__ __forceinline__ void warp_row_f32(const float* __restrict__ row, float* buf, int lane) {
+    __syncwarp();
+    for (int k = lane; k < NC; k += 32) buf[k] = row[k];
+    __syncwarp();
+}
 
 // ---- P2M ---------------------------------------------------------------------------------
 // rows32: the multipole rows are FP32 (NCP floats per leaf) instead of FP64.  The FP32 kernel
@@ -1518,7 +1524,8 @@ __global__ void __launch_bounds__(256) k_l2l_a(ShiftTab tab, AdaptiveView av, in
 template <class T>
 __global__ void __launch_bounds__(256) k_leaf_a(AdaptiveView av, const int* __restrict__ leaves, int nleaves,
                                                 const double* __restrict__ L, const double* __restrict__ M,
-                                                double* __restrict__ phi, double* __restrict__ field) {
+                                                const float* __restrict__ Mf, double* __restrict__ phi,
+                                                double* __restrict__ field) {
     __shared__ float s_rows[8][2][NCP];  // per warp: the W box's multipoles and the leaf's locals, FP32
     extern __shared__ __align__(16) float4 s_list_a[];  // FP32: per warp kLeafSeg records (2 float4s each)
     const int lane = threadIdx.x;
@@ -1596,14 +1603,28 @@ __global__ void __launch_bounds__(256) k_leaf_a(AdaptiveView av, const int* __re
                 done += fill;
                 fill = 0;
             };
+            const int* ijk_b = av.ijk + 3 * (size_t)b;
             auto add_leaf = [&](int sb) {
-                double scx, scy, scz, sh;
-                abox_geom(av, sb, scx, scy, scz, sh);
-                const float r = (float)(sh * ih);
-                const double ox = (scx - cx) * ih, oy = (scy - cy) * ih, oz = (scz - cz) * ih;
-                const float ohx = (float)ox, ohy = (float)oy, ohz = (float)oz;
-                const float olx = (float)(ox - (double)ohx), oly = (float)(oy - (double)ohy),
-                            olz = (float)(oz - (double)ohz);
+                // the source leaf's centre offset in this leaf's widths and its width ratio,
+                // from the integer box coordinates (same tree): with d = lev_b - lev_s,
+                // (c_s - c_b) / h_b = N / 2^(1 + max(0, -d)),
+                // N = (2 i_s + 1) 2^max(0, d) - (2 i_b + 1) 2^max(0, -d) -- as hi + lo floats,
+                // exactly, and without FP64 instructions (1/64 of the FP32 rate here)
+                const int d = lev - av.level[sb];
+                const int up = d > 0 ? d : 0, dn = d < 0 ? -d : 0;
+                const float r = __int_as_float((127 + d) << 23);          // h_s / h_b = 2^d
+                const float sc = __int_as_float((127 - 1 - dn) << 23);    // 2^-(1 + dn)
+                const int* ijk_s = av.ijk + 3 * (size_t)sb;
+                float oh[3], ol[3];
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    const long long N = ((2ll * ijk_s[k] + 1) << up) - ((2ll * ijk_b[k] + 1) << dn);
+                    const float h = (float)N;
+                    oh[k] = h * sc;
+                    ol[k] = (float)(N - (long long)h) * sc;
+                }
+                const float ohx = oh[0], ohy = oh[1], ohz = oh[2];
+                const float olx = ol[0], oly = ol[1], olz = ol[2];
                 if (!DAFMM_RANGE(av.pbeg[sb], av.pend[sb], av.n, kChkBoxRange)) return;
                 const int r0 = av.xq0[sb], n = av.pend[sb] - av.pbeg[sb];
                 if (!DAFMM_RANGE(r0, (long long)r0 + n, av.nrec, kChkRecord)) return;
@@ -1644,25 +1665,72 @@ __global__ void __launch_bounds__(256) k_leaf_a(AdaptiveView av, const int* __re
             fz = ((double)acc.zh + (double)acc.zl) * ih * ih;
         }
         // M2P from the W list (Sec. 3.2): phi = F/h_w, E = -grad_s F / h_w^2
-        for (int wi = w0; wi < w1; ++wi) {
-            const int wb = av.w_idx[wi];
-            if (!DAFMM_IN(wb, av.nbox, kChkBoxIndex)) continue;
-            double wx, wy, wz, wh;
-            abox_geom(av, wb, wx, wy, wz, wh);
-            const double iwh = 1.0 / wh;
-            T F, g0, g1, g2;
-            const T sx0 = (T)((av.x[tt] - wx) * iwh), sy0 = (T)((av.y[tt] - wy) * iwh),
-                    sz0 = (T)((av.z[tt] - wz) * iwh);
-            if constexpr (sizeof(T) == 4) {
-                warp_row_to_f32(M + (size_t)wb * NCP, mrow, lane);
-                gen::GEN(m2p)<T>(SmemRowF{mrow}, sx0, sy0, sz0, F, g0, g1, g2);
-            } else {
+        if constexpr (sizeof(T) == 8) {
+            for (int wi = w0; wi < w1; ++wi) {
+                const int wb = av.w_idx[wi];
+                if (!DAFMM_IN(wb, av.nbox, kChkBoxIndex)) continue;
+                double wx, wy, wz, wh;
+                abox_geom(av, wb, wx, wy, wz, wh);
+                const double iwh = 1.0 / wh;
+                T F, g0, g1, g2;
+                const T sx0 = (T)((av.x[tt] - wx) * iwh), sy0 = (T)((av.y[tt] - wy) * iwh),
+                        sz0 = (T)((av.z[tt] - wz) * iwh);
                 gen::GEN(m2p)<T>(RowLoad<T>{M + (size_t)wb * NCP}, sx0, sy0, sz0, F, g0, g1, g2);
+                fphi += (double)F * iwh;
+                fx -= (double)g0 * iwh * iwh;
+                fy -= (double)g1 * iwh * iwh;
+                fz -= (double)g2 * iwh * iwh;
             }
-            fphi += (double)F * iwh;
-            fx -= (double)g0 * iwh * iwh;
-            fy -= (double)g1 * iwh * iwh;
-            fz -= (double)g2 * iwh * iwh;
+        } else {
+            // FP32, without FP64 instructions (this part runs FP64 at 1/64 of the FP32 rate): the
+            // W box is finer than the leaf by dl levels of the same tree, so with integer box
+            // coordinates i at each level (c_b - c_w) / h_w = ((2 i_b + 1) 2^dl - (2 i_w + 1)) / 2
+            // per axis, exactly; the target in the W box's frame is its leaf-frame offset (record
+            // and remainder) times 2^dl plus that; the box's multipoles come as FP32 rows (Mf).
+            // Its terms are summed in FP32 and join the FP64 sums once per target.
+            const float4 pw = xq_load(av.xq, av.xq0[b] + (tt - i0)), plw = xq_load(av.xl, av.xq0[b] + (tt - i0));
+            const float ihf = (float)ih;
+            float wphi = 0.f, wfx = 0.f, wfy = 0.f, wfz = 0.f;
+            const int* ib = av.ijk + 3 * (size_t)b;
+            for (int wi = w0; wi < w1; ++wi) {
+                const int wb = av.w_idx[wi];
+                if (!DAFMM_IN(wb, av.nbox, kChkBoxIndex)) continue;
+                const int dl = av.level[wb] - lev;
+                float sx0, sy0, sz0, iw;
+                if (dl >= 0 && dl <= 30) {
+                    const float r = (float)(1u << dl);
+                    const long long rr = 1ll << dl;
+                    const int* iwb = av.ijk + 3 * (size_t)wb;
+                    const float ox = 0.5f * (float)((2ll * ib[0] + 1) * rr - (2ll * iwb[0] + 1));
+                    const float oy = 0.5f * (float)((2ll * ib[1] + 1) * rr - (2ll * iwb[1] + 1));
+                    const float oz = 0.5f * (float)((2ll * ib[2] + 1) * rr - (2ll * iwb[2] + 1));
+                    sx0 = fmaf(plw.x, r, fmaf(pw.x, r, ox));
+                    sy0 = fmaf(plw.y, r, fmaf(pw.y, r, oy));
+                    sz0 = fmaf(plw.z, r, fmaf(pw.z, r, oz));
+                    iw = ihf * r;
+                } else {  // (not a W-list shape; kept general)
+                    double wx, wy, wz, wh;
+                    abox_geom(av, wb, wx, wy, wz, wh);
+                    const double iwh = 1.0 / wh;
+                    sx0 = (float)((av.x[tt] - wx) * iwh);
+                    sy0 = (float)((av.y[tt] - wy) * iwh);
+                    sz0 = (float)((av.z[tt] - wz) * iwh);
+                    iw = (float)iwh;
+                }
+                if (Mf) warp_row_f32(Mf + (size_t)wb * NCP, mrow, lane);
+                else warp_row_to_f32(M + (size_t)wb * NCP, mrow, lane);
+                T F, g0, g1, g2;
+                gen::GEN(m2p)<T>(SmemRowF{mrow}, sx0, sy0, sz0, F, g0, g1, g2);
+                wphi = fmaf(F, iw, wphi);
+                const float iw2 = iw * iw;
+                wfx = fmaf(-g0, iw2, wfx);
+                wfy = fmaf(-g1, iw2, wfy);
+                wfz = fmaf(-g2, iw2, wfz);
+            }
+            fphi += (double)wphi;
+            fx += (double)wfx;
+            fy += (double)wfy;
+            fz += (double)wfz;
         }
         // L2P of this leaf's local expansion
         if (lev >= 2) {
@@ -2024,17 +2092,18 @@ static cudaError_t l2l_a_launch(const OrderData& od, const AdaptiveView& av, int
 }
 
 static cudaError_t leaf_a_launch(const AdaptiveView& av, const int* leaves, int nleaves, int prec, const double* L,
-                                 const double* M, double* phi, double* field, int warps, cudaStream_t s) {
+                                 const double* M, const float* Mf, double* phi, double* field, int warps,
+                                 cudaStream_t s) {
     if (nleaves == 0) return cudaSuccess;
     warps = warps < 1 ? 1 : (warps > 8 ? 8 : warps);
     dim3 blk(32, warps), grd((nleaves + warps - 1) / warps);
     if (prec == DAFMM_FP64) {
-        k_leaf_a<double><<<grd, blk, 0, s>>>(av, leaves, nleaves, L, M, phi, field);
+        k_leaf_a<double><<<grd, blk, 0, s>>>(av, leaves, nleaves, L, M, nullptr, phi, field);
     } else {
         const size_t smem = (size_t)warps * 2 * kLeafSeg * sizeof(float4);
         cudaError_t e = cudaFuncSetAttribute(k_leaf_a<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        k_leaf_a<float><<<grd, blk, smem, s>>>(av, leaves, nleaves, L, M, phi, field);
+        k_leaf_a<float><<<grd, blk, smem, s>>>(av, leaves, nleaves, L, M, Mf, phi, field);
     }
     return cudaGetLastError();
 }

@@ -200,7 +200,7 @@ struct OrderOps {
     // L2L from the parents [lb, le) of one level into their children
     cudaError_t (*l2l_a)(const OrderData&, const AdaptiveView&, int prec, int lb, int le, double* L, cudaStream_t);
     cudaError_t (*leaf_a)(const AdaptiveView&, const int* leaves, int nleaves, int prec, const double* L,
-                          const double* M, double* phi, double* field, int warps, cudaStream_t);
+                          const double* M, const float* Mf, double* phi, double* field, int warps, cudaStream_t);
     // the M2L by rotation of a uniform tree's level in float-float (DAFMM_FF; tables rot_Tf,
     // ax_valf; source rows as FP32 high and low parts), and the conversion of n doubles into
     // float-float pairs

@@ -1506,17 +1506,40 @@ __global__ void __launch_bounds__(256) k_l2l_a(ShiftTab tab, AdaptiveView av, in
         src[r * (NCP + 1) + k] = P < le ? (T)L[(size_t)P * NCP + k] : T(0);
     }
     __syncthreads();
-    const int P = b0 + lane;
-    if (P >= le || abox_is_leaf(av, P)) return;
-    int ch[8];
+    if constexpr (sizeof(T) == 8) {
+        // FP64 (bound by the FP64 pipe): lane = parent, every lane on the same row b
+        const int P = b0 + lane;
+        if (P >= le || abox_is_leaf(av, P)) return;
+        int ch[8];
 #pragma unroll
-    for (int c = 0; c < 8; ++c) ch[c] = av.child[8 * P + c];
-    for (int b = w; b < NC; b += 8) {
-        T R[8];
-        l2l_row(tab, b, src + lane * (NCP + 1), R);
+        for (int c = 0; c < 8; ++c) ch[c] = av.child[8 * P + c];
+        for (int b = w; b < NC; b += 8) {
+            T R[8];
+            l2l_row(tab, b, src + lane * (NCP + 1), R);
 #pragma unroll
-        for (int c = 0; c < 8; ++c)
-            if (ch[c] >= 0 && DAFMM_IN(ch[c], av.nbox, kChkBoxIndex)) L[(size_t)ch[c] * NCP + b] += (double)R[c];
+            for (int c = 0; c < 8; ++c)
+                if (ch[c] >= 0 && DAFMM_IN(ch[c], av.nbox, kChkBoxIndex)) L[(size_t)ch[c] * NCP + b] += (double)R[c];
+        }
+        return;
+    }
+    // FP32: warp w takes parents w, w + 8, ...; its lanes take consecutive rows b, so that the
+    // read-modify-write of each child's row is one coalesced access per warp instead of 32
+    // scattered ones (an ncu capture of the lane-per-parent form: long-scoreboard stalls 14 per
+    // issue, the L2 hit rate 45 %; clustered N = 4e6, p = 10: L2L 3.69 -> 3.26 ms)
+    for (int r = w; r < 32; r += 8) {
+        const int P = b0 + r;
+        if (P >= le || abox_is_leaf(av, P)) continue;
+        int ch[8];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) ch[c] = av.child[8 * P + c];
+        const T* srow = src + r * (NCP + 1);
+        for (int b = lane; b < NC; b += 32) {
+            T R[8];
+            l2l_row(tab, b, srow, R);
+#pragma unroll
+            for (int c = 0; c < 8; ++c)
+                if (ch[c] >= 0 && DAFMM_IN(ch[c], av.nbox, kChkBoxIndex)) L[(size_t)ch[c] * NCP + b] += (double)R[c];
+        }
     }
 }
 

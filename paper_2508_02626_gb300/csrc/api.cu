@@ -1119,7 +1119,7 @@ int build_adaptive(dafmm_ctx* c, dafmm_tree* t, const double* dxyz, const double
     if ((rc = cnt3.alloc(3 * nb1 * 4 + 32, "list counts"))) return rc;
     int* cu = cnt3.as<int>();
     unsigned long long* nv = reinterpret_cast<unsigned long long*>(cu + ((3 * nb1 + 1) & ~size_t(1)));
-    // overflow of the list traversal, this build's own flag: the context's record of expired
+    // overflow of the list traversal, the tree build's own flag: the context's record of expired
     // device waits (read by dafmm_sync) must survive a tree build
     int* lflag = reinterpret_cast<int*>(nv + 1);
     if ((rc = dev_alloc(c, (void**)&t->u_ptr, nb1 * 4, "lists")) || (rc = dev_alloc(c, (void**)&t->w_ptr, nb1 * 4, "lists")) ||

@@ -1,5 +1,5 @@
-"""The clock record of bench.py: NVML reason bits and nvidia-smi rows become the named reasons
-a bench line is judged by (hw_slowdown, hw_thermal_slowdown, sw_thermal_slowdown,
+"""The clock record of bench.py: NVML reason bits and nvidia-smi rows become the named
+throttle reasons a bench line reports (hw_slowdown, hw_thermal_slowdown, sw_thermal_slowdown,
 sw_power_cap), the denser NVML samples give the median clock when present, and a host with
 neither tool says so instead of reporting a clock."""
 import os

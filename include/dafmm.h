@@ -218,7 +218,8 @@ int dafmm_last_phase_ms(dafmm_ctx* ctx, double* out10);
  *   exponent <= 1; the M2L contracts those (p + 1)^2 coefficients against K^_v restricted and
  *   composed accordingly (81 instead of 165 at p = 8) and restores the others by Laplace's
  *   equation -- the same result up to rounding with about a quarter of the multiply-adds.
- *   0 = all ncoef coefficients. */
+ *   On uniform trees the P2M and the M2M then compute the multipoles' free coefficients only
+ *   (the M2M by its table composed with that expansion).  0 = all ncoef coefficients. */
 #define DAFMM_OPT_M2L_HARMONIC 6
 int dafmm_set_option(dafmm_ctx* ctx, int option, int64_t value);
 
@@ -226,8 +227,10 @@ int dafmm_set_option(dafmm_ctx* ctx, int option, int64_t value);
  * into host memory `out` as doubles (8^level x ncp values; ncp = ncoef rounded up to 8).
  * which: 0 multipoles, 1 locals, 2/3 TF32 high/low parts of the multipoles, 4/5 of the
  * locals.  The FP32 mode keeps the locals (M2L and L2L on tensor cores) and the multipoles
- * (F16 M2L, SIMT M2M) in FP32; they are returned as doubles all the same.  Synchronises the device.  Returns the number of values,
- * or a negative code. */
+ * (F16 M2L, SIMT M2M) in FP32; they are returned as doubles all the same.  With the harmonic basis
+ * (DAFMM_OPT_M2L_HARMONIC, uniform trees, FP32 and MIXED) the device computes only the multipoles'
+ * (p + 1)^2 free coefficients (z exponent <= 1); the others are filled in here from Laplace's
+ * equation.  Synchronises the device.  Returns the number of values, or a negative code. */
 int64_t dafmm_debug_level(const dafmm_tree* tree, int which, int level, double* out, int64_t cap);
 
 /* Wait for `stream` and report failures recorded on the device by bounded waits inside the

@@ -268,6 +268,15 @@ int ensure_order(dafmm_ctx* c, int p, cudaStream_t s, bool need_k) {
             shift_rp8(t, od.nc, rp8.data());
             if ((rc = upload(c, w == 0 ? &od.m2m_rp8 : &od.l2l_rp8, rp8.data(), rp8.size(), "shift table"))) return rc;
         }
+        {  // the M2M of harmonic multipoles
+            const HostShiftTable& t = ops->m2mh;
+            std::vector<float> vf(t.val, t.val + t.nnz);
+            if ((rc = upload(c, &od.m2mh_rowptr, t.rowptr, (size_t)od.nc + 1, "shift table"))) return rc;
+            if ((rc = upload(c, &od.m2mh_col, t.col, (size_t)t.nnz, "shift table"))) return rc;
+            if ((rc = upload(c, &od.m2mh_par, t.par, (size_t)t.nnz, "shift table"))) return rc;
+            if ((rc = upload(c, &od.m2mh_val, t.val, (size_t)t.nnz, "shift table"))) return rc;
+            if ((rc = upload(c, &od.m2mh_valf, vf.data(), (size_t)t.nnz, "shift table"))) return rc;
+        }
         // DA product table: for each output k, the pairs (i, j) with e_i + e_j = e_k
         std::vector<int> ex(3 * od.nc);
         for (int n = 0; n <= p; ++n)
@@ -365,6 +374,14 @@ void free_order(dafmm_ctx* c, OrderData& od) {
         dev_free(c, w == 0 ? (void*)od.m2m_valf : (void*)od.l2l_valf, t.nnz * sizeof(float));
         dev_free(c, w == 0 ? (void*)od.m2m_rp8 : (void*)od.l2l_rp8, (8 * (size_t)nc + 1) * sizeof(int));
     }
+    {
+        const HostShiftTable& t = ops->m2mh;
+        dev_free(c, od.m2mh_rowptr, od.m2mh_rowptr ? (nc + 1) * sizeof(int) : 0);
+        dev_free(c, od.m2mh_col, od.m2mh_col ? t.nnz * sizeof(unsigned short) : 0);
+        dev_free(c, od.m2mh_par, od.m2mh_par ? (size_t)t.nnz : 0);
+        dev_free(c, od.m2mh_val, od.m2mh_val ? t.nnz * sizeof(double) : 0);
+        dev_free(c, od.m2mh_valf, od.m2mh_valf ? t.nnz * sizeof(float) : 0);
+    }
     dev_free(c, od.mul_rowptr, ((size_t)nc + 1) * sizeof(int));
     dev_free(c, od.mul_pairs, od.mul_npairs * sizeof(ushort2));
     dev_free(c, od.mul_minus, (size_t)3 * nc * sizeof(short));
@@ -387,6 +404,7 @@ void free_order(dafmm_ctx* c, OrderData& od) {
         dev_free(c, od.k16h_inv_c, (size_t)kNumKeys * sizeof(float));
         dev_free(c, od.hx_step, std::max<size_t>(nstep, 1) * sizeof(int4));
         dev_free(c, od.hx_w, std::max<size_t>(nstep, 1) * sizeof(float2));
+        dev_free(c, od.hx_w64, std::max<size_t>(nstep, 1) * sizeof(double2));
         const size_t ctf = (size_t)kNumKeys * tc_npt_h(od.p) * harm_row(od.p) * sizeof(float);
         dev_free(c, od.Khih, ctf);
         dev_free(c, od.Kloh, ctf);
@@ -514,12 +532,14 @@ int ensure_k16h(dafmm_ctx* c, int p, cudaStream_t s) {
     const size_t ctf = (size_t)kNumKeys * npt * nhp * sizeof(float);
     int4* stp = nullptr;
     float2* wd = nullptr;
+    double2* wd64 = nullptr;
     auto release = [&]() {
         dev_free(c, hi, hi ? c16 : 0); dev_free(c, lo, lo ? c16 : 0);
         dev_free(c, ir, ir ? (size_t)npt * sizeof(float) : 0);
         dev_free(c, icv, icv ? (size_t)kNumKeys * sizeof(float) : 0);
         dev_free(c, stp, stp ? nstep * sizeof(int4) : 0);
         dev_free(c, wd, wd ? nstep * sizeof(float2) : 0);
+        dev_free(c, wd64, wd64 ? nstep * sizeof(double2) : 0);
         dev_free(c, thi, thi ? ctf : 0); dev_free(c, tlo, tlo ? ctf : 0);
     };
     auto release_scratch = [&]() {
@@ -533,6 +553,7 @@ int ensure_k16h(dafmm_ctx* c, int p, cudaStream_t s) {
         (rc = dev_alloc(c, (void**)&icv, (size_t)kNumKeys * sizeof(float), "M2L matrix factors")) ||
         (rc = dev_alloc(c, (void**)&stp, nstep * sizeof(int4), "harmonic expansion")) ||
         (rc = dev_alloc(c, (void**)&wd, nstep * sizeof(float2), "harmonic expansion")) ||
+        (rc = dev_alloc(c, (void**)&wd64, nstep * sizeof(double2), "harmonic expansion")) ||
         (rc = dev_alloc(c, (void**)&thi, ctf, "M2L matrices (harmonic, TF32 split)")) ||
         (rc = dev_alloc(c, (void**)&tlo, ctf, "M2L matrices (harmonic, TF32 split)")) ||
         (rc = dev_alloc(c, &xd, xb, "harmonic expansion (scratch)")) ||
@@ -547,6 +568,8 @@ int ensure_k16h(dafmm_ctx* c, int p, cudaStream_t s) {
         e = cudaMemcpyAsync(stp, step.data(), step.size() * sizeof(int4), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess && !w.empty())
         e = cudaMemcpyAsync(wd, w.data(), w.size() * sizeof(float2), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && !w64.empty())
+        e = cudaMemcpyAsync(wd64, w64.data(), w64.size() * sizeof(double2), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess)
         e = tc_prepare_k16h(od.K64, kNumKeys, p, static_cast<const double*>(xd), static_cast<double*>(khd), hi, lo, ir,
                             icv, scratch, thi, tlo, s);
@@ -562,6 +585,7 @@ int ensure_k16h(dafmm_ctx* c, int p, cudaStream_t s) {
     od.k16h_inv_c = icv;
     od.hx_step = stp;
     od.hx_w = wd;
+    od.hx_w64 = wd64;
     od.Khih = thi;
     od.Kloh = tlo;
     for (int k = 0; k < kMaxOrder + 3; ++k) od.hx_cst[k] = cst[k];
@@ -1217,14 +1241,6 @@ int eval_adaptive(dafmm_tree* t, int order, int precision, double* dphi, double*
     bool f32_locals = false;
     mark(0);
     if (far) {
-        CK(c, ops->p2m_a(av, t->leaves, t->nleaves, precision, t->aM, s), "P2M");
-        ++launches;
-        mark(1);
-        for (int l = t->maxlev - 1; l >= 2; --l) {
-            CK(c, ops->m2m_a(od, av, precision, t->level_start[l], t->level_start[l + 1], t->aM, s), "M2M");
-            ++launches;
-        }
-        mark(2);
         const size_t cnt = (size_t)t->nbox * od.ncp;
         const bool tc = precision != DAFMM_FP64 && c->m2l_kernel == 0 && c->tc_capable && order >= 2 &&
                         (precision != DAFMM_FP32 || (c->tc_mask & 1));
@@ -1250,6 +1266,21 @@ int eval_adaptive(dafmm_tree* t, int order, int precision, double* dphi, double*
             if ((rc = ensure_k16h(c, order, s))) return rc;
         }
         float* lh = t->aLh;
+        // P2M and M2M in the harmonic basis too when the M2L is: free coefficients only (the
+        // M2L reads nothing else); the others are filled in after the M2M, for the M2P
+        const int prec_m = precision | (harm ? kRowsHarm : 0);
+        CK(c, ops->p2m_a(av, t->leaves, t->nleaves, prec_m, t->aM, s), "P2M");
+        ++launches;
+        mark(1);
+        for (int l = t->maxlev - 1; l >= 2; --l) {
+            CK(c, ops->m2m_a(od, av, prec_m, t->level_start[l], t->level_start[l + 1], t->aM, s), "M2M");
+            ++launches;
+        }
+        if (harm) {
+            CK(c, tc_harm_fill(order, t->aM, t->nbox, od.hx_step, od.hx_w64, od.hx_cst, s), "M2M (harmonic fill)");
+            ++launches;
+        }
+        mark(2);
         if (f16) {
             if (!harm && (rc = ensure_k16(c, order, s))) return rc;
             const void* src = t->aM;
@@ -1836,13 +1867,17 @@ int dafmm_eval(dafmm_tree* t, int order, double theta, int precision, double* ph
         // all in FP32).
         f32_locals = tc_m2l && tc_l2l;
         const bool f32_mult = f16_m2l && !tc_m2m;
-        const int prec_m = precision | (f32_mult ? kRowsF32 : 0);
         Expansions& ex = t->ex;
         ex.M_f32 = f32_mult;
         // the tensor-core M2L in the harmonic basis: (p + 1)^2 free coefficients per row instead
         // of ncoef (F16 operands in the FP32 mode, TF32 in MIXED)
         const bool harm = tc_m2l && c->m2l_harm && (f16_m2l || !tc_m2m);  // (the tensor-core M2M
                                                                            // writes full TF32 rows)
+        // ... and then P2M and M2M in it too: the M2L reads only the multipoles' free
+        // coefficients, so only those are computed (the SIMT M2M; P2M in FP32)
+        const bool harm_m = harm && !tc_m2m;
+        ex.M_harm = harm_m;
+        const int prec_m = precision | (f32_mult ? kRowsF32 : 0) | (harm_m ? kRowsHarm : 0);
         if (f16_m2l && (rc = ensure_f16_levels(t, s))) return rc;
         if (harm && ((rc = ensure_lh_levels(t)) || (rc = ensure_k16h(c, order, s)))) return rc;
         if (f16_m2l && !harm && (rc = ensure_k16(c, order, s))) return rc;
@@ -2160,6 +2195,20 @@ int64_t dafmm_debug_level(const dafmm_tree* t, int which, int level, double* out
         std::vector<float> tmp(cnt);
         if (cudaMemcpy(tmp.data(), src, cnt * sizeof(float), cudaMemcpyDeviceToHost) != cudaSuccess) return DAFMM_ERR_CUDA;
         for (int64_t i = 0; i < cnt; ++i) out[i] = tmp[i];
+    }
+    if (which == 0 && e.M_harm) {
+        // harmonic-basis multipoles: the device wrote the free coefficients only; the others
+        // follow by Laplace's equation (in order of increasing z exponent), in FP64
+        std::vector<int4> step;
+        std::vector<double2> w;
+        int cst[kMaxOrder + 3];
+        harm_steps(e.p, step, w, cst);
+        const int ncp = ncp_of(e.p), nc = ncoef_of(e.p);
+        for (int64_t r = 0; r < cnt / ncp; ++r) {
+            double* row = out + r * ncp;
+            for (size_t q = 0; q < step.size(); ++q) row[step[q].x] = w[q].x * row[step[q].y] + w[q].y * row[step[q].z];
+            for (int k = nc; k < ncp; ++k) row[k] = 0.0;
+        }
     }
     return cnt;
 }

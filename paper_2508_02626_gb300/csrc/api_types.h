@@ -55,6 +55,7 @@ struct Expansions {
     float* Lh[dafmm::kMaxUniformDepth + 1] = {};
     bool L_f32 = false;  // the last evaluation left FP32 rows (ncp floats per box) in L
     bool M_f32 = false;  // ... and in M
+    bool M_harm = false;  // ... and harmonic-basis multipoles (free coefficients only) in M
 };
 
 struct dafmm_tree {

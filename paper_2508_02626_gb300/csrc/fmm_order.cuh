@@ -58,14 +58,15 @@ struct SmemSink {
 // reduced row by row (lane j takes coefficient 32 c + j), so the staging needs 32 x 33
 // values per warp instead of ncoef x 33.  The generated code passes k as a constant, so the
 // flush tests fold away.
-template <class T, int NJ>
+// NO: the number of coefficients the generated code emits (NC; the harmonic P2M: (p + 1)^2).
+template <class T, int NJ, int NO = NC>
 struct ChunkSink {
     T* buf;       // [32][33] per warp
     int lane;
     T (&acc)[NJ];  // acc[c] += coefficient 32 c + lane
     __device__ __forceinline__ void operator()(int k, T v) const {
         buf[(k & 31) * 33 + lane] = v;
-        if ((k & 31) == 31 || k == NC - 1) {
+        if ((k & 31) == 31 || k == NO - 1) {
             __syncwarp();
             if (lane <= (k & 31)) {
                 T s = T(0);
@@ -113,7 +114,10 @@ __device__ __forceinline__ void warp_row_f32(const float* __restrict__ row, floa
 // rows32: the multipole rows are FP32 (NCP floats per leaf) instead of FP64.  The FP32 kernel
 // reads the particles' FP32 leaf-frame records, which hold exactly the values it would compute
 // from the FP64 coordinates ((x - c) / h rounded once to FP32), without FP64 arithmetic.
-template <class T>
+// H: the harmonic basis -- the generated code emits only the (p + 1)^2 free coefficients
+// (z exponent <= 1), which are summed and written at their layout positions; the others are
+// not computed (the multipole's homogeneous parts are harmonic, Eq. 2, so they are implied).
+template <class T, bool H = false>
 __global__ void k_p2m(TreeView tv, double* __restrict__ M, int rows32) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* sm = reinterpret_cast<T*>(smem_raw) + threadIdx.y * (32 * 33);
@@ -128,11 +132,12 @@ __global__ void k_p2m(TreeView tv, double* __restrict__ M, int rows32) {
     const double cy = tv.y0 + ((double)b + 0.5) * tv.h_leaf;
     const double cz = tv.z0 + ((double)c + 0.5) * tv.h_leaf;
     const int r_own = xq_base(i0, leaf) - i0;  // FP32 record of sorted position i: i + r_own
-    constexpr int NJ = (NC + 31) / 32;
+    constexpr int NO = H ? nharm_of(P) : NC;
+    constexpr int NJ = (NO + 31) / 32;
     T acc[NJ];
 #pragma unroll
     for (int j = 0; j < NJ; ++j) acc[j] = T(0);
-    ChunkSink<T, NJ> sink{sm, lane, acc};
+    ChunkSink<T, NJ, NO> sink{sm, lane, acc};
     for (int base = i0; base < i1; base += 32) {
         const int i = base + lane;
         T x = T(0), y = T(0), z = T(0), q = T(0);
@@ -150,21 +155,22 @@ __global__ void k_p2m(TreeView tv, double* __restrict__ M, int rows32) {
                 q = (T)tv.q[i];
             }
         }
-        gen::GEN(p2m)<T>(x, y, z, q, sink);
+        if constexpr (H) gen::GEN(p2mh)<T>(x, y, z, q, sink);
+        else gen::GEN(p2m)<T>(x, y, z, q, sink);
     }
     if (rows32) {
         float* Mf = reinterpret_cast<float*>(M) + (size_t)leaf * NCP;
 #pragma unroll
         for (int j = 0; j < NJ; ++j) {
             const int k = lane + 32 * j;
-            if (k < NC) Mf[k] = (float)acc[j];
+            if (k < NO) Mf[H ? harm_full_index(k) : k] = (float)acc[j];
         }
         return;
     }
 #pragma unroll
     for (int j = 0; j < NJ; ++j) {
         const int k = lane + 32 * j;
-        if (k < NC) M[(size_t)leaf * NCP + k] = (double)acc[j];
+        if (k < NO) M[(size_t)leaf * NCP + (H ? harm_full_index(k) : k)] = (double)acc[j];
     }
 }
 
@@ -213,18 +219,22 @@ constexpr size_t m2m_smem() {
     return (size_t)8 * m2m_parents<T>() * (NCP + 1) * sizeof(T);
 }
 
-// M2M from the children at level lc into the parents at level lc - 1 (uniform tree)
+// M2M from the children at level lc into the parents at level lc - 1 (uniform tree).  harm:
+// harmonic multipoles -- tab is the harmonic M2M table, which reads and writes only the free
+// coefficients, so only those are staged and computed.
 template <class T>
 __global__ void __launch_bounds__(256) k_m2m(ShiftTab tab, int lc, const double* __restrict__ Mc,
-                                             double* __restrict__ Mp, int rows32) {
+                                             double* __restrict__ Mp, int rows32, int harm) {
     constexpr int PP = m2m_parents<T>(), RS = 32 / PP;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* S = reinterpret_cast<T*>(smem_raw);  // [8][PP][NCP + 1]
     const int Pc = 1 << (lc - 1);
     const int nparent = Pc * Pc * Pc;
     const int lin0 = blockIdx.x * PP;
-    for (int e = threadIdx.x; e < PP * NC; e += 256) {
-        const int r = e / NC, k = e - r * NC;
+    const int NO = harm ? nharm_of(P) : NC;  // coefficients staged and computed per box
+    for (int e = threadIdx.x; e < PP * NO; e += 256) {
+        const int r = e / NO, j = e - r * NO;
+        const int k = harm ? harm_full_index(j) : j;
         const int lin = lin0 + r;
         T m[8];
 #pragma unroll
@@ -243,7 +253,8 @@ __global__ void __launch_bounds__(256) k_m2m(ShiftTab tab, int lc, const double*
     if (lin >= nparent) return;
     const int px = lin % Pc, py = (lin / Pc) % Pc, pz = lin / (Pc * Pc);
     const size_t ob = (size_t)octmajor_index(lc - 1, px, py, pz) * NCP;
-    for (int b = w * RS + sub; b < NC; b += 8 * RS) {
+    for (int j = w * RS + sub; j < NO; j += 8 * RS) {
+        const int b = harm ? harm_full_index(j) : j;
         T acc = T(0);
         for (int e = tab.rowptr[b]; e < tab.rowptr[b + 1]; ++e)
             acc += tab_val<T>(tab, e) * S[(tab.par[e] * PP + r) * (NCP + 1) + tab.col[e]];
@@ -1306,8 +1317,9 @@ __device__ __forceinline__ bool abox_is_leaf(const AdaptiveView& av, int b) {
            c0.x < 0 && c0.y < 0 && c0.z < 0 && c0.w < 0 && c1.x < 0 && c1.y < 0 && c1.z < 0 && c1.w < 0;
 }
 
-// P2M (Eq. 2) at the leaves listed in `leaves`: one warp per leaf, as in k_p2m
-template <class T>
+// P2M (Eq. 2) at the leaves listed in `leaves`: one warp per leaf, as in k_p2m (H: the
+// harmonic basis's free coefficients only, written at their layout positions)
+template <class T, bool H = false>
 __global__ void k_p2m_a(AdaptiveView av, const int* __restrict__ leaves, int nleaves, double* __restrict__ M) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* sm = reinterpret_cast<T*>(smem_raw) + threadIdx.y * (32 * 33);
@@ -1321,39 +1333,59 @@ __global__ void k_p2m_a(AdaptiveView av, const int* __restrict__ leaves, int nle
     const double ih = 1.0 / h;
     int i0 = av.pbeg[b], i1 = av.pend[b];
     if (!DAFMM_RANGE(i0, i1, av.n, kChkBoxRange)) i0 = i1 = 0;
-    constexpr int NJ = (NC + 31) / 32;
+    if constexpr (sizeof(T) == 4) {  // the leaf's records
+        if (!DAFMM_RANGE(av.xq0[b], (long long)av.xq0[b] + (i1 - i0), av.nrec, kChkRecord)) i0 = i1 = 0;
+    }
+    constexpr int NO = H ? nharm_of(P) : NC;
+    constexpr int NJ = (NO + 31) / 32;
     T acc[NJ];
 #pragma unroll
     for (int j = 0; j < NJ; ++j) acc[j] = T(0);
-    ChunkSink<T, NJ> sink{sm, lane, acc};
+    ChunkSink<T, NJ, NO> sink{sm, lane, acc};
     for (int base = i0; base < i1; base += 32) {
         const int i = base + lane;
         T x = T(0), y = T(0), z = T(0), q = T(0);
         if (i < i1) {
-            x = (T)((av.x[i] - cx) * ih);
-            y = (T)((av.y[i] - cy) * ih);
-            z = (T)((av.z[i] - cz) * ih);
-            q = (T)av.q[i];
+            if constexpr (sizeof(T) == 4) {
+                // the particle's FP32 record: its offset from this leaf's centre in leaf widths
+                // (what the FP64 form computes, rounded once) and its charge, without FP64
+                // instructions (1/64 of the FP32 rate on this part)
+                const float4 r = xq_load(av.xq, av.xq0[b] + (i - i0));
+                x = r.x;
+                y = r.y;
+                z = r.z;
+                q = r.w;
+            } else {
+                x = (T)((av.x[i] - cx) * ih);
+                y = (T)((av.y[i] - cy) * ih);
+                z = (T)((av.z[i] - cz) * ih);
+                q = (T)av.q[i];
+            }
         }
-        gen::GEN(p2m)<T>(x, y, z, q, sink);
+        if constexpr (H) gen::GEN(p2mh)<T>(x, y, z, q, sink);
+        else gen::GEN(p2m)<T>(x, y, z, q, sink);
     }
 #pragma unroll
     for (int j = 0; j < NJ; ++j) {
         const int k = lane + 32 * j;
-        if (k < NC) M[(size_t)b * NCP + k] = (double)acc[j];
+        if (k < NO) M[(size_t)b * NCP + (H ? harm_full_index(k) : k)] = (double)acc[j];
     }
 }
 
 // M2M (Eq. 4) into the non-leaf boxes [lb, le) of one level, from their existing children
-// (missing children count as zero; leaves keep their P2M result)
+// (missing children count as zero; leaves keep their P2M result).  harm: harmonic multipoles,
+// tab the harmonic M2M table -- free coefficients only, as in k_m2m.
 template <class T>
-__global__ void __launch_bounds__(256) k_m2m_a(ShiftTab tab, AdaptiveView av, int lb, int le, double* __restrict__ M) {
+__global__ void __launch_bounds__(256) k_m2m_a(ShiftTab tab, AdaptiveView av, int lb, int le, double* __restrict__ M,
+                                               int harm) {
     constexpr int PP = m2m_parents<T>(), RS = 32 / PP;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* S = reinterpret_cast<T*>(smem_raw);  // [8][PP][NCP + 1]
     const int b0 = lb + blockIdx.x * PP;
-    for (int e = threadIdx.x; e < PP * NC; e += 256) {
-        const int r = e / NC, k = e - r * NC;
+    const int NO = harm ? nharm_of(P) : NC;
+    for (int e = threadIdx.x; e < PP * NO; e += 256) {
+        const int r = e / NO, j = e - r * NO;
+        const int k = harm ? harm_full_index(j) : j;
         const int bx = b0 + r;
         T m[8];
 #pragma unroll
@@ -1371,7 +1403,8 @@ __global__ void __launch_bounds__(256) k_m2m_a(ShiftTab tab, AdaptiveView av, in
     const int bx = b0 + r;
     if (bx >= le || abox_is_leaf(av, bx)) return;
     double* out = M + (size_t)bx * NCP;
-    for (int b = w * RS + sub; b < NC; b += 8 * RS) {
+    for (int j = w * RS + sub; j < NO; j += 8 * RS) {
+        const int b = harm ? harm_full_index(j) : j;
         T acc = T(0);
         for (int e = tab.rowptr[b]; e < tab.rowptr[b + 1]; ++e)
             acc += tab_val<T>(tab, e) * S[(tab.par[e] * PP + r) * (NCP + 1) + tab.col[e]];
@@ -1844,8 +1877,10 @@ static cudaError_t set_smem(K kernel, size_t bytes) {
 static cudaError_t p2m_launch(const TreeView& tv, int prec, double* M, cudaStream_t s) {
     if (tv.nleaf == 0) return cudaSuccess;
     const int rows32 = (prec & kRowsF32) ? 1 : 0;
-    prec &= ~kRowsF32;
+    const bool harm = (prec & kRowsHarm) != 0;
+    prec &= ~(kRowsF32 | kRowsHarm);
     const bool f64 = prec == DAFMM_FP64, fff = prec == DAFMM_FF;
+    if (harm && (f64 || fff)) return cudaErrorInvalidValue;  // (the FP32 kernel only)
     const size_t per_warp = (size_t)32 * 33 * (f64 || fff ? 8 : 4);
     int wpb = (int)((96 * 1024) / per_warp);
     wpb = wpb < 1 ? 1 : (wpb > 4 ? 4 : wpb);
@@ -1858,6 +1893,9 @@ static cudaError_t p2m_launch(const TreeView& tv, int prec, double* M, cudaStrea
     } else if (fff) {
         if ((e = set_smem(k_p2m<ff>, smem)) != cudaSuccess) return e;
         k_p2m<ff><<<grd, blk, smem, s>>>(tv, M, 0);
+    } else if (harm) {
+        if ((e = set_smem(k_p2m<float, true>, smem)) != cudaSuccess) return e;
+        k_p2m<float, true><<<grd, blk, smem, s>>>(tv, M, rows32);
     } else {
         if ((e = set_smem(k_p2m<float>, smem)) != cudaSuccess) return e;
         k_p2m<float><<<grd, blk, smem, s>>>(tv, M, rows32);
@@ -1868,19 +1906,22 @@ static cudaError_t p2m_launch(const TreeView& tv, int prec, double* M, cudaStrea
 static cudaError_t m2m_launch(const OrderData& od, int prec, int lc, const double* Mc, double* Mp,
                               cudaStream_t s) {
     const int rows32 = (prec & kRowsF32) ? 1 : 0;
-    prec &= ~kRowsF32;
+    const int harm = (prec & kRowsHarm) ? 1 : 0;
+    prec &= ~(kRowsF32 | kRowsHarm);
+    if (harm && (prec == DAFMM_FP64 || prec == DAFMM_FF || !od.m2mh_rowptr)) return cudaErrorInvalidValue;
     const int Pc = 1 << (lc - 1);
     const int nparent = Pc * Pc * Pc;
     const bool f32 = prec == DAFMM_FP32;
+    const ShiftTab tab = harm ? od.m2mh() : od.m2m();
     cudaError_t e;
     if (!f32) {
         constexpr int PP = m2m_parents<double>();
         if ((e = set_smem(k_m2m<double>, m2m_smem<double>())) != cudaSuccess) return e;
-        k_m2m<double><<<(nparent + PP - 1) / PP, 256, m2m_smem<double>(), s>>>(od.m2m(), lc, Mc, Mp, 0);
+        k_m2m<double><<<(nparent + PP - 1) / PP, 256, m2m_smem<double>(), s>>>(tab, lc, Mc, Mp, 0, harm);
     } else {
         constexpr int PP = m2m_parents<float>();
         if ((e = set_smem(k_m2m<float>, m2m_smem<float>())) != cudaSuccess) return e;
-        k_m2m<float><<<(nparent + PP - 1) / PP, 256, m2m_smem<float>(), s>>>(od.m2m(), lc, Mc, Mp, rows32);
+        k_m2m<float><<<(nparent + PP - 1) / PP, 256, m2m_smem<float>(), s>>>(tab, lc, Mc, Mp, rows32, harm);
     }
     return cudaGetLastError();
 }
@@ -2013,7 +2054,10 @@ static cudaError_t kgen_launch(OrderData& od, const short* key_list, int nkeys, 
 static cudaError_t p2m_a_launch(const AdaptiveView& av, const int* leaves, int nleaves, int prec, double* M,
                                 cudaStream_t s) {
     if (nleaves == 0) return cudaSuccess;
+    const bool harm = (prec & kRowsHarm) != 0;
+    prec &= ~kRowsHarm;
     const bool f64 = prec == DAFMM_FP64;
+    if (harm && (f64 || prec == DAFMM_FF)) return cudaErrorInvalidValue;  // (the FP32 kernel only)
     const size_t per_warp = (size_t)32 * 33 * (f64 ? 8 : 4);
     int wpb = (int)((96 * 1024) / per_warp);
     wpb = wpb < 1 ? 1 : (wpb > 4 ? 4 : wpb);
@@ -2023,6 +2067,9 @@ static cudaError_t p2m_a_launch(const AdaptiveView& av, const int* leaves, int n
     if (f64) {
         if ((e = set_smem(k_p2m_a<double>, smem)) != cudaSuccess) return e;
         k_p2m_a<double><<<grd, blk, smem, s>>>(av, leaves, nleaves, M);
+    } else if (harm) {
+        if ((e = set_smem(k_p2m_a<float, true>, smem)) != cudaSuccess) return e;
+        k_p2m_a<float, true><<<grd, blk, smem, s>>>(av, leaves, nleaves, M);
     } else {
         if ((e = set_smem(k_p2m_a<float>, smem)) != cudaSuccess) return e;
         k_p2m_a<float><<<grd, blk, smem, s>>>(av, leaves, nleaves, M);
@@ -2033,16 +2080,20 @@ static cudaError_t p2m_a_launch(const AdaptiveView& av, const int* leaves, int n
 static cudaError_t m2m_a_launch(const OrderData& od, const AdaptiveView& av, int prec, int lb, int le, double* M,
                                 cudaStream_t s) {
     if (le <= lb) return cudaSuccess;
+    const int harm = (prec & kRowsHarm) ? 1 : 0;
+    prec &= ~kRowsHarm;
+    if (harm && (prec == DAFMM_FP64 || prec == DAFMM_FF || !od.m2mh_rowptr)) return cudaErrorInvalidValue;
     const bool f32 = prec == DAFMM_FP32;
+    const ShiftTab tab = harm ? od.m2mh() : od.m2m();
     cudaError_t e;
     if (!f32) {
         constexpr int PP = m2m_parents<double>();
         if ((e = set_smem(k_m2m_a<double>, m2m_smem<double>())) != cudaSuccess) return e;
-        k_m2m_a<double><<<(le - lb + PP - 1) / PP, 256, m2m_smem<double>(), s>>>(od.m2m(), av, lb, le, M);
+        k_m2m_a<double><<<(le - lb + PP - 1) / PP, 256, m2m_smem<double>(), s>>>(tab, av, lb, le, M, harm);
     } else {
         constexpr int PP = m2m_parents<float>();
         if ((e = set_smem(k_m2m_a<float>, m2m_smem<float>())) != cudaSuccess) return e;
-        k_m2m_a<float><<<(le - lb + PP - 1) / PP, 256, m2m_smem<float>(), s>>>(od.m2m(), av, lb, le, M);
+        k_m2m_a<float><<<(le - lb + PP - 1) / PP, 256, m2m_smem<float>(), s>>>(tab, av, lb, le, M, harm);
     }
     return cudaGetLastError();
 }
@@ -2176,6 +2227,8 @@ const OrderOps* DAFMM_CAT(order_ops_p, DAFMM_P)() {
                        gen::GENT(m2m, _val)},
         HostShiftTable{gen::GENT(l2l, _nnz), gen::GENT(l2l, _rowptr), gen::GENT(l2l, _col), gen::GENT(l2l, _par),
                        gen::GENT(l2l, _val)},
+        HostShiftTable{gen::GENT(m2mh, _nnz), gen::GENT(m2mh, _rowptr), gen::GENT(m2mh, _col), gen::GENT(m2mh, _par),
+                       gen::GENT(m2mh, _val)},
         p2m_launch, m2m_launch, l2l_launch, m2l_launch, leaf_launch, kgen_launch, m2l_rot_launch, rot_setup_launch,
         ROT_TSZ,
         op_p2m, op_p2l, op_l2p, op_m2p, op_shift,

@@ -83,6 +83,10 @@ struct OrderData {
     int* l2l_rowptr = nullptr; unsigned short* l2l_col = nullptr; unsigned char* l2l_par = nullptr;
     double* l2l_val = nullptr; float* l2l_valf = nullptr;
     int* m2m_rp8 = nullptr; int* l2l_rp8 = nullptr;
+    // the M2M of harmonic multipoles (free rows composed with the expansion from the free
+    // coefficients; no rp8 runs)
+    int* m2mh_rowptr = nullptr; unsigned short* m2mh_col = nullptr; unsigned char* m2mh_par = nullptr;
+    double* m2mh_val = nullptr; float* m2mh_valf = nullptr;
     // F16 splits of the M2L matrices with their power-of-two row and matrix factors
     void* Kh16 = nullptr; void* Kl16 = nullptr;
     float* k16_inv_r = nullptr; float* k16_inv_c = nullptr;
@@ -94,6 +98,7 @@ struct OrderData {
     float* Khih = nullptr; float* Kloh = nullptr;  // TF32 parts [343][npt_h][harm_row] (MIXED)
     int4* hx_step = nullptr;      // [ncoef - nharm]: (i, i1, i2, 0), in order of increasing c
     float2* hx_w = nullptr;       // their weights (w1, w2): a[i] = w1 a[i1] + w2 a[i2]
+    double2* hx_w64 = nullptr;    // the same weights in FP64 (the multipoles' fill)
     int hx_cst[kMaxOrder + 3] = {};  // steps of z exponent c: [hx_cst[c], hx_cst[c + 1])
     int* mul_rowptr = nullptr; ushort2* mul_pairs = nullptr; short* mul_minus = nullptr;
     size_t mul_npairs = 0;
@@ -133,6 +138,7 @@ struct OrderData {
     float2* ax_valf = nullptr;
     ShiftTab m2m() const { return ShiftTab{m2m_rowptr, m2m_col, m2m_par, m2m_val, m2m_valf, m2m_rp8}; }
     ShiftTab l2l() const { return ShiftTab{l2l_rowptr, l2l_col, l2l_par, l2l_val, l2l_valf, l2l_rp8}; }
+    ShiftTab m2mh() const { return ShiftTab{m2mh_rowptr, m2mh_col, m2mh_par, m2mh_val, m2mh_valf, nullptr}; }
     MulTab mul() const { return MulTab{mul_rowptr, mul_pairs, mul_minus}; }
 };
 
@@ -164,10 +170,15 @@ constexpr int kRowsF32 = 0x100;
 // or-ed into the precision argument of m2l_a (FP64 only): the M2L by rotation (Sec. 3.4)
 constexpr int kM2LRot = 0x200;
 constexpr int kM2LHarm = 0x400;  // with kM2LRot: the rotation in its harmonic form
+// or-ed into the precision argument of p2m, m2m_level, p2m_a and m2m_a (FP32 and MIXED): the
+// multipoles are harmonic-basis rows -- only the (p + 1)^2 free coefficients (z exponent <= 1)
+// are computed and written, at their layout positions; the other entries are left as they are
+// (adaptive trees fill them in afterwards, tc_harm_fill, for the M2P)
+constexpr int kRowsHarm = 0x800;
 
 struct OrderOps {
     int p, nc, ncp;
-    HostShiftTable m2m, l2l;
+    HostShiftTable m2m, l2l, m2mh;
     // precision argument: DAFMM_FP64 / DAFMM_MIXED / DAFMM_FP32
     cudaError_t (*p2m)(const TreeView&, int prec, double* Mleaf, cudaStream_t);
     cudaError_t (*m2m_level)(const OrderData&, int prec, int lchild, const double* Mc, double* Mp,

@@ -3,13 +3,14 @@
 For every order p this writes ``da_ops_p{p}.cuh`` with
 
   p2m_o{p}(x, y, z, q, out)       P2M of one charge (Eq. 2) in scaled offsets
+  p2mh_o{p}(x, y, z, q, out)      the same, free coefficients of the harmonic basis only
   p2l_o{p}(X, Y, Z, q, out)       P2L of one charge (Eq. 6), w = centre - source, scaled
   l2p_o{p}(L, x, y, z, ...)       L2P with gradient (Sec. 3.2)
   m2p_o{p}(M, x, y, z, ...)       M2P with gradient (Sec. 3.2)
   m2lmap_o{p}(X, Y, Z, inv, isq)  the M2L transfer-map factors (Eq. 5)
 
 and ``da_tables_p{p}.h`` with the level-independent M2M (Eq. 4, octant-reduced
-as in Sec. 3.3) and L2L (Eq. 7) matrices in compressed rows.
+as in Sec. 3.3, also in the harmonic basis) and L2L (Eq. 7) matrices in compressed rows.
 
 Like the paper's parser, the emitter walks the symbolic coefficients term by
 term (sign, rational coefficient, powers of the base symbols), computes every
@@ -230,6 +231,14 @@ def generate(p, outdir):
     parts.append("// P2M, Eq. 2: out(k, q * coefficient k of (1 - 2 s.d + s^2 d^2)^(-1/2)), s = (x,y,z)\n")
     parts.append(code + "\n")
     stats["p2m"] = n
+    free = ops.free_coefficients(p)
+    code, n = emit_poly_outputs(
+        "p2mh_o%d" % p, p, ("x", "y", "z", "R2"), [c[i] for i in free], "qq", "q", "T x, T y, T z, T q",
+        ["const T R2 = x * x + y * y + z * z;"])
+    parts.append("// P2M in the harmonic basis: out(j, coefficient of free index j), the (p + 1)^2 coefficients\n"
+                 "// of z exponent <= 1 in layout order (the others follow by Laplace's equation)\n")
+    parts.append(code + "\n")
+    stats["p2mh"] = n
     syms, c = ops.p2l(p)
     code, n = emit_poly_outputs(
         "p2l_o%d" % p, p, ("X", "Y", "Z", "rho"), c, "qir", "q * ir", "T X, T Y, T Z, T q",
@@ -257,9 +266,15 @@ def generate(p, outdir):
     tparts = [HEADER % dict(p=p, nc=nc), "#pragma once\nnamespace dafmm {\nnamespace gen {\n\n"]
     tparts.append("// M2M (Eq. 4) in scaled variables, child octant (0,0,0): M~'_b = sum T[b][a] M~_a.\n"
                   "// Octant c flips the sign of entry (b,a) when popcount(par & c) is odd (Sec. 3.3).\n")
-    code, nnz = csr_table("m2m_o%d" % p, p, ops.m2m_scaled_table(p))
+    T = ops.m2m_scaled_table(p)
+    code, nnz = csr_table("m2m_o%d" % p, p, T)
     tparts.append(code)
     stats["m2m_nnz"] = nnz
+    tparts.append("\n// M2M of harmonic multipoles: the free rows of the table above composed with the expansion\n"
+                  "// from the free coefficients (Laplace's equation); reads and writes free coefficients only.\n")
+    code, nnz = csr_table("m2mh_o%d" % p, p, ops.m2m_harmonic_table(p, T))
+    tparts.append(code)
+    stats["m2mh_nnz"] = nnz
     tparts.append("\n// L2L (Eq. 7) in scaled variables, child octant (0,0,0): L~'_b = sum T[b][a] L~_a.\n")
     code, nnz = csr_table("l2l_o%d" % p, p, ops.l2l_scaled_table(p))
     tparts.append(code)

@@ -165,3 +165,63 @@ def octant_sign(e_out, e_in, octant):
         if (octant >> v) & 1 and (e_out[v] + e_in[v]) % 2:
             s = -s
     return s
+
+
+# ---- the harmonic basis -------------------------------------------------------------------
+def free_coefficients(p):
+    """Layout indices of the free coefficients of a harmonic expansion: those with z exponent
+    c <= 1, (p + 1)^2 of them, in layout order.  The homogeneous parts of the multipole
+    expansion (Eq. 2, the Legendre generating function) are harmonic polynomials, so every
+    other coefficient follows from these by Laplace's equation."""
+    return [i for i, e in enumerate(exponents(p)) if e[2] <= 1]
+
+
+def harmonic_expansion(p):
+    """X as sparse rows: X[i] = {free index j: Fraction} with a = X a[free] for every harmonic
+    coefficient vector a.  Laplace's equation on the degree-n homogeneous part gives
+    (c + 2)(c + 1) a[a, b, c + 2] = -(a + 2)(a + 1) a[a + 2, b, c] - (b + 2)(b + 1) a[a, b + 2, c],
+    applied in order of increasing c.  Every step keeps the parity of each exponent, so X[i]
+    only involves free coefficients of i's parity pattern."""
+    ex = exponents(p)
+    free = free_coefficients(p)
+    X = [None] * len(ex)
+    for j, i in enumerate(free):
+        X[i] = {j: Fraction(1)}
+    for i in sorted(range(len(ex)), key=lambda i: ex[i][2]):
+        a, b, c = ex[i]
+        if c <= 1:
+            continue
+        row = {}
+        d = Fraction(c * (c - 1))
+        for src, w in ((index(a + 2, b, c - 2), -Fraction((a + 2) * (a + 1)) / d),
+                       (index(a, b + 2, c - 2), -Fraction((b + 2) * (b + 1)) / d)):
+            for j, v in X[src].items():
+                row[j] = row.get(j, Fraction(0)) + w * v
+        X[i] = {j: v for j, v in row.items() if v != 0}
+    return X
+
+
+def m2m_harmonic_table(p, T=None):
+    """The M2M table (m2m_scaled_table) for harmonic multipoles: rows restricted to the free
+    coefficients and composed with the expansion X, so that the parent's free coefficients
+    follow from the child's free coefficients alone (the M2M of a harmonic expansion is
+    harmonic: it is the P2M of the same charges about another centre).  Dense nc x nc with
+    zero rows and columns outside the free coefficients; column j of X becomes the layout
+    column of free coefficient j, so the octant parity of an entry is that of its row and
+    column layout exponents, as in the full table."""
+    if T is None:
+        T = m2m_scaled_table(p)
+    nc = ncoef(p)
+    free = free_coefficients(p)
+    X = harmonic_expansion(p)
+    out = [[Fraction(0)] * nc for _ in range(nc)]
+    for b in free:
+        acc = {}
+        for a in range(nc):
+            t = T[b][a]
+            if t:
+                for j, v in X[a].items():
+                    acc[j] = acc.get(j, Fraction(0)) + t * v
+        for j, v in acc.items():
+            out[b][free[j]] = v
+    return out

@@ -53,6 +53,17 @@ static int p2m_any(int p, const T* s, T q, T* out) {
     }
     return -1;
 }
+// the harmonic-basis P2M: free coefficient j into out[j]
+template <class T>
+static int p2mh_any(int p, const T* s, T q, T* out) {
+    Store<T> st{out};
+    switch (p) {
+#define C(P) case P: p2mh_o##P<T>(s[0], s[1], s[2], q, st); return 0;
+        ORDERS(C)
+#undef C
+    }
+    return -1;
+}
 template <class T>
 static int p2l_any(int p, const T* w, T q, T* out) {
     Store<T> st{out};
@@ -92,6 +103,13 @@ int hc_p2m(int p, int prec, const double* s, double q, double* out, int nc) {
     for (int k = 0; k < nc; ++k) out[k] = of[k];
     return rc;
 }
+int hc_p2mh(int p, int prec, const double* s, double q, double* out, int nh) {
+    if (prec == 64) return p2mh_any<double>(p, s, q, out);
+    float sf[3] = {(float)s[0], (float)s[1], (float)s[2]}, of[300];
+    int rc = p2mh_any<float>(p, sf, (float)q, of);
+    for (int k = 0; k < nh; ++k) out[k] = of[k];
+    return rc;
+}
 int hc_p2l(int p, int prec, const double* w, double q, double* out, int nc) {
     if (prec == 64) return p2l_any<double>(p, w, q, out);
     float wf[3] = {(float)w[0], (float)w[1], (float)w[2]}, of[300];
@@ -126,7 +144,7 @@ int hc_m2lmap(int p, const double* v, double* inv, double* isq) {
     }
     return -1;
 }
-// apply a shift table (0 = M2M, 1 = L2L) for octant c: out = T_c in
+// apply a shift table (0 = M2M, 1 = L2L, 2 = M2M of harmonic multipoles) for octant c: out = T_c in
 int hc_shift(int p, int which, int c, const double* in, double* out, int nc) {
     const int* rp = nullptr;
     const unsigned short* col = nullptr;
@@ -134,6 +152,7 @@ int hc_shift(int p, int which, int c, const double* in, double* out, int nc) {
     const double* val = nullptr;
     switch (p) {
 #define C(P) case P: if (which == 0) { rp = m2m_o##P##_rowptr; col = m2m_o##P##_col; par = m2m_o##P##_par; val = m2m_o##P##_val; } \
+                     else if (which == 2) { rp = m2mh_o##P##_rowptr; col = m2mh_o##P##_col; par = m2mh_o##P##_par; val = m2mh_o##P##_val; } \
                      else { rp = l2l_o##P##_rowptr; col = l2l_o##P##_col; par = l2l_o##P##_par; val = l2l_o##P##_val; } break;
         ORDERS(C)
 #undef C

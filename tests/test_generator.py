@@ -30,6 +30,7 @@ def hc():
     lib = ctypes.CDLL(so)
     D = ctypes.POINTER(ctypes.c_double)
     for nm, args in {"hc_p2m": [ctypes.c_int, ctypes.c_int, D, ctypes.c_double, D, ctypes.c_int],
+                     "hc_p2mh": [ctypes.c_int, ctypes.c_int, D, ctypes.c_double, D, ctypes.c_int],
                      "hc_p2l": [ctypes.c_int, ctypes.c_int, D, ctypes.c_double, D, ctypes.c_int],
                      "hc_l2p": [ctypes.c_int, ctypes.c_int, D, D, D, ctypes.c_int],
                      "hc_m2p": [ctypes.c_int, ctypes.c_int, D, D, D, ctypes.c_int],
@@ -151,3 +152,65 @@ def test_generated_shift_tables(hc, p):
         # parent width 1, child width 1/2: L~' = L' * (1/2)^|b|
         ref = O.l2l(p, L, (o - 0.5) * 0.5) / 2.0 ** n
         assert np.abs(out - ref).max() <= 1e-13 * np.abs(ref).max()
+
+
+def free_layout(p):
+    """Layout indices of the coefficients of z exponent <= 1, from the oracle's exponents."""
+    return [i for i, e in enumerate(O.exponents(p)) if e[2] <= 1]
+
+
+@pytest.mark.parametrize("p", ORDERS)
+def test_generated_harmonic_p2m(hc, p):
+    """The harmonic-basis P2M emits exactly the oracle P2M's coefficients of z exponent <= 1,
+    (p + 1)^2 of them, in layout order."""
+    rng = np.random.default_rng(400 + p)
+    free = free_layout(p)
+    nh = (p + 1) ** 2
+    assert len(free) == nh
+    for prec, tol in ((64, 1e-12), (32, 2e-5)):
+        got, ref = [], []
+        for _ in range(200):
+            s = rng.uniform(-0.5, 0.5, 3)
+            q = rng.uniform(-1, 1)
+            out = np.zeros(nh)
+            assert hc.hc_p2mh(p, prec, P(s), q, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), nh) == 0
+            full = np.zeros(O.ncoef(p))
+            full[free] = out
+            got.append(full)
+            r = np.array(O.p2m(p, s[None, :], [q]))
+            r[[i for i in range(O.ncoef(p)) if i not in set(free)]] = 0.0
+            ref.append(r)
+        assert per_order_rel(np.array(got), np.array(ref), p) <= tol
+
+
+@pytest.mark.parametrize("p", ORDERS)
+def test_generated_harmonic_m2m_table(hc, p):
+    """The M2M table of harmonic multipoles: from the child's free coefficients alone it gives
+    the parent's free coefficients of the oracle's M2M (scaled variables, every octant), and it
+    reads and writes nothing else.  A generic (non-harmonic) child vector gives a different
+    result from the full table, so the composition with Laplace's equation is what makes it
+    right."""
+    rng = np.random.default_rng(500 + p)
+    nc = O.ncoef(p)
+    ex = O.exponents(p)
+    n = ex.sum(1)
+    free = free_layout(p)
+    other = [i for i in range(nc) if i not in set(free)]
+    for c in range(8):
+        o = np.array([c & 1, (c >> 1) & 1, (c >> 2) & 1])
+        M = O.p2m(p, rng.uniform(-0.5, 0.5, (30, 3)), rng.uniform(-1, 1, 30))
+        Mf = np.array(M, dtype=float)
+        Mf[other] = np.nan  # reading a non-free coefficient would show up as NaN
+        out = np.zeros(nc)
+        assert hc.hc_shift(p, 2, c, P(Mf),
+                           out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), nc) == 0
+        ref = O.m2m(p, M, 0.5 - o) / 2.0 ** n
+        assert np.all(np.isfinite(out))
+        assert np.abs(out[free] - ref[free]).max() <= 1e-13 * np.abs(ref).max()
+        assert np.all(out[other] == 0.0)
+    if p >= 3:  # (up to p = 2 no free row of the full table reads a coefficient with c >= 2)
+        G = rng.standard_normal(nc)
+        full, harm = np.zeros(nc), np.zeros(nc)
+        assert hc.hc_shift(p, 0, 0, P(G), full.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), nc) == 0
+        assert hc.hc_shift(p, 2, 0, P(G), harm.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), nc) == 0
+        assert np.abs(full[free] - harm[free]).max() > 1e-3 * np.abs(full).max()

@@ -275,3 +275,64 @@ def test_harmonic_m2l(ctx, p):
             assert rel(out[harm][1], ref_E) <= TOL_E[prec], (prec, harm, rel(out[harm][1], ref_E))
         assert rel(out[1][0], out[0][0]) <= TOL[prec]
         assert rel(out[1][1], out[0][1]) <= TOL_E[prec]
+
+
+@pytest.mark.parametrize("p", [3, 6, 8, 10])
+def test_harmonic_multipoles(ctx, p):
+    """P2M and M2M in the harmonic basis (uniform trees, FP32 and MIXED, the default): the
+    multipoles of every level against the oracle's P2M (Eq. 2) of each box's particles about the
+    box centre, in box-scaled variables (M~_a = M_a / h^|a|), degree by degree.  The free
+    coefficients (z exponent <= 1) are what the device computes: within the FP32 bound.  The
+    others are filled in by Laplace's equation on reading; the recursion
+    a_i = w1 a_i1 + w2 a_i2 carries the free coefficients' errors into them with gain at most
+    G_i = |w1| G_i1 + |w2| G_i2 (G = 1 on the free ones), so they are held to G_i times the bound.
+    With the harmonic basis off, every coefficient is within the bound."""
+    depth = 4
+    x, q = W.uniform(20000, seed=900 + p)
+    dom = W.UNIT_CUBE
+    ex = O.exponents(p)
+    deg = ex.sum(1)
+    nc = O.ncoef(p)
+    ncp = (nc + 7) // 8 * 8
+    idx = {tuple(int(v) for v in e): i for i, e in enumerate(ex)}
+    gain = np.ones(nc)
+    for i in sorted(range(nc), key=lambda i: ex[i][2]):
+        a, b, c = (int(v) for v in ex[i])
+        if c >= 2:
+            gain[i] = ((a + 2) * (a + 1) * gain[idx[(a + 2, b, c - 2)]] +
+                       (b + 2) * (b + 1) * gain[idx[(a, b + 2, c - 2)]]) / (c * (c - 1))
+    xt, qt = torch.from_numpy(x).cuda(), torch.from_numpy(q).cuda()
+    n = len(q)
+    ref = {}
+    for lev in range(2, depth + 1):
+        h = dom[3] / 2 ** lev
+        ijk = np.minimum(np.floor((x - dom[:3]) / h).astype(int), 2 ** lev - 1)
+        P2 = 2 ** (lev - 1)
+        oct_ = (ijk[:, 0] & 1) | ((ijk[:, 1] & 1) << 1) | ((ijk[:, 2] & 1) << 2)
+        row = oct_ * P2 ** 3 + ((ijk[:, 2] >> 1) * P2 + (ijk[:, 1] >> 1)) * P2 + (ijk[:, 0] >> 1)
+        R = np.zeros((8 ** lev, nc))
+        for b in np.unique(row):
+            sel = row == b
+            c = dom[:3] + (ijk[sel][0] + 0.5) * h
+            R[b] = O.p2m(p, (x[sel] - c) / h, q[sel])
+        ref[lev] = R
+    for prec, tol in (("fp32", 2e-5), ("mixed", 2e-5)):
+        for harm in (1, 0):
+            B.dafmm_set_option(ctx.h, B.DAFMM_OPT_M2L_HARMONIC, harm)
+            try:
+                tree = ctx.build_tree(xt, qt, domain=dom, uniform_depth=depth)
+                phi = torch.empty(n, dtype=torch.float64, device="cuda")
+                E = torch.empty((n, 3), dtype=torch.float64, device="cuda")
+                tree.eval(p, phi, E, precision=prec)
+                B.dafmm_sync(ctx.h)
+                for lev in range(2, depth + 1):
+                    M = B.dafmm_debug_level(tree.h, "M", lev, ncp)[:, :nc]
+                    for k in range(p + 1):
+                        s = deg == k
+                        scale = np.abs(ref[lev][:, s]).max()
+                        err = np.abs(M[:, s] - ref[lev][:, s]).max(0) / scale
+                        bound = tol * (gain[s] if harm else 1.0)
+                        assert np.all(err <= bound), (prec, harm, lev, k, (err / bound).max())
+                tree.free()
+            finally:
+                B.dafmm_set_option(ctx.h, B.DAFMM_OPT_M2L_HARMONIC, 1)

@@ -218,8 +218,9 @@ int dafmm_last_phase_ms(dafmm_ctx* ctx, double* out10);
  *   exponent <= 1; the M2L contracts those (p + 1)^2 coefficients against K^_v restricted and
  *   composed accordingly (81 instead of 165 at p = 8) and restores the others by Laplace's
  *   equation -- the same result up to rounding with about a quarter of the multiply-adds.
- *   On uniform trees the P2M and the M2M then compute the multipoles' free coefficients only
- *   (the M2M by its table composed with that expansion).  0 = all ncoef coefficients. */
+ *   The P2M and the M2M then compute the multipoles' free coefficients only (the M2M by its
+ *   table composed with that expansion; adaptive trees fill in the rest for the M2P).
+ *   0 = all ncoef coefficients. */
 #define DAFMM_OPT_M2L_HARMONIC 6
 int dafmm_set_option(dafmm_ctx* ctx, int option, int64_t value);
 

@@ -1277,7 +1277,7 @@ int eval_adaptive(dafmm_tree* t, int order, int precision, double* dphi, double*
             ++launches;
         }
         if (harm) {
-            CK(c, tc_harm_fill(order, t->aM, t->nbox, od.hx_step, od.hx_w64, od.hx_cst, s), "M2M (harmonic fill)");
+            CK(c, harm_fill(order, t->aM, t->nbox, od.hx_step, od.hx_w64, od.hx_cst, s), "M2M (harmonic fill)");
             ++launches;
         }
         mark(2);

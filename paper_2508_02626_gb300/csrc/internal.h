@@ -224,6 +224,11 @@ struct OrderOps {
 
 const OrderOps* order_ops(int p);
 
+// harm_fill.cu: the coefficients of z exponent >= 2 of nrows FP64 multipole rows (ncp doubles
+// each) from their free ones, in place; step, w and cst as made by the harmonic-basis setup
+// (OrderData::hx_step, hx_w64, hx_cst)
+cudaError_t harm_fill(int p, double* M, int nrows, const int4* step, const double2* w, const int* cst, cudaStream_t s);
+
 // numerical-DA operator batches (da_numeric.cu), FP64, one warp per instance; `op` is one of
 // kDa*, the arguments those of the single-operator entry points (a: first array, b: second,
 // oct: child octants of M2M/L2L)

@@ -537,40 +537,6 @@ __global__ void __launch_bounds__(128) k_harm_expand(HarmSegments sg, const int4
     }
 }
 
-struct HarmCst {
-    int c[kMaxOrder + 3];  // steps of z exponent c: [c[c], c[c + 1])
-};
-
-// The coefficients of z exponent >= 2 of FP64 multipole rows from their free ones, in place
-// (the homogeneous parts are harmonic, Eq. 2): one warp per row, the free coefficients staged
-// in shared memory, the steps a[i] = w1 a[i1] + w2 a[i2] of Laplace's equation applied in
-// order of increasing z exponent, each result written to the row as it is made.
-__global__ void __launch_bounds__(128) k_harm_fill(double* __restrict__ M, int nrows, const int4* __restrict__ step,
-                                                   const double2* __restrict__ w, HarmCst cst, int p, int ncp,
-                                                   int nh) {
-    __shared__ double sbuf[4][ncp_of(kMaxOrder)];
-    const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
-    const int row = (int)(blockIdx.x * 4 + wi);
-    if (row >= nrows) return;
-    double* buf = sbuf[wi];
-    double* r = M + (size_t)row * ncp;
-    for (int k = lane; k < nh; k += 32) {
-        const int i = harm_full_index(k);
-        buf[i] = r[i];
-    }
-    __syncwarp();
-    for (int c = 2; c <= p; ++c) {
-        for (int s = cst.c[c] + lane; s < cst.c[c + 1]; s += 32) {
-            const int4 st = step[s];
-            const double2 ww = w[s];
-            const double v = fma(ww.x, buf[st.y], ww.y * buf[st.z]);
-            buf[st.x] = v;
-            r[st.x] = v;
-        }
-        __syncwarp();
-    }
-}
-
 }  // namespace tc
 
 // ---- host side ---------------------------------------------------------------------------------
@@ -644,16 +610,6 @@ cudaError_t tc_prepare_k16h(const double* K, int nkey, int p, const double* X, d
     tc::k_k16_split<<<152 * 16, 256, 0, s>>>(Kh, nkey, nh, nhp, npt, rowlen, er, ec, static_cast<__half*>(hi),
                                               static_cast<__half*>(lo), inv_r, inv_c);
     tc::k_split_rows<<<152 * 16, 256, 0, s>>>(Kh, nkey, nh, nhp, npt, thi, tlo);
-    return cudaGetLastError();
-}
-
-cudaError_t tc_harm_fill(int p, double* M, int nrows, const int4* step, const double2* w, const int* cst,
-                         cudaStream_t s) {
-    if (nrows <= 0 || p < 2) return cudaSuccess;
-    if (!step || !w) return cudaErrorInvalidValue;
-    tc::HarmCst hc;
-    for (int c = 0; c < kMaxOrder + 3; ++c) hc.c[c] = c <= p + 1 ? cst[c] : 0;
-    tc::k_harm_fill<<<(nrows + 3) / 4, 128, 0, s>>>(M, nrows, step, w, hc, p, ncp_of(p), nharm_of(p));
     return cudaGetLastError();
 }
 

@@ -126,10 +126,6 @@ struct TCGArgs {
     int nbox;                 // boxes of the tree (the bound of the checked build's index checks)
 };
 
-// the multipoles' coefficients of z exponent >= 2 from their free ones, in place (FP64 rows of
-// ncp doubles, harmonic basis; step, w and cst as for tc_harm_expand, w in FP64)
-cudaError_t tc_harm_fill(int p, double* M, int nrows, const int4* step, const double2* w, const int* cst,
-                         cudaStream_t s);
 
 int tc_npt(int p);  // rows of the split matrix tables (nc padded to the MMA N granule)
 int tc_rowlen16(int p);  // F16 operand row length: ncoef rounded up to 16

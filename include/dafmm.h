@@ -94,6 +94,10 @@ size_t dafmm_bytes_in_use(const dafmm_ctx* ctx);
  *                 Rokhlin: V (M2L), U (P2P), W (M2P) and X (P2L).
  * Box membership: k = floor((x - x0) * 2^21 / size), clamped to [0, 2^21), per axis; a box
  * of level l holds the particles whose k >> (21 - l) equal its integer coordinates.
+ * Ordering: the call returns once the host arrays have been copied (they may then be reused).
+ * A pooled context building a uniform tree from host arrays leaves the rest of the build in
+ * flight on `stream`; every later call on the tree (on any stream) is ordered after it.
+ * Otherwise the call returns with the tree built. 
  * Errors: DAFMM_ERR_INVALID_ARG for n < 0, missing arrays, max_leaf < 1 on an adaptive
  * tree, depth > 7 or a bad domain; DAFMM_ERR_OVER_BUDGET when the context's budget or the
  * device runs out of memory. */

@@ -1470,6 +1470,22 @@ const OrderOps* order_ops(int p) {
 }
 }  // namespace dafmm
 
+int tree_ready(dafmm_tree* t, cudaStream_t s) {
+    if (!t->built) return DAFMM_OK;
+    dafmm_ctx* c = t->ctx;
+    const cudaError_t q = cudaEventQuery(t->built);
+    if (q == cudaErrorNotReady) {
+        CK(c, cudaStreamWaitEvent(s, t->built, 0), "wait for the tree build");
+        return DAFMM_OK;
+    }
+    // the build has ended: its scratch returns to the pool
+    for (const auto& d : t->deferred) dev_free(c, d.first, d.second);
+    t->deferred.clear();
+    cudaEventDestroy(t->built);
+    t->built = nullptr;
+    return q == cudaSuccess ? DAFMM_OK : cuda_fail(c, q, "tree build");
+}
+
 // ================================ C ABI =======================================================
 extern "C" {
 
@@ -1531,6 +1547,7 @@ void dafmm_destroy(dafmm_ctx* c) {
     for (int p = 0; p <= kMaxOrder; ++p) free_order(c, c->ord[p]);
     for (int k = 0; k < 8; ++k)
         if (c->ev[k]) cudaEventDestroy(c->ev[k]);
+    if (c->ev_in) cudaEventDestroy(c->ev_in);
     dev_free(c, c->d_err, sizeof(int));
     if (c->arena_base) cudaFree(c->arena_base);
     delete c;
@@ -1560,6 +1577,13 @@ int dafmm_build_tree(dafmm_ctx* c, const double* xyz, const double* q, int64_t n
     if ((rc = stage_in(c, q, (size_t)n * sizeof(double), s, sq))) return rc;
     const double* dxyz = (const double*)sx.dev;
     const double* dq = (const double*)sq.dev;
+    // a pooled context builds a uniform tree from host inputs asynchronously (below); the end
+    // of the input copies is marked for it
+    const bool async_build = c->arena_base && sx.owned && sq.owned && uniform_depth >= 0;
+    if (async_build) {
+        if (!c->ev_in) CK(c, cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming), "event");
+        CK(c, cudaEventRecord(c->ev_in, s), "event");
+    }
 
     dafmm_tree* t = new dafmm_tree();
     t->ctx = c;
@@ -1651,6 +1675,32 @@ int dafmm_build_tree(dafmm_ctx* c, const double* xyz, const double* q, int64_t n
     if (e == cudaSuccess)
         e = launch_gather_uniform(dxyz, dq, t->perm, n, keys, make_view(t), t->x, t->y, t->z, t->q, t->xq,
                                   t->leaf_start, s);
+    if (async_build && e == cudaSuccess) {
+        // pooled context, host inputs (staged into the pool): the build stays in flight on its
+        // stream.  An event marks its end (the tree's later users wait for it, tree_ready), its
+        // scratch and staging go back to the pool once it has completed, and the largest leaf is
+        // read back only when asked for.  The caller's host arrays may be reused once this
+        // returns: their copies are waited for.
+        e = cudaEventCreateWithFlags(&t->built, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventRecord(t->built, s);
+        if (e == cudaSuccess) e = cudaEventSynchronize(c->ev_in);
+        if (e == cudaSuccess) {
+            t->deferred.push_back({keys, N * sizeof(uint64_t)});
+            t->deferred.push_back({tmp, tmpb});
+            for (Staged* st : {&sx, &sq})
+                if (st->owned) {
+                    t->deferred.push_back({st->dev, st->bytes});
+                    st->owned = false;
+                }
+            t->max_per_leaf = -1;
+            c->trees.push_back(t);
+            *out = t;
+            return DAFMM_OK;
+        }
+        if (t->built) cudaEventDestroy(t->built);
+        t->built = nullptr;
+        cudaStreamSynchronize(s);  // nothing may still use the scratch freed below
+    }
     // the largest leaf (for the caller's information)
     std::vector<int> ls((size_t)t->nleaf + 1);
     if (e == cudaSuccess)
@@ -1739,6 +1789,11 @@ int dafmm_tree_free(dafmm_tree* t) {
     if (!t) return DAFMM_ERR_INVALID_ARG;
     dafmm_ctx* c = t->ctx;
     cudaSetDevice(c->device);
+    // (the work that uses the tree, its build included, has completed: the caller's contract)
+    for (const auto& d : t->deferred) dev_free(c, d.first, d.second);
+    t->deferred.clear();
+    if (t->built) cudaEventDestroy(t->built);
+    t->built = nullptr;
     free_expansions(t);
     const size_t N = (size_t)t->n;
     dev_free(c, t->x, N * sizeof(double));
@@ -1786,6 +1841,17 @@ int dafmm_tree_info(const dafmm_tree* t, int64_t* info, double* domain4) {
             for (int d = 0; d < 4; ++d) domain4[d] = t->dom[d];
         return DAFMM_OK;
     }
+    if (t->max_per_leaf < 0) {  // the asynchronous build's largest leaf, read back once
+        dafmm_tree* tm = const_cast<dafmm_tree*>(t);
+        if (cudaSetDevice(t->ctx->device) != cudaSuccess || (t->built && cudaEventSynchronize(t->built) != cudaSuccess))
+            return DAFMM_ERR_CUDA;
+        std::vector<int> ls((size_t)t->nleaf + 1);
+        if (cudaMemcpy(ls.data(), t->leaf_start, ls.size() * sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+            return DAFMM_ERR_CUDA;
+        int mx = 0;
+        for (int b = 0; b < t->nleaf; ++b) mx = std::max(mx, ls[b + 1] - ls[b]);
+        tm->max_per_leaf = mx;
+    }
     info[0] = t->n;
     info[1] = t->depth;
     info[2] = t->nleaf;
@@ -1811,10 +1877,11 @@ int dafmm_eval(dafmm_tree* t, int order, double theta, int precision, double* ph
         return fail(c, DAFMM_ERR_INVALID_ARG, "precision");
     CK(c, cudaSetDevice(c->device), "cudaSetDevice");
     cudaStream_t s = (cudaStream_t)stream;
+    int rc;
+    if ((rc = tree_ready(t, s))) return rc;
     if (t->n == 0) return DAFMM_OK;
     const OrderOps* ops = order_ops(order);
     const bool far = t->depth >= 2;
-    int rc;
     if ((rc = ensure_order(c, order, s, far))) return rc;
     if (far && (rc = ensure_expansions(t, order, s))) return rc;
     // outputs
@@ -2121,6 +2188,7 @@ int dafmm_graph_create(dafmm_tree* t, int order, int precision, double* phi, dou
     int rc = dafmm_eval(t, order, 1.0, precision, phi, field, stream);
     if (rc) return rc;
     CK(c, cudaStreamSynchronize(s), "graph warm-up");
+    if ((rc = tree_ready(t, s))) return rc;  // (the build has completed: no wait is captured)
     cudaStream_t cs = s;
     if (!cs) CK(c, cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking), "capture stream");
     const bool prof = c->profile;

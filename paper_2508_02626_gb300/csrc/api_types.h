@@ -5,6 +5,7 @@
 #include <math.h>
 
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "internal.h"
@@ -21,6 +22,7 @@ struct dafmm_ctx {
     // profiling: events at the phase boundaries of the last evaluation
     bool profile = false;
     cudaEvent_t ev[8] = {};
+    cudaEvent_t ev_in = nullptr;  // end of a build's input copies (asynchronous uniform builds)
     int last_launches = 0;
     bool have_profile = false;
     int m2l_kernel = 0;       // 0 tensor cores, 1 SIMT
@@ -64,7 +66,7 @@ struct dafmm_tree {
     double dom[4] = {0, 0, 0, 1};
     int depth = 0;
     int nleaf = 1;
-    int max_per_leaf = 0;
+    int max_per_leaf = 0;           // -1: not read back yet (the asynchronous uniform build)
     double *x = nullptr, *y = nullptr, *z = nullptr, *q = nullptr;
     float4* xq = nullptr;  // 2 * xq_n4 float4s: FP32 records, then their remainders
     size_t xq_n4 = 0;      // float4s of one half of xq
@@ -73,6 +75,10 @@ struct dafmm_tree {
     Expansions ex;
     double* out_scratch = nullptr;  // device outputs when the caller passes host buffers
     size_t out_scratch_bytes = 0;
+    // a uniform tree built asynchronously (pooled contexts): `built` completes with the build
+    // on its stream; the build's scratch (`deferred`) goes back to the pool once it has
+    cudaEvent_t built = nullptr;
+    std::vector<std::pair<void*, size_t>> deferred;
     // adaptive trees (boxes breadth-first; see tree_adaptive.h)
     bool adaptive = false;
     int nbox = 1, maxlev = 0, cap = 0, max_leaf = 0;
@@ -136,3 +142,7 @@ namespace dafmm {
 int ctx_alloc(dafmm_ctx* c, void** p, size_t bytes, const char* what);
 void ctx_free(dafmm_ctx* c, void* p, size_t bytes);
 }  // namespace dafmm
+
+// the uniform tree's build (if still asynchronous) ordered before work on stream s; the build's
+// scratch is returned once the build has completed.  Returns a DAFMM code.
+int tree_ready(dafmm_tree* t, cudaStream_t s);

@@ -161,8 +161,9 @@ extern "C" int dafmm_eval_noalloc(dafmm_tree* t, int order, double* phi, double*
     if (cudaSetDevice(c->device) != cudaSuccess) return set_err(c, DAFMM_ERR_CUDA, "cudaSetDevice");
     if (!device_or_null(phi) || !device_or_null(field))
         return set_err(c, DAFMM_ERR_INVALID_ARG, "dafmm_eval_noalloc: outputs must be device memory");
-    if (t->n == 0) return DAFMM_OK;
     cudaStream_t s = (cudaStream_t)stream;
+    if (tree_ready(t, s) != DAFMM_OK) return set_err(c, DAFMM_ERR_CUDA, "dafmm_eval_noalloc: tree build");
+    if (t->n == 0) return DAFMM_OK;
     const OrderOps* ops = order_ops(order);
     const int nc = ops->nc, ncp = ops->ncp;
     const bool far = t->depth >= 2;

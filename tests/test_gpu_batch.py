@@ -249,3 +249,59 @@ def test_autotuner_picks_and_caches(ctx, tmp_path):
         assert r2["cached"] and r2["max_leaf"] == r1["max_leaf"] and r2["leaf_warps"] == r1["leaf_warps"]
     finally:
         B.dafmm_set_option(ctx.h, B.DAFMM_OPT_LEAF_WARPS, 4)
+
+
+def test_pooled_uniform_build_from_host_arrays():
+    """A pooled context builds a uniform tree from host arrays asynchronously: the call returns
+    once the arrays are copied, the rest of the build stays in flight on its stream, and every
+    later call on the tree is ordered after it.  Checked against an ordinary context's
+    synchronous build, bit for bit: evaluation right after the build on the build's stream, on
+    another stream, and through pageable and pinned host outputs; the tree's information
+    (largest leaf, read back on demand) right after the build; the host input arrays
+    overwritten as soon as the build returns; a tree freed without evaluation; and the pool
+    back to its baseline after every cycle."""
+    n, depth, p = 60_000, 4, 6
+    x, q = W.uniform(n, seed=77)
+    dom = W.UNIT_CUBE
+    plain = B.Context(0)
+    t = plain.build_tree(x, q, domain=dom, uniform_depth=depth)
+    info_ref = t.info()
+    ref_phi, ref_E = np.zeros(n), np.zeros((n, 3))
+    t.eval(p, ref_phi, ref_E, precision="fp32")
+    t.free()
+    plain.close()
+    pool = B.Context(0, pool_bytes=1 << 30)
+    side = torch.cuda.Stream()
+    xp, qp = torch.from_numpy(x.copy()).pin_memory(), torch.from_numpy(q.copy()).pin_memory()
+    php = torch.zeros(n, dtype=torch.float64).pin_memory()
+    Ep = torch.zeros((n, 3), dtype=torch.float64).pin_memory()
+    base = None
+    for it in range(4):
+        xp.copy_(torch.from_numpy(x))
+        qp.copy_(torch.from_numpy(q))
+        t = pool.build_tree(xp, qp, domain=dom, uniform_depth=depth, stream=side if it % 2 else None)
+        xp.fill_(float("nan"))  # the host arrays are free once the call returns
+        qp.fill_(float("nan"))
+        if it == 0:
+            info = t.info()
+            assert all(info[k] == info_ref[k] for k in info_ref if k != "domain"), (info, info_ref)
+        if it == 2:  # freed without evaluation
+            t.free()
+            torch.cuda.synchronize()
+            continue
+        if it == 3:  # evaluated on another stream than the build's
+            other = torch.cuda.Stream()
+            phi = np.zeros(n)
+            E = np.zeros((n, 3))
+            t.eval(p, phi, E, precision="fp32", stream=other)
+        else:
+            t.eval(p, php, Ep, precision="fp32", stream=side if it % 2 else None)
+            phi, E = php.numpy().copy(), Ep.numpy().copy()
+        assert np.array_equal(phi, ref_phi), it
+        assert np.array_equal(E, ref_E), it
+        t.free()
+        torch.cuda.synchronize()
+        used = B.dafmm_bytes_in_use(pool.h)
+        base = used if base is None else base
+        assert used == base, (it, used, base)
+    pool.close()

@@ -33,18 +33,32 @@ UNIT = "particles/s"
 # hash to the recorded value, reported as null otherwise
 M2L_TRAFFIC = {"fp32": (25.4e6, "eef784baa41f372b")}
 M2L_SOURCES = ("paper_2508_02626_gb300/csrc/tc_common.cuh", "paper_2508_02626_gb300/csrc/tc_ops.cu")
+# the same for the near-field kernel k_leaf<float> (its source: fmm_order.cuh)
+LEAF_TRAFFIC = {"fp32": (117.9e6, "4aaa03a736a0c822")}
+LEAF_SOURCES = ("paper_2508_02626_gb300/csrc/fmm_order.cuh",)
+
+
+def sources_hash(files):
+    import hashlib
+    h = hashlib.sha1()
+    for f in files:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
 
 
 def m2l_traffic(precision):
-    import hashlib
     rec = M2L_TRAFFIC.get(precision)
     if rec is None:
         return None
-    h = hashlib.sha1()
-    for f in M2L_SOURCES:
-        with open(os.path.join(ROOT, f), "rb") as fh:
-            h.update(fh.read())
-    return rec[0] if h.hexdigest()[:16] == rec[1] else None
+    return rec[0] if sources_hash(M2L_SOURCES) == rec[1] else None
+
+
+def leaf_traffic(precision):
+    rec = LEAF_TRAFFIC.get(precision)
+    if rec is None or rec[0] is None:
+        return None
+    return rec[0] if sources_hash(LEAF_SOURCES) == rec[1] else None
 
 
 def load_peaks():
@@ -522,6 +536,14 @@ def run_ours(args, rank, world):
                 "executed_frac": None if executed is None else round(executed / peak, 4),
                 "peak_source": peak_note}
 
+    near_roof = None
+    if args.precision != "fp64":
+        near_roof = near_field_roofline(x, dom, depth, ph["leaf"], peaks.get("sm_max_mhz", 2070.0), measured_alu)
+        if "error" in near_roof:
+            near_roof = None
+        else:
+            near_roof["traffic"] = leaf_traffic(args.precision)
+            near_roof["traffic_unit"] = "bytes per launch"
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -533,10 +555,10 @@ def run_ours(args, rank, world):
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "phases_ms": {k: round(v, 4) for k, v in ph.items() if k != "launches"},
         "gpu_launches": int(ph["launches"]) * args.steps,
-        "roofline": roofline,
-        "roofline_near_field": (near_field_roofline(x, dom, depth, ph["leaf"], peaks.get("sm_max_mhz", 2070.0),
-                                                    measured_alu)
-                                if args.precision != "fp64" else None),
+        # `roofline` describes the step's dominant kernel: the near field (k_leaf, about 55% of
+        # the FP32 step); the M2L contraction's figures follow under roofline_m2l
+        "roofline": near_roof if near_roof is not None else roofline,
+        "roofline_m2l": roofline if near_roof is not None else None,
         "peaks": probes,
         "clocks": ck,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": n * 4 * 8,

@@ -977,7 +977,7 @@ __device__ __forceinline__ void two_sum_add(float& hi, float& lo, float v) {
     hi = s;
 }
 
-// compensated (hi, lo) sums of the near field: FP32 partial sums over at most 64 sources are
+// compensated (hi, lo) sums of the near field: FP32 partial sums over at most 128 sources are
 // folded into them, so that long neighbour lists keep FP32-level error
 struct CompSums {
     float ph = 0.f, pl = 0.f, xh = 0.f, xl = 0.f, yh = 0.f, yl = 0.f, zh = 0.f, zl = 0.f;
@@ -1051,13 +1051,17 @@ constexpr int kLeafSeg = DAFMM_LEAF_SEG;
 #define DAFMM_LEAF_MINB 8
 #endif
 
+// list pairs (two sources each) per FP32 partial sum of the near field: 64 pairs, 128 sources
+// (64 in each packed half) -- one fold per list segment of kLeafSeg = 128 records
+constexpr int kFoldPairs = 64;
+
 // the pairwise sums of one segment of the list: pairs [pa, pe) for this lane's target, those
-// below pown from the target's own leaf (guarded), FP32 partial sums over at most 64 sources
-// folded into the compensated sums
+// below pown from the target's own leaf (guarded), FP32 partial sums over at most kFoldPairs
+// pairs folded into the compensated sums
 __device__ __forceinline__ void p2p_segment(const float4* __restrict__ buf, int pa, int pe, int pown, float2 tx,
                                             float2 ty, float2 tz, float2 lx, float2 ly, float2 lz, CompSums& cs) {
-    for (int pb = pa; pb < pe; pb += 32) {
-        const int pc = min(pe, pb + 32);
+    for (int pb = pa; pb < pe; pb += kFoldPairs) {
+        const int pc = min(pe, pb + kFoldPairs);
         const int pm = max(pb, min(pc, pown));
         float2 P = make_float2(0.f, 0.f), X = P, Y = P, Z = P;
         if (pb < pm) p2p_pairs<true>(buf, pb, pm, tx, ty, tz, lx, ly, lz, P, X, Y, Z);

@@ -2,7 +2,7 @@
 with the kernels).
 
 Each lane adds its pair terms in FP32, two sources per packed instruction, so two running
-halves per group of at most 64 sources.  The group's sum is folded into a compensated
+halves per group of at most 128 sources (one group per 128-record list segment).  The group's sum is folded into a compensated
 (hi, lo) pair by an error-free two-sum.  Against the exact (FP64) sum of the same FP32 terms,
 the result's error stays within a few FP32 units of sum |term|, whatever the list length:
 27 neighbour leaves of ~30 particles, 27 leaves of 512, or 1e5 sources.  A plain FP32
@@ -30,7 +30,7 @@ def two_sum_add(hi, lo, v):
     return s, lo
 
 
-def near_field_sum(v, group=64):
+def near_field_sum(v, group=128):
     hi = lo = F(0)
     for g0 in range(0, len(v), group):
         a = b = F(0)  # the two halves of the packed sums

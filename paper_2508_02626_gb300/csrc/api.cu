@@ -1958,7 +1958,16 @@ int dafmm_eval(dafmm_tree* t, int order, double theta, int precision, double* ph
             a.num_sms = c->num_sms;
             return a;
         };
-        CK(c, ops->p2m(tv, prec_m, ex.M[L], s), "P2M");
+        // the FP32 harmonic P2M also writes the finest level's F16 split (its warp holds each row)
+        const bool p2m_f16 = f16_m2l && f32_mult && harm_m;
+        F16Rows fr;
+        if (p2m_f16) {
+            fr.hi = ex.Mh16[L];
+            fr.lo = ex.Ml16[L];
+            fr.inv = ex.Minv[L];
+            fr.rowlen = tc_rowlen16h(order);
+        }
+        CK(c, ops->p2m(tv, prec_m, ex.M[L], p2m_f16 ? &fr : nullptr, s), "P2M");
         ++launches;
         mark(1);
         if (tc_m2m) {
@@ -1990,15 +1999,18 @@ int dafmm_eval(dafmm_tree* t, int order, double theta, int precision, double* ph
             int nrows[8];
             void *hi[8], *lo[8];
             float* inv[8];
-            for (int l = 2; l <= L; ++l) {
+            const int lsplit = p2m_f16 ? L - 1 : L;  // (the P2M split the finest level)
+            for (int l = 2; l <= lsplit; ++l) {
                 src[l - 2] = ex.M[l];
                 nrows[l - 2] = (int)level_boxes(l);
                 hi[l - 2] = ex.Mh16[l];
                 lo[l - 2] = ex.Ml16[l];
                 inv[l - 2] = ex.Minv[l];
             }
-            CK(c, tc_split_f16_multi(L - 1, src, nrows, hi, lo, inv, order, s, f32_mult, harm), "split");
-            ++launches;
+            if (lsplit >= 2) {
+                CK(c, tc_split_f16_multi(lsplit - 1, src, nrows, hi, lo, inv, order, s, f32_mult, harm), "split");
+                ++launches;
+            }
         } else if (precision != DAFMM_FP64 && !fff && !(tc_m2m && tc_m2l))
             for (int l = 2; l <= L; ++l) {
                 const size_t cnt = level_boxes(l) * od.ncp;

@@ -18,6 +18,7 @@
 //   L2L  (Eq. 7)  k_l2l       32 parents per block, 8 child tables by sign flips
 //   L2P + P2P     k_leaf      one warp per target leaf: pairwise sum over the 27 neighbour
 //                             leaves and the generated L2P of the leaf's local expansion
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <type_traits>
@@ -117,8 +118,10 @@ __device__ __forceinline__ void warp_row_f32(const float* __restrict__ row, floa
 // H: the harmonic basis -- the generated code emits only the (p + 1)^2 free coefficients
 // (z exponent <= 1), which are summed and written at their layout positions; the others are
 // not computed (the multipole's homogeneous parts are harmonic, Eq. 2, so they are implied).
+// f16 (H, FP32 rows): the row's F16 split as well, as tc_split_f16_multi makes it -- the warp
+// holds the whole row, so its largest magnitude is one warp reduction away.
 template <class T, bool H = false>
-__global__ void k_p2m(TreeView tv, double* __restrict__ M, int rows32) {
+__global__ void k_p2m(TreeView tv, double* __restrict__ M, int rows32, F16Rows f16) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* sm = reinterpret_cast<T*>(smem_raw) + threadIdx.y * (32 * 33);
     const int lane = threadIdx.x;
@@ -164,6 +167,31 @@ __global__ void k_p2m(TreeView tv, double* __restrict__ M, int rows32) {
         for (int j = 0; j < NJ; ++j) {
             const int k = lane + 32 * j;
             if (k < NO) Mf[H ? harm_full_index(k) : k] = (float)acc[j];
+        }
+        if constexpr (H && sizeof(T) == 4) {
+            if (f16.hi) {
+                float mx = 0.f;
+#pragma unroll
+                for (int j = 0; j < NJ; ++j)
+                    if (lane + 32 * j < NO) mx = fmaxf(mx, fabsf((float)acc[j]));
+                for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+                int e = 0;
+                if (mx > 0.f) frexpf(mx, &e);  // mx = f 2^e, f in [0.5, 1)
+                e = e < -120 ? -120 : (e > 120 ? 120 : e);
+                const float sc = ldexpf(1.f, -e);
+                __half* hi = static_cast<__half*>(f16.hi) + (size_t)leaf * f16.rowlen;
+                __half* lo = static_cast<__half*>(f16.lo) + (size_t)leaf * f16.rowlen;
+#pragma unroll
+                for (int j = 0; j < NJ; ++j) {
+                    const int k = lane + 32 * j;
+                    if (k >= f16.rowlen) break;
+                    const float f = (k < NO ? (float)acc[j] : 0.f) * sc;
+                    const __half h = __float2half_rn(f);
+                    hi[k] = h;
+                    lo[k] = __float2half_rn(f - __half2float(h));
+                }
+                if (lane == 0) f16.inv[leaf] = ldexpf(1.f, e);
+            }
         }
         return;
     }
@@ -1878,13 +1906,18 @@ static cudaError_t set_smem(K kernel, size_t bytes) {
     return cudaSuccess;
 }
 
-static cudaError_t p2m_launch(const TreeView& tv, int prec, double* M, cudaStream_t s) {
+static cudaError_t p2m_launch(const TreeView& tv, int prec, double* M, const F16Rows* f16, cudaStream_t s) {
     if (tv.nleaf == 0) return cudaSuccess;
+    const F16Rows fr = f16 ? *f16 : F16Rows{};
     const int rows32 = (prec & kRowsF32) ? 1 : 0;
     const bool harm = (prec & kRowsHarm) != 0;
     prec &= ~(kRowsF32 | kRowsHarm);
     const bool f64 = prec == DAFMM_FP64, fff = prec == DAFMM_FF;
     if (harm && (f64 || fff)) return cudaErrorInvalidValue;  // (the FP32 kernel only)
+    // the fused F16 split: FP32 harmonic rows, every padded row position held by the warp
+    if (fr.hi && (!harm || !rows32 || !fr.lo || !fr.inv || fr.rowlen < nharm_of(P) ||
+                  fr.rowlen > 32 * ((nharm_of(P) + 31) / 32)))
+        return cudaErrorInvalidValue;
     const size_t per_warp = (size_t)32 * 33 * (f64 || fff ? 8 : 4);
     int wpb = (int)((96 * 1024) / per_warp);
     wpb = wpb < 1 ? 1 : (wpb > 4 ? 4 : wpb);
@@ -1893,16 +1926,16 @@ static cudaError_t p2m_launch(const TreeView& tv, int prec, double* M, cudaStrea
     cudaError_t e;
     if (f64) {
         if ((e = set_smem(k_p2m<double>, smem)) != cudaSuccess) return e;
-        k_p2m<double><<<grd, blk, smem, s>>>(tv, M, 0);
+        k_p2m<double><<<grd, blk, smem, s>>>(tv, M, 0, F16Rows{});
     } else if (fff) {
         if ((e = set_smem(k_p2m<ff>, smem)) != cudaSuccess) return e;
-        k_p2m<ff><<<grd, blk, smem, s>>>(tv, M, 0);
+        k_p2m<ff><<<grd, blk, smem, s>>>(tv, M, 0, F16Rows{});
     } else if (harm) {
         if ((e = set_smem(k_p2m<float, true>, smem)) != cudaSuccess) return e;
-        k_p2m<float, true><<<grd, blk, smem, s>>>(tv, M, rows32);
+        k_p2m<float, true><<<grd, blk, smem, s>>>(tv, M, rows32, fr);
     } else {
         if ((e = set_smem(k_p2m<float>, smem)) != cudaSuccess) return e;
-        k_p2m<float><<<grd, blk, smem, s>>>(tv, M, rows32);
+        k_p2m<float><<<grd, blk, smem, s>>>(tv, M, rows32, F16Rows{});
     }
     return cudaGetLastError();
 }

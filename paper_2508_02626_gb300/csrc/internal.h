@@ -176,11 +176,22 @@ constexpr int kM2LHarm = 0x400;  // with kM2LRot: the rotation in its harmonic f
 // (adaptive trees fill them in afterwards, tc_harm_fill, for the M2P)
 constexpr int kRowsHarm = 0x800;
 
+// F16 split rows written by the P2M itself (the FP32 mode's harmonic basis, finest level): row
+// b of hi and lo holds rowlen halves (the free coefficients scaled by 2^-e, e the exponent of
+// the row's largest magnitude, zero-padded), inv[b] = 2^e -- what tc_split_f16_multi writes
+struct F16Rows {
+    void* hi = nullptr;
+    void* lo = nullptr;
+    float* inv = nullptr;
+    int rowlen = 0;
+};
+
 struct OrderOps {
     int p, nc, ncp;
     HostShiftTable m2m, l2l, m2mh;
     // precision argument: DAFMM_FP64 / DAFMM_MIXED / DAFMM_FP32
-    cudaError_t (*p2m)(const TreeView&, int prec, double* Mleaf, cudaStream_t);
+    // f16 (optional, FP32 harmonic rows only): the F16 split of the rows, written as well
+    cudaError_t (*p2m)(const TreeView&, int prec, double* Mleaf, const F16Rows* f16, cudaStream_t);
     cudaError_t (*m2m_level)(const OrderData&, int prec, int lchild, const double* Mc, double* Mp,
                              cudaStream_t);
     cudaError_t (*l2l_level)(const OrderData&, int prec, int lchild, const double* Lp, double* Lc,

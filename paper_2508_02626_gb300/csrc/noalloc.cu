@@ -243,7 +243,7 @@ extern "C" int dafmm_eval_noalloc(dafmm_tree* t, int order, double* phi, double*
     const int Ld = t->depth;
     if (far) {
         if (e == cudaSuccess) e = ops->kgen(od, nullptr, kNumKeys, s);
-        if (e == cudaSuccess) e = ops->p2m(tv, DAFMM_FP64, M[Ld], s);
+        if (e == cudaSuccess) e = ops->p2m(tv, DAFMM_FP64, M[Ld], nullptr, s);
         for (int lc = Ld; lc >= 3 && e == cudaSuccess; --lc) e = ops->m2m_level(od, DAFMM_FP64, lc, M[lc], M[lc - 1], s);
         for (int l = 2; l <= Ld && e == cudaSuccess; ++l)
             e = ops->m2l_level(od, DAFMM_FP64, l, M[l], nullptr, L[l], 1.0 / ldexp(t->dom[3], -l), s);

@@ -301,7 +301,9 @@ int dafmm_eval_noalloc(dafmm_tree* tree, int order, double* phi, double* field, 
 #define DAFMM_PEAK_MMA_F16 5
 int dafmm_probe_peak(int device, int kind, double* rate, double* ms);
 
-/* Device bytes an evaluation of a tree with these parameters needs (an upper estimate). */
+/* Device bytes an evaluation of a tree with these parameters needs (an upper estimate; for a
+ * uniform tree it includes the build's scratch and the staging of host input arrays, which a
+ * pooled context's asynchronous build keeps until the build has completed). */
 size_t dafmm_footprint(int64_t n, int order, int uniform_depth, int max_leaf, int precision);
 
 /* ---- single-operator batches (the paper's per-operator verification, Sec. 3) --------

@@ -2344,6 +2344,9 @@ size_t dafmm_footprint(int64_t n, int order, int uniform_depth, int max_leaf, in
     for (int l = 2; l <= depth; ++l) b += level_boxes(l) * ncp * (8 + 8 + 4);
     b += (size_t)kNumKeys * nc * ncp * 12;
     b += (size_t)n * 12 + radix_sort_temp_bytes(n);  // build-time scratch
+    // the staging of host input arrays (xyz and q): a pooled context's asynchronous build holds
+    // it, with the scratch above, until the build has completed
+    b += (size_t)n * 32;
     return b;
 }
 

@@ -51,6 +51,11 @@ def test_footprint_is_monotone_and_rejects_bad_order():
     c = binding.dafmm_footprint(1_000_000, 10, 5)
     assert 0 < a < b < c
     assert binding.dafmm_footprint(1000, 11, 3) == 0
+    # a uniform tree's estimate covers what its build holds: particles (FP64 SoA, FP32 records
+    # and remainders, permutation: 68 B each), sort keys (8 B) and the staged host inputs
+    # (32 B) -- at least 108 B per particle beyond the expansions and tables
+    n = 1_000_000
+    assert binding.dafmm_footprint(n, 8, 5) - binding.dafmm_footprint(0, 8, 5) >= 108 * n
 
 
 def test_no_device_is_reported_not_crashed():
